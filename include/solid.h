@@ -1,0 +1,227 @@
+/*
+ * solid.h -- C-ABI of the GB300 solidification / macro-segregation time step.
+ *
+ * One time step of the operator-splitting, fully decoupled, matrix-based
+ * scheme (Algorithm 1, Sec. 4 of Feng, Chen, Yu & Sun, arXiv 2303.10783):
+ *   1 intermediate velocity u* from the semi-implicit momentum equation (Eq. 3.3)
+ *   2 pressure-correction Poisson equation (Eq. 3.4)
+ *   3 velocity projection (Eq. 3.5)
+ *   4 solute transport by the matrix-based technique (Eq. 3.6-3.10)
+ *   5 liquidus from the new mixture concentration (Eq. 3.14)
+ *   6 intermediate temperature T* (first energy split step, Eq. 3.12)
+ *   7 latent-heat correction and liquid fraction from the quadratic lever
+ *     relation (Eq. 3.13, 3.15-3.17)
+ *   8 liquid and solid concentrations (Eq. 3.18-3.19)
+ * on a uniform staggered (MAC) grid (Sec. 3, Eq. 3.20-3.25) with 5/7-point
+ * DIA systems (Sec. 4, Eq. 4.1-4.4). Every step runs in the library's own
+ * CUDA kernels on the case's stream; there is no CPU fallback.
+ *
+ * Conventions
+ *   - Cell arrays hold nx*ny*nz doubles, x fastest, then y, then z.
+ *     Face arrays: u has (nx+1)*ny*nz entries (x-faces), v nx*(ny+1)*nz,
+ *     w nx*ny*(nz+1); faces 0 and n along their own axis are walls.
+ *     2D cases have nz = 1 and no w.
+ *   - The vertical axis is y in 2D and z in 3D; gravity points along minus it.
+ *   - All walls are rigid, no-slip and impermeable to solute; each wall is
+ *     adiabatic or Robin-cooled (heat flux U (T - T_ext), U = 1/(1/h + dx/(2k))).
+ *   - Device memory: the caller allocates one workspace of ss_workspace_bytes()
+ *     bytes (any device allocator, e.g. torch) and keeps it alive until
+ *     ss_destroy(); the library carves every field, DIA plane and solver
+ *     vector out of it and calls no cudaMalloc for case state. Host-side
+ *     case bookkeeping is malloc'd by the library.
+ *   - Streams: every device operation of a case is enqueued on the stream
+ *     given to ss_create_case (a cudaStream_t passed as void*; NULL = legacy
+ *     default stream). Calls that return data synchronise that stream.
+ *   - Errors: every call returns an ss_status and never exits or traps.
+ *     ss_last_error() gives a message for the calling thread. Solver
+ *     outcomes are sticky on the device: a solve that reaches its iteration
+ *     cap keeps its last iterate and records SS_ENOTCONV; a non-finite
+ *     residual records SS_ENAN; ss_get_stats() / ss_sync() report and clear
+ *     them.
+ */
+#ifndef SOLID_H
+#define SOLID_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ss_case ss_case;
+
+typedef enum {
+  SS_OK = 0,
+  SS_EINVAL = 1,    /* bad argument (NULL pointer, bad size, bad enum) */
+  SS_ENOMEM = 2,    /* workspace too small */
+  SS_ENOTCONV = 3,  /* a linear solve hit its iteration cap */
+  SS_ENAN = 4,      /* a non-finite value appeared in a solve */
+  SS_ECUDA = 5,     /* a CUDA runtime call failed (message in ss_last_error) */
+  SS_ESTATE = 6,    /* call not allowed in the current state */
+  SS_ETIMEOUT = 7   /* a device-side wait gave up (kernel returned early) */
+} ss_status;
+
+enum { SS_FP64 = 0, SS_MIXED = 1 };                  /* ss_grid.precision */
+enum { SS_ADIABATIC = 0, SS_ROBIN = 1 };             /* ss_bc.thermal */
+enum { SS_XM = 0, SS_XP = 1, SS_YM = 2, SS_YP = 3, SS_ZM = 4, SS_ZP = 5 };  /* walls */
+
+/* Field identifiers: bit i of a mask selects field i; pointer arrays passed
+ * to ss_get_fields / ss_set_fields are indexed by these ids (SS_NFIELDS long). */
+enum { SS_U = 0, SS_V = 1, SS_W = 2, SS_P = 3, SS_T = 4, SS_C = 5, SS_GL = 6, SS_CL = 7, SS_CS = 8,
+       SS_NFIELDS = 9 };
+
+/* Linear systems of one step, for the stage-level entry points. */
+enum { SS_SYS_U = 0, SS_SYS_V = 1, SS_SYS_W = 2, SS_SYS_P = 3, SS_SYS_C = 4, SS_SYS_T = 5, SS_NSYS = 6 };
+
+/* Grid, time step and solver controls. */
+typedef struct {
+  int dim;                   /* 2 or 3 */
+  int nx, ny, nz;            /* cells per axis (nz is forced to 1 in 2D); each >= 1 */
+  double lx, ly, lz;         /* domain extents [m] (lz ignored in 2D) */
+  double dt;                 /* time step [s] */
+  int precision;             /* SS_FP64, or SS_MIXED: FP32 inner Krylov iterations
+                                inside FP64 iterative refinement */
+  double tol_p;              /* relative 2-norm residual tolerance, pressure solve */
+  double tol_t;              /* same for the transport solves (u, v, w, C, T) */
+  int max_it_p, max_it_t;    /* iteration caps (>= 1) */
+} ss_grid;
+
+/* Alloy and model data (Table 1 style). C is the mass fraction of the
+ * solute-rich species in wt%. */
+typedef struct {
+  double Tm;        /* melting point at C = 0 [K] (Eq. 2.20) */
+  double m;         /* liquidus slope [K/wt%] (< 0) */
+  double kp;        /* partition coefficient, 0 < kp < 1 */
+  double C0;        /* nominal concentration; Boussinesq reference C_ref [wt%] */
+  double rho;       /* density [kg/m^3] */
+  double k;         /* thermal conductivity [W/mK] */
+  double cp;        /* specific heat [J/kgK] */
+  double L;         /* latent heat [J/kg] */
+  double mu;        /* liquid viscosity [Pa s] */
+  double Dl;        /* liquid solute diffusivity [m^2/s] (Eq. 3.7) */
+  double betaT;     /* thermal expansion [1/K] (Eq. 2.9) */
+  double betaC;     /* solutal expansion [1/wt%] (Eq. 2.9) */
+  double K0;        /* Carman-Kozeny prefactor [m^2]: K = K0 g^3/(1-g)^2 (Eq. 2.8) */
+  double Ce;        /* eutectic concentration [wt%]; <= 0 disables the eutectic branch */
+  double gravity;   /* [m/s^2] */
+  double darcy_eps; /* K^{-1} = (1-g)^2 / (K0 (g^3 + darcy_eps)) */
+  double Tref;      /* Boussinesq reference temperature [K] (Eq. 2.9) */
+} ss_alloy;
+
+/* Thermal condition of one wall. */
+typedef struct {
+  int thermal;      /* SS_ADIABATIC or SS_ROBIN */
+  double h;         /* heat transfer coefficient [W/m^2K] (> 0 for Robin) */
+  double Text;      /* external temperature [K] */
+} ss_bc;
+
+/* Per-step diagnostics of the most recent step (or stage call). */
+typedef struct {
+  long long steps;          /* steps completed since creation */
+  int iters[SS_NSYS];       /* iterations of each solve (inner iterations in SS_MIXED) */
+  int refinements[SS_NSYS]; /* FP64 refinement sweeps (SS_MIXED), else 0 */
+  double relres[SS_NSYS];   /* final relative residual of each solve (FP64 residual) */
+  int status;               /* sticky ss_status of the solves since the last read */
+} ss_stats;
+
+/* Stage timing: when profiling is on, the step driver records a CUDA event
+ * pair on the case's stream around every stage; ss_get_profile returns the
+ * accumulated device time per stage (ms) and the number of library kernels
+ * launched per stage since the previous ss_get_profile call (launch counts
+ * are kept whether or not profiling is on). */
+enum { SS_PROF_ASSEMBLE = 0,   /* + SS_SYS_*: assembly of that system */
+       SS_PROF_SOLVE = 6,      /* + SS_SYS_*: its solve */
+       SS_PROF_PROJECT = 12, SS_PROF_LEVER = 13, SS_NPROF = 14 };
+typedef struct {
+  double ms[SS_NPROF];
+  long long launches[SS_NPROF];
+  long long kernels;        /* total library kernel launches */
+  long long iters[SS_NSYS]; /* Krylov iterations summed over the solves of each system */
+} ss_profile;
+
+/* Bytes of device workspace a case of this grid needs (256-byte aligned
+ * start required). Returns SS_EINVAL for a bad grid. */
+ss_status ss_workspace_bytes(const ss_grid* grid, size_t* bytes);
+
+/* Create a case on the current CUDA device. `workspace` is a device pointer
+ * of at least ss_workspace_bytes() bytes, owned by the caller and kept alive
+ * until ss_destroy(). The fields start at u = p = 0 and no alloy; call
+ * ss_set_alloy before stepping. */
+ss_status ss_create_case(const ss_grid* grid, void* workspace, size_t workspace_bytes, void* stream,
+                         ss_case** out);
+
+/* Set the alloy and model data; resets T = Tref, C = C0, u = p = 0 and the
+ * liquid fraction to its equilibrium value (Eq. 3.15). Walls default to
+ * adiabatic. Allowed before the first step only (SS_ESTATE afterwards). */
+ss_status ss_set_alloy(ss_case* c, const ss_alloy* alloy);
+
+/* Set the thermal condition of wall `face` (SS_XM..SS_ZP). Allowed at any time
+ * between steps. */
+ss_status ss_set_boundary(ss_case* c, int face, const ss_bc* bc);
+
+/* Enqueue n time steps (Algorithm 1) on the case's stream and return without
+ * waiting. Launch failures return SS_ECUDA; solver outcomes are sticky (see
+ * ss_sync / ss_get_stats). */
+ss_status ss_step(ss_case* c, int n);
+
+/* Wait for the case's stream; return and clear the sticky solver status. */
+ss_status ss_sync(ss_case* c);
+
+/* Copy the fields selected by `mask` into caller-owned buffers dst[id]
+ * (device pointers if dst_is_device, else host). Synchronises the stream. */
+ss_status ss_get_fields(ss_case* c, unsigned mask, void* const* dst, int dst_is_device);
+
+/* Overwrite the fields selected by `mask` from src[id] (restart, or seeded
+ * initial noise). Other fields are left as they are. */
+ss_status ss_set_fields(ss_case* c, unsigned mask, const void* const* src, int src_is_device);
+
+/* Recompute g_l, C_l and C_s from the current T and C in equilibrium: g_l = 1
+ * at or above the liquidus, else Eq. 3.15 clamped to [0, 1]; C_l by
+ * Eq. 3.18 (capped at C_e), C_s = kp C_l (Eq. 3.19). */
+ss_status ss_equilibrate(ss_case* c);
+
+/* Diagnostics of the last step; synchronises; clears the sticky status. */
+ss_status ss_get_stats(ss_case* c, ss_stats* out);
+
+/* Turn per-stage event timing on (1) or off (0). */
+ss_status ss_set_profiling(ss_case* c, int on);
+
+/* Accumulated stage times and launch counts since the previous call
+ * (synchronises the stream, then resets the accumulators). */
+ss_status ss_get_profile(ss_case* c, ss_profile* out);
+
+/* Destroy the case (synchronises its stream). The workspace is the caller's. */
+ss_status ss_destroy(ss_case* c);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char* ss_last_error(void);
+
+/* ---- Stage-level entry points: each runs one stage of Algorithm 1 on the
+ * case's current fields, exactly as ss_step does, for stage-by-stage checks.
+ *
+ * ss_assemble(c, sys): build the DIA system `sys` from the current fields
+ *   SS_SYS_U/V/W: momentum predictor rows (Eq. 3.3) from u^n, p^n, T^n, C_l^n, g_l^n;
+ *   SS_SYS_P: pressure-correction right-hand side -(rho/dt) div u* (Eq. 3.4),
+ *             mean removed, with u* the last solved momentum components;
+ *   SS_SYS_C: solute system (Eq. 3.10) advected by the current u;
+ *   SS_SYS_T: T* system (Eq. 3.12) advected by the current u.
+ * ss_solve(c, sys): solve the assembled system (initial guess: the current
+ *   field for U/V/W/C/T, 0 for P) into the system's solution vector; returns
+ *   the solve's outcome.
+ * ss_get_system(c, sys, dst, dst_is_device): copy planes and vectors of the
+ *   system into dst[0..8] = P, W, E, S, N, B, T (DIA planes, Eq. 4.1), b
+ *   (right-hand side), x (solution); NULL entries are skipped. SS_SYS_P has
+ *   no planes (matrix-free constant Laplacian): only b and x.
+ * ss_project(c): Eq. 3.5 with the solved u* and p'; p += p'.
+ * ss_lever(c): Eq. 3.13-3.19 treating the current T field as T*, the
+ *   current g_l as g_l^n and the current C as C^{n+1}. */
+ss_status ss_assemble(ss_case* c, int sys);
+ss_status ss_solve(ss_case* c, int sys);
+ss_status ss_get_system(ss_case* c, int sys, void* const* dst, int dst_is_device);
+ss_status ss_project(ss_case* c);
+ss_status ss_lever(ss_case* c);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SOLID_H */

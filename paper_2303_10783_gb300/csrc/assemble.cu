@@ -1,0 +1,400 @@
+// Term-wise assembly of the DIA systems and the pointwise stages of one step.
+//
+//   k_assemble_momentum<A>   rows of the intermediate-velocity system for
+//                            component A (Eq. 3.3 with the momentum form Eq. 2.7)
+//   k_assemble_cells<SOLUTE> solute system (Eq. 3.6-3.10) or T* system (Eq. 3.12)
+//   k_poisson_rhs            -(rho/dt) div u* (Eq. 3.4)
+//   k_project                u^{n+1} = u* - (dt/rho) grad p', p += p' (Eq. 3.5)
+//   k_lever                  latent-heat correction and quadratic lever rule
+//                            (Eq. 3.13-3.19), plus K^{-1} (Eq. 2.8) and A_g
+//                            (Eq. 3.8) for the next step
+//   k_equilibrate            equilibrium g_l, C_l, C_s of given (T, C) (Eq. 3.15, 3.18-3.19)
+//
+// One thread per row, grid-stride. Each row is written once with coalesced
+// stores (consecutive threads own consecutive x). The constant diffusion
+// parts of the stencils (Sec. 4, term-wise strategy) are launch constants;
+// per step only the velocity-, fraction- and field-dependent terms are read.
+//
+// Coefficients follow the vectorised form of Eq. 4.3-4.4: per axis the
+// convection tuple [-max(F_b,0); max(F_f,0) - min(F_b,0); min(F_f,0)]/h and
+// the diffusion tuple [-D_b; D_b + D_f; -D_f]/h^2 (sign of -div(D grad)),
+// where F_b/F_f are the advecting velocities on the back/front faces of the
+// control volume and a neighbour that is not an unknown drops its coupling.
+#include "solid_internal.cuh"
+
+namespace solid {
+namespace {
+
+inline int grid_for(long long n) {
+  long long b = (n + kBlock - 1) / kBlock;
+  if (b > 152LL * 16) b = 152LL * 16;
+  if (b < 1) b = 1;
+  return (int)b;
+}
+
+struct Axes {
+  int n[3];
+  double ih[3], ih2[3];
+};
+
+__device__ __forceinline__ Axes axes_of(const Params& pr) {
+  Axes ax;
+  ax.n[0] = pr.nx; ax.n[1] = pr.ny; ax.n[2] = pr.nz;
+  ax.ih[0] = 1.0 / pr.hx; ax.ih[1] = 1.0 / pr.hy; ax.ih[2] = 1.0 / pr.hz;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) ax.ih2[a] = ax.ih[a] * ax.ih[a];
+  return ax;
+}
+
+// flat index of (i, j, k) in the face array of velocity component d
+__device__ __forceinline__ int fidx(const Params& pr, int d, int i, int j, int k) {
+  const int fx = pr.nx + (d == 0), fy = pr.ny + (d == 1);
+  return i + fx * (j + fy * k);
+}
+
+__device__ __forceinline__ int cidx(const Params& pr, int i, int j, int k) { return i + pr.nx * (j + pr.ny * k); }
+
+__device__ __forceinline__ void write_row(const Sys& s, int r, int dim, double P, const double nbB[3],
+                                          const double nbF[3], double b) {
+  s.a.P[r] = P;
+  s.a.W[r] = nbB[0];
+  s.a.E[r] = nbF[0];
+  s.a.S[r] = nbB[1];
+  s.a.N[r] = nbF[1];
+  if (dim == 3) {
+    s.a.B[r] = nbB[2];
+    s.a.T_[r] = nbF[2];
+  }
+  s.b[r] = b;
+  s.a.idiag[r] = 1.0 / P;
+}
+
+template <int A>
+__global__ void __launch_bounds__(kBlock) k_assemble_momentum(Params pr, Sys s, const double* __restrict__ u,
+                                                              const double* __restrict__ v,
+                                                              const double* __restrict__ w, double* ustar,
+                                                              const double* __restrict__ p,
+                                                              const double* __restrict__ T,
+                                                              const double* __restrict__ Cl,
+                                                              const double* __restrict__ Kinv) {
+  const Axes ax = axes_of(pr);
+  const double* vel[3] = {u, v, w};
+  const int mx = s.d.mx, my = s.d.my;
+  const int n = (int)s.d.n;
+  const int sA = (A == 0) ? 1 : (A == 1) ? mx : mx * my;    // stride of axis A in the row grid
+  const double nu = pr.mu / pr.rho;
+  const double idt = 1.0 / pr.dt;
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+    const int i = r % mx, t = r / mx, j = t % my, k = t / my;
+    const int idx[3] = {i, j, k};
+    const int f = idx[A];
+    const double own = vel[A][r];
+    ustar[r] = own;   // initial guess of the predictor solve: u^n
+    double nbB[3] = {0.0, 0.0, 0.0}, nbF[3] = {0.0, 0.0, 0.0};
+    if (f == 0 || f == ax.n[A]) {   // wall face: identity row, datum 0
+      write_row(s, r, pr.dim, 1.0, nbB, nbF, 0.0);
+      continue;
+    }
+    // the two cells sharing this face along A
+    int lo[3] = {i, j, k};
+    lo[A] -= 1;
+    const int c_lo = cidx(pr, lo[0], lo[1], lo[2]);
+    const int c_hi = cidx(pr, i, j, k);
+    double P = 0.0;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      if (d >= pr.dim) break;
+      double Fb, Ff, Db, Df;
+      bool hb, hf;
+      if (d == A) {
+        Fb = 0.5 * (vel[A][r - sA] + own);
+        Ff = 0.5 * (own + vel[A][r + sA]);
+        hb = (f - 1 >= 1);
+        hf = (f + 1 <= ax.n[A] - 1);
+        Db = nu;
+        Df = nu;
+      } else {
+        int lo_f[3] = {lo[0], lo[1], lo[2]}, hi_f[3] = {i, j, k};
+        lo_f[d] += 1;
+        hi_f[d] += 1;
+        Fb = 0.5 * (vel[d][fidx(pr, d, lo[0], lo[1], lo[2])] + vel[d][fidx(pr, d, i, j, k)]);
+        Ff = 0.5 * (vel[d][fidx(pr, d, lo_f[0], lo_f[1], lo_f[2])] + vel[d][fidx(pr, d, hi_f[0], hi_f[1], hi_f[2])]);
+        hb = (idx[d] >= 1);
+        hf = (idx[d] <= ax.n[d] - 2);
+        Db = hb ? nu : 2.0 * nu;   // no-slip ghost = -interior beyond a wall
+        Df = hf ? nu : 2.0 * nu;
+      }
+      P += (fmax(Ff, 0.0) - fmin(Fb, 0.0)) * ax.ih[d] + (Db + Df) * ax.ih2[d];
+      nbB[d] = hb ? (-fmax(Fb, 0.0) * ax.ih[d] - Db * ax.ih2[d]) : 0.0;
+      nbF[d] = hf ? (fmin(Ff, 0.0) * ax.ih[d] - Df * ax.ih2[d]) : 0.0;
+    }
+    P += idt + nu * 0.5 * (Kinv[c_lo] + Kinv[c_hi]);
+    double b = own * idt - (p[c_hi] - p[c_lo]) * ax.ih[A] / pr.rho;
+    if (A == pr.vert) {
+      const double Tf = 0.5 * (T[c_lo] + T[c_hi]);
+      const double Cf = 0.5 * (Cl[c_lo] + Cl[c_hi]);
+      b += pr.gravity * (pr.betaT * (Tf - pr.Tref) + pr.betaC * (Cf - pr.C0));
+    }
+    write_row(s, r, pr.dim, P, nbB, nbF, b);
+  }
+}
+
+// Cell-centred systems. SOLUTE = true: solute (Eq. 3.10) with diffusivity
+// g_l^n D_l on faces and column scaling by A_g = 1/(1 - (1-k_p)(1-g_l^n));
+// false: T* (Eq. 3.12) with diffusivity k/(rho c_p) and Robin walls.
+// `Ag` holds A_g per cell (kept current by k_lever / k_equilibrate).
+template <bool SOLUTE>
+__global__ void __launch_bounds__(kBlock) k_assemble_cells(Params pr, Sys s, const double* __restrict__ u,
+                                                           const double* __restrict__ v,
+                                                           const double* __restrict__ w,
+                                                           const double* __restrict__ phi_n,
+                                                           const double* __restrict__ gl,
+                                                           const double* __restrict__ Ag) {
+  const Axes ax = axes_of(pr);
+  const double* vel[3] = {u, v, w};
+  const int nx = pr.nx, ny = pr.ny;
+  const int n = (int)s.d.n;
+  const int stride[3] = {1, nx, nx * ny};
+  const double alpha = pr.k / (pr.rho * pr.cp);
+  const double idt = 1.0 / pr.dt;
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+    const int i = r % nx, t = r / nx, j = t % ny, k = t / ny;
+    const int idx[3] = {i, j, k};
+    double m0 = 0.0, nbB[3] = {0.0, 0.0, 0.0}, nbF[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      if (a >= pr.dim) break;
+      int fr[3] = {i, j, k};
+      fr[a] += 1;
+      const double Fb = vel[a][fidx(pr, a, i, j, k)];
+      const double Ff = vel[a][fidx(pr, a, fr[0], fr[1], fr[2])];
+      const bool hb = idx[a] >= 1, hf = idx[a] <= ax.n[a] - 2;
+      double Db, Df;
+      if (SOLUTE) {
+        Db = hb ? pr.Dl * (0.5 * (gl[r - stride[a]] + gl[r])) : 0.0;
+        Df = hf ? pr.Dl * (0.5 * (gl[r] + gl[r + stride[a]])) : 0.0;
+      } else {
+        Db = hb ? alpha : 0.0;
+        Df = hf ? alpha : 0.0;
+      }
+      m0 += (fmax(Ff, 0.0) - fmin(Fb, 0.0)) * ax.ih[a] + (Db + Df) * ax.ih2[a];
+      double cb = hb ? (-fmax(Fb, 0.0) * ax.ih[a] - Db * ax.ih2[a]) : 0.0;
+      double cf = hf ? (fmin(Ff, 0.0) * ax.ih[a] - Df * ax.ih2[a]) : 0.0;
+      if (SOLUTE) {
+        cb = hb ? cb * Ag[r - stride[a]] : 0.0;
+        cf = hf ? cf * Ag[r + stride[a]] : 0.0;
+      }
+      nbB[a] = cb;
+      nbF[a] = cf;
+    }
+    double P, b = phi_n[r] * idt;
+    if (SOLUTE) {
+      P = idt + m0 * Ag[r];
+    } else {
+      P = m0 + idt;
+      // Robin walls: flux U (T_P - T_ext) per unit area, divided by rho cp h
+      const int wall[6] = {i == 0, i == nx - 1, j == 0, j == ny - 1, pr.dim == 3 && k == 0,
+                           pr.dim == 3 && k == pr.nz - 1};
+#pragma unroll
+      for (int q = 0; q < 6; ++q) {
+        if (wall[q] && pr.robin_coef[q] != 0.0) {
+          P += pr.robin_coef[q];
+          b += pr.robin_coef[q] * pr.robin_text[q];
+        }
+      }
+    }
+    write_row(s, r, pr.dim, P, nbB, nbF, b);
+  }
+}
+
+__global__ void __launch_bounds__(kBlock) k_poisson_rhs(Params pr, const double* __restrict__ us,
+                                                        const double* __restrict__ vs,
+                                                        const double* __restrict__ ws, double* b) {
+  const Axes ax = axes_of(pr);
+  const int nx = pr.nx, ny = pr.ny;
+  const int n = pr.nx * pr.ny * pr.nz;
+  const double scale = -pr.rho / pr.dt;
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+    const int i = r % nx, t = r / nx, j = t % ny, k = t / ny;
+    double div = (us[fidx(pr, 0, i + 1, j, k)] - us[fidx(pr, 0, i, j, k)]) * ax.ih[0] +
+                 (vs[fidx(pr, 1, i, j + 1, k)] - vs[fidx(pr, 1, i, j, k)]) * ax.ih[1];
+    if (pr.dim == 3) div += (ws[fidx(pr, 2, i, j, k + 1)] - ws[fidx(pr, 2, i, j, k)]) * ax.ih[2];
+    b[r] = scale * div;
+  }
+}
+
+// Faces of u, v, w then cells of p, one flat index space.
+__global__ void __launch_bounds__(kBlock) k_project(Params pr, double* u, double* v, double* w,
+                                                    const double* __restrict__ us,
+                                                    const double* __restrict__ vs,
+                                                    const double* __restrict__ ws,
+                                                    const double* __restrict__ pc, double* p) {
+  const Axes ax = axes_of(pr);
+  const int nx = pr.nx, ny = pr.ny, nz = pr.nz;
+  const int nu_ = (nx + 1) * ny * nz, nv = nx * (ny + 1) * nz, nw = (pr.dim == 3) ? nx * ny * (nz + 1) : 0;
+  const int nc = nx * ny * nz;
+  const int total = nu_ + nv + nw + nc;
+  const double kk = pr.dt / pr.rho;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < total; q += gridDim.x * blockDim.x) {
+    if (q < nu_ + nv + nw) {
+      int d, r;
+      if (q < nu_) { d = 0; r = q; }
+      else if (q < nu_ + nv) { d = 1; r = q - nu_; }
+      else { d = 2; r = q - nu_ - nv; }
+      const int fx = nx + (d == 0), fy = ny + (d == 1);
+      const int i = r % fx, t = r / fx, j = t % fy, k = t / fy;
+      const int idx[3] = {i, j, k};
+      double* out = (d == 0) ? u : (d == 1) ? v : w;
+      const double* in = (d == 0) ? us : (d == 1) ? vs : ws;
+      if (idx[d] == 0 || idx[d] == ax.n[d]) { out[r] = 0.0; continue; }
+      int lo[3] = {i, j, k};
+      lo[d] -= 1;
+      const double grad = (pc[cidx(pr, i, j, k)] - pc[cidx(pr, lo[0], lo[1], lo[2])]) * ax.ih[d];
+      out[r] = in[r] - kk * grad;
+    } else {
+      const int c = q - (nu_ + nv + nw);
+      p[c] += pc[c];
+    }
+  }
+}
+
+struct Phase {
+  double Cl, Kinv, Ag;
+};
+
+__device__ __forceinline__ Phase phase_of(const Params& pr, double C, double g) {
+  Phase o;
+  const double denom = 1.0 + (1.0 - g) * (pr.kp - 1.0);
+  o.Cl = C / denom;                                  // Eq. 3.18
+  if (pr.has_eutectic) o.Cl = fmin(o.Cl, pr.Ce);
+  o.Ag = 1.0 / (1.0 - (1.0 - pr.kp) * (1.0 - g));  // Eq. 3.8, for the next solute step
+  const double s = 1.0 - g;
+  o.Kinv = s * s / (pr.K0 * (g * g * g + pr.eps));  // Eq. 2.8, regularised
+  return o;
+}
+
+__global__ void __launch_bounds__(kBlock) k_lever(Params pr, double* T, double* gl, const double* __restrict__ C,
+                                                  double* Cl, double* Cs, double* Kinv, double* Ag, int n) {
+  const double kp = pr.kp, Tm = pr.Tm;
+  const double cpL = pr.cp / pr.L, Lcp = pr.L / pr.cp;
+  const double a = 1.0 - kp;
+  const double Te = pr.Tm + pr.m * pr.Ce;
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+    const double Ts = T[r], gn = gl[r], Cn = C[r];
+    const double Tl = Tm + pr.m * Cn;                                       // Eq. 3.14
+    const double b = kp - gn * (1.0 - kp) + cpL * (1.0 - kp) * (Tm - Ts);  // Eq. 3.17
+    const double c = -(gn + cpL * Ts) * kp + cpL * (Tl - (1.0 - kp) * Tm);
+    const double sq = sqrt(fmax(b * b - 4.0 * a * c, 0.0));
+    // larger root of Eq. 3.16 (a > 0), in the form free of cancellation
+    double g = (b > 0.0) ? (2.0 * c) / (-b - sq) : (-b + sq) / (2.0 * a);
+    g = fmin(fmax(g, 0.0), 1.0);
+    double Tn = Ts - Lcp * (g - gn);                                         // Eq. 3.13
+    if (pr.has_eutectic && Tn < Te && g > 0.0) {   // isothermal eutectic plateau
+      const double ge = gn - cpL * (Te - Ts);
+      if (ge >= 0.0) { g = ge; Tn = Te; }
+      else { g = 0.0; Tn = Ts + Lcp * gn; }
+    }
+    const Phase ph = phase_of(pr, Cn, g);
+    T[r] = Tn;
+    gl[r] = g;
+    Cl[r] = ph.Cl;
+    Cs[r] = kp * ph.Cl;                                                      // Eq. 3.19
+    Kinv[r] = ph.Kinv;
+    Ag[r] = ph.Ag;
+  }
+}
+
+__global__ void __launch_bounds__(kBlock) k_equilibrate(Params pr, const double* __restrict__ T,
+                                                        const double* __restrict__ C, double* gl, double* Cl,
+                                                        double* Cs, double* Kinv, double* Ag, int n, int from_T,
+                                                        int write_cl) {
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+    double g = gl[r];
+    if (from_T) {
+      const double Tv = T[r], Tl = pr.Tm + pr.m * C[r];
+      g = 1.0 - (Tv - Tl) / ((1.0 - pr.kp) * (Tv - pr.Tm));                 // Eq. 3.15
+      g = (Tv >= Tl) ? 1.0 : fmin(fmax(g, 0.0), 1.0);
+      gl[r] = g;
+    }
+    const Phase ph = phase_of(pr, C[r], g);
+    if (write_cl) {
+      Cl[r] = ph.Cl;
+      Cs[r] = pr.kp * ph.Cl;
+    }
+    Kinv[r] = ph.Kinv;
+    Ag[r] = ph.Ag;
+  }
+}
+
+__global__ void __launch_bounds__(kBlock) k_to_fp32(const double* __restrict__ src, float* dst, int n) {
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) dst[r] = (float)src[r];
+}
+
+}  // namespace
+
+cudaError_t launch_assemble_momentum(int comp, const Params& pr, const Sys& sys, const double* const vel[3],
+                                     double* ustar, const double* p, const double* T, const double* Cl,
+                                     const double* Kinv, cudaStream_t st) {
+  const int g = grid_for(sys.d.n);
+  if (comp == 0)
+    k_assemble_momentum<0><<<g, kBlock, 0, st>>>(pr, sys, vel[0], vel[1], vel[2], ustar, p, T, Cl, Kinv);
+  else if (comp == 1)
+    k_assemble_momentum<1><<<g, kBlock, 0, st>>>(pr, sys, vel[0], vel[1], vel[2], ustar, p, T, Cl, Kinv);
+  else
+    k_assemble_momentum<2><<<g, kBlock, 0, st>>>(pr, sys, vel[0], vel[1], vel[2], ustar, p, T, Cl, Kinv);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_assemble_solute(const Params& pr, const Sys& sys, const double* const vel[3], const double* gl,
+                                   const double* C, const double* Ag, cudaStream_t st) {
+  k_assemble_cells<true><<<grid_for(sys.d.n), kBlock, 0, st>>>(pr, sys, vel[0], vel[1], vel[2], C, gl, Ag);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_assemble_temperature(const Params& pr, const Sys& sys, const double* const vel[3],
+                                        const double* T, cudaStream_t st) {
+  k_assemble_cells<false><<<grid_for(sys.d.n), kBlock, 0, st>>>(pr, sys, vel[0], vel[1], vel[2], T, nullptr,
+                                                                 nullptr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_poisson_rhs(const Params& pr, const double* const ustar[3], double* b, cudaStream_t st) {
+  const long long n = (long long)pr.nx * pr.ny * pr.nz;
+  k_poisson_rhs<<<grid_for(n), kBlock, 0, st>>>(pr, ustar[0], ustar[1], ustar[2], b);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_project(const Params& pr, double* const vel[3], const double* const ustar[3], const double* pc,
+                           double* p, cudaStream_t st) {
+  const long long nx = pr.nx, ny = pr.ny, nz = pr.nz;
+  const long long total = (nx + 1) * ny * nz + nx * (ny + 1) * nz + (pr.dim == 3 ? nx * ny * (nz + 1) : 0) + nx * ny * nz;
+  k_project<<<grid_for(total), kBlock, 0, st>>>(pr, vel[0], vel[1], vel[2], ustar[0], ustar[1], ustar[2], pc, p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lever(const Params& pr, double* T, double* gl, const double* C, double* Cl, double* Cs,
+                         double* Kinv, double* Ag, cudaStream_t st) {
+  const int n = pr.nx * pr.ny * pr.nz;
+  k_lever<<<grid_for(n), kBlock, 0, st>>>(pr, T, gl, C, Cl, Cs, Kinv, Ag, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_equilibrate(const Params& pr, const double* T, const double* C, double* gl, double* Cl,
+                               double* Cs, double* Kinv, double* Ag, int from_T, int write_cl, cudaStream_t st) {
+  const int n = pr.nx * pr.ny * pr.nz;
+  k_equilibrate<<<grid_for(n), kBlock, 0, st>>>(pr, T, C, gl, Cl, Cs, Kinv, Ag, n, from_T, write_cl);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fp32_planes(const Sys& sys, int dim, cudaStream_t st) {
+  const int n = (int)sys.d.n, g = grid_for(n);
+  const double* src[8] = {sys.a.P, sys.a.W, sys.a.E, sys.a.S, sys.a.N, sys.a.B, sys.a.T_, sys.a.idiag};
+  float* dst[8] = {sys.af.P, sys.af.W, sys.af.E, sys.af.S, sys.af.N, sys.af.B, sys.af.T_, sys.af.idiag};
+  for (int q = 0; q < 8; ++q) {
+    if ((q == 5 || q == 6) && dim != 3) continue;
+    k_to_fp32<<<g, kBlock, 0, st>>>(src[q], dst[q], n);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace solid

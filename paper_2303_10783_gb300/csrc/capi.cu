@@ -1,0 +1,615 @@
+// C-ABI of libsolid: case lifetime, workspace layout, the Algorithm 1 step
+// driver and field I/O. See include/solid.h for the contract of each call.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "solid_internal.cuh"
+
+using namespace solid;
+
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+ss_status fail(ss_status s, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof g_err, fmt, ap);
+  va_end(ap);
+  return s;
+}
+
+#define CUDA_TRY(expr)                                                                  \
+  do {                                                                                  \
+    cudaError_t e_ = (expr);                                                            \
+    if (e_ != cudaSuccess) return fail(SS_ECUDA, "%s: %s", #expr, cudaGetErrorString(e_)); \
+  } while (0)
+
+__global__ void k_fill(double* x, double v, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    x[i] = v;
+}
+
+// Workspace planner: the same walk computes the size and the pointers.
+struct Planner {
+  char* base;
+  size_t off;
+  long long guard;
+  explicit Planner(char* b, long long g) : base(b), off(0), guard(g) {}
+  template <typename T>
+  T* vec(long long n) {
+    const size_t bytes = (size_t)(n + 2 * guard) * sizeof(T);
+    T* p = base ? reinterpret_cast<T*>(base + off) + guard : nullptr;
+    off += (bytes + 255) & ~(size_t)255;
+    return p;
+  }
+  template <typename T>
+  T* raw(size_t bytes) {
+    T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+    off += (bytes + 255) & ~(size_t)255;
+    return p;
+  }
+};
+
+}  // namespace
+
+struct ss_case {
+  ss_grid g;
+  Params pr;
+  cudaStream_t stream;
+  char* ws;
+  size_t ws_bytes;
+  double *u, *v, *w, *p, *T, *C, *gl, *Cl, *Cs, *Kinv, *Ag;
+  double *ustar[3], *pc, *pb;
+  Sys sys[SS_NSYS];
+  Scratch sc;
+  DevStatus* st;
+  int alloy_set;
+  long long steps;
+  ss_bc bc[6];
+  long long n_face[3], n_cell;
+  // stage profiling
+  int profiling;
+  std::vector<cudaEvent_t>* pool;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>>* pending;
+  long long launches[SS_NPROF];
+};
+
+namespace {
+
+bool grid_ok(const ss_grid* g, char* why, size_t len) {
+  if (!g) { snprintf(why, len, "grid is NULL"); return false; }
+  if (g->dim != 2 && g->dim != 3) { snprintf(why, len, "dim must be 2 or 3 (got %d)", g->dim); return false; }
+  const int nz = g->dim == 3 ? g->nz : 1;
+  if (g->nx < 1 || g->ny < 1 || nz < 1) { snprintf(why, len, "cell counts must be >= 1"); return false; }
+  const double cells = (double)(g->nx + 1) * (g->ny + 1) * (nz + 1);
+  if (cells > 1.5e9) { snprintf(why, len, "grid too large for 32-bit row indices"); return false; }
+  if (!(g->lx > 0) || !(g->ly > 0) || (g->dim == 3 && !(g->lz > 0))) { snprintf(why, len, "extents must be > 0"); return false; }
+  if (!(g->dt > 0)) { snprintf(why, len, "dt must be > 0"); return false; }
+  if (g->precision != SS_FP64 && g->precision != SS_MIXED) { snprintf(why, len, "unknown precision %d", g->precision); return false; }
+  if (!(g->tol_p > 0) || !(g->tol_t > 0)) { snprintf(why, len, "tolerances must be > 0"); return false; }
+  if (g->max_it_p < 1 || g->max_it_t < 1) { snprintf(why, len, "iteration caps must be >= 1"); return false; }
+  return true;
+}
+
+void plan(ss_case* c, Planner& pl) {
+  const long long nx = c->g.nx, ny = c->g.ny, nz = c->g.dim == 3 ? c->g.nz : 1;
+  c->n_cell = nx * ny * nz;
+  c->n_face[0] = (nx + 1) * ny * nz;
+  c->n_face[1] = nx * (ny + 1) * nz;
+  c->n_face[2] = nx * ny * (nz + 1);
+  const long long nmax = std::max(std::max(c->n_face[0], c->n_face[1]), std::max(c->n_face[2], c->n_cell));
+  c->st = pl.raw<DevStatus>(sizeof(DevStatus));
+  c->u = pl.vec<double>(c->n_face[0]);
+  c->v = pl.vec<double>(c->n_face[1]);
+  c->w = pl.vec<double>(c->n_face[2]);
+  c->p = pl.vec<double>(c->n_cell);
+  c->T = pl.vec<double>(c->n_cell);
+  c->C = pl.vec<double>(c->n_cell);
+  c->gl = pl.vec<double>(c->n_cell);
+  c->Cl = pl.vec<double>(c->n_cell);
+  c->Cs = pl.vec<double>(c->n_cell);
+  c->Kinv = pl.vec<double>(c->n_cell);
+  c->Ag = pl.vec<double>(c->n_cell);
+  for (int a = 0; a < 3; ++a) c->ustar[a] = pl.vec<double>(c->n_face[a]);
+  c->pc = pl.vec<double>(c->n_cell);
+  c->pb = pl.vec<double>(c->n_cell);
+  // one set of DIA planes shared by the u, v, w, C and T systems: each is
+  // assembled right before its solve (Sec. 4 term-wise assembly per step)
+  Planes<double> a;
+  a.P = pl.vec<double>(nmax); a.W = pl.vec<double>(nmax); a.E = pl.vec<double>(nmax);
+  a.S = pl.vec<double>(nmax); a.N = pl.vec<double>(nmax);
+  a.B = pl.vec<double>(nmax); a.T_ = pl.vec<double>(nmax); a.idiag = pl.vec<double>(nmax);
+  double* b = pl.vec<double>(nmax);
+  Planes<float> af = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  if (c->g.precision == SS_MIXED) {
+    af.P = pl.vec<float>(nmax); af.W = pl.vec<float>(nmax); af.E = pl.vec<float>(nmax);
+    af.S = pl.vec<float>(nmax); af.N = pl.vec<float>(nmax);
+    af.B = pl.vec<float>(nmax); af.T_ = pl.vec<float>(nmax); af.idiag = pl.vec<float>(nmax);
+  }
+  const int mdims[3][3] = {{(int)nx + 1, (int)ny, (int)nz}, {(int)nx, (int)ny + 1, (int)nz}, {(int)nx, (int)ny, (int)nz + 1}};
+  for (int s = 0; s < SS_NSYS; ++s) {
+    Sys& S = c->sys[s];
+    S.a = a;
+    S.af = af;
+    S.b = b;
+    if (s <= SS_SYS_W) {
+      S.d = {mdims[s][0], mdims[s][1], mdims[s][2], c->n_face[s]};
+      S.x = c->ustar[s];
+    } else {
+      S.d = {(int)nx, (int)ny, (int)nz, c->n_cell};
+      S.x = (s == SS_SYS_C) ? c->C : (s == SS_SYS_T) ? c->T : c->pc;
+    }
+  }
+  c->sys[SS_SYS_P].b = c->pb;
+  for (int q = 0; q < 8; ++q) c->sc.v[q] = pl.vec<double>(nmax);
+  for (int q = 0; q < 8; ++q) c->sc.f[q] = (c->g.precision == SS_MIXED) ? pl.vec<float>(nmax) : nullptr;
+  c->sc.max_blocks = max_cooperative_blocks();
+  c->sc.partial = pl.raw<double>((size_t)kMaxRedSlots * c->sc.max_blocks * sizeof(double));
+}
+
+long long guard_of(const ss_grid* g) { return (long long)(g->nx + 1) * (g->ny + 1) + 64; }
+
+void fill_params(ss_case* c, const ss_alloy* al) {
+  Params& pr = c->pr;
+  pr.dim = c->g.dim;
+  pr.nx = c->g.nx;
+  pr.ny = c->g.ny;
+  pr.nz = c->g.dim == 3 ? c->g.nz : 1;
+  pr.vert = c->g.dim == 2 ? 1 : 2;
+  pr.hx = c->g.lx / c->g.nx;
+  pr.hy = c->g.ly / c->g.ny;
+  pr.hz = c->g.dim == 3 ? c->g.lz / c->g.nz : 1.0;
+  pr.dt = c->g.dt;
+  if (al) {
+    pr.Tm = al->Tm; pr.m = al->m; pr.kp = al->kp; pr.C0 = al->C0; pr.rho = al->rho; pr.k = al->k;
+    pr.cp = al->cp; pr.L = al->L; pr.mu = al->mu; pr.Dl = al->Dl; pr.betaT = al->betaT; pr.betaC = al->betaC;
+    pr.K0 = al->K0; pr.Ce = al->Ce; pr.gravity = al->gravity; pr.eps = al->darcy_eps; pr.Tref = al->Tref;
+    pr.has_eutectic = al->Ce > 0.0;
+  }
+  const double h[3] = {pr.hx, pr.hy, pr.hz};
+  for (int q = 0; q < 6; ++q) {
+    const int axis = q / 2;
+    pr.robin_coef[q] = 0.0;
+    pr.robin_text[q] = 0.0;
+    if (c->bc[q].thermal == SS_ROBIN && axis < pr.dim && c->alloy_set) {
+      const double U = 1.0 / (1.0 / c->bc[q].h + h[axis] / (2.0 * pr.k));
+      pr.robin_coef[q] = U / (pr.rho * pr.cp * h[axis]);
+      pr.robin_text[q] = c->bc[q].Text;
+    }
+  }
+}
+
+ss_status check_case(ss_case* c) {
+  if (!c) return fail(SS_EINVAL, "case is NULL");
+  return SS_OK;
+}
+
+double* field_ptr(ss_case* c, int id) {
+  switch (id) {
+    case SS_U: return c->u;
+    case SS_V: return c->v;
+    case SS_W: return c->w;
+    case SS_P: return c->p;
+    case SS_T: return c->T;
+    case SS_C: return c->C;
+    case SS_GL: return c->gl;
+    case SS_CL: return c->Cl;
+    case SS_CS: return c->Cs;
+  }
+  return nullptr;
+}
+
+long long field_len(ss_case* c, int id) {
+  if (id <= SS_W) return c->n_face[id];
+  return c->n_cell;
+}
+
+const double* const* vel_of(ss_case* c, const double* out[3]) {
+  out[0] = c->u; out[1] = c->v; out[2] = c->w;
+  return out;
+}
+
+cudaEvent_t take_event(ss_case* c) {
+  if (!c->pool->empty()) {
+    cudaEvent_t e = c->pool->back();
+    c->pool->pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// RAII timer around one stage: records an event pair when profiling is on
+// and counts the kernels the stage launches.
+struct StageTimer {
+  ss_case* c;
+  int id;
+  cudaEvent_t a;
+  StageTimer(ss_case* c_, int id_, int kernels) : c(c_), id(id_), a(nullptr) {
+    c->launches[id] += kernels;
+    if (c->profiling) {
+      a = take_event(c);
+      cudaEventRecord(a, c->stream);
+    }
+  }
+  ~StageTimer() {
+    if (a) {
+      cudaEvent_t b = take_event(c);
+      cudaEventRecord(b, c->stream);
+      c->pending->push_back({id, {a, b}});
+    }
+  }
+};
+
+ss_status stage_assemble(ss_case* c, int sys) {
+  StageTimer tm(c, SS_PROF_ASSEMBLE + (sys >= 0 && sys < SS_NSYS ? sys : 0),
+                1 + ((c->g.precision == SS_MIXED && sys != SS_SYS_P) ? (c->pr.dim == 3 ? 8 : 6) : 0));
+  const double* vel[3];
+  vel_of(c, vel);
+  cudaError_t e;
+  switch (sys) {
+    case SS_SYS_U:
+    case SS_SYS_V:
+    case SS_SYS_W:
+      e = launch_assemble_momentum(sys, c->pr, c->sys[sys], vel, c->ustar[sys], c->p, c->T, c->Cl, c->Kinv, c->stream);
+      break;
+    case SS_SYS_P: {
+      const double* us[3] = {c->ustar[0], c->ustar[1], c->ustar[2]};
+      e = launch_poisson_rhs(c->pr, us, c->pb, c->stream);
+      break;
+    }
+    case SS_SYS_C: e = launch_assemble_solute(c->pr, c->sys[sys], vel, c->gl, c->C, c->Ag, c->stream); break;
+    case SS_SYS_T: e = launch_assemble_temperature(c->pr, c->sys[sys], vel, c->T, c->stream); break;
+    default: return fail(SS_EINVAL, "unknown system %d", sys);
+  }
+  if (e != cudaSuccess) return fail(SS_ECUDA, "assembly of system %d: %s", sys, cudaGetErrorString(e));
+  if (c->g.precision == SS_MIXED && sys != SS_SYS_P) {
+    e = launch_fp32_planes(c->sys[sys], c->pr.dim, c->stream);
+    if (e != cudaSuccess) return fail(SS_ECUDA, "plane conversion: %s", cudaGetErrorString(e));
+  }
+  return SS_OK;
+}
+
+ss_status stage_solve(ss_case* c, int sys) {
+  StageTimer tm(c, SS_PROF_SOLVE + (sys >= 0 && sys < SS_NSYS ? sys : 0), 1);
+  SolverCtl ctl;
+  ctl.mixed = c->g.precision == SS_MIXED;
+  ctl.stat_index = sys;
+  cudaError_t e;
+  if (sys == SS_SYS_P) {
+    ctl.tol = c->g.tol_p;
+    ctl.max_it = c->g.max_it_p;
+    e = launch_pcg_poisson(c->pr, c->pb, c->pc, ctl, c->sc, c->st, c->stream);
+  } else if (sys >= 0 && sys < SS_NSYS) {
+    if (sys == SS_SYS_W && c->pr.dim != 3) return SS_OK;
+    ctl.tol = c->g.tol_t;
+    ctl.max_it = c->g.max_it_t;
+    e = launch_bicgstab(c->sys[sys], c->pr.dim == 3, ctl, c->sc, c->st, c->stream);
+  } else {
+    return fail(SS_EINVAL, "unknown system %d", sys);
+  }
+  if (e != cudaSuccess) return fail(SS_ECUDA, "solve of system %d: %s", sys, cudaGetErrorString(e));
+  return SS_OK;
+}
+
+ss_status stage_project(ss_case* c) {
+  StageTimer tm(c, SS_PROF_PROJECT, 1);
+  double* vel[3] = {c->u, c->v, c->w};
+  const double* us[3] = {c->ustar[0], c->ustar[1], c->ustar[2]};
+  cudaError_t e = launch_project(c->pr, vel, us, c->pc, c->p, c->stream);
+  if (e != cudaSuccess) return fail(SS_ECUDA, "projection: %s", cudaGetErrorString(e));
+  return SS_OK;
+}
+
+ss_status stage_lever(ss_case* c) {
+  StageTimer tm(c, SS_PROF_LEVER, 1);
+  cudaError_t e = launch_lever(c->pr, c->T, c->gl, c->C, c->Cl, c->Cs, c->Kinv, c->Ag, c->stream);
+  if (e != cudaSuccess) return fail(SS_ECUDA, "lever update: %s", cudaGetErrorString(e));
+  return SS_OK;
+}
+
+#define STAGE_TRY(expr)            \
+  do {                             \
+    ss_status s_ = (expr);         \
+    if (s_ != SS_OK) return s_;    \
+  } while (0)
+
+ss_status one_step(ss_case* c) {
+  const int ncomp = c->pr.dim;
+  for (int a = 0; a < ncomp; ++a) {           // 1: intermediate velocity (Eq. 3.3)
+    STAGE_TRY(stage_assemble(c, a));
+    STAGE_TRY(stage_solve(c, a));
+  }
+  STAGE_TRY(stage_assemble(c, SS_SYS_P));     // 2: pressure correction (Eq. 3.4)
+  STAGE_TRY(stage_solve(c, SS_SYS_P));
+  STAGE_TRY(stage_project(c));                // 3: projection (Eq. 3.5)
+  STAGE_TRY(stage_assemble(c, SS_SYS_C));     // 4: solute (Eq. 3.10)
+  STAGE_TRY(stage_solve(c, SS_SYS_C));
+  STAGE_TRY(stage_assemble(c, SS_SYS_T));     // 5-6: T* (Eq. 3.12); T_l is formed in the lever stage
+  STAGE_TRY(stage_solve(c, SS_SYS_T));
+  STAGE_TRY(stage_lever(c));                  // 7-8: lever rule, T, g_l, C_l, C_s (Eq. 3.13-3.19)
+  return SS_OK;
+}
+
+ss_status read_status(ss_case* c, DevStatus* host) {
+  CUDA_TRY(cudaMemcpyAsync(host, c->st, sizeof(DevStatus), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  CUDA_TRY(cudaMemsetAsync(&c->st->sticky, 0, sizeof(int), c->stream));
+  CUDA_TRY(cudaMemsetAsync(&c->st->err, 0, sizeof(int), c->stream));
+  if (host->err != kErrNone) return fail(SS_ETIMEOUT, "a device-side grid barrier timed out; the solve returned early");
+  if (host->sticky == SS_ENAN) return fail(SS_ENAN, "a non-finite residual appeared in a solve");
+  if (host->sticky == SS_ENOTCONV) return fail(SS_ENOTCONV, "a solve reached its iteration cap");
+  return SS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* ss_last_error(void) { return g_err; }
+
+ss_status ss_workspace_bytes(const ss_grid* grid, size_t* bytes) {
+  char why[256];
+  if (!bytes) return fail(SS_EINVAL, "bytes is NULL");
+  if (!grid_ok(grid, why, sizeof why)) return fail(SS_EINVAL, "%s", why);
+  ss_case tmp;
+  memset(&tmp, 0, sizeof tmp);
+  tmp.g = *grid;
+  Planner pl(nullptr, guard_of(grid));
+  plan(&tmp, pl);
+  *bytes = pl.off;
+  return SS_OK;
+}
+
+ss_status ss_create_case(const ss_grid* grid, void* workspace, size_t workspace_bytes, void* stream, ss_case** out) {
+  char why[256];
+  if (!out) return fail(SS_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!grid_ok(grid, why, sizeof why)) return fail(SS_EINVAL, "%s", why);
+  if (!workspace) return fail(SS_EINVAL, "workspace is NULL");
+  if (((uintptr_t)workspace & 255) != 0) return fail(SS_EINVAL, "workspace must be 256-byte aligned");
+  size_t need = 0;
+  ss_status s = ss_workspace_bytes(grid, &need);
+  if (s != SS_OK) return s;
+  if (workspace_bytes < need) return fail(SS_ENOMEM, "workspace has %zu bytes, needs %zu", workspace_bytes, need);
+  ss_case* c = new (std::nothrow) ss_case;
+  if (!c) return fail(SS_ENOMEM, "host allocation failed");
+  memset(c, 0, sizeof *c);
+  c->g = *grid;
+  if (c->g.dim == 2) c->g.nz = 1;
+  c->pool = new (std::nothrow) std::vector<cudaEvent_t>();
+  c->pending = new (std::nothrow) std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>>();
+  if (!c->pool || !c->pending) {
+    delete c->pool;
+    delete c->pending;
+    delete c;
+    return fail(SS_ENOMEM, "host allocation failed");
+  }
+  c->stream = (cudaStream_t)stream;
+  c->ws = (char*)workspace;
+  c->ws_bytes = workspace_bytes;
+  Planner pl(c->ws, guard_of(grid));
+  plan(c, pl);
+  fill_params(c, nullptr);
+  cudaError_t e = cudaMemsetAsync(c->ws, 0, need, c->stream);   // zero fields and guard bands
+  if (e != cudaSuccess) {
+    delete c->pool;
+    delete c->pending;
+    delete c;
+    return fail(SS_ECUDA, "workspace clear: %s", cudaGetErrorString(e));
+  }
+  *out = c;
+  return SS_OK;
+}
+
+ss_status ss_set_alloy(ss_case* c, const ss_alloy* al) {
+  STAGE_TRY(check_case(c));
+  if (!al) return fail(SS_EINVAL, "alloy is NULL");
+  if (c->steps > 0) return fail(SS_ESTATE, "set_alloy after the first step");
+  if (!(al->kp > 0 && al->kp < 1)) return fail(SS_EINVAL, "kp must be in (0, 1)");
+  if (!(al->rho > 0 && al->k > 0 && al->cp > 0 && al->L > 0 && al->mu > 0 && al->K0 > 0 && al->darcy_eps > 0))
+    return fail(SS_EINVAL, "rho, k, cp, L, mu, K0, darcy_eps must be > 0");
+  if (al->Dl < 0) return fail(SS_EINVAL, "Dl must be >= 0");
+  c->alloy_set = 1;
+  fill_params(c, al);
+  const long long nf[3] = {c->n_face[0], c->n_face[1], c->n_face[2]};
+  CUDA_TRY(cudaMemsetAsync(c->u, 0, nf[0] * sizeof(double), c->stream));
+  CUDA_TRY(cudaMemsetAsync(c->v, 0, nf[1] * sizeof(double), c->stream));
+  CUDA_TRY(cudaMemsetAsync(c->w, 0, nf[2] * sizeof(double), c->stream));
+  CUDA_TRY(cudaMemsetAsync(c->p, 0, c->n_cell * sizeof(double), c->stream));
+  k_fill<<<256, 256, 0, c->stream>>>(c->T, al->Tref, c->n_cell);
+  k_fill<<<256, 256, 0, c->stream>>>(c->C, al->C0, c->n_cell);
+  CUDA_TRY(cudaGetLastError());
+  return ss_equilibrate(c);
+}
+
+ss_status ss_set_boundary(ss_case* c, int face, const ss_bc* bc) {
+  STAGE_TRY(check_case(c));
+  if (!bc) return fail(SS_EINVAL, "bc is NULL");
+  if (face < 0 || face > 5) return fail(SS_EINVAL, "face must be 0..5");
+  if (bc->thermal != SS_ADIABATIC && bc->thermal != SS_ROBIN) return fail(SS_EINVAL, "unknown thermal condition");
+  if (bc->thermal == SS_ROBIN && !(bc->h > 0)) return fail(SS_EINVAL, "Robin h must be > 0");
+  c->bc[face] = *bc;
+  fill_params(c, nullptr);
+  return SS_OK;
+}
+
+ss_status ss_step(ss_case* c, int n) {
+  STAGE_TRY(check_case(c));
+  if (n < 0) return fail(SS_EINVAL, "n must be >= 0");
+  if (!c->alloy_set) return fail(SS_ESTATE, "set_alloy before stepping");
+  for (int q = 0; q < n; ++q) {
+    STAGE_TRY(one_step(c));
+    c->steps++;
+  }
+  return SS_OK;
+}
+
+ss_status ss_sync(ss_case* c) {
+  STAGE_TRY(check_case(c));
+  DevStatus h;
+  return read_status(c, &h);
+}
+
+ss_status ss_get_fields(ss_case* c, unsigned mask, void* const* dst, int dst_is_device) {
+  STAGE_TRY(check_case(c));
+  if (!dst) return fail(SS_EINVAL, "dst is NULL");
+  for (int id = 0; id < SS_NFIELDS; ++id) {
+    if (!(mask & (1u << id))) continue;
+    if (id == SS_W && c->pr.dim != 3) continue;
+    if (!dst[id]) return fail(SS_EINVAL, "dst[%d] is NULL", id);
+    CUDA_TRY(cudaMemcpyAsync(dst[id], field_ptr(c, id), field_len(c, id) * sizeof(double),
+                             dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+  }
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  return SS_OK;
+}
+
+ss_status ss_set_fields(ss_case* c, unsigned mask, const void* const* src, int src_is_device) {
+  STAGE_TRY(check_case(c));
+  if (!src) return fail(SS_EINVAL, "src is NULL");
+  for (int id = 0; id < SS_NFIELDS; ++id) {
+    if (!(mask & (1u << id))) continue;
+    if (id == SS_W && c->pr.dim != 3) continue;
+    if (!src[id]) return fail(SS_EINVAL, "src[%d] is NULL", id);
+    CUDA_TRY(cudaMemcpyAsync(field_ptr(c, id), src[id], field_len(c, id) * sizeof(double),
+                             src_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
+  }
+  if ((mask & (1u << SS_GL)) && c->alloy_set) {
+    // keep K^{-1} and A_g consistent with the new g_l; C_l and C_s stay as they are
+    cudaError_t e = launch_equilibrate(c->pr, c->T, c->C, c->gl, c->Cl, c->Cs, c->Kinv, c->Ag, 0, 0, c->stream);
+    if (e != cudaSuccess) return fail(SS_ECUDA, "derived fields: %s", cudaGetErrorString(e));
+  }
+  if (!src_is_device) CUDA_TRY(cudaStreamSynchronize(c->stream));
+  return SS_OK;
+}
+
+ss_status ss_equilibrate(ss_case* c) {
+  STAGE_TRY(check_case(c));
+  if (!c->alloy_set) return fail(SS_ESTATE, "set_alloy first");
+  cudaError_t e = launch_equilibrate(c->pr, c->T, c->C, c->gl, c->Cl, c->Cs, c->Kinv, c->Ag, 1, 1, c->stream);
+  if (e != cudaSuccess) return fail(SS_ECUDA, "equilibrate: %s", cudaGetErrorString(e));
+  return SS_OK;
+}
+
+ss_status ss_get_stats(ss_case* c, ss_stats* out) {
+  STAGE_TRY(check_case(c));
+  if (!out) return fail(SS_EINVAL, "out is NULL");
+  DevStatus h;
+  ss_status s = read_status(c, &h);
+  out->steps = c->steps;
+  for (int q = 0; q < SS_NSYS; ++q) {
+    out->iters[q] = h.stat[q].iters;
+    out->refinements[q] = h.stat[q].refinements;
+    out->relres[q] = h.stat[q].relres;
+  }
+  out->status = (s == SS_OK) ? SS_OK : (int)s;
+  return s;
+}
+
+ss_status ss_set_profiling(ss_case* c, int on) {
+  STAGE_TRY(check_case(c));
+  c->profiling = on ? 1 : 0;
+  return SS_OK;
+}
+
+ss_status ss_get_profile(ss_case* c, ss_profile* out) {
+  STAGE_TRY(check_case(c));
+  if (!out) return fail(SS_EINVAL, "out is NULL");
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  memset(out, 0, sizeof *out);
+  for (auto& pe : *c->pending) {
+    float ms = 0.f;
+    CUDA_TRY(cudaEventElapsedTime(&ms, pe.second.first, pe.second.second));
+    out->ms[pe.first] += ms;
+    c->pool->push_back(pe.second.first);
+    c->pool->push_back(pe.second.second);
+  }
+  c->pending->clear();
+  for (int q = 0; q < SS_NPROF; ++q) {
+    out->launches[q] = c->launches[q];
+    out->kernels += c->launches[q];
+    c->launches[q] = 0;
+  }
+  DevStatus h;
+  CUDA_TRY(cudaMemcpy(&h, c->st, sizeof(DevStatus), cudaMemcpyDeviceToHost));
+  for (int s = 0; s < SS_NSYS; ++s) {
+    out->iters[s] = h.stat[s].iters_total;
+    CUDA_TRY(cudaMemsetAsync(&c->st->stat[s].iters_total, 0, sizeof(long long), c->stream));
+  }
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  return SS_OK;
+}
+
+ss_status ss_destroy(ss_case* c) {
+  if (!c) return SS_OK;
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  for (auto& pe : *c->pending) {
+    cudaEventDestroy(pe.second.first);
+    cudaEventDestroy(pe.second.second);
+  }
+  for (auto ev : *c->pool) cudaEventDestroy(ev);
+  delete c->pool;
+  delete c->pending;
+  delete c;
+  if (e != cudaSuccess) return fail(SS_ECUDA, "destroy: %s", cudaGetErrorString(e));
+  return SS_OK;
+}
+
+ss_status ss_assemble(ss_case* c, int sys) {
+  STAGE_TRY(check_case(c));
+  if (!c->alloy_set) return fail(SS_ESTATE, "set_alloy first");
+  if (sys == SS_SYS_W && c->pr.dim != 3) return fail(SS_EINVAL, "no w system in 2D");
+  return stage_assemble(c, sys);
+}
+
+ss_status ss_solve(ss_case* c, int sys) {
+  STAGE_TRY(check_case(c));
+  if (!c->alloy_set) return fail(SS_ESTATE, "set_alloy first");
+  if (sys == SS_SYS_W && c->pr.dim != 3) return fail(SS_EINVAL, "no w system in 2D");
+  STAGE_TRY(stage_solve(c, sys));
+  return ss_sync(c);
+}
+
+ss_status ss_get_system(ss_case* c, int sys, void* const* dst, int dst_is_device) {
+  STAGE_TRY(check_case(c));
+  if (!dst) return fail(SS_EINVAL, "dst is NULL");
+  if (sys < 0 || sys >= SS_NSYS) return fail(SS_EINVAL, "unknown system %d", sys);
+  const Sys& S = c->sys[sys];
+  const double* src[9] = {S.a.P, S.a.W, S.a.E, S.a.S, S.a.N, S.a.B, S.a.T_, S.b, S.x};
+  const cudaMemcpyKind kind = dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  for (int q = 0; q < 9; ++q) {
+    if (!dst[q]) continue;
+    if (sys == SS_SYS_P && q < 7) continue;
+    if ((q == 5 || q == 6) && c->pr.dim != 3) {   // no z diagonals in 2D
+      if (dst_is_device) CUDA_TRY(cudaMemsetAsync(dst[q], 0, S.d.n * sizeof(double), c->stream));
+      else memset(dst[q], 0, S.d.n * sizeof(double));
+      continue;
+    }
+    CUDA_TRY(cudaMemcpyAsync(dst[q], src[q], S.d.n * sizeof(double), kind, c->stream));
+  }
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  return SS_OK;
+}
+
+ss_status ss_project(ss_case* c) {
+  STAGE_TRY(check_case(c));
+  return stage_project(c);
+}
+
+ss_status ss_lever(ss_case* c) {
+  STAGE_TRY(check_case(c));
+  if (!c->alloy_set) return fail(SS_ESTATE, "set_alloy first");
+  return stage_lever(c);
+}
+
+}  // extern "C"

@@ -1,0 +1,358 @@
+// Persistent Krylov solvers for the DIA systems of one step.
+//
+// Each solve is ONE cooperative launch: every block stays resident for the
+// whole solve, owns a fixed grid-stride set of rows, and meets the others at
+// grid barriers between dependent phases. Dot products are reduced
+// deterministically (warp shuffles, then per-block partials summed in block
+// order by every block), so every block takes the same convergence decision
+// and the result does not depend on timing. Convergence is checked on the
+// device; the host never waits inside a solve.
+//
+//   k_bicgstab      Jacobi-preconditioned BiCGSTAB for the nonsymmetric
+//                   transport systems (u*, v*, w*: Eq. 3.3; C: Eq. 3.10;
+//                   T*: Eq. 3.12) stored as 5/7 DIA planes (Eq. 4.1).
+//   k_pcg_poisson   Jacobi-preconditioned CG for the pressure correction
+//                   (Eq. 3.4): the constant-coefficient Neumann Laplacian is
+//                   applied matrix-free (term-wise strategy of Sec. 4: the
+//                   operator never changes, so it is never assembled).
+//
+// Vectors that other blocks write during the solve (the SpMV operands) are
+// read with ld.global.cg so a stale L1 line can never be used.
+#include "solid_internal.cuh"
+
+namespace solid {
+namespace {
+
+struct BcgArgs {
+  Sys sys;
+  int has_z;
+  double tol;
+  int max_it;
+  int stat_index;
+  double *r, *rh, *p, *v, *y, *z, *t;
+  double* partial;
+  int max_blocks;
+  DevStatus* st;
+};
+
+__device__ __forceinline__ double spmv_row(const Planes<double>& a, const double* x, int r, int sy, int sz,
+                                           int has_z) {
+  double acc = __ldg(a.P + r) * __ldcg(x + r);
+  acc = fma(__ldg(a.W + r), __ldcg(x + r - 1), acc);
+  acc = fma(__ldg(a.E + r), __ldcg(x + r + 1), acc);
+  acc = fma(__ldg(a.S + r), __ldcg(x + r - sy), acc);
+  acc = fma(__ldg(a.N + r), __ldcg(x + r + sy), acc);
+  if (has_z) {
+    acc = fma(__ldg(a.B + r), __ldcg(x + r - sz), acc);
+    acc = fma(__ldg(a.T_ + r), __ldcg(x + r + sz), acc);
+  }
+  return acc;
+}
+
+__device__ void record(DevStatus* st, int idx, int iters, bool converged, double relres) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    SolveStat& s = st->stat[idx];
+    s.iters = iters;
+    s.iters_total += iters;
+    s.refinements = 0;
+    s.converged = converged ? 1 : 0;
+    s.nonfinite = isfinite(relres) ? 0 : 1;
+    s.relres = relres;
+    if (!isfinite(relres)) atomicExch(&st->sticky, (int)SS_ENAN);
+    else if (!converged) atomicCAS(&st->sticky, (int)SS_OK, (int)SS_ENOTCONV);
+  }
+}
+
+__global__ void __launch_bounds__(kBlock, 2) k_bicgstab(BcgArgs A) {
+  unsigned int epoch = 0;
+  const int n = (int)A.sys.d.n;
+  const int sy = A.sys.d.mx, sz = A.sys.d.mx * A.sys.d.my;
+  const int t0 = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
+  const Planes<double> a = A.sys.a;
+  double* x = A.sys.x;
+  const double* b = A.sys.b;
+  double *r = A.r, *rh = A.rh, *p = A.p, *v = A.v, *y = A.y, *z = A.z, *t = A.t;
+
+  // r = b - A x0, rhat = r
+  Vec<2> acc = {{0.0, 0.0}};
+  for (int i = t0; i < n; i += gs) {
+    const double ri = b[i] - spmv_row(a, x, i, sy, sz, A.has_z);
+    r[i] = ri;
+    rh[i] = ri;
+    p[i] = 0.0;
+    v[i] = 0.0;
+    acc.v[0] += ri * ri;
+    acc.v[1] += b[i] * b[i];
+  }
+  Vec<2> tot;
+  if (!grid_sum<2>(acc, A.partial, A.max_blocks, 6, A.st, epoch, tot)) return;
+  const double bnorm = sqrt(tot.v[1]);
+  double res = sqrt(tot.v[0]);
+  if (bnorm == 0.0) {   // b = 0: the solution is 0
+    for (int i = t0; i < n; i += gs) x[i] = 0.0;
+    record(A.st, A.stat_index, 0, true, 0.0);
+    return;
+  }
+  const double thr = A.tol * bnorm;
+  double rho = tot.v[0], rho_old = 1.0, alpha = 1.0, omega = 1.0;
+  int it = 0;
+  bool conv = res <= thr;
+  while (!conv && it < A.max_it && isfinite(res)) {
+    ++it;
+    const double beta = (rho / rho_old) * (alpha / omega);
+    for (int i = t0; i < n; i += gs) {            // p = r + beta (p - omega v); y = M^-1 p
+      const double pi = r[i] + beta * (p[i] - omega * v[i]);
+      p[i] = pi;
+      y[i] = __ldg(a.idiag + i) * pi;
+    }
+    if (!grid_barrier(A.st, gridDim.x, epoch)) return;
+    Vec<1> d1 = {{0.0}};
+    for (int i = t0; i < n; i += gs) {            // v = A y
+      const double vi = spmv_row(a, y, i, sy, sz, A.has_z);
+      v[i] = vi;
+      d1.v[0] += rh[i] * vi;
+    }
+    Vec<1> o1;
+    if (!grid_sum<1>(d1, A.partial, A.max_blocks, 0, A.st, epoch, o1)) return;
+    alpha = rho / o1.v[0];
+    Vec<1> d2 = {{0.0}};
+    for (int i = t0; i < n; i += gs) {            // s = r - alpha v (in r); z = M^-1 s
+      const double si = r[i] - alpha * v[i];
+      r[i] = si;
+      z[i] = __ldg(a.idiag + i) * si;
+      d2.v[0] += si * si;
+    }
+    Vec<1> o2;
+    if (!grid_sum<1>(d2, A.partial, A.max_blocks, 1, A.st, epoch, o2)) return;
+    if (sqrt(o2.v[0]) <= thr) {                  // early exit on the half step
+      for (int i = t0; i < n; i += gs) x[i] += alpha * y[i];
+      res = sqrt(o2.v[0]);
+      conv = true;
+      break;
+    }
+    Vec<2> d3 = {{0.0, 0.0}};
+    for (int i = t0; i < n; i += gs) {            // t = A z
+      const double ti = spmv_row(a, z, i, sy, sz, A.has_z);
+      t[i] = ti;
+      d3.v[0] += ti * r[i];
+      d3.v[1] += ti * ti;
+    }
+    Vec<2> o3;
+    if (!grid_sum<2>(d3, A.partial, A.max_blocks, 2, A.st, epoch, o3)) return;
+    omega = (o3.v[1] > 0.0) ? o3.v[0] / o3.v[1] : 0.0;
+    Vec<2> d4 = {{0.0, 0.0}};
+    for (int i = t0; i < n; i += gs) {            // x += alpha y + omega z; r = s - omega t
+      x[i] += alpha * y[i] + omega * z[i];
+      const double ri = r[i] - omega * t[i];
+      r[i] = ri;
+      d4.v[0] += rh[i] * ri;
+      d4.v[1] += ri * ri;
+    }
+    Vec<2> o4;
+    if (!grid_sum<2>(d4, A.partial, A.max_blocks, 4, A.st, epoch, o4)) return;
+    res = sqrt(o4.v[1]);
+    conv = res <= thr;
+    rho_old = rho;
+    rho = o4.v[0];
+    if (rho == 0.0 || omega == 0.0) break;   // breakdown: report the current iterate
+  }
+  record(A.st, A.stat_index, it, conv, res / bnorm);
+}
+
+struct PcgArgs {
+  int nx, ny, nz, dim;
+  double cx, cy, cz;      // 1/h^2 per axis
+  double* b;
+  double* x;
+  double *r, *p, *q;
+  double tol;
+  int max_it;
+  int stat_index;
+  double* partial;
+  int max_blocks;
+  DevStatus* st;
+};
+
+// A = -L: (A p)_c = sum over existing neighbours of (p_c - p_nb)/h^2
+__device__ __forceinline__ double lap_row(const PcgArgs& A, const double* p, int r, int i, int j, int k,
+                                          double diag) {
+  const int sy = A.nx, sz = A.nx * A.ny;
+  double acc = diag * __ldcg(p + r);
+  const double sxs = (i > 0 ? __ldcg(p + r - 1) : 0.0) + (i < A.nx - 1 ? __ldcg(p + r + 1) : 0.0);
+  acc = fma(-A.cx, sxs, acc);
+  const double sys = (j > 0 ? __ldcg(p + r - sy) : 0.0) + (j < A.ny - 1 ? __ldcg(p + r + sy) : 0.0);
+  acc = fma(-A.cy, sys, acc);
+  if (A.dim == 3) {
+    const double szs = (k > 0 ? __ldcg(p + r - sz) : 0.0) + (k < A.nz - 1 ? __ldcg(p + r + sz) : 0.0);
+    acc = fma(-A.cz, szs, acc);
+  }
+  return acc;
+}
+
+__device__ __forceinline__ int nb_code(const PcgArgs& A, int i, int j, int k) {
+  const int cx = (i > 0) + (i < A.nx - 1);
+  const int cy = (j > 0) + (j < A.ny - 1);
+  const int cz = (A.dim == 3) ? (k > 0) + (k < A.nz - 1) : 0;
+  return cx + 3 * cy + 9 * cz;
+}
+
+__global__ void __launch_bounds__(kBlock, 2) k_pcg_poisson(PcgArgs A) {
+  __shared__ double s_diag[27], s_minv[27];
+  if (threadIdx.x < 27) {
+    const int c = threadIdx.x;
+    const double d = (c % 3) * A.cx + ((c / 3) % 3) * A.cy + (c / 9) * A.cz;
+    s_diag[c] = d;
+    s_minv[c] = (d > 0.0) ? 1.0 / d : 0.0;
+  }
+  __syncthreads();
+  unsigned int epoch = 0;
+  const int n = A.nx * A.ny * A.nz;
+  const int t0 = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
+  double *b = A.b, *x = A.x, *r = A.r, *p = A.p, *q = A.q;
+
+  // consistency: remove the mean of the right-hand side (Neumann null space)
+  Vec<1> sb = {{0.0}};
+  for (int i = t0; i < n; i += gs) sb.v[0] += b[i];
+  Vec<1> ob;
+  if (!grid_sum<1>(sb, A.partial, A.max_blocks, 8, A.st, epoch, ob)) return;
+  const double mean_b = ob.v[0] / (double)n;
+  Vec<2> acc = {{0.0, 0.0}};
+  for (int i = t0; i < n; i += gs) {
+    const int ii = i % A.nx, tt = i / A.nx, jj = tt % A.ny, kk = tt / A.ny;
+    const double bi = b[i] - mean_b;
+    b[i] = bi;
+    x[i] = 0.0;
+    r[i] = bi;
+    const double zi = s_minv[nb_code(A, ii, jj, kk)] * bi;
+    p[i] = zi;
+    acc.v[0] += bi * zi;
+    acc.v[1] += bi * bi;
+  }
+  Vec<2> o0;
+  if (!grid_sum<2>(acc, A.partial, A.max_blocks, 9, A.st, epoch, o0)) return;
+  const double bnorm = sqrt(o0.v[1]);
+  double rz = o0.v[0], res = bnorm;
+  int it = 0;
+  bool conv = (bnorm == 0.0);
+  const double thr = A.tol * bnorm;
+  while (!conv && it < A.max_it && isfinite(res)) {
+    ++it;
+    Vec<1> d1 = {{0.0}};
+    for (int i = t0; i < n; i += gs) {            // q = A p
+      const int ii = i % A.nx, tt = i / A.nx, jj = tt % A.ny, kk = tt / A.ny;
+      const double qi = lap_row(A, p, i, ii, jj, kk, s_diag[nb_code(A, ii, jj, kk)]);
+      q[i] = qi;
+      d1.v[0] += p[i] * qi;
+    }
+    Vec<1> o1;
+    if (!grid_sum<1>(d1, A.partial, A.max_blocks, 10, A.st, epoch, o1)) return;
+    const double alpha = rz / o1.v[0];
+    Vec<2> d2 = {{0.0, 0.0}};
+    for (int i = t0; i < n; i += gs) {            // x += alpha p; r -= alpha q; z = M^-1 r
+      const int ii = i % A.nx, tt = i / A.nx, jj = tt % A.ny, kk = tt / A.ny;
+      x[i] += alpha * p[i];
+      const double ri = r[i] - alpha * q[i];
+      r[i] = ri;
+      const double zi = s_minv[nb_code(A, ii, jj, kk)] * ri;
+      d2.v[0] += ri * zi;
+      d2.v[1] += ri * ri;
+    }
+    Vec<2> o2;
+    if (!grid_sum<2>(d2, A.partial, A.max_blocks, 11, A.st, epoch, o2)) return;
+    res = sqrt(o2.v[1]);
+    conv = res <= thr;
+    if (conv) break;
+    const double beta = o2.v[0] / rz;
+    rz = o2.v[0];
+    for (int i = t0; i < n; i += gs) {            // p = z + beta p
+      const int ii = i % A.nx, tt = i / A.nx, jj = tt % A.ny, kk = tt / A.ny;
+      p[i] = s_minv[nb_code(A, ii, jj, kk)] * r[i] + beta * p[i];
+    }
+    if (!grid_barrier(A.st, gridDim.x, epoch)) return;
+  }
+  // gauge: zero-mean correction
+  Vec<1> sx = {{0.0}};
+  for (int i = t0; i < n; i += gs) sx.v[0] += x[i];
+  Vec<1> ox;
+  if (!grid_sum<1>(sx, A.partial, A.max_blocks, 12, A.st, epoch, ox)) return;
+  const double mean_x = ox.v[0] / (double)n;
+  for (int i = t0; i < n; i += gs) x[i] -= mean_x;
+  record(A.st, A.stat_index, it, conv, bnorm > 0.0 ? res / bnorm : 0.0);
+}
+
+int g_num_sms = 0;
+
+int coop_limit(const void* kernel) {
+  if (g_num_sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+  }
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kBlock, 0);
+  if (per_sm > 4) per_sm = 4;
+  return per_sm * g_num_sms;
+}
+
+int blocks_for(const void* kernel, long long rows, int max_blocks) {
+  long long want = (rows + kBlock - 1) / kBlock;
+  int lim = coop_limit(kernel);
+  if (lim > max_blocks) lim = max_blocks;
+  if (want > lim) want = lim;
+  if (want < 1) want = 1;
+  return (int)want;
+}
+
+}  // namespace
+
+int cooperative_blocks(const void* kernel, long long rows) { return blocks_for(kernel, rows, 1 << 30); }
+
+int max_cooperative_blocks() {
+  int a = coop_limit((const void*)k_bicgstab);
+  int b = coop_limit((const void*)k_pcg_poisson);
+  return a > b ? a : b;
+}
+
+cudaError_t launch_bicgstab(const Sys& sys, int has_z, const SolverCtl& ctl, Scratch& sc, DevStatus* st,
+                            cudaStream_t s) {
+  BcgArgs A;
+  A.sys = sys;
+  A.has_z = has_z;
+  A.tol = ctl.tol;
+  A.max_it = ctl.max_it;
+  A.stat_index = ctl.stat_index;
+  A.r = sc.v[0]; A.rh = sc.v[1]; A.p = sc.v[2]; A.v = sc.v[3]; A.y = sc.v[4]; A.z = sc.v[5]; A.t = sc.v[6];
+  A.partial = sc.partial;
+  A.max_blocks = sc.max_blocks;
+  A.st = st;
+  const int nb = blocks_for((const void*)k_bicgstab, sys.d.n, sc.max_blocks);
+  cudaError_t e = cudaMemsetAsync(&st->barrier, 0, sizeof(unsigned int), s);
+  if (e != cudaSuccess) return e;
+  void* args[] = {&A};
+  return cudaLaunchCooperativeKernel((const void*)k_bicgstab, dim3(nb), dim3(kBlock), args, 0, s);
+}
+
+cudaError_t launch_pcg_poisson(const Params& pr, double* b, double* x, const SolverCtl& ctl, Scratch& sc,
+                               DevStatus* st, cudaStream_t s) {
+  PcgArgs A;
+  A.nx = pr.nx; A.ny = pr.ny; A.nz = pr.nz; A.dim = pr.dim;
+  A.cx = 1.0 / (pr.hx * pr.hx);
+  A.cy = 1.0 / (pr.hy * pr.hy);
+  A.cz = (pr.dim == 3) ? 1.0 / (pr.hz * pr.hz) : 0.0;
+  A.b = b; A.x = x;
+  A.r = sc.v[0]; A.p = sc.v[4]; A.q = sc.v[3];
+  A.tol = ctl.tol;
+  A.max_it = ctl.max_it;
+  A.stat_index = ctl.stat_index;
+  A.partial = sc.partial;
+  A.max_blocks = sc.max_blocks;
+  A.st = st;
+  const long long n = (long long)pr.nx * pr.ny * pr.nz;
+  const int nb = blocks_for((const void*)k_pcg_poisson, n, sc.max_blocks);
+  cudaError_t e = cudaMemsetAsync(&st->barrier, 0, sizeof(unsigned int), s);
+  if (e != cudaSuccess) return e;
+  void* args[] = {&A};
+  return cudaLaunchCooperativeKernel((const void*)k_pcg_poisson, dim3(nb), dim3(kBlock), args, 0, s);
+}
+
+}  // namespace solid

@@ -1,0 +1,213 @@
+// Internal declarations shared by the CUDA translation units of libsolid.
+//
+// Layout in HBM (all carved from the caller's workspace, 256-byte aligned):
+//   * every vector (field, DIA plane, solver vector) is a flat FP64 (or FP32)
+//     array on its own row grid, x fastest, with a zero guard band of G
+//     entries in front and behind, so that the 7-point stencil of any row
+//     (offsets +-1, +-mx, +-mx*my) reads inside the allocation without
+//     branches; the coefficient of a neighbour outside the grid is 0.
+//   * DIA systems store 7 planes P, W, E, S, N, B, T (Eq. 4.1), the right-hand
+//     side b and the inverse diagonal used by the Jacobi preconditioner.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/solid.h"
+
+namespace solid {
+
+constexpr int kBlock = 256;              // threads per block of every kernel
+constexpr int kMaxRedSlots = 16;         // reduction slots (one per reduction site)
+constexpr long long kSpinLimit = 1LL << 22;  // grid-barrier polls before giving up (~1 s)
+
+// device-side error codes (sticky word in DevStatus::err)
+enum : int { kErrNone = 0, kErrBarrier = 1 };
+
+struct Dims {
+  int mx, my, mz;      // row grid of a system / field
+  long long n;         // mx * my * mz
+};
+
+// Per-solve outcome written by the solver kernels.
+struct SolveStat {
+  long long iters_total;   // summed over solves since the host last read it
+  int iters;
+  int refinements;
+  int converged;       // 1 converged, 0 hit the cap
+  int nonfinite;       // 1 if a non-finite residual appeared
+  double relres;
+};
+
+// Device status block (one per case).
+struct DevStatus {
+  unsigned int barrier;          // grid-barrier arrival counter (reset before each cooperative launch)
+  unsigned int pad0;
+  int err;                       // sticky kErr* code of device-side waits
+  int sticky;                    // sticky ss_status of solves since the last read
+  SolveStat stat[SS_NSYS];
+  double scal[kMaxRedSlots * 4]; // broadcast scalars (unused by the all-blocks reduction)
+};
+
+template <typename T>
+struct Planes {
+  T *P, *W, *E, *S, *N, *B, *T_, *idiag;
+};
+
+struct Sys {
+  Dims d;
+  Planes<double> a;      // FP64 planes
+  Planes<float> af;      // FP32 copies for the mixed-precision inner solve (may be null)
+  double* b;
+  double* x;             // solution (aliases a field or a scratch vector)
+};
+
+// Physical and numerical parameters passed by value to kernels.
+struct Params {
+  int dim, nx, ny, nz, vert;
+  double hx, hy, hz, dt;
+  double Tm, m, kp, C0, rho, k, cp, L, mu, Dl, betaT, betaC, K0, Ce, gravity, eps, Tref;
+  int has_eutectic;
+  // Robin coefficient coef = U / (rho cp h) and T_ext per wall (coef 0: adiabatic)
+  double robin_coef[6], robin_text[6];
+};
+
+// Krylov scratch: 8 FP64 vectors + 8 FP32 vectors, each of `nmax` rows with guards.
+struct Scratch {
+  double* v[8];
+  float* f[8];
+  double* partial;       // [kMaxRedSlots][max_blocks]
+  int max_blocks;
+};
+
+// ---------------------------------------------------------------- device helpers
+
+__device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int* p) {
+  unsigned int v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Grid-wide barrier for cooperative launches. The arrival counter is zeroed
+// by the host before the launch; `epoch` counts barriers passed by this block.
+// A poll limit bounds the wait: on expiry the sticky error is set and every
+// block returns false from then on, so the kernel unwinds instead of hanging.
+__device__ __forceinline__ bool grid_barrier(DevStatus* st, unsigned int nblocks, unsigned int& epoch) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    epoch += 1u;
+    const unsigned int target = epoch * nblocks;
+    __threadfence();
+    atomicAdd(&st->barrier, 1u);
+    int ok = 1;
+    long long spins = 0;
+    while (ld_acquire_u32(&st->barrier) < target) {
+      if (*(volatile int*)&st->err != kErrNone) { ok = 0; break; }
+      if (++spins > kSpinLimit) { atomicExch(&st->err, kErrBarrier); ok = 0; break; }
+      __nanosleep(32);
+    }
+    __threadfence();
+    s_ok = ok && (*(volatile int*)&st->err == kErrNone);
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+template <int K>
+struct Vec { double v[K]; };
+
+// Block-wide sum of K doubles; result valid in all threads.
+template <int K>
+__device__ __forceinline__ Vec<K> block_sum(Vec<K> x) {
+  __shared__ double sh[K][kBlock / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < K; ++q) {
+    double s = x.v[q];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) sh[q][wid] = s;
+  }
+  __syncthreads();
+  Vec<K> r;
+#pragma unroll
+  for (int q = 0; q < K; ++q) {
+    double s = 0.0;
+#pragma unroll
+    for (int w = 0; w < kBlock / 32; ++w) s += sh[q][w];
+    r.v[q] = s;
+  }
+  __syncthreads();
+  return r;
+}
+
+// Deterministic grid reduction of K doubles: every block writes its partial
+// sums to slots [slot, slot+K), passes a grid barrier, then sums all blocks'
+// partials in block order (same order in every block, so every block gets
+// bit-identical totals). Returns false if the barrier gave up.
+template <int K>
+__device__ __forceinline__ bool grid_sum(Vec<K> x, double* partial, int max_blocks, int slot, DevStatus* st,
+                                         unsigned int& epoch, Vec<K>& out) {
+  Vec<K> b = block_sum<K>(x);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int q = 0; q < K; ++q) partial[(size_t)(slot + q) * max_blocks + blockIdx.x] = b.v[q];
+  }
+  if (!grid_barrier(st, gridDim.x, epoch)) return false;
+  __shared__ double tot[K];
+  if (threadIdx.x < 32) {
+#pragma unroll
+    for (int q = 0; q < K; ++q) {
+      const volatile double* pp = partial + (size_t)(slot + q) * max_blocks;
+      double s = 0.0;
+      for (int i = threadIdx.x; i < (int)gridDim.x; i += 32) s += pp[i];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+      if (threadIdx.x == 0) tot[q] = s;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < K; ++q) out.v[q] = tot[q];
+  __syncthreads();
+  return true;
+}
+
+// ---------------------------------------------------------------- host-side launchers
+
+// assemble.cu
+cudaError_t launch_assemble_momentum(int comp, const Params& pr, const Sys& sys, const double* const vel[3],
+                                     double* ustar, const double* p, const double* T, const double* Cl,
+                                     const double* Kinv, cudaStream_t s);
+cudaError_t launch_assemble_solute(const Params& pr, const Sys& sys, const double* const vel[3], const double* gl,
+                                   const double* C, const double* Ag, cudaStream_t s);
+cudaError_t launch_assemble_temperature(const Params& pr, const Sys& sys, const double* const vel[3],
+                                        const double* T, cudaStream_t s);
+cudaError_t launch_poisson_rhs(const Params& pr, const double* const ustar[3], double* b, cudaStream_t s);
+cudaError_t launch_project(const Params& pr, double* const vel[3], const double* const ustar[3], const double* pc,
+                           double* p, cudaStream_t s);
+cudaError_t launch_lever(const Params& pr, double* T, double* gl, const double* C, double* Cl, double* Cs,
+                         double* Kinv, double* Ag, cudaStream_t s);
+// from_T: recompute g_l from (T, C) in equilibrium; write_cl: recompute C_l, C_s.
+// K^{-1} and A_g are always refreshed from g_l.
+cudaError_t launch_equilibrate(const Params& pr, const double* T, const double* C, double* gl, double* Cl,
+                               double* Cs, double* Kinv, double* Ag, int from_T, int write_cl, cudaStream_t s);
+cudaError_t launch_fp32_planes(const Sys& sys, int dim, cudaStream_t s);
+
+// krylov.cu
+struct SolverCtl {
+  double tol;
+  int max_it;
+  int mixed;             // 1: FP32 inner iterations in FP64 iterative refinement
+  int stat_index;        // SS_SYS_* slot of DevStatus::stat
+};
+cudaError_t launch_bicgstab(const Sys& sys, int has_z, const SolverCtl& ctl, Scratch& sc, DevStatus* st,
+                            cudaStream_t s);
+cudaError_t launch_pcg_poisson(const Params& pr, double* b, double* x, const SolverCtl& ctl, Scratch& sc,
+                               DevStatus* st, cudaStream_t s);
+int cooperative_blocks(const void* kernel, long long rows);
+int max_cooperative_blocks();
+
+}  // namespace solid

@@ -1,0 +1,301 @@
+"""Parity of the CUDA path (through the C-ABI) with the FP64 CPU oracle.
+
+Stage by stage (assembly planes, lever update, each solve, projection) on
+seeded random states, then whole steps: 100 steps on the 2D cavity and on a
+ragged 3D box must match the oracle to a relative L-infinity error of 1e-9
+on every field. At the full 128x96x96 size the oracle checks what it can
+afford: assembly and lever rule on every row, residuals of the GPU solves,
+divergence, solute conservation and phase bounds."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle.scheme import State
+from paper_2303_10783_gb300 import cases, solid
+
+pytestmark = pytest.mark.gpu
+
+STEP_TOL = 1e-9          # relative L-inf bound on every field after 100 steps (FP64 path)
+PLANE_TOL = 1e-12        # assembly planes, relative to the row scale
+
+
+def _rel(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+def _oracle_state(f):
+    return State([f["u"], f["v"], f["w"]], f["p"], f["T"], f["C"], f["gl"], f["Cl"], f.get("Cs", 0.1 * f["Cl"]))
+
+
+def _tight(case):
+    case["tol_p"] = 1e-14
+    case["tol_t"] = 1e-14
+    case["max_it_p"] = 50000
+    case["max_it_t"] = 5000
+    return case
+
+
+CASES_2D = [cases.cavity_2d(61, 37, robin={"x-": (400.0, 298.0), "y+": (60.0, 300.0)})]
+CASES_3D = [cases.box_3d(27, 19, 13, robin={"x-": (400.0, 298.0), "z+": (60.0, 300.0)})]
+SMALL = CASES_2D + CASES_3D
+
+
+def _random_case(case, seed):
+    c = solid.Case(case)
+    f = cases.random_state(case, seed)
+    c.set_fields(f)
+    return c, f
+
+
+@pytest.mark.parametrize("case", SMALL, ids=["2d", "3d"])
+def test_assembly_planes_match_oracle(lib, case):
+    c, f = _random_case(case, 11)
+    g = oracle.Grid(case)
+    st = _oracle_state(f)
+    for a, name in enumerate("uvw"[: case["dim"]]):
+        c.assemble(name)
+        gpu = c.get_system(name)
+        ref = oracle.assemble_momentum(g, st, case, a)
+        scale = np.abs(ref["P"]).max()
+        for k in oracle.PLANES + ("b",):
+            s = scale if k != "b" else np.abs(ref["b"]).max()
+            assert np.abs(gpu[k] - ref[k]).max() <= PLANE_TOL * s, (name, k)
+        assert np.array_equal(gpu["x"], f[name])    # u* starts from u^n
+    # pressure right-hand side from u* = u^n
+    c.assemble("p")
+    gp = c.get_system("p")["b"]
+    ref = oracle.poisson_rhs(g, st.vel, case)
+    assert _rel(gp - gp.mean(), ref) < 1e-12
+    for name, ref in (("C", oracle.assemble_solute(g, st.vel, st.gl, st.C, case)),
+                      ("T", oracle.assemble_temperature(g, st.vel, st.T, case))):
+        c.assemble(name)
+        gpu = c.get_system(name)
+        scale = np.abs(ref["P"]).max()
+        for k in oracle.PLANES:
+            assert np.abs(gpu[k] - ref[k]).max() <= PLANE_TOL * scale, (name, k)
+        assert _rel(gpu["b"], ref["b"]) < 1e-14
+    c.close()
+
+
+@pytest.mark.parametrize("with_eutectic", [True, False])
+def test_lever_kernel_matches_oracle(lib, with_eutectic):
+    case = cases.box_3d(33, 17, 9)
+    if not with_eutectic:
+        case["alloy"]["Ce"] = None
+    al = case["alloy"]
+    rng = np.random.default_rng(7)
+    shape = cases.cell_shape(case)
+    C = al["C0"] * rng.uniform(0.2, 8.0, shape)
+    Tl = al["Tm"] + al["m"] * C
+    Ts = Tl + rng.uniform(-60.0, 5.0, shape)
+    gn = rng.uniform(0.0, 1.0, shape)
+    gn[rng.uniform(size=shape) < 0.2] = 1.0
+    gn[rng.uniform(size=shape) < 0.1] = 0.0
+    c = solid.Case(case)
+    c.set_fields({"T": Ts, "gl": gn, "C": C})
+    c.lever()
+    gpu = c.get_fields(("T", "gl", "Cl", "Cs", "C"))
+    T, g, Cl, Cs = oracle.lever_update(Ts, gn, C, al)
+    assert np.abs(gpu["gl"] - g).max() < 1e-12
+    assert _rel(gpu["T"], T) < 1e-14
+    assert _rel(gpu["Cl"], Cl) < 1e-12
+    assert _rel(gpu["Cs"], Cs) < 1e-12
+    assert np.array_equal(gpu["C"], C)
+    c.close()
+
+
+@pytest.mark.parametrize("case", SMALL, ids=["2d", "3d"])
+def test_solves_match_oracle(lib, case):
+    case = _tight(dict(case))
+    c, f = _random_case(case, 12)
+    g = oracle.Grid(case)
+    st = _oracle_state(f)
+    # predictor components
+    ustar = []
+    for a, name in enumerate("uvw"[: case["dim"]]):
+        c.assemble(name)
+        c.solve(name)
+        x = c.get_system(name)["x"]
+        ref = oracle.solve_system(oracle.assemble_momentum(g, st, case, a))
+        assert _rel(x, ref) < 1e-11, name
+        ustar.append(ref)
+    if case["dim"] == 2:
+        ustar.append(np.zeros(g.faces(2)))
+    # pressure correction and projection
+    c.assemble("p")
+    c.solve("p")
+    pc = c.get_system("p")["x"]
+    pref = oracle.solve_poisson(g, oracle.poisson_rhs(g, ustar, case))
+    assert _rel(pc, pref) < 1e-10
+    assert abs(pc.mean()) < 1e-12 * np.abs(pref).max()
+    c.project()
+    out = c.get_fields(("u", "v", "w", "p"))
+    vel = oracle.project(g, ustar, pref, case)
+    for a, name in enumerate("uvw"[: case["dim"]]):
+        assert _rel(out[name], vel[a]) < 1e-10, name
+    assert np.abs(oracle.divergence(g, [out["u"], out["v"], out["w"]])).max() < 1e-10
+    # solute and temperature with the projected velocity
+    st2 = _oracle_state(dict(f, u=vel[0], v=vel[1], w=vel[2]))
+    c.assemble("C")
+    c.solve("C")
+    Cref = oracle.solve_system(oracle.assemble_solute(g, st2.vel, st2.gl, st2.C, case))
+    assert _rel(c.get_fields(("C",))["C"], Cref) < 1e-12
+    c.assemble("T")
+    c.solve("T")
+    Tref = oracle.solve_system(oracle.assemble_temperature(g, st2.vel, st2.T, case))
+    assert _rel(c.get_fields(("T",))["T"], Tref) < 1e-12
+    c.close()
+
+
+def _run_pair(case, nsteps, T0shift=-0.8):
+    f = cases.initial_fields(case)
+    T0 = f["T"] + T0shift
+    c = solid.Case(case)
+    c.initialize(T0, f["C"])
+    g = oracle.Grid(case)
+    st = oracle.initial_state(case, T0, f["C"])
+    init = c.get_fields()
+    for k in ("T", "C", "gl", "Cl", "Cs"):
+        assert _rel(init[k], getattr(st, k)) < 1e-15, k
+    c.step(nsteps)
+    c.sync()
+    stats = c.stats()
+    gpu = c.get_fields()
+    for _ in range(nsteps):
+        st = oracle.step(g, st, case)
+    c.close()
+    return gpu, st, stats
+
+
+@pytest.mark.parametrize("case", [cases.cavity_2d(), cases.box_3d(19, 13, 11)], ids=["2d-50x30", "3d-19x13x11"])
+def test_step_parity_100_steps(lib, case):
+    """The FP64 GPU step matches the oracle to 1e-9 relative L-inf on every field after 100 steps."""
+    case = _tight(dict(case))
+    gpu, st, stats = _run_pair(case, 100)
+    assert stats["status"] == solid.SS_OK
+    for k in ("p", "T", "C", "gl", "Cl", "Cs"):
+        assert _rel(gpu[k], getattr(st, k)) < STEP_TOL, (k, _rel(gpu[k], getattr(st, k)))
+    # the velocity is one vector field (Eq. 2.1): its relative error is taken
+    # against the largest velocity component, so a small transverse component
+    # is not judged against its own, much smaller, scale
+    vmax = max(np.abs(x).max() for x in st.vel)
+    for a, k in enumerate("uvw"[: case["dim"]]):
+        err = np.abs(gpu[k] - st.vel[a]).max() / vmax
+        assert err < STEP_TOL, (k, err)
+    assert st.gl.min() < 1.0   # the mush formed: the lever rule and Darcy terms were exercised
+
+
+@pytest.mark.parametrize("dims", [(1, 1, 1), (2, 1, 1), (3, 2, 2), (1, 5, 3)])
+def test_degenerate_grids(lib, dims):
+    """Single-cell and one-cell-thick grids step without error and keep the invariants."""
+    nx, ny, nz = dims
+    case = _tight(cases.box_3d(nx, ny, nz))
+    gpu, st, stats = _run_pair(case, 5)
+    assert stats["status"] == solid.SS_OK
+    for k in ("T", "C", "gl", "u", "v", "w"):
+        assert np.abs(gpu[k] - getattr(st, k)).max() <= 1e-9 * max(np.abs(getattr(st, k)).max(), 1e-12), k
+
+
+def test_fully_solid_and_fully_liquid(lib):
+    case = _tight(cases.cavity_2d(20, 12))
+    for shift in (+5.0, -60.0):
+        gpu, st, stats = _run_pair(case, 10, T0shift=shift)
+        assert stats["status"] == solid.SS_OK
+        for k in ("T", "gl", "C", "u", "v"):
+            assert np.abs(gpu[k] - getattr(st, k)).max() <= 1e-9 * max(np.abs(getattr(st, k)).max(), 1e-12), (shift, k)
+
+
+def test_iteration_cap_is_reported(lib):
+    """A solve that hits its cap records SS_ENOTCONV (sticky) and keeps its iterate; nothing traps."""
+    case = cases.cavity_2d(30, 20, tol_p=1e-14, max_it_p=2)
+    f = cases.initial_fields(case)
+    c = solid.Case(case)
+    c.initialize(f["T"] - 0.8, f["C"])
+    c.step(2)
+    assert c.sync(allow=(solid.SS_ENOTCONV,)) == solid.SS_ENOTCONV
+    s = c.stats()
+    assert s["iters"]["p"] == 2
+    assert c.sync() == solid.SS_OK       # cleared by the read
+    assert np.all(np.isfinite(c.get_fields(("u", "T"))["u"]))
+    c.close()
+
+
+def test_bad_arguments(lib):
+    import ctypes
+    case = cases.cavity_2d(10, 8)
+    c = solid.Case(case)
+    assert lib.ss_step(c.h, -1) == solid.SS_EINVAL
+    assert lib.ss_assemble(c.h, 2) == solid.SS_EINVAL    # no w system in 2D
+    assert lib.ss_set_boundary(c.h, 7, ctypes.byref(solid.BC(1, 10.0, 300.0))) == solid.SS_EINVAL
+    c.step(1)
+    c.sync()
+    al = solid.alloy_struct(case)
+    assert lib.ss_set_alloy(c.h, ctypes.byref(al)) == solid.SS_ESTATE
+    g = solid.grid_struct(case)
+    h = ctypes.c_void_p()
+    assert lib.ss_create_case(ctypes.byref(g), ctypes.c_void_p(c.workspace.data_ptr()), 1024, None,
+                              ctypes.byref(h)) == solid.SS_ENOMEM
+    c.close()
+
+
+# ------------------------------------------------------------------ full size (the benchmark workload)
+
+@pytest.fixture(scope="module")
+def full():
+    case = cases.box_3d()
+    return case
+
+
+def test_full_size_assembly_and_lever(lib, full):
+    """128x96x96: every assembled row and every lever-rule cell equals the oracle's."""
+    case = full
+    c, f = _random_case(case, 21)
+    g = oracle.Grid(case)
+    st = _oracle_state(f)
+    for a, name in enumerate("uvw"):
+        c.assemble(name)
+        gpu = c.get_system(name)
+        ref = oracle.assemble_momentum(g, st, case, a)
+        scale = np.abs(ref["P"]).max()
+        for k in oracle.PLANES:
+            assert np.abs(gpu[k] - ref[k]).max() <= PLANE_TOL * scale, (name, k)
+    c.assemble("T")
+    gpu = c.get_system("T")
+    ref = oracle.assemble_temperature(g, st.vel, st.T, case)
+    assert np.abs(gpu["P"] - ref["P"]).max() <= PLANE_TOL * np.abs(ref["P"]).max()
+    c.lever()
+    out = c.get_fields(("T", "gl"))
+    T, gl, _, _ = oracle.lever_update(f["T"], f["gl"], f["C"], case["alloy"])
+    assert np.abs(out["gl"] - gl).max() < 1e-12
+    assert _rel(out["T"], T) < 1e-14
+    c.close()
+
+
+def test_full_size_steps_keep_invariants(lib, full):
+    """Three benchmark steps at 128x96x96 (bench tolerances): every solve
+    converges, the true residual of the last T* solve meets its tolerance,
+    the projected velocity is divergence-free, solute mass is conserved and
+    0 <= g_l <= 1."""
+    case = dict(full)
+    f = cases.initial_fields(case)
+    c = solid.Case(case)
+    c.initialize(f["T"] - 0.8, f["C"])
+    C0 = c.get_fields(("C",))["C"].sum()
+    c.step(3)
+    s = c.stats()
+    assert s["status"] == solid.SS_OK, s
+    out = c.get_fields()
+    g = oracle.Grid(case)
+    assert np.abs(oracle.divergence(g, [out["u"], out["v"], out["w"]])).max() < 1e-9
+    assert abs(out["C"].sum() - C0) <= 1e-11 * C0
+    assert out["gl"].min() >= 0.0 and out["gl"].max() <= 1.0 and out["gl"].min() < 1.0
+    for k in ("u", "v", "w", "p", "T", "C"):
+        assert np.all(np.isfinite(out[k]))
+    # re-solve one T* system and check its true residual with the oracle's sparse view
+    c.assemble("T")
+    c.solve("T")
+    sysT = c.get_system("T")
+    A = oracle.sparse_from_planes(sysT)
+    r = sysT["b"].ravel() - A @ sysT["x"].ravel()
+    assert np.linalg.norm(r) <= 10 * case["tol_t"] * np.linalg.norm(sysT["b"])
+    c.close()
