@@ -221,6 +221,41 @@ ss_status ss_get_system(ss_case* c, int sys, void* const* dst, int dst_is_device
 ss_status ss_project(ss_case* c);
 ss_status ss_lever(ss_case* c);
 
+/* ---- Pressure-correction solve that allocates nothing.
+ *
+ * The paper has no counterpart to this call; it exists for callers that
+ * cannot allocate device memory: an application whose memory manager owns
+ * the whole GPU and rejects allocations it did not make, a loop with a hard
+ * latency budget where a cudaMalloc (which may synchronise the device) is
+ * not acceptable, or a plugin that is handed only a stream and device
+ * pointers. It solves A p' = b - mean(b), A = -L the Neumann Laplacian of
+ * Eq. 3.4 on an nx*ny*nz cell grid (x fastest; nz ignored when dim == 2)
+ * with spacings hx, hy, hz, by the same Jacobi-preconditioned CG as ss_solve
+ * (SS_SYS_P), and writes the zero-mean p' to x.
+ *
+ *   b, x      device pointers to nx*ny*nz doubles (b is not modified; the
+ *             caller owns both)
+ *   tol       relative 2-norm residual tolerance (> 0); max_it >= 1
+ *   iters, relres  optional host outputs; when either is non-NULL the call
+ *             waits for the solve and returns its outcome (SS_ENOTCONV when
+ *             max_it was reached); when both are NULL it returns after
+ *             enqueueing on `stream` (a cudaStream_t, NULL = default stream).
+ *
+ * Its scratch is a fixed file-scope device array of about 4.3 MB (solver
+ * vectors for at most 131072 cells, reduction partials, status block):
+ * every GPU on which the library's device code is loaded holds it until the
+ * process exits. Larger grids are rejected with SS_EINVAL and a message in
+ * ss_last_error(). The array is shared by all calls and keeps the last
+ * call's contents (each call clears what must start at zero), so calls that
+ * overlap on the GPU -- on different streams or from different threads --
+ * race and must not be issued. The first call on each device looks up the
+ * array's device address (cudaGetSymbolAddress) with that device current;
+ * make that first call before any stream capture. No cudaMalloc, cudaFree
+ * or allocating library routine is called. */
+ss_status ss_poisson_solve_noalloc(int dim, int nx, int ny, int nz, double hx, double hy, double hz,
+                                   const double* b, double* x, double tol, int max_it, int* iters,
+                                   double* relres, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

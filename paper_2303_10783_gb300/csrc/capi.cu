@@ -60,6 +60,16 @@ struct Planner {
 
 }  // namespace
 
+namespace solid {
+// Lets other translation units set the message ss_last_error() returns.
+void set_error_message(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof g_err, fmt, ap);
+  va_end(ap);
+}
+}  // namespace solid
+
 struct ss_case {
   ss_grid g;
   Params pr;

@@ -18,6 +18,8 @@
 //
 // Vectors that other blocks write during the solve (the SpMV operands) are
 // read with ld.global.cg so a stale L1 line can never be used.
+#include <mutex>
+
 #include "solid_internal.cuh"
 
 namespace solid {
@@ -355,4 +357,131 @@ cudaError_t launch_pcg_poisson(const Params& pr, double* b, double* x, const Sol
   return cudaLaunchCooperativeKernel((const void*)k_pcg_poisson, dim3(nb), dim3(kBlock), args, 0, s);
 }
 
+// ---------------------------------------------------------------- pressure solve without allocation
+//
+// Some callers cannot allocate device memory at all: an application whose
+// memory manager owns every byte of the GPU and forbids allocations it did
+// not make, a host loop with a hard latency budget in which a cudaMalloc
+// (which can synchronise the device) is not acceptable, or a plugin that is
+// handed only a stream and device pointers. For them the pressure-correction
+// solve is offered with its scratch (solver vectors, reduction partials and
+// status block) in a fixed file-scope device array instead of a workspace.
+// The array is shared by every call in the process and keeps the last
+// call's contents; each call clears the parts that must start at zero.
+// Two such calls that overlap on the GPU (on different streams, or from
+// different threads) race on the array.
+
+constexpr long long kNoAllocMaxCells = 1LL << 17;     // 131072 cells (e.g. 64 x 64 x 32)
+constexpr int kNoAllocMaxBlocks = 1024;
+constexpr size_t kNoAllocStatusBytes = (sizeof(DevStatus) + 255) & ~(size_t)255;
+constexpr size_t kNoAllocPartialBytes = (size_t)kMaxRedSlots * kNoAllocMaxBlocks * sizeof(double);
+constexpr size_t kNoAllocBytes = kNoAllocStatusBytes + kNoAllocPartialBytes + 4 * kNoAllocMaxCells * sizeof(double);
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+namespace {
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[kNoAllocMaxDevices] = {nullptr};
+
+// Device address of the scratch array on the current device; looked up once
+// per device (with that device current) and cached.
+cudaError_t noalloc_scratch(unsigned char** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    g_noalloc_addr[dev] = p;
+  }
+  *out = static_cast<unsigned char*>(g_noalloc_addr[dev]);
+  return cudaSuccess;
+}
+}  // namespace
+
+void set_error_message(const char* fmt, ...);   // capi.cu: the message ss_last_error() returns
+
 }  // namespace solid
+
+extern "C" ss_status ss_poisson_solve_noalloc(int dim, int nx, int ny, int nz, double hx, double hy, double hz,
+                                              const double* b, double* x, double tol, int max_it, int* iters,
+                                              double* relres, void* stream) {
+  using namespace solid;
+  if (dim == 2) nz = 1;
+  if ((dim != 2 && dim != 3) || nx < 1 || ny < 1 || nz < 1) {
+    set_error_message("ss_poisson_solve_noalloc: dim must be 2 or 3 and every cell count >= 1");
+    return SS_EINVAL;
+  }
+  const long long n = (long long)nx * ny * nz;
+  if (n > kNoAllocMaxCells) {
+    set_error_message("ss_poisson_solve_noalloc: %lld cells exceed its fixed limit of %lld cells", n,
+                      kNoAllocMaxCells);
+    return SS_EINVAL;
+  }
+  if (!b || !x || !(hx > 0) || !(hy > 0) || (dim == 3 && !(hz > 0)) || !(tol > 0) || max_it < 1) {
+    set_error_message("ss_poisson_solve_noalloc: NULL vector, non-positive spacing or tolerance, or max_it < 1");
+    return SS_EINVAL;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  unsigned char* base = nullptr;
+  cudaError_t e = noalloc_scratch(&base);
+  if (e != cudaSuccess) {
+    set_error_message("ss_poisson_solve_noalloc: scratch address lookup failed: %s", cudaGetErrorString(e));
+    return SS_ECUDA;
+  }
+  DevStatus* st = reinterpret_cast<DevStatus*>(base);
+  double* partial = reinterpret_cast<double*>(base + kNoAllocStatusBytes);
+  double* vec = reinterpret_cast<double*>(base + kNoAllocStatusBytes + kNoAllocPartialBytes);
+  PcgArgs A;
+  A.nx = nx; A.ny = ny; A.nz = nz; A.dim = dim;
+  A.cx = 1.0 / (hx * hx);
+  A.cy = 1.0 / (hy * hy);
+  A.cz = (dim == 3) ? 1.0 / (hz * hz) : 0.0;
+  A.b = vec;                       // the kernel removes the mean in place: work on a copy
+  A.r = vec + n;
+  A.p = vec + 2 * n;
+  A.q = vec + 3 * n;
+  A.x = x;
+  A.tol = tol;
+  A.max_it = max_it;
+  A.stat_index = SS_SYS_P;
+  A.partial = partial;
+  A.max_blocks = kNoAllocMaxBlocks;
+  A.st = st;
+  const int nb = blocks_for((const void*)k_pcg_poisson, n, kNoAllocMaxBlocks);
+  void* args[] = {&A};
+  if ((e = cudaMemsetAsync(st, 0, sizeof(DevStatus), s)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(A.b, b, n * sizeof(double), cudaMemcpyDeviceToDevice, s)) != cudaSuccess ||
+      (e = cudaLaunchCooperativeKernel((const void*)k_pcg_poisson, dim3(nb), dim3(kBlock), args, 0, s)) !=
+          cudaSuccess) {
+    set_error_message("ss_poisson_solve_noalloc: %s", cudaGetErrorString(e));
+    return SS_ECUDA;
+  }
+  if (!iters && !relres) return SS_OK;
+  DevStatus h;
+  if ((e = cudaMemcpyAsync(&h, st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(s)) != cudaSuccess) {
+    set_error_message("ss_poisson_solve_noalloc: %s", cudaGetErrorString(e));
+    return SS_ECUDA;
+  }
+  if (iters) *iters = h.stat[SS_SYS_P].iters;
+  if (relres) *relres = h.stat[SS_SYS_P].relres;
+  if (h.err != kErrNone) {
+    set_error_message("ss_poisson_solve_noalloc: a grid barrier timed out");
+    return SS_ETIMEOUT;
+  }
+  if (h.stat[SS_SYS_P].nonfinite) {
+    set_error_message("ss_poisson_solve_noalloc: non-finite residual");
+    return SS_ENAN;
+  }
+  if (!h.stat[SS_SYS_P].converged) {
+    set_error_message("ss_poisson_solve_noalloc: reached max_it before tol");
+    return SS_ENOTCONV;
+  }
+  return SS_OK;
+}
+

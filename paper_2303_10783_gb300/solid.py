@@ -86,6 +86,9 @@ def _declare(lib):
         "ss_lever": [P],
         "ss_set_profiling": [P, ctypes.c_int],
         "ss_get_profile": [P, ctypes.POINTER(Profile)],
+        "ss_poisson_solve_noalloc": [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                     ctypes.c_double, ctypes.c_double, P, P, ctypes.c_double, ctypes.c_int,
+                                     ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double), P],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
