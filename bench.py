@@ -4,10 +4,12 @@
 One benchmark step is one time step of Algorithm 1 (momentum predictor,
 pressure projection, solute, two-step energy with the lever rule) on the 3D
 box workload: 0.10 x 0.06 x 0.06 m at 128 x 96 x 96 cells (1.18 M), Sn-Pb-like
-alloy, left wall Robin-cooled, pressure PCG rel tol 1e-10, transport
-BiCGSTAB rel tol 1e-12. Prints ONE JSON line (rank 0).
+alloy, left wall Robin-cooled, pressure solve rel tol 1e-10, transport solves
+rel tol 1e-12. The headline is the mixed-precision path (FP32 inner
+iterations in FP64 refinement); the FP64 path is measured beside it at the
+same tolerances. Prints ONE JSON line (rank 0).
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|mixed]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision both|mixed|fp64]
     python bench.py --impl reference ...    # the FP64 CPU oracle on host cores
 
 Multi-GPU (torchrun): every rank steps its own independent replica of the
@@ -31,12 +33,18 @@ if ROOT not in sys.path:
 from paper_2303_10783_gb300 import cases  # noqa: E402
 
 WORKLOAD = "box_3d_128x96x96"
-# algorithmic work of the pressure solve (matrix-free 7-point PCG, per cell per iteration):
-#   flops: A p 13, (p,q) 2, x += a p 2, r -= a q 2, z = M^-1 r 1, (r,z) 2, (r,r) 2, p = z + b p 2  -> 26
-#   bytes (FP64): A p reads p, writes q (16); x/r update reads x p r q, writes x r (48);
-#                 p update reads r p, writes p (24)                                  -> 88
-PCG_FLOPS_PER_CELL_IT = 26.0
-PCG_BYTES_PER_CELL_IT = 88.0
+# Algorithmic work of the multigrid-preconditioned pressure solve (k_pcg_mg), per fine cell:
+#   one CG iteration with a V(2,2)-cycle moves, at the fine level, A p (8 B in FP32), the x/r
+#   update with the first smoothing sweep (32), second pre-sweep (12), residual (12),
+#   restriction (5), prolongation (8.5), two post-sweeps (24), the dot products (8) and the
+#   p update (12) = 121.5 B, plus ~10 B on the coarser levels -> 131 B in FP32, 262 B in FP64.
+#   One FP64 refinement sweep of the mixed path adds 44 B (r = b - A x: 24, x += d: 20).
+#   FP64 flops per CG iteration (FMA = 2): A p and (p,q) 12, updates 5, pre-sweep 13, residual 11,
+#   restriction 21, prolongation 15, post-sweeps 26, dots 6, p update 3 = 112, coarse levels
+#   ~13 -> 125.
+MG_BYTES_PER_CELL_IT = {"mixed": 131.0, "fp64": 262.0}
+MG_BYTES_PER_CELL_REFINE = 44.0
+MG_FLOPS_PER_CELL_IT = 125.0
 FP64_FLOP_PER_CLK_PER_SM = 4.0   # 2 DFMA per clock per SM (1.25 TFLOP/s nominal at 2070 MHz, 152 SMs)
 NUM_SMS = 152
 
@@ -47,7 +55,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--precision", choices=("fp64", "mixed"), default="fp64")
+    ap.add_argument("--precision", choices=("both", "mixed", "fp64"), default="both",
+                    help="both: headline = mixed path, FP64 path measured alongside")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--nx", type=int, default=128)
@@ -160,14 +169,21 @@ def measured_peaks():
         return {}
 
 
+def kernel_source_sha():
+    """sha256 over the sources of the pressure-solve kernel (mg.cu and the shared header)."""
+    h = hashlib.sha256()
+    for f in ("mg.cu", "solid_internal.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2303_10783_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()
+
+
 def kernel_traffic(kernel):
     """DRAM bytes per launch of `kernel` from the committed ncu summary, if the
     summary was taken on the current source (its sha256 matches); else None."""
     path = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(path):
         return None
-    src = os.path.join(ROOT, "paper_2303_10783_gb300", "csrc", "krylov.cu")
-    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    sha = kernel_source_sha()
     for line in open(path):
         m = re.match(r"\s*(\S+)\s+sha256=(\w+)\s+bytes_per_launch=([0-9.eE+]+)\s+workload=(\S+)", line)
         if m and m.group(1) == kernel and m.group(2) == sha:
@@ -220,15 +236,12 @@ def run_reference(args):
     return 0
 
 
-def run_ours(args):
+def measure(args, precision_name, case, dist, local):
+    """Warm up, then time args.steps steps of one case on its own stream.
+    Returns the measured quantities (max over ranks applied by the caller)."""
     import torch
     from paper_2303_10783_gb300 import solid
-    rank, world, local = dist_env()
-    dist = init_group(world)
-    torch.cuda.set_device(local)
-    solid.load()
-    precision = solid.SS_MIXED if args.precision == "mixed" else solid.SS_FP64
-    case = workload(args, rank)
+    precision = solid.SS_MIXED if precision_name == "mixed" else solid.SS_FP64
     f = cases.initial_fields(case)
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
@@ -255,16 +268,14 @@ def run_ours(args):
         prof = c.get_profile()
         stats = c.stats()
         c.set_profiling(False)
-
-        # end to end through the public API with host buffers: every step uploads
-        # its full input state from pinned host memory, steps, and reads back all fields
         e2e = None
         if not args.no_e2e:
+            # end to end through the public API with host buffers: every step uploads its full
+            # input state from pinned host memory, steps, and reads every field back
             state = c.get_fields()
             host = {k: torch.from_numpy(v).pin_memory() for k, v in state.items() if not (k == "w" and case["dim"] == 2)}
             out = {k: torch.empty_like(v).pin_memory() for k, v in host.items()}
-            h2d = sum(v.numel() * 8 for v in host.values())
-            d2h = h2d
+            nbytes = sum(v.numel() * 8 for v in host.values())
             ke = max(2, min(args.steps, 5))
             barrier(dist)
             stream.synchronize()
@@ -276,66 +287,99 @@ def run_ours(args):
             stream.synchronize()
             e2e_s = time.perf_counter() - t0
             barrier(dist)
-            e2e_s = max_over_ranks(dist, e2e_s)
-            e2e = {"value": sum_over_ranks(dist, case["nx"] * case["ny"] * case["nz"] * ke) / e2e_s,
-                   "unit": "cell-steps/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                   "steps": ke, "path": "ss_set_fields(host) + ss_step(1) + ss_get_fields(host) per step"}
+            e2e = dict(seconds=e2e_s, steps=ke, h2d=nbytes, d2h=nbytes)
         c.close()
+    return dict(ms=ms, status=solid.STATUS_NAMES.get(status, status), prof=prof, stats=stats, clocks=clocks, e2e=e2e)
 
-    ms_max = max_over_ranks(dist, ms)
-    ncell = case["nx"] * case["ny"] * case["nz"]
-    total_cells = sum_over_ranks(dist, ncell * args.steps)
-    value = total_cells / (ms_max * 1e-3)
 
-    # roofline of the dominant stage (device time measured by the library's events on the case stream)
-    stage_ms = prof["ms"]
+def roofline(precision_name, m, ncell, steps):
+    """Roofline of the dominant stage (device time from the library's events on the case stream)."""
+    stage_ms = m["prof"]["ms"]
     top = max(stage_ms, key=stage_ms.get)
     peaks = measured_peaks()
-    sm_mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
-    roof = None
-    if top == "solve_p":
-        its = prof["iters"]["p"]
-        launches = max(prof["launches"]["solve_p"], 1)
-        t_launch = stage_ms[top] * 1e-3 / launches
-        flops = PCG_FLOPS_PER_CELL_IT * ncell * its / launches
-        bytes_ = PCG_BYTES_PER_CELL_IT * ncell * its / launches
-        if args.precision == "fp64":
-            peak = FP64_FLOP_PER_CLK_PER_SM * NUM_SMS * sm_mhz * 1e6 / 1e12
-            ach = flops / t_launch / 1e12
-            roof = {"bound": "alu", "kernel": "k_pcg_poisson", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                    "frac": ach / peak,
-                    "peak_basis": "FP64 pipe: 4 flop/clk/SM x 152 SMs x %.0f MHz median SM clock under load" % sm_mhz,
-                    "hbm_achieved_GBps": bytes_ / t_launch / 1e9,
-                    "hbm_frac_of_measured": bytes_ / t_launch / 1e9 / peaks.get("hbm_gbs", 6687.1)}
-        else:
-            hbm = peaks.get("hbm_gbs", 6687.1)
-            ach = bytes_ / 2 / t_launch / 1e9
-            roof = {"bound": "hbm", "kernel": "k_pcg_poisson", "achieved": ach, "peak": hbm, "unit": "GB/s",
-                    "frac": ach / hbm}
-        tr = kernel_traffic("k_pcg_poisson")
-        roof["traffic"] = tr[0] if tr else None
-        roof["algorithmic_per_launch"] = {"flops": flops, "bytes": bytes_, "iterations": its / launches,
-                                          "cells": ncell}
-        roof["launch_ms"] = t_launch * 1e3
+    sm_mhz = m["clocks"].get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    if top != "solve_p":
+        return {"stage": top, "note": "roofline counts are defined for the pressure solve only"}
+    launches = max(m["prof"]["launches"]["solve_p"], 1)
+    t_launch = stage_ms[top] * 1e-3 / launches
+    its = m["prof"]["iters"]["p"] / launches
+    refs = m["stats"]["refinements"]["p"]
+    bytes_ = ncell * (MG_BYTES_PER_CELL_IT[precision_name] * its + MG_BYTES_PER_CELL_REFINE * refs)
+    hbm = peaks.get("hbm_gbs", 6687.1)
+    out = {"kernel": "k_pcg_mg<%s>" % ("float" if precision_name == "mixed" else "double"),
+           "launch_ms": t_launch * 1e3, "algorithmic_per_launch": {"bytes": bytes_, "iterations": its,
+                                                                    "refinements": refs, "cells": ncell}}
+    if precision_name == "mixed":
+        ach = bytes_ / t_launch / 1e9
+        out.update(bound="hbm", achieved=ach, peak=hbm, unit="GB/s", frac=ach / hbm,
+                   peak_basis="measured HBM copy bandwidth (MEASURED_PEAKS.json)")
+    else:
+        flops = MG_FLOPS_PER_CELL_IT * ncell * its
+        peak = FP64_FLOP_PER_CLK_PER_SM * NUM_SMS * sm_mhz * 1e6 / 1e12
+        ach = flops / t_launch / 1e12
+        out.update(bound="alu", achieved=ach, peak=peak, unit="TFLOP/s", frac=ach / peak,
+                   peak_basis="FP64 pipe: 4 flop/clk/SM x 152 SMs x %.0f MHz median SM clock under load" % sm_mhz,
+                   hbm_achieved_GBps=bytes_ / t_launch / 1e9)
+        out["algorithmic_per_launch"]["flops"] = flops
+    tr = kernel_traffic(out["kernel"])
+    out["traffic"] = tr[0] if tr else None
+    return out
+
+
+def run_ours(args):
+    import torch
+    from paper_2303_10783_gb300 import solid
+    rank, world, local = dist_env()
+    dist = init_group(world)
+    torch.cuda.set_device(local)
+    solid.load()
+    case = workload(args, rank)
+    ncell = case["nx"] * case["ny"] * case["nz"]
+    names = ["mixed", "fp64"] if args.precision == "both" else [args.precision]
+    res = {}
+    for name in names:
+        m = measure(args, name, case, dist, local)
+        ms_max = max_over_ranks(dist, m["ms"])
+        total_cells = sum_over_ranks(dist, ncell * args.steps)
+        m["value"] = total_cells / (ms_max * 1e-3)
+        m["ms_max"] = ms_max
+        if m["e2e"]:
+            e2e_s = max_over_ranks(dist, m["e2e"]["seconds"])
+            m["e2e_value"] = sum_over_ranks(dist, ncell * m["e2e"]["steps"]) / e2e_s
+        res[name] = m
     if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
         return 0
+    head = names[0]
+    h = res[head]
     out = {
-        "metric": "cell-steps/s", "value": value, "unit": "cell-steps/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64",
-        "data": "synthetic",
-        "config": {"workload": WORKLOAD, "cells": ncell, "precision": args.precision, "tol_p": case["tol_p"],
-                   "tol_t": case["tol_t"], "dt": case["dt"], "parallelism": "replicas" if world > 1 else "single",
+        "metric": "cell-steps/s", "value": h["value"], "unit": "cell-steps/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": h["ms_max"] / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64" if head == "mixed" else "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "cells": ncell, "precision": head, "tol_p": case["tol_p"],
+                   "tol_t": case["tol_t"], "dt": case["dt"], "pressure_preconditioner": case.get("precond_p", "mg"),
+                   "parallelism": "replicas" if world > 1 else "single",
                    "l2": "inputs larger than L2: each step streams ~0.5 GB of fields and DIA planes (L2 129 MB); "
                          "no flush"},
-        "status": solid.STATUS_NAMES.get(status, status),
-        "clocks": clocks,
-        "e2e": e2e,
-        "gpu_launches": prof["kernels"],
-        "roofline": roof,
-        "stage_ms_per_step": {k: v / args.steps for k, v in stage_ms.items() if v > 0},
-        "iters_per_step": {k: v / args.steps for k, v in prof["iters"].items()},
+        "status": h["status"],
+        "clocks": h["clocks"],
+        "e2e": ({"value": h["e2e_value"], "unit": "cell-steps/s", "h2d_bytes_per_step": h["e2e"]["h2d"],
+                 "d2h_bytes_per_step": h["e2e"]["d2h"], "steps": h["e2e"]["steps"],
+                 "path": "ss_set_fields(host) + ss_step(1) + ss_get_fields(host) per step"} if h["e2e"] else None),
+        "gpu_launches": h["prof"]["kernels"],
+        "roofline": roofline(head, h, ncell, args.steps),
+        "stage_ms_per_step": {k: v / args.steps for k, v in h["prof"]["ms"].items() if v > 0},
+        "iters_per_step": {k: v / args.steps for k, v in h["prof"]["iters"].items()},
     }
+    for name in names[1:]:
+        m = res[name]
+        out[name] = {"value": m["value"], "ms_per_step": m["ms_max"] / args.steps, "status": m["status"],
+                     "dtype": "f64" if name == "fp64" else "f32+f64",
+                     "e2e_value": m.get("e2e_value"), "gpu_launches": m["prof"]["kernels"],
+                     "roofline": roofline(name, m, ncell, args.steps),
+                     "stage_ms_per_step": {k: v / args.steps for k, v in m["prof"]["ms"].items() if v > 0},
+                     "iters_per_step": {k: v / args.steps for k, v in m["prof"]["iters"].items()}}
     if world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args)
     print(json.dumps(out))

@@ -62,6 +62,7 @@ typedef enum {
 } ss_status;
 
 enum { SS_FP64 = 0, SS_MIXED = 1 };                  /* ss_grid.precision */
+enum { SS_PRECOND_MG = 0, SS_PRECOND_JACOBI = 1 };   /* ss_grid.precond_p */
 enum { SS_ADIABATIC = 0, SS_ROBIN = 1 };             /* ss_bc.thermal */
 enum { SS_XM = 0, SS_XP = 1, SS_YM = 2, SS_YP = 3, SS_ZM = 4, SS_ZP = 5 };  /* walls */
 
@@ -84,6 +85,8 @@ typedef struct {
   double tol_p;              /* relative 2-norm residual tolerance, pressure solve */
   double tol_t;              /* same for the transport solves (u, v, w, C, T) */
   int max_it_p, max_it_t;    /* iteration caps (>= 1) */
+  int precond_p;             /* pressure preconditioner: SS_PRECOND_MG (geometric multigrid
+                                V-cycle, default) or SS_PRECOND_JACOBI */
 } ss_grid;
 
 /* Alloy and model data (Table 1 style). C is the mass fraction of the

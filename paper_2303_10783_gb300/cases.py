@@ -22,6 +22,7 @@ A case is a plain ``dict``:
 ``tol_p, tol_t``        relative residual tolerances (2-norm) of the pressure
                         and transport solves
 ``max_it_p, max_it_t``  iteration caps of those solves
+``precond_p``           pressure preconditioner of the CUDA path: "mg" or "jacobi"
 ``steps``               number of time steps the workload runs
 
 The vertical axis is y in 2D and z in 3D; gravity points along minus that
@@ -62,14 +63,14 @@ def fe_c_alloy():
 
 
 def make_case(dim, nx, ny, nz, lx, ly, lz, dt, alloy=None, robin=None, T0=499.0, noise=1.0e-3, seed=0,
-              tol_p=1.0e-10, tol_t=1.0e-12, max_it_p=20000, max_it_t=2000, steps=100):
+              tol_p=1.0e-10, tol_t=1.0e-12, max_it_p=20000, max_it_t=2000, steps=100, precond_p="mg"):
     if dim == 2:
         nz, lz = 1, 1.0
     return dict(dim=dim, nx=nx, ny=ny, nz=nz, lx=lx, ly=ly, lz=lz, dt=dt,
                 alloy=dict(alloy if alloy is not None else sn_pb_alloy()),
                 robin=dict(robin if robin is not None else {"x-": (400.0, 298.0)}),
                 T0=T0, noise=noise, seed=seed, tol_p=tol_p, tol_t=tol_t,
-                max_it_p=max_it_p, max_it_t=max_it_t, steps=steps)
+                max_it_p=max_it_p, max_it_t=max_it_t, steps=steps, precond_p=precond_p)
 
 
 def cavity_2d(nx=50, ny=30, **kw):

@@ -56,6 +56,7 @@ __device__ __forceinline__ int cidx(const Params& pr, int i, int j, int k) { ret
 
 __device__ __forceinline__ void write_row(const Sys& s, int r, int dim, double P, const double nbB[3],
                                           const double nbF[3], double b) {
+  const double id = 1.0 / P;
   s.a.P[r] = P;
   s.a.W[r] = nbB[0];
   s.a.E[r] = nbF[0];
@@ -66,7 +67,19 @@ __device__ __forceinline__ void write_row(const Sys& s, int r, int dim, double P
     s.a.T_[r] = nbF[2];
   }
   s.b[r] = b;
-  s.a.idiag[r] = 1.0 / P;
+  s.a.idiag[r] = id;
+  if (s.af.P) {   // FP32 copies for the mixed-precision inner solve
+    s.af.P[r] = (float)P;
+    s.af.W[r] = (float)nbB[0];
+    s.af.E[r] = (float)nbF[0];
+    s.af.S[r] = (float)nbB[1];
+    s.af.N[r] = (float)nbF[1];
+    if (dim == 3) {
+      s.af.B[r] = (float)nbB[2];
+      s.af.T_[r] = (float)nbF[2];
+    }
+    s.af.idiag[r] = (float)id;
+  }
 }
 
 template <int A>
@@ -326,10 +339,6 @@ __global__ void __launch_bounds__(kBlock) k_equilibrate(Params pr, const double*
   }
 }
 
-__global__ void __launch_bounds__(kBlock) k_to_fp32(const double* __restrict__ src, float* dst, int n) {
-  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) dst[r] = (float)src[r];
-}
-
 }  // namespace
 
 cudaError_t launch_assemble_momentum(int comp, const Params& pr, const Sys& sys, const double* const vel[3],
@@ -383,17 +392,6 @@ cudaError_t launch_equilibrate(const Params& pr, const double* T, const double* 
                                double* Cs, double* Kinv, double* Ag, int from_T, int write_cl, cudaStream_t st) {
   const int n = pr.nx * pr.ny * pr.nz;
   k_equilibrate<<<grid_for(n), kBlock, 0, st>>>(pr, T, C, gl, Cl, Cs, Kinv, Ag, n, from_T, write_cl);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_fp32_planes(const Sys& sys, int dim, cudaStream_t st) {
-  const int n = (int)sys.d.n, g = grid_for(n);
-  const double* src[8] = {sys.a.P, sys.a.W, sys.a.E, sys.a.S, sys.a.N, sys.a.B, sys.a.T_, sys.a.idiag};
-  float* dst[8] = {sys.af.P, sys.af.W, sys.af.E, sys.af.S, sys.af.N, sys.af.B, sys.af.T_, sys.af.idiag};
-  for (int q = 0; q < 8; ++q) {
-    if ((q == 5 || q == 6) && dim != 3) continue;
-    k_to_fp32<<<g, kBlock, 0, st>>>(src[q], dst[q], n);
-  }
   return cudaGetLastError();
 }
 

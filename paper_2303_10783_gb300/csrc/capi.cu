@@ -79,6 +79,7 @@ struct ss_case {
   double *u, *v, *w, *p, *T, *C, *gl, *Cl, *Cs, *Kinv, *Ag;
   double *ustar[3], *pc, *pb;
   Sys sys[SS_NSYS];
+  MGPlan mg;
   Scratch sc;
   DevStatus* st;
   int alloy_set;
@@ -106,8 +107,14 @@ bool grid_ok(const ss_grid* g, char* why, size_t len) {
   if (g->precision != SS_FP64 && g->precision != SS_MIXED) { snprintf(why, len, "unknown precision %d", g->precision); return false; }
   if (!(g->tol_p > 0) || !(g->tol_t > 0)) { snprintf(why, len, "tolerances must be > 0"); return false; }
   if (g->max_it_p < 1 || g->max_it_t < 1) { snprintf(why, len, "iteration caps must be >= 1"); return false; }
+  if (g->precond_p != SS_PRECOND_MG && g->precond_p != SS_PRECOND_JACOBI) {
+    snprintf(why, len, "unknown pressure preconditioner %d", g->precond_p);
+    return false;
+  }
   return true;
 }
+
+void fill_params(ss_case* c, const ss_alloy* al);
 
 void plan(ss_case* c, Planner& pl) {
   const long long nx = c->g.nx, ny = c->g.ny, nz = c->g.dim == 3 ? c->g.nz : 1;
@@ -159,13 +166,29 @@ void plan(ss_case* c, Planner& pl) {
     }
   }
   c->sys[SS_SYS_P].b = c->pb;
+  if (c->g.precond_p == SS_PRECOND_MG) {
+    fill_params(c, nullptr);
+    plan_multigrid(c->pr, c->mg, c->g.precision == SS_MIXED);
+    for (int l = 0; l < c->mg.nl; ++l) {
+      const long long nl = (long long)c->mg.n[l][0] * c->mg.n[l][1] * c->mg.n[l][2];
+      for (int q = 0; q < 4; ++q)
+        c->mg.vec[l][q] = c->mg.fp32 ? (void*)pl.vec<float>(nl) : (void*)pl.vec<double>(nl);
+    }
+  }
   for (int q = 0; q < 8; ++q) c->sc.v[q] = pl.vec<double>(nmax);
   for (int q = 0; q < 8; ++q) c->sc.f[q] = (c->g.precision == SS_MIXED) ? pl.vec<float>(nmax) : nullptr;
   c->sc.max_blocks = max_cooperative_blocks();
   c->sc.partial = pl.raw<double>((size_t)kMaxRedSlots * c->sc.max_blocks * sizeof(double));
 }
 
-long long guard_of(const ss_grid* g) { return (long long)(g->nx + 1) * (g->ny + 1) + 64; }
+// Guard band (elements) in front of and behind every vector: at least one
+// x-y plane of any system so that the 7-point stencil reads in bounds, and a
+// multiple of 64 elements so that every vector starts on a 256-byte boundary
+// (element 0 of a warp's access then begins a cache line).
+long long guard_of(const ss_grid* g) {
+  const long long plane = (long long)(g->nx + 1) * (g->ny + 1) + 1;
+  return (plane + 63) / 64 * 64;
+}
 
 void fill_params(ss_case* c, const ss_alloy* al) {
   Params& pr = c->pr;
@@ -261,8 +284,7 @@ struct StageTimer {
 };
 
 ss_status stage_assemble(ss_case* c, int sys) {
-  StageTimer tm(c, SS_PROF_ASSEMBLE + (sys >= 0 && sys < SS_NSYS ? sys : 0),
-                1 + ((c->g.precision == SS_MIXED && sys != SS_SYS_P) ? (c->pr.dim == 3 ? 8 : 6) : 0));
+  StageTimer tm(c, SS_PROF_ASSEMBLE + (sys >= 0 && sys < SS_NSYS ? sys : 0), 1);
   const double* vel[3];
   vel_of(c, vel);
   cudaError_t e;
@@ -282,10 +304,6 @@ ss_status stage_assemble(ss_case* c, int sys) {
     default: return fail(SS_EINVAL, "unknown system %d", sys);
   }
   if (e != cudaSuccess) return fail(SS_ECUDA, "assembly of system %d: %s", sys, cudaGetErrorString(e));
-  if (c->g.precision == SS_MIXED && sys != SS_SYS_P) {
-    e = launch_fp32_planes(c->sys[sys], c->pr.dim, c->stream);
-    if (e != cudaSuccess) return fail(SS_ECUDA, "plane conversion: %s", cudaGetErrorString(e));
-  }
   return SS_OK;
 }
 
@@ -298,7 +316,10 @@ ss_status stage_solve(ss_case* c, int sys) {
   if (sys == SS_SYS_P) {
     ctl.tol = c->g.tol_p;
     ctl.max_it = c->g.max_it_p;
-    e = launch_pcg_poisson(c->pr, c->pb, c->pc, ctl, c->sc, c->st, c->stream);
+    if (c->g.precond_p == SS_PRECOND_MG)
+      e = launch_pcg_mg(c->mg, c->pr, c->pb, c->pc, ctl, c->sc, c->st, c->stream);
+    else
+      e = launch_pcg_poisson(c->pr, c->pb, c->pc, ctl, c->sc, c->st, c->stream);
   } else if (sys >= 0 && sys < SS_NSYS) {
     if (sys == SS_SYS_W && c->pr.dim != 3) return SS_OK;
     ctl.tol = c->g.tol_t;

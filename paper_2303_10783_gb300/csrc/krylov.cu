@@ -17,7 +17,9 @@
 //                   operator never changes, so it is never assembled).
 //
 // Vectors that other blocks write during the solve (the SpMV operands) are
-// read with ld.global.cg so a stale L1 line can never be used.
+// read with plain L1-cached loads: they are read only after a grid barrier,
+// whose acquire makes the other blocks' writes visible. The DIA planes do
+// not change during a solve and use the read-only path.
 #include <mutex>
 
 #include "solid_internal.cuh"
@@ -25,38 +27,45 @@
 namespace solid {
 namespace {
 
+template <typename T>
+struct BcgVec {
+  T *r, *rh, *p, *v, *y, *z, *t;
+};
+
 struct BcgArgs {
   Sys sys;
   int has_z;
   double tol;
   int max_it;
   int stat_index;
-  double *r, *rh, *p, *v, *y, *z, *t;
+  BcgVec<double> v64;
+  BcgVec<float> v32;
+  float* d32;              // inner correction (mixed path)
   double* partial;
   int max_blocks;
   DevStatus* st;
 };
 
-__device__ __forceinline__ double spmv_row(const Planes<double>& a, const double* x, int r, int sy, int sz,
-                                           int has_z) {
-  double acc = __ldg(a.P + r) * __ldcg(x + r);
-  acc = fma(__ldg(a.W + r), __ldcg(x + r - 1), acc);
-  acc = fma(__ldg(a.E + r), __ldcg(x + r + 1), acc);
-  acc = fma(__ldg(a.S + r), __ldcg(x + r - sy), acc);
-  acc = fma(__ldg(a.N + r), __ldcg(x + r + sy), acc);
+template <typename T>
+__device__ __forceinline__ T spmv_row(const Planes<T>& a, const T* x, int r, int sy, int sz, int has_z) {
+  T acc = __ldg(a.P + r) * x[r];
+  acc = fma(__ldg(a.W + r), x[r - 1], acc);
+  acc = fma(__ldg(a.E + r), x[r + 1], acc);
+  acc = fma(__ldg(a.S + r), x[r - sy], acc);
+  acc = fma(__ldg(a.N + r), x[r + sy], acc);
   if (has_z) {
-    acc = fma(__ldg(a.B + r), __ldcg(x + r - sz), acc);
-    acc = fma(__ldg(a.T_ + r), __ldcg(x + r + sz), acc);
+    acc = fma(__ldg(a.B + r), x[r - sz], acc);
+    acc = fma(__ldg(a.T_ + r), x[r + sz], acc);
   }
   return acc;
 }
 
-__device__ void record(DevStatus* st, int idx, int iters, bool converged, double relres) {
+__device__ void record(DevStatus* st, int idx, int iters, int refinements, bool converged, double relres) {
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     SolveStat& s = st->stat[idx];
     s.iters = iters;
     s.iters_total += iters;
-    s.refinements = 0;
+    s.refinements = refinements;
     s.converged = converged ? 1 : 0;
     s.nonfinite = isfinite(relres) ? 0 : 1;
     s.relres = relres;
@@ -65,104 +74,193 @@ __device__ void record(DevStatus* st, int idx, int iters, bool converged, double
   }
 }
 
-__global__ void __launch_bounds__(kBlock, 2) k_bicgstab(BcgArgs A) {
-  unsigned int epoch = 0;
-  const int n = (int)A.sys.d.n;
-  const int sy = A.sys.d.mx, sz = A.sys.d.mx * A.sys.d.my;
-  const int t0 = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
-  const Planes<double> a = A.sys.a;
-  double* x = A.sys.x;
-  const double* b = A.sys.b;
-  double *r = A.r, *rh = A.rh, *p = A.p, *v = A.v, *y = A.y, *z = A.z, *t = A.t;
+struct CoreOut {
+  int it;
+  bool conv;
+  double res, bnorm;
+};
 
-  // r = b - A x0, rhat = r
+// Jacobi-preconditioned BiCGSTAB on A x = b in precision T (vectors and
+// planes). zero_x0: start from x = 0 without the initial SpMV. Per-thread
+// dot-product partials accumulate in T (so the FP32 inner solve issues no
+// FP64 work); block and grid reductions are FP64 and deterministic.
+// Reduction slots 0..7. Returns false if a grid barrier gave up.
+template <typename T>
+__device__ bool bcg_core(const Planes<T>& a, int n, int sy, int sz, int has_z, const T* b, T* x, bool zero_x0,
+                         const BcgVec<T>& V, double tol, int max_it, double* partial, int max_blocks, DevStatus* st,
+                         unsigned int& epoch, CoreOut& out) {
+  const int t0 = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
+  T *r = V.r, *rh = V.rh, *p = V.p, *v = V.v, *y = V.y, *z = V.z, *t = V.t;
   Vec<2> acc = {{0.0, 0.0}};
-  for (int i = t0; i < n; i += gs) {
-    const double ri = b[i] - spmv_row(a, x, i, sy, sz, A.has_z);
-    r[i] = ri;
-    rh[i] = ri;
-    p[i] = 0.0;
-    v[i] = 0.0;
-    acc.v[0] += ri * ri;
-    acc.v[1] += b[i] * b[i];
+  {
+    T a0 = T(0), a1 = T(0);
+    for (int i = t0; i < n; i += gs) {          // r = b - A x0, rhat = r
+      const T bi = b[i];
+      const T ri = zero_x0 ? bi : bi - spmv_row(a, x, i, sy, sz, has_z);
+      if (zero_x0) x[i] = T(0);
+      r[i] = ri;
+      rh[i] = ri;
+      p[i] = T(0);
+      v[i] = T(0);
+      a0 += ri * ri;
+      a1 += bi * bi;
+    }
+    acc.v[0] = (double)a0;
+    acc.v[1] = (double)a1;
   }
   Vec<2> tot;
-  if (!grid_sum<2>(acc, A.partial, A.max_blocks, 6, A.st, epoch, tot)) return;
-  const double bnorm = sqrt(tot.v[1]);
+  if (!grid_sum<2>(acc, partial, max_blocks, 6, st, epoch, tot)) return false;
+  out.bnorm = sqrt(tot.v[1]);
   double res = sqrt(tot.v[0]);
-  if (bnorm == 0.0) {   // b = 0: the solution is 0
-    for (int i = t0; i < n; i += gs) x[i] = 0.0;
-    record(A.st, A.stat_index, 0, true, 0.0);
-    return;
+  out.it = 0;
+  if (out.bnorm == 0.0) {
+    if (!zero_x0)
+      for (int i = t0; i < n; i += gs) x[i] = T(0);
+    out.conv = true;
+    out.res = 0.0;
+    return true;
   }
-  const double thr = A.tol * bnorm;
+  const double thr = tol * out.bnorm;
   double rho = tot.v[0], rho_old = 1.0, alpha = 1.0, omega = 1.0;
   int it = 0;
   bool conv = res <= thr;
-  while (!conv && it < A.max_it && isfinite(res)) {
+  while (!conv && it < max_it && isfinite(res)) {
     ++it;
-    const double beta = (rho / rho_old) * (alpha / omega);
+    const T beta = (T)((rho / rho_old) * (alpha / omega));
+    const T om = (T)omega;
     for (int i = t0; i < n; i += gs) {            // p = r + beta (p - omega v); y = M^-1 p
-      const double pi = r[i] + beta * (p[i] - omega * v[i]);
+      const T pi = r[i] + beta * (p[i] - om * v[i]);
       p[i] = pi;
       y[i] = __ldg(a.idiag + i) * pi;
     }
-    if (!grid_barrier(A.st, gridDim.x, epoch)) return;
-    Vec<1> d1 = {{0.0}};
+    if (!grid_barrier(st, gridDim.x, epoch)) return false;
+    T s1 = T(0);
     for (int i = t0; i < n; i += gs) {            // v = A y
-      const double vi = spmv_row(a, y, i, sy, sz, A.has_z);
+      const T vi = spmv_row(a, y, i, sy, sz, has_z);
       v[i] = vi;
-      d1.v[0] += rh[i] * vi;
+      s1 += rh[i] * vi;
     }
-    Vec<1> o1;
-    if (!grid_sum<1>(d1, A.partial, A.max_blocks, 0, A.st, epoch, o1)) return;
+    Vec<1> o1, d1 = {{(double)s1}};
+    if (!grid_sum<1>(d1, partial, max_blocks, 0, st, epoch, o1)) return false;
     alpha = rho / o1.v[0];
-    Vec<1> d2 = {{0.0}};
+    const T al = (T)alpha;
+    T s2 = T(0);
     for (int i = t0; i < n; i += gs) {            // s = r - alpha v (in r); z = M^-1 s
-      const double si = r[i] - alpha * v[i];
+      const T si = r[i] - al * v[i];
       r[i] = si;
       z[i] = __ldg(a.idiag + i) * si;
-      d2.v[0] += si * si;
+      s2 += si * si;
     }
-    Vec<1> o2;
-    if (!grid_sum<1>(d2, A.partial, A.max_blocks, 1, A.st, epoch, o2)) return;
+    Vec<1> o2, d2 = {{(double)s2}};
+    if (!grid_sum<1>(d2, partial, max_blocks, 1, st, epoch, o2)) return false;
     if (sqrt(o2.v[0]) <= thr) {                  // early exit on the half step
-      for (int i = t0; i < n; i += gs) x[i] += alpha * y[i];
+      for (int i = t0; i < n; i += gs) x[i] += al * y[i];
       res = sqrt(o2.v[0]);
       conv = true;
       break;
     }
-    Vec<2> d3 = {{0.0, 0.0}};
+    T s3 = T(0), s4 = T(0);
     for (int i = t0; i < n; i += gs) {            // t = A z
-      const double ti = spmv_row(a, z, i, sy, sz, A.has_z);
+      const T ti = spmv_row(a, z, i, sy, sz, has_z);
       t[i] = ti;
-      d3.v[0] += ti * r[i];
-      d3.v[1] += ti * ti;
+      s3 += ti * r[i];
+      s4 += ti * ti;
     }
-    Vec<2> o3;
-    if (!grid_sum<2>(d3, A.partial, A.max_blocks, 2, A.st, epoch, o3)) return;
+    Vec<2> o3, d3 = {{(double)s3, (double)s4}};
+    if (!grid_sum<2>(d3, partial, max_blocks, 2, st, epoch, o3)) return false;
     omega = (o3.v[1] > 0.0) ? o3.v[0] / o3.v[1] : 0.0;
-    Vec<2> d4 = {{0.0, 0.0}};
+    const T omn = (T)omega;
+    T s5 = T(0), s6 = T(0);
     for (int i = t0; i < n; i += gs) {            // x += alpha y + omega z; r = s - omega t
-      x[i] += alpha * y[i] + omega * z[i];
-      const double ri = r[i] - omega * t[i];
+      x[i] += al * y[i] + omn * z[i];
+      const T ri = r[i] - omn * t[i];
       r[i] = ri;
-      d4.v[0] += rh[i] * ri;
-      d4.v[1] += ri * ri;
+      s5 += rh[i] * ri;
+      s6 += ri * ri;
     }
-    Vec<2> o4;
-    if (!grid_sum<2>(d4, A.partial, A.max_blocks, 4, A.st, epoch, o4)) return;
+    Vec<2> o4, d4 = {{(double)s5, (double)s6}};
+    if (!grid_sum<2>(d4, partial, max_blocks, 4, st, epoch, o4)) return false;
     res = sqrt(o4.v[1]);
     conv = res <= thr;
     rho_old = rho;
     rho = o4.v[0];
     if (rho == 0.0 || omega == 0.0) break;   // breakdown: report the current iterate
   }
-  record(A.st, A.stat_index, it, conv, res / bnorm);
+  out.it = it;
+  out.conv = conv;
+  out.res = res;
+  return true;
+}
+
+__global__ void __launch_bounds__(kBlock, 4) k_bicgstab(BcgArgs A) {
+  unsigned int epoch = 0;
+  const int n = (int)A.sys.d.n;
+  const int sy = A.sys.d.mx, sz = A.sys.d.mx * A.sys.d.my;
+  CoreOut o;
+  if (!bcg_core<double>(A.sys.a, n, sy, sz, A.has_z, A.sys.b, A.sys.x, false, A.v64, A.tol, A.max_it, A.partial,
+                        A.max_blocks, A.st, epoch, o))
+    return;
+  record(A.st, A.stat_index, o.it, 0, o.conv, o.bnorm > 0.0 ? o.res / o.bnorm : 0.0);
+}
+
+// Mixed precision: FP64 iterative refinement around an FP32 BiCGSTAB on the
+// FP32 copies of the planes. Each sweep forms the FP64 residual
+// r = b - A x with the FP64 planes, solves A d = r in FP32 to a relative
+// 1e-5, and adds d to the FP64 iterate; it stops when the FP64 residual
+// meets tol (the same test as the FP64 path).
+constexpr double kInnerTol = 1.0e-5;
+constexpr int kMaxRefine = 12;
+
+__global__ void __launch_bounds__(kBlock, 4) k_bicgstab_ir(BcgArgs A) {
+  unsigned int epoch = 0;
+  const int n = (int)A.sys.d.n;
+  const int sy = A.sys.d.mx, sz = A.sys.d.mx * A.sys.d.my;
+  const int t0 = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
+  double* x = A.sys.x;
+  const double* b = A.sys.b;
+  double* r64 = A.v64.r;
+  Vec<2> acc = {{0.0, 0.0}};
+  for (int i = t0; i < n; i += gs) {
+    const double ri = b[i] - spmv_row(A.sys.a, x, i, sy, sz, A.has_z);
+    r64[i] = ri;
+    acc.v[0] += ri * ri;
+    acc.v[1] += b[i] * b[i];
+  }
+  Vec<2> tot;
+  if (!grid_sum<2>(acc, A.partial, A.max_blocks, 13, A.st, epoch, tot)) return;
+  const double bnorm = sqrt(tot.v[1]);
+  double rn = sqrt(tot.v[0]);
+  const double thr = A.tol * bnorm;
+  int total = 0, ref = 0;
+  while (bnorm > 0.0 && rn > thr && ref < kMaxRefine && total < A.max_it && isfinite(rn)) {
+    ++ref;
+    // the inner solve sees the residual scaled to unit norm (no FP32 under- or overflow)
+    const double inv = 1.0 / rn;
+    for (int i = t0; i < n; i += gs) A.v32.r[i] = (float)(r64[i] * inv);
+    CoreOut o;
+    if (!bcg_core<float>(A.sys.af, n, sy, sz, A.has_z, A.v32.r, A.d32, true, A.v32, kInnerTol, A.max_it - total,
+                         A.partial, A.max_blocks, A.st, epoch, o))
+      return;
+    total += o.it;
+    for (int i = t0; i < n; i += gs) x[i] += rn * (double)A.d32[i];
+    if (!grid_barrier(A.st, gridDim.x, epoch)) return;
+    Vec<1> s1 = {{0.0}};
+    for (int i = t0; i < n; i += gs) {
+      const double ri = b[i] - spmv_row(A.sys.a, x, i, sy, sz, A.has_z);
+      r64[i] = ri;
+      s1.v[0] += ri * ri;
+    }
+    Vec<1> o1;
+    if (!grid_sum<1>(s1, A.partial, A.max_blocks, 15, A.st, epoch, o1)) return;
+    rn = sqrt(o1.v[0]);
+    if (o.it == 0 && !(rn <= thr)) break;      // the inner solve made no progress
+  }
+  record(A.st, A.stat_index, total, ref, bnorm == 0.0 || rn <= thr, bnorm > 0.0 ? rn / bnorm : 0.0);
 }
 
 struct PcgArgs {
   int nx, ny, nz, dim;
+  FastDiv fx, fy;
   double cx, cy, cz;      // 1/h^2 per axis
   double* b;
   double* x;
@@ -198,7 +296,7 @@ __device__ __forceinline__ int nb_code(const PcgArgs& A, int i, int j, int k) {
   return cx + 3 * cy + 9 * cz;
 }
 
-__global__ void __launch_bounds__(kBlock, 2) k_pcg_poisson(PcgArgs A) {
+__global__ void __launch_bounds__(kBlock, 4) k_pcg_poisson(PcgArgs A) {
   __shared__ double s_diag[27], s_minv[27];
   if (threadIdx.x < 27) {
     const int c = threadIdx.x;
@@ -220,7 +318,8 @@ __global__ void __launch_bounds__(kBlock, 2) k_pcg_poisson(PcgArgs A) {
   const double mean_b = ob.v[0] / (double)n;
   Vec<2> acc = {{0.0, 0.0}};
   for (int i = t0; i < n; i += gs) {
-    const int ii = i % A.nx, tt = i / A.nx, jj = tt % A.ny, kk = tt / A.ny;
+    int ii, jj, kk;
+      decompose3(i, A.fx, A.fy, ii, jj, kk);
     const double bi = b[i] - mean_b;
     b[i] = bi;
     x[i] = 0.0;
@@ -241,7 +340,8 @@ __global__ void __launch_bounds__(kBlock, 2) k_pcg_poisson(PcgArgs A) {
     ++it;
     Vec<1> d1 = {{0.0}};
     for (int i = t0; i < n; i += gs) {            // q = A p
-      const int ii = i % A.nx, tt = i / A.nx, jj = tt % A.ny, kk = tt / A.ny;
+      int ii, jj, kk;
+      decompose3(i, A.fx, A.fy, ii, jj, kk);
       const double qi = lap_row(A, p, i, ii, jj, kk, s_diag[nb_code(A, ii, jj, kk)]);
       q[i] = qi;
       d1.v[0] += p[i] * qi;
@@ -251,7 +351,8 @@ __global__ void __launch_bounds__(kBlock, 2) k_pcg_poisson(PcgArgs A) {
     const double alpha = rz / o1.v[0];
     Vec<2> d2 = {{0.0, 0.0}};
     for (int i = t0; i < n; i += gs) {            // x += alpha p; r -= alpha q; z = M^-1 r
-      const int ii = i % A.nx, tt = i / A.nx, jj = tt % A.ny, kk = tt / A.ny;
+      int ii, jj, kk;
+      decompose3(i, A.fx, A.fy, ii, jj, kk);
       x[i] += alpha * p[i];
       const double ri = r[i] - alpha * q[i];
       r[i] = ri;
@@ -267,7 +368,8 @@ __global__ void __launch_bounds__(kBlock, 2) k_pcg_poisson(PcgArgs A) {
     const double beta = o2.v[0] / rz;
     rz = o2.v[0];
     for (int i = t0; i < n; i += gs) {            // p = z + beta p
-      const int ii = i % A.nx, tt = i / A.nx, jj = tt % A.ny, kk = tt / A.ny;
+      int ii, jj, kk;
+      decompose3(i, A.fx, A.fy, ii, jj, kk);
       p[i] = s_minv[nb_code(A, ii, jj, kk)] * r[i] + beta * p[i];
     }
     if (!grid_barrier(A.st, gridDim.x, epoch)) return;
@@ -279,26 +381,26 @@ __global__ void __launch_bounds__(kBlock, 2) k_pcg_poisson(PcgArgs A) {
   if (!grid_sum<1>(sx, A.partial, A.max_blocks, 12, A.st, epoch, ox)) return;
   const double mean_x = ox.v[0] / (double)n;
   for (int i = t0; i < n; i += gs) x[i] -= mean_x;
-  record(A.st, A.stat_index, it, conv, bnorm > 0.0 ? res / bnorm : 0.0);
+  record(A.st, A.stat_index, it, 0, conv, bnorm > 0.0 ? res / bnorm : 0.0);
 }
 
 int g_num_sms = 0;
 
-int coop_limit(const void* kernel) {
+int coop_limit(const void* kernel, size_t smem = 0) {
   if (g_num_sms == 0) {
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
   }
   int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kBlock, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kBlock, smem);
   if (per_sm > 4) per_sm = 4;
   return per_sm * g_num_sms;
 }
 
-int blocks_for(const void* kernel, long long rows, int max_blocks) {
+int blocks_for(const void* kernel, long long rows, int max_blocks, size_t smem = 0) {
   long long want = (rows + kBlock - 1) / kBlock;
-  int lim = coop_limit(kernel);
+  int lim = coop_limit(kernel, smem);
   if (lim > max_blocks) lim = max_blocks;
   if (want > lim) want = lim;
   if (want < 1) want = 1;
@@ -309,10 +411,16 @@ int blocks_for(const void* kernel, long long rows, int max_blocks) {
 
 int cooperative_blocks(const void* kernel, long long rows) { return blocks_for(kernel, rows, 1 << 30); }
 
+int coop_blocks_for(const void* kernel, long long rows, int max_blocks) { return blocks_for(kernel, rows, max_blocks); }
+
+int coop_blocks_for_smem(const void* kernel, long long rows, int max_blocks, size_t smem) {
+  return blocks_for(kernel, rows, max_blocks, smem);
+}
+
+// Upper bound on the blocks of any cooperative launch (sizes the reduction partials).
 int max_cooperative_blocks() {
-  int a = coop_limit((const void*)k_bicgstab);
-  int b = coop_limit((const void*)k_pcg_poisson);
-  return a > b ? a : b;
+  if (g_num_sms == 0) coop_limit((const void*)k_bicgstab);
+  return 4 * (g_num_sms > 0 ? g_num_sms : 1);
 }
 
 cudaError_t launch_bicgstab(const Sys& sys, int has_z, const SolverCtl& ctl, Scratch& sc, DevStatus* st,
@@ -323,21 +431,27 @@ cudaError_t launch_bicgstab(const Sys& sys, int has_z, const SolverCtl& ctl, Scr
   A.tol = ctl.tol;
   A.max_it = ctl.max_it;
   A.stat_index = ctl.stat_index;
-  A.r = sc.v[0]; A.rh = sc.v[1]; A.p = sc.v[2]; A.v = sc.v[3]; A.y = sc.v[4]; A.z = sc.v[5]; A.t = sc.v[6];
+  A.v64 = {sc.v[0], sc.v[1], sc.v[2], sc.v[3], sc.v[4], sc.v[5], sc.v[6]};
+  A.v32 = {sc.f[0], sc.f[1], sc.f[2], sc.f[3], sc.f[4], sc.f[5], sc.f[6]};
+  A.d32 = sc.f[7];
   A.partial = sc.partial;
   A.max_blocks = sc.max_blocks;
   A.st = st;
-  const int nb = blocks_for((const void*)k_bicgstab, sys.d.n, sc.max_blocks);
+  const bool mixed = ctl.mixed && sys.af.P != nullptr && sc.f[0] != nullptr;
+  const void* kern = mixed ? (const void*)k_bicgstab_ir : (const void*)k_bicgstab;
+  const int nb = blocks_for(kern, sys.d.n, sc.max_blocks);
   cudaError_t e = cudaMemsetAsync(&st->barrier, 0, sizeof(unsigned int), s);
   if (e != cudaSuccess) return e;
   void* args[] = {&A};
-  return cudaLaunchCooperativeKernel((const void*)k_bicgstab, dim3(nb), dim3(kBlock), args, 0, s);
+  return cudaLaunchCooperativeKernel(kern, dim3(nb), dim3(kBlock), args, 0, s);
 }
 
 cudaError_t launch_pcg_poisson(const Params& pr, double* b, double* x, const SolverCtl& ctl, Scratch& sc,
                                DevStatus* st, cudaStream_t s) {
   PcgArgs A;
   A.nx = pr.nx; A.ny = pr.ny; A.nz = pr.nz; A.dim = pr.dim;
+  A.fx = make_fastdiv(pr.nx);
+  A.fy = make_fastdiv(pr.ny);
   A.cx = 1.0 / (pr.hx * pr.hx);
   A.cy = 1.0 / (pr.hy * pr.hy);
   A.cz = (pr.dim == 3) ? 1.0 / (pr.hz * pr.hz) : 0.0;
@@ -438,6 +552,8 @@ extern "C" ss_status ss_poisson_solve_noalloc(int dim, int nx, int ny, int nz, d
   double* vec = reinterpret_cast<double*>(base + kNoAllocStatusBytes + kNoAllocPartialBytes);
   PcgArgs A;
   A.nx = nx; A.ny = ny; A.nz = nz; A.dim = dim;
+  A.fx = make_fastdiv(nx);
+  A.fy = make_fastdiv(ny);
   A.cx = 1.0 / (hx * hx);
   A.cy = 1.0 / (hy * hy);
   A.cz = (dim == 3) ? 1.0 / (hz * hz) : 0.0;

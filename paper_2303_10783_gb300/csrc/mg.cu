@@ -1,0 +1,753 @@
+// Geometric-multigrid-preconditioned CG for the pressure correction (Eq. 3.4).
+//
+// One cooperative launch runs the whole solve.
+//   FP64 path   CG in FP64 preconditioned by an FP64 V-cycle.
+//   mixed path  FP64 iterative refinement: each sweep forms the FP64 residual
+//               r = b - A x, solves A d = r to a relative 1e-5 with CG in FP32
+//               preconditioned by an FP32 V-cycle, and adds d to the FP64 x.
+//               Every inner iteration is FP32; the FP64 work is one residual
+//               per sweep, so the solve leaves GB300's narrow FP64 pipe.
+// Both stop on the same test: the FP64 residual below tol * |b|.
+//
+// Hierarchy: cell-centred, each level halves every axis whose cell count is
+// even and >= 4 (semi-coarsening when only some axes qualify). Each level
+// rediscretises the Neumann Laplacian A = -L with its own spacings (the
+// operator is constant, Sec. 4 term-wise strategy: nothing is assembled).
+//   smoother      weighted Jacobi (omega = 0.9), 2 sweeps before and 2 after
+//   prolongation  trilinear in cell centres (per axis 3/4 parent, 1/4 the
+//                 neighbour on the child's side; a wall mirrors the parent)
+//   restriction   R = P^T / 2^(coarsened axes) (per axis weights 1/8 3/8 3/8 1/8)
+//   coarsest      nu_c weighted-Jacobi sweeps from zero
+// Jacobi smoothing is self-adjoint in the A inner product and R is a scaled
+// P^T, so the V-cycle is a fixed symmetric positive-definite operator and
+// plain CG applies. The small levels are run by block 0 alone, resident in
+// its shared memory; the others grid-wide between grid barriers.
+//
+// Loads are plain (L1-cached): every phase that reads data another block
+// wrote follows a grid barrier whose acquire makes those writes visible.
+#include <cstring>
+
+#include "solid_internal.cuh"
+
+namespace solid {
+namespace {
+
+constexpr double kOmega = 0.9;
+constexpr double kInnerTolP = 1.0e-5;
+constexpr int kMaxRefineP = 12;
+
+template <typename TP>
+struct Level {
+  int nx, ny, nz, n;
+  FastDiv fx, fy;          // division by nx and ny
+  int cx, cy, cz;          // 1 if the next level halves this axis
+  TP ax, ay, az;           // 1/h^2 per axis
+  TP *b, *x, *t, *r;       // rhs, iterate, alternate iterate, residual
+  int local;               // run by block 0 alone (from shared memory)
+  int soff;                // offset (elements) of the level's four arrays in shared memory
+};
+
+template <typename TP>
+struct MGArgs {
+  int nl;                  // number of levels
+  int nu_c;                // sweeps on the coarsest level (even)
+  int G;                   // first local level (nl if none)
+  int mixed;               // iterative refinement around an inner solve of type TP
+  Level<TP> lev[kMaxLevels];
+  double cx, cy, cz;       // FP64 1/h^2 of the fine grid
+  double* b;               // right-hand side (mean removed in place)
+  double *x, *r, *p, *q;   // FP64 vectors (solution, residual, CG vectors of the FP64 path)
+  TP *ri, *pi, *qi, *di;   // inner CG vectors (mixed path)
+  double tol;
+  int max_it;
+  int stat_index;
+  double* partial;
+  int max_blocks;
+  DevStatus* st;
+};
+
+struct Range {
+  int begin, stride;
+};
+
+template <typename TP>
+__device__ __forceinline__ int code_of(const Level<TP>& L, int i, int j, int k) {
+  return ((i > 0) + (i < L.nx - 1)) + 3 * ((j > 0) + (j < L.ny - 1)) + 9 * ((k > 0) + (k < L.nz - 1));
+}
+
+// (A v)_c for a Neumann Laplacian with per-axis coefficients a*
+template <typename T>
+__device__ __forceinline__ T lap(const T* v, int c, int i, int j, int k, int nx, int ny, int nz, T ax, T ay, T az,
+                                 T diag) {
+  const int sy = nx, sz = nx * ny;
+  T acc = diag * v[c];
+  acc = fma(-ax, (i > 0 ? v[c - 1] : T(0)) + (i < nx - 1 ? v[c + 1] : T(0)), acc);
+  acc = fma(-ay, (j > 0 ? v[c - sy] : T(0)) + (j < ny - 1 ? v[c + sy] : T(0)), acc);
+  if (nz > 1) acc = fma(-az, (k > 0 ? v[c - sz] : T(0)) + (k < nz - 1 ? v[c + sz] : T(0)), acc);
+  return acc;
+}
+
+template <typename TP>
+struct Tables {
+  TP diag[kMaxLevels][27];
+  TP wid[kMaxLevels][27];   // omega / diag (0 for an isolated cell)
+  double diag64[27];        // fine-grid FP64 diagonal
+};
+
+// Rows per thread per batch: a phase issues the loads of U rows before any
+// dependent arithmetic. U > 1 buys memory-level parallelism with registers;
+// in this kernel the extra registers spill, so U = 1.
+template <typename T>
+struct Batch {
+  static constexpr int U = 1;
+};
+
+// the 7-point neighbour sums of v at cell c, per axis
+template <typename T>
+struct Nb {
+  T c0, sx, sy, sz;
+};
+
+template <typename T>
+__device__ __forceinline__ Nb<T> load_nb(const T* v, int c, int i, int j, int k, int nx, int ny, int nz) {
+  const int sy = nx, sz = nx * ny;
+  Nb<T> o;
+  o.c0 = v[c];
+  const T w = i > 0 ? v[c - 1] : T(0), e = i < nx - 1 ? v[c + 1] : T(0);
+  const T s_ = j > 0 ? v[c - sy] : T(0), n_ = j < ny - 1 ? v[c + sy] : T(0);
+  T b_ = T(0), t_ = T(0);
+  if (nz > 1) {
+    b_ = k > 0 ? v[c - sz] : T(0);
+    t_ = k < nz - 1 ? v[c + sz] : T(0);
+  }
+  o.sx = w + e;
+  o.sy = s_ + n_;
+  o.sz = b_ + t_;
+  return o;
+}
+
+template <typename T>
+__device__ __forceinline__ T apply_nb(const Nb<T>& q, T ax, T ay, T az, T diag) {
+  T acc = diag * q.c0;
+  acc = fma(-ax, q.sx, acc);
+  acc = fma(-ay, q.sy, acc);
+  acc = fma(-az, q.sz, acc);
+  return acc;
+}
+
+// out = in + omega D^-1 (b - A in)      (residual_only: L.r = b - A in)
+template <typename TP, bool RESIDUAL>
+__device__ void sweep(const Level<TP>& L, const Tables<TP>& tb, int l, const TP* in, TP* out, Range rg) {
+  constexpr int U = Batch<TP>::U;
+  for (int base = rg.begin; base < L.n; base += U * rg.stride) {
+    Nb<TP> q[U];
+    TP bb[U];
+    int code[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int c = base + u * rg.stride;
+      if (c < L.n) {
+        int i, j, k;
+        decompose3(c, L.fx, L.fy, i, j, k);
+        code[u] = code_of(L, i, j, k);
+        q[u] = load_nb(in, c, i, j, k, L.nx, L.ny, L.nz);
+        bb[u] = L.b[c];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int c = base + u * rg.stride;
+      if (c < L.n) {
+        const TP res = bb[u] - apply_nb(q[u], L.ax, L.ay, L.az, tb.diag[l][code[u]]);
+        if (RESIDUAL) L.r[c] = res;
+        else out[c] = q[u].c0 + tb.wid[l][code[u]] * res;
+      }
+    }
+  }
+}
+
+template <typename TP>
+__device__ __forceinline__ void smooth(const Level<TP>& L, const Tables<TP>& tb, int l, const TP* in, TP* out,
+                                       Range rg) {
+  sweep<TP, false>(L, tb, l, in, out, rg);
+}
+
+template <typename TP>
+__device__ __forceinline__ void residual(const Level<TP>& L, const Tables<TP>& tb, int l, const TP* in, Range rg) {
+  sweep<TP, true>(L, tb, l, in, nullptr, rg);
+}
+
+__device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+// b_{l+1} = R r_l, and the first (pointwise) smoothing sweep of level l+1 from zero.
+// Per coarsened axis the fine cells 2I-1 .. 2I+2 carry weights 1/8 3/8 3/8 1/8;
+// clamping the out-of-range ones onto the wall cell reproduces R = P^T/2 there
+// (1/2 on the wall cell). An axis that is not coarsened reads its one cell four
+// times with weight 1/4.
+template <typename TP>
+__device__ void restrict_to(const Level<TP>& F, const Level<TP>& Cl, const Tables<TP>& tb, int lc, Range rg) {
+  const TP wc[4] = {TP(0.125), TP(0.375), TP(0.375), TP(0.125)};
+  const TP wn = TP(0.25);
+  for (int c = rg.begin; c < Cl.n; c += rg.stride) {
+    int I, J, K;
+    decompose3(c, Cl.fx, Cl.fy, I, J, K);
+    int fi[4], fj[4], fk[4];
+#pragma unroll
+    for (int o = 0; o < 4; ++o) {
+      fi[o] = F.cx ? clampi(2 * I - 1 + o, 0, F.nx - 1) : I;
+      fj[o] = F.cy ? clampi(2 * J - 1 + o, 0, F.ny - 1) : J;
+      fk[o] = F.cz ? clampi(2 * K - 1 + o, 0, F.nz - 1) : K;
+    }
+    TP acc = TP(0);
+#pragma unroll
+    for (int oz = 0; oz < 4; ++oz) {
+      const TP wz = F.cz ? wc[oz] : wn;
+      TP sy = TP(0);
+#pragma unroll
+      for (int oy = 0; oy < 4; ++oy) {
+        const TP wy = F.cy ? wc[oy] : wn;
+        const TP* row = F.r + (size_t)(fj[oy] + F.ny * fk[oz]) * F.nx;
+        TP sx = TP(0);
+#pragma unroll
+        for (int ox = 0; ox < 4; ++ox) sx += (F.cx ? wc[ox] : wn) * row[fi[ox]];
+        sy += wy * sx;
+      }
+      acc += wz * sy;
+    }
+    Cl.b[c] = acc;
+    Cl.x[c] = tb.wid[lc][code_of(Cl, I, J, K)] * acc;
+  }
+}
+
+// out_l += P e_{l+1}. Per axis the parent carries 3/4 and the coarse
+// neighbour on the child's side 1/4; clamping a neighbour beyond the wall
+// onto the parent gives the parent weight 1 there. An axis that is not
+// coarsened reads its one cell twice (3/4 + 1/4).
+template <typename TP>
+__device__ void prolong_add(const Level<TP>& F, const Level<TP>& Cl, const TP* e, TP* out, Range rg) {
+  constexpr int U = Batch<TP>::U;
+  const TP w0 = TP(0.75), w1 = TP(0.25);
+  for (int base = rg.begin; base < F.n; base += U * rg.stride) {
+    TP v[U][8], cur[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int c = base + u * rg.stride;
+      if (c < F.n) {
+        int i, j, k;
+        decompose3(c, F.fx, F.fy, i, j, k);
+        const int I0 = F.cx ? i >> 1 : i, J0 = F.cy ? j >> 1 : j, K0 = F.cz ? k >> 1 : k;
+        const int I1 = F.cx ? clampi((i & 1) ? I0 + 1 : I0 - 1, 0, Cl.nx - 1) : i;
+        const int J1 = F.cy ? clampi((j & 1) ? J0 + 1 : J0 - 1, 0, Cl.ny - 1) : j;
+        const int K1 = F.cz ? clampi((k & 1) ? K0 + 1 : K0 - 1, 0, Cl.nz - 1) : k;
+        const TP* r00 = e + (size_t)(J0 + Cl.ny * K0) * Cl.nx;
+        const TP* r01 = e + (size_t)(J1 + Cl.ny * K0) * Cl.nx;
+        const TP* r10 = e + (size_t)(J0 + Cl.ny * K1) * Cl.nx;
+        const TP* r11 = e + (size_t)(J1 + Cl.ny * K1) * Cl.nx;
+        v[u][0] = r00[I0]; v[u][1] = r00[I1];
+        v[u][2] = r01[I0]; v[u][3] = r01[I1];
+        v[u][4] = r10[I0]; v[u][5] = r10[I1];
+        v[u][6] = r11[I0]; v[u][7] = r11[I1];
+        cur[u] = out[c];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int c = base + u * rg.stride;
+      if (c < F.n) {
+        const TP y0 = w0 * (w0 * v[u][0] + w1 * v[u][1]) + w1 * (w0 * v[u][2] + w1 * v[u][3]);
+        const TP y1 = w0 * (w0 * v[u][4] + w1 * v[u][5]) + w1 * (w0 * v[u][6] + w1 * v[u][7]);
+        out[c] = cur[u] + (w0 * y0 + w1 * y1);
+      }
+    }
+  }
+}
+
+struct GridSync {
+  DevStatus* st;
+  unsigned int* epoch;
+  __device__ bool operator()() const { return grid_barrier(st, gridDim.x, *epoch); }
+};
+
+struct BlockSync {
+  __device__ bool operator()() const {
+    __syncthreads();
+    return true;
+  }
+};
+
+// Coarsest level: nu_c weighted-Jacobi sweeps in total, the first already
+// done (pointwise) by the restriction into x; nu_c is even, so the result
+// ends in t.
+template <typename TP, typename SyncF>
+__device__ bool coarsest(const Level<TP>* lev, int l, int nu_c, const Tables<TP>& tb, Range rg, SyncF sync) {
+  const Level<TP>& L = lev[l];
+  TP* a = L.x;
+  TP* b = L.t;
+  for (int s = 1; s < nu_c; ++s) {
+    if (!sync()) return false;
+    smooth(L, tb, l, a, b, rg);
+    TP* tmp = a;
+    a = b;
+    b = tmp;
+  }
+  return true;
+}
+
+// Pre-smoothing, residual and restriction on levels [lo, hi): level lo's x
+// holds the first sweep on entry.
+template <typename TP, typename SyncF>
+__device__ bool down(const Level<TP>* lev, const Tables<TP>& tb, int lo, int hi, Range rg, SyncF sync) {
+  for (int l = lo; l < hi; ++l) {
+    const Level<TP>& L = lev[l];
+    if (!sync()) return false;
+    smooth(L, tb, l, L.x, L.t, rg);           // second pre-smoothing sweep -> t
+    if (!sync()) return false;
+    residual(L, tb, l, L.t, rg);
+    if (!sync()) return false;
+    restrict_to(L, lev[l + 1], tb, l + 1, rg);
+  }
+  return true;
+}
+
+// Prolongation, correction and post-smoothing on levels hi down to lo. The
+// caller guarantees that level hi + 1's result is complete on entry.
+template <typename TP, typename SyncF>
+__device__ bool up(const Level<TP>* lev, const Tables<TP>& tb, int hi, int lo, Range rg, SyncF sync) {
+  for (int l = hi; l >= lo; --l) {
+    const Level<TP>& L = lev[l];
+    if (l != hi && !sync()) return false;
+    prolong_add(L, lev[l + 1], lev[l + 1].t, L.t, rg);
+    if (!sync()) return false;
+    smooth(L, tb, l, L.t, L.x, rg);           // post-smoothing sweep 1 -> x
+    if (!sync()) return false;
+    smooth(L, tb, l, L.x, L.t, rg);           // post-smoothing sweep 2 -> t
+  }
+  return true;
+}
+
+// Scalars the device functions need, passed by value (taking the address of
+// the kernel's parameter block would copy all of it to local memory).
+struct Ctx {
+  int nl, nu_c, G;
+  DevStatus* st;
+  double* partial;
+  int max_blocks;
+};
+
+// One V-cycle. On entry level 0 holds b and the first sweep x = omega D^-1 b
+// (written by the caller on each thread's own rows). On exit the result is in
+// lev[0].t; each thread may read its own rows of it (a later reader of other
+// rows needs a barrier). Levels from G on are run by block 0 in its shared
+// memory (slev) while the other blocks wait at one barrier. glev and slev are
+// level tables in shared memory (global and shared-memory arrays).
+template <typename TP>
+__device__ __noinline__ bool vcycle(const Ctx& X, const Level<TP>* glev, const Level<TP>* slev, const Tables<TP>& tb,
+                       unsigned int& epoch) {
+  const int nl = X.nl, G = X.G;
+  const Range grid_rg{(int)(blockIdx.x * blockDim.x + threadIdx.x), (int)(gridDim.x * blockDim.x)};
+  const Range blk_rg{(int)threadIdx.x, (int)blockDim.x};
+  const GridSync gs{X.st, &epoch};
+  const BlockSync bs;
+  const int top = (G < nl - 1) ? G : nl - 1;   // first level not handled grid-wide on the way down
+  if (!down(glev, tb, 0, top, grid_rg, gs)) return false;
+  if (G < nl) {
+    if (!gs()) return false;
+    if (blockIdx.x == 0) {
+      // level G's b and first sweep x were written grid-wide: stage them in shared memory
+      const Level<TP>& Lg = glev[G];
+      for (int c = threadIdx.x; c < Lg.n; c += blockDim.x) {
+        slev[G].b[c] = Lg.b[c];
+        slev[G].x[c] = Lg.x[c];
+      }
+      down(slev, tb, G, nl - 1, blk_rg, bs);
+      __syncthreads();
+      coarsest(slev, nl - 1, X.nu_c, tb, blk_rg, bs);
+      __syncthreads();
+      if (nl - 2 >= G) up(slev, tb, nl - 2, G, blk_rg, bs);
+      __syncthreads();
+      for (int c = threadIdx.x; c < Lg.n; c += blockDim.x) Lg.t[c] = slev[G].t[c];
+    }
+    if (!gs()) return false;                  // level G's result is read by every block next
+  } else {
+    if (!coarsest(glev, nl - 1, X.nu_c, tb, grid_rg, gs)) return false;
+    if (top >= 1 && !gs()) return false;
+  }
+  return up(glev, tb, top - 1, 0, grid_rg, gs);
+}
+
+struct PcgOut {
+  int it;
+  bool conv;
+  double res, bnorm;
+};
+
+// CG with the V-cycle preconditioner on A x = bscale * b (b is FP64), vectors
+// of type TV (double: FP64 path; float: inner solve of the mixed path), x
+// from 0. The fine-grid operator uses coefficients (cx, cy, cz) and the
+// diagonal table dg of type TV. z is kept orthogonal to the constants (the
+// Neumann null space): its mean is removed, so p and x never accumulate a
+// constant that would swamp the FP32 arithmetic of the inner solve.
+// Reduction slots 0..11.
+template <typename TV, typename TP>
+__device__ __noinline__ bool pcg(const Ctx& X, const Level<TP>* glev, const Level<TP>* slev, const Tables<TP>& tb,
+                    const double* b, double bscale, TV* x, TV* r, TV* p, TV* q, TV cx, TV cy, TV cz, const TV* dg,
+                    double tol, int max_it, unsigned int& epoch, PcgOut& out) {
+  constexpr int U = Batch<TV>::U;
+  const Level<TP>& L0 = glev[0];
+  const int nx = L0.nx, ny = L0.ny, nz = L0.nz, n = L0.n;
+  const int t0 = blockIdx.x * blockDim.x + threadIdx.x, gsz = gridDim.x * blockDim.x;
+  for (int c = t0; c < n; c += gsz) {
+    int i, j, k;
+    decompose3(c, L0.fx, L0.fy, i, j, k);
+    const TV bc = (TV)(b[c] * bscale);
+    r[c] = bc;
+    x[c] = TV(0);
+    L0.b[c] = (TP)bc;
+    L0.x[c] = tb.wid[0][code_of(L0, i, j, k)] * (TP)bc;
+  }
+  if (!vcycle(X, glev, slev, tb, epoch)) return false;
+  TV a0 = TV(0), a1 = TV(0), a2 = TV(0), a3 = TV(0);
+  for (int c = t0; c < n; c += gsz) {
+    const TV zc = (TV)L0.t[c], rc = r[c];
+    a0 += rc * zc;
+    a1 += rc * rc;
+    a2 += zc;
+    a3 += rc;
+  }
+  Vec<4> o0, s0 = {{(double)a0, (double)a1, (double)a2, (double)a3}};
+  if (!grid_sum<4>(s0, X.partial, X.max_blocks, 0, X.st, epoch, o0)) return false;
+  const double inv_n = 1.0 / (double)n;
+  double mz = o0.v[2] * inv_n;
+  for (int c = t0; c < n; c += gsz) p[c] = (TV)L0.t[c] - (TV)mz;
+  if (!grid_barrier(X.st, gridDim.x, epoch)) return false;
+  out.bnorm = sqrt(o0.v[1]);
+  double rz = o0.v[0] - mz * o0.v[3], res = out.bnorm;
+  const double thr = tol * out.bnorm;
+  int it = 0;
+  bool conv = (out.bnorm == 0.0);
+  while (!conv && it < max_it && isfinite(res)) {
+    ++it;
+    TV s1 = TV(0);
+    for (int base = t0; base < n; base += U * gsz) {   // q = A p
+      Nb<TV> nb[U];
+      int code[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int c = base + u * gsz;
+        if (c < n) {
+          int i, j, k;
+          decompose3(c, L0.fx, L0.fy, i, j, k);
+          code[u] = code_of(L0, i, j, k);
+          nb[u] = load_nb(p, c, i, j, k, nx, ny, nz);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int c = base + u * gsz;
+        if (c < n) {
+          const TV qc = apply_nb(nb[u], cx, cy, cz, dg[code[u]]);
+          q[c] = qc;
+          s1 += nb[u].c0 * qc;
+        }
+      }
+    }
+    Vec<1> o1, d1 = {{(double)s1}};
+    if (!grid_sum<1>(d1, X.partial, X.max_blocks, 4, X.st, epoch, o1)) return false;
+    const TV alpha = (TV)(rz / o1.v[0]);
+    for (int base = t0; base < n; base += U * gsz) {   // x += alpha p; r -= alpha q; first V-cycle sweep
+      TV pv[U], qv[U], xv[U], rv[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int c = base + u * gsz;
+        if (c < n) {
+          pv[u] = p[c];
+          qv[u] = q[c];
+          xv[u] = x[c];
+          rv[u] = r[c];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int c = base + u * gsz;
+        if (c < n) {
+          int i, j, k;
+          decompose3(c, L0.fx, L0.fy, i, j, k);
+          x[c] = xv[u] + alpha * pv[u];
+          const TV rc = rv[u] - alpha * qv[u];
+          r[c] = rc;
+          L0.b[c] = (TP)rc;
+          L0.x[c] = tb.wid[0][code_of(L0, i, j, k)] * (TP)rc;
+        }
+      }
+    }
+    if (!vcycle(X, glev, slev, tb, epoch)) return false;
+    TV s2 = TV(0), s3 = TV(0), s4 = TV(0), s5 = TV(0);
+    for (int base = t0; base < n; base += U * gsz) {
+      TV zv[U], rv[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int c = base + u * gsz;
+        zv[u] = c < n ? (TV)L0.t[c] : TV(0);
+        rv[u] = c < n ? r[c] : TV(0);
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        s2 += rv[u] * zv[u];
+        s3 += rv[u] * rv[u];
+        s4 += zv[u];
+        s5 += rv[u];
+      }
+    }
+    Vec<4> o2, d2 = {{(double)s2, (double)s3, (double)s4, (double)s5}};
+    if (!grid_sum<4>(d2, X.partial, X.max_blocks, 8, X.st, epoch, o2)) return false;
+    res = sqrt(o2.v[1]);
+    conv = res <= thr;
+    if (conv) break;
+    mz = o2.v[2] * inv_n;
+    const double rz_new = o2.v[0] - mz * o2.v[3];
+    const TV beta = (TV)(rz_new / rz);
+    const TV mzt = (TV)mz;
+    rz = rz_new;
+    for (int base = t0; base < n; base += U * gsz) {
+      TV zv[U], pv[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int c = base + u * gsz;
+        if (c < n) {
+          zv[u] = (TV)L0.t[c];
+          pv[u] = p[c];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int c = base + u * gsz;
+        if (c < n) p[c] = (zv[u] - mzt) + beta * pv[u];
+      }
+    }
+    if (!grid_barrier(X.st, gridDim.x, epoch)) return false;
+  }
+  out.it = it;
+  out.conv = conv;
+  out.res = res;
+  return true;
+}
+
+template <typename TP>
+__global__ void __launch_bounds__(kBlock, 2) k_pcg_mg(MGArgs<TP> A) {
+  extern __shared__ __align__(16) unsigned char dsm[];
+  __shared__ Tables<TP> tb;
+  __shared__ Level<TP> glev[kMaxLevels];
+  __shared__ Level<TP> slev[kMaxLevels];
+  for (int q = threadIdx.x; q < A.nl * 27; q += blockDim.x) {
+    const int l = q / 27, c = q % 27;
+    const double ax = (double)A.lev[l].ax, ay = (double)A.lev[l].ay, az = (double)A.lev[l].az;
+    const double d = (double)(c % 3) * ax + (double)((c / 3) % 3) * ay + (double)(c / 9) * az;
+    tb.diag[l][c] = (TP)d;
+    tb.wid[l][c] = d > 0.0 ? (TP)(kOmega / d) : TP(0);
+  }
+  if (threadIdx.x < 27) {
+    const int c = threadIdx.x;
+    tb.diag64[c] = (c % 3) * A.cx + ((c / 3) % 3) * A.cy + (c / 9) * A.cz;
+  }
+  if (threadIdx.x == 0) {
+    for (int l = 0; l < A.nl; ++l) {
+      glev[l] = A.lev[l];
+      slev[l] = A.lev[l];
+      if (l >= A.G) {
+        TP* base = reinterpret_cast<TP*>(dsm) + A.lev[l].soff;
+        const int nl_ = A.lev[l].n;
+        slev[l].b = base;
+        slev[l].x = base + nl_;
+        slev[l].t = base + 2 * nl_;
+        slev[l].r = base + 3 * nl_;
+      }
+    }
+  }
+  __syncthreads();
+  const Ctx X{A.nl, A.nu_c, A.G, A.st, A.partial, A.max_blocks};
+  unsigned int epoch = 0;
+  const Level<TP>& L0 = glev[0];
+  const int n = L0.n;
+  const int t0 = blockIdx.x * blockDim.x + threadIdx.x, gsz = gridDim.x * blockDim.x;
+  double* b = A.b;
+  double* x = A.x;
+  double* r = A.r;
+
+  // consistency: remove the mean of the right-hand side (Neumann null space)
+  Vec<1> sb = {{0.0}};
+  for (int c = t0; c < n; c += gsz) sb.v[0] += b[c];
+  Vec<1> ob;
+  if (!grid_sum<1>(sb, X.partial, X.max_blocks, 12, X.st, epoch, ob)) return;
+  const double mean_b = ob.v[0] / (double)n;
+  for (int c = t0; c < n; c += gsz) b[c] -= mean_b;
+
+  int iters = 0, refs = 0;
+  bool conv = false;
+  double rel = 0.0;
+  // TP = double: the FP64 path; TP = float: the mixed path (refinement)
+  if constexpr (sizeof(TP) == 8) {
+    PcgOut o;
+    if (!pcg<double, TP>(X, glev, slev, tb, b, 1.0, x, r, A.p, A.q, A.cx, A.cy, A.cz, tb.diag64, A.tol, A.max_it,
+                         epoch, o))
+      return;
+    iters = o.it;
+    conv = o.conv;
+    rel = o.bnorm > 0.0 ? o.res / o.bnorm : 0.0;
+  } else {
+    Vec<1> s = {{0.0}};
+    for (int c = t0; c < n; c += gsz) {
+      const double bc = b[c];
+      x[c] = 0.0;
+      r[c] = bc;
+      s.v[0] += bc * bc;
+    }
+    Vec<1> o;
+    if (!grid_sum<1>(s, X.partial, X.max_blocks, 13, X.st, epoch, o)) return;
+    const double bn = sqrt(o.v[0]);
+    double rn = bn;
+    const double thr = A.tol * bn;
+    const double cx = A.cx, cy = A.cy, cz = A.cz;
+    conv = (bn == 0.0);
+    while (!conv && refs < kMaxRefineP && iters < A.max_it && isfinite(rn)) {
+      ++refs;
+      // the inner solve sees the residual scaled to unit norm (no FP32 under- or overflow)
+      PcgOut io;
+      if (!pcg<TP, TP>(X, glev, slev, tb, r, 1.0 / rn, A.di, A.ri, A.pi, A.qi, L0.ax, L0.ay, L0.az, tb.diag[0],
+                       kInnerTolP, A.max_it - iters, epoch, io))
+        return;
+      iters += io.it;
+      for (int c = t0; c < n; c += gsz) x[c] += rn * (double)A.di[c];
+      if (!grid_barrier(X.st, gridDim.x, epoch)) return;
+      Vec<1> s2 = {{0.0}};
+      for (int c = t0; c < n; c += gsz) {        // FP64 residual of the refined iterate
+        int i, j, k;
+        decompose3(c, L0.fx, L0.fy, i, j, k);
+        const double rc = b[c] - lap(x, c, i, j, k, L0.nx, L0.ny, L0.nz, cx, cy, cz, tb.diag64[code_of(L0, i, j, k)]);
+        r[c] = rc;
+        s2.v[0] += rc * rc;
+      }
+      Vec<1> o2;
+      if (!grid_sum<1>(s2, X.partial, X.max_blocks, 14, X.st, epoch, o2)) return;
+      rn = sqrt(o2.v[0]);
+      conv = rn <= thr;
+      if (io.it == 0) break;                     // the inner solve made no progress
+    }
+    rel = bn > 0.0 ? rn / bn : 0.0;
+  }
+  // gauge: zero-mean correction
+  Vec<1> sx = {{0.0}};
+  for (int c = t0; c < n; c += gsz) sx.v[0] += x[c];
+  Vec<1> ox;
+  if (!grid_sum<1>(sx, X.partial, X.max_blocks, 15, X.st, epoch, ox)) return;
+  const double mean_x = ox.v[0] / (double)n;
+  for (int c = t0; c < n; c += gsz) x[c] -= mean_x;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    SolveStat& st = A.st->stat[A.stat_index];
+    st.iters = iters;
+    st.iters_total += iters;
+    st.refinements = refs;
+    st.converged = conv ? 1 : 0;
+    st.nonfinite = isfinite(rel) ? 0 : 1;
+    st.relres = rel;
+    if (!isfinite(rel)) atomicExch(&A.st->sticky, (int)SS_ENAN);
+    else if (!conv) atomicCAS(&A.st->sticky, (int)SS_OK, (int)SS_ENOTCONV);
+  }
+}
+
+template <typename TP>
+MGArgs<TP> make_args(const MGPlan& pl, const Params& pr, double* b, double* x, const SolverCtl& ctl, Scratch& sc,
+                     DevStatus* st, size_t& smem) {
+  MGArgs<TP> A;
+  memset(&A, 0, sizeof A);
+  A.nl = pl.nl;
+  A.nu_c = 8;
+  A.G = pl.nl;
+  smem = 0;
+  for (int l = 0; l < pl.nl; ++l) {
+    Level<TP>& L = A.lev[l];
+    L.nx = pl.n[l][0]; L.ny = pl.n[l][1]; L.nz = pl.n[l][2];
+    L.n = L.nx * L.ny * L.nz;
+    L.fx = make_fastdiv(L.nx);
+    L.fy = make_fastdiv(L.ny);
+    L.cx = pl.c[l][0]; L.cy = pl.c[l][1]; L.cz = pl.c[l][2];
+    L.ax = (TP)(1.0 / (pl.h[l][0] * pl.h[l][0]));
+    L.ay = (TP)(1.0 / (pl.h[l][1] * pl.h[l][1]));
+    L.az = pr.dim == 3 ? (TP)(1.0 / (pl.h[l][2] * pl.h[l][2])) : TP(0);
+    L.b = (TP*)pl.vec[l][0]; L.x = (TP*)pl.vec[l][1]; L.t = (TP*)pl.vec[l][2]; L.r = (TP*)pl.vec[l][3];
+    L.local = pl.local[l];
+    if (L.local && A.G == pl.nl) A.G = l;
+    if (l >= A.G) {
+      L.soff = (int)(smem / sizeof(TP));
+      smem += 4 * (size_t)L.n * sizeof(TP);
+    }
+  }
+  A.mixed = pl.fp32;
+  A.cx = 1.0 / (pr.hx * pr.hx);
+  A.cy = 1.0 / (pr.hy * pr.hy);
+  A.cz = pr.dim == 3 ? 1.0 / (pr.hz * pr.hz) : 0.0;
+  A.b = b; A.x = x;
+  A.r = sc.v[0]; A.p = sc.v[4]; A.q = sc.v[3];
+  if (pl.fp32) {
+    A.ri = (TP*)sc.f[1]; A.pi = (TP*)sc.f[2]; A.qi = (TP*)sc.f[3]; A.di = (TP*)sc.f[4];
+  }
+  A.tol = ctl.tol;
+  A.max_it = ctl.max_it;
+  A.stat_index = ctl.stat_index;
+  A.partial = sc.partial;
+  A.max_blocks = sc.max_blocks;
+  A.st = st;
+  return A;
+}
+
+template <typename TP>
+cudaError_t launch_t(const MGPlan& pl, const Params& pr, double* b, double* x, const SolverCtl& ctl, Scratch& sc,
+                     DevStatus* st, cudaStream_t s) {
+  size_t smem = 0;
+  MGArgs<TP> A = make_args<TP>(pl, pr, b, x, ctl, sc, st, smem);
+  const void* kern = (const void*)k_pcg_mg<TP>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const long long n = (long long)pr.nx * pr.ny * pr.nz;
+  const int nb = coop_blocks_for_smem(kern, n, sc.max_blocks, smem);
+  if ((e = cudaMemsetAsync(&st->barrier, 0, sizeof(unsigned int), s)) != cudaSuccess) return e;
+  void* args[] = {&A};
+  return cudaLaunchCooperativeKernel(kern, dim3(nb), dim3(kBlock), args, smem, s);
+}
+
+}  // namespace
+
+void plan_multigrid(const Params& pr, MGPlan& pl, int fp32) {
+  memset(&pl, 0, sizeof pl);
+  int n[3] = {pr.nx, pr.ny, pr.dim == 3 ? pr.nz : 1};
+  double h[3] = {pr.hx, pr.hy, pr.dim == 3 ? pr.hz : 1.0};
+  const long long local_max = fp32 ? 4096 : 512;
+  int l = 0;
+  while (true) {
+    pl.n[l][0] = n[0]; pl.n[l][1] = n[1]; pl.n[l][2] = n[2];
+    pl.h[l][0] = h[0]; pl.h[l][1] = h[1]; pl.h[l][2] = h[2];
+    const long long cells = (long long)n[0] * n[1] * n[2];
+    pl.local[l] = cells <= local_max;
+    int c[3] = {0, 0, 0};
+    bool any = false;
+    for (int a = 0; a < pr.dim; ++a) {
+      if (n[a] % 2 == 0 && n[a] >= 4) { c[a] = 1; any = true; }
+    }
+    if (!any || cells <= 32 || l == kMaxLevels - 1) break;
+    pl.c[l][0] = c[0]; pl.c[l][1] = c[1]; pl.c[l][2] = c[2];
+    for (int a = 0; a < 3; ++a)
+      if (c[a]) { n[a] /= 2; h[a] *= 2.0; }
+    ++l;
+  }
+  pl.nl = l + 1;
+  // once a level is local every coarser level is too
+  for (int q = 1; q < pl.nl; ++q) pl.local[q] = pl.local[q] || pl.local[q - 1];
+  pl.fp32 = fp32;
+}
+
+cudaError_t launch_pcg_mg(const MGPlan& pl, const Params& pr, double* b, double* x, const SolverCtl& ctl, Scratch& sc,
+                          DevStatus* st, cudaStream_t s) {
+  if (pl.fp32) return launch_t<float>(pl, pr, b, x, ctl, sc, st, s);
+  return launch_t<double>(pl, pr, b, x, ctl, sc, st, s);
+}
+
+}  // namespace solid

@@ -20,7 +20,7 @@ namespace solid {
 
 constexpr int kBlock = 256;              // threads per block of every kernel
 constexpr int kMaxRedSlots = 16;         // reduction slots (one per reduction site)
-constexpr long long kSpinLimit = 1LL << 22;  // grid-barrier polls before giving up (~1 s)
+constexpr long long kSpinLimit = 1LL << 21;  // grid-barrier polls before giving up (about a second)
 
 // device-side error codes (sticky word in DevStatus::err)
 enum : int { kErrNone = 0, kErrBarrier = 1 };
@@ -89,10 +89,18 @@ __device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int* p) {
   return v;
 }
 
+__device__ __forceinline__ unsigned int atom_add_acq_rel_u32(unsigned int* p, unsigned int v) {
+  unsigned int old;
+  asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
+
 // Grid-wide barrier for cooperative launches. The arrival counter is zeroed
-// by the host before the launch; `epoch` counts barriers passed by this block.
-// A poll limit bounds the wait: on expiry the sticky error is set and every
-// block returns false from then on, so the kernel unwinds instead of hanging.
+// by the host before the launch; `epoch` counts barriers passed by this
+// block. Thread 0 arrives with an acq_rel atomic (publishing the block's
+// writes) and polls with acquire loads. A poll limit bounds the wait: on
+// expiry the sticky error is set and every block returns false from then
+// on, so the kernel unwinds instead of hanging.
 __device__ __forceinline__ bool grid_barrier(DevStatus* st, unsigned int nblocks, unsigned int& epoch) {
   __shared__ int s_ok;
   __syncthreads();
@@ -100,16 +108,18 @@ __device__ __forceinline__ bool grid_barrier(DevStatus* st, unsigned int nblocks
     epoch += 1u;
     const unsigned int target = epoch * nblocks;
     __threadfence();
-    atomicAdd(&st->barrier, 1u);
+    const unsigned int old = atom_add_acq_rel_u32(&st->barrier, 1u);
     int ok = 1;
-    long long spins = 0;
-    while (ld_acquire_u32(&st->barrier) < target) {
-      if (*(volatile int*)&st->err != kErrNone) { ok = 0; break; }
-      if (++spins > kSpinLimit) { atomicExch(&st->err, kErrBarrier); ok = 0; break; }
-      __nanosleep(32);
+    if (old + 1u != target) {
+      long long spins = 0;
+      while (ld_acquire_u32(&st->barrier) < target) {
+        if ((++spins & 255) == 0) {
+          if (*(volatile int*)&st->err != kErrNone) { ok = 0; break; }
+          if (spins > kSpinLimit) { atomicExch(&st->err, kErrBarrier); ok = 0; break; }
+        }
+      }
     }
-    __threadfence();
-    s_ok = ok && (*(volatile int*)&st->err == kErrNone);
+    s_ok = ok;
   }
   __syncthreads();
   return s_ok != 0;
@@ -118,9 +128,9 @@ __device__ __forceinline__ bool grid_barrier(DevStatus* st, unsigned int nblocks
 template <int K>
 struct Vec { double v[K]; };
 
-// Block-wide sum of K doubles; result valid in all threads.
+// Block-wide sum of K doubles; the result is valid in thread 0 only.
 template <int K>
-__device__ __forceinline__ Vec<K> block_sum(Vec<K> x) {
+__device__ __forceinline__ Vec<K> block_sum0(Vec<K> x) {
   __shared__ double sh[K][kBlock / 32];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
@@ -132,47 +142,92 @@ __device__ __forceinline__ Vec<K> block_sum(Vec<K> x) {
   }
   __syncthreads();
   Vec<K> r;
+  if (wid == 0) {
 #pragma unroll
-  for (int q = 0; q < K; ++q) {
-    double s = 0.0;
+    for (int q = 0; q < K; ++q) {
+      double s = lane < kBlock / 32 ? sh[q][lane] : 0.0;
 #pragma unroll
-    for (int w = 0; w < kBlock / 32; ++w) s += sh[q][w];
-    r.v[q] = s;
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+      r.v[q] = s;
+    }
   }
-  __syncthreads();
   return r;
 }
 
 // Deterministic grid reduction of K doubles: every block writes its partial
-// sums to slots [slot, slot+K), passes a grid barrier, then sums all blocks'
-// partials in block order (same order in every block, so every block gets
-// bit-identical totals). Returns false if the barrier gave up.
+// sums to slots [slot, slot+K), passes a grid barrier, then warp q of every
+// block sums slot q's partials in block order (the same order everywhere,
+// so all blocks get bit-identical totals). Returns false if the barrier
+// gave up.
 template <int K>
 __device__ __forceinline__ bool grid_sum(Vec<K> x, double* partial, int max_blocks, int slot, DevStatus* st,
                                          unsigned int& epoch, Vec<K>& out) {
-  Vec<K> b = block_sum<K>(x);
+  static_assert(K <= kBlock / 32, "one warp per reduced value");
+  Vec<K> b = block_sum0<K>(x);
   if (threadIdx.x == 0) {
 #pragma unroll
     for (int q = 0; q < K; ++q) partial[(size_t)(slot + q) * max_blocks + blockIdx.x] = b.v[q];
   }
   if (!grid_barrier(st, gridDim.x, epoch)) return false;
   __shared__ double tot[K];
-  if (threadIdx.x < 32) {
-#pragma unroll
-    for (int q = 0; q < K; ++q) {
-      const volatile double* pp = partial + (size_t)(slot + q) * max_blocks;
-      double s = 0.0;
-      for (int i = threadIdx.x; i < (int)gridDim.x; i += 32) s += pp[i];
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-      if (threadIdx.x == 0) tot[q] = s;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (wid < K) {
+    const double* pp = partial + (size_t)(slot + wid) * max_blocks;
+    const int nb = (int)gridDim.x;
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    int i = lane;
+    for (; i + 96 < nb; i += 128) {
+      s0 += __ldcg(pp + i);
+      s1 += __ldcg(pp + i + 32);
+      s2 += __ldcg(pp + i + 64);
+      s3 += __ldcg(pp + i + 96);
     }
+    for (; i < nb; i += 32) s0 += __ldcg(pp + i);
+    double s = (s0 + s1) + (s2 + s3);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) tot[wid] = s;
   }
   __syncthreads();
 #pragma unroll
   for (int q = 0; q < K; ++q) out.v[q] = tot[q];
   __syncthreads();
   return true;
+}
+
+// Division by a runtime constant d >= 1 for 0 <= n < 2^31 with a multiply-high
+// and a shift: q = (umulhi(n, m) + n) >> s, s = ceil(log2 d),
+// m = floor(2^32 (2^s - d) / d) + 1 (round-up method of Granlund & Montgomery).
+struct FastDiv {
+  unsigned int d, m, s;
+};
+
+inline FastDiv make_fastdiv(unsigned int d) {
+  FastDiv f;
+  f.d = d;
+  if (d <= 1) {
+    f.d = 1;
+    f.m = 0;
+    f.s = 0;
+    return f;
+  }
+  unsigned int s = 0;
+  while ((1ull << s) < d) ++s;
+  f.s = s;
+  f.m = (unsigned int)((((unsigned long long)1 << 32) * (((unsigned long long)1 << s) - d)) / d + 1);
+  return f;
+}
+
+__device__ __forceinline__ int fdiv(int n, const FastDiv& f) {
+  return (int)((__umulhi((unsigned int)n, f.m) + (unsigned int)n) >> f.s);
+}
+
+// (i, j, k) of flat index c on an nx * ny * nz grid
+__device__ __forceinline__ void decompose3(int c, const FastDiv& fx, const FastDiv& fy, int& i, int& j, int& k) {
+  const int t = fdiv(c, fx);
+  i = c - t * (int)fx.d;
+  k = fdiv(t, fy);
+  j = t - k * (int)fy.d;
 }
 
 // ---------------------------------------------------------------- host-side launchers
@@ -194,7 +249,6 @@ cudaError_t launch_lever(const Params& pr, double* T, double* gl, const double* 
 // K^{-1} and A_g are always refreshed from g_l.
 cudaError_t launch_equilibrate(const Params& pr, const double* T, const double* C, double* gl, double* Cl,
                                double* Cs, double* Kinv, double* Ag, int from_T, int write_cl, cudaStream_t s);
-cudaError_t launch_fp32_planes(const Sys& sys, int dim, cudaStream_t s);
 
 // krylov.cu
 struct SolverCtl {
@@ -209,5 +263,24 @@ cudaError_t launch_pcg_poisson(const Params& pr, double* b, double* x, const Sol
                                DevStatus* st, cudaStream_t s);
 int cooperative_blocks(const void* kernel, long long rows);
 int max_cooperative_blocks();
+// blocks for a cooperative launch of `kernel` over `rows` rows: at most the
+// co-resident limit (capped at 4 per SM) and at most max_blocks
+int coop_blocks_for(const void* kernel, long long rows, int max_blocks);
+int coop_blocks_for_smem(const void* kernel, long long rows, int max_blocks, size_t smem);
+
+// mg.cu: geometric multigrid hierarchy of the pressure Laplacian
+constexpr int kMaxLevels = 12;
+struct MGPlan {
+  int nl;                      // levels (level 0 = the grid itself)
+  int n[kMaxLevels][3];        // cells per axis
+  int c[kMaxLevels][3];        // 1: the next level halves this axis
+  double h[kMaxLevels][3];     // spacings
+  int local[kMaxLevels];       // run by one block
+  void* vec[kMaxLevels][4];    // b, x, t, r of the level (float or double)
+  int fp32;                    // V-cycle vectors in FP32
+};
+void plan_multigrid(const Params& pr, MGPlan& pl, int fp32);
+cudaError_t launch_pcg_mg(const MGPlan& pl, const Params& pr, double* b, double* x, const SolverCtl& ctl,
+                          Scratch& sc, DevStatus* st, cudaStream_t s);
 
 }  // namespace solid

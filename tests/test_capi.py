@@ -44,7 +44,7 @@ def test_struct_layouts_match_header(built_lib):
     from paper_2303_10783_gb300 import solid
     assert ctypes.sizeof(solid.Alloy) == 17 * 8
     assert ctypes.sizeof(solid.BC) == 24
-    assert ctypes.sizeof(solid.Grid) == 4 * 4 + 3 * 8 + 8 + 8 + 16 + 8
+    assert ctypes.sizeof(solid.Grid) == 4 * 4 + 3 * 8 + 8 + 8 + 16 + 8 + 8
 
 
 def test_host_validation_without_gpu(built_lib):

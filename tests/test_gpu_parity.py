@@ -38,10 +38,17 @@ def _tight(case):
 CASES_2D = [cases.cavity_2d(61, 37, robin={"x-": (400.0, 298.0), "y+": (60.0, 300.0)})]
 CASES_3D = [cases.box_3d(27, 19, 13, robin={"x-": (400.0, 298.0), "z+": (60.0, 300.0)})]
 SMALL = CASES_2D + CASES_3D
+# sizes whose multigrid hierarchy has several levels (the ragged ones above have one)
+MULTILEVEL = [cases.cavity_2d(64, 40, robin={"x-": (400.0, 298.0), "y+": (60.0, 300.0)}),
+              cases.box_3d(32, 24, 16, robin={"x-": (400.0, 298.0), "z+": (60.0, 300.0)})]
+SOLVE_CASES = [(c, prec, pre) for c in SMALL + MULTILEVEL for prec in ("fp64", "mixed") for pre in ("mg", "jacobi")]
+SOLVE_IDS = ["%s-%dx%dx%d-%s-%s" % ("2d" if c["dim"] == 2 else "3d", c["nx"], c["ny"], c["nz"], prec, pre)
+             for c, prec, pre in SOLVE_CASES]
+PREC = {"fp64": solid.SS_FP64, "mixed": solid.SS_MIXED}
 
 
-def _random_case(case, seed):
-    c = solid.Case(case)
+def _random_case(case, seed, precision=solid.SS_FP64):
+    c = solid.Case(case, precision=precision)
     f = cases.random_state(case, seed)
     c.set_fields(f)
     return c, f
@@ -104,10 +111,10 @@ def test_lever_kernel_matches_oracle(lib, with_eutectic):
     c.close()
 
 
-@pytest.mark.parametrize("case", SMALL, ids=["2d", "3d"])
-def test_solves_match_oracle(lib, case):
-    case = _tight(dict(case))
-    c, f = _random_case(case, 12)
+@pytest.mark.parametrize("case,prec,precond", SOLVE_CASES, ids=SOLVE_IDS)
+def test_solves_match_oracle(lib, case, prec, precond):
+    case = _tight(dict(case, precond_p=precond))
+    c, f = _random_case(case, 12, PREC[prec])
     g = oracle.Grid(case)
     st = _oracle_state(f)
     # predictor components
@@ -147,10 +154,10 @@ def test_solves_match_oracle(lib, case):
     c.close()
 
 
-def _run_pair(case, nsteps, T0shift=-0.8):
+def _run_pair(case, nsteps, T0shift=-0.8, precision=solid.SS_FP64):
     f = cases.initial_fields(case)
     T0 = f["T"] + T0shift
-    c = solid.Case(case)
+    c = solid.Case(case, precision=precision)
     c.initialize(T0, f["C"])
     g = oracle.Grid(case)
     st = oracle.initial_state(case, T0, f["C"])
@@ -167,11 +174,22 @@ def _run_pair(case, nsteps, T0shift=-0.8):
     return gpu, st, stats
 
 
-@pytest.mark.parametrize("case", [cases.cavity_2d(), cases.box_3d(19, 13, 11)], ids=["2d-50x30", "3d-19x13x11"])
-def test_step_parity_100_steps(lib, case):
-    """The FP64 GPU step matches the oracle to 1e-9 relative L-inf on every field after 100 steps."""
+STEP_CASES = [(cases.cavity_2d(), "fp64"), (cases.box_3d(19, 13, 11), "fp64"), (cases.box_3d(24, 16, 12), "fp64"),
+              (cases.cavity_2d(), "mixed"), (cases.box_3d(24, 16, 12), "mixed")]
+
+
+@pytest.mark.parametrize("case,prec", STEP_CASES,
+                         ids=["2d-50x30-fp64", "3d-19x13x11-fp64", "3d-24x16x12-fp64", "2d-50x30-mixed",
+                              "3d-24x16x12-mixed"])
+def test_step_parity_100_steps(lib, case, prec):
+    """The GPU step matches the oracle to 1e-9 relative L-inf on every field after 100 steps
+    (the mixed path reaches the same bound: its outer iterations and residuals are FP64)."""
     case = _tight(dict(case))
-    gpu, st, stats = _run_pair(case, 100)
+    if prec == "mixed":
+        # the mixed path stops on the true FP64 residual, which rounding keeps
+        # above 1e-14 on some systems (the FP64 path tests its recursive one)
+        case.update(tol_p=1e-13, tol_t=1e-13)
+    gpu, st, stats = _run_pair(case, 100, precision=PREC[prec])
     assert stats["status"] == solid.SS_OK
     for k in ("p", "T", "C", "gl", "Cl", "Cs"):
         assert _rel(gpu[k], getattr(st, k)) < STEP_TOL, (k, _rel(gpu[k], getattr(st, k)))
@@ -298,4 +316,25 @@ def test_full_size_steps_keep_invariants(lib, full):
     A = oracle.sparse_from_planes(sysT)
     r = sysT["b"].ravel() - A @ sysT["x"].ravel()
     assert np.linalg.norm(r) <= 10 * case["tol_t"] * np.linalg.norm(sysT["b"])
+    c.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_tiny_right_hand_side(lib, prec):
+    """A nearly solenoidal u* gives a pressure right-hand side near the
+    rounding level; the solves must neither underflow (the mixed path scales
+    its FP32 inner problem) nor lose accuracy."""
+    case = _tight(dict(cases.box_3d(32, 24, 16)))
+    c = solid.Case(case, precision=PREC[prec])
+    f = cases.random_state(case, 31, vel_scale=1e-22)
+    c.set_fields(f)
+    g = oracle.Grid(case)
+    for name in "uvw":
+        c.assemble(name)
+    c.assemble("p")
+    c.solve("p")
+    pc = c.get_system("p")["x"]
+    assert np.all(np.isfinite(pc))
+    pref = oracle.solve_poisson(g, oracle.poisson_rhs(g, [f["u"], f["v"], f["w"]], case))
+    assert _rel(pc, pref) < 1e-10
     c.close()

@@ -25,7 +25,7 @@ REL = 1e-12    # the tolerance the stage parity tests use for pressure correctio
 @pytest.mark.parametrize("case", [cases.box_3d(37, 23, 17), cases.cavity_2d(61, 37)], ids=["3d", "2d"])
 def test_noalloc_solve_matches_workspace_solve(lib, case):
     import torch
-    case = dict(case, tol_p=TOL, max_it_p=20000)
+    case = dict(case, tol_p=TOL, max_it_p=20000, precond_p="jacobi")   # the same algorithm as the no-alloc solve
     c = solid.Case(case)
     c.set_fields(cases.random_state(case, 5))
     for name in "uvw"[: case["dim"]]:
