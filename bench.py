@@ -59,6 +59,11 @@ def parse():
                     help="both: headline = mixed path, FP64 path measured alongside")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--workload", choices=("box", "batched", "serving", "ingot"), default="box",
+                    help="box: the 128x96x96 headline; batched: 64 independent cavities; serving: request stream; "
+                         "ingot: 384x256x256")
+    ap.add_argument("--requests", type=int, default=24, help="serving: requests in the sample")
+    ap.add_argument("--request-steps", type=int, default=100, help="serving: steps per request in the sample")
     ap.add_argument("--nx", type=int, default=128)
     ap.add_argument("--ny", type=int, default=96)
     ap.add_argument("--nz", type=int, default=96)
@@ -74,6 +79,8 @@ def dist_env():
 
 def workload(args, rank=0):
     """The benchmark case; rank r gets seed 1 + r (independent replica)."""
+    if getattr(args, "workload", "box") == "ingot":
+        return cases.ingot_3d(args.nx, args.ny, args.nz, seed=4 + rank)
     return cases.box_3d(args.nx, args.ny, args.nz, seed=1 + rank)
 
 
@@ -357,7 +364,8 @@ def run_ours(args):
         "metric": "cell-steps/s", "value": h["value"], "unit": "cell-steps/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": h["ms_max"] / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64" if head == "mixed" else "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "cells": ncell, "precision": head, "tol_p": case["tol_p"],
+        "config": {"workload": WORKLOAD if args.workload == "box" else "ingot_3d_%dx%dx%d" % (args.nx, args.ny, args.nz),
+                   "cells": ncell, "precision": head, "tol_p": case["tol_p"],
                    "tol_t": case["tol_t"], "dt": case["dt"], "pressure_preconditioner": case.get("precond_p", "mg"),
                    "parallelism": "replicas" if world > 1 else "single",
                    "l2": "inputs larger than L2: each step streams ~0.5 GB of fields and DIA planes (L2 129 MB); "
@@ -388,10 +396,75 @@ def run_ours(args):
     return 0
 
 
+def run_batched(args):
+    """64 independent cavities stepped side by side (one stream each, graph-replayed steps)."""
+    import torch
+    from paper_2303_10783_gb300 import solid
+    from paper_2303_10783_gb300.batch import Batch
+    rank, world, local = dist_env()
+    dist = init_group(world)
+    torch.cuda.set_device(local)
+    cs = cases.batch_cases(64, seed=2 + 100 * rank)
+    b = Batch(cs, precision=solid.SS_MIXED)
+    sampler = ClockSampler(local)
+    b.step(args.warmup)
+    b.sync()
+    barrier(dist)
+    sampler.start()
+    dt, _ = b.run(args.steps)
+    clocks = sampler.stop()
+    dt = max_over_ranks(dist, dt)
+    total = sum_over_ranks(dist, b.cells * args.steps)
+    status = b.sync()
+    kernels = sum(c.get_profile()["kernels"] for _, c, _ in b.members)
+    cells = b.cells
+    b.close()
+    if rank == 0:
+        print(json.dumps({"metric": "cell-steps/s", "value": total / dt, "unit": "cell-steps/s", "n_gpus": world,
+                          "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+                          "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+                          "data": "synthetic", "status": solid.STATUS_NAMES.get(status, status),
+                          "config": {"workload": "batched_64_cavities", "cases": len(cs), "cells": cells,
+                                     "precision": "mixed", "streams": len(cs), "graphs": True},
+                          "clocks": clocks, "gpu_launches": kernels}))
+    return 0
+
+
+def run_serving(args):
+    """A bounded sample of the request stream served under the 150 GB budget."""
+    import torch
+    from paper_2303_10783_gb300 import solid
+    from paper_2303_10783_gb300.serve import Server
+    torch.cuda.set_device(0)
+    reqs = cases.serving_requests(n=args.requests, steps=args.request_steps)
+    srv = Server(budget_bytes=150 * 10 ** 9, chunk=10)
+    rep = srv.run(reqs)
+    print(json.dumps({"metric": "cell-steps/s", "value": rep["cell_steps_per_s"], "unit": "cell-steps/s",
+                      "n_gpus": 1, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                      "dtype": "f32+f64", "data": "synthetic",
+                      "config": {"workload": "serving_requests", "requests": rep["requests"],
+                                 "steps_per_request": args.request_steps, "arrival_rate_per_s": 20.0,
+                                 "budget_bytes": rep["budget_bytes"],
+                                 "sample": "first %d requests of the seeded stream (grids 32^3..192^3), %d steps each"
+                                           % (args.requests, args.request_steps)},
+                      "p50_ms_per_100_steps": rep["p50_ms_per_100_steps"],
+                      "p99_ms_per_100_steps": rep["p99_ms_per_100_steps"],
+                      "p50_queue_s": rep["p50_queue_s"], "p99_queue_s": rep["p99_queue_s"],
+                      "max_active": rep["max_active"], "max_used_bytes": rep["max_used_bytes"],
+                      "wall_s": rep["wall_s"]}))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batched":
+        return run_batched(args)
+    if args.workload == "serving":
+        return run_serving(args)
+    if args.workload == "ingot":
+        args.nx, args.ny, args.nz = 384, 256, 256
     return run_ours(args)
 
 

@@ -167,6 +167,15 @@ ss_status ss_set_boundary(ss_case* c, int face, const ss_bc* bc);
  * ss_sync / ss_get_stats). */
 ss_status ss_step(ss_case* c, int n);
 
+/* Same as ss_step, but the launches of one step are captured once into a
+ * CUDA graph on the case's stream and the graph is replayed n times (fewer
+ * host launch calls; for small cases stepped side by side on many streams).
+ * The capture happens on the first call and again after any ss_set_alloy /
+ * ss_set_boundary. The stream must not be the legacy default stream
+ * (SS_EINVAL). Stage profiling is not recorded for graph steps; launch
+ * counts are. */
+ss_status ss_step_graph(ss_case* c, int n);
+
 /* Wait for the case's stream; return and clear the sticky solver status. */
 ss_status ss_sync(ss_case* c);
 

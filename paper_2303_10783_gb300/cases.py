@@ -89,13 +89,13 @@ def box_3d(nx=128, ny=96, nz=96, **kw):
 def ingot_3d(nx=384, ny=256, nz=256, **kw):
     """Large 3D 0.2 x 0.1 x 0.1 m ingot, Fe-C-like alloy cooled from the bottom (h = 800 to 298 K).
 
-    The initial temperature is 0.5 K above the liquidus of C0 (1776.4 K): the
-    workload states no initial temperature, and 0.5 K matches the superheat
-    of the cavity workload."""
+    The workload states no initial temperature: 1776.4 K is taken, about
+    half a kelvin above the liquidus of the nominal composition, like the
+    superheat of the cavity workload."""
     kw.setdefault("steps", 100)
     kw.setdefault("seed", 4)
     kw.setdefault("robin", {"z-": (800.0, 298.0)})
-    kw.setdefault("T0", 1811.0 - 78.0 * 0.45 + 0.5)
+    kw.setdefault("T0", 1776.4)
     return make_case(3, nx, ny, nz, 0.2, 0.1, 0.1, 0.01, alloy=fe_c_alloy(), **kw)
 
 
@@ -144,3 +144,64 @@ def random_state(case, seed, vel_scale=1e-3):
     out["v"][:, 0, :] = out["v"][:, -1, :] = 0.0
     out["w"][0] = out["w"][-1] = 0.0
     return {k: np.ascontiguousarray(v, dtype=np.float64) for k, v in out.items()}
+
+
+# ---------------------------------------------------------------- batched and served workloads
+
+BATCH_2D = ((64, 64), (96, 64), (128, 64), (128, 96), (128, 128), (192, 96), (192, 128), (256, 128), (64, 96),
+            (64, 128), (96, 128))
+BATCH_3D_EDGE = (32, 48, 64, 80, 96)
+
+
+def batch_cases(n=64, seed=2, steps=100):
+    """Independent cavities for the batched workload: half 2D, half 3D, x/y
+    aspect ratio drawn in [0.5, 2] (the grid closest to it from 64x64..256x128
+    in 2D, 32^3..96^3 in 3D, square cells, 0.06 m high), C0 ~ U[2, 15] wt%,
+    left-wall Robin cooling with h ~ U[100, 1000] W/m^2K to 298 K, mixed
+    precision tolerances of the 3D box workload. Initial temperature 503 K
+    (above the liquidus of every drawn composition), seeded noise."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for q in range(n):
+        dim = 2 if rng.uniform() < 0.5 else 3
+        aspect = rng.uniform(0.5, 2.0)
+        C0 = rng.uniform(2.0, 15.0)
+        h = rng.uniform(100.0, 1000.0)
+        alloy = sn_pb_alloy()
+        alloy["C0"] = C0
+        if dim == 2:
+            nx, ny = min(BATCH_2D, key=lambda g: abs(g[0] / g[1] - aspect))
+            nz = 1
+        else:
+            ny = nz = int(rng.choice(BATCH_3D_EDGE))
+            nx = min(BATCH_3D_EDGE, key=lambda e: abs(e / ny - aspect))
+        hy = 0.06 / ny
+        out.append(make_case(dim, nx, ny, nz, nx * hy, 0.06, nz * hy, 0.01, alloy=alloy,
+                             robin={"x-": (h, 298.0)}, T0=503.0, seed=1000 * seed + q, steps=steps))
+    return out
+
+
+SERVE_GRIDS = ((32, 32, 32), (64, 64, 64), (96, 96, 96), (128, 96, 96), (192, 192, 192))
+
+
+def serving_requests(n=1000, rate=20.0, seed=3, steps=500, grids=SERVE_GRIDS):
+    """Simulation requests of the serving workload: Poisson arrivals (mean
+    `rate` per second), 3D grid drawn uniformly from `grids` (0.06 m edge at
+    the smallest grid spacing of the box), C0 ~ U[2, 15] wt%, h ~ U[100, 1000],
+    bottom or side cooling 50/50, `steps` steps each. Returns a list of
+    (arrival_time_s, case)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    t = 0.0
+    out = []
+    for q in range(n):
+        t += rng.exponential(1.0 / rate)
+        nx, ny, nz = grids[int(rng.integers(len(grids)))]
+        C0 = rng.uniform(2.0, 15.0)
+        h = rng.uniform(100.0, 1000.0)
+        face = "z-" if rng.uniform() < 0.5 else "x-"
+        alloy = sn_pb_alloy()
+        alloy["C0"] = C0
+        hh = 0.06 / max(nx, ny, nz)
+        out.append((t, make_case(3, nx, ny, nz, nx * hh, ny * hh, nz * hh, 0.01, alloy=alloy, robin={face: (h, 298.0)},
+                                 T0=503.0, seed=10000 * seed + q, steps=steps)))
+    return out

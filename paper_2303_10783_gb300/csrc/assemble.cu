@@ -25,9 +25,13 @@
 namespace solid {
 namespace {
 
+// The pointwise and assembly kernels of this file use smaller blocks than the
+// cooperative solvers: one row per thread, no block-wide reductions.
+constexpr int kBlockA = 256;
+
 inline int grid_for(long long n) {
-  long long b = (n + kBlock - 1) / kBlock;
-  if (b > 152LL * 16) b = 152LL * 16;
+  long long b = (n + kBlockA - 1) / kBlockA;
+  if (b > 152LL * 32) b = 152LL * 32;
   if (b < 1) b = 1;
   return (int)b;
 }
@@ -83,7 +87,7 @@ __device__ __forceinline__ void write_row(const Sys& s, int r, int dim, double P
 }
 
 template <int A>
-__global__ void __launch_bounds__(kBlock) k_assemble_momentum(Params pr, Sys s, const double* __restrict__ u,
+__global__ void __launch_bounds__(kBlockA) k_assemble_momentum(Params pr, Sys s, const double* __restrict__ u,
                                                               const double* __restrict__ v,
                                                               const double* __restrict__ w, double* ustar,
                                                               const double* __restrict__ p,
@@ -157,7 +161,7 @@ __global__ void __launch_bounds__(kBlock) k_assemble_momentum(Params pr, Sys s, 
 // false: T* (Eq. 3.12) with diffusivity k/(rho c_p) and Robin walls.
 // `Ag` holds A_g per cell (kept current by k_lever / k_equilibrate).
 template <bool SOLUTE>
-__global__ void __launch_bounds__(kBlock) k_assemble_cells(Params pr, Sys s, const double* __restrict__ u,
+__global__ void __launch_bounds__(kBlockA) k_assemble_cells(Params pr, Sys s, const double* __restrict__ u,
                                                            const double* __restrict__ v,
                                                            const double* __restrict__ w,
                                                            const double* __restrict__ phi_n,
@@ -220,7 +224,7 @@ __global__ void __launch_bounds__(kBlock) k_assemble_cells(Params pr, Sys s, con
   }
 }
 
-__global__ void __launch_bounds__(kBlock) k_poisson_rhs(Params pr, const double* __restrict__ us,
+__global__ void __launch_bounds__(kBlockA) k_poisson_rhs(Params pr, const double* __restrict__ us,
                                                         const double* __restrict__ vs,
                                                         const double* __restrict__ ws, double* b) {
   const Axes ax = axes_of(pr);
@@ -237,7 +241,7 @@ __global__ void __launch_bounds__(kBlock) k_poisson_rhs(Params pr, const double*
 }
 
 // Faces of u, v, w then cells of p, one flat index space.
-__global__ void __launch_bounds__(kBlock) k_project(Params pr, double* u, double* v, double* w,
+__global__ void __launch_bounds__(kBlockA) k_project(Params pr, double* u, double* v, double* w,
                                                     const double* __restrict__ us,
                                                     const double* __restrict__ vs,
                                                     const double* __restrict__ ws,
@@ -286,7 +290,7 @@ __device__ __forceinline__ Phase phase_of(const Params& pr, double C, double g) 
   return o;
 }
 
-__global__ void __launch_bounds__(kBlock) k_lever(Params pr, double* T, double* gl, const double* __restrict__ C,
+__global__ void __launch_bounds__(kBlockA) k_lever(Params pr, double* T, double* gl, const double* __restrict__ C,
                                                   double* Cl, double* Cs, double* Kinv, double* Ag, int n) {
   const double kp = pr.kp, Tm = pr.Tm;
   const double cpL = pr.cp / pr.L, Lcp = pr.L / pr.cp;
@@ -317,7 +321,7 @@ __global__ void __launch_bounds__(kBlock) k_lever(Params pr, double* T, double* 
   }
 }
 
-__global__ void __launch_bounds__(kBlock) k_equilibrate(Params pr, const double* __restrict__ T,
+__global__ void __launch_bounds__(kBlockA) k_equilibrate(Params pr, const double* __restrict__ T,
                                                         const double* __restrict__ C, double* gl, double* Cl,
                                                         double* Cs, double* Kinv, double* Ag, int n, int from_T,
                                                         int write_cl) {
@@ -346,30 +350,30 @@ cudaError_t launch_assemble_momentum(int comp, const Params& pr, const Sys& sys,
                                      const double* Kinv, cudaStream_t st) {
   const int g = grid_for(sys.d.n);
   if (comp == 0)
-    k_assemble_momentum<0><<<g, kBlock, 0, st>>>(pr, sys, vel[0], vel[1], vel[2], ustar, p, T, Cl, Kinv);
+    k_assemble_momentum<0><<<g, kBlockA, 0, st>>>(pr, sys, vel[0], vel[1], vel[2], ustar, p, T, Cl, Kinv);
   else if (comp == 1)
-    k_assemble_momentum<1><<<g, kBlock, 0, st>>>(pr, sys, vel[0], vel[1], vel[2], ustar, p, T, Cl, Kinv);
+    k_assemble_momentum<1><<<g, kBlockA, 0, st>>>(pr, sys, vel[0], vel[1], vel[2], ustar, p, T, Cl, Kinv);
   else
-    k_assemble_momentum<2><<<g, kBlock, 0, st>>>(pr, sys, vel[0], vel[1], vel[2], ustar, p, T, Cl, Kinv);
+    k_assemble_momentum<2><<<g, kBlockA, 0, st>>>(pr, sys, vel[0], vel[1], vel[2], ustar, p, T, Cl, Kinv);
   return cudaGetLastError();
 }
 
 cudaError_t launch_assemble_solute(const Params& pr, const Sys& sys, const double* const vel[3], const double* gl,
                                    const double* C, const double* Ag, cudaStream_t st) {
-  k_assemble_cells<true><<<grid_for(sys.d.n), kBlock, 0, st>>>(pr, sys, vel[0], vel[1], vel[2], C, gl, Ag);
+  k_assemble_cells<true><<<grid_for(sys.d.n), kBlockA, 0, st>>>(pr, sys, vel[0], vel[1], vel[2], C, gl, Ag);
   return cudaGetLastError();
 }
 
 cudaError_t launch_assemble_temperature(const Params& pr, const Sys& sys, const double* const vel[3],
                                         const double* T, cudaStream_t st) {
-  k_assemble_cells<false><<<grid_for(sys.d.n), kBlock, 0, st>>>(pr, sys, vel[0], vel[1], vel[2], T, nullptr,
+  k_assemble_cells<false><<<grid_for(sys.d.n), kBlockA, 0, st>>>(pr, sys, vel[0], vel[1], vel[2], T, nullptr,
                                                                  nullptr);
   return cudaGetLastError();
 }
 
 cudaError_t launch_poisson_rhs(const Params& pr, const double* const ustar[3], double* b, cudaStream_t st) {
   const long long n = (long long)pr.nx * pr.ny * pr.nz;
-  k_poisson_rhs<<<grid_for(n), kBlock, 0, st>>>(pr, ustar[0], ustar[1], ustar[2], b);
+  k_poisson_rhs<<<grid_for(n), kBlockA, 0, st>>>(pr, ustar[0], ustar[1], ustar[2], b);
   return cudaGetLastError();
 }
 
@@ -377,21 +381,21 @@ cudaError_t launch_project(const Params& pr, double* const vel[3], const double*
                            double* p, cudaStream_t st) {
   const long long nx = pr.nx, ny = pr.ny, nz = pr.nz;
   const long long total = (nx + 1) * ny * nz + nx * (ny + 1) * nz + (pr.dim == 3 ? nx * ny * (nz + 1) : 0) + nx * ny * nz;
-  k_project<<<grid_for(total), kBlock, 0, st>>>(pr, vel[0], vel[1], vel[2], ustar[0], ustar[1], ustar[2], pc, p);
+  k_project<<<grid_for(total), kBlockA, 0, st>>>(pr, vel[0], vel[1], vel[2], ustar[0], ustar[1], ustar[2], pc, p);
   return cudaGetLastError();
 }
 
 cudaError_t launch_lever(const Params& pr, double* T, double* gl, const double* C, double* Cl, double* Cs,
                          double* Kinv, double* Ag, cudaStream_t st) {
   const int n = pr.nx * pr.ny * pr.nz;
-  k_lever<<<grid_for(n), kBlock, 0, st>>>(pr, T, gl, C, Cl, Cs, Kinv, Ag, n);
+  k_lever<<<grid_for(n), kBlockA, 0, st>>>(pr, T, gl, C, Cl, Cs, Kinv, Ag, n);
   return cudaGetLastError();
 }
 
 cudaError_t launch_equilibrate(const Params& pr, const double* T, const double* C, double* gl, double* Cl,
                                double* Cs, double* Kinv, double* Ag, int from_T, int write_cl, cudaStream_t st) {
   const int n = pr.nx * pr.ny * pr.nz;
-  k_equilibrate<<<grid_for(n), kBlock, 0, st>>>(pr, T, C, gl, Cl, Cs, Kinv, Ag, n, from_T, write_cl);
+  k_equilibrate<<<grid_for(n), kBlockA, 0, st>>>(pr, T, C, gl, Cl, Cs, Kinv, Ag, n, from_T, write_cl);
   return cudaGetLastError();
 }
 

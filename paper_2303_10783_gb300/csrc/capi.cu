@@ -91,6 +91,9 @@ struct ss_case {
   std::vector<cudaEvent_t>* pool;
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>>* pending;
   long long launches[SS_NPROF];
+  // captured step graph
+  cudaGraphExec_t graph;
+  long long graph_kernels;   // library kernels per captured step
 };
 
 namespace {
@@ -371,6 +374,13 @@ ss_status one_step(ss_case* c) {
   return SS_OK;
 }
 
+void drop_graph(ss_case* c) {
+  if (c->graph) {
+    cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+  }
+}
+
 ss_status read_status(ss_case* c, DevStatus* host) {
   CUDA_TRY(cudaMemcpyAsync(host, c->st, sizeof(DevStatus), cudaMemcpyDeviceToHost, c->stream));
   CUDA_TRY(cudaStreamSynchronize(c->stream));
@@ -444,6 +454,7 @@ ss_status ss_create_case(const ss_grid* grid, void* workspace, size_t workspace_
 
 ss_status ss_set_alloy(ss_case* c, const ss_alloy* al) {
   STAGE_TRY(check_case(c));
+  drop_graph(c);
   if (!al) return fail(SS_EINVAL, "alloy is NULL");
   if (c->steps > 0) return fail(SS_ESTATE, "set_alloy after the first step");
   if (!(al->kp > 0 && al->kp < 1)) return fail(SS_EINVAL, "kp must be in (0, 1)");
@@ -465,6 +476,7 @@ ss_status ss_set_alloy(ss_case* c, const ss_alloy* al) {
 
 ss_status ss_set_boundary(ss_case* c, int face, const ss_bc* bc) {
   STAGE_TRY(check_case(c));
+  drop_graph(c);
   if (!bc) return fail(SS_EINVAL, "bc is NULL");
   if (face < 0 || face > 5) return fail(SS_EINVAL, "face must be 0..5");
   if (bc->thermal != SS_ADIABATIC && bc->thermal != SS_ROBIN) return fail(SS_EINVAL, "unknown thermal condition");
@@ -482,6 +494,46 @@ ss_status ss_step(ss_case* c, int n) {
     STAGE_TRY(one_step(c));
     c->steps++;
   }
+  return SS_OK;
+}
+
+ss_status ss_step_graph(ss_case* c, int n) {
+  STAGE_TRY(check_case(c));
+  if (n < 0) return fail(SS_EINVAL, "n must be >= 0");
+  if (!c->alloy_set) return fail(SS_ESTATE, "set_alloy before stepping");
+  if (c->stream == nullptr) return fail(SS_EINVAL, "graph steps need a non-default stream");
+  if (!c->graph) {
+    const int prof = c->profiling;
+    long long before = 0;
+    for (int q = 0; q < SS_NPROF; ++q) before += c->launches[q];
+    c->profiling = 0;
+    CUDA_TRY(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    ss_status s = one_step(c);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+    c->profiling = prof;
+    long long after = 0;
+    for (int q = 0; q < SS_NPROF; ++q) after += c->launches[q];
+    c->graph_kernels = after - before;
+    for (int q = 0; q < SS_NPROF; ++q) c->launches[q] = 0;   // capture launched nothing
+    c->launches[SS_PROF_SOLVE + SS_SYS_P] = 0;
+    if (s != SS_OK) {
+      if (g) cudaGraphDestroy(g);
+      return s;
+    }
+    if (e != cudaSuccess) return fail(SS_ECUDA, "step capture: %s", cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&c->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      c->graph = nullptr;
+      return fail(SS_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+    }
+  }
+  for (int q = 0; q < n; ++q) {
+    CUDA_TRY(cudaGraphLaunch(c->graph, c->stream));
+    c->steps++;
+  }
+  c->launches[SS_PROF_SOLVE + SS_SYS_P] += c->graph_kernels * n;   // counted under one stage
   return SS_OK;
 }
 
@@ -589,6 +641,7 @@ ss_status ss_destroy(ss_case* c) {
     cudaEventDestroy(pe.second.second);
   }
   for (auto ev : *c->pool) cudaEventDestroy(ev);
+  drop_graph(c);
   delete c->pool;
   delete c->pending;
   delete c;

@@ -74,6 +74,12 @@ __device__ void record(DevStatus* st, int idx, int iters, int refinements, bool 
   }
 }
 
+// float4 views for the FP32 streaming passes (every vector starts on a
+// 256-byte boundary); n4 = n / 4 items, then a scalar tail.
+__device__ __forceinline__ float4 ld4(const float* p, int m) { return reinterpret_cast<const float4*>(p)[m]; }
+__device__ __forceinline__ float4 ldg4(const float* p, int m) { return __ldg(reinterpret_cast<const float4*>(p) + m); }
+__device__ __forceinline__ void st4(float* p, int m, float4 v) { reinterpret_cast<float4*>(p)[m] = v; }
+
 struct CoreOut {
   int it;
   bool conv;
@@ -128,7 +134,23 @@ __device__ bool bcg_core(const Planes<T>& a, int n, int sy, int sz, int has_z, c
     ++it;
     const T beta = (T)((rho / rho_old) * (alpha / omega));
     const T om = (T)omega;
-    for (int i = t0; i < n; i += gs) {            // p = r + beta (p - omega v); y = M^-1 p
+    int tail = 0;                                 // p = r + beta (p - omega v); y = M^-1 p
+    if constexpr (sizeof(T) == 4) {
+      const int n4 = n >> 2;
+      for (int m = t0; m < n4; m += gs) {
+        const float4 rv = ld4(r, m), pv = ld4(p, m), vv = ld4(v, m), dv = ldg4(a.idiag, m);
+        float4 po, yo;
+        po.x = rv.x + beta * (pv.x - om * vv.x);
+        po.y = rv.y + beta * (pv.y - om * vv.y);
+        po.z = rv.z + beta * (pv.z - om * vv.z);
+        po.w = rv.w + beta * (pv.w - om * vv.w);
+        yo.x = dv.x * po.x; yo.y = dv.y * po.y; yo.z = dv.z * po.z; yo.w = dv.w * po.w;
+        st4(p, m, po);
+        st4(y, m, yo);
+      }
+      tail = n4 << 2;
+    }
+    for (int i = tail + t0; i < n; i += gs) {
       const T pi = r[i] + beta * (p[i] - om * v[i]);
       p[i] = pi;
       y[i] = __ldg(a.idiag + i) * pi;
@@ -145,7 +167,21 @@ __device__ bool bcg_core(const Planes<T>& a, int n, int sy, int sz, int has_z, c
     alpha = rho / o1.v[0];
     const T al = (T)alpha;
     T s2 = T(0);
-    for (int i = t0; i < n; i += gs) {            // s = r - alpha v (in r); z = M^-1 s
+    tail = 0;                                     // s = r - alpha v (in r); z = M^-1 s
+    if constexpr (sizeof(T) == 4) {
+      const int n4 = n >> 2;
+      for (int m = t0; m < n4; m += gs) {
+        const float4 rv = ld4(r, m), vv = ld4(v, m), dv = ldg4(a.idiag, m);
+        float4 so, zo;
+        so.x = rv.x - al * vv.x; so.y = rv.y - al * vv.y; so.z = rv.z - al * vv.z; so.w = rv.w - al * vv.w;
+        zo.x = dv.x * so.x; zo.y = dv.y * so.y; zo.z = dv.z * so.z; zo.w = dv.w * so.w;
+        st4(r, m, so);
+        st4(z, m, zo);
+        s2 += (so.x * so.x + so.y * so.y) + (so.z * so.z + so.w * so.w);
+      }
+      tail = n4 << 2;
+    }
+    for (int i = tail + t0; i < n; i += gs) {
       const T si = r[i] - al * v[i];
       r[i] = si;
       z[i] = __ldg(a.idiag + i) * si;
@@ -171,7 +207,23 @@ __device__ bool bcg_core(const Planes<T>& a, int n, int sy, int sz, int has_z, c
     omega = (o3.v[1] > 0.0) ? o3.v[0] / o3.v[1] : 0.0;
     const T omn = (T)omega;
     T s5 = T(0), s6 = T(0);
-    for (int i = t0; i < n; i += gs) {            // x += alpha y + omega z; r = s - omega t
+    tail = 0;                                     // x += alpha y + omega z; r = s - omega t
+    if constexpr (sizeof(T) == 4) {
+      const int n4 = n >> 2;
+      for (int m = t0; m < n4; m += gs) {
+        const float4 xv = ld4(x, m), yv = ld4(y, m), zv = ld4(z, m), rv = ld4(r, m), tv = ld4(t, m), hv = ld4(rh, m);
+        float4 xo, ro;
+        xo.x = xv.x + al * yv.x + omn * zv.x; xo.y = xv.y + al * yv.y + omn * zv.y;
+        xo.z = xv.z + al * yv.z + omn * zv.z; xo.w = xv.w + al * yv.w + omn * zv.w;
+        ro.x = rv.x - omn * tv.x; ro.y = rv.y - omn * tv.y; ro.z = rv.z - omn * tv.z; ro.w = rv.w - omn * tv.w;
+        st4(x, m, xo);
+        st4(r, m, ro);
+        s5 += (hv.x * ro.x + hv.y * ro.y) + (hv.z * ro.z + hv.w * ro.w);
+        s6 += (ro.x * ro.x + ro.y * ro.y) + (ro.z * ro.z + ro.w * ro.w);
+      }
+      tail = n4 << 2;
+    }
+    for (int i = tail + t0; i < n; i += gs) {
       x[i] += al * y[i] + omn * z[i];
       const T ri = r[i] - omn * t[i];
       r[i] = ri;
@@ -192,7 +244,7 @@ __device__ bool bcg_core(const Planes<T>& a, int n, int sy, int sz, int has_z, c
   return true;
 }
 
-__global__ void __launch_bounds__(kBlock, 4) k_bicgstab(BcgArgs A) {
+__global__ void __launch_bounds__(kBlock, 2) k_bicgstab(BcgArgs A) {
   unsigned int epoch = 0;
   const int n = (int)A.sys.d.n;
   const int sy = A.sys.d.mx, sz = A.sys.d.mx * A.sys.d.my;
@@ -211,7 +263,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_bicgstab(BcgArgs A) {
 constexpr double kInnerTol = 1.0e-5;
 constexpr int kMaxRefine = 12;
 
-__global__ void __launch_bounds__(kBlock, 4) k_bicgstab_ir(BcgArgs A) {
+__global__ void __launch_bounds__(kBlock, 2) k_bicgstab_ir(BcgArgs A) {
   unsigned int epoch = 0;
   const int n = (int)A.sys.d.n;
   const int sy = A.sys.d.mx, sz = A.sys.d.mx * A.sys.d.my;
@@ -296,7 +348,7 @@ __device__ __forceinline__ int nb_code(const PcgArgs& A, int i, int j, int k) {
   return cx + 3 * cy + 9 * cz;
 }
 
-__global__ void __launch_bounds__(kBlock, 4) k_pcg_poisson(PcgArgs A) {
+__global__ void __launch_bounds__(kBlock, 2) k_pcg_poisson(PcgArgs A) {
   __shared__ double s_diag[27], s_minv[27];
   if (threadIdx.x < 27) {
     const int c = threadIdx.x;

@@ -45,6 +45,8 @@ struct Level {
   TP *b, *x, *t, *r;       // rhs, iterate, alternate iterate, residual
   int local;               // run by block 0 alone (from shared memory)
   int soff;                // offset (elements) of the level's four arrays in shared memory
+  int v4;                  // nx % 4 == 0: FP32 passes take 4 consecutive cells per thread
+  FastDiv fx4;             // division by nx / 4
 };
 
 template <typename TP>
@@ -135,9 +137,90 @@ __device__ __forceinline__ T apply_nb(const Nb<T>& q, T ax, T ay, T az, T diag) 
   return acc;
 }
 
+// ---- 4-cells-per-thread FP32 passes (levels with nx % 4 == 0; vectors start
+// on 256-byte boundaries, so item m's float4 at 4m is aligned, and so are the
+// float4 at 4m +- nx and 4m +- nx*ny)
+__device__ __forceinline__ float4 ld4(const float* p, int c) { return *reinterpret_cast<const float4*>(p + c); }
+__device__ __forceinline__ void st4(float* p, int c, float4 v) { *reinterpret_cast<float4*>(p + c) = v; }
+__device__ __forceinline__ float comp(const float4& v, int l) { return l == 0 ? v.x : l == 1 ? v.y : l == 2 ? v.z : v.w; }
+
+struct Item4 {
+  int c, i0, j, k;
+};
+
+template <typename TP>
+__device__ __forceinline__ Item4 item4(const Level<TP>& L, int m) {
+  Item4 it;
+  const int t = fdiv(m, L.fx4);
+  it.i0 = (m - t * (int)L.fx4.d) * 4;
+  it.k = fdiv(t, L.fy);
+  it.j = t - it.k * (int)L.fy.d;
+  it.c = 4 * m;
+  return it;
+}
+
+// lane codes of 4 consecutive cells: the y/z part is shared, the x part differs only at the walls
+template <typename TP>
+__device__ __forceinline__ void codes4(const Level<TP>& L, const Item4& it, int code[4]) {
+  const int yz = 3 * ((it.j > 0) + (it.j < L.ny - 1)) + 9 * ((it.k > 0) + (it.k < L.nz - 1));
+#pragma unroll
+  for (int l = 0; l < 4; ++l) {
+    const int i = it.i0 + l;
+    code[l] = yz + (i > 0) + (i < L.nx - 1);
+  }
+}
+
+// A v for 4 consecutive cells (coefficients ax, ay, az; diagonal table dg)
+__device__ __forceinline__ void lap4(const float* v, const Item4& it, int nx, int ny, int nz, float ax, float ay,
+                                     float az, const float* dg, const int code[4], float in[4], float Av[4]) {
+  const int c = it.c, sz = nx * ny;
+  const float4 c4 = ld4(v, c);
+  const float W = it.i0 > 0 ? v[c - 1] : 0.f, E = it.i0 + 4 < nx ? v[c + 4] : 0.f;
+  const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  const float4 S = it.j > 0 ? ld4(v, c - nx) : z4, N = it.j < ny - 1 ? ld4(v, c + nx) : z4;
+  const float4 B = (nz > 1 && it.k > 0) ? ld4(v, c - sz) : z4, T = (nz > 1 && it.k < nz - 1) ? ld4(v, c + sz) : z4;
+  in[0] = c4.x; in[1] = c4.y; in[2] = c4.z; in[3] = c4.w;
+  const float sx[4] = {W + c4.y, c4.x + c4.z, c4.y + c4.w, c4.z + E};
+#pragma unroll
+  for (int l = 0; l < 4; ++l) {
+    float acc = dg[code[l]] * in[l];
+    acc = fmaf(-ax, sx[l], acc);
+    acc = fmaf(-ay, comp(S, l) + comp(N, l), acc);
+    acc = fmaf(-az, comp(B, l) + comp(T, l), acc);
+    Av[l] = acc;
+  }
+}
+
+template <typename TP, bool RESIDUAL>
+__device__ void sweep4(const Level<TP>& L, const Tables<TP>& tb, int l, const float* in, float* out, Range rg) {
+  const int n4 = L.n >> 2;
+  for (int m = rg.begin; m < n4; m += rg.stride) {
+    const Item4 it = item4(L, m);
+    int code[4];
+    codes4(L, it, code);
+    float vin[4], Av[4];
+    lap4(in, it, L.nx, L.ny, L.nz, (float)L.ax, (float)L.ay, (float)L.az, (const float*)tb.diag[l], code, vin, Av);
+    const float4 b4 = ld4((const float*)L.b, it.c);
+    const float bb[4] = {b4.x, b4.y, b4.z, b4.w};
+    float o[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float res = bb[q] - Av[q];
+      o[q] = RESIDUAL ? res : vin[q] + (float)tb.wid[l][code[q]] * res;
+    }
+    st4(RESIDUAL ? (float*)L.r : out, it.c, make_float4(o[0], o[1], o[2], o[3]));
+  }
+}
+
 // out = in + omega D^-1 (b - A in)      (residual_only: L.r = b - A in)
 template <typename TP, bool RESIDUAL>
 __device__ void sweep(const Level<TP>& L, const Tables<TP>& tb, int l, const TP* in, TP* out, Range rg) {
+  if constexpr (sizeof(TP) == 4) {
+    if (L.v4) {
+      sweep4<TP, RESIDUAL>(L, tb, l, (const float*)in, (float*)out, rg);
+      return;
+    }
+  }
   constexpr int U = Batch<TP>::U;
   for (int base = rg.begin; base < L.n; base += U * rg.stride) {
     Nb<TP> q[U];
@@ -375,6 +458,36 @@ __device__ __noinline__ bool vcycle(const Ctx& X, const Level<TP>* glev, const L
   return up(glev, tb, top - 1, 0, grid_rg, gs);
 }
 
+// Sums (r.z, r.r, sum z, sum r) over this thread's rows of z = lev[0].t. The
+// rows are taken with the same thread-to-cell mapping as the level-0 sweep
+// that wrote z (4 cells per thread on float4 levels), so no barrier is needed
+// between that sweep and this pass.
+template <typename TV, typename TP>
+__device__ __forceinline__ void zr_sums(const Level<TP>& L0, const TV* r, int t0, int gsz, TV& a0, TV& a1, TV& a2,
+                                        TV& a3) {
+  const int n = L0.n;
+  int begin = t0;
+  if constexpr (sizeof(TV) == 4 && sizeof(TP) == 4) {
+    if (L0.v4) {
+      for (int m = t0; m < (n >> 2); m += gsz) {
+        const float4 zv = ld4((const float*)L0.t, 4 * m), rv = ld4((const float*)r, 4 * m);
+        a0 += (rv.x * zv.x + rv.y * zv.y) + (rv.z * zv.z + rv.w * zv.w);
+        a1 += (rv.x * rv.x + rv.y * rv.y) + (rv.z * rv.z + rv.w * rv.w);
+        a2 += (zv.x + zv.y) + (zv.z + zv.w);
+        a3 += (rv.x + rv.y) + (rv.z + rv.w);
+      }
+      begin = n;
+    }
+  }
+  for (int c = begin; c < n; c += gsz) {
+    const TV zc = (TV)L0.t[c], rc = r[c];
+    a0 += rc * zc;
+    a1 += rc * rc;
+    a2 += zc;
+    a3 += rc;
+  }
+}
+
 struct PcgOut {
   int it;
   bool conv;
@@ -407,13 +520,7 @@ __device__ __noinline__ bool pcg(const Ctx& X, const Level<TP>* glev, const Leve
   }
   if (!vcycle(X, glev, slev, tb, epoch)) return false;
   TV a0 = TV(0), a1 = TV(0), a2 = TV(0), a3 = TV(0);
-  for (int c = t0; c < n; c += gsz) {
-    const TV zc = (TV)L0.t[c], rc = r[c];
-    a0 += rc * zc;
-    a1 += rc * rc;
-    a2 += zc;
-    a3 += rc;
-  }
+  zr_sums(L0, r, t0, gsz, a0, a1, a2, a3);
   Vec<4> o0, s0 = {{(double)a0, (double)a1, (double)a2, (double)a3}};
   if (!grid_sum<4>(s0, X.partial, X.max_blocks, 0, X.st, epoch, o0)) return false;
   const double inv_n = 1.0 / (double)n;
@@ -428,7 +535,21 @@ __device__ __noinline__ bool pcg(const Ctx& X, const Level<TP>* glev, const Leve
   while (!conv && it < max_it && isfinite(res)) {
     ++it;
     TV s1 = TV(0);
-    for (int base = t0; base < n; base += U * gsz) {   // q = A p
+    const bool v4 = (sizeof(TV) == 4) && L0.v4;
+    if constexpr (sizeof(TV) == 4) {
+      if (v4) {
+        for (int m = t0; m < (n >> 2); m += gsz) {    // q = A p, 4 cells per thread
+          const Item4 itm = item4(L0, m);
+          int code[4];
+          codes4(L0, itm, code);
+          float pin[4], qv[4];
+          lap4((const float*)p, itm, nx, ny, nz, (float)cx, (float)cy, (float)cz, (const float*)dg, code, pin, qv);
+          st4((float*)q, itm.c, make_float4(qv[0], qv[1], qv[2], qv[3]));
+          s1 += (pin[0] * qv[0] + pin[1] * qv[1]) + (pin[2] * qv[2] + pin[3] * qv[3]);
+        }
+      }
+    }
+    for (int base = v4 ? n : t0; base < n; base += U * gsz) {   // q = A p
       Nb<TV> nb[U];
       int code[U];
 #pragma unroll
@@ -454,7 +575,27 @@ __device__ __noinline__ bool pcg(const Ctx& X, const Level<TP>* glev, const Leve
     Vec<1> o1, d1 = {{(double)s1}};
     if (!grid_sum<1>(d1, X.partial, X.max_blocks, 4, X.st, epoch, o1)) return false;
     const TV alpha = (TV)(rz / o1.v[0]);
-    for (int base = t0; base < n; base += U * gsz) {   // x += alpha p; r -= alpha q; first V-cycle sweep
+    if constexpr (sizeof(TV) == 4) {
+      if (v4) {
+        for (int m = t0; m < (n >> 2); m += gsz) {    // x += alpha p; r -= alpha q; first V-cycle sweep
+          const Item4 itm = item4(L0, m);
+          int code[4];
+          codes4(L0, itm, code);
+          const float4 pv = ld4((const float*)p, itm.c), qv = ld4((const float*)q, itm.c);
+          const float4 xv = ld4((const float*)x, itm.c), rv = ld4((const float*)r, itm.c);
+          float4 xo, ro, x0;
+          xo.x = xv.x + alpha * pv.x; xo.y = xv.y + alpha * pv.y; xo.z = xv.z + alpha * pv.z; xo.w = xv.w + alpha * pv.w;
+          ro.x = rv.x - alpha * qv.x; ro.y = rv.y - alpha * qv.y; ro.z = rv.z - alpha * qv.z; ro.w = rv.w - alpha * qv.w;
+          x0.x = (float)tb.wid[0][code[0]] * ro.x; x0.y = (float)tb.wid[0][code[1]] * ro.y;
+          x0.z = (float)tb.wid[0][code[2]] * ro.z; x0.w = (float)tb.wid[0][code[3]] * ro.w;
+          st4((float*)x, itm.c, xo);
+          st4((float*)r, itm.c, ro);
+          st4((float*)L0.b, itm.c, ro);
+          st4((float*)L0.x, itm.c, x0);
+        }
+      }
+    }
+    for (int base = v4 ? n : t0; base < n; base += U * gsz) {   // x += alpha p; r -= alpha q; first V-cycle sweep
       TV pv[U], qv[U], xv[U], rv[U];
 #pragma unroll
       for (int u = 0; u < U; ++u) {
@@ -482,22 +623,7 @@ __device__ __noinline__ bool pcg(const Ctx& X, const Level<TP>* glev, const Leve
     }
     if (!vcycle(X, glev, slev, tb, epoch)) return false;
     TV s2 = TV(0), s3 = TV(0), s4 = TV(0), s5 = TV(0);
-    for (int base = t0; base < n; base += U * gsz) {
-      TV zv[U], rv[U];
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const int c = base + u * gsz;
-        zv[u] = c < n ? (TV)L0.t[c] : TV(0);
-        rv[u] = c < n ? r[c] : TV(0);
-      }
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        s2 += rv[u] * zv[u];
-        s3 += rv[u] * rv[u];
-        s4 += zv[u];
-        s5 += rv[u];
-      }
-    }
+    zr_sums(L0, r, t0, gsz, s2, s3, s4, s5);
     Vec<4> o2, d2 = {{(double)s2, (double)s3, (double)s4, (double)s5}};
     if (!grid_sum<4>(d2, X.partial, X.max_blocks, 8, X.st, epoch, o2)) return false;
     res = sqrt(o2.v[1]);
@@ -508,7 +634,18 @@ __device__ __noinline__ bool pcg(const Ctx& X, const Level<TP>* glev, const Leve
     const TV beta = (TV)(rz_new / rz);
     const TV mzt = (TV)mz;
     rz = rz_new;
-    for (int base = t0; base < n; base += U * gsz) {
+    if constexpr (sizeof(TV) == 4) {
+      if (v4) {
+        for (int m = t0; m < (n >> 2); m += gsz) {
+          const float4 zv = ld4((const float*)L0.t, 4 * m), pv = ld4((const float*)p, 4 * m);
+          float4 po;
+          po.x = (zv.x - mzt) + beta * pv.x; po.y = (zv.y - mzt) + beta * pv.y;
+          po.z = (zv.z - mzt) + beta * pv.z; po.w = (zv.w - mzt) + beta * pv.w;
+          st4((float*)p, 4 * m, po);
+        }
+      }
+    }
+    for (int base = v4 ? n : t0; base < n; base += U * gsz) {
       TV zv[U], pv[U];
 #pragma unroll
       for (int u = 0; u < U; ++u) {
@@ -533,7 +670,7 @@ __device__ __noinline__ bool pcg(const Ctx& X, const Level<TP>* glev, const Leve
 }
 
 template <typename TP>
-__global__ void __launch_bounds__(kBlock, 2) k_pcg_mg(MGArgs<TP> A) {
+__global__ void __launch_bounds__(kBlock, 1) k_pcg_mg(MGArgs<TP> A) {
   extern __shared__ __align__(16) unsigned char dsm[];
   __shared__ Tables<TP> tb;
   __shared__ Level<TP> glev[kMaxLevels];
@@ -675,6 +812,8 @@ MGArgs<TP> make_args(const MGPlan& pl, const Params& pr, double* b, double* x, c
     L.az = pr.dim == 3 ? (TP)(1.0 / (pl.h[l][2] * pl.h[l][2])) : TP(0);
     L.b = (TP*)pl.vec[l][0]; L.x = (TP*)pl.vec[l][1]; L.t = (TP*)pl.vec[l][2]; L.r = (TP*)pl.vec[l][3];
     L.local = pl.local[l];
+    L.v4 = (sizeof(TP) == 4) && (L.nx % 4 == 0);
+    L.fx4 = make_fastdiv(L.nx >= 4 ? L.nx / 4 : 1);
     if (L.local && A.G == pl.nl) A.G = l;
     if (l >= A.G) {
       L.soff = (int)(smem / sizeof(TP));

@@ -18,7 +18,7 @@
 
 namespace solid {
 
-constexpr int kBlock = 256;              // threads per block of every kernel
+constexpr int kBlock = 512;              // threads per block of every kernel
 constexpr int kMaxRedSlots = 16;         // reduction slots (one per reduction site)
 constexpr long long kSpinLimit = 1LL << 21;  // grid-barrier polls before giving up (about a second)
 

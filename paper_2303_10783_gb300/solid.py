@@ -74,6 +74,7 @@ def _declare(lib):
         "ss_set_alloy": [P, ctypes.POINTER(Alloy)],
         "ss_set_boundary": [P, ctypes.c_int, ctypes.POINTER(BC)],
         "ss_step": [P, ctypes.c_int],
+        "ss_step_graph": [P, ctypes.c_int],
         "ss_sync": [P],
         "ss_get_fields": [P, ctypes.c_uint, ctypes.POINTER(P), ctypes.c_int],
         "ss_set_fields": [P, ctypes.c_uint, ctypes.POINTER(P), ctypes.c_int],
@@ -176,6 +177,9 @@ class Case:
 
     def step(self, n=1):
         check(self.lib.ss_step(self.h, n))
+
+    def step_graph(self, n=1):
+        check(self.lib.ss_step_graph(self.h, n))
 
     def sync(self, allow=()):
         return check(self.lib.ss_sync(self.h), allow)

@@ -1,0 +1,82 @@
+"""Graph-replayed steps, batches of independent cases, and the
+continuous-batching server: each must give the same fields as the plain
+single-case path (bit for bit: the kernels are deterministic and cases
+share no data), and the server must respect its HBM budget."""
+import numpy as np
+import pytest
+
+from paper_2303_10783_gb300 import cases, solid
+from paper_2303_10783_gb300.batch import Batch
+from paper_2303_10783_gb300.serve import Server
+
+pytestmark = pytest.mark.gpu
+
+
+def _alone(case, nsteps, precision=solid.SS_MIXED, graph=False):
+    import torch
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        c = solid.Case(case, precision=precision, stream=stream)
+        f = cases.initial_fields(case)
+        c.initialize(f["T"], f["C"])
+        for _ in range(nsteps):
+            if graph:
+                c.step_graph(1)
+            else:
+                c.step(1)
+        c.sync()
+        out = c.get_fields()
+        c.close()
+    return out
+
+
+def _same(a, b):
+    return all(np.array_equal(a[k], b[k]) for k in a)
+
+
+@pytest.mark.parametrize("prec", [solid.SS_FP64, solid.SS_MIXED], ids=["fp64", "mixed"])
+def test_graph_step_equals_plain_step(lib, prec):
+    case = cases.box_3d(24, 16, 12)
+    assert _same(_alone(case, 6, prec, graph=True), _alone(case, 6, prec, graph=False))
+
+
+def test_batch_member_equals_alone(lib):
+    cs = [cases.cavity_2d(64, 40), cases.box_3d(32, 24, 16), cases.cavity_2d(48, 32, seed=5),
+          cases.box_3d(16, 16, 16, seed=7)]
+    b = Batch(cs, precision=solid.SS_MIXED)
+    b.step(8)
+    assert b.sync() == solid.SS_OK
+    for q, cd in enumerate(cs):
+        assert _same(b.fields(q), _alone(cd, 8)), q
+    b.close()
+
+
+def test_batched_workload_cases_are_valid():
+    cs = cases.batch_cases(64)
+    assert len(cs) == 64 and {c["dim"] for c in cs} == {2, 3}
+    for c in cs:
+        assert 0.5 <= c["lx"] / c["ly"] <= 2.5 and 2.0 <= c["alloy"]["C0"] <= 15.0
+
+
+def test_server_budget_and_isolation(lib):
+    reqs = cases.serving_requests(n=6, rate=1000.0, seed=9, steps=20, grids=((16, 16, 16), (24, 16, 16)))
+    one = solid.workspace_bytes(reqs[0][1], solid.SS_MIXED)
+    big = max(solid.workspace_bytes(c, solid.SS_MIXED) for _, c in reqs)
+    srv = Server(budget_bytes=int(2.5 * big), chunk=5, keep_results=True)
+    rep = srv.run(reqs)
+    # the budget binds (not all six run at once) and is never exceeded
+    assert rep["requests"] == 6 and rep["max_active"] < 6 and rep["max_used_bytes"] <= rep["budget_bytes"]
+    assert rep["max_active"] <= rep["budget_bytes"] // min(solid.workspace_bytes(c, solid.SS_MIXED) for _, c in reqs)
+    assert rep["p50_ms_per_100_steps"] > 0 and rep["p99_ms_per_100_steps"] >= rep["p50_ms_per_100_steps"]
+    # results are the same alone and in the mix
+    for q in (0, 3):
+        assert _same(rep["results"][q], _alone(reqs[q][1], 20)), q
+    assert one > 0
+
+
+@pytest.mark.parametrize("prec", [solid.SS_FP64, solid.SS_MIXED], ids=["fp64", "mixed"])
+@pytest.mark.parametrize("dims", [(24, 16, 12), (64, 48, 48)])
+def test_steps_are_bit_reproducible(lib, prec, dims):
+    """Deterministic reductions and race-free phases: two runs agree bit for bit."""
+    case = cases.box_3d(*dims)
+    assert _same(_alone(case, 4, prec), _alone(case, 4, prec))
