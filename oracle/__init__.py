@@ -26,7 +26,7 @@ itself is "parity unpinned" at those sizes.
 """
 from .scheme import (Grid, State, initial_state, step, run, assemble_momentum, assemble_solute,
                      assemble_temperature, assemble_scalar, poisson_matrix, poisson_rhs, project,
-                     lever_update, inverse_permeability, liquidus, equilibrium_fraction,
+                     lever_update, inverse_permeability, liquidus, equilibrium_fraction, thermal_walls,
                      divergence, sparse_from_planes, PLANES)
 from .forward import forward_assemble
 from .solve import solve_system, solve_poisson
@@ -34,6 +34,6 @@ from .solve import solve_system, solve_poisson
 __all__ = [
     "Grid", "State", "initial_state", "step", "run", "assemble_momentum", "assemble_solute",
     "assemble_temperature", "assemble_scalar", "poisson_matrix", "poisson_rhs", "project",
-    "lever_update", "inverse_permeability", "liquidus", "equilibrium_fraction", "divergence",
+    "lever_update", "inverse_permeability", "liquidus", "equilibrium_fraction", "thermal_walls", "divergence",
     "sparse_from_planes", "PLANES", "forward_assemble", "solve_system", "solve_poisson",
 ]

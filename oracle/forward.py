@@ -38,6 +38,11 @@ def _add(idx, e, s=1):
     return (idx[0] + s * e[0], idx[1] + s * e[1], idx[2] + s * e[2])
 
 
+def _slip_wall(case, a, side):
+    names = {("x-"): (0, 0), "x+": (0, 1), "y-": (1, 0), "y+": (1, 1), "z-": (2, 0), "z+": (2, 1)}
+    return any(names[f] == (a, side) for f in case.get("slip", ()))
+
+
 def _upwind_flux(F, phi_back, phi_front):
     """(Phi F) on a face with Phi_back behind and Phi_front in front (Eq. 3.29)."""
     return (phi_back if F >= 0.0 else phi_front) * F
@@ -78,9 +83,12 @@ def momentum_eq(grid, st, case, a, phi):
                     else:
                         Uf = 0.5 * (_get(st.vel[d], *_add(c_lo, ed)) + _get(st.vel[d], *_add(c_hi, ed)))
                         Ub = 0.5 * (_get(st.vel[d], *c_lo) + _get(st.vel[d], *c_hi))
-                        # no-slip ghost beyond a wall: minus the interior value
-                        Pf = _get(phi, *_add(idx, ed)) if idx[d] + 1 <= n[d] - 1 else -P
-                        Pb = _get(phi, *_add(idx, ed, -1)) if idx[d] - 1 >= 0 else -P
+                        # ghost beyond a wall: minus the interior value (no-slip) or
+                        # the interior value itself (free-slip)
+                        gf = P if _slip_wall(case, d, 1) else -P
+                        gb = P if _slip_wall(case, d, 0) else -P
+                        Pf = _get(phi, *_add(idx, ed)) if idx[d] + 1 <= n[d] - 1 else gf
+                        Pb = _get(phi, *_add(idx, ed, -1)) if idx[d] - 1 >= 0 else gb
                     r += (_upwind_flux(Uf, P, Pf) - _upwind_flux(Ub, Pb, P)) / h
                     r -= nu * ((Pf - P) - (P - Pb)) / h ** 2
                 r += nu * 0.5 * (_get(Kinv, *c_lo) + _get(Kinv, *c_hi)) * P
@@ -140,13 +148,26 @@ def solute_eq(grid, vel, gl_n, C_n, case, C):
     return _cell_eq(grid, vel, C, C_n, case["dt"], D, to_cl, [])
 
 
-def temperature_eq(grid, vel, T_n, case, T):
-    """Eq(T*) of the first energy step (Eq. 3.12) with Robin walls."""
-    from .scheme import _robin_faces, robin_conductance
+def temperature_eq(grid, vel, T_n, case, T, t=None):
+    """Eq(T*) of the first energy step (Eq. 3.12) with its cooled walls: the
+    wall flux is written from the wall's own definition (film plus half cell
+    for Robin, the half cell to the prescribed wall temperature for Dirichlet)."""
     al = case["alloy"]
-    alpha = al["k"] / (al["rho"] * al["cp"])
-    robin = [(a, s, robin_conductance(case, a, hc, grid) / (al["rho"] * al["cp"] * grid.h[a]), Text)
-             for a, s, hc, Text in _robin_faces(case)]
+    k = al["k"]
+    t = case["dt"] if t is None else t
+    alpha = k / (al["rho"] * al["cp"])
+    names = {"x-": (0, 0), "x+": (0, 1), "y-": (1, 0), "y+": (1, 1), "z-": (2, 0), "z+": (2, 1)}
+    robin = []
+    for face, (hc, Text) in case.get("robin", {}).items():
+        a, s = names[face]
+        if a < grid.dim:
+            dx = grid.h[a]
+            robin.append((a, s, 1.0 / ((1.0 / hc + dx / (2.0 * k)) * al["rho"] * al["cp"] * dx), Text))
+    for face, (Tw0, rate) in case.get("dirichlet", {}).items():
+        a, s = names[face]
+        if a < grid.dim:
+            dx = grid.h[a]
+            robin.append((a, s, k / (0.5 * dx) / (al["rho"] * al["cp"] * dx), Tw0 + rate * t))
     return _cell_eq(grid, vel, T, T_n, case["dt"], lambda a, lo, hi: alpha, lambda t: t, robin)
 
 
@@ -189,8 +210,8 @@ def forward_solute(grid, vel, gl_n, C_n, case):
     return forward_assemble(grid, lambda c: solute_eq(grid, vel, gl_n, C_n, case, c), grid.cells)
 
 
-def forward_temperature(grid, vel, T_n, case):
-    return forward_assemble(grid, lambda t: temperature_eq(grid, vel, T_n, case, t), grid.cells)
+def forward_temperature(grid, vel, T_n, case, t=None):
+    return forward_assemble(grid, lambda T: temperature_eq(grid, vel, T_n, case, T, t), grid.cells)
 
 
 def forward_poisson(grid):

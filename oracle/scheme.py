@@ -39,7 +39,9 @@ Readings of points the paper leaves open (each restated in the design doc):
   constant hydrostatic term, which the pressure absorbs);
 * the permeability is K = K0 g^3/(1-g)^2 (Eq. 2.8 with K0 in place of
   lambda_2^2/180) and K^{-1} = (1-g)^2 / (K0 (g^3 + eps));
-* Robin cooling: wall heat flux U (T_P - T_ext) with U = 1/(1/h + dx/(2k));
+* cooled walls: heat flux U (T_P - T_ext) with U = 1/(1/h + dx/(2k)) for a
+  Robin wall and U = 2k/dx with T_ext = T_w(t^{n+1}) for a Dirichlet wall;
+* free-slip walls (Example 2) use the ghost +u_P: no shear on the wall;
 * the larger root of Eq. 3.16, clamped to [0, 1]; the eutectic plateau holds
   T = T_e while liquid remains (Sec. 3 after Eq. 3.17, Table 1);
 * pressure-correction gauge: the right-hand side of Eq. 3.4 has its mean
@@ -116,7 +118,8 @@ class State:
 
     FIELDS = ("u", "v", "w", "p", "T", "C", "gl", "Cl", "Cs")
 
-    def __init__(self, vel, p, T, C, gl, Cl, Cs):
+    def __init__(self, vel, p, T, C, gl, Cl, Cs, t=0.0):
+        self.t = float(t)
         self.vel = [np.array(v, dtype=np.float64) for v in vel]
         self.p, self.T, self.C = (np.array(x, dtype=np.float64) for x in (p, T, C))
         self.gl, self.Cl, self.Cs = (np.array(x, dtype=np.float64) for x in (gl, Cl, Cs))
@@ -129,7 +132,7 @@ class State:
         return {k: getattr(self, k) for k in self.FIELDS}
 
     def copy(self):
-        return State(self.vel, self.p, self.T, self.C, self.gl, self.Cl, self.Cs)
+        return State(self.vel, self.p, self.T, self.C, self.gl, self.Cl, self.Cs, self.t)
 
 
 # ----------------------------------------------------------------- model relations
@@ -244,8 +247,12 @@ def assemble_momentum(grid, st, case, a, Kinv=None):
             j = _index(shape, d)
             has[(d, 0)] = j >= 1
             has[(d, 1)] = j <= nd - 2
-            D[(d, 0)] = np.where(j >= 1, nu, 2.0 * nu)
-            D[(d, 1)] = np.where(j <= nd - 2, nu, 2.0 * nu)
+            # beyond a wall the ghost is -u_P (no-slip: 2 nu/h^2 on the diagonal)
+            # or +u_P (free-slip: no shear, nothing on the diagonal)
+            wb = 0.0 if _slip(case, d, 0) else 2.0 * nu
+            wf = 0.0 if _slip(case, d, 1) else 2.0 * nu
+            D[(d, 0)] = np.where(j >= 1, nu, wb)
+            D[(d, 1)] = np.where(j <= nd - 2, nu, wf)
     P, nb = conv_diff_coeffs(shape, grid.dim, grid.h, F, D, has)
     Kp = _pad(Kinv, a)
     Kface = 0.5 * (_sl(Kp, a, 0, na + 1) + _sl(Kp, a, 1, na + 2))
@@ -306,27 +313,40 @@ def assemble_solute(grid, vel, gl_n, C_n, case):
     return out
 
 
-def _robin_faces(case):
-    """[(axis, side, h, T_ext)] for each Robin-cooled wall."""
-    names = {"x-": (0, 0), "x+": (0, 1), "y-": (1, 0), "y+": (1, 1), "z-": (2, 0), "z+": (2, 1)}
+_FACE = {"x-": (0, 0), "x+": (0, 1), "y-": (1, 0), "y+": (1, 1), "z-": (2, 0), "z+": (2, 1)}
+
+
+def _slip(case, a, s):
+    """True if the wall on side s of axis a is free-slip."""
+    return any(_FACE[f] == (a, s) for f in case.get("slip", ()))
+
+
+def thermal_walls(case, grid, t):
+    """[(axis, side, U, T_ext)] for every cooled wall at time t: a Robin wall
+    has U = 1/(1/h + dx/(2k)) (film and half cell in series) and a fixed T_ext;
+    a Dirichlet wall has U = 2k/dx (the half cell alone) and the wall
+    temperature T_w(t) = T_w0 + rate t (Example 2's linear cooling)."""
+    k = case["alloy"]["k"]
     out = []
-    for face, (hc, Text) in case["robin"].items():
-        a, s = names[face]
-        if a < int(case["dim"]):
-            out.append((a, s, float(hc), float(Text)))
+    for face, (hc, Text) in case.get("robin", {}).items():
+        a, s = _FACE[face]
+        if a < grid.dim:
+            out.append((a, s, 1.0 / (1.0 / hc + grid.h[a] / (2.0 * k)), float(Text)))
+    for face, (Tw0, rate) in case.get("dirichlet", {}).items():
+        a, s = _FACE[face]
+        if a < grid.dim:
+            out.append((a, s, 2.0 * k / grid.h[a], float(Tw0) + float(rate) * t))
     return out
 
 
-def robin_conductance(case, a, hc, grid):
-    """Series conductance of the wall film and the half cell: U = 1/(1/h + dx/(2k))."""
-    return 1.0 / (1.0 / hc + grid.h[a] / (2.0 * case["alloy"]["k"]))
-
-
-def assemble_temperature(grid, vel, T_n, case, source=None):
+def assemble_temperature(grid, vel, T_n, case, source=None, t=None):
     """First energy split step (Eq. 3.12): (T* - T^n)/dt + div(u^{n+1} T*) =
-    div(k/(rho c_p) grad T*), with Robin cooling on the listed walls and
-    zero flux elsewhere. ``source`` (optional, per cell) is the S_Phi of
-    Eq. 3.26, used only by manufactured-solution tests."""
+    div(k/(rho c_p) grad T*), with the cooled walls of ``thermal_walls`` at
+    the new time level ``t`` (default dt) and zero flux elsewhere.
+    ``source`` (optional, per cell) is the S_Phi of Eq. 3.26, used only by
+    manufactured-solution tests."""
+    if t is None:
+        t = case["dt"]
     al = case["alloy"]
     alpha = al["k"] / (al["rho"] * al["cp"])
     Dface = []
@@ -338,8 +358,8 @@ def assemble_temperature(grid, vel, T_n, case, source=None):
     b = T_n / case["dt"]
     if source is not None:
         b = b + source
-    for a, s, hc, Text in _robin_faces(case):
-        coef = robin_conductance(case, a, hc, grid) / (al["rho"] * al["cp"] * grid.h[a])
+    for a, s, U, Text in thermal_walls(case, grid, t):
+        coef = U / (al["rho"] * al["cp"] * grid.h[a])
         i = _index(grid.cells, a)
         wall = (i == 0) if s == 0 else (i == grid.n[a] - 1)
         P = P + np.where(wall, coef, 0.0)
@@ -488,12 +508,13 @@ def step(grid, st, case, method="auto", info=None):
     p = st.p + pc
     sysc = assemble_solute(grid, vel, st.gl, st.C, case)
     C = solve_system(sysc, x0=st.C, method=method, rtol=tol_t)
-    syst = assemble_temperature(grid, vel, st.T, case)
+    t_new = st.t + case["dt"]
+    syst = assemble_temperature(grid, vel, st.T, case, t=t_new)
     Tstar = solve_system(syst, x0=st.T, method=method, rtol=tol_t)
     T, gl, Cl, Cs = lever_update(Tstar, st.gl, C, al)
     if info is not None:
         info.update(ustar=ustar, pc=pc, Tstar=Tstar, sysc=sysc, syst=syst)
-    return State(vel, p, T, C, gl, Cl, Cs)
+    return State(vel, p, T, C, gl, Cl, Cs, t_new)
 
 
 def run(case, nsteps, T=None, C=None, method="auto"):

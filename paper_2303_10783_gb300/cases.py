@@ -14,7 +14,13 @@ A case is a plain ``dict``:
 ``dt``                  time step in seconds
 ``alloy``               dict of material data (see :func:`sn_pb_alloy`)
 ``robin``               dict face -> (h [W/m^2K], T_ext [K]); faces not listed
-                        are adiabatic. Faces are ``x-, x+, y-, y+, z-, z+``.
+                        in ``robin`` or ``dirichlet`` are adiabatic. Faces are
+                        ``x-, x+, y-, y+, z-, z+``.
+``dirichlet``           dict face -> (T_w0 [K], rate [K/s]): wall held at
+                        T_w(t) = T_w0 + rate t
+``slip``                faces that are free-slip (the others are no-slip)
+``perturb``             None, or a factor applied to C on the central
+                        vertical line (Example 2 seeds freckles with 1.0001)
 ``T0``                  nominal initial temperature [K]; also the Boussinesq
                         reference temperature
 ``noise``               half-width of the uniform initial temperature noise [K]
@@ -26,7 +32,7 @@ A case is a plain ``dict``:
 ``steps``               number of time steps the workload runs
 
 The vertical axis is y in 2D and z in 3D; gravity points along minus that
-axis. All walls are rigid and no-slip.
+axis. All walls are rigid and impermeable.
 """
 import numpy as np
 
@@ -63,12 +69,14 @@ def fe_c_alloy():
 
 
 def make_case(dim, nx, ny, nz, lx, ly, lz, dt, alloy=None, robin=None, T0=499.0, noise=1.0e-3, seed=0,
-              tol_p=1.0e-10, tol_t=1.0e-12, max_it_p=20000, max_it_t=2000, steps=100, precond_p="mg"):
+              tol_p=1.0e-10, tol_t=1.0e-12, max_it_p=20000, max_it_t=2000, steps=100, precond_p="mg",
+              dirichlet=None, slip=(), perturb=None):
     if dim == 2:
         nz, lz = 1, 1.0
     return dict(dim=dim, nx=nx, ny=ny, nz=nz, lx=lx, ly=ly, lz=lz, dt=dt,
                 alloy=dict(alloy if alloy is not None else sn_pb_alloy()),
                 robin=dict(robin if robin is not None else {"x-": (400.0, 298.0)}),
+                dirichlet=dict(dirichlet or {}), slip=tuple(slip), perturb=perturb,
                 T0=T0, noise=noise, seed=seed, tol_p=tol_p, tol_t=tol_t,
                 max_it_p=max_it_p, max_it_t=max_it_t, steps=steps, precond_p=precond_p)
 
@@ -99,6 +107,29 @@ def ingot_3d(nx=384, ny=256, nz=256, **kw):
     return make_case(3, nx, ny, nz, 0.2, 0.1, 0.1, 0.01, alloy=fe_c_alloy(), **kw)
 
 
+def pb_sn_alloy():
+    """Pb-48%Sn alloy of Example 2 (Table 1; C in wt% Sn, temperatures in K)."""
+    a = sn_pb_alloy()
+    a.update(Tm=327.5 + 273.15, m=-2.334, kp=0.307, C0=48.0, rho=9000.0, k=50.0, cp=200.0, L=5.35e4,
+             betaT=1.0e-4, betaC=4.5e-3, Ce=61.9)
+    return a
+
+
+def freckle_2d(nx=30, ny=90, slip=False, **kw):
+    """Example 2 in 2D: Pb-48%Sn in a cavity of aspect ratio nx:ny (1 mm
+    cells), cooled from the bottom by a wall temperature
+    falling linearly from 216 C at 0.05 K/s, the top held adiabatic here,
+    side walls no-slip (or free-slip), C raised by 1e-4 relative on the
+    central vertical line, dt = 0.01 s. The initial melt is at 216 C."""
+    kw.setdefault("steps", 100)
+    kw.setdefault("seed", 5)
+    h = 1.0e-3
+    walls = ("x-", "x+") if slip else ()
+    return make_case(2, nx, ny, 1, nx * h, ny * h, 1.0, 0.01, alloy=pb_sn_alloy(), robin={},
+                     dirichlet={"y-": (216.0 + 273.15, -0.05)}, slip=walls, T0=216.0 + 273.15,
+                     perturb=1.0001, **kw)
+
+
 def cell_shape(case):
     """numpy shape (nz, ny, nx) of a cell-centred field."""
     return (case["nz"], case["ny"], case["nx"])
@@ -112,6 +143,12 @@ def initial_fields(case):
     shape = cell_shape(case)
     T = case["T0"] + rng.uniform(-case["noise"], case["noise"], size=shape)
     C = np.full(shape, case["alloy"]["C0"], dtype=np.float64)
+    if case.get("perturb"):
+        nx, ny = case["nx"], case["ny"]
+        if case["dim"] == 2:
+            C[:, :, nx // 2] *= case["perturb"]
+        else:
+            C[:, ny // 2, nx // 2] *= case["perturb"]
     return dict(T=np.ascontiguousarray(T, dtype=np.float64), C=C)
 
 

@@ -29,3 +29,11 @@ def neumann_lambda(St, nu):
 def neumann_front(t, alpha, St, nu):
     """Solid-liquid front position X(t) = 2 lambda sqrt(alpha t)."""
     return 2.0 * neumann_lambda(St, nu) * np.sqrt(alpha * t)
+
+
+def linear_wall_semi_infinite(x, t, alpha, Ti, rate):
+    """T(x, t) for x > 0, T(x, 0) = Ti, wall temperature Ti + rate * t
+    (Carslaw & Jaeger Sec. 2.5): T - Ti = rate t 4 i^2erfc(xi), with
+    4 i^2erfc(z) = (1 + 2 z^2) erfc(z) - 2 z exp(-z^2)/sqrt(pi), xi = x/(2 sqrt(alpha t))."""
+    xi = x / (2.0 * np.sqrt(alpha * t))
+    return Ti + rate * t * ((1.0 + 2.0 * xi * xi) * erfc(xi) - 2.0 * xi * np.exp(-xi * xi) / np.sqrt(np.pi))

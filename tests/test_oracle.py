@@ -176,6 +176,24 @@ def test_vectorised_equals_forward_assembly(dim):
 
 
 @pytest.mark.parametrize("dim", [2, 3])
+def test_forward_equals_vectorised_with_slip_and_dirichlet_walls(dim):
+    """The same Sec. 4 cross-check with Example 2's walls: free-slip sides and a
+    bottom wall held at a time-dependent temperature."""
+    vert = "y-" if dim == 2 else "z-"
+    case = _small(dim, robin={"x-": (400.0, 298.0)}, dirichlet={vert: (480.0, -0.05)},
+                  slip=("x-", "x+", "y+") if dim == 3 else ("x-", "x+"))
+    g = oracle.Grid(case)
+    st = _state_from_random(case, 6)
+    pairs = [(oracle.assemble_momentum(g, st, case, a), fw.forward_momentum(g, st, case, a)) for a in range(dim)]
+    pairs.append((oracle.assemble_temperature(g, st.vel, st.T, case, t=2.5),
+                  fw.forward_temperature(g, st.vel, st.T, case, t=2.5)))
+    for vec, fwd in pairs:
+        for k in vec:
+            scale = max(np.abs(vec[k]).max(), np.abs(vec["P"]).max())
+            assert np.abs(vec[k] - fwd[k]).max() <= 1e-11 * scale, k
+
+
+@pytest.mark.parametrize("dim", [2, 3])
 def test_dia_pattern(dim):
     """Every system has only the 5 (2D) / 7 (3D) diagonals of Eq. 4.1 and no coupling wraps a row."""
     case = _small(dim)
@@ -343,6 +361,24 @@ def test_hydrostatic_rest():
     assert np.all(np.abs(st.T - case["T0"]) < 1e-10)
 
 
+def test_free_slip_mirror_symmetry():
+    """Free-slip side walls keep the x-mirror symmetry of the cavity."""
+    base = dict(nx=12, ny=8)
+    A = cases.cavity_2d(robin={"x-": (400.0, 298.0)}, slip=("x-", "x+", "y-", "y+"), **base)
+    B = cases.cavity_2d(robin={"x+": (400.0, 298.0)}, slip=("x-", "x+", "y-", "y+"), **base)
+    f = cases.initial_fields(A)
+    g = oracle.Grid(A)
+    sa = oracle.initial_state(A, f["T"] - 0.5, f["C"])
+    sb = oracle.initial_state(B, f["T"][:, :, ::-1] - 0.5, f["C"])
+    for _ in range(10):
+        sa = oracle.step(g, sa, A)
+        sb = oracle.step(g, sb, B)
+    flip = lambda x: x[:, :, ::-1]
+    vscale = max(np.abs(x).max() for x in sa.vel)
+    assert np.abs(flip(sb.v) - sa.v).max() < 1e-11 * vscale and np.abs(-flip(sb.u) - sa.u).max() < 1e-11 * vscale
+    assert _rel(flip(sb.T), sa.T) < 1e-12
+
+
 @pytest.mark.parametrize("dim", [2, 3])
 def test_mirror_symmetry(dim):
     """Cooling the right wall instead of the left, with the initial noise
@@ -401,6 +437,30 @@ def test_robin_conduction_closed_form():
     assert e2 < 5e-3
     order = np.log2(e1 / e2)
     assert 0.7 < order < 1.6, order
+
+
+def _linear_wall_error(nx, dt, t_end=2.0, rate=-20.0):
+    case = _slab(nx, dt)
+    case["robin"] = {}
+    case["dirichlet"] = {"x-": (600.0, rate)}
+    case["T0"] = 600.0
+    st = oracle.run(case, int(round(t_end / dt)))
+    g = oracle.Grid(case)
+    al = case["alloy"]
+    alpha = al["k"] / (al["rho"] * al["cp"])
+    x = (np.arange(nx) + 0.5) * g.h[0]
+    exact = cf.linear_wall_semi_infinite(x, t_end, alpha, 600.0, rate)
+    assert np.all(st.gl == 1.0)
+    return np.abs(st.T[0, 0] - exact).max() / (abs(rate) * t_end)
+
+
+def test_linearly_cooled_wall_closed_form():
+    """Example 2's wall temperature falling linearly in time against Carslaw &
+    Jaeger's semi-infinite solution; first-order convergence in (h, dt)."""
+    e1 = _linear_wall_error(100, 0.02)
+    e2 = _linear_wall_error(200, 0.01)
+    assert e2 < 2e-2
+    assert 0.6 < np.log2(e1 / e2) < 1.8, (e1, e2)
 
 
 def _stefan_front(nx, dt, t_end):
