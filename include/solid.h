@@ -63,7 +63,8 @@ typedef enum {
 
 enum { SS_FP64 = 0, SS_MIXED = 1 };                  /* ss_grid.precision */
 enum { SS_PRECOND_MG = 0, SS_PRECOND_JACOBI = 1 };   /* ss_grid.precond_p */
-enum { SS_ADIABATIC = 0, SS_ROBIN = 1 };             /* ss_bc.thermal */
+enum { SS_ADIABATIC = 0, SS_ROBIN = 1, SS_DIRICHLET = 2 };  /* ss_bc.thermal */
+enum { SS_NOSLIP = 0, SS_FREESLIP = 1 };             /* ss_bc.flow */
 enum { SS_XM = 0, SS_XP = 1, SS_YM = 2, SS_YP = 3, SS_ZM = 4, SS_ZP = 5 };  /* walls */
 
 /* Field identifiers: bit i of a mask selects field i; pointer arrays passed
@@ -111,11 +112,19 @@ typedef struct {
   double Tref;      /* Boussinesq reference temperature [K] (Eq. 2.9) */
 } ss_alloy;
 
-/* Thermal condition of one wall. */
+/* Condition of one wall. All walls are impermeable (normal velocity 0).
+ * Thermal: SS_ADIABATIC; SS_ROBIN, flux h (T - Text) through a film of
+ * coefficient h in series with half a cell (Sec. 5, Example 1); SS_DIRICHLET,
+ * wall temperature Text + dTdt * t at time t, reached over half a cell (Sec. 5,
+ * Example 2 cools the bottom this way). The energy step of the step that
+ * ends at time t takes the wall value at t. Flow: SS_NOSLIP (tangential
+ * velocity 0 at the wall) or SS_FREESLIP (no tangential stress). */
 typedef struct {
-  int thermal;      /* SS_ADIABATIC or SS_ROBIN */
+  int thermal;      /* SS_ADIABATIC, SS_ROBIN or SS_DIRICHLET */
   double h;         /* heat transfer coefficient [W/m^2K] (> 0 for Robin) */
-  double Text;      /* external temperature [K] */
+  double Text;      /* external (Robin) or initial wall (Dirichlet) temperature [K] */
+  double dTdt;      /* wall temperature rate [K/s] (Dirichlet only) */
+  int flow;         /* SS_NOSLIP or SS_FREESLIP */
 } ss_bc;
 
 /* Per-step diagnostics of the most recent step (or stage call). */
@@ -158,8 +167,9 @@ ss_status ss_create_case(const ss_grid* grid, void* workspace, size_t workspace_
  * adiabatic. Allowed before the first step only (SS_ESTATE afterwards). */
 ss_status ss_set_alloy(ss_case* c, const ss_alloy* alloy);
 
-/* Set the thermal condition of wall `face` (SS_XM..SS_ZP). Allowed at any time
- * between steps. */
+/* Set the thermal and flow condition of wall `face` (SS_XM..SS_ZP). Allowed
+ * at any time between steps. SS_EINVAL for an unknown condition, a Robin h
+ * that is not > 0, or a non-finite wall temperature or rate. */
 ss_status ss_set_boundary(ss_case* c, int face, const ss_bc* bc);
 
 /* Enqueue n time steps (Algorithm 1) on the case's stream and return without
@@ -191,6 +201,12 @@ ss_status ss_set_fields(ss_case* c, unsigned mask, const void* const* src, int s
  * at or above the liquidus, else Eq. 3.15 clamped to [0, 1]; C_l by
  * Eq. 3.18 (capped at C_e), C_s = kp C_l (Eq. 3.19). */
 ss_status ss_equilibrate(ss_case* c);
+
+/* Simulated time of the fields (0 at creation; each step adds dt, in the
+ * lever stage that closes it). ss_set_time is stream-ordered; ss_get_time
+ * synchronises the stream. Restarting from saved fields sets both. */
+ss_status ss_set_time(ss_case* c, double t);
+ss_status ss_get_time(ss_case* c, double* t);
 
 /* Diagnostics of the last step; synchronises; clears the sticky status. */
 ss_status ss_get_stats(ss_case* c, ss_stats* out);
@@ -226,7 +242,9 @@ const char* ss_last_error(void);
  *   no planes (matrix-free constant Laplacian): only b and x.
  * ss_project(c): Eq. 3.5 with the solved u* and p'; p += p'.
  * ss_lever(c): Eq. 3.13-3.19 treating the current T field as T*, the
- *   current g_l as g_l^n and the current C as C^{n+1}. */
+ *   current g_l as g_l^n and the current C as C^{n+1}; it closes a step and
+ *   so advances the case's time by dt.
+ * ss_assemble(c, SS_SYS_T) takes the wall temperatures at the case's time + dt. */
 ss_status ss_assemble(ss_case* c, int sys);
 ss_status ss_solve(ss_case* c, int sys);
 ss_status ss_get_system(ss_case* c, int sys, void* const* dst, int dst_is_device);

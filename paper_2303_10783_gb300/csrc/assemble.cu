@@ -138,8 +138,10 @@ __global__ void __launch_bounds__(kBlockA) k_assemble_momentum(Params pr, Sys s,
         Ff = 0.5 * (vel[d][fidx(pr, d, lo_f[0], lo_f[1], lo_f[2])] + vel[d][fidx(pr, d, hi_f[0], hi_f[1], hi_f[2])]);
         hb = (idx[d] >= 1);
         hf = (idx[d] <= ax.n[d] - 2);
-        Db = hb ? nu : 2.0 * nu;   // no-slip ghost = -interior beyond a wall
-        Df = hf ? nu : 2.0 * nu;
+        // beyond a wall the ghost is -interior (no-slip: the wall face then
+        // carries 2 nu) or +interior (free-slip: no viscous flux)
+        Db = hb ? nu : (pr.slip[2 * d] ? 0.0 : 2.0 * nu);
+        Df = hf ? nu : (pr.slip[2 * d + 1] ? 0.0 : 2.0 * nu);
       }
       P += (fmax(Ff, 0.0) - fmin(Fb, 0.0)) * ax.ih[d] + (Db + Df) * ax.ih2[d];
       nbB[d] = hb ? (-fmax(Fb, 0.0) * ax.ih[d] - Db * ax.ih2[d]) : 0.0;
@@ -158,7 +160,8 @@ __global__ void __launch_bounds__(kBlockA) k_assemble_momentum(Params pr, Sys s,
 
 // Cell-centred systems. SOLUTE = true: solute (Eq. 3.10) with diffusivity
 // g_l^n D_l on faces and column scaling by A_g = 1/(1 - (1-k_p)(1-g_l^n));
-// false: T* (Eq. 3.12) with diffusivity k/(rho c_p) and Robin walls.
+// false: T* (Eq. 3.12) with diffusivity k/(rho c_p) and cooled walls, whose
+// temperature is taken at the new time level *time + dt.
 // `Ag` holds A_g per cell (kept current by k_lever / k_equilibrate).
 template <bool SOLUTE>
 __global__ void __launch_bounds__(kBlockA) k_assemble_cells(Params pr, Sys s, const double* __restrict__ u,
@@ -166,7 +169,8 @@ __global__ void __launch_bounds__(kBlockA) k_assemble_cells(Params pr, Sys s, co
                                                            const double* __restrict__ w,
                                                            const double* __restrict__ phi_n,
                                                            const double* __restrict__ gl,
-                                                           const double* __restrict__ Ag) {
+                                                           const double* __restrict__ Ag,
+                                                           const double* __restrict__ time) {
   const Axes ax = axes_of(pr);
   const double* vel[3] = {u, v, w};
   const int nx = pr.nx, ny = pr.ny;
@@ -209,14 +213,16 @@ __global__ void __launch_bounds__(kBlockA) k_assemble_cells(Params pr, Sys s, co
       P = idt + m0 * Ag[r];
     } else {
       P = m0 + idt;
-      // Robin walls: flux U (T_P - T_ext) per unit area, divided by rho cp h
+      // cooled walls: flux coef (T_P - T_w(t^{n+1})) (Robin through the film and
+      // half a cell; Dirichlet through half a cell)
       const int wall[6] = {i == 0, i == nx - 1, j == 0, j == ny - 1, pr.dim == 3 && k == 0,
                            pr.dim == 3 && k == pr.nz - 1};
+      const double t_new = *time + pr.dt;
 #pragma unroll
       for (int q = 0; q < 6; ++q) {
-        if (wall[q] && pr.robin_coef[q] != 0.0) {
-          P += pr.robin_coef[q];
-          b += pr.robin_coef[q] * pr.robin_text[q];
+        if (wall[q] && pr.wall_coef[q] != 0.0) {
+          P += pr.wall_coef[q];
+          b += pr.wall_coef[q] * (pr.wall_T0[q] + pr.wall_rate[q] * t_new);
         }
       }
     }
@@ -290,8 +296,11 @@ __device__ __forceinline__ Phase phase_of(const Params& pr, double C, double g) 
   return o;
 }
 
-__global__ void __launch_bounds__(kBlockA) k_lever(Params pr, double* T, double* gl, const double* __restrict__ C,
-                                                  double* Cl, double* Cs, double* Kinv, double* Ag, int n) {
+// The lever update closes a step: it also advances the case's time by dt.
+__global__ void __launch_bounds__(kBlockA) k_lever(Params pr, double* time, double* T, double* gl,
+                                                  const double* __restrict__ C, double* Cl, double* Cs, double* Kinv,
+                                                  double* Ag, int n) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) *time += pr.dt;
   const double kp = pr.kp, Tm = pr.Tm;
   const double cpL = pr.cp / pr.L, Lcp = pr.L / pr.cp;
   const double a = 1.0 - kp;
@@ -360,14 +369,14 @@ cudaError_t launch_assemble_momentum(int comp, const Params& pr, const Sys& sys,
 
 cudaError_t launch_assemble_solute(const Params& pr, const Sys& sys, const double* const vel[3], const double* gl,
                                    const double* C, const double* Ag, cudaStream_t st) {
-  k_assemble_cells<true><<<grid_for(sys.d.n), kBlockA, 0, st>>>(pr, sys, vel[0], vel[1], vel[2], C, gl, Ag);
+  k_assemble_cells<true><<<grid_for(sys.d.n), kBlockA, 0, st>>>(pr, sys, vel[0], vel[1], vel[2], C, gl, Ag, nullptr);
   return cudaGetLastError();
 }
 
 cudaError_t launch_assemble_temperature(const Params& pr, const Sys& sys, const double* const vel[3],
-                                        const double* T, cudaStream_t st) {
+                                        const double* time, const double* T, cudaStream_t st) {
   k_assemble_cells<false><<<grid_for(sys.d.n), kBlockA, 0, st>>>(pr, sys, vel[0], vel[1], vel[2], T, nullptr,
-                                                                 nullptr);
+                                                                 nullptr, time);
   return cudaGetLastError();
 }
 
@@ -385,10 +394,10 @@ cudaError_t launch_project(const Params& pr, double* const vel[3], const double*
   return cudaGetLastError();
 }
 
-cudaError_t launch_lever(const Params& pr, double* T, double* gl, const double* C, double* Cl, double* Cs,
-                         double* Kinv, double* Ag, cudaStream_t st) {
+cudaError_t launch_lever(const Params& pr, double* time, double* T, double* gl, const double* C, double* Cl,
+                         double* Cs, double* Kinv, double* Ag, cudaStream_t st) {
   const int n = pr.nx * pr.ny * pr.nz;
-  k_lever<<<grid_for(n), kBlockA, 0, st>>>(pr, T, gl, C, Cl, Cs, Kinv, Ag, n);
+  k_lever<<<grid_for(n), kBlockA, 0, st>>>(pr, time, T, gl, C, Cl, Cs, Kinv, Ag, n);
   return cudaGetLastError();
 }
 

@@ -213,12 +213,20 @@ void fill_params(ss_case* c, const ss_alloy* al) {
   const double h[3] = {pr.hx, pr.hy, pr.hz};
   for (int q = 0; q < 6; ++q) {
     const int axis = q / 2;
-    pr.robin_coef[q] = 0.0;
-    pr.robin_text[q] = 0.0;
-    if (c->bc[q].thermal == SS_ROBIN && axis < pr.dim && c->alloy_set) {
-      const double U = 1.0 / (1.0 / c->bc[q].h + h[axis] / (2.0 * pr.k));
-      pr.robin_coef[q] = U / (pr.rho * pr.cp * h[axis]);
-      pr.robin_text[q] = c->bc[q].Text;
+    const ss_bc& bc = c->bc[q];
+    pr.wall_coef[q] = 0.0;
+    pr.wall_T0[q] = 0.0;
+    pr.wall_rate[q] = 0.0;
+    pr.slip[q] = bc.flow == SS_FREESLIP;
+    if (axis >= pr.dim || !c->alloy_set) continue;
+    if (bc.thermal == SS_ROBIN) {            // film h_c in series with half a cell
+      const double U = 1.0 / (1.0 / bc.h + h[axis] / (2.0 * pr.k));
+      pr.wall_coef[q] = U / (pr.rho * pr.cp * h[axis]);
+      pr.wall_T0[q] = bc.Text;
+    } else if (bc.thermal == SS_DIRICHLET) { // wall temperature over half a cell
+      pr.wall_coef[q] = pr.k / (0.5 * h[axis]) / (pr.rho * pr.cp * h[axis]);
+      pr.wall_T0[q] = bc.Text;
+      pr.wall_rate[q] = bc.dTdt;
     }
   }
 }
@@ -303,7 +311,7 @@ ss_status stage_assemble(ss_case* c, int sys) {
       break;
     }
     case SS_SYS_C: e = launch_assemble_solute(c->pr, c->sys[sys], vel, c->gl, c->C, c->Ag, c->stream); break;
-    case SS_SYS_T: e = launch_assemble_temperature(c->pr, c->sys[sys], vel, c->T, c->stream); break;
+    case SS_SYS_T: e = launch_assemble_temperature(c->pr, c->sys[sys], vel, &c->st->time, c->T, c->stream); break;
     default: return fail(SS_EINVAL, "unknown system %d", sys);
   }
   if (e != cudaSuccess) return fail(SS_ECUDA, "assembly of system %d: %s", sys, cudaGetErrorString(e));
@@ -346,7 +354,7 @@ ss_status stage_project(ss_case* c) {
 
 ss_status stage_lever(ss_case* c) {
   StageTimer tm(c, SS_PROF_LEVER, 1);
-  cudaError_t e = launch_lever(c->pr, c->T, c->gl, c->C, c->Cl, c->Cs, c->Kinv, c->Ag, c->stream);
+  cudaError_t e = launch_lever(c->pr, &c->st->time, c->T, c->gl, c->C, c->Cl, c->Cs, c->Kinv, c->Ag, c->stream);
   if (e != cudaSuccess) return fail(SS_ECUDA, "lever update: %s", cudaGetErrorString(e));
   return SS_OK;
 }
@@ -479,8 +487,11 @@ ss_status ss_set_boundary(ss_case* c, int face, const ss_bc* bc) {
   drop_graph(c);
   if (!bc) return fail(SS_EINVAL, "bc is NULL");
   if (face < 0 || face > 5) return fail(SS_EINVAL, "face must be 0..5");
-  if (bc->thermal != SS_ADIABATIC && bc->thermal != SS_ROBIN) return fail(SS_EINVAL, "unknown thermal condition");
+  if (bc->thermal != SS_ADIABATIC && bc->thermal != SS_ROBIN && bc->thermal != SS_DIRICHLET)
+    return fail(SS_EINVAL, "unknown thermal condition");
   if (bc->thermal == SS_ROBIN && !(bc->h > 0)) return fail(SS_EINVAL, "Robin h must be > 0");
+  if (bc->flow != SS_NOSLIP && bc->flow != SS_FREESLIP) return fail(SS_EINVAL, "unknown flow condition");
+  if (!std::isfinite(bc->Text) || !std::isfinite(bc->dTdt)) return fail(SS_EINVAL, "wall temperature not finite");
   c->bc[face] = *bc;
   fill_params(c, nullptr);
   return SS_OK;
@@ -581,6 +592,22 @@ ss_status ss_equilibrate(ss_case* c) {
   if (!c->alloy_set) return fail(SS_ESTATE, "set_alloy first");
   cudaError_t e = launch_equilibrate(c->pr, c->T, c->C, c->gl, c->Cl, c->Cs, c->Kinv, c->Ag, 1, 1, c->stream);
   if (e != cudaSuccess) return fail(SS_ECUDA, "equilibrate: %s", cudaGetErrorString(e));
+  return SS_OK;
+}
+
+ss_status ss_set_time(ss_case* c, double t) {
+  STAGE_TRY(check_case(c));
+  if (!std::isfinite(t)) return fail(SS_EINVAL, "time must be finite");
+  k_fill<<<1, 32, 0, c->stream>>>(&c->st->time, t, 1);
+  CUDA_TRY(cudaGetLastError());
+  return SS_OK;
+}
+
+ss_status ss_get_time(ss_case* c, double* t) {
+  STAGE_TRY(check_case(c));
+  if (!t) return fail(SS_EINVAL, "t is NULL");
+  CUDA_TRY(cudaMemcpyAsync(t, &c->st->time, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
   return SS_OK;
 }
 

@@ -48,6 +48,7 @@ struct DevStatus {
   int sticky;                    // sticky ss_status of solves since the last read
   SolveStat stat[SS_NSYS];
   double scal[kMaxRedSlots * 4]; // broadcast scalars (unused by the all-blocks reduction)
+  double time;                   // simulated time of the fields; k_lever advances it by dt
 };
 
 template <typename T>
@@ -69,8 +70,11 @@ struct Params {
   double hx, hy, hz, dt;
   double Tm, m, kp, C0, rho, k, cp, L, mu, Dl, betaT, betaC, K0, Ce, gravity, eps, Tref;
   int has_eutectic;
-  // Robin coefficient coef = U / (rho cp h) and T_ext per wall (coef 0: adiabatic)
-  double robin_coef[6], robin_text[6];
+  // Thermal walls: flux coef (T_P - T_w(t)) per unit volume and rho c_p, with
+  // T_w(t) = wall_T0 + wall_rate t (coef 0: adiabatic). Robin: coef = U/(rho cp h),
+  // U = 1/(1/h_c + h/2k), rate 0; Dirichlet: coef = 2k/(rho cp h^2).
+  double wall_coef[6], wall_T0[6], wall_rate[6];
+  int slip[6];   // 1: free-slip wall (tangential ghost = interior), 0: no-slip
 };
 
 // Krylov scratch: 8 FP64 vectors + 8 FP32 vectors, each of `nmax` rows with guards.
@@ -239,12 +243,13 @@ cudaError_t launch_assemble_momentum(int comp, const Params& pr, const Sys& sys,
 cudaError_t launch_assemble_solute(const Params& pr, const Sys& sys, const double* const vel[3], const double* gl,
                                    const double* C, const double* Ag, cudaStream_t s);
 cudaError_t launch_assemble_temperature(const Params& pr, const Sys& sys, const double* const vel[3],
-                                        const double* T, cudaStream_t s);
+                                        const double* time, const double* T, cudaStream_t s);
 cudaError_t launch_poisson_rhs(const Params& pr, const double* const ustar[3], double* b, cudaStream_t s);
 cudaError_t launch_project(const Params& pr, double* const vel[3], const double* const ustar[3], const double* pc,
                            double* p, cudaStream_t s);
-cudaError_t launch_lever(const Params& pr, double* T, double* gl, const double* C, double* Cl, double* Cs,
-                         double* Kinv, double* Ag, cudaStream_t s);
+// `time` is advanced by dt (the lever update closes a step).
+cudaError_t launch_lever(const Params& pr, double* time, double* T, double* gl, const double* C, double* Cl,
+                         double* Cs, double* Kinv, double* Ag, cudaStream_t s);
 // from_T: recompute g_l from (T, C) in equilibrium; write_cl: recompute C_l, C_s.
 // K^{-1} and A_g are always refreshed from g_l.
 cudaError_t launch_equilibrate(const Params& pr, const double* T, const double* C, double* gl, double* Cl,

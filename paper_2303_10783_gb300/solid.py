@@ -18,7 +18,8 @@ STATUS_NAMES = {0: "SS_OK", 1: "SS_EINVAL", 2: "SS_ENOMEM", 3: "SS_ENOTCONV", 4:
                 6: "SS_ESTATE", 7: "SS_ETIMEOUT"}
 SS_FP64, SS_MIXED = 0, 1
 SS_PRECOND_MG, SS_PRECOND_JACOBI = 0, 1
-SS_ADIABATIC, SS_ROBIN = 0, 1
+SS_ADIABATIC, SS_ROBIN, SS_DIRICHLET = 0, 1, 2
+SS_NOSLIP, SS_FREESLIP = 0, 1
 FIELDS = ("u", "v", "w", "p", "T", "C", "gl", "Cl", "Cs")
 FIELD_ID = {name: i for i, name in enumerate(FIELDS)}
 SYSTEMS = ("u", "v", "w", "p", "C", "T")
@@ -41,7 +42,8 @@ class Alloy(ctypes.Structure):
 
 
 class BC(ctypes.Structure):
-    _fields_ = [("thermal", ctypes.c_int), ("h", ctypes.c_double), ("Text", ctypes.c_double)]
+    _fields_ = [("thermal", ctypes.c_int), ("h", ctypes.c_double), ("Text", ctypes.c_double),
+                ("dTdt", ctypes.c_double), ("flow", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -80,6 +82,8 @@ def _declare(lib):
         "ss_set_fields": [P, ctypes.c_uint, ctypes.POINTER(P), ctypes.c_int],
         "ss_equilibrate": [P],
         "ss_get_stats": [P, ctypes.POINTER(Stats)],
+        "ss_set_time": [P, ctypes.c_double],
+        "ss_get_time": [P, ctypes.POINTER(ctypes.c_double)],
         "ss_destroy": [P],
         "ss_assemble": [P, ctypes.c_int],
         "ss_solve": [P, ctypes.c_int],
@@ -166,14 +170,31 @@ class Case:
         self.h = h
         al = alloy_struct(case)
         check(self.lib.ss_set_alloy(self.h, ctypes.byref(al)))
-        for face, (hc, Text) in case["robin"].items():
-            if FACE_ID[face] // 2 < self.dim:
-                self.set_boundary(face, SS_ROBIN, hc, Text)
+        for face in FACE_ID:
+            if FACE_ID[face] // 2 >= self.dim:
+                continue
+            flow = SS_FREESLIP if face in case.get("slip", ()) else SS_NOSLIP
+            if face in case["robin"]:
+                hc, Text = case["robin"][face]
+                self.set_boundary(face, SS_ROBIN, hc, Text, flow=flow)
+            elif face in case.get("dirichlet", {}):
+                Tw0, rate = case["dirichlet"][face]
+                self.set_boundary(face, SS_DIRICHLET, 0.0, Tw0, rate, flow=flow)
+            elif flow != SS_NOSLIP:
+                self.set_boundary(face, SS_ADIABATIC, flow=flow)
 
     # -- C-ABI calls, same names
-    def set_boundary(self, face, thermal, h=0.0, Text=0.0):
-        bc = BC(thermal, h, Text)
+    def set_boundary(self, face, thermal, h=0.0, Text=0.0, dTdt=0.0, flow=SS_NOSLIP):
+        bc = BC(thermal, h, Text, dTdt, flow)
         check(self.lib.ss_set_boundary(self.h, FACE_ID[face] if isinstance(face, str) else face, ctypes.byref(bc)))
+
+    def set_time(self, t):
+        check(self.lib.ss_set_time(self.h, float(t)))
+
+    def get_time(self):
+        t = ctypes.c_double(0.0)
+        check(self.lib.ss_get_time(self.h, ctypes.byref(t)))
+        return t.value
 
     def step(self, n=1):
         check(self.lib.ss_step(self.h, n))

@@ -43,7 +43,7 @@ def test_struct_layouts_match_header(built_lib):
     """The ctypes mirrors agree with the header's field order (spot checks by size)."""
     from paper_2303_10783_gb300 import solid
     assert ctypes.sizeof(solid.Alloy) == 17 * 8
-    assert ctypes.sizeof(solid.BC) == 24
+    assert ctypes.sizeof(solid.BC) == 8 + 8 + 8 + 8 + 8   # int (padded), h, Text, dTdt, int (padded)
     assert ctypes.sizeof(solid.Grid) == 4 * 4 + 3 * 8 + 8 + 8 + 16 + 8 + 8
 
 
