@@ -202,6 +202,13 @@ ss_status ss_set_fields(ss_case* c, unsigned mask, const void* const* src, int s
  * Eq. 3.18 (capped at C_e), C_s = kp C_l (Eq. 3.19). */
 ss_status ss_equilibrate(ss_case* c);
 
+/* The FP64 -> FP32 rounding (to nearest, ties to even) that forms the FP32
+ * plane copies, applied to n device values src -> dst in order on `stream`
+ * (a cudaStream_t; NULL: the legacy default stream). For checking that
+ * rounding against a reference conversion. SS_EINVAL for n < 0 or NULL
+ * pointers with n > 0. */
+ss_status ss_convert_f64_to_f32(const double* src, float* dst, long long n, void* stream);
+
 /* Simulated time of the fields (0 at creation; each step adds dt, in the
  * lever stage that closes it). ss_set_time is stream-ordered; ss_get_time
  * synchronises the stream. Restarting from saved fields sets both. */
@@ -240,6 +247,12 @@ const char* ss_last_error(void);
  *   system into dst[0..8] = P, W, E, S, N, B, T (DIA planes, Eq. 4.1), b
  *   (right-hand side), x (solution); NULL entries are skipped. SS_SYS_P has
  *   no planes (matrix-free constant Laplacian): only b and x.
+ * ss_get_system_f32(c, sys, dst, dst_is_device): SS_MIXED cases only
+ *   (SS_ESTATE otherwise; SS_EINVAL for SS_SYS_P): copy the FP32 planes the
+ *   inner solves use into dst[0..7] = P, W, E, S, N, B, T, inverse diagonal
+ *   (n floats each); NULL entries are skipped. Each plane entry is its FP64
+ *   entry rounded to nearest, ties to even; the inverse diagonal is the FP32
+ *   reciprocal of the FP32 P.
  * ss_project(c): Eq. 3.5 with the solved u* and p'; p += p'.
  * ss_lever(c): Eq. 3.13-3.19 treating the current T field as T*, the
  *   current g_l as g_l^n and the current C as C^{n+1}; it closes a step and
@@ -248,6 +261,7 @@ const char* ss_last_error(void);
 ss_status ss_assemble(ss_case* c, int sys);
 ss_status ss_solve(ss_case* c, int sys);
 ss_status ss_get_system(ss_case* c, int sys, void* const* dst, int dst_is_device);
+ss_status ss_get_system_f32(ss_case* c, int sys, void* const* dst, int dst_is_device);
 ss_status ss_project(ss_case* c);
 ss_status ss_lever(ss_case* c);
 

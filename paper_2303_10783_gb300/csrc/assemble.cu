@@ -44,9 +44,11 @@ struct Axes {
 __device__ __forceinline__ Axes axes_of(const Params& pr) {
   Axes ax;
   ax.n[0] = pr.nx; ax.n[1] = pr.ny; ax.n[2] = pr.nz;
-  ax.ih[0] = 1.0 / pr.hx; ax.ih[1] = 1.0 / pr.hy; ax.ih[2] = 1.0 / pr.hz;
 #pragma unroll
-  for (int a = 0; a < 3; ++a) ax.ih2[a] = ax.ih[a] * ax.ih[a];
+  for (int a = 0; a < 3; ++a) {
+    ax.ih[a] = pr.ih[a];
+    ax.ih2[a] = pr.ih2[a];
+  }
   return ax;
 }
 
@@ -58,9 +60,48 @@ __device__ __forceinline__ int fidx(const Params& pr, int d, int i, int j, int k
 
 __device__ __forceinline__ int cidx(const Params& pr, int i, int j, int k) { return i + pr.nx * (j + pr.ny * k); }
 
+// These kernels are bound by the FP64 pipe (a small fraction of the FP32
+// rate on this GPU), so work that needs no FP64 arithmetic is done on the
+// integer pipes: the sign split of an advecting velocity and the FP64 -> FP32
+// rounding of the plane copies.
+
+// max(F, 0) and min(F, 0) by the sign bit (a -0 goes to the negative side,
+// which changes no coefficient).
+struct Split {
+  double pos, neg;
+};
+__device__ __forceinline__ Split split(double F) {
+  const bool negative = __double2hiint(F) < 0;
+  return {negative ? 0.0 : F, negative ? F : 0.0};
+}
+
+// IEEE-754 binary64 -> binary32 rounding to nearest, ties to even, on the
+// integer pipes for values whose result is a normal float (exponent of d in
+// [-126, 127]) and for zeros; other values (subnormal, overflowing, non-finite
+// results) take the hardware conversion. The 52-bit fraction keeps its top 23
+// bits; the 29 dropped bits decide the rounding; a carry out of the fraction
+// correctly increments the exponent (up to infinity).
+__device__ __forceinline__ float to_f32(double d) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(d);
+  const unsigned hi = (unsigned)(u >> 32), lo = (unsigned)u;
+  const unsigned e = (hi >> 20) & 0x7FFu;
+  const unsigned sign = hi & 0x80000000u;
+  if (e - 897u <= 253u) {
+    const unsigned m = ((hi & 0xFFFFFu) << 3) | (lo >> 29);
+    const unsigned rest = lo & 0x1FFFFFFFu;
+    unsigned bits = sign | ((e - 896u) << 23) | m;
+    bits += (rest > 0x10000000u || (rest == 0x10000000u && (m & 1u))) ? 1u : 0u;
+    return __uint_as_float(bits);
+  }
+  if ((u << 1) == 0ull) return __uint_as_float(sign);
+  return __double2float_rn(d);
+}
+
+// The mixed path's FP64 residual never reads the FP64 inverse diagonal: it is
+// written on the FP64 path only, and the FP32 one is an FP32 reciprocal
+// (both are Jacobi preconditioners; the residuals use the planes).
 __device__ __forceinline__ void write_row(const Sys& s, int r, int dim, double P, const double nbB[3],
                                           const double nbF[3], double b) {
-  const double id = 1.0 / P;
   s.a.P[r] = P;
   s.a.W[r] = nbB[0];
   s.a.E[r] = nbF[0];
@@ -71,18 +112,20 @@ __device__ __forceinline__ void write_row(const Sys& s, int r, int dim, double P
     s.a.T_[r] = nbF[2];
   }
   s.b[r] = b;
-  s.a.idiag[r] = id;
   if (s.af.P) {   // FP32 copies for the mixed-precision inner solve
-    s.af.P[r] = (float)P;
-    s.af.W[r] = (float)nbB[0];
-    s.af.E[r] = (float)nbF[0];
-    s.af.S[r] = (float)nbB[1];
-    s.af.N[r] = (float)nbF[1];
+    const float Pf = to_f32(P);
+    s.af.P[r] = Pf;
+    s.af.W[r] = to_f32(nbB[0]);
+    s.af.E[r] = to_f32(nbF[0]);
+    s.af.S[r] = to_f32(nbB[1]);
+    s.af.N[r] = to_f32(nbF[1]);
     if (dim == 3) {
-      s.af.B[r] = (float)nbB[2];
-      s.af.T_[r] = (float)nbF[2];
+      s.af.B[r] = to_f32(nbB[2]);
+      s.af.T_[r] = to_f32(nbF[2]);
     }
-    s.af.idiag[r] = (float)id;
+    s.af.idiag[r] = 1.0f / Pf;
+  } else {
+    s.a.idiag[r] = 1.0 / P;
   }
 }
 
@@ -99,8 +142,7 @@ __global__ void __launch_bounds__(kBlockA) k_assemble_momentum(Params pr, Sys s,
   const int mx = s.d.mx, my = s.d.my;
   const int n = (int)s.d.n;
   const int sA = (A == 0) ? 1 : (A == 1) ? mx : mx * my;    // stride of axis A in the row grid
-  const double nu = pr.mu / pr.rho;
-  const double idt = 1.0 / pr.dt;
+  const double idt = pr.idt;
   for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
     const int i = r % mx, t = r / mx, j = t % my, k = t / my;
     const int idx[3] = {i, j, k};
@@ -121,34 +163,37 @@ __global__ void __launch_bounds__(kBlockA) k_assemble_momentum(Params pr, Sys s,
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
       if (d >= pr.dim) break;
-      double Fb, Ff, Db, Df;
+      // sums (not means) of the two velocities that advect across the back and
+      // front faces of this control volume; the 1/2 is folded into hh = 1/(2h)
+      double sb, sf, Db, Df;   // Db, Df: diffusion coefficient / h^2 of the two faces
       bool hb, hf;
       if (d == A) {
-        Fb = 0.5 * (vel[A][r - sA] + own);
-        Ff = 0.5 * (own + vel[A][r + sA]);
+        sb = vel[A][r - sA] + own;
+        sf = own + vel[A][r + sA];
         hb = (f - 1 >= 1);
         hf = (f + 1 <= ax.n[A] - 1);
-        Db = nu;
-        Df = nu;
+        Db = pr.nu_ih2[d];
+        Df = pr.nu_ih2[d];
       } else {
         int lo_f[3] = {lo[0], lo[1], lo[2]}, hi_f[3] = {i, j, k};
         lo_f[d] += 1;
         hi_f[d] += 1;
-        Fb = 0.5 * (vel[d][fidx(pr, d, lo[0], lo[1], lo[2])] + vel[d][fidx(pr, d, i, j, k)]);
-        Ff = 0.5 * (vel[d][fidx(pr, d, lo_f[0], lo_f[1], lo_f[2])] + vel[d][fidx(pr, d, hi_f[0], hi_f[1], hi_f[2])]);
+        sb = vel[d][fidx(pr, d, lo[0], lo[1], lo[2])] + vel[d][fidx(pr, d, i, j, k)];
+        sf = vel[d][fidx(pr, d, lo_f[0], lo_f[1], lo_f[2])] + vel[d][fidx(pr, d, hi_f[0], hi_f[1], hi_f[2])];
         hb = (idx[d] >= 1);
         hf = (idx[d] <= ax.n[d] - 2);
         // beyond a wall the ghost is -interior (no-slip: the wall face then
         // carries 2 nu) or +interior (free-slip: no viscous flux)
-        Db = hb ? nu : (pr.slip[2 * d] ? 0.0 : 2.0 * nu);
-        Df = hf ? nu : (pr.slip[2 * d + 1] ? 0.0 : 2.0 * nu);
+        Db = hb ? pr.nu_ih2[d] : (pr.slip[2 * d] ? 0.0 : pr.two_nu_ih2[d]);
+        Df = hf ? pr.nu_ih2[d] : (pr.slip[2 * d + 1] ? 0.0 : pr.two_nu_ih2[d]);
       }
-      P += (fmax(Ff, 0.0) - fmin(Fb, 0.0)) * ax.ih[d] + (Db + Df) * ax.ih2[d];
-      nbB[d] = hb ? (-fmax(Fb, 0.0) * ax.ih[d] - Db * ax.ih2[d]) : 0.0;
-      nbF[d] = hf ? (fmin(Ff, 0.0) * ax.ih[d] - Df * ax.ih2[d]) : 0.0;
+      const Split b_ = split(sb), f_ = split(sf);
+      P += fma(f_.pos - b_.neg, pr.hh[d], Db + Df);
+      nbB[d] = hb ? fma(-b_.pos, pr.hh[d], -Db) : 0.0;
+      nbF[d] = hf ? fma(f_.neg, pr.hh[d], -Df) : 0.0;
     }
-    P += idt + nu * 0.5 * (Kinv[c_lo] + Kinv[c_hi]);
-    double b = own * idt - (p[c_hi] - p[c_lo]) * ax.ih[A] / pr.rho;
+    P += idt + pr.half_nu * (Kinv[c_lo] + Kinv[c_hi]);
+    double b = fma(own, idt, -(p[c_hi] - p[c_lo]) * pr.ih_irho[A]);
     if (A == pr.vert) {
       const double Tf = 0.5 * (T[c_lo] + T[c_hi]);
       const double Cf = 0.5 * (Cl[c_lo] + Cl[c_hi]);
@@ -176,8 +221,7 @@ __global__ void __launch_bounds__(kBlockA) k_assemble_cells(Params pr, Sys s, co
   const int nx = pr.nx, ny = pr.ny;
   const int n = (int)s.d.n;
   const int stride[3] = {1, nx, nx * ny};
-  const double alpha = pr.k / (pr.rho * pr.cp);
-  const double idt = 1.0 / pr.dt;
+  const double idt = pr.idt;
   for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
     const int i = r % nx, t = r / nx, j = t % ny, k = t / ny;
     const int idx[3] = {i, j, k};
@@ -187,20 +231,20 @@ __global__ void __launch_bounds__(kBlockA) k_assemble_cells(Params pr, Sys s, co
       if (a >= pr.dim) break;
       int fr[3] = {i, j, k};
       fr[a] += 1;
-      const double Fb = vel[a][fidx(pr, a, i, j, k)];
-      const double Ff = vel[a][fidx(pr, a, fr[0], fr[1], fr[2])];
+      const Split b_ = split(vel[a][fidx(pr, a, i, j, k)]);
+      const Split f_ = split(vel[a][fidx(pr, a, fr[0], fr[1], fr[2])]);
       const bool hb = idx[a] >= 1, hf = idx[a] <= ax.n[a] - 2;
-      double Db, Df;
+      double Db, Df;   // diffusion coefficient / h^2 of the back and front faces
       if (SOLUTE) {
-        Db = hb ? pr.Dl * (0.5 * (gl[r - stride[a]] + gl[r])) : 0.0;
-        Df = hf ? pr.Dl * (0.5 * (gl[r] + gl[r + stride[a]])) : 0.0;
+        Db = hb ? pr.half_Dl_ih2[a] * (gl[r - stride[a]] + gl[r]) : 0.0;
+        Df = hf ? pr.half_Dl_ih2[a] * (gl[r] + gl[r + stride[a]]) : 0.0;
       } else {
-        Db = hb ? alpha : 0.0;
-        Df = hf ? alpha : 0.0;
+        Db = hb ? pr.alpha_ih2[a] : 0.0;
+        Df = hf ? pr.alpha_ih2[a] : 0.0;
       }
-      m0 += (fmax(Ff, 0.0) - fmin(Fb, 0.0)) * ax.ih[a] + (Db + Df) * ax.ih2[a];
-      double cb = hb ? (-fmax(Fb, 0.0) * ax.ih[a] - Db * ax.ih2[a]) : 0.0;
-      double cf = hf ? (fmin(Ff, 0.0) * ax.ih[a] - Df * ax.ih2[a]) : 0.0;
+      m0 += fma(f_.pos - b_.neg, ax.ih[a], Db + Df);
+      double cb = hb ? fma(-b_.pos, ax.ih[a], -Db) : 0.0;
+      double cf = hf ? fma(f_.neg, ax.ih[a], -Df) : 0.0;
       if (SOLUTE) {
         cb = hb ? cb * Ag[r - stride[a]] : 0.0;
         cf = hf ? cf * Ag[r + stride[a]] : 0.0;
@@ -236,7 +280,7 @@ __global__ void __launch_bounds__(kBlockA) k_poisson_rhs(Params pr, const double
   const Axes ax = axes_of(pr);
   const int nx = pr.nx, ny = pr.ny;
   const int n = pr.nx * pr.ny * pr.nz;
-  const double scale = -pr.rho / pr.dt;
+  const double scale = pr.rhs_scale;
   for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
     const int i = r % nx, t = r / nx, j = t % ny, k = t / ny;
     double div = (us[fidx(pr, 0, i + 1, j, k)] - us[fidx(pr, 0, i, j, k)]) * ax.ih[0] +
@@ -252,12 +296,11 @@ __global__ void __launch_bounds__(kBlockA) k_project(Params pr, double* u, doubl
                                                     const double* __restrict__ vs,
                                                     const double* __restrict__ ws,
                                                     const double* __restrict__ pc, double* p) {
-  const Axes ax = axes_of(pr);
   const int nx = pr.nx, ny = pr.ny, nz = pr.nz;
   const int nu_ = (nx + 1) * ny * nz, nv = nx * (ny + 1) * nz, nw = (pr.dim == 3) ? nx * ny * (nz + 1) : 0;
   const int nc = nx * ny * nz;
   const int total = nu_ + nv + nw + nc;
-  const double kk = pr.dt / pr.rho;
+  const double kk = pr.proj_k;
   for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < total; q += gridDim.x * blockDim.x) {
     if (q < nu_ + nv + nw) {
       int d, r;
@@ -266,13 +309,16 @@ __global__ void __launch_bounds__(kBlockA) k_project(Params pr, double* u, doubl
       else { d = 2; r = q - nu_ - nv; }
       const int fx = nx + (d == 0), fy = ny + (d == 1);
       const int i = r % fx, t = r / fx, j = t % fy, k = t / fy;
-      const int idx[3] = {i, j, k};
+      // position along d, cell count along d and cell stride along d, without
+      // arrays indexed by the runtime axis (they would live in local memory)
+      const int f = (d == 0) ? i : (d == 1) ? j : k;
+      const int nd = (d == 0) ? nx : (d == 1) ? ny : nz;
+      const int sd = (d == 0) ? 1 : (d == 1) ? nx : nx * ny;
       double* out = (d == 0) ? u : (d == 1) ? v : w;
       const double* in = (d == 0) ? us : (d == 1) ? vs : ws;
-      if (idx[d] == 0 || idx[d] == ax.n[d]) { out[r] = 0.0; continue; }
-      int lo[3] = {i, j, k};
-      lo[d] -= 1;
-      const double grad = (pc[cidx(pr, i, j, k)] - pc[cidx(pr, lo[0], lo[1], lo[2])]) * ax.ih[d];
+      if (f == 0 || f == nd) { out[r] = 0.0; continue; }
+      const int c_hi = cidx(pr, i, j, k);
+      const double grad = (pc[c_hi] - pc[c_hi - sd]) * pr.ih[d];
       out[r] = in[r] - kk * grad;
     } else {
       const int c = q - (nu_ + nv + nw);
@@ -287,11 +333,11 @@ struct Phase {
 
 __device__ __forceinline__ Phase phase_of(const Params& pr, double C, double g) {
   Phase o;
-  const double denom = 1.0 + (1.0 - g) * (pr.kp - 1.0);
-  o.Cl = C / denom;                                  // Eq. 3.18
-  if (pr.has_eutectic) o.Cl = fmin(o.Cl, pr.Ce);
-  o.Ag = 1.0 / (1.0 - (1.0 - pr.kp) * (1.0 - g));  // Eq. 3.8, for the next solute step
   const double s = 1.0 - g;
+  // g + kp (1 - g) = 1 - (1 - kp)(1 - g): the denominator of Eq. 3.18 is 1/A_g (Eq. 3.8)
+  o.Ag = 1.0 / (1.0 - pr.lev_a * s);                 // Eq. 3.8, for the next solute step
+  o.Cl = C * o.Ag;                                   // Eq. 3.18
+  if (pr.has_eutectic) o.Cl = fmin(o.Cl, pr.Ce);
   o.Kinv = s * s / (pr.K0 * (g * g * g + pr.eps));  // Eq. 2.8, regularised
   return o;
 }
@@ -302,17 +348,17 @@ __global__ void __launch_bounds__(kBlockA) k_lever(Params pr, double* time, doub
                                                   double* Ag, int n) {
   if (blockIdx.x == 0 && threadIdx.x == 0) *time += pr.dt;
   const double kp = pr.kp, Tm = pr.Tm;
-  const double cpL = pr.cp / pr.L, Lcp = pr.L / pr.cp;
-  const double a = 1.0 - kp;
-  const double Te = pr.Tm + pr.m * pr.Ce;
+  const double cpL = pr.cpL, Lcp = pr.Lcp;
+  const double a = pr.lev_a;
+  const double Te = pr.Te;
   for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
     const double Ts = T[r], gn = gl[r], Cn = C[r];
     const double Tl = Tm + pr.m * Cn;                                       // Eq. 3.14
-    const double b = kp - gn * (1.0 - kp) + cpL * (1.0 - kp) * (Tm - Ts);  // Eq. 3.17
-    const double c = -(gn + cpL * Ts) * kp + cpL * (Tl - (1.0 - kp) * Tm);
-    const double sq = sqrt(fmax(b * b - 4.0 * a * c, 0.0));
+    const double b = kp - gn * a + pr.lev_cpLa * (Tm - Ts);                // Eq. 3.17
+    const double c = -(gn + cpL * Ts) * kp + cpL * (Tl - pr.lev_aTm);
+    const double sq = sqrt(fmax(b * b - pr.lev_4a * c, 0.0));
     // larger root of Eq. 3.16 (a > 0), in the form free of cancellation
-    double g = (b > 0.0) ? (2.0 * c) / (-b - sq) : (-b + sq) / (2.0 * a);
+    double g = (b > 0.0) ? (2.0 * c) / (-b - sq) : (-b + sq) / pr.lev_2a;
     g = fmin(fmax(g, 0.0), 1.0);
     double Tn = Ts - Lcp * (g - gn);                                         // Eq. 3.13
     if (pr.has_eutectic && Tn < Te && g > 0.0) {   // isothermal eutectic plateau
@@ -352,7 +398,17 @@ __global__ void __launch_bounds__(kBlockA) k_equilibrate(Params pr, const double
   }
 }
 
+__global__ void __launch_bounds__(kBlockA) k_to_f32(const double* __restrict__ src, float* dst, long long n) {
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x)
+    dst[q] = to_f32(src[q]);
+}
+
 }  // namespace
+
+cudaError_t launch_to_f32(const double* src, float* dst, long long n, cudaStream_t st) {
+  k_to_f32<<<grid_for(n), kBlockA, 0, st>>>(src, dst, n);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_assemble_momentum(int comp, const Params& pr, const Sys& sys, const double* const vel[3],
                                      double* ustar, const double* p, const double* T, const double* Cl,

@@ -211,6 +211,35 @@ void fill_params(ss_case* c, const ss_alloy* al) {
     pr.has_eutectic = al->Ce > 0.0;
   }
   const double h[3] = {pr.hx, pr.hy, pr.hz};
+  for (int a = 0; a < 3; ++a) {
+    pr.ih[a] = 1.0 / h[a];
+    pr.ih2[a] = pr.ih[a] * pr.ih[a];
+  }
+  pr.idt = 1.0 / pr.dt;
+  if (c->alloy_set || al) {
+    pr.nu = pr.mu / pr.rho;
+    pr.irho = 1.0 / pr.rho;
+    pr.alphaT = pr.k / (pr.rho * pr.cp);
+    pr.rhs_scale = -pr.rho / pr.dt;
+    pr.proj_k = pr.dt / pr.rho;
+    pr.cpL = pr.cp / pr.L;
+    pr.Lcp = pr.L / pr.cp;
+    pr.half_nu = 0.5 * pr.nu;
+    pr.lev_a = 1.0 - pr.kp;
+    pr.lev_cpLa = pr.cpL * pr.lev_a;
+    pr.lev_aTm = pr.lev_a * pr.Tm;
+    pr.lev_4a = 4.0 * pr.lev_a;
+    pr.lev_2a = 2.0 * pr.lev_a;
+    pr.Te = pr.Tm + pr.m * pr.Ce;
+    for (int a = 0; a < 3; ++a) {
+      pr.hh[a] = 0.5 * pr.ih[a];
+      pr.nu_ih2[a] = pr.nu * pr.ih2[a];
+      pr.two_nu_ih2[a] = 2.0 * pr.nu_ih2[a];
+      pr.ih_irho[a] = pr.ih[a] * pr.irho;
+      pr.alpha_ih2[a] = pr.alphaT * pr.ih2[a];
+      pr.half_Dl_ih2[a] = 0.5 * pr.Dl * pr.ih2[a];
+    }
+  }
   for (int q = 0; q < 6; ++q) {
     const int axis = q / 2;
     const ss_bc& bc = c->bc[q];
@@ -709,6 +738,37 @@ ss_status ss_get_system(ss_case* c, int sys, void* const* dst, int dst_is_device
     CUDA_TRY(cudaMemcpyAsync(dst[q], src[q], S.d.n * sizeof(double), kind, c->stream));
   }
   CUDA_TRY(cudaStreamSynchronize(c->stream));
+  return SS_OK;
+}
+
+ss_status ss_get_system_f32(ss_case* c, int sys, void* const* dst, int dst_is_device) {
+  STAGE_TRY(check_case(c));
+  if (!dst) return fail(SS_EINVAL, "dst is NULL");
+  if (sys < 0 || sys >= SS_NSYS) return fail(SS_EINVAL, "unknown system %d", sys);
+  if (sys == SS_SYS_P) return fail(SS_EINVAL, "the pressure system has no planes");
+  const Sys& S = c->sys[sys];
+  if (!S.af.P) return fail(SS_ESTATE, "FP32 planes exist in SS_MIXED cases only");
+  const float* src[8] = {S.af.P, S.af.W, S.af.E, S.af.S, S.af.N, S.af.B, S.af.T_, S.af.idiag};
+  const cudaMemcpyKind kind = dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  for (int q = 0; q < 8; ++q) {
+    if (!dst[q]) continue;
+    if ((q == 5 || q == 6) && c->pr.dim != 3) {
+      if (dst_is_device) CUDA_TRY(cudaMemsetAsync(dst[q], 0, S.d.n * sizeof(float), c->stream));
+      else memset(dst[q], 0, S.d.n * sizeof(float));
+      continue;
+    }
+    CUDA_TRY(cudaMemcpyAsync(dst[q], src[q], S.d.n * sizeof(float), kind, c->stream));
+  }
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  return SS_OK;
+}
+
+ss_status ss_convert_f64_to_f32(const double* src, float* dst, long long n, void* stream) {
+  if (n < 0) return fail(SS_EINVAL, "n must be >= 0");
+  if (n > 0 && (!src || !dst)) return fail(SS_EINVAL, "src/dst is NULL");
+  if (n == 0) return SS_OK;
+  cudaError_t e = launch_to_f32(src, dst, n, (cudaStream_t)stream);
+  if (e != cudaSuccess) return fail(SS_ECUDA, "convert: %s", cudaGetErrorString(e));
   return SS_OK;
 }
 

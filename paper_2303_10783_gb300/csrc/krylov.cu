@@ -80,6 +80,37 @@ __device__ __forceinline__ float4 ld4(const float* p, int m) { return reinterpre
 __device__ __forceinline__ float4 ldg4(const float* p, int m) { return __ldg(reinterpret_cast<const float4*>(p) + m); }
 __device__ __forceinline__ void st4(float* p, int m, float4 v) { reinterpret_cast<float4*>(p)[m] = v; }
 
+// Four consecutive rows 4m..4m+3 of y = A x for FP32 planes, in the same
+// order of operations as spmv_row. The y- and z-neighbour vectors are read as
+// float4 when their offsets keep 16-byte alignment (sy, sz multiples of 4),
+// else as four scalars; all loads are issued before the arithmetic.
+__device__ __forceinline__ float4 ldx4(const float* x, int r, bool aligned) {
+  if (aligned) return *reinterpret_cast<const float4*>(x + r);
+  return make_float4(x[r], x[r + 1], x[r + 2], x[r + 3]);
+}
+
+__device__ __forceinline__ float4 spmv4(const Planes<float>& a, const float* x, int m, int sy, int sz, int has_z,
+                                        bool ay, bool az) {
+  const int r = 4 * m;
+  const float4 P = ldg4(a.P, m), W = ldg4(a.W, m), E = ldg4(a.E, m), S = ldg4(a.S, m), N = ldg4(a.N, m);
+  const float4 xc = ld4(x, m);
+  const float xw = x[r - 1], xe = x[r + 4];
+  const float4 xs = ldx4(x, r - sy, ay), xn = ldx4(x, r + sy, ay);
+  float4 o;
+  o.x = P.x * xc.x; o.y = P.y * xc.y; o.z = P.z * xc.z; o.w = P.w * xc.w;
+  o.x = fmaf(W.x, xw, o.x); o.y = fmaf(W.y, xc.x, o.y); o.z = fmaf(W.z, xc.y, o.z); o.w = fmaf(W.w, xc.z, o.w);
+  o.x = fmaf(E.x, xc.y, o.x); o.y = fmaf(E.y, xc.z, o.y); o.z = fmaf(E.z, xc.w, o.z); o.w = fmaf(E.w, xe, o.w);
+  o.x = fmaf(S.x, xs.x, o.x); o.y = fmaf(S.y, xs.y, o.y); o.z = fmaf(S.z, xs.z, o.z); o.w = fmaf(S.w, xs.w, o.w);
+  o.x = fmaf(N.x, xn.x, o.x); o.y = fmaf(N.y, xn.y, o.y); o.z = fmaf(N.z, xn.z, o.z); o.w = fmaf(N.w, xn.w, o.w);
+  if (has_z) {
+    const float4 B = ldg4(a.B, m), T = ldg4(a.T_, m);
+    const float4 xb = ldx4(x, r - sz, az), xt = ldx4(x, r + sz, az);
+    o.x = fmaf(B.x, xb.x, o.x); o.y = fmaf(B.y, xb.y, o.y); o.z = fmaf(B.z, xb.z, o.z); o.w = fmaf(B.w, xb.w, o.w);
+    o.x = fmaf(T.x, xt.x, o.x); o.y = fmaf(T.y, xt.y, o.y); o.z = fmaf(T.z, xt.z, o.z); o.w = fmaf(T.w, xt.w, o.w);
+  }
+  return o;
+}
+
 struct CoreOut {
   int it;
   bool conv;
@@ -127,6 +158,7 @@ __device__ bool bcg_core(const Planes<T>& a, int n, int sy, int sz, int has_z, c
     return true;
   }
   const double thr = tol * out.bnorm;
+  const bool ay = (sy & 3) == 0, az = (sz & 3) == 0;
   double rho = tot.v[0], rho_old = 1.0, alpha = 1.0, omega = 1.0;
   int it = 0;
   bool conv = res <= thr;
@@ -157,7 +189,17 @@ __device__ bool bcg_core(const Planes<T>& a, int n, int sy, int sz, int has_z, c
     }
     if (!grid_barrier(st, gridDim.x, epoch)) return false;
     T s1 = T(0);
-    for (int i = t0; i < n; i += gs) {            // v = A y
+    tail = 0;                                     // v = A y
+    if constexpr (sizeof(T) == 4) {
+      const int n4 = n >> 2;
+      for (int m = t0; m < n4; m += gs) {
+        const float4 vv = spmv4(a, y, m, sy, sz, has_z, ay, az), hv = ld4(rh, m);
+        st4(v, m, vv);
+        s1 += (hv.x * vv.x + hv.y * vv.y) + (hv.z * vv.z + hv.w * vv.w);
+      }
+      tail = n4 << 2;
+    }
+    for (int i = tail + t0; i < n; i += gs) {
       const T vi = spmv_row(a, y, i, sy, sz, has_z);
       v[i] = vi;
       s1 += rh[i] * vi;
@@ -196,7 +238,18 @@ __device__ bool bcg_core(const Planes<T>& a, int n, int sy, int sz, int has_z, c
       break;
     }
     T s3 = T(0), s4 = T(0);
-    for (int i = t0; i < n; i += gs) {            // t = A z
+    tail = 0;                                     // t = A z
+    if constexpr (sizeof(T) == 4) {
+      const int n4 = n >> 2;
+      for (int m = t0; m < n4; m += gs) {
+        const float4 tv = spmv4(a, z, m, sy, sz, has_z, ay, az), rv = ld4(r, m);
+        st4(t, m, tv);
+        s3 += (tv.x * rv.x + tv.y * rv.y) + (tv.z * rv.z + tv.w * rv.w);
+        s4 += (tv.x * tv.x + tv.y * tv.y) + (tv.z * tv.z + tv.w * tv.w);
+      }
+      tail = n4 << 2;
+    }
+    for (int i = tail + t0; i < n; i += gs) {
       const T ti = spmv_row(a, z, i, sy, sz, has_z);
       t[i] = ti;
       s3 += ti * r[i];

@@ -58,8 +58,9 @@ struct MGArgs {
   Level<TP> lev[kMaxLevels];
   double cx, cy, cz;       // FP64 1/h^2 of the fine grid
   double* b;               // right-hand side (mean removed in place)
-  double *x, *r, *p, *q;   // FP64 vectors (solution, residual, CG vectors of the FP64 path)
-  TP *ri, *pi, *qi, *di;   // inner CG vectors (mixed path)
+  double *x, *r, *p, *p2, *q;  // FP64 vectors (solution, residual, CG vectors of the FP64 path;
+                               // p and p2 alternate as old and new search direction)
+  TP *ri, *pi, *pi2, *qi, *di; // inner CG vectors (mixed path)
   double tol;
   int max_it;
   int stat_index;
@@ -306,8 +307,55 @@ __device__ void restrict_to(const Level<TP>& F, const Level<TP>& Cl, const Table
 // neighbour on the child's side 1/4; clamping a neighbour beyond the wall
 // onto the parent gives the parent weight 1 there. An axis that is not
 // coarsened reads its one cell twice (3/4 + 1/4).
+//
+// On float4 levels (x is then always coarsened) a thread takes 4 consecutive
+// fine cells 4m..4m+3 of one x-row: their parents and x-neighbours are the
+// coarse cells i0/2 - 1 .. i0/2 + 2, four per coarse row, so 16 coarse loads
+// serve 4 cells. The arithmetic per cell is the same as in the scalar loop.
+template <typename TP>
+__device__ void prolong4(const Level<TP>& F, const Level<TP>& Cl, const float* e, float* out, Range rg) {
+  const float w0 = 0.75f, w1 = 0.25f;
+  const int n4 = F.n >> 2;
+  for (int m = rg.begin; m < n4; m += rg.stride) {
+    const Item4 it = item4(F, m);
+    const int j = it.j, k = it.k;
+    const int J0 = F.cy ? j >> 1 : j, K0 = F.cz ? k >> 1 : k;
+    const int J1 = F.cy ? clampi((j & 1) ? J0 + 1 : J0 - 1, 0, Cl.ny - 1) : j;
+    const int K1 = F.cz ? clampi((k & 1) ? K0 + 1 : K0 - 1, 0, Cl.nz - 1) : k;
+    const int I = it.i0 >> 1;
+    const int xa = clampi(I - 1, 0, Cl.nx - 1), xb = I, xc = I + 1, xd = clampi(I + 2, 0, Cl.nx - 1);
+    const float* rows[4] = {e + (size_t)(J0 + Cl.ny * K0) * Cl.nx, e + (size_t)(J1 + Cl.ny * K0) * Cl.nx,
+                            e + (size_t)(J0 + Cl.ny * K1) * Cl.nx, e + (size_t)(J1 + Cl.ny * K1) * Cl.nx};
+    float c[4][4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      c[q][0] = rows[q][xa];
+      c[q][1] = rows[q][xb];
+      c[q][2] = rows[q][xc];
+      c[q][3] = rows[q][xd];
+    }
+    const float4 cur = ld4(out, it.c);
+    // per lane: parent (I0) and x-neighbour (I1) column of the 4 coarse values
+    const int par[4] = {1, 1, 2, 2}, nbr[4] = {0, 2, 1, 3};
+    float o[4];
+#pragma unroll
+    for (int l = 0; l < 4; ++l) {
+      const float y0 = w0 * (w0 * c[0][par[l]] + w1 * c[0][nbr[l]]) + w1 * (w0 * c[1][par[l]] + w1 * c[1][nbr[l]]);
+      const float y1 = w0 * (w0 * c[2][par[l]] + w1 * c[2][nbr[l]]) + w1 * (w0 * c[3][par[l]] + w1 * c[3][nbr[l]]);
+      o[l] = comp(cur, l) + (w0 * y0 + w1 * y1);
+    }
+    st4(out, it.c, make_float4(o[0], o[1], o[2], o[3]));
+  }
+}
+
 template <typename TP>
 __device__ void prolong_add(const Level<TP>& F, const Level<TP>& Cl, const TP* e, TP* out, Range rg) {
+  if constexpr (sizeof(TP) == 4) {
+    if (F.v4 && F.cx) {
+      prolong4(F, Cl, (const float*)e, (float*)out, rg);
+      return;
+    }
+  }
   constexpr int U = Batch<TP>::U;
   const TP w0 = TP(0.75), w1 = TP(0.25);
   for (int base = rg.begin; base < F.n; base += U * rg.stride) {
@@ -488,6 +536,68 @@ __device__ __forceinline__ void zr_sums(const Level<TP>& L0, const TV* r, int t0
   }
 }
 
+// The new search direction p' = (z - mz) + beta p at one point (beta and p
+// unused in the first iteration, where p' = z - mz).
+template <typename T>
+struct Dir {
+  const T* z;
+  const T* p;
+  T mz, beta;
+  bool first;
+  __device__ __forceinline__ T at(int c) const { return first ? z[c] - mz : (z[c] - mz) + beta * p[c]; }
+  __device__ __forceinline__ float4 at4(int c) const {
+    const float4 a = ld4((const float*)z, c);
+    float4 o = make_float4(a.x - (float)mz, a.y - (float)mz, a.z - (float)mz, a.w - (float)mz);
+    if (!first) {
+      const float4 b = ld4((const float*)p, c);
+      const float bt = (float)beta;
+      o.x = o.x + bt * b.x; o.y = o.y + bt * b.y; o.z = o.z + bt * b.z; o.w = o.w + bt * b.w;
+    }
+    return o;
+  }
+};
+
+// load_nb of the direction p' (same sums, same order, as load_nb of a stored p')
+template <typename T>
+__device__ __forceinline__ Nb<T> load_nb_dir(const Dir<T>& d, int c, int i, int j, int k, int nx, int ny, int nz) {
+  const int sy = nx, sz = nx * ny;
+  Nb<T> o;
+  o.c0 = d.at(c);
+  const T w = i > 0 ? d.at(c - 1) : T(0), e = i < nx - 1 ? d.at(c + 1) : T(0);
+  const T s_ = j > 0 ? d.at(c - sy) : T(0), n_ = j < ny - 1 ? d.at(c + sy) : T(0);
+  T b_ = T(0), t_ = T(0);
+  if (nz > 1) {
+    b_ = k > 0 ? d.at(c - sz) : T(0);
+    t_ = k < nz - 1 ? d.at(c + sz) : T(0);
+  }
+  o.sx = w + e;
+  o.sy = s_ + n_;
+  o.sz = b_ + t_;
+  return o;
+}
+
+// lap4 of the direction p' (same arithmetic as lap4 of a stored p')
+__device__ __forceinline__ void lap4_dir(const Dir<float>& d, const Item4& it, int nx, int ny, int nz, float ax,
+                                         float ay, float az, const float* dg, const int code[4], float in[4],
+                                         float Av[4]) {
+  const int c = it.c, sz = nx * ny;
+  const float4 c4 = d.at4(c);
+  const float W = it.i0 > 0 ? d.at(c - 1) : 0.f, E = it.i0 + 4 < nx ? d.at(c + 4) : 0.f;
+  const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  const float4 S = it.j > 0 ? d.at4(c - nx) : z4, N = it.j < ny - 1 ? d.at4(c + nx) : z4;
+  const float4 B = (nz > 1 && it.k > 0) ? d.at4(c - sz) : z4, T = (nz > 1 && it.k < nz - 1) ? d.at4(c + sz) : z4;
+  in[0] = c4.x; in[1] = c4.y; in[2] = c4.z; in[3] = c4.w;
+  const float sx[4] = {W + c4.y, c4.x + c4.z, c4.y + c4.w, c4.z + E};
+#pragma unroll
+  for (int l = 0; l < 4; ++l) {
+    float acc = dg[code[l]] * in[l];
+    acc = fmaf(-ax, sx[l], acc);
+    acc = fmaf(-ay, comp(S, l) + comp(N, l), acc);
+    acc = fmaf(-az, comp(B, l) + comp(T, l), acc);
+    Av[l] = acc;
+  }
+}
+
 struct PcgOut {
   int it;
   bool conv;
@@ -500,11 +610,18 @@ struct PcgOut {
 // diagonal table dg of type TV. z is kept orthogonal to the constants (the
 // Neumann null space): its mean is removed, so p and x never accumulate a
 // constant that would swamp the FP32 arithmetic of the inner solve.
+//
+// One iteration has two grid-wide reductions and the V-cycle, and no other
+// barrier: the new search direction p' = (z - mz) + beta p is formed on the
+// fly wherever q = A p' needs it (z is complete after the reduction that
+// gave beta), and written to the other of the two p buffers, so no block
+// overwrites an old p value that another block still reads. The arithmetic
+// is the same, operation for operation, as forming p' in a pass of its own.
 // Reduction slots 0..11.
 template <typename TV, typename TP>
 __device__ __noinline__ bool pcg(const Ctx& X, const Level<TP>* glev, const Level<TP>* slev, const Tables<TP>& tb,
-                    const double* b, double bscale, TV* x, TV* r, TV* p, TV* q, TV cx, TV cy, TV cz, const TV* dg,
-                    double tol, int max_it, unsigned int& epoch, PcgOut& out) {
+                    const double* b, double bscale, TV* x, TV* r, TV* p_a, TV* p_b, TV* q, TV cx, TV cy, TV cz,
+                    const TV* dg, double tol, int max_it, unsigned int& epoch, PcgOut& out) {
   constexpr int U = Batch<TV>::U;
   const Level<TP>& L0 = glev[0];
   const int nx = L0.nx, ny = L0.ny, nz = L0.nz, n = L0.n;
@@ -525,31 +642,42 @@ __device__ __noinline__ bool pcg(const Ctx& X, const Level<TP>* glev, const Leve
   if (!grid_sum<4>(s0, X.partial, X.max_blocks, 0, X.st, epoch, o0)) return false;
   const double inv_n = 1.0 / (double)n;
   double mz = o0.v[2] * inv_n;
-  for (int c = t0; c < n; c += gsz) p[c] = (TV)L0.t[c] - (TV)mz;
-  if (!grid_barrier(X.st, gridDim.x, epoch)) return false;
   out.bnorm = sqrt(o0.v[1]);
   double rz = o0.v[0] - mz * o0.v[3], res = out.bnorm;
   const double thr = tol * out.bnorm;
   int it = 0;
   bool conv = (out.bnorm == 0.0);
+  TV beta = TV(0);
+  TV* p_old = p_a;
+  TV* p = p_b;
+  const bool v4 = (sizeof(TV) == 4) && L0.v4;
+  // FP64 vectors: forming p' at the 7 stencil points would cost ~14 FP64
+  // operations per cell on a pipe far slower than the FP32 one, so the FP64
+  // path keeps p' in a pass of its own (and one more barrier).
+  constexpr bool kFused = sizeof(TV) == 4;
+  if constexpr (!kFused) {
+    for (int c = t0; c < n; c += gsz) p[c] = (TV)L0.t[c] - (TV)mz;
+    if (!grid_barrier(X.st, gridDim.x, epoch)) return false;
+  }
   while (!conv && it < max_it && isfinite(res)) {
+    const Dir<TV> dir{(const TV*)L0.t, p_old, (TV)mz, beta, it == 0};
     ++it;
     TV s1 = TV(0);
-    const bool v4 = (sizeof(TV) == 4) && L0.v4;
     if constexpr (sizeof(TV) == 4) {
       if (v4) {
-        for (int m = t0; m < (n >> 2); m += gsz) {    // q = A p, 4 cells per thread
+        for (int m = t0; m < (n >> 2); m += gsz) {    // p' and q = A p', 4 cells per thread
           const Item4 itm = item4(L0, m);
           int code[4];
           codes4(L0, itm, code);
           float pin[4], qv[4];
-          lap4((const float*)p, itm, nx, ny, nz, (float)cx, (float)cy, (float)cz, (const float*)dg, code, pin, qv);
+          lap4_dir(dir, itm, nx, ny, nz, (float)cx, (float)cy, (float)cz, (const float*)dg, code, pin, qv);
+          st4((float*)p, itm.c, make_float4(pin[0], pin[1], pin[2], pin[3]));
           st4((float*)q, itm.c, make_float4(qv[0], qv[1], qv[2], qv[3]));
           s1 += (pin[0] * qv[0] + pin[1] * qv[1]) + (pin[2] * qv[2] + pin[3] * qv[3]);
         }
       }
     }
-    for (int base = v4 ? n : t0; base < n; base += U * gsz) {   // q = A p
+    for (int base = v4 ? n : t0; base < n; base += U * gsz) {   // p' and q = A p'
       Nb<TV> nb[U];
       int code[U];
 #pragma unroll
@@ -559,7 +687,7 @@ __device__ __noinline__ bool pcg(const Ctx& X, const Level<TP>* glev, const Leve
           int i, j, k;
           decompose3(c, L0.fx, L0.fy, i, j, k);
           code[u] = code_of(L0, i, j, k);
-          nb[u] = load_nb(p, c, i, j, k, nx, ny, nz);
+          nb[u] = kFused ? load_nb_dir(dir, c, i, j, k, nx, ny, nz) : load_nb(p, c, i, j, k, nx, ny, nz);
         }
       }
 #pragma unroll
@@ -567,6 +695,7 @@ __device__ __noinline__ bool pcg(const Ctx& X, const Level<TP>* glev, const Leve
         const int c = base + u * gsz;
         if (c < n) {
           const TV qc = apply_nb(nb[u], cx, cy, cz, dg[code[u]]);
+          if (kFused) p[c] = nb[u].c0;
           q[c] = qc;
           s1 += nb[u].c0 * qc;
         }
@@ -631,37 +760,17 @@ __device__ __noinline__ bool pcg(const Ctx& X, const Level<TP>* glev, const Leve
     if (conv) break;
     mz = o2.v[2] * inv_n;
     const double rz_new = o2.v[0] - mz * o2.v[3];
-    const TV beta = (TV)(rz_new / rz);
-    const TV mzt = (TV)mz;
+    beta = (TV)(rz_new / rz);
     rz = rz_new;
-    if constexpr (sizeof(TV) == 4) {
-      if (v4) {
-        for (int m = t0; m < (n >> 2); m += gsz) {
-          const float4 zv = ld4((const float*)L0.t, 4 * m), pv = ld4((const float*)p, 4 * m);
-          float4 po;
-          po.x = (zv.x - mzt) + beta * pv.x; po.y = (zv.y - mzt) + beta * pv.y;
-          po.z = (zv.z - mzt) + beta * pv.z; po.w = (zv.w - mzt) + beta * pv.w;
-          st4((float*)p, 4 * m, po);
-        }
-      }
+    if constexpr (kFused) {
+      TV* tmp = p_old;  // this iteration's p' is the next iteration's old p
+      p_old = p;
+      p = tmp;
+    } else {
+      const TV mzt = (TV)mz;
+      for (int c = t0; c < n; c += gsz) p[c] = ((TV)L0.t[c] - mzt) + beta * p[c];
+      if (!grid_barrier(X.st, gridDim.x, epoch)) return false;
     }
-    for (int base = v4 ? n : t0; base < n; base += U * gsz) {
-      TV zv[U], pv[U];
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const int c = base + u * gsz;
-        if (c < n) {
-          zv[u] = (TV)L0.t[c];
-          pv[u] = p[c];
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const int c = base + u * gsz;
-        if (c < n) p[c] = (zv[u] - mzt) + beta * pv[u];
-      }
-    }
-    if (!grid_barrier(X.st, gridDim.x, epoch)) return false;
   }
   out.it = it;
   out.conv = conv;
@@ -724,8 +833,8 @@ __global__ void __launch_bounds__(kBlock, 1) k_pcg_mg(MGArgs<TP> A) {
   // TP = double: the FP64 path; TP = float: the mixed path (refinement)
   if constexpr (sizeof(TP) == 8) {
     PcgOut o;
-    if (!pcg<double, TP>(X, glev, slev, tb, b, 1.0, x, r, A.p, A.q, A.cx, A.cy, A.cz, tb.diag64, A.tol, A.max_it,
-                         epoch, o))
+    if (!pcg<double, TP>(X, glev, slev, tb, b, 1.0, x, r, A.p, A.p2, A.q, A.cx, A.cy, A.cz, tb.diag64, A.tol,
+                         A.max_it, epoch, o))
       return;
     iters = o.it;
     conv = o.conv;
@@ -749,8 +858,8 @@ __global__ void __launch_bounds__(kBlock, 1) k_pcg_mg(MGArgs<TP> A) {
       ++refs;
       // the inner solve sees the residual scaled to unit norm (no FP32 under- or overflow)
       PcgOut io;
-      if (!pcg<TP, TP>(X, glev, slev, tb, r, 1.0 / rn, A.di, A.ri, A.pi, A.qi, L0.ax, L0.ay, L0.az, tb.diag[0],
-                       kInnerTolP, A.max_it - iters, epoch, io))
+      if (!pcg<TP, TP>(X, glev, slev, tb, r, 1.0 / rn, A.di, A.ri, A.pi, A.pi2, A.qi, L0.ax, L0.ay, L0.az,
+                       tb.diag[0], kInnerTolP, A.max_it - iters, epoch, io))
         return;
       iters += io.it;
       for (int c = t0; c < n; c += gsz) x[c] += rn * (double)A.di[c];
@@ -825,9 +934,9 @@ MGArgs<TP> make_args(const MGPlan& pl, const Params& pr, double* b, double* x, c
   A.cy = 1.0 / (pr.hy * pr.hy);
   A.cz = pr.dim == 3 ? 1.0 / (pr.hz * pr.hz) : 0.0;
   A.b = b; A.x = x;
-  A.r = sc.v[0]; A.p = sc.v[4]; A.q = sc.v[3];
+  A.r = sc.v[0]; A.p = sc.v[4]; A.p2 = sc.v[5]; A.q = sc.v[3];
   if (pl.fp32) {
-    A.ri = (TP*)sc.f[1]; A.pi = (TP*)sc.f[2]; A.qi = (TP*)sc.f[3]; A.di = (TP*)sc.f[4];
+    A.ri = (TP*)sc.f[1]; A.pi = (TP*)sc.f[2]; A.pi2 = (TP*)sc.f[5]; A.qi = (TP*)sc.f[3]; A.di = (TP*)sc.f[4];
   }
   A.tol = ctl.tol;
   A.max_it = ctl.max_it;

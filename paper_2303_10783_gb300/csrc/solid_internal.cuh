@@ -75,6 +75,27 @@ struct Params {
   // U = 1/(1/h_c + h/2k), rate 0; Dirichlet: coef = 2k/(rho cp h^2).
   double wall_coef[6], wall_T0[6], wall_rate[6];
   int slip[6];   // 1: free-slip wall (tangential ghost = interior), 0: no-slip
+  // Launch constants formed once on the host (IEEE division rounds the same
+  // there): the FP64 pipe is the bound of the assembly kernels, so no thread
+  // recomputes them.
+  double ih[3], ih2[3];      // 1/h and 1/h^2 per axis
+  double idt;                // 1/dt
+  double nu;                 // mu/rho
+  double irho;               // 1/rho
+  double alphaT;             // k/(rho cp)
+  double rhs_scale;          // -rho/dt (pressure right-hand side)
+  double proj_k;             // dt/rho (projection)
+  double cpL, Lcp;           // cp/L and L/cp (lever rule)
+  double hh[3];              // 0.5/h (face averages of the advecting velocity folded in)
+  double nu_ih2[3];          // nu/h^2 (momentum diffusion across one face)
+  double two_nu_ih2[3];      // 2 nu/h^2 (no-slip wall face: ghost = -interior)
+  double half_nu;            // nu/2 (face mean of the Darcy term)
+  double ih_irho[3];         // 1/(h rho) (pressure gradient)
+  double alpha_ih2[3];       // k/(rho cp h^2) (energy diffusion across one face)
+  double half_Dl_ih2[3];     // D_l/(2 h^2) (solute diffusion: face mean of g_l D_l)
+  // lever rule (Eq. 3.16-3.17): a = 1 - kp and products of constants with it
+  double lev_a, lev_cpLa, lev_aTm, lev_4a, lev_2a;
+  double Te;                 // eutectic temperature Tm + m Ce
 };
 
 // Krylov scratch: 8 FP64 vectors + 8 FP32 vectors, each of `nmax` rows with guards.
@@ -252,6 +273,8 @@ cudaError_t launch_lever(const Params& pr, double* time, double* T, double* gl, 
                          double* Cs, double* Kinv, double* Ag, cudaStream_t s);
 // from_T: recompute g_l from (T, C) in equilibrium; write_cl: recompute C_l, C_s.
 // K^{-1} and A_g are always refreshed from g_l.
+// The FP64 -> FP32 rounding of the FP32 plane copies, on n device values.
+cudaError_t launch_to_f32(const double* src, float* dst, long long n, cudaStream_t s);
 cudaError_t launch_equilibrate(const Params& pr, const double* T, const double* C, double* gl, double* Cl,
                                double* Cs, double* Kinv, double* Ag, int from_T, int write_cl, cudaStream_t s);
 

@@ -88,6 +88,8 @@ def _declare(lib):
         "ss_assemble": [P, ctypes.c_int],
         "ss_solve": [P, ctypes.c_int],
         "ss_get_system": [P, ctypes.c_int, ctypes.POINTER(P), ctypes.c_int],
+        "ss_get_system_f32": [P, ctypes.c_int, ctypes.POINTER(P), ctypes.c_int],
+        "ss_convert_f64_to_f32": [P, P, ctypes.c_longlong, P],
         "ss_project": [P],
         "ss_lever": [P],
         "ss_set_profiling": [P, ctypes.c_int],
@@ -290,6 +292,18 @@ class Case:
         check(self.lib.ss_get_system(self.h, SYS_ID[sys], ptrs, 0))
         return out
 
+    def get_system_f32(self, sys):
+        """Dict of the FP32 planes P, W, E, S, N, B, T and inverse diagonal "idiag" (mixed cases)."""
+        shape = self.sys_shapes[sys]
+        ptrs = (ctypes.c_void_p * 8)()
+        out = {}
+        for q, name in enumerate(PLANE_NAMES[:7] + ("idiag",)):
+            a = np.empty(shape, dtype=np.float32)
+            ptrs[q] = a.ctypes.data
+            out[name] = a
+        check(self.lib.ss_get_system_f32(self.h, SYS_ID[sys], ptrs, 0))
+        return out
+
     def project(self):
         check(self.lib.ss_project(self.h))
 
@@ -325,3 +339,13 @@ class Case:
             self.close()
         except Exception:
             pass
+
+
+def convert_f64_to_f32(src):
+    """The library's FP64 -> FP32 plane rounding applied to a CUDA float64 tensor."""
+    import torch
+    src = src.contiguous()
+    dst = torch.empty(src.shape, dtype=torch.float32, device=src.device)
+    check(load().ss_convert_f64_to_f32(ctypes.c_void_p(src.data_ptr()), ctypes.c_void_p(dst.data_ptr()),
+                                       src.numel(), ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)))
+    return dst

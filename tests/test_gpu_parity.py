@@ -416,3 +416,47 @@ def test_tiny_right_hand_side(lib, prec):
     pref = oracle.solve_poisson(g, oracle.poisson_rhs(g, [f["u"], f["v"], f["w"]], case))
     assert _rel(pc, pref) < 1e-10
     c.close()
+
+
+def test_fp32_planes_are_the_rounded_fp64_planes(lib):
+    """The inner solves of the mixed path use the FP64 planes rounded to
+    nearest (ties to even) and the FP32 reciprocal of the rounded diagonal."""
+    case = cases.box_3d(27, 19, 13, robin={"x-": (400.0, 298.0), "z+": (60.0, 300.0)})
+    c = solid.Case(case, precision=solid.SS_MIXED)
+    c.set_fields(cases.random_state(case, 21))
+    for name in ("u", "v", "w", "C", "T"):
+        c.assemble(name)
+        a64 = c.get_system(name)
+        a32 = c.get_system_f32(name)
+        for k in oracle.PLANES:
+            assert np.array_equal(a32[k].view(np.uint32), a64[k].astype(np.float32).view(np.uint32)), (name, k)
+        expect = (np.float32(1.0) / a32["P"]).astype(np.float32)
+        assert np.array_equal(a32["idiag"].view(np.uint32), expect.view(np.uint32)), name
+    c.close()
+
+
+def test_fp64_to_fp32_rounding_matches_ieee(lib):
+    """The integer-pipe FP64 -> FP32 rounding of the plane copies equals IEEE
+    round-to-nearest-even on random values of every magnitude, on exact ties
+    (both parities), at the normal/subnormal and overflow edges, and on zeros,
+    infinities and NaN."""
+    import torch
+    rng = np.random.default_rng(5)
+    vals = [rng.standard_normal(20000) * np.exp2(rng.integers(-160, 160, 20000).astype(np.float64))]
+    f = rng.standard_normal(5000).astype(np.float32)
+    ulp = np.spacing(np.abs(f)).astype(np.float64)
+    vals += [f.astype(np.float64) + 0.5 * ulp * s for s in (1.0, -1.0)]            # exact ties
+    vals += [f.astype(np.float64) + 0.5 * ulp * (1.0 + 2.0 ** -20)]               # just above a tie
+    fmax = float(np.finfo(np.float32).max)
+    tiny = float(np.finfo(np.float32).tiny)
+    edges = [0.0, -0.0, np.inf, -np.inf, fmax, -fmax, fmax * (1 + 2.0 ** -25), fmax * (1 + 2.0 ** -23),
+             tiny, -tiny, tiny * (1 - 2.0 ** -30), tiny * 0.75, 2.0 ** -149, 2.0 ** -150, 2.0 ** -151, 1e-300,
+             1e300, 1.0, 1.0 + 2.0 ** -24, 1.0 + 3 * 2.0 ** -24, 3.4e38, np.nan]
+    vals.append(np.array(edges))
+    x = np.concatenate(vals)
+    got = solid.convert_f64_to_f32(torch.from_numpy(x).cuda()).cpu().numpy()
+    with np.errstate(over="ignore"):
+        ref = x.astype(np.float32)
+    nan = np.isnan(ref)
+    assert np.array_equal(np.isnan(got), nan)
+    assert np.array_equal(got[~nan].view(np.uint32), ref[~nan].view(np.uint32))
