@@ -38,6 +38,7 @@ struct BcgArgs {
   double tol;
   int max_it;
   int stat_index;
+  double inner_tol;        // relative tolerance of each FP32 inner solve (mixed path)
   BcgVec<double> v64;
   BcgVec<float> v32;
   float* d32;              // inner correction (mixed path)
@@ -310,10 +311,10 @@ __global__ void __launch_bounds__(kBlock, 2) k_bicgstab(BcgArgs A) {
 
 // Mixed precision: FP64 iterative refinement around an FP32 BiCGSTAB on the
 // FP32 copies of the planes. Each sweep forms the FP64 residual
-// r = b - A x with the FP64 planes, solves A d = r in FP32 to a relative
-// 1e-5, and adds d to the FP64 iterate; it stops when the FP64 residual
-// meets tol (the same test as the FP64 path).
-constexpr double kInnerTol = 1.0e-5;
+// r = b - A x with the FP64 planes, solves A d = r in FP32 to the relative
+// inner tolerance chosen per system by the caller, and adds d to the FP64
+// iterate; it stops when the FP64 residual meets tol (the same test as the
+// FP64 path).
 constexpr int kMaxRefine = 12;
 
 __global__ void __launch_bounds__(kBlock, 2) k_bicgstab_ir(BcgArgs A) {
@@ -343,7 +344,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_bicgstab_ir(BcgArgs A) {
     const double inv = 1.0 / rn;
     for (int i = t0; i < n; i += gs) A.v32.r[i] = (float)(r64[i] * inv);
     CoreOut o;
-    if (!bcg_core<float>(A.sys.af, n, sy, sz, A.has_z, A.v32.r, A.d32, true, A.v32, kInnerTol, A.max_it - total,
+    if (!bcg_core<float>(A.sys.af, n, sy, sz, A.has_z, A.v32.r, A.d32, true, A.v32, A.inner_tol, A.max_it - total,
                          A.partial, A.max_blocks, A.st, epoch, o))
       return;
     total += o.it;
@@ -536,6 +537,7 @@ cudaError_t launch_bicgstab(const Sys& sys, int has_z, const SolverCtl& ctl, Scr
   A.tol = ctl.tol;
   A.max_it = ctl.max_it;
   A.stat_index = ctl.stat_index;
+  A.inner_tol = ctl.inner_tol;
   A.v64 = {sc.v[0], sc.v[1], sc.v[2], sc.v[3], sc.v[4], sc.v[5], sc.v[6]};
   A.v32 = {sc.f[0], sc.f[1], sc.f[2], sc.f[3], sc.f[4], sc.f[5], sc.f[6]};
   A.d32 = sc.f[7];

@@ -33,7 +33,6 @@ namespace solid {
 namespace {
 
 constexpr double kOmega = 0.9;
-constexpr double kInnerTolP = 1.0e-5;
 constexpr int kMaxRefineP = 12;
 
 template <typename TP>
@@ -62,6 +61,7 @@ struct MGArgs {
                                // p and p2 alternate as old and new search direction)
   TP *ri, *pi, *pi2, *qi, *di; // inner CG vectors (mixed path)
   double tol;
+  double inner_tol;        // relative tolerance of each FP32 inner solve (mixed path)
   int max_it;
   int stat_index;
   double* partial;
@@ -859,7 +859,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_pcg_mg(MGArgs<TP> A) {
       // the inner solve sees the residual scaled to unit norm (no FP32 under- or overflow)
       PcgOut io;
       if (!pcg<TP, TP>(X, glev, slev, tb, r, 1.0 / rn, A.di, A.ri, A.pi, A.pi2, A.qi, L0.ax, L0.ay, L0.az,
-                       tb.diag[0], kInnerTolP, A.max_it - iters, epoch, io))
+                       tb.diag[0], A.inner_tol, A.max_it - iters, epoch, io))
         return;
       iters += io.it;
       for (int c = t0; c < n; c += gsz) x[c] += rn * (double)A.di[c];
@@ -939,6 +939,7 @@ MGArgs<TP> make_args(const MGPlan& pl, const Params& pr, double* b, double* x, c
     A.ri = (TP*)sc.f[1]; A.pi = (TP*)sc.f[2]; A.pi2 = (TP*)sc.f[5]; A.qi = (TP*)sc.f[3]; A.di = (TP*)sc.f[4];
   }
   A.tol = ctl.tol;
+  A.inner_tol = ctl.inner_tol;
   A.max_it = ctl.max_it;
   A.stat_index = ctl.stat_index;
   A.partial = sc.partial;
