@@ -179,7 +179,7 @@ void plan(ss_case* c, Planner& pl) {
     }
   }
   for (int q = 0; q < 8; ++q) c->sc.v[q] = pl.vec<double>(nmax);
-  for (int q = 0; q < 8; ++q) c->sc.f[q] = (c->g.precision == SS_MIXED) ? pl.vec<float>(nmax) : nullptr;
+  for (int q = 0; q < 9; ++q) c->sc.f[q] = (c->g.precision == SS_MIXED) ? pl.vec<float>(nmax) : nullptr;
   c->sc.max_blocks = max_cooperative_blocks();
   c->sc.partial = pl.raw<double>((size_t)kMaxRedSlots * c->sc.max_blocks * sizeof(double));
 }

@@ -32,6 +32,11 @@ struct BcgVec {
   T *r, *rh, *p, *v, *y, *z, *t;
 };
 
+// vectors of the fused FP32 inner solve (bcg_fused): r/s pair, rhat, p pair, v pair, t
+struct FusedVec {
+  float *r0, *r1, *rh, *p0, *p1, *v0, *v1, *t;
+};
+
 struct BcgArgs {
   Sys sys;
   int has_z;
@@ -41,6 +46,7 @@ struct BcgArgs {
   double inner_tol;        // relative tolerance of each FP32 inner solve (mixed path)
   BcgVec<double> v64;
   BcgVec<float> v32;
+  FusedVec f32;            // vectors of the fused FP32 inner solve (mixed path)
   float* d32;              // inner correction (mixed path)
   double* partial;
   int max_blocks;
@@ -298,6 +304,227 @@ __device__ bool bcg_core(const Planes<T>& a, int n, int sy, int sz, int has_z, c
   return true;
 }
 
+// ---- FP32 inner solve with three grid-wide synchronisations per iteration.
+//
+// The same Jacobi-preconditioned BiCGSTAB as bcg_core<float>, with the
+// preconditioned vectors never stored: y = D^-1 (r + beta (p - omega v)) and
+// z = D^-1 (r - alpha v) are formed wherever the SpMV needs them (the row and
+// its six neighbours), from vectors that are complete after the previous
+// reduction. So the p and y update merges into v = A y, and the s and z
+// update into t = A z: per iteration three passes and three reductions
+// instead of five. Every pass writes only buffers that no thread reads in
+// the same pass: p and v alternate between two buffers each, r and s share
+// a pair (s is written beside r; the new r overwrites s in place, row by row).
+// The FP64 solver keeps bcg_core: forming y and z at seven points would cost
+// FP64-pipe work that the saved passes do not repay.
+struct YDir {   // y = D^-1 (r + beta (p - om v))
+  const float *r, *p, *v, *d;
+  float beta, om;
+  __device__ __forceinline__ float at(int q) const { return d[q] * (r[q] + beta * (p[q] - om * v[q])); }
+  __device__ __forceinline__ float4 at4(int q) const {   // q multiple of 4
+    const float4 a = *reinterpret_cast<const float4*>(r + q), b = *reinterpret_cast<const float4*>(p + q);
+    const float4 c = *reinterpret_cast<const float4*>(v + q), e = __ldg(reinterpret_cast<const float4*>(d + q));
+    return make_float4(e.x * (a.x + beta * (b.x - om * c.x)), e.y * (a.y + beta * (b.y - om * c.y)),
+                       e.z * (a.z + beta * (b.z - om * c.z)), e.w * (a.w + beta * (b.w - om * c.w)));
+  }
+};
+
+struct ZDir {   // z = D^-1 (r - al v)
+  const float *r, *v, *d;
+  float al;
+  __device__ __forceinline__ float at(int q) const { return d[q] * (r[q] - al * v[q]); }
+  __device__ __forceinline__ float4 at4(int q) const {
+    const float4 a = *reinterpret_cast<const float4*>(r + q), c = *reinterpret_cast<const float4*>(v + q);
+    const float4 e = __ldg(reinterpret_cast<const float4*>(d + q));
+    return make_float4(e.x * (a.x - al * c.x), e.y * (a.y - al * c.y), e.z * (a.z - al * c.z),
+                       e.w * (a.w - al * c.w));
+  }
+};
+
+template <class F>
+__device__ __forceinline__ float4 dir4(const F& f, int q, bool aligned) {
+  if (aligned) return f.at4(q);
+  return make_float4(f.at(q), f.at(q + 1), f.at(q + 2), f.at(q + 3));
+}
+
+// rows 4m..4m+3 of A f, the centre values xc given (same order of operations as spmv4)
+template <class F>
+__device__ __forceinline__ float4 spmv4_dir(const Planes<float>& a, const F& f, float4 xc, int m, int sy, int sz,
+                                            int has_z, bool ay, bool az) {
+  const int r = 4 * m;
+  const float4 P = ldg4(a.P, m), W = ldg4(a.W, m), E = ldg4(a.E, m), S = ldg4(a.S, m), N = ldg4(a.N, m);
+  const float xw = f.at(r - 1), xe = f.at(r + 4);
+  const float4 xs = dir4(f, r - sy, ay), xn = dir4(f, r + sy, ay);
+  float4 o;
+  o.x = P.x * xc.x; o.y = P.y * xc.y; o.z = P.z * xc.z; o.w = P.w * xc.w;
+  o.x = fmaf(W.x, xw, o.x); o.y = fmaf(W.y, xc.x, o.y); o.z = fmaf(W.z, xc.y, o.z); o.w = fmaf(W.w, xc.z, o.w);
+  o.x = fmaf(E.x, xc.y, o.x); o.y = fmaf(E.y, xc.z, o.y); o.z = fmaf(E.z, xc.w, o.z); o.w = fmaf(E.w, xe, o.w);
+  o.x = fmaf(S.x, xs.x, o.x); o.y = fmaf(S.y, xs.y, o.y); o.z = fmaf(S.z, xs.z, o.z); o.w = fmaf(S.w, xs.w, o.w);
+  o.x = fmaf(N.x, xn.x, o.x); o.y = fmaf(N.y, xn.y, o.y); o.z = fmaf(N.z, xn.z, o.z); o.w = fmaf(N.w, xn.w, o.w);
+  if (has_z) {
+    const float4 B = ldg4(a.B, m), T = ldg4(a.T_, m);
+    const float4 xb = dir4(f, r - sz, az), xt = dir4(f, r + sz, az);
+    o.x = fmaf(B.x, xb.x, o.x); o.y = fmaf(B.y, xb.y, o.y); o.z = fmaf(B.z, xb.z, o.z); o.w = fmaf(B.w, xb.w, o.w);
+    o.x = fmaf(T.x, xt.x, o.x); o.y = fmaf(T.y, xt.y, o.y); o.z = fmaf(T.z, xt.z, o.z); o.w = fmaf(T.w, xt.w, o.w);
+  }
+  return o;
+}
+
+template <class F>
+__device__ __forceinline__ float spmv_dir(const Planes<float>& a, const F& f, float xc, int r, int sy, int sz,
+                                          int has_z) {
+  float acc = __ldg(a.P + r) * xc;
+  acc = fmaf(__ldg(a.W + r), f.at(r - 1), acc);
+  acc = fmaf(__ldg(a.E + r), f.at(r + 1), acc);
+  acc = fmaf(__ldg(a.S + r), f.at(r - sy), acc);
+  acc = fmaf(__ldg(a.N + r), f.at(r + sy), acc);
+  if (has_z) {
+    acc = fmaf(__ldg(a.B + r), f.at(r - sz), acc);
+    acc = fmaf(__ldg(a.T_ + r), f.at(r + sz), acc);
+  }
+  return acc;
+}
+
+__device__ __forceinline__ float dot4(float4 a, float4 b) { return (a.x * b.x + a.y * b.y) + (a.z * b.z + a.w * b.w); }
+
+// A x = b from x = 0 in FP32 (b in V.r0). Reduction slots 0..7, like bcg_core.
+__device__ bool bcg_fused(const Planes<float>& a, int n, int sy, int sz, int has_z, float* x, FusedVec V,
+                          double tol, int max_it, double* partial, int max_blocks, DevStatus* st,
+                          unsigned int& epoch, CoreOut& out) {
+  const int t0 = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
+  const int n4 = n >> 2, tail = n4 << 2;
+  const bool ay = (sy & 3) == 0, az = (sz & 3) == 0;
+  float *R = V.r0, *S = V.r1, *Po = V.p0, *Pn = V.p1, *Vo = V.v0, *Vn = V.v1;
+  const float* rh = V.rh;
+  const float* dg = a.idiag;
+  Vec<2> acc = {{0.0, 0.0}};
+  {
+    float a0 = 0.f;
+    for (int i = t0; i < n; i += gs) {            // x = 0, rhat = r, p = v = 0
+      const float ri = R[i];
+      x[i] = 0.f;
+      V.rh[i] = ri;
+      Po[i] = 0.f;
+      Vo[i] = 0.f;
+      a0 += ri * ri;
+    }
+    acc.v[0] = (double)a0;
+    acc.v[1] = (double)a0;
+  }
+  Vec<2> tot;
+  if (!grid_sum<2>(acc, partial, max_blocks, 6, st, epoch, tot)) return false;
+  out.bnorm = sqrt(tot.v[1]);
+  double res = sqrt(tot.v[0]);
+  out.it = 0;
+  if (out.bnorm == 0.0) {
+    out.conv = true;
+    out.res = 0.0;
+    return true;
+  }
+  const double thr = tol * out.bnorm;
+  double rho = tot.v[0], rho_old = 1.0, alpha = 1.0, omega = 1.0;
+  int it = 0;
+  bool conv = res <= thr;
+  while (!conv && it < max_it && isfinite(res)) {
+    ++it;
+    const float beta = (float)((rho / rho_old) * (alpha / omega));
+    const float om = (float)omega;
+    // pass 1: p' = r + beta (p - om v) (stored), v' = A D^-1 p', (rhat, v')
+    const YDir yd{R, Po, Vo, dg, beta, om};
+    float s1 = 0.f;
+    for (int m = t0; m < n4; m += gs) {
+      const float4 rv = ld4(R, m), pv = ld4(Po, m), vv = ld4(Vo, m), dv = ldg4(dg, m);
+      float4 pn;
+      pn.x = rv.x + beta * (pv.x - om * vv.x); pn.y = rv.y + beta * (pv.y - om * vv.y);
+      pn.z = rv.z + beta * (pv.z - om * vv.z); pn.w = rv.w + beta * (pv.w - om * vv.w);
+      st4(Pn, m, pn);
+      const float4 yc = make_float4(dv.x * pn.x, dv.y * pn.y, dv.z * pn.z, dv.w * pn.w);
+      const float4 vn = spmv4_dir(a, yd, yc, m, sy, sz, has_z, ay, az);
+      st4(Vn, m, vn);
+      s1 += dot4(ld4(rh, m), vn);
+    }
+    for (int i = tail + t0; i < n; i += gs) {
+      const float pn = R[i] + beta * (Po[i] - om * Vo[i]);
+      Pn[i] = pn;
+      const float vn = spmv_dir(a, yd, __ldg(dg + i) * pn, i, sy, sz, has_z);
+      Vn[i] = vn;
+      s1 += rh[i] * vn;
+    }
+    Vec<1> o1, d1 = {{(double)s1}};
+    if (!grid_sum<1>(d1, partial, max_blocks, 0, st, epoch, o1)) return false;
+    alpha = rho / o1.v[0];
+    const float al = (float)alpha;
+    // pass 2: s = r - al v' (stored beside r), t = A D^-1 s, (t,s), (t,t), (s,s)
+    const ZDir zd{R, Vn, dg, al};
+    float s3 = 0.f, s4 = 0.f, s2 = 0.f;
+    for (int m = t0; m < n4; m += gs) {
+      const float4 rv = ld4(R, m), vv = ld4(Vn, m), dv = ldg4(dg, m);
+      const float4 sv = make_float4(rv.x - al * vv.x, rv.y - al * vv.y, rv.z - al * vv.z, rv.w - al * vv.w);
+      st4(S, m, sv);
+      const float4 zc = make_float4(dv.x * sv.x, dv.y * sv.y, dv.z * sv.z, dv.w * sv.w);
+      const float4 tv = spmv4_dir(a, zd, zc, m, sy, sz, has_z, ay, az);
+      st4(V.t, m, tv);
+      s3 += dot4(tv, sv);
+      s4 += dot4(tv, tv);
+      s2 += dot4(sv, sv);
+    }
+    for (int i = tail + t0; i < n; i += gs) {
+      const float si = R[i] - al * Vn[i];
+      S[i] = si;
+      const float ti = spmv_dir(a, zd, __ldg(dg + i) * si, i, sy, sz, has_z);
+      V.t[i] = ti;
+      s3 += ti * si;
+      s4 += ti * ti;
+      s2 += si * si;
+    }
+    Vec<3> o3, d3 = {{(double)s3, (double)s4, (double)s2}};
+    if (!grid_sum<3>(d3, partial, max_blocks, 2, st, epoch, o3)) return false;
+    if (sqrt(o3.v[2]) <= thr) {                  // converged on the half step: x += al D^-1 p'
+      for (int i = t0; i < n; i += gs) x[i] += al * (__ldg(dg + i) * Pn[i]);
+      res = sqrt(o3.v[2]);
+      conv = true;
+      break;
+    }
+    omega = (o3.v[1] > 0.0) ? o3.v[0] / o3.v[1] : 0.0;
+    const float omn = (float)omega;
+    // pass 3: x += al D^-1 p' + omn D^-1 s; r = s - omn t (over s); (rhat, r), (r, r)
+    float s5 = 0.f, s6 = 0.f;
+    for (int m = t0; m < n4; m += gs) {
+      const float4 xv = ld4(x, m), pv = ld4(Pn, m), sv = ld4(S, m), tv = ld4(V.t, m), dv = ldg4(dg, m);
+      float4 xo, ro;
+      xo.x = xv.x + al * (dv.x * pv.x) + omn * (dv.x * sv.x); xo.y = xv.y + al * (dv.y * pv.y) + omn * (dv.y * sv.y);
+      xo.z = xv.z + al * (dv.z * pv.z) + omn * (dv.z * sv.z); xo.w = xv.w + al * (dv.w * pv.w) + omn * (dv.w * sv.w);
+      ro.x = sv.x - omn * tv.x; ro.y = sv.y - omn * tv.y; ro.z = sv.z - omn * tv.z; ro.w = sv.w - omn * tv.w;
+      st4(x, m, xo);
+      st4(S, m, ro);
+      s5 += dot4(ld4(rh, m), ro);
+      s6 += dot4(ro, ro);
+    }
+    for (int i = tail + t0; i < n; i += gs) {
+      const float di = __ldg(dg + i);
+      x[i] += al * (di * Pn[i]) + omn * (di * S[i]);
+      const float ri = S[i] - omn * V.t[i];
+      S[i] = ri;
+      s5 += rh[i] * ri;
+      s6 += ri * ri;
+    }
+    Vec<2> o4, d4 = {{(double)s5, (double)s6}};
+    if (!grid_sum<2>(d4, partial, max_blocks, 4, st, epoch, o4)) return false;
+    res = sqrt(o4.v[1]);
+    conv = res <= thr;
+    rho_old = rho;
+    rho = o4.v[0];
+    float* tmp = R; R = S; S = tmp;               // the new r lives in S
+    tmp = Po; Po = Pn; Pn = tmp;
+    tmp = Vo; Vo = Vn; Vn = tmp;
+    if (rho == 0.0 || omega == 0.0) break;       // breakdown: report the current iterate
+  }
+  out.it = it;
+  out.conv = conv;
+  out.res = res;
+  return true;
+}
+
 __global__ void __launch_bounds__(kBlock, 2) k_bicgstab(BcgArgs A) {
   unsigned int epoch = 0;
   const int n = (int)A.sys.d.n;
@@ -317,7 +544,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_bicgstab(BcgArgs A) {
 // FP64 path).
 constexpr int kMaxRefine = 12;
 
-__global__ void __launch_bounds__(kBlock, 2) k_bicgstab_ir(BcgArgs A) {
+__global__ void __launch_bounds__(kBlock, 1) k_bicgstab_ir(BcgArgs A) {
   unsigned int epoch = 0;
   const int n = (int)A.sys.d.n;
   const int sy = A.sys.d.mx, sz = A.sys.d.mx * A.sys.d.my;
@@ -342,10 +569,12 @@ __global__ void __launch_bounds__(kBlock, 2) k_bicgstab_ir(BcgArgs A) {
     ++ref;
     // the inner solve sees the residual scaled to unit norm (no FP32 under- or overflow)
     const double inv = 1.0 / rn;
-    for (int i = t0; i < n; i += gs) A.v32.r[i] = (float)(r64[i] * inv);
+    // (bcg_fused first reads r0 on the rows this thread wrote; the reduction
+    // that follows orders it before any neighbour read)
+    for (int i = t0; i < n; i += gs) A.f32.r0[i] = (float)(r64[i] * inv);
     CoreOut o;
-    if (!bcg_core<float>(A.sys.af, n, sy, sz, A.has_z, A.v32.r, A.d32, true, A.v32, A.inner_tol, A.max_it - total,
-                         A.partial, A.max_blocks, A.st, epoch, o))
+    if (!bcg_fused(A.sys.af, n, sy, sz, A.has_z, A.d32, A.f32, A.inner_tol, A.max_it - total, A.partial,
+                   A.max_blocks, A.st, epoch, o))
       return;
     total += o.it;
     for (int i = t0; i < n; i += gs) x[i] += rn * (double)A.d32[i];
@@ -540,6 +769,7 @@ cudaError_t launch_bicgstab(const Sys& sys, int has_z, const SolverCtl& ctl, Scr
   A.inner_tol = ctl.inner_tol;
   A.v64 = {sc.v[0], sc.v[1], sc.v[2], sc.v[3], sc.v[4], sc.v[5], sc.v[6]};
   A.v32 = {sc.f[0], sc.f[1], sc.f[2], sc.f[3], sc.f[4], sc.f[5], sc.f[6]};
+  A.f32 = {sc.f[0], sc.f[1], sc.f[2], sc.f[3], sc.f[4], sc.f[5], sc.f[6], sc.f[8]};
   A.d32 = sc.f[7];
   A.partial = sc.partial;
   A.max_blocks = sc.max_blocks;

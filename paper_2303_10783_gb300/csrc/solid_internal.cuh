@@ -98,10 +98,10 @@ struct Params {
   double Te;                 // eutectic temperature Tm + m Ce
 };
 
-// Krylov scratch: 8 FP64 vectors + 8 FP32 vectors, each of `nmax` rows with guards.
+// Krylov scratch: 8 FP64 vectors + 9 FP32 vectors, each of `nmax` rows with guards.
 struct Scratch {
   double* v[8];
-  float* f[8];
+  float* f[9];
   double* partial;       // [kMaxRedSlots][max_blocks]
   int max_blocks;
 };
