@@ -543,6 +543,9 @@ __global__ void __launch_bounds__(kBlock, 2) k_bicgstab(BcgArgs A) {
 // iterate; it stops when the FP64 residual meets tol (the same test as the
 // FP64 path).
 constexpr int kMaxRefine = 12;
+// Inner iterations per refinement sweep: bounds a sweep whose FP32 iteration
+// stalls (the outer FP64 loop then continues from the best iterate).
+constexpr int kMaxInner = 200;
 
 __global__ void __launch_bounds__(kBlock, 1) k_bicgstab_ir(BcgArgs A) {
   unsigned int epoch = 0;
@@ -573,8 +576,9 @@ __global__ void __launch_bounds__(kBlock, 1) k_bicgstab_ir(BcgArgs A) {
     // that follows orders it before any neighbour read)
     for (int i = t0; i < n; i += gs) A.f32.r0[i] = (float)(r64[i] * inv);
     CoreOut o;
-    if (!bcg_fused(A.sys.af, n, sy, sz, A.has_z, A.d32, A.f32, A.inner_tol, A.max_it - total, A.partial,
-                   A.max_blocks, A.st, epoch, o))
+    const int cap = (A.max_it - total < kMaxInner) ? A.max_it - total : kMaxInner;
+    if (!bcg_fused(A.sys.af, n, sy, sz, A.has_z, A.d32, A.f32, A.inner_tol, cap, A.partial, A.max_blocks, A.st,
+                   epoch, o))
       return;
     total += o.it;
     for (int i = t0; i < n; i += gs) x[i] += rn * (double)A.d32[i];

@@ -34,6 +34,10 @@ namespace {
 
 constexpr double kOmega = 0.9;
 constexpr int kMaxRefineP = 12;
+// Inner iterations per refinement sweep of the mixed path: the V-cycle-
+// preconditioned CG needs 5-8 per sweep; the cap only bounds a sweep whose
+// FP32 iteration cannot make progress (the outer FP64 loop continues).
+constexpr int kMaxInnerP = 100;
 
 template <typename TP>
 struct Level {
@@ -604,7 +608,7 @@ struct PcgOut {
   double res, bnorm;
 };
 
-// CG with the V-cycle preconditioner on A x = bscale * b (b is FP64), vectors
+// CG with the V-cycle preconditioner on A x = bscale * (b - bshift) (b is FP64), vectors
 // of type TV (double: FP64 path; float: inner solve of the mixed path), x
 // from 0. The fine-grid operator uses coefficients (cx, cy, cz) and the
 // diagonal table dg of type TV. z is kept orthogonal to the constants (the
@@ -620,7 +624,8 @@ struct PcgOut {
 // Reduction slots 0..11.
 template <typename TV, typename TP>
 __device__ __noinline__ bool pcg(const Ctx& X, const Level<TP>* glev, const Level<TP>* slev, const Tables<TP>& tb,
-                    const double* b, double bscale, TV* x, TV* r, TV* p_a, TV* p_b, TV* q, TV cx, TV cy, TV cz,
+                    const double* b, double bshift, double bscale, TV* x, TV* r, TV* p_a, TV* p_b, TV* q, TV cx,
+                    TV cy, TV cz,
                     const TV* dg, double tol, int max_it, unsigned int& epoch, PcgOut& out) {
   constexpr int U = Batch<TV>::U;
   const Level<TP>& L0 = glev[0];
@@ -629,7 +634,7 @@ __device__ __noinline__ bool pcg(const Ctx& X, const Level<TP>* glev, const Leve
   for (int c = t0; c < n; c += gsz) {
     int i, j, k;
     decompose3(c, L0.fx, L0.fy, i, j, k);
-    const TV bc = (TV)(b[c] * bscale);
+    const TV bc = (TV)((b[c] - bshift) * bscale);
     r[c] = bc;
     x[c] = TV(0);
     L0.b[c] = (TP)bc;
@@ -833,7 +838,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_pcg_mg(MGArgs<TP> A) {
   // TP = double: the FP64 path; TP = float: the mixed path (refinement)
   if constexpr (sizeof(TP) == 8) {
     PcgOut o;
-    if (!pcg<double, TP>(X, glev, slev, tb, b, 1.0, x, r, A.p, A.p2, A.q, A.cx, A.cy, A.cz, tb.diag64, A.tol,
+    if (!pcg<double, TP>(X, glev, slev, tb, b, 0.0, 1.0, x, r, A.p, A.p2, A.q, A.cx, A.cy, A.cz, tb.diag64, A.tol,
                          A.max_it, epoch, o))
       return;
     iters = o.it;
@@ -851,30 +856,39 @@ __global__ void __launch_bounds__(kBlock, 1) k_pcg_mg(MGArgs<TP> A) {
     if (!grid_sum<1>(s, X.partial, X.max_blocks, 13, X.st, epoch, o)) return;
     const double bn = sqrt(o.v[0]);
     double rn = bn;
+    double rmean = 0.0;   // b is mean-free
     const double thr = A.tol * bn;
     const double cx = A.cx, cy = A.cy, cz = A.cz;
     conv = (bn == 0.0);
     while (!conv && refs < kMaxRefineP && iters < A.max_it && isfinite(rn)) {
       ++refs;
-      // the inner solve sees the residual scaled to unit norm (no FP32 under- or overflow)
+      // The inner solve sees the residual without its mean and scaled to unit
+      // norm (no FP32 under- or overflow). The mean is the part of the FP64
+      // residual in the operator's null space (the constants): it is rounding
+      // of A x, no correction can remove it, and left in the inner right-hand
+      // side it would stall the inner iteration once the rest falls below it.
       PcgOut io;
-      if (!pcg<TP, TP>(X, glev, slev, tb, r, 1.0 / rn, A.di, A.ri, A.pi, A.pi2, A.qi, L0.ax, L0.ay, L0.az,
-                       tb.diag[0], A.inner_tol, A.max_it - iters, epoch, io))
+      const int cap = (A.max_it - iters < kMaxInnerP) ? A.max_it - iters : kMaxInnerP;
+      if (!pcg<TP, TP>(X, glev, slev, tb, r, rmean, 1.0 / rn, A.di, A.ri, A.pi, A.pi2, A.qi, L0.ax, L0.ay, L0.az,
+                       tb.diag[0], A.inner_tol, cap, epoch, io))
         return;
       iters += io.it;
       for (int c = t0; c < n; c += gsz) x[c] += rn * (double)A.di[c];
       if (!grid_barrier(X.st, gridDim.x, epoch)) return;
-      Vec<1> s2 = {{0.0}};
+      Vec<2> s2 = {{0.0, 0.0}};
       for (int c = t0; c < n; c += gsz) {        // FP64 residual of the refined iterate
         int i, j, k;
         decompose3(c, L0.fx, L0.fy, i, j, k);
         const double rc = b[c] - lap(x, c, i, j, k, L0.nx, L0.ny, L0.nz, cx, cy, cz, tb.diag64[code_of(L0, i, j, k)]);
         r[c] = rc;
         s2.v[0] += rc * rc;
+        s2.v[1] += rc;
       }
-      Vec<1> o2;
-      if (!grid_sum<1>(s2, X.partial, X.max_blocks, 14, X.st, epoch, o2)) return;
-      rn = sqrt(o2.v[0]);
+      Vec<2> o2;
+      if (!grid_sum<2>(s2, X.partial, X.max_blocks, 14, X.st, epoch, o2)) return;
+      // norm of the residual's range part: sum (r - mean)^2 = sum r^2 - n mean^2
+      rmean = o2.v[1] / (double)n;
+      rn = sqrt(fmax(o2.v[0] - (double)n * rmean * rmean, 0.0));
       conv = rn <= thr;
       if (io.it == 0) break;                     // the inner solve made no progress
     }

@@ -260,6 +260,23 @@ def test_example2_walls_step_parity(lib, case, prec):
     assert st.gl.min() < 1.0
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_minimal_model_step_parity(lib, prec):
+    """The minimal model (D_l = 0, Sec. 2): 100 steps of the cavity against the oracle."""
+    case = cases.cavity_2d()
+    case["alloy"] = dict(case["alloy"], Dl=0.0)
+    case = _tight(case)
+    if prec == "mixed":
+        case.update(tol_p=1e-13, tol_t=1e-13)
+    gpu, st, stats = _run_pair(case, 100, precision=PREC[prec])
+    assert stats["status"] == solid.SS_OK
+    for k in ("p", "T", "C", "gl", "Cl", "Cs"):
+        assert _rel(gpu[k], getattr(st, k)) < STEP_TOL, (k, _rel(gpu[k], getattr(st, k)))
+    vmax = max(np.abs(x).max() for x in st.vel)
+    for a, k in enumerate("uv"):
+        assert np.abs(gpu[k] - st.vel[a]).max() / vmax < STEP_TOL, k
+
+
 def test_temperature_assembly_at_a_given_time(lib):
     """ss_assemble(T) takes the wall temperature at the case's time + dt."""
     case = _example2(3, True)

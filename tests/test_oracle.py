@@ -313,6 +313,24 @@ def test_solute_mass_conserved(cavity_run):
         assert abs(st.C.sum() - s0) <= 1e-12 * s0
 
 
+def test_minimal_model_without_flow_keeps_solute(cavity_run):
+    """Minimal model (Sec. 2: no solute diffusion in the liquid, D_l = 0): with
+    the melt at rest the solute system reduces to I/dt and C^{n+1} = C^n
+    exactly, whatever g_l; with D_l > 0 the same state does redistribute
+    solute (so the check discriminates)."""
+    case = _small(3)
+    st = _state_from_random(case, 8)
+    g = oracle.Grid(case)
+    rest = [np.zeros_like(v) for v in st.vel]
+    for Dl, moves in ((0.0, False), (case["alloy"]["Dl"], True)):
+        c2 = dict(case, alloy=dict(case["alloy"], Dl=Dl))
+        C = oracle.solve_system(oracle.assemble_solute(g, rest, st.gl, st.C, c2))
+        if moves:
+            assert np.abs(C - st.C).max() > 1e-9 * np.abs(st.C).max()
+        else:
+            assert np.abs(C - st.C).max() <= 1e-13 * np.abs(st.C).max()
+
+
 def test_energy_balance(cavity_run):
     """Sum of T + (L/c_p) g changes only by the Robin wall flux (Eq. 3.12 + 3.13)."""
     case, g, hist, infos = cavity_run
