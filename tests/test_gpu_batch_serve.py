@@ -80,3 +80,23 @@ def test_steps_are_bit_reproducible(lib, prec, dims):
     """Deterministic reductions and race-free phases: two runs agree bit for bit."""
     case = cases.box_3d(*dims)
     assert _same(_alone(case, 4, prec), _alone(case, 4, prec))
+
+
+def test_mixed_pressure_refinement_does_not_stall(lib):
+    """Once the mixed pressure solve's FP64 residual is at rounding level, its
+    mean (the Neumann null-space part, which no correction can remove) must
+    not reach the FP32 inner solve: on this 96x128 batch case it once made the
+    inner CG run to the iteration cap at steps 6 and 7. Every step must stay
+    at a few V-cycle iterations and meet the tolerance."""
+    case = cases.batch_cases(n=64)[48]
+    assert (case["dim"], case["nx"], case["ny"]) == (2, 96, 128)
+    c = solid.Case(case, precision=solid.SS_MIXED)
+    f = cases.initial_fields(case)
+    c.initialize(f["T"], f["C"])
+    for _ in range(8):
+        c.step(1)
+        assert c.sync() == solid.SS_OK
+        s = c.stats()
+        assert s["iters"]["p"] <= 40, s["iters"]
+        assert s["relres"]["p"] <= case["tol_p"]
+    c.close()
