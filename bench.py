@@ -275,6 +275,9 @@ def measure(args, precision_name, case, dist, local):
         prof = c.get_profile()
         stats = c.stats()
         c.set_profiling(False)
+        # fields after warm-up + timed steps (outside the timed region), to state the
+        # mixed path's per-field error against the FP64 path on the full workload
+        fields = c.get_fields(("u", "v", "w", "p", "T", "C", "gl"))
         e2e = None
         if not args.no_e2e:
             # end to end through the public API with host buffers: every step uploads its full
@@ -296,7 +299,21 @@ def measure(args, precision_name, case, dist, local):
             barrier(dist)
             e2e = dict(seconds=e2e_s, steps=ke, h2d=nbytes, d2h=nbytes)
         c.close()
-    return dict(ms=ms, status=solid.STATUS_NAMES.get(status, status), prof=prof, stats=stats, clocks=clocks, e2e=e2e)
+    return dict(ms=ms, status=solid.STATUS_NAMES.get(status, status), prof=prof, stats=stats, clocks=clocks, e2e=e2e,
+                fields=fields)
+
+
+def field_errors(a, b, dim):
+    """Relative L-inf difference of fields a against b: scalars against their own
+    largest value, the velocity as one vector field against its largest component."""
+    import numpy as np
+    out = {}
+    for k in ("p", "T", "C", "gl"):
+        out[k] = float(np.abs(a[k] - b[k]).max() / max(np.abs(b[k]).max(), 1e-300))
+    comps = ("u", "v", "w")[:dim]
+    vmax = max(float(np.abs(b[k]).max()) for k in comps)
+    out["velocity"] = max(float(np.abs(a[k] - b[k]).max()) for k in comps) / max(vmax, 1e-300)
+    return out
 
 
 def roofline(precision_name, m, ncell, steps):
@@ -388,6 +405,9 @@ def run_ours(args):
                      "roofline": roofline(name, m, ncell, args.steps),
                      "stage_ms_per_step": {k: v / args.steps for k, v in m["prof"]["ms"].items() if v > 0},
                      "iters_per_step": {k: v / args.steps for k, v in m["prof"]["iters"].items()}}
+    if "mixed" in res and "fp64" in res:
+        out["mixed_vs_fp64"] = {"after_steps": args.warmup + args.steps, "bound": 1e-6,
+                                "rel_linf": field_errors(res["mixed"]["fields"], res["fp64"]["fields"], case["dim"])}
     if world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args)
     print(json.dumps(out))
