@@ -80,7 +80,7 @@ struct ss_case {
   double *ustar[3], *pc, *pb;
   Sys sys[SS_NSYS];
   MGPlan mg;
-  Scratch sc;
+  Scratch sc[kMaxTeams];   // Krylov scratch per team of a joint solve (set 0 for every other solve)
   DevStatus* st;
   int alloy_set;
   long long steps;
@@ -141,25 +141,38 @@ void plan(ss_case* c, Planner& pl) {
   for (int a = 0; a < 3; ++a) c->ustar[a] = pl.vec<double>(c->n_face[a]);
   c->pc = pl.vec<double>(c->n_cell);
   c->pb = pl.vec<double>(c->n_cell);
-  // one set of DIA planes shared by the u, v, w, C and T systems: each is
-  // assembled right before its solve (Sec. 4 term-wise assembly per step)
-  Planes<double> a;
-  a.P = pl.vec<double>(nmax); a.W = pl.vec<double>(nmax); a.E = pl.vec<double>(nmax);
-  a.S = pl.vec<double>(nmax); a.N = pl.vec<double>(nmax);
-  a.B = pl.vec<double>(nmax); a.T_ = pl.vec<double>(nmax); a.idiag = pl.vec<double>(nmax);
-  double* b = pl.vec<double>(nmax);
-  Planes<float> af = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
-  if (c->g.precision == SS_MIXED) {
-    af.P = pl.vec<float>(nmax); af.W = pl.vec<float>(nmax); af.E = pl.vec<float>(nmax);
-    af.S = pl.vec<float>(nmax); af.N = pl.vec<float>(nmax);
-    af.B = pl.vec<float>(nmax); af.T_ = pl.vec<float>(nmax); af.idiag = pl.vec<float>(nmax);
+  // DIA planes: one set per momentum component, so that u*, v*, w* can be
+  // solved together (one launch, one team of blocks each); the C and T
+  // systems reuse the u* set, each assembled right before its solve (Sec. 4
+  // term-wise assembly per step)
+  const bool mixed = c->g.precision == SS_MIXED;
+  Planes<double> a[3];
+  Planes<float> af[3];
+  double* b[3];
+  const int ncomp = c->g.dim;
+  for (int q = 0; q < 3; ++q) {
+    if (q >= ncomp) {   // no w* system in 2D: alias the first set
+      a[q] = a[0]; af[q] = af[0]; b[q] = b[0];
+      continue;
+    }
+    a[q].P = pl.vec<double>(nmax); a[q].W = pl.vec<double>(nmax); a[q].E = pl.vec<double>(nmax);
+    a[q].S = pl.vec<double>(nmax); a[q].N = pl.vec<double>(nmax);
+    a[q].B = pl.vec<double>(nmax); a[q].T_ = pl.vec<double>(nmax); a[q].idiag = pl.vec<double>(nmax);
+    b[q] = pl.vec<double>(nmax);
+    af[q] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    if (mixed) {
+      af[q].P = pl.vec<float>(nmax); af[q].W = pl.vec<float>(nmax); af[q].E = pl.vec<float>(nmax);
+      af[q].S = pl.vec<float>(nmax); af[q].N = pl.vec<float>(nmax);
+      af[q].B = pl.vec<float>(nmax); af[q].T_ = pl.vec<float>(nmax); af[q].idiag = pl.vec<float>(nmax);
+    }
   }
   const int mdims[3][3] = {{(int)nx + 1, (int)ny, (int)nz}, {(int)nx, (int)ny + 1, (int)nz}, {(int)nx, (int)ny, (int)nz + 1}};
   for (int s = 0; s < SS_NSYS; ++s) {
     Sys& S = c->sys[s];
-    S.a = a;
-    S.af = af;
-    S.b = b;
+    const int set = (s <= SS_SYS_W) ? s : 0;
+    S.a = a[set];
+    S.af = af[set];
+    S.b = b[set];
     if (s <= SS_SYS_W) {
       S.d = {mdims[s][0], mdims[s][1], mdims[s][2], c->n_face[s]};
       S.x = c->ustar[s];
@@ -178,10 +191,19 @@ void plan(ss_case* c, Planner& pl) {
         c->mg.vec[l][q] = c->mg.fp32 ? (void*)pl.vec<float>(nl) : (void*)pl.vec<double>(nl);
     }
   }
-  for (int q = 0; q < 8; ++q) c->sc.v[q] = pl.vec<double>(nmax);
-  for (int q = 0; q < 9; ++q) c->sc.f[q] = (c->g.precision == SS_MIXED) ? pl.vec<float>(nmax) : nullptr;
-  c->sc.max_blocks = max_cooperative_blocks();
-  c->sc.partial = pl.raw<double>((size_t)kMaxRedSlots * c->sc.max_blocks * sizeof(double));
+  // Krylov scratch: set 0 serves every solve (multigrid included); sets 1, 2
+  // serve the v* and w* teams of the joint momentum solve, with only the
+  // vectors a transport solve uses (the mixed solve's FP64 refinement
+  // residual and FP32 inner vectors, or the FP64 solve's seven vectors).
+  for (int t = 0; t < kMaxTeams; ++t) {
+    Scratch& sc = c->sc[t];
+    const bool used = (t == 0) || (t < ncomp);
+    const int nv = !used ? 0 : (t == 0) ? 8 : (mixed ? 1 : 7);
+    for (int q = 0; q < 8; ++q) sc.v[q] = (q < nv) ? pl.vec<double>(nmax) : nullptr;
+    for (int q = 0; q < 9; ++q) sc.f[q] = (used && mixed) ? pl.vec<float>(nmax) : nullptr;
+    sc.max_blocks = max_cooperative_blocks();
+    sc.partial = used ? pl.raw<double>((size_t)kMaxRedSlots * sc.max_blocks * sizeof(double)) : nullptr;
+  }
 }
 
 // Guard band (elements) in front of and behind every vector: at least one
@@ -369,14 +391,14 @@ ss_status stage_solve(ss_case* c, int sys) {
     ctl.tol = c->g.tol_p;
     ctl.max_it = c->g.max_it_p;
     if (c->g.precond_p == SS_PRECOND_MG)
-      e = launch_pcg_mg(c->mg, c->pr, c->pb, c->pc, ctl, c->sc, c->st, c->stream);
+      e = launch_pcg_mg(c->mg, c->pr, c->pb, c->pc, ctl, c->sc[0], c->st, c->stream);
     else
-      e = launch_pcg_poisson(c->pr, c->pb, c->pc, ctl, c->sc, c->st, c->stream);
+      e = launch_pcg_poisson(c->pr, c->pb, c->pc, ctl, c->sc[0], c->st, c->stream);
   } else if (sys >= 0 && sys < SS_NSYS) {
     if (sys == SS_SYS_W && c->pr.dim != 3) return SS_OK;
     ctl.tol = c->g.tol_t;
     ctl.max_it = c->g.max_it_t;
-    e = launch_bicgstab(c->sys[sys], c->pr.dim == 3, ctl, c->sc, c->st, c->stream);
+    e = launch_bicgstab(c->sys[sys], c->pr.dim == 3, ctl, c->sc[0], c->st, c->stream);
   } else {
     return fail(SS_EINVAL, "unknown system %d", sys);
   }
@@ -406,12 +428,34 @@ ss_status stage_lever(ss_case* c) {
     if (s_ != SS_OK) return s_;    \
   } while (0)
 
+// The u*, v*, w* systems of Eq. 3.3 are independent (each uses u^n only):
+// one cooperative launch solves all of them, one team of blocks per
+// component. Its time and its launch are counted under solve_u.
+ss_status stage_solve_momentum(ss_case* c) {
+  StageTimer tm(c, SS_PROF_SOLVE + SS_SYS_U, 1);
+  const int ncomp = c->pr.dim;
+  SolverCtl ctl[kMaxTeams];
+  const Sys* sys[kMaxTeams];
+  Scratch* sc[kMaxTeams];
+  for (int q = 0; q < ncomp; ++q) {
+    ctl[q].mixed = c->g.precision == SS_MIXED;
+    ctl[q].stat_index = q;
+    ctl[q].inner_tol = kInnerTolTransport;
+    ctl[q].tol = c->g.tol_t;
+    ctl[q].max_it = c->g.max_it_t;
+    sys[q] = &c->sys[q];
+    sc[q] = &c->sc[q];
+  }
+  cudaError_t e = launch_bicgstab_multi(sys, ncomp, ncomp == 3, ctl, sc, c->st, c->stream);
+  if (e != cudaSuccess) return fail(SS_ECUDA, "joint momentum solve: %s", cudaGetErrorString(e));
+  return SS_OK;
+}
+
 ss_status one_step(ss_case* c) {
   const int ncomp = c->pr.dim;
-  for (int a = 0; a < ncomp; ++a) {           // 1: intermediate velocity (Eq. 3.3)
+  for (int a = 0; a < ncomp; ++a)             // 1: intermediate velocity (Eq. 3.3)
     STAGE_TRY(stage_assemble(c, a));
-    STAGE_TRY(stage_solve(c, a));
-  }
+  STAGE_TRY(stage_solve_momentum(c));
   STAGE_TRY(stage_assemble(c, SS_SYS_P));     // 2: pressure correction (Eq. 3.4)
   STAGE_TRY(stage_solve(c, SS_SYS_P));
   STAGE_TRY(stage_project(c));                // 3: projection (Eq. 3.5)

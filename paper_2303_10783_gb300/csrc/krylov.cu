@@ -20,6 +20,7 @@
 // read with plain L1-cached loads: they are read only after a grid barrier,
 // whose acquire makes the other blocks' writes visible. The DIA planes do
 // not change during a solve and use the read-only path.
+#include <cstring>
 #include <mutex>
 
 #include "solid_internal.cuh"
@@ -67,8 +68,10 @@ __device__ __forceinline__ T spmv_row(const Planes<T>& a, const T* x, int r, int
   return acc;
 }
 
-__device__ void record(DevStatus* st, int idx, int iters, int refinements, bool converged, double relres) {
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
+// Solve statistics, written by thread 0 of the leading block of the solving team.
+__device__ void record(DevStatus* st, bool leader, int idx, int iters, int refinements, bool converged,
+                       double relres) {
+  if (leader && threadIdx.x == 0) {
     SolveStat& s = st->stat[idx];
     s.iters = iters;
     s.iters_total += iters;
@@ -131,9 +134,9 @@ struct CoreOut {
 // Reduction slots 0..7. Returns false if a grid barrier gave up.
 template <typename T>
 __device__ bool bcg_core(const Planes<T>& a, int n, int sy, int sz, int has_z, const T* b, T* x, bool zero_x0,
-                         const BcgVec<T>& V, double tol, int max_it, double* partial, int max_blocks, DevStatus* st,
+                         const BcgVec<T>& V, double tol, int max_it, const Team& tm, int max_blocks, DevStatus* st,
                          unsigned int& epoch, CoreOut& out) {
-  const int t0 = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
+  const int t0 = tm.rank * blockDim.x + threadIdx.x, gs = tm.size * blockDim.x;
   T *r = V.r, *rh = V.rh, *p = V.p, *v = V.v, *y = V.y, *z = V.z, *t = V.t;
   Vec<2> acc = {{0.0, 0.0}};
   {
@@ -153,7 +156,7 @@ __device__ bool bcg_core(const Planes<T>& a, int n, int sy, int sz, int has_z, c
     acc.v[1] = (double)a1;
   }
   Vec<2> tot;
-  if (!grid_sum<2>(acc, partial, max_blocks, 6, st, epoch, tot)) return false;
+  if (!team_sum<2>(acc, tm, max_blocks, 6, st, epoch, tot)) return false;
   out.bnorm = sqrt(tot.v[1]);
   double res = sqrt(tot.v[0]);
   out.it = 0;
@@ -194,7 +197,7 @@ __device__ bool bcg_core(const Planes<T>& a, int n, int sy, int sz, int has_z, c
       p[i] = pi;
       y[i] = __ldg(a.idiag + i) * pi;
     }
-    if (!grid_barrier(st, gridDim.x, epoch)) return false;
+    if (!team_barrier(st, tm, epoch)) return false;
     T s1 = T(0);
     tail = 0;                                     // v = A y
     if constexpr (sizeof(T) == 4) {
@@ -212,7 +215,7 @@ __device__ bool bcg_core(const Planes<T>& a, int n, int sy, int sz, int has_z, c
       s1 += rh[i] * vi;
     }
     Vec<1> o1, d1 = {{(double)s1}};
-    if (!grid_sum<1>(d1, partial, max_blocks, 0, st, epoch, o1)) return false;
+    if (!team_sum<1>(d1, tm, max_blocks, 0, st, epoch, o1)) return false;
     alpha = rho / o1.v[0];
     const T al = (T)alpha;
     T s2 = T(0);
@@ -237,7 +240,7 @@ __device__ bool bcg_core(const Planes<T>& a, int n, int sy, int sz, int has_z, c
       s2 += si * si;
     }
     Vec<1> o2, d2 = {{(double)s2}};
-    if (!grid_sum<1>(d2, partial, max_blocks, 1, st, epoch, o2)) return false;
+    if (!team_sum<1>(d2, tm, max_blocks, 1, st, epoch, o2)) return false;
     if (sqrt(o2.v[0]) <= thr) {                  // early exit on the half step
       for (int i = t0; i < n; i += gs) x[i] += al * y[i];
       res = sqrt(o2.v[0]);
@@ -263,7 +266,7 @@ __device__ bool bcg_core(const Planes<T>& a, int n, int sy, int sz, int has_z, c
       s4 += ti * ti;
     }
     Vec<2> o3, d3 = {{(double)s3, (double)s4}};
-    if (!grid_sum<2>(d3, partial, max_blocks, 2, st, epoch, o3)) return false;
+    if (!team_sum<2>(d3, tm, max_blocks, 2, st, epoch, o3)) return false;
     omega = (o3.v[1] > 0.0) ? o3.v[0] / o3.v[1] : 0.0;
     const T omn = (T)omega;
     T s5 = T(0), s6 = T(0);
@@ -291,7 +294,7 @@ __device__ bool bcg_core(const Planes<T>& a, int n, int sy, int sz, int has_z, c
       s6 += ri * ri;
     }
     Vec<2> o4, d4 = {{(double)s5, (double)s6}};
-    if (!grid_sum<2>(d4, partial, max_blocks, 4, st, epoch, o4)) return false;
+    if (!team_sum<2>(d4, tm, max_blocks, 4, st, epoch, o4)) return false;
     res = sqrt(o4.v[1]);
     conv = res <= thr;
     rho_old = rho;
@@ -389,9 +392,9 @@ __device__ __forceinline__ float dot4(float4 a, float4 b) { return (a.x * b.x + 
 
 // A x = b from x = 0 in FP32 (b in V.r0). Reduction slots 0..7, like bcg_core.
 __device__ bool bcg_fused(const Planes<float>& a, int n, int sy, int sz, int has_z, float* x, FusedVec V,
-                          double tol, int max_it, double* partial, int max_blocks, DevStatus* st,
+                          double tol, int max_it, const Team& tm, int max_blocks, DevStatus* st,
                           unsigned int& epoch, CoreOut& out) {
-  const int t0 = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
+  const int t0 = tm.rank * blockDim.x + threadIdx.x, gs = tm.size * blockDim.x;
   const int n4 = n >> 2, tail = n4 << 2;
   const bool ay = (sy & 3) == 0, az = (sz & 3) == 0;
   float *R = V.r0, *S = V.r1, *Po = V.p0, *Pn = V.p1, *Vo = V.v0, *Vn = V.v1;
@@ -412,7 +415,7 @@ __device__ bool bcg_fused(const Planes<float>& a, int n, int sy, int sz, int has
     acc.v[1] = (double)a0;
   }
   Vec<2> tot;
-  if (!grid_sum<2>(acc, partial, max_blocks, 6, st, epoch, tot)) return false;
+  if (!team_sum<2>(acc, tm, max_blocks, 6, st, epoch, tot)) return false;
   out.bnorm = sqrt(tot.v[1]);
   double res = sqrt(tot.v[0]);
   out.it = 0;
@@ -451,7 +454,7 @@ __device__ bool bcg_fused(const Planes<float>& a, int n, int sy, int sz, int has
       s1 += rh[i] * vn;
     }
     Vec<1> o1, d1 = {{(double)s1}};
-    if (!grid_sum<1>(d1, partial, max_blocks, 0, st, epoch, o1)) return false;
+    if (!team_sum<1>(d1, tm, max_blocks, 0, st, epoch, o1)) return false;
     alpha = rho / o1.v[0];
     const float al = (float)alpha;
     // pass 2: s = r - al v' (stored beside r), t = A D^-1 s, (t,s), (t,t), (s,s)
@@ -478,7 +481,7 @@ __device__ bool bcg_fused(const Planes<float>& a, int n, int sy, int sz, int has
       s2 += si * si;
     }
     Vec<3> o3, d3 = {{(double)s3, (double)s4, (double)s2}};
-    if (!grid_sum<3>(d3, partial, max_blocks, 2, st, epoch, o3)) return false;
+    if (!team_sum<3>(d3, tm, max_blocks, 2, st, epoch, o3)) return false;
     if (sqrt(o3.v[2]) <= thr) {                  // converged on the half step: x += al D^-1 p'
       for (int i = t0; i < n; i += gs) x[i] += al * (__ldg(dg + i) * Pn[i]);
       res = sqrt(o3.v[2]);
@@ -509,7 +512,7 @@ __device__ bool bcg_fused(const Planes<float>& a, int n, int sy, int sz, int has
       s6 += ri * ri;
     }
     Vec<2> o4, d4 = {{(double)s5, (double)s6}};
-    if (!grid_sum<2>(d4, partial, max_blocks, 4, st, epoch, o4)) return false;
+    if (!team_sum<2>(d4, tm, max_blocks, 4, st, epoch, o4)) return false;
     res = sqrt(o4.v[1]);
     conv = res <= thr;
     rho_old = rho;
@@ -525,15 +528,15 @@ __device__ bool bcg_fused(const Planes<float>& a, int n, int sy, int sz, int has
   return true;
 }
 
-__global__ void __launch_bounds__(kBlock, 2) k_bicgstab(BcgArgs A) {
+__device__ __forceinline__ void fp64_solve(const BcgArgs& A, const Team& tm) {
   unsigned int epoch = 0;
   const int n = (int)A.sys.d.n;
   const int sy = A.sys.d.mx, sz = A.sys.d.mx * A.sys.d.my;
   CoreOut o;
-  if (!bcg_core<double>(A.sys.a, n, sy, sz, A.has_z, A.sys.b, A.sys.x, false, A.v64, A.tol, A.max_it, A.partial,
+  if (!bcg_core<double>(A.sys.a, n, sy, sz, A.has_z, A.sys.b, A.sys.x, false, A.v64, A.tol, A.max_it, tm,
                         A.max_blocks, A.st, epoch, o))
     return;
-  record(A.st, A.stat_index, o.it, 0, o.conv, o.bnorm > 0.0 ? o.res / o.bnorm : 0.0);
+  record(A.st, tm.rank == 0, A.stat_index, o.it, 0, o.conv, o.bnorm > 0.0 ? o.res / o.bnorm : 0.0);
 }
 
 // Mixed precision: FP64 iterative refinement around an FP32 BiCGSTAB on the
@@ -547,11 +550,11 @@ constexpr int kMaxRefine = 12;
 // stalls (the outer FP64 loop then continues from the best iterate).
 constexpr int kMaxInner = 200;
 
-__global__ void __launch_bounds__(kBlock, 1) k_bicgstab_ir(BcgArgs A) {
+__device__ __forceinline__ void ir_solve(const BcgArgs& A, const Team& tm) {
   unsigned int epoch = 0;
   const int n = (int)A.sys.d.n;
   const int sy = A.sys.d.mx, sz = A.sys.d.mx * A.sys.d.my;
-  const int t0 = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
+  const int t0 = tm.rank * blockDim.x + threadIdx.x, gs = tm.size * blockDim.x;
   double* x = A.sys.x;
   const double* b = A.sys.b;
   double* r64 = A.v64.r;
@@ -563,7 +566,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_bicgstab_ir(BcgArgs A) {
     acc.v[1] += b[i] * b[i];
   }
   Vec<2> tot;
-  if (!grid_sum<2>(acc, A.partial, A.max_blocks, 13, A.st, epoch, tot)) return;
+  if (!team_sum<2>(acc, tm, A.max_blocks, 13, A.st, epoch, tot)) return;
   const double bnorm = sqrt(tot.v[1]);
   double rn = sqrt(tot.v[0]);
   const double thr = A.tol * bnorm;
@@ -577,12 +580,12 @@ __global__ void __launch_bounds__(kBlock, 1) k_bicgstab_ir(BcgArgs A) {
     for (int i = t0; i < n; i += gs) A.f32.r0[i] = (float)(r64[i] * inv);
     CoreOut o;
     const int cap = (A.max_it - total < kMaxInner) ? A.max_it - total : kMaxInner;
-    if (!bcg_fused(A.sys.af, n, sy, sz, A.has_z, A.d32, A.f32, A.inner_tol, cap, A.partial, A.max_blocks, A.st,
-                   epoch, o))
+    if (!bcg_fused(A.sys.af, n, sy, sz, A.has_z, A.d32, A.f32, A.inner_tol, cap, tm, A.max_blocks, A.st, epoch,
+                   o))
       return;
     total += o.it;
     for (int i = t0; i < n; i += gs) x[i] += rn * (double)A.d32[i];
-    if (!grid_barrier(A.st, gridDim.x, epoch)) return;
+    if (!team_barrier(A.st, tm, epoch)) return;
     Vec<1> s1 = {{0.0}};
     for (int i = t0; i < n; i += gs) {
       const double ri = b[i] - spmv_row(A.sys.a, x, i, sy, sz, A.has_z);
@@ -590,12 +593,48 @@ __global__ void __launch_bounds__(kBlock, 1) k_bicgstab_ir(BcgArgs A) {
       s1.v[0] += ri * ri;
     }
     Vec<1> o1;
-    if (!grid_sum<1>(s1, A.partial, A.max_blocks, 15, A.st, epoch, o1)) return;
+    if (!team_sum<1>(s1, tm, A.max_blocks, 15, A.st, epoch, o1)) return;
     rn = sqrt(o1.v[0]);
     if (o.it == 0 && !(rn <= thr)) break;      // the inner solve made no progress
   }
-  record(A.st, A.stat_index, total, ref, bnorm == 0.0 || rn <= thr, bnorm > 0.0 ? rn / bnorm : 0.0);
+  record(A.st, tm.rank == 0, A.stat_index, total, ref, bnorm == 0.0 || rn <= thr, bnorm > 0.0 ? rn / bnorm : 0.0);
 }
+
+// Up to kMaxTeams independent systems in one cooperative launch: team s is
+// the blocks [first[s], first[s+1]) and solves sys[s] with its own barrier
+// counter and reduction partials (the momentum components u*, v*, w* of
+// Eq. 3.3 are independent, so they share one launch instead of three).
+struct BcgMulti {
+  BcgArgs sys[kMaxTeams];
+  int nsys;
+  int first[kMaxTeams + 1];
+};
+
+// The team of this block. Each system's arguments are named with a constant
+// index (no runtime indexing of the parameter block, which would copy it to
+// local memory).
+template <bool MIXED>
+__device__ __forceinline__ void solve_team(const BcgMulti& M) {
+  const int b = (int)blockIdx.x;
+  const int s = (M.nsys > 2 && b >= M.first[2]) ? 2 : (M.nsys > 1 && b >= M.first[1]) ? 1 : 0;
+  const int f0 = s == 0 ? 0 : s == 1 ? M.first[1] : M.first[2];
+  const int f1 = s == 0 ? M.first[1] : s == 1 ? M.first[2] : M.first[3];
+  DevStatus* st = M.sys[0].st;
+  if (s == 0) {
+    const Team tm{b - f0, f1 - f0, &st->team_arrivals[0], M.sys[0].partial};
+    if (MIXED) ir_solve(M.sys[0], tm); else fp64_solve(M.sys[0], tm);
+  } else if (s == 1) {
+    const Team tm{b - f0, f1 - f0, &st->team_arrivals[1], M.sys[1].partial};
+    if (MIXED) ir_solve(M.sys[1], tm); else fp64_solve(M.sys[1], tm);
+  } else {
+    const Team tm{b - f0, f1 - f0, &st->team_arrivals[2], M.sys[2].partial};
+    if (MIXED) ir_solve(M.sys[2], tm); else fp64_solve(M.sys[2], tm);
+  }
+}
+
+__global__ void __launch_bounds__(kBlock, 2) k_bicgstab(BcgMulti M) { solve_team<false>(M); }
+
+__global__ void __launch_bounds__(kBlock, 1) k_bicgstab_ir(BcgMulti M) { solve_team<true>(M); }
 
 struct PcgArgs {
   int nx, ny, nz, dim;
@@ -720,7 +759,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_pcg_poisson(PcgArgs A) {
   if (!grid_sum<1>(sx, A.partial, A.max_blocks, 12, A.st, epoch, ox)) return;
   const double mean_x = ox.v[0] / (double)n;
   for (int i = t0; i < n; i += gs) x[i] -= mean_x;
-  record(A.st, A.stat_index, it, 0, conv, bnorm > 0.0 ? res / bnorm : 0.0);
+  record(A.st, blockIdx.x == 0, A.stat_index, it, 0, conv, bnorm > 0.0 ? res / bnorm : 0.0);
 }
 
 int g_num_sms = 0;
@@ -762,29 +801,73 @@ int max_cooperative_blocks() {
   return 4 * (g_num_sms > 0 ? g_num_sms : 1);
 }
 
+cudaError_t launch_bicgstab_multi(const Sys* const* sys, int nsys, int has_z, const SolverCtl* ctl,
+                                  Scratch* const* sc, DevStatus* st, cudaStream_t s) {
+  if (nsys < 1 || nsys > kMaxTeams) return cudaErrorInvalidValue;
+  BcgMulti M;
+  memset(&M, 0, sizeof M);
+  M.nsys = nsys;
+  bool mixed = true;
+  for (int q = 0; q < nsys; ++q) {
+    BcgArgs& A = M.sys[q];
+    const Scratch& c = *sc[q];
+    A.sys = *sys[q];
+    A.has_z = has_z;
+    A.tol = ctl[q].tol;
+    A.max_it = ctl[q].max_it;
+    A.stat_index = ctl[q].stat_index;
+    A.inner_tol = ctl[q].inner_tol;
+    A.v64 = {c.v[0], c.v[1], c.v[2], c.v[3], c.v[4], c.v[5], c.v[6]};
+    A.v32 = {c.f[0], c.f[1], c.f[2], c.f[3], c.f[4], c.f[5], c.f[6]};
+    A.f32 = {c.f[0], c.f[1], c.f[2], c.f[3], c.f[4], c.f[5], c.f[6], c.f[8]};
+    A.d32 = c.f[7];
+    A.partial = c.partial;
+    A.max_blocks = c.max_blocks;
+    A.st = st;
+    mixed = mixed && ctl[q].mixed && sys[q]->af.P != nullptr && c.f[0] != nullptr;
+  }
+  const void* kern = mixed ? (const void*)k_bicgstab_ir : (const void*)k_bicgstab;
+  // blocks per team: as many as the system's rows want, scaled down in
+  // proportion to the rows when the teams together exceed what one
+  // cooperative launch can keep resident
+  int lim = coop_limit(kern);
+  long long want[kMaxTeams], rows = 0, total = 0;
+  for (int q = 0; q < nsys; ++q) {
+    if (lim > sc[q]->max_blocks) lim = sc[q]->max_blocks;
+    want[q] = (sys[q]->d.n + kBlock - 1) / kBlock;
+    if (want[q] < 1) want[q] = 1;
+    rows += sys[q]->d.n;
+    total += want[q];
+  }
+  if (lim < nsys) return cudaErrorCooperativeLaunchTooLarge;
+  if (total > lim) {
+    total = 0;
+    for (int q = 0; q < nsys; ++q) {
+      want[q] = (long long)((double)lim * (double)sys[q]->d.n / (double)(rows > 0 ? rows : 1));
+      if (want[q] < 1) want[q] = 1;
+      total += want[q];
+    }
+    while (total > lim) {                      // rounding: take from the largest team
+      int big = 0;
+      for (int q = 1; q < nsys; ++q) if (want[q] > want[big]) big = q;
+      --want[big];
+      --total;
+    }
+  }
+  M.first[0] = 0;
+  for (int q = 0; q < nsys; ++q) M.first[q + 1] = M.first[q] + (int)want[q];
+  for (int q = nsys + 1; q <= kMaxTeams; ++q) M.first[q] = M.first[nsys];
+  cudaError_t e = cudaMemsetAsync(st->team_arrivals, 0, sizeof(st->team_arrivals), s);
+  if (e != cudaSuccess) return e;
+  void* args[] = {&M};
+  return cudaLaunchCooperativeKernel(kern, dim3(M.first[nsys]), dim3(kBlock), args, 0, s);
+}
+
 cudaError_t launch_bicgstab(const Sys& sys, int has_z, const SolverCtl& ctl, Scratch& sc, DevStatus* st,
                             cudaStream_t s) {
-  BcgArgs A;
-  A.sys = sys;
-  A.has_z = has_z;
-  A.tol = ctl.tol;
-  A.max_it = ctl.max_it;
-  A.stat_index = ctl.stat_index;
-  A.inner_tol = ctl.inner_tol;
-  A.v64 = {sc.v[0], sc.v[1], sc.v[2], sc.v[3], sc.v[4], sc.v[5], sc.v[6]};
-  A.v32 = {sc.f[0], sc.f[1], sc.f[2], sc.f[3], sc.f[4], sc.f[5], sc.f[6]};
-  A.f32 = {sc.f[0], sc.f[1], sc.f[2], sc.f[3], sc.f[4], sc.f[5], sc.f[6], sc.f[8]};
-  A.d32 = sc.f[7];
-  A.partial = sc.partial;
-  A.max_blocks = sc.max_blocks;
-  A.st = st;
-  const bool mixed = ctl.mixed && sys.af.P != nullptr && sc.f[0] != nullptr;
-  const void* kern = mixed ? (const void*)k_bicgstab_ir : (const void*)k_bicgstab;
-  const int nb = blocks_for(kern, sys.d.n, sc.max_blocks);
-  cudaError_t e = cudaMemsetAsync(&st->barrier, 0, sizeof(unsigned int), s);
-  if (e != cudaSuccess) return e;
-  void* args[] = {&A};
-  return cudaLaunchCooperativeKernel(kern, dim3(nb), dim3(kBlock), args, 0, s);
+  const Sys* sp[1] = {&sys};
+  Scratch* cp[1] = {&sc};
+  return launch_bicgstab_multi(sp, 1, has_z, &ctl, cp, st, s);
 }
 
 cudaError_t launch_pcg_poisson(const Params& pr, double* b, double* x, const SolverCtl& ctl, Scratch& sc,

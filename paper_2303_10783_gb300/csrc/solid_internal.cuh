@@ -41,6 +41,10 @@ struct SolveStat {
 };
 
 // Device status block (one per case).
+// Largest number of independent systems one cooperative solve launch handles
+// (the three momentum components), each by its own team of blocks.
+constexpr int kMaxTeams = 3;
+
 struct DevStatus {
   unsigned int barrier;          // grid-barrier arrival counter (reset before each cooperative launch)
   unsigned int pad0;
@@ -49,6 +53,7 @@ struct DevStatus {
   SolveStat stat[SS_NSYS];
   double scal[kMaxRedSlots * 4]; // broadcast scalars (unused by the all-blocks reduction)
   double time;                   // simulated time of the fields; k_lever advances it by dt
+  unsigned int team_arrivals[kMaxTeams]; // barrier counters of the teams of a multi-system solve
 };
 
 template <typename T>
@@ -120,24 +125,34 @@ __device__ __forceinline__ unsigned int atom_add_acq_rel_u32(unsigned int* p, un
   return old;
 }
 
-// Grid-wide barrier for cooperative launches. The arrival counter is zeroed
-// by the host before the launch; `epoch` counts barriers passed by this
+// A team: the blocks [first, first + size) of a cooperative launch that work
+// on one system. It has its own barrier counter and reduction partials, so
+// teams of one launch proceed independently. A whole grid is one team.
+struct Team {
+  int rank;                 // this block's index within the team
+  int size;                 // blocks in the team
+  unsigned int* counter;    // the team's arrival counter (zeroed by the host before the launch)
+  double* partial;          // the team's reduction partials, [kMaxRedSlots][max_blocks]
+};
+
+// Barrier over the blocks of a team. `epoch` counts barriers passed by this
 // block. Thread 0 arrives with an acq_rel atomic (publishing the block's
 // writes) and polls with acquire loads. A poll limit bounds the wait: on
 // expiry the sticky error is set and every block returns false from then
-// on, so the kernel unwinds instead of hanging.
-__device__ __forceinline__ bool grid_barrier(DevStatus* st, unsigned int nblocks, unsigned int& epoch) {
+// on, so the kernel unwinds instead of hanging. The error flag is shared by
+// all teams, so one team's failure unwinds every team.
+__device__ __forceinline__ bool team_barrier(DevStatus* st, const Team& t, unsigned int& epoch) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
     epoch += 1u;
-    const unsigned int target = epoch * nblocks;
+    const unsigned int target = epoch * (unsigned int)t.size;
     __threadfence();
-    const unsigned int old = atom_add_acq_rel_u32(&st->barrier, 1u);
+    const unsigned int old = atom_add_acq_rel_u32(t.counter, 1u);
     int ok = 1;
     if (old + 1u != target) {
       long long spins = 0;
-      while (ld_acquire_u32(&st->barrier) < target) {
+      while (ld_acquire_u32(t.counter) < target) {
         if ((++spins & 255) == 0) {
           if (*(volatile int*)&st->err != kErrNone) { ok = 0; break; }
           if (spins > kSpinLimit) { atomicExch(&st->err, kErrBarrier); ok = 0; break; }
@@ -148,6 +163,13 @@ __device__ __forceinline__ bool grid_barrier(DevStatus* st, unsigned int nblocks
   }
   __syncthreads();
   return s_ok != 0;
+}
+
+// Grid-wide barrier for cooperative launches (the whole grid as one team,
+// counting on st->barrier).
+__device__ __forceinline__ bool grid_barrier(DevStatus* st, unsigned int nblocks, unsigned int& epoch) {
+  const Team t{(int)blockIdx.x, (int)nblocks, &st->barrier, nullptr};
+  return team_barrier(st, t, epoch);
 }
 
 template <int K>
@@ -179,26 +201,26 @@ __device__ __forceinline__ Vec<K> block_sum0(Vec<K> x) {
   return r;
 }
 
-// Deterministic grid reduction of K doubles: every block writes its partial
-// sums to slots [slot, slot+K), passes a grid barrier, then warp q of every
-// block sums slot q's partials in block order (the same order everywhere,
-// so all blocks get bit-identical totals). Returns false if the barrier
-// gave up.
+// Deterministic reduction of K doubles over a team: every block writes its
+// partial sums to slots [slot, slot+K), passes the team barrier, then warp q
+// of every block sums slot q's partials in block order (the same order
+// everywhere, so all blocks get bit-identical totals). Returns false if the
+// barrier gave up.
 template <int K>
-__device__ __forceinline__ bool grid_sum(Vec<K> x, double* partial, int max_blocks, int slot, DevStatus* st,
+__device__ __forceinline__ bool team_sum(Vec<K> x, const Team& t, int max_blocks, int slot, DevStatus* st,
                                          unsigned int& epoch, Vec<K>& out) {
   static_assert(K <= kBlock / 32, "one warp per reduced value");
   Vec<K> b = block_sum0<K>(x);
   if (threadIdx.x == 0) {
 #pragma unroll
-    for (int q = 0; q < K; ++q) partial[(size_t)(slot + q) * max_blocks + blockIdx.x] = b.v[q];
+    for (int q = 0; q < K; ++q) t.partial[(size_t)(slot + q) * max_blocks + t.rank] = b.v[q];
   }
-  if (!grid_barrier(st, gridDim.x, epoch)) return false;
+  if (!team_barrier(st, t, epoch)) return false;
   __shared__ double tot[K];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   if (wid < K) {
-    const double* pp = partial + (size_t)(slot + wid) * max_blocks;
-    const int nb = (int)gridDim.x;
+    const double* pp = t.partial + (size_t)(slot + wid) * max_blocks;
+    const int nb = t.size;
     double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
     int i = lane;
     for (; i + 96 < nb; i += 128) {
@@ -218,6 +240,14 @@ __device__ __forceinline__ bool grid_sum(Vec<K> x, double* partial, int max_bloc
   for (int q = 0; q < K; ++q) out.v[q] = tot[q];
   __syncthreads();
   return true;
+}
+
+// The same over the whole grid (counting on st->barrier).
+template <int K>
+__device__ __forceinline__ bool grid_sum(Vec<K> x, double* partial, int max_blocks, int slot, DevStatus* st,
+                                         unsigned int& epoch, Vec<K>& out) {
+  const Team t{(int)blockIdx.x, (int)gridDim.x, &st->barrier, partial};
+  return team_sum<K>(x, t, max_blocks, slot, st, epoch, out);
 }
 
 // Division by a runtime constant d >= 1 for 0 <= n < 2^31 with a multiply-high
@@ -288,6 +318,10 @@ struct SolverCtl {
 };
 cudaError_t launch_bicgstab(const Sys& sys, int has_z, const SolverCtl& ctl, Scratch& sc, DevStatus* st,
                             cudaStream_t s);
+// nsys (<= kMaxTeams) independent systems in one cooperative launch, each
+// solved by its own team of blocks with its own scratch sc[q].
+cudaError_t launch_bicgstab_multi(const Sys* const* sys, int nsys, int has_z, const SolverCtl* ctl,
+                                  Scratch* const* sc, DevStatus* st, cudaStream_t s);
 cudaError_t launch_pcg_poisson(const Params& pr, double* b, double* x, const SolverCtl& ctl, Scratch& sc,
                                DevStatus* st, cudaStream_t s);
 int cooperative_blocks(const void* kernel, long long rows);
