@@ -13,7 +13,8 @@
 // even and >= 4 (semi-coarsening when only some axes qualify). Each level
 // rediscretises the Neumann Laplacian A = -L with its own spacings (the
 // operator is constant, Sec. 4 term-wise strategy: nothing is assembled).
-//   smoother      weighted Jacobi (omega = 0.9), 2 sweeps before and 2 after
+//   smoother      2 weighted-Jacobi sweeps before and 2 after, weights of a
+//                 degree-2 Chebyshev polynomial (see kChebLo)
 //   prolongation  trilinear in cell centres (per axis 3/4 parent, 1/4 the
 //                 neighbour on the child's side; a wall mirrors the parent)
 //   restriction   R = P^T / 2^(coarsened axes) (per axis weights 1/8 3/8 3/8 1/8)
@@ -32,7 +33,20 @@
 namespace solid {
 namespace {
 
+// Smoothing: the two sweeps before and after the coarse correction form a
+// degree-2 Chebyshev polynomial in D^-1 A on [kChebLo, kChebHi]: the
+// spectrum of the Jacobi-scaled Neumann Laplacian lies in [0, 2]
+// (Gershgorin, every row), and the sweeps must damp its upper part, which
+// the coarse level cannot represent. Weights are the reciprocals of the
+// polynomial's roots, omega_1,2 = 1 / (c -+ d cos(pi/4)), c = (hi+lo)/2,
+// d = (hi-lo)/2. Both sweeps are polynomials in D^-1 A, so pre- and
+// post-smoothing commute and the V-cycle stays symmetric. The coarsest level
+// takes nu_c weighted-Jacobi sweeps with kOmega.
 constexpr double kOmega = 0.9;
+constexpr double kChebLo = 0.4;
+constexpr double kChebHi = 2.0;
+constexpr double kOmega1 = 1.0 / (0.5 * (kChebHi + kChebLo) + 0.5 * (kChebHi - kChebLo) * 0.70710678118654752);
+constexpr double kOmega2 = 1.0 / (0.5 * (kChebHi + kChebLo) - 0.5 * (kChebHi - kChebLo) * 0.70710678118654752);
 constexpr int kMaxRefineP = 12;
 // Inner iterations per refinement sweep of the mixed path: the V-cycle-
 // preconditioned CG needs 5-8 per sweep; the cap only bounds a sweep whose
@@ -97,7 +111,9 @@ __device__ __forceinline__ T lap(const T* v, int c, int i, int j, int k, int nx,
 template <typename TP>
 struct Tables {
   TP diag[kMaxLevels][27];
-  TP wid[kMaxLevels][27];   // omega / diag (0 for an isolated cell)
+  TP wid[kMaxLevels][27];   // omega_1 / diag (0 for an isolated cell)
+  TP wid2[kMaxLevels][27];  // omega_2 / diag
+  TP widc[kMaxLevels][27];  // kOmega / diag (coarsest-level sweeps)
   double diag64[27];        // fine-grid FP64 diagonal
 };
 
@@ -197,7 +213,8 @@ __device__ __forceinline__ void lap4(const float* v, const Item4& it, int nx, in
 }
 
 template <typename TP, bool RESIDUAL>
-__device__ void sweep4(const Level<TP>& L, const Tables<TP>& tb, int l, const float* in, float* out, Range rg) {
+__device__ void sweep4(const Level<TP>& L, const Tables<TP>& tb, int l, const float* in, float* out, Range rg,
+                       const TP* wt) {
   const int n4 = L.n >> 2;
   for (int m = rg.begin; m < n4; m += rg.stride) {
     const Item4 it = item4(L, m);
@@ -211,7 +228,7 @@ __device__ void sweep4(const Level<TP>& L, const Tables<TP>& tb, int l, const fl
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const float res = bb[q] - Av[q];
-      o[q] = RESIDUAL ? res : vin[q] + (float)tb.wid[l][code[q]] * res;
+      o[q] = RESIDUAL ? res : vin[q] + (float)wt[code[q]] * res;
     }
     st4(RESIDUAL ? (float*)L.r : out, it.c, make_float4(o[0], o[1], o[2], o[3]));
   }
@@ -219,10 +236,11 @@ __device__ void sweep4(const Level<TP>& L, const Tables<TP>& tb, int l, const fl
 
 // out = in + omega D^-1 (b - A in)      (residual_only: L.r = b - A in)
 template <typename TP, bool RESIDUAL>
-__device__ void sweep(const Level<TP>& L, const Tables<TP>& tb, int l, const TP* in, TP* out, Range rg) {
+__device__ void sweep(const Level<TP>& L, const Tables<TP>& tb, int l, const TP* in, TP* out, Range rg,
+                      const TP* wt) {
   if constexpr (sizeof(TP) == 4) {
     if (L.v4) {
-      sweep4<TP, RESIDUAL>(L, tb, l, (const float*)in, (float*)out, rg);
+      sweep4<TP, RESIDUAL>(L, tb, l, (const float*)in, (float*)out, rg, wt);
       return;
     }
   }
@@ -248,21 +266,22 @@ __device__ void sweep(const Level<TP>& L, const Tables<TP>& tb, int l, const TP*
       if (c < L.n) {
         const TP res = bb[u] - apply_nb(q[u], L.ax, L.ay, L.az, tb.diag[l][code[u]]);
         if (RESIDUAL) L.r[c] = res;
-        else out[c] = q[u].c0 + tb.wid[l][code[u]] * res;
+        else out[c] = q[u].c0 + wt[code[u]] * res;
       }
     }
   }
 }
 
+// one weighted-Jacobi sweep with the weight table wt (tb.wid, tb.wid2 or tb.widc of level l)
 template <typename TP>
 __device__ __forceinline__ void smooth(const Level<TP>& L, const Tables<TP>& tb, int l, const TP* in, TP* out,
-                                       Range rg) {
-  sweep<TP, false>(L, tb, l, in, out, rg);
+                                       Range rg, const TP* wt) {
+  sweep<TP, false>(L, tb, l, in, out, rg, wt);
 }
 
 template <typename TP>
 __device__ __forceinline__ void residual(const Level<TP>& L, const Tables<TP>& tb, int l, const TP* in, Range rg) {
-  sweep<TP, true>(L, tb, l, in, nullptr, rg);
+  sweep<TP, true>(L, tb, l, in, nullptr, rg, tb.wid[l]);
 }
 
 __device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
@@ -420,7 +439,7 @@ __device__ bool coarsest(const Level<TP>* lev, int l, int nu_c, const Tables<TP>
   TP* b = L.t;
   for (int s = 1; s < nu_c; ++s) {
     if (!sync()) return false;
-    smooth(L, tb, l, a, b, rg);
+    smooth(L, tb, l, a, b, rg, tb.widc[l]);
     TP* tmp = a;
     a = b;
     b = tmp;
@@ -435,7 +454,7 @@ __device__ bool down(const Level<TP>* lev, const Tables<TP>& tb, int lo, int hi,
   for (int l = lo; l < hi; ++l) {
     const Level<TP>& L = lev[l];
     if (!sync()) return false;
-    smooth(L, tb, l, L.x, L.t, rg);           // second pre-smoothing sweep -> t
+    smooth(L, tb, l, L.x, L.t, rg, tb.wid2[l]);   // second pre-smoothing sweep -> t
     if (!sync()) return false;
     residual(L, tb, l, L.t, rg);
     if (!sync()) return false;
@@ -453,9 +472,9 @@ __device__ bool up(const Level<TP>* lev, const Tables<TP>& tb, int hi, int lo, R
     if (l != hi && !sync()) return false;
     prolong_add(L, lev[l + 1], lev[l + 1].t, L.t, rg);
     if (!sync()) return false;
-    smooth(L, tb, l, L.t, L.x, rg);           // post-smoothing sweep 1 -> x
+    smooth(L, tb, l, L.t, L.x, rg, tb.wid2[l]);   // post-smoothing sweep 1 -> x
     if (!sync()) return false;
-    smooth(L, tb, l, L.x, L.t, rg);           // post-smoothing sweep 2 -> t
+    smooth(L, tb, l, L.x, L.t, rg, tb.wid[l]);    // post-smoothing sweep 2 -> t
   }
   return true;
 }
@@ -794,7 +813,9 @@ __global__ void __launch_bounds__(kBlock, 1) k_pcg_mg(MGArgs<TP> A) {
     const double ax = (double)A.lev[l].ax, ay = (double)A.lev[l].ay, az = (double)A.lev[l].az;
     const double d = (double)(c % 3) * ax + (double)((c / 3) % 3) * ay + (double)(c / 9) * az;
     tb.diag[l][c] = (TP)d;
-    tb.wid[l][c] = d > 0.0 ? (TP)(kOmega / d) : TP(0);
+    tb.wid[l][c] = d > 0.0 ? (TP)(kOmega1 / d) : TP(0);
+    tb.wid2[l][c] = d > 0.0 ? (TP)(kOmega2 / d) : TP(0);
+    tb.widc[l][c] = d > 0.0 ? (TP)(kOmega / d) : TP(0);
   }
   if (threadIdx.x < 27) {
     const int c = threadIdx.x;
