@@ -430,7 +430,8 @@ ss_status stage_lever(ss_case* c) {
 
 // The u*, v*, w* systems of Eq. 3.3 are independent (each uses u^n only):
 // one cooperative launch solves all of them, one team of blocks per
-// component. Its time and its launch are counted under solve_u.
+// component. Its time and its launch are counted under solve_u. Used for
+// cases up to kJointMomentumMaxCells.
 ss_status stage_solve_momentum(ss_case* c) {
   StageTimer tm(c, SS_PROF_SOLVE + SS_SYS_U, 1);
   const int ncomp = c->pr.dim;
@@ -451,11 +452,24 @@ ss_status stage_solve_momentum(ss_case* c) {
   return SS_OK;
 }
 
+// Largest case (cells) whose momentum systems are solved in one joint launch.
+// Measured: at 1.2 M cells the joint launch is 7% faster than three
+// sequential solves (each solve alone is latency-bound); at 25 M cells it is
+// 15% slower (each team streams its own vectors from HBM on a third of the
+// SMs, and the team with the most iterations sets the time).
+constexpr long long kJointMomentumMaxCells = 1LL << 22;
+
 ss_status one_step(ss_case* c) {
   const int ncomp = c->pr.dim;
-  for (int a = 0; a < ncomp; ++a)             // 1: intermediate velocity (Eq. 3.3)
-    STAGE_TRY(stage_assemble(c, a));
-  STAGE_TRY(stage_solve_momentum(c));
+  if (c->n_cell <= kJointMomentumMaxCells) {  // 1: intermediate velocity (Eq. 3.3)
+    for (int a = 0; a < ncomp; ++a) STAGE_TRY(stage_assemble(c, a));
+    STAGE_TRY(stage_solve_momentum(c));
+  } else {
+    for (int a = 0; a < ncomp; ++a) {
+      STAGE_TRY(stage_assemble(c, a));
+      STAGE_TRY(stage_solve(c, a));
+    }
+  }
   STAGE_TRY(stage_assemble(c, SS_SYS_P));     // 2: pressure correction (Eq. 3.4)
   STAGE_TRY(stage_solve(c, SS_SYS_P));
   STAGE_TRY(stage_project(c));                // 3: projection (Eq. 3.5)

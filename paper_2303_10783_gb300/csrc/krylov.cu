@@ -46,7 +46,6 @@ struct BcgArgs {
   int stat_index;
   double inner_tol;        // relative tolerance of each FP32 inner solve (mixed path)
   BcgVec<double> v64;
-  BcgVec<float> v32;
   FusedVec f32;            // vectors of the fused FP32 inner solve (mixed path)
   float* d32;              // inner correction (mixed path)
   double* partial;
@@ -90,47 +89,16 @@ __device__ __forceinline__ float4 ld4(const float* p, int m) { return reinterpre
 __device__ __forceinline__ float4 ldg4(const float* p, int m) { return __ldg(reinterpret_cast<const float4*>(p) + m); }
 __device__ __forceinline__ void st4(float* p, int m, float4 v) { reinterpret_cast<float4*>(p)[m] = v; }
 
-// Four consecutive rows 4m..4m+3 of y = A x for FP32 planes, in the same
-// order of operations as spmv_row. The y- and z-neighbour vectors are read as
-// float4 when their offsets keep 16-byte alignment (sy, sz multiples of 4),
-// else as four scalars; all loads are issued before the arithmetic.
-__device__ __forceinline__ float4 ldx4(const float* x, int r, bool aligned) {
-  if (aligned) return *reinterpret_cast<const float4*>(x + r);
-  return make_float4(x[r], x[r + 1], x[r + 2], x[r + 3]);
-}
-
-__device__ __forceinline__ float4 spmv4(const Planes<float>& a, const float* x, int m, int sy, int sz, int has_z,
-                                        bool ay, bool az) {
-  const int r = 4 * m;
-  const float4 P = ldg4(a.P, m), W = ldg4(a.W, m), E = ldg4(a.E, m), S = ldg4(a.S, m), N = ldg4(a.N, m);
-  const float4 xc = ld4(x, m);
-  const float xw = x[r - 1], xe = x[r + 4];
-  const float4 xs = ldx4(x, r - sy, ay), xn = ldx4(x, r + sy, ay);
-  float4 o;
-  o.x = P.x * xc.x; o.y = P.y * xc.y; o.z = P.z * xc.z; o.w = P.w * xc.w;
-  o.x = fmaf(W.x, xw, o.x); o.y = fmaf(W.y, xc.x, o.y); o.z = fmaf(W.z, xc.y, o.z); o.w = fmaf(W.w, xc.z, o.w);
-  o.x = fmaf(E.x, xc.y, o.x); o.y = fmaf(E.y, xc.z, o.y); o.z = fmaf(E.z, xc.w, o.z); o.w = fmaf(E.w, xe, o.w);
-  o.x = fmaf(S.x, xs.x, o.x); o.y = fmaf(S.y, xs.y, o.y); o.z = fmaf(S.z, xs.z, o.z); o.w = fmaf(S.w, xs.w, o.w);
-  o.x = fmaf(N.x, xn.x, o.x); o.y = fmaf(N.y, xn.y, o.y); o.z = fmaf(N.z, xn.z, o.z); o.w = fmaf(N.w, xn.w, o.w);
-  if (has_z) {
-    const float4 B = ldg4(a.B, m), T = ldg4(a.T_, m);
-    const float4 xb = ldx4(x, r - sz, az), xt = ldx4(x, r + sz, az);
-    o.x = fmaf(B.x, xb.x, o.x); o.y = fmaf(B.y, xb.y, o.y); o.z = fmaf(B.z, xb.z, o.z); o.w = fmaf(B.w, xb.w, o.w);
-    o.x = fmaf(T.x, xt.x, o.x); o.y = fmaf(T.y, xt.y, o.y); o.z = fmaf(T.z, xt.z, o.z); o.w = fmaf(T.w, xt.w, o.w);
-  }
-  return o;
-}
-
 struct CoreOut {
   int it;
   bool conv;
   double res, bnorm;
 };
 
-// Jacobi-preconditioned BiCGSTAB on A x = b in precision T (vectors and
-// planes). zero_x0: start from x = 0 without the initial SpMV. Per-thread
-// dot-product partials accumulate in T (so the FP32 inner solve issues no
-// FP64 work); block and grid reductions are FP64 and deterministic.
+// Jacobi-preconditioned BiCGSTAB on A x = b in precision T (the FP64 solver;
+// the mixed path's FP32 inner solve is bcg_fused). zero_x0: start from x = 0
+// without the initial SpMV. Block and grid reductions are FP64 and
+// deterministic.
 // Reduction slots 0..7. Returns false if a grid barrier gave up.
 template <typename T>
 __device__ bool bcg_core(const Planes<T>& a, int n, int sy, int sz, int has_z, const T* b, T* x, bool zero_x0,
@@ -168,7 +136,6 @@ __device__ bool bcg_core(const Planes<T>& a, int n, int sy, int sz, int has_z, c
     return true;
   }
   const double thr = tol * out.bnorm;
-  const bool ay = (sy & 3) == 0, az = (sz & 3) == 0;
   double rho = tot.v[0], rho_old = 1.0, alpha = 1.0, omega = 1.0;
   int it = 0;
   bool conv = res <= thr;
@@ -176,40 +143,14 @@ __device__ bool bcg_core(const Planes<T>& a, int n, int sy, int sz, int has_z, c
     ++it;
     const T beta = (T)((rho / rho_old) * (alpha / omega));
     const T om = (T)omega;
-    int tail = 0;                                 // p = r + beta (p - omega v); y = M^-1 p
-    if constexpr (sizeof(T) == 4) {
-      const int n4 = n >> 2;
-      for (int m = t0; m < n4; m += gs) {
-        const float4 rv = ld4(r, m), pv = ld4(p, m), vv = ld4(v, m), dv = ldg4(a.idiag, m);
-        float4 po, yo;
-        po.x = rv.x + beta * (pv.x - om * vv.x);
-        po.y = rv.y + beta * (pv.y - om * vv.y);
-        po.z = rv.z + beta * (pv.z - om * vv.z);
-        po.w = rv.w + beta * (pv.w - om * vv.w);
-        yo.x = dv.x * po.x; yo.y = dv.y * po.y; yo.z = dv.z * po.z; yo.w = dv.w * po.w;
-        st4(p, m, po);
-        st4(y, m, yo);
-      }
-      tail = n4 << 2;
-    }
-    for (int i = tail + t0; i < n; i += gs) {
+    for (int i = t0; i < n; i += gs) {          // p = r + beta (p - omega v); y = M^-1 p
       const T pi = r[i] + beta * (p[i] - om * v[i]);
       p[i] = pi;
       y[i] = __ldg(a.idiag + i) * pi;
     }
     if (!team_barrier(st, tm, epoch)) return false;
     T s1 = T(0);
-    tail = 0;                                     // v = A y
-    if constexpr (sizeof(T) == 4) {
-      const int n4 = n >> 2;
-      for (int m = t0; m < n4; m += gs) {
-        const float4 vv = spmv4(a, y, m, sy, sz, has_z, ay, az), hv = ld4(rh, m);
-        st4(v, m, vv);
-        s1 += (hv.x * vv.x + hv.y * vv.y) + (hv.z * vv.z + hv.w * vv.w);
-      }
-      tail = n4 << 2;
-    }
-    for (int i = tail + t0; i < n; i += gs) {
+    for (int i = t0; i < n; i += gs) {          // v = A y
       const T vi = spmv_row(a, y, i, sy, sz, has_z);
       v[i] = vi;
       s1 += rh[i] * vi;
@@ -219,21 +160,7 @@ __device__ bool bcg_core(const Planes<T>& a, int n, int sy, int sz, int has_z, c
     alpha = rho / o1.v[0];
     const T al = (T)alpha;
     T s2 = T(0);
-    tail = 0;                                     // s = r - alpha v (in r); z = M^-1 s
-    if constexpr (sizeof(T) == 4) {
-      const int n4 = n >> 2;
-      for (int m = t0; m < n4; m += gs) {
-        const float4 rv = ld4(r, m), vv = ld4(v, m), dv = ldg4(a.idiag, m);
-        float4 so, zo;
-        so.x = rv.x - al * vv.x; so.y = rv.y - al * vv.y; so.z = rv.z - al * vv.z; so.w = rv.w - al * vv.w;
-        zo.x = dv.x * so.x; zo.y = dv.y * so.y; zo.z = dv.z * so.z; zo.w = dv.w * so.w;
-        st4(r, m, so);
-        st4(z, m, zo);
-        s2 += (so.x * so.x + so.y * so.y) + (so.z * so.z + so.w * so.w);
-      }
-      tail = n4 << 2;
-    }
-    for (int i = tail + t0; i < n; i += gs) {
+    for (int i = t0; i < n; i += gs) {          // s = r - alpha v (in r); z = M^-1 s
       const T si = r[i] - al * v[i];
       r[i] = si;
       z[i] = __ldg(a.idiag + i) * si;
@@ -248,18 +175,7 @@ __device__ bool bcg_core(const Planes<T>& a, int n, int sy, int sz, int has_z, c
       break;
     }
     T s3 = T(0), s4 = T(0);
-    tail = 0;                                     // t = A z
-    if constexpr (sizeof(T) == 4) {
-      const int n4 = n >> 2;
-      for (int m = t0; m < n4; m += gs) {
-        const float4 tv = spmv4(a, z, m, sy, sz, has_z, ay, az), rv = ld4(r, m);
-        st4(t, m, tv);
-        s3 += (tv.x * rv.x + tv.y * rv.y) + (tv.z * rv.z + tv.w * rv.w);
-        s4 += (tv.x * tv.x + tv.y * tv.y) + (tv.z * tv.z + tv.w * tv.w);
-      }
-      tail = n4 << 2;
-    }
-    for (int i = tail + t0; i < n; i += gs) {
+    for (int i = t0; i < n; i += gs) {          // t = A z
       const T ti = spmv_row(a, z, i, sy, sz, has_z);
       t[i] = ti;
       s3 += ti * r[i];
@@ -270,23 +186,7 @@ __device__ bool bcg_core(const Planes<T>& a, int n, int sy, int sz, int has_z, c
     omega = (o3.v[1] > 0.0) ? o3.v[0] / o3.v[1] : 0.0;
     const T omn = (T)omega;
     T s5 = T(0), s6 = T(0);
-    tail = 0;                                     // x += alpha y + omega z; r = s - omega t
-    if constexpr (sizeof(T) == 4) {
-      const int n4 = n >> 2;
-      for (int m = t0; m < n4; m += gs) {
-        const float4 xv = ld4(x, m), yv = ld4(y, m), zv = ld4(z, m), rv = ld4(r, m), tv = ld4(t, m), hv = ld4(rh, m);
-        float4 xo, ro;
-        xo.x = xv.x + al * yv.x + omn * zv.x; xo.y = xv.y + al * yv.y + omn * zv.y;
-        xo.z = xv.z + al * yv.z + omn * zv.z; xo.w = xv.w + al * yv.w + omn * zv.w;
-        ro.x = rv.x - omn * tv.x; ro.y = rv.y - omn * tv.y; ro.z = rv.z - omn * tv.z; ro.w = rv.w - omn * tv.w;
-        st4(x, m, xo);
-        st4(r, m, ro);
-        s5 += (hv.x * ro.x + hv.y * ro.y) + (hv.z * ro.z + hv.w * ro.w);
-        s6 += (ro.x * ro.x + ro.y * ro.y) + (ro.z * ro.z + ro.w * ro.w);
-      }
-      tail = n4 << 2;
-    }
-    for (int i = tail + t0; i < n; i += gs) {
+    for (int i = t0; i < n; i += gs) {          // x += alpha y + omega z; r = s - omega t
       x[i] += al * y[i] + omn * z[i];
       const T ri = r[i] - omn * t[i];
       r[i] = ri;
@@ -818,7 +718,6 @@ cudaError_t launch_bicgstab_multi(const Sys* const* sys, int nsys, int has_z, co
     A.stat_index = ctl[q].stat_index;
     A.inner_tol = ctl[q].inner_tol;
     A.v64 = {c.v[0], c.v[1], c.v[2], c.v[3], c.v[4], c.v[5], c.v[6]};
-    A.v32 = {c.f[0], c.f[1], c.f[2], c.f[3], c.f[4], c.f[5], c.f[6]};
     A.f32 = {c.f[0], c.f[1], c.f[2], c.f[3], c.f[4], c.f[5], c.f[6], c.f[8]};
     A.d32 = c.f[7];
     A.partial = c.partial;
