@@ -64,6 +64,8 @@ def parse():
                          "ingot: 384x256x256")
     ap.add_argument("--requests", type=int, default=24, help="serving: requests in the sample")
     ap.add_argument("--request-steps", type=int, default=100, help="serving: steps per request in the sample")
+    ap.add_argument("--block-cap", type=int, default=0,
+                    help="serving: blocks per cooperative solver launch of each request (0: no cap)")
     ap.add_argument("--nx", type=int, default=128)
     ap.add_argument("--ny", type=int, default=96)
     ap.add_argument("--nz", type=int, default=96)
@@ -430,6 +432,11 @@ def run_batched(args):
     sampler = ClockSampler(local)
     b.step(args.warmup)
     b.sync()
+    # project autotuner: the solver block cap that steps this batch fastest
+    # (trials run from a saved state that is restored, outside the timed region)
+    cap, trials = b.autotune()
+    for _, c, _ in b.members:
+        c.get_profile()   # count launches of the timed region only
     barrier(dist)
     sampler.start()
     dt, _ = b.run(args.steps)
@@ -446,7 +453,9 @@ def run_batched(args):
                           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
                           "data": "synthetic", "status": solid.STATUS_NAMES.get(status, status),
                           "config": {"workload": "batched_64_cavities", "cases": len(cs), "cells": cells,
-                                     "precision": "mixed", "streams": len(cs), "graphs": True},
+                                     "precision": "mixed", "streams": len(cs), "graphs": True,
+                                     "block_cap": cap,
+                                     "autotune_ms_per_step": {str(k): 1e3 * v for k, v in trials.items()}},
                           "clocks": clocks, "gpu_launches": kernels}))
     return 0
 
@@ -458,7 +467,7 @@ def run_serving(args):
     from paper_2303_10783_gb300.serve import Server
     torch.cuda.set_device(0)
     reqs = cases.serving_requests(n=args.requests, steps=args.request_steps)
-    srv = Server(budget_bytes=150 * 10 ** 9, chunk=10)
+    srv = Server(budget_bytes=150 * 10 ** 9, chunk=10, block_cap=args.block_cap)
     rep = srv.run(reqs)
     print(json.dumps({"metric": "cell-steps/s", "value": rep["cell_steps_per_s"], "unit": "cell-steps/s",
                       "n_gpus": 1, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,

@@ -202,6 +202,17 @@ ss_status ss_set_fields(ss_case* c, unsigned mask, const void* const* src, int s
  * Eq. 3.18 (capped at C_e), C_s = kp C_l (Eq. 3.19). */
 ss_status ss_equilibrate(ss_case* c);
 
+/* Cap the blocks of every cooperative solver launch of this case at
+ * max_blocks (0: no cap; the device's co-resident limit applies). Cases
+ * stepped side by side on their own streams then share the GPU: a small case
+ * whose solves are bound by synchronisation keeps few SMs busy for long, so
+ * fewer blocks per case let more cases run at once. The block count sets the
+ * order of the solvers' reductions: fields are deterministic for a given cap
+ * and differ at rounding level between caps. A launch that solves the
+ * momentum components together takes at least one block per component.
+ * Drops a captured step graph. SS_EINVAL for max_blocks < 0. */
+ss_status ss_set_block_cap(ss_case* c, int max_blocks);
+
 /* The FP64 -> FP32 rounding (to nearest, ties to even) that forms the FP32
  * plane copies, applied to n device values src -> dst in order on `stream`
  * (a cudaStream_t; NULL: the legacy default stream). For checking that

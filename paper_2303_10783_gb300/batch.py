@@ -65,6 +65,49 @@ class Batch:
         dt = time.perf_counter() - t0
         return dt, self.cells * steps / dt
 
+    def set_block_cap(self, max_blocks):
+        for _, c, _ in self.members:
+            c.set_block_cap(max_blocks)
+
+    def autotune(self, caps=(0, 64, 32, 16, 8), steps=2):
+        """Choose the solver block cap (``ss_set_block_cap``) that steps this
+        batch fastest. A cooperative solve of a small case is bound by its
+        synchronisations, not by its SMs; fewer blocks per case let more
+        cases' solves run at once, but too few starve the larger cases.
+        Each candidate steps the batch ``steps`` times from the same state;
+        the state (every field and the case time) is saved before and
+        restored after each trial, so tuning leaves the cases where they
+        were. Returns (best cap, {cap: seconds per step})."""
+        import torch
+        saved = []
+        for _, c, _ in self.members:
+            f = c.get_fields(device=True)
+            saved.append((f, c.get_time()))
+
+        def restore():
+            for (f, t), (_, c, _) in zip(saved, self.members):
+                c.set_fields(f)
+                c.set_time(t)
+            for _, c, _ in self.members:
+                c.sync()
+
+        timing = {}
+        for cap in caps:
+            self.set_block_cap(cap)
+            self.step(1)                 # captures each case's graph with this launch shape
+            self.sync()
+            restore()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            self.step(steps)
+            self.sync()
+            torch.cuda.synchronize()
+            timing[cap] = (time.perf_counter() - t0) / steps
+            restore()
+        best = min(timing, key=timing.get)
+        self.set_block_cap(best)
+        return best, timing
+
     def fields(self, q):
         return self.members[q][1].get_fields()
 

@@ -94,6 +94,7 @@ struct ss_case {
   // captured step graph
   cudaGraphExec_t graph;
   long long graph_kernels;   // library kernels per captured step
+  int block_cap;             // > 0: blocks per cooperative solver launch at most (ss_set_block_cap)
 };
 
 namespace {
@@ -384,6 +385,7 @@ ss_status stage_solve(ss_case* c, int sys) {
   StageTimer tm(c, SS_PROF_SOLVE + (sys >= 0 && sys < SS_NSYS ? sys : 0), 1);
   SolverCtl ctl;
   ctl.mixed = c->g.precision == SS_MIXED;
+  ctl.block_cap = c->block_cap;
   ctl.stat_index = sys;
   ctl.inner_tol = sys == SS_SYS_P ? kInnerTolPressure : sys == SS_SYS_T ? kInnerTolEnergy : kInnerTolTransport;
   cudaError_t e;
@@ -440,6 +442,7 @@ ss_status stage_solve_momentum(ss_case* c) {
   Scratch* sc[kMaxTeams];
   for (int q = 0; q < ncomp; ++q) {
     ctl[q].mixed = c->g.precision == SS_MIXED;
+    ctl[q].block_cap = c->block_cap;
     ctl[q].stat_index = q;
     ctl[q].inner_tol = kInnerTolTransport;
     ctl[q].tol = c->g.tol_t;
@@ -691,6 +694,14 @@ ss_status ss_equilibrate(ss_case* c) {
   if (!c->alloy_set) return fail(SS_ESTATE, "set_alloy first");
   cudaError_t e = launch_equilibrate(c->pr, c->T, c->C, c->gl, c->Cl, c->Cs, c->Kinv, c->Ag, 1, 1, c->stream);
   if (e != cudaSuccess) return fail(SS_ECUDA, "equilibrate: %s", cudaGetErrorString(e));
+  return SS_OK;
+}
+
+ss_status ss_set_block_cap(ss_case* c, int max_blocks) {
+  STAGE_TRY(check_case(c));
+  if (max_blocks < 0) return fail(SS_EINVAL, "max_blocks must be >= 0");
+  drop_graph(c);   // launch configurations are part of a captured step
+  c->block_cap = max_blocks;
   return SS_OK;
 }
 

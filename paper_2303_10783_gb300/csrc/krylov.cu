@@ -730,6 +730,8 @@ cudaError_t launch_bicgstab_multi(const Sys* const* sys, int nsys, int has_z, co
   // proportion to the rows when the teams together exceed what one
   // cooperative launch can keep resident
   int lim = coop_limit(kern);
+  // a cap below one block per team is raised to that
+  if (ctl[0].block_cap > 0 && lim > ctl[0].block_cap) lim = ctl[0].block_cap > nsys ? ctl[0].block_cap : nsys;
   long long want[kMaxTeams], rows = 0, total = 0;
   for (int q = 0; q < nsys; ++q) {
     if (lim > sc[q]->max_blocks) lim = sc[q]->max_blocks;
@@ -787,7 +789,8 @@ cudaError_t launch_pcg_poisson(const Params& pr, double* b, double* x, const Sol
   A.max_blocks = sc.max_blocks;
   A.st = st;
   const long long n = (long long)pr.nx * pr.ny * pr.nz;
-  const int nb = blocks_for((const void*)k_pcg_poisson, n, sc.max_blocks);
+  const int nb = blocks_for((const void*)k_pcg_poisson, n,
+                            ctl.block_cap > 0 && ctl.block_cap < sc.max_blocks ? ctl.block_cap : sc.max_blocks);
   cudaError_t e = cudaMemsetAsync(&st->barrier, 0, sizeof(unsigned int), s);
   if (e != cudaSuccess) return e;
   void* args[] = {&A};

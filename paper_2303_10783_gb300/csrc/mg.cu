@@ -992,7 +992,8 @@ cudaError_t launch_t(const MGPlan& pl, const Params& pr, double* b, double* x, c
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const long long n = (long long)pr.nx * pr.ny * pr.nz;
-  const int nb = coop_blocks_for_smem(kern, n, sc.max_blocks, smem);
+  const int nb = coop_blocks_for_smem(kern, n, ctl.block_cap > 0 && ctl.block_cap < sc.max_blocks ? ctl.block_cap
+                                                                                          : sc.max_blocks, smem);
   if ((e = cudaMemsetAsync(&st->barrier, 0, sizeof(unsigned int), s)) != cudaSuccess) return e;
   void* args[] = {&A};
   return cudaLaunchCooperativeKernel(kern, dim3(nb), dim3(kBlock), args, smem, s);

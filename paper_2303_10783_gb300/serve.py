@@ -37,10 +37,13 @@ class Request:
 class Server:
     """``budget_bytes``: HBM the active requests' workspaces may hold.
     ``chunk``: steps per request per round. ``keep_results``: copy each
-    finished request's fields to the host (for checks)."""
+    finished request's fields to the host (for checks). ``block_cap``: blocks
+    per cooperative solver launch of each request (0: no cap); requests that
+    share the GPU run more of their solves at once with a cap."""
 
-    def __init__(self, budget_bytes, precision=solid.SS_MIXED, chunk=10, keep_results=False):
+    def __init__(self, budget_bytes, precision=solid.SS_MIXED, chunk=10, keep_results=False, block_cap=0):
         self.budget = int(budget_bytes)
+        self.block_cap = int(block_cap)
         self.precision = precision
         self.chunk = int(chunk)
         self.keep = keep_results
@@ -53,6 +56,8 @@ class Server:
         r.stream = torch.cuda.Stream()
         with torch.cuda.stream(r.stream):
             r.sim = solid.Case(r.case, precision=self.precision, stream=r.stream)
+            if self.block_cap:
+                r.sim.set_block_cap(self.block_cap)
             f = cases_mod.initial_fields(r.case)
             r.sim.initialize(f["T"], f["C"])
         r.admitted = now

@@ -83,6 +83,7 @@ def _declare(lib):
         "ss_equilibrate": [P],
         "ss_get_stats": [P, ctypes.POINTER(Stats)],
         "ss_set_time": [P, ctypes.c_double],
+        "ss_set_block_cap": [P, ctypes.c_int],
         "ss_get_time": [P, ctypes.POINTER(ctypes.c_double)],
         "ss_destroy": [P],
         "ss_assemble": [P, ctypes.c_int],
@@ -189,6 +190,10 @@ class Case:
     def set_boundary(self, face, thermal, h=0.0, Text=0.0, dTdt=0.0, flow=SS_NOSLIP):
         bc = BC(thermal, h, Text, dTdt, flow)
         check(self.lib.ss_set_boundary(self.h, FACE_ID[face] if isinstance(face, str) else face, ctypes.byref(bc)))
+
+    def set_block_cap(self, max_blocks):
+        """At most ``max_blocks`` blocks per cooperative solver launch (0: no cap)."""
+        check(self.lib.ss_set_block_cap(self.h, int(max_blocks)))
 
     def set_time(self, t):
         check(self.lib.ss_set_time(self.h, float(t)))

@@ -100,3 +100,56 @@ def test_mixed_pressure_refinement_does_not_stall(lib):
         assert s["iters"]["p"] <= 40, s["iters"]
         assert s["relres"]["p"] <= case["tol_p"]
     c.close()
+
+
+def test_block_cap_is_deterministic_and_batch_equals_alone(lib):
+    """With a solver block cap the fields are again bit-reproducible, and a
+    capped case gives the same fields alone and in a capped batch; the cap only
+    reorders reductions, so capped and uncapped runs agree to rounding."""
+    import ctypes
+    case = cases.box_3d(24, 16, 12)
+    def run(cap, graph):
+        import torch
+        stream = torch.cuda.Stream()
+        with torch.cuda.stream(stream):
+            c = solid.Case(case, precision=solid.SS_MIXED, stream=stream)
+            c.set_block_cap(cap)
+            f = cases.initial_fields(case)
+            c.initialize(f["T"], f["C"])
+            for _ in range(5):
+                c.step_graph(1) if graph else c.step(1)
+            c.sync()
+            out = c.get_fields()
+            c.close()
+        return out
+    a, b = run(4, False), run(4, True)
+    assert _same(a, b)
+    full = run(0, False)
+    for k in ("T", "C", "gl", "p"):
+        assert np.abs(a[k] - full[k]).max() <= 1e-9 * np.abs(full[k]).max(), k
+    others = [cases.box_3d(16, 12, 8, seed=3), cases.cavity_2d(40, 24)]
+    bt = Batch([case] + others, precision=solid.SS_MIXED)
+    bt.set_block_cap(4)
+    bt.step(5)
+    bt.sync()
+    assert _same(bt.fields(0), a)
+    bt.close()
+    c = solid.Case(case)
+    assert lib.ss_set_block_cap(c.h, -1) == solid.SS_EINVAL
+    c.close()
+
+
+def test_batch_autotune_restores_state(lib):
+    """The batch autotuner times each candidate cap from a saved state and
+    restores it: the cases' fields after tuning equal those before."""
+    cs = [cases.box_3d(20, 12, 10, seed=4), cases.cavity_2d(48, 32)]
+    bt = Batch(cs, precision=solid.SS_MIXED)
+    bt.step(2)
+    bt.sync()
+    before = [bt.fields(q) for q in range(len(cs))]
+    best, timing = bt.autotune(caps=(0, 8, 2), steps=1)
+    assert best in (0, 8, 2) and set(timing) == {0, 8, 2}
+    after = [bt.fields(q) for q in range(len(cs))]
+    for x, y in zip(before, after):
+        assert _same(x, y)
+    bt.close()
