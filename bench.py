@@ -64,8 +64,9 @@ def parse():
                          "ingot: 384x256x256")
     ap.add_argument("--requests", type=int, default=24, help="serving: requests in the sample")
     ap.add_argument("--request-steps", type=int, default=100, help="serving: steps per request in the sample")
-    ap.add_argument("--block-cap", type=int, default=0,
-                    help="serving: blocks per cooperative solver launch of each request (0: no cap)")
+    ap.add_argument("--block-cap", type=int, default=-1,
+                    help="serving: blocks per cooperative solver launch of each request (0: no cap; "
+                         "-1: in proportion to the request's cells)")
     ap.add_argument("--nx", type=int, default=128)
     ap.add_argument("--ny", type=int, default=96)
     ap.add_argument("--nz", type=int, default=96)

@@ -38,8 +38,9 @@ class Server:
     """``budget_bytes``: HBM the active requests' workspaces may hold.
     ``chunk``: steps per request per round. ``keep_results``: copy each
     finished request's fields to the host (for checks). ``block_cap``: blocks
-    per cooperative solver launch of each request (0: no cap); requests that
-    share the GPU run more of their solves at once with a cap."""
+    per cooperative solver launch of each request (0: no cap; -1: in
+    proportion to the request's size); requests that share the GPU run more
+    of their solves at once with a cap."""
 
     def __init__(self, budget_bytes, precision=solid.SS_MIXED, chunk=10, keep_results=False, block_cap=0):
         self.budget = int(budget_bytes)
@@ -51,13 +52,22 @@ class Server:
         self.max_active = 0
         self.max_used = 0
 
+    @staticmethod
+    def _cap_for(r):
+        """Blocks per solver launch in proportion to the request's size: one
+        per 8192 cells, at least 16; no cap once that reaches 152 (one block
+        per SM of this GPU)."""
+        cap = max(16, r.cells // 8192)
+        return 0 if cap >= 152 else cap
+
     def _admit(self, r, now):
         import torch
         r.stream = torch.cuda.Stream()
         with torch.cuda.stream(r.stream):
             r.sim = solid.Case(r.case, precision=self.precision, stream=r.stream)
-            if self.block_cap:
-                r.sim.set_block_cap(self.block_cap)
+            cap = self._cap_for(r) if self.block_cap < 0 else self.block_cap
+            if cap:
+                r.sim.set_block_cap(cap)
             f = cases_mod.initial_fields(r.case)
             r.sim.initialize(f["T"], f["C"])
         r.admitted = now
