@@ -264,6 +264,15 @@ const char* ss_last_error(void);
  *   (n floats each); NULL entries are skipped. Each plane entry is its FP64
  *   entry rounded to nearest, ties to even; the inverse diagonal is the FP32
  *   reciprocal of the FP32 P.
+ * ss_assemble_forward(c, sys): validation mode of ss_assemble (Sec. 4,
+ *   forward method, Eq. 4.5-4.7): the row equations are written from their
+ *   fluxes and wall ghosts and the DIA planes and right-hand side recovered by
+ *   residual probing with 3-colour trial vectors. It writes the same buffers
+ *   as ss_assemble (ss_get_system then returns them; a following ss_solve
+ *   uses them) and should agree with it to rounding. It evaluates each row's
+ *   equation 8 times (about 30x the time of ss_assemble: 3 ms against
+ *   0.1 ms per system at 1.2 M rows). SS_EINVAL for SS_SYS_P (no planes) or
+ *   an unknown system.
  * ss_project(c): Eq. 3.5 with the solved u* and p'; p += p'.
  * ss_lever(c): Eq. 3.13-3.19 treating the current T field as T*, the
  *   current g_l as g_l^n and the current C as C^{n+1}; it closes a step and
@@ -273,6 +282,7 @@ ss_status ss_assemble(ss_case* c, int sys);
 ss_status ss_solve(ss_case* c, int sys);
 ss_status ss_get_system(ss_case* c, int sys, void* const* dst, int dst_is_device);
 ss_status ss_get_system_f32(ss_case* c, int sys, void* const* dst, int dst_is_device);
+ss_status ss_assemble_forward(ss_case* c, int sys);
 ss_status ss_project(ss_case* c);
 ss_status ss_lever(ss_case* c);
 

@@ -398,6 +398,181 @@ __global__ void __launch_bounds__(kBlockA) k_equilibrate(Params pr, const double
   }
 }
 
+
+// ---- Forward assembly (Sec. 4, Eq. 4.5-4.7), a validation mode.
+//
+// The discrete equation of each row, Eq_r(phi), is written straight from its
+// fluxes and wall ghosts (independently of the term-wise kernels above).
+// Eq is affine, Eq(phi) = A phi - b, so b = -Eq(0), and the coefficient of
+// row r on stencil point q is Eq_r(e) - Eq_r(0) for the trial vector e that
+// is 1 on the cells of q's colour (colour = (i mod 3, j mod 3, k mod 3)): the
+// seven points of a stencil have seven distinct colours. A trial vector is a
+// function of the indices, so no probe vector is stored.
+__device__ __forceinline__ int colour_of(int i, int j, int k) { return (i % 3) + 3 * (j % 3) + 9 * (k % 3); }
+
+// (phi F) on a face with phi_back behind and phi_front in front: first-order upwind
+__device__ __forceinline__ double upwind_flux(double F, double back, double front) {
+  return (F >= 0.0 ? back : front) * F;
+}
+
+// Eq_r of component A of the intermediate velocity (Eq. 3.3) at the face
+// (i, j, k), for the trial vector that is 1 on colour c (c < 0: all zero).
+template <int A>
+__device__ double momentum_equation(const Params& pr, const double* const vel[3], const double* p, const double* T,
+                                    const double* Cl, const double* Kinv, int i, int j, int k, int c) {
+  const int n[3] = {pr.nx, pr.ny, pr.nz};
+  const int idx[3] = {i, j, k};
+  const double h[3] = {pr.hx, pr.hy, pr.hz};
+  const int fx = pr.nx + (A == 0), fy = pr.ny + (A == 1);
+  auto trial = [&](int ii, int jj, int kk) -> double { return (c >= 0 && colour_of(ii, jj, kk) == c) ? 1.0 : 0.0; };
+  auto u_at = [&](int d, int ii, int jj, int kk) -> double {
+    const int gx = pr.nx + (d == 0), gy = pr.ny + (d == 1);
+    return vel[d][ii + gx * (jj + gy * kk)];
+  };
+  const double P = trial(i, j, k);
+  if (idx[A] == 0 || idx[A] == n[A]) return P;            // wall face: phi - 0
+  const double nu = pr.mu / pr.rho;
+  int lo[3] = {i, j, k};
+  lo[A] -= 1;                                               // the cells on either side of the face
+  const double own = vel[A][i + fx * (j + fy * k)];
+  double r = (P - own) / pr.dt;
+  for (int d = 0; d < pr.dim; ++d) {
+    int f[3] = {i, j, k}, b[3] = {i, j, k};
+    f[d] += 1;
+    b[d] -= 1;
+    double Uf, Ub, Pf, Pb;
+    if (d == A) {
+      Uf = 0.5 * (own + u_at(A, f[0], f[1], f[2]));
+      Ub = 0.5 * (u_at(A, b[0], b[1], b[2]) + own);
+      Pf = (f[A] == n[A]) ? 0.0 : trial(f[0], f[1], f[2]);  // the wall face holds 0
+      Pb = (b[A] == 0) ? 0.0 : trial(b[0], b[1], b[2]);
+    } else {
+      int lf[3] = {lo[0], lo[1], lo[2]}, hf[3] = {i, j, k};
+      lf[d] += 1;
+      hf[d] += 1;
+      Uf = 0.5 * (u_at(d, lf[0], lf[1], lf[2]) + u_at(d, hf[0], hf[1], hf[2]));
+      Ub = 0.5 * (u_at(d, lo[0], lo[1], lo[2]) + u_at(d, i, j, k));
+      // beyond a wall: ghost = -phi (no-slip) or +phi (free-slip)
+      const double gf = pr.slip[2 * d + 1] ? P : -P, gb = pr.slip[2 * d] ? P : -P;
+      Pf = (idx[d] + 1 <= n[d] - 1) ? trial(f[0], f[1], f[2]) : gf;
+      Pb = (idx[d] - 1 >= 0) ? trial(b[0], b[1], b[2]) : gb;
+    }
+    r += (upwind_flux(Uf, P, Pf) - upwind_flux(Ub, Pb, P)) / h[d];
+    r -= nu * ((Pf - P) - (P - Pb)) / (h[d] * h[d]);
+  }
+  const int clo = lo[0] + pr.nx * (lo[1] + pr.ny * lo[2]), chi = i + pr.nx * (j + pr.ny * k);
+  r += nu * 0.5 * (Kinv[clo] + Kinv[chi]) * P;
+  r += (p[chi] - p[clo]) / (h[A] * pr.rho);
+  if (A == pr.vert) {
+    const double Tf = 0.5 * (T[clo] + T[chi]), Cf = 0.5 * (Cl[clo] + Cl[chi]);
+    r -= pr.gravity * (pr.betaT * (Tf - pr.Tref) + pr.betaC * (Cf - pr.C0));
+  }
+  return r;
+}
+
+// Eq_r of the solute step (SOLUTE: Eq. 3.7 with C_l = A_g C, Eq. 3.8-3.10)
+// or of T* (Eq. 3.12 with its cooled walls) at cell (i, j, k), for the trial
+// vector that is 1 on colour c (c < 0: all zero).
+template <bool SOLUTE>
+__device__ double cell_equation(const Params& pr, const double* const vel[3], const double* phi_n, const double* gl,
+                                const double* Ag, double t_new, int i, int j, int k, int c) {
+  const int n[3] = {pr.nx, pr.ny, pr.nz};
+  const int idx[3] = {i, j, k};
+  const double h[3] = {pr.hx, pr.hy, pr.hz};
+  const int cell = i + pr.nx * (j + pr.ny * k);
+  auto trial = [&](int ii, int jj, int kk) -> double { return (c >= 0 && colour_of(ii, jj, kk) == c) ? 1.0 : 0.0; };
+  // the transported quantity: C_l = A_g C for the solute, T itself for energy
+  auto q_at = [&](int ii, int jj, int kk) -> double {
+    const double v = trial(ii, jj, kk);
+    return SOLUTE ? v * Ag[ii + pr.nx * (jj + pr.ny * kk)] : v;
+  };
+  const double P = q_at(i, j, k);
+  double r = (trial(i, j, k) - phi_n[cell]) / pr.dt;
+  const double alpha = pr.k / (pr.rho * pr.cp);
+  for (int a = 0; a < pr.dim; ++a) {
+    int f[3] = {i, j, k}, b[3] = {i, j, k};
+    f[a] += 1;
+    b[a] -= 1;
+    const int gx = pr.nx + (a == 0), gy = pr.ny + (a == 1);
+    const double Uf = vel[a][f[0] + gx * (f[1] + gy * f[2])], Ub = vel[a][i + gx * (j + gy * k)];
+    const bool has_f = idx[a] + 1 <= n[a] - 1, has_b = idx[a] - 1 >= 0;
+    const double Qf = has_f ? q_at(f[0], f[1], f[2]) : 0.0, Qb = has_b ? q_at(b[0], b[1], b[2]) : 0.0;
+    r += (upwind_flux(Uf, P, Qf) - upwind_flux(Ub, Qb, P)) / h[a];
+    double Df = 0.0, Db = 0.0;   // zero-flux walls
+    if (SOLUTE) {
+      if (has_f) Df = pr.Dl * 0.5 * (gl[cell] + gl[f[0] + pr.nx * (f[1] + pr.ny * f[2])]);
+      if (has_b) Db = pr.Dl * 0.5 * (gl[b[0] + pr.nx * (b[1] + pr.ny * b[2])] + gl[cell]);
+    } else {
+      if (has_f) Df = alpha;
+      if (has_b) Db = alpha;
+    }
+    r -= (Df * (Qf - P) - Db * (P - Qb)) / (h[a] * h[a]);
+  }
+  if (!SOLUTE) {   // cooled walls: coef (T_P - T_w(t^{n+1}))
+    const bool wall[6] = {i == 0, i == pr.nx - 1, j == 0, j == pr.ny - 1, pr.dim == 3 && k == 0,
+                          pr.dim == 3 && k == pr.nz - 1};
+    for (int w = 0; w < 6; ++w)
+      if (wall[w] && pr.wall_coef[w] != 0.0)
+        r += pr.wall_coef[w] * (trial(i, j, k) - (pr.wall_T0[w] + pr.wall_rate[w] * t_new));
+  }
+  return r;
+}
+
+// Probe the row's equation: b = -Eq(0); each stencil coefficient from the
+// trial vector of its point's colour (0 for points outside the row grid).
+template <typename EqF>
+__device__ __forceinline__ void probe_row(const Sys& s, int r, int dim, int i, int j, int k, int mx, int my, int mz,
+                                          EqF eq) {
+  const double base = eq(-1);
+  const double P = eq(colour_of(i, j, k)) - base;
+  double nbB[3] = {0.0, 0.0, 0.0}, nbF[3] = {0.0, 0.0, 0.0};
+  const int m[3] = {mx, my, mz};
+  const int idx[3] = {i, j, k};
+  for (int a = 0; a < dim; ++a) {
+    int f[3] = {i, j, k}, b[3] = {i, j, k};
+    f[a] += 1;
+    b[a] -= 1;
+    if (idx[a] - 1 >= 0) nbB[a] = eq(colour_of(b[0], b[1], b[2])) - base;
+    if (idx[a] + 1 <= m[a] - 1) nbF[a] = eq(colour_of(f[0], f[1], f[2])) - base;
+  }
+  write_row(s, r, dim, P, nbB, nbF, -base);
+}
+
+template <int A>
+__global__ void __launch_bounds__(kBlockA) k_forward_momentum(Params pr, Sys s, const double* __restrict__ u,
+                                                             const double* __restrict__ v,
+                                                             const double* __restrict__ w,
+                                                             const double* __restrict__ p,
+                                                             const double* __restrict__ T,
+                                                             const double* __restrict__ Cl,
+                                                             const double* __restrict__ Kinv) {
+  const double* vel[3] = {u, v, w};
+  const int mx = s.d.mx, my = s.d.my, mz = s.d.mz, n = (int)s.d.n;
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+    const int i = r % mx, t = r / mx, j = t % my, k = t / my;
+    probe_row(s, r, pr.dim, i, j, k, mx, my, mz,
+              [&](int c) { return momentum_equation<A>(pr, vel, p, T, Cl, Kinv, i, j, k, c); });
+  }
+}
+
+template <bool SOLUTE>
+__global__ void __launch_bounds__(kBlockA) k_forward_cells(Params pr, Sys s, const double* __restrict__ u,
+                                                          const double* __restrict__ v,
+                                                          const double* __restrict__ w,
+                                                          const double* __restrict__ phi_n,
+                                                          const double* __restrict__ gl,
+                                                          const double* __restrict__ Ag,
+                                                          const double* __restrict__ time) {
+  const double* vel[3] = {u, v, w};
+  const int nx = pr.nx, ny = pr.ny, n = (int)s.d.n;
+  const double t_new = SOLUTE ? 0.0 : *time + pr.dt;
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+    const int i = r % nx, t = r / nx, j = t % ny, k = t / ny;
+    probe_row(s, r, pr.dim, i, j, k, nx, ny, pr.nz,
+              [&](int c) { return cell_equation<SOLUTE>(pr, vel, phi_n, gl, Ag, t_new, i, j, k, c); });
+  }
+}
+
 __global__ void __launch_bounds__(kBlockA) k_to_f32(const double* __restrict__ src, float* dst, long long n) {
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x)
     dst[q] = to_f32(src[q]);
@@ -407,6 +582,22 @@ __global__ void __launch_bounds__(kBlockA) k_to_f32(const double* __restrict__ s
 
 cudaError_t launch_to_f32(const double* src, float* dst, long long n, cudaStream_t st) {
   k_to_f32<<<grid_for(n), kBlockA, 0, st>>>(src, dst, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_forward_assemble(int sys, const Params& pr, const Sys& sy, const double* const vel[3],
+                                    const double* p, const double* T, const double* C, const double* Cl,
+                                    const double* gl, const double* Kinv, const double* Ag, const double* time,
+                                    cudaStream_t st) {
+  const int g = grid_for(sy.d.n);
+  switch (sys) {
+    case SS_SYS_U: k_forward_momentum<0><<<g, kBlockA, 0, st>>>(pr, sy, vel[0], vel[1], vel[2], p, T, Cl, Kinv); break;
+    case SS_SYS_V: k_forward_momentum<1><<<g, kBlockA, 0, st>>>(pr, sy, vel[0], vel[1], vel[2], p, T, Cl, Kinv); break;
+    case SS_SYS_W: k_forward_momentum<2><<<g, kBlockA, 0, st>>>(pr, sy, vel[0], vel[1], vel[2], p, T, Cl, Kinv); break;
+    case SS_SYS_C: k_forward_cells<true><<<g, kBlockA, 0, st>>>(pr, sy, vel[0], vel[1], vel[2], C, gl, Ag, time); break;
+    case SS_SYS_T: k_forward_cells<false><<<g, kBlockA, 0, st>>>(pr, sy, vel[0], vel[1], vel[2], T, gl, Ag, time); break;
+    default: return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 

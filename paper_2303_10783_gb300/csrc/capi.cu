@@ -822,6 +822,23 @@ ss_status ss_get_system(ss_case* c, int sys, void* const* dst, int dst_is_device
   return SS_OK;
 }
 
+ss_status ss_assemble_forward(ss_case* c, int sys) {
+  STAGE_TRY(check_case(c));
+  if (!c->alloy_set) return fail(SS_ESTATE, "set_alloy first");
+  if (sys < 0 || sys >= SS_NSYS || sys == SS_SYS_P) return fail(SS_EINVAL, "system %d has no planes to assemble", sys);
+  if (sys == SS_SYS_W && c->pr.dim != 3) return fail(SS_EINVAL, "no w system in 2D");
+  const double* vel[3];
+  vel_of(c, vel);
+  cudaError_t e = launch_forward_assemble(sys, c->pr, c->sys[sys], vel, c->p, c->T, c->C, c->Cl, c->gl, c->Kinv,
+                                          c->Ag, &c->st->time, c->stream);
+  if (e != cudaSuccess) return fail(SS_ECUDA, "forward assembly of system %d: %s", sys, cudaGetErrorString(e));
+  if (sys <= SS_SYS_W) {   // the predictor's initial guess, as the term-wise assembly sets it
+    const long long nf = c->n_face[sys];
+    CUDA_TRY(cudaMemcpyAsync(c->ustar[sys], vel[sys], nf * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+  }
+  return SS_OK;
+}
+
 ss_status ss_get_system_f32(ss_case* c, int sys, void* const* dst, int dst_is_device) {
   STAGE_TRY(check_case(c));
   if (!dst) return fail(SS_EINVAL, "dst is NULL");

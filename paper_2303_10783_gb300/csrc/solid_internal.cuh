@@ -303,6 +303,11 @@ cudaError_t launch_lever(const Params& pr, double* time, double* T, double* gl, 
                          double* Cs, double* Kinv, double* Ag, cudaStream_t s);
 // from_T: recompute g_l from (T, C) in equilibrium; write_cl: recompute C_l, C_s.
 // K^{-1} and A_g are always refreshed from g_l.
+// Forward (residual-probing) assembly of system sys into its planes (validation mode).
+cudaError_t launch_forward_assemble(int sys, const Params& pr, const Sys& sy, const double* const vel[3],
+                                    const double* p, const double* T, const double* C, const double* Cl,
+                                    const double* gl, const double* Kinv, const double* Ag, const double* time,
+                                    cudaStream_t st);
 // The FP64 -> FP32 rounding of the FP32 plane copies, on n device values.
 cudaError_t launch_to_f32(const double* src, float* dst, long long n, cudaStream_t s);
 cudaError_t launch_equilibrate(const Params& pr, const double* T, const double* C, double* gl, double* Cl,

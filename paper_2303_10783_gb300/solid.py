@@ -90,6 +90,7 @@ def _declare(lib):
         "ss_solve": [P, ctypes.c_int],
         "ss_get_system": [P, ctypes.c_int, ctypes.POINTER(P), ctypes.c_int],
         "ss_get_system_f32": [P, ctypes.c_int, ctypes.POINTER(P), ctypes.c_int],
+        "ss_assemble_forward": [P, ctypes.c_int],
         "ss_convert_f64_to_f32": [P, P, ctypes.c_longlong, P],
         "ss_project": [P],
         "ss_lever": [P],
@@ -296,6 +297,10 @@ class Case:
             out[name] = a
         check(self.lib.ss_get_system(self.h, SYS_ID[sys], ptrs, 0))
         return out
+
+    def assemble_forward(self, sys):
+        """Forward (residual-probing) assembly of ``sys``, a validation mode of assemble."""
+        check(self.lib.ss_assemble_forward(self.h, SYS_ID[sys]))
 
     def get_system_f32(self, sys):
         """Dict of the FP32 planes P, W, E, S, N, B, T and inverse diagonal "idiag" (mixed cases)."""
