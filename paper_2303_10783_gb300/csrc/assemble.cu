@@ -261,10 +261,10 @@ __global__ void __launch_bounds__(kBlockA) k_assemble_cells(Params pr, Sys s, co
       // half a cell; Dirichlet through half a cell)
       const int wall[6] = {i == 0, i == nx - 1, j == 0, j == ny - 1, pr.dim == 3 && k == 0,
                            pr.dim == 3 && k == pr.nz - 1};
-      const double t_new = *time + pr.dt;
 #pragma unroll
       for (int q = 0; q < 6; ++q) {
-        if (wall[q] && pr.wall_coef[q] != 0.0) {
+        if (wall[q] && ((pr.wall_mask >> q) & 1)) {   // boundary rows only: no FP64 work elsewhere
+          const double t_new = *time + pr.dt;
           P += pr.wall_coef[q];
           b += pr.wall_coef[q] * (pr.wall_T0[q] + pr.wall_rate[q] * t_new);
         }

@@ -95,6 +95,9 @@ struct ss_case {
   cudaGraphExec_t graph;
   long long graph_kernels;   // library kernels per captured step
   int block_cap;             // > 0: blocks per cooperative solver launch at most (ss_set_block_cap)
+  int cinv_n;                // cells of an exactly solved coarsest level (0: none)
+  double cinv_host[kExactCoarse * kExactCoarse];   // its pseudo-inverse, row-major
+  float cinv_host32[kExactCoarse * kExactCoarse];  // the same in FP32 (mixed cases)
 };
 
 namespace {
@@ -191,6 +194,11 @@ void plan(ss_case* c, Planner& pl) {
       for (int q = 0; q < 4; ++q)
         c->mg.vec[l][q] = c->mg.fp32 ? (void*)pl.vec<float>(nl) : (void*)pl.vec<double>(nl);
     }
+    // a small coarsest level is solved exactly: its pseudo-inverse, formed on
+    // the host here and copied into the workspace when the case is created
+    c->cinv_n = coarse_pseudo_inverse(c->mg, c->g.dim, c->cinv_host);
+    if (c->cinv_n > 0)
+      c->mg.cinv = pl.raw<char>((size_t)c->cinv_n * c->cinv_n * (c->mg.fp32 ? sizeof(float) : sizeof(double)));
   }
   // Krylov scratch: set 0 serves every solve (multigrid included); sets 1, 2
   // serve the v* and w* teams of the joint momentum solve, with only the
@@ -263,6 +271,7 @@ void fill_params(ss_case* c, const ss_alloy* al) {
       pr.half_Dl_ih2[a] = 0.5 * pr.Dl * pr.ih2[a];
     }
   }
+  pr.wall_mask = 0;
   for (int q = 0; q < 6; ++q) {
     const int axis = q / 2;
     const ss_bc& bc = c->bc[q];
@@ -280,6 +289,7 @@ void fill_params(ss_case* c, const ss_alloy* al) {
       pr.wall_T0[q] = bc.Text;
       pr.wall_rate[q] = bc.dTdt;
     }
+    if (pr.wall_coef[q] != 0.0) pr.wall_mask |= 1 << q;
   }
 }
 
@@ -552,6 +562,17 @@ ss_status ss_create_case(const ss_grid* grid, void* workspace, size_t workspace_
   plan(c, pl);
   fill_params(c, nullptr);
   cudaError_t e = cudaMemsetAsync(c->ws, 0, need, c->stream);   // zero fields and guard bands
+  if (e == cudaSuccess && c->mg.cinv) {
+    const size_t nn = (size_t)c->cinv_n * c->cinv_n;
+    const void* src = c->cinv_host;
+    if (c->mg.fp32) {
+      for (size_t q = 0; q < nn; ++q) c->cinv_host32[q] = (float)c->cinv_host[q];
+      src = c->cinv_host32;
+    }
+    e = cudaMemcpyAsync(c->mg.cinv, src, nn * (c->mg.fp32 ? sizeof(float) : sizeof(double)), cudaMemcpyHostToDevice,
+                        c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  }
   if (e != cudaSuccess) {
     delete c->pool;
     delete c->pending;

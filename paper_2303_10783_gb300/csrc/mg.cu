@@ -18,7 +18,9 @@
 //   prolongation  trilinear in cell centres (per axis 3/4 parent, 1/4 the
 //                 neighbour on the child's side; a wall mirrors the parent)
 //   restriction   R = P^T / 2^(coarsened axes) (per axis weights 1/8 3/8 3/8 1/8)
-//   coarsest      nu_c weighted-Jacobi sweeps from zero
+//   coarsest      one product with the pseudo-inverse of its operator when it
+//                 has at most kExactCoarse cells, else nu_c weighted-Jacobi
+//                 sweeps from zero
 // Jacobi smoothing is self-adjoint in the A inner product and R is a scaled
 // P^T, so the V-cycle is a fixed symmetric positive-definite operator and
 // plain CG applies. The small levels are run by block 0 alone, resident in
@@ -26,7 +28,10 @@
 //
 // Loads are plain (L1-cached): every phase that reads data another block
 // wrote follows a grid barrier whose acquire makes those writes visible.
+#include <cmath>
 #include <cstring>
+#include <utility>
+#include <vector>
 
 #include "solid_internal.cuh"
 
@@ -85,6 +90,7 @@ struct MGArgs {
   double* partial;
   int max_blocks;
   DevStatus* st;
+  const TP* cinv;          // pseudo-inverse of the coarsest level, or nullptr (sweeps)
 };
 
 struct Range {
@@ -433,8 +439,19 @@ struct BlockSync {
 // done (pointwise) by the restriction into x; nu_c is even, so the result
 // ends in t.
 template <typename TP, typename SyncF>
-__device__ bool coarsest(const Level<TP>* lev, int l, int nu_c, const Tables<TP>& tb, Range rg, SyncF sync) {
+__device__ bool coarsest(const Level<TP>* lev, int l, int nu_c, const Tables<TP>& tb, Range rg, SyncF sync,
+                         const TP* cinv) {
   const Level<TP>& L = lev[l];
+  if (cinv) {   // exact: t = pinv(A) b, one product with the precomputed pseudo-inverse
+    if (!sync()) return false;
+    for (int c = rg.begin; c < L.n; c += rg.stride) {
+      const TP* row = cinv + (size_t)c * L.n;
+      TP acc = TP(0);
+      for (int q = 0; q < L.n; ++q) acc += row[q] * L.b[q];
+      L.t[c] = acc;
+    }
+    return true;
+  }
   TP* a = L.x;
   TP* b = L.t;
   for (int s = 1; s < nu_c; ++s) {
@@ -486,6 +503,7 @@ struct Ctx {
   DevStatus* st;
   double* partial;
   int max_blocks;
+  const void* cinv;        // pseudo-inverse of the coarsest level (TP), or nullptr
 };
 
 // One V-cycle. On entry level 0 holds b and the first sweep x = omega D^-1 b
@@ -515,7 +533,7 @@ __device__ __noinline__ bool vcycle(const Ctx& X, const Level<TP>* glev, const L
       }
       down(slev, tb, G, nl - 1, blk_rg, bs);
       __syncthreads();
-      coarsest(slev, nl - 1, X.nu_c, tb, blk_rg, bs);
+      coarsest(slev, nl - 1, X.nu_c, tb, blk_rg, bs, (const TP*)X.cinv);
       __syncthreads();
       if (nl - 2 >= G) up(slev, tb, nl - 2, G, blk_rg, bs);
       __syncthreads();
@@ -523,7 +541,7 @@ __device__ __noinline__ bool vcycle(const Ctx& X, const Level<TP>* glev, const L
     }
     if (!gs()) return false;                  // level G's result is read by every block next
   } else {
-    if (!coarsest(glev, nl - 1, X.nu_c, tb, grid_rg, gs)) return false;
+    if (!coarsest(glev, nl - 1, X.nu_c, tb, grid_rg, gs, (const TP*)X.cinv)) return false;
     if (top >= 1 && !gs()) return false;
   }
   return up(glev, tb, top - 1, 0, grid_rg, gs);
@@ -836,7 +854,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_pcg_mg(MGArgs<TP> A) {
     }
   }
   __syncthreads();
-  const Ctx X{A.nl, A.nu_c, A.G, A.st, A.partial, A.max_blocks};
+  const Ctx X{A.nl, A.nu_c, A.G, A.st, A.partial, A.max_blocks, A.cinv};
   unsigned int epoch = 0;
   const Level<TP>& L0 = glev[0];
   const int n = L0.n;
@@ -980,6 +998,7 @@ MGArgs<TP> make_args(const MGPlan& pl, const Params& pr, double* b, double* x, c
   A.partial = sc.partial;
   A.max_blocks = sc.max_blocks;
   A.st = st;
+  A.cinv = (const TP*)pl.cinv;
   return A;
 }
 
@@ -1027,6 +1046,53 @@ void plan_multigrid(const Params& pr, MGPlan& pl, int fp32) {
   // once a level is local every coarser level is too
   for (int q = 1; q < pl.nl; ++q) pl.local[q] = pl.local[q] || pl.local[q - 1];
   pl.fp32 = fp32;
+}
+
+int coarse_pseudo_inverse(const MGPlan& pl, int dim, double* out) {
+  const int L = pl.nl - 1;
+  const int nx = pl.n[L][0], ny = pl.n[L][1], nz = pl.n[L][2];
+  const int n = nx * ny * nz;
+  if (n > kExactCoarse || pl.nl < 2) return 0;
+  const double cx = 1.0 / (pl.h[L][0] * pl.h[L][0]), cy = 1.0 / (pl.h[L][1] * pl.h[L][1]);
+  const double cz = dim == 3 ? 1.0 / (pl.h[L][2] * pl.h[L][2]) : 0.0;
+  // B = A + J/n beside the identity, reduced by Gauss-Jordan with partial pivoting
+  std::vector<double> a((size_t)n * 2 * n, 0.0);
+  auto B = [&](int r, int q) -> double& { return a[(size_t)r * 2 * n + q]; };
+  for (int k = 0; k < nz; ++k)
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i) {
+        const int r = i + nx * (j + ny * k);
+        const int nbs[6][2] = {{i > 0, r - 1}, {i < nx - 1, r + 1}, {j > 0, r - nx}, {j < ny - 1, r + nx},
+                               {k > 0, r - nx * ny}, {k < nz - 1, r + nx * ny}};
+        const double coef[6] = {cx, cx, cy, cy, cz, cz};
+        for (int q = 0; q < 6; ++q)
+          if (nbs[q][0] && coef[q] != 0.0) {
+            B(r, r) += coef[q];
+            B(r, nbs[q][1]) -= coef[q];
+          }
+      }
+  for (int r = 0; r < n; ++r) {
+    for (int q = 0; q < n; ++q) B(r, q) += 1.0 / n;
+    B(r, n + r) = 1.0;
+  }
+  for (int col = 0; col < n; ++col) {
+    int piv = col;
+    for (int r = col + 1; r < n; ++r)
+      if (std::fabs(B(r, col)) > std::fabs(B(piv, col))) piv = r;
+    if (piv != col)
+      for (int q = 0; q < 2 * n; ++q) std::swap(B(piv, q), B(col, q));
+    const double d = B(col, col);
+    for (int q = 0; q < 2 * n; ++q) B(col, q) /= d;
+    for (int r = 0; r < n; ++r) {
+      if (r == col) continue;
+      const double f = B(r, col);
+      if (f != 0.0)
+        for (int q = 0; q < 2 * n; ++q) B(r, q) -= f * B(col, q);
+    }
+  }
+  for (int r = 0; r < n; ++r)
+    for (int q = 0; q < n; ++q) out[(size_t)r * n + q] = B(r, n + q) - 1.0 / n;
+  return n;
 }
 
 cudaError_t launch_pcg_mg(const MGPlan& pl, const Params& pr, double* b, double* x, const SolverCtl& ctl, Scratch& sc,

@@ -80,6 +80,7 @@ struct Params {
   // U = 1/(1/h_c + h/2k), rate 0; Dirichlet: coef = 2k/(rho cp h^2).
   double wall_coef[6], wall_T0[6], wall_rate[6];
   int slip[6];   // 1: free-slip wall (tangential ghost = interior), 0: no-slip
+  int wall_mask; // bit q set when wall q is cooled (wall_coef[q] != 0): an integer test per row
   // Launch constants formed once on the host (IEEE division rounds the same
   // there): the FP64 pipe is the bound of the assembly kernels, so no thread
   // recomputes them.
@@ -347,8 +348,17 @@ struct MGPlan {
   int local[kMaxLevels];       // run by one block
   void* vec[kMaxLevels][4];    // b, x, t, r of the level (float or double)
   int fp32;                    // V-cycle vectors in FP32
+  void* cinv;                  // coarsest level of at most kExactCoarse cells: its pseudo-inverse
+                               // (row-major, float or double), else nullptr
 };
+// Coarsest levels up to this many cells are solved exactly (one product with
+// the pseudo-inverse of their Neumann operator) instead of by sweeps.
+constexpr int kExactCoarse = 64;
 void plan_multigrid(const Params& pr, MGPlan& pl, int fp32);
+// The pseudo-inverse of the coarsest level's Neumann operator, row-major
+// (pinv(A) = (A + J/n)^-1 - J/n, J the all-ones matrix), into out[n*n];
+// returns n, or 0 when the coarsest level has more than kExactCoarse cells.
+int coarse_pseudo_inverse(const MGPlan& pl, int dim, double* out);
 cudaError_t launch_pcg_mg(const MGPlan& pl, const Params& pr, double* b, double* x, const SolverCtl& ctl,
                           Scratch& sc, DevStatus* st, cudaStream_t s);
 
