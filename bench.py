@@ -435,6 +435,7 @@ def run_ours(args):
         "roofline": roofline(head, h, ncell, args.steps),
         "stage_ms_per_step": {k: v / args.steps for k, v in h["prof"]["ms"].items() if v > 0},
         "iters_per_step": {k: v / args.steps for k, v in h["prof"]["iters"].items()},
+        "refinements_last_step": dict(h["stats"]["refinements"]),
     }
     for name in names[1:]:
         m = res[name]

@@ -95,6 +95,17 @@ struct CoreOut {
   double res, bnorm;
 };
 
+// The BiCGSTAB scalars, formed by thread 0 of each block after each
+// reduction (every block forms the same values from the same totals); the
+// vector passes read them from shared memory.
+template <typename T>
+struct BcgScalars {
+  double rho, alpha, omega, res, bnorm;
+  T beta, om, al, omn;
+  int state;   // 0: iterate on; 1: converged on the half step; 2: stop
+  int conv;
+};
+
 // Jacobi-preconditioned BiCGSTAB on A x = b in precision T (the FP64 solver;
 // the mixed path's FP32 inner solve is bcg_fused). zero_x0: start from x = 0
 // without the initial SpMV. Block and grid reductions are FP64 and
@@ -123,10 +134,22 @@ __device__ bool bcg_core(const Planes<T>& a, int n, int sy, int sz, int has_z, c
     acc.v[0] = (double)a0;
     acc.v[1] = (double)a1;
   }
-  Vec<2> tot;
-  if (!team_sum<2>(acc, tm, max_blocks, 6, st, epoch, tot)) return false;
-  out.bnorm = sqrt(tot.v[1]);
-  double res = sqrt(tot.v[0]);
+  __shared__ BcgScalars<T> ks;
+  double thr = 0.0;                               // read by thread 0 only
+  if (!team_sum_post<2>(acc, tm, max_blocks, 6, st, epoch, [&](const double* tot) {
+        ks.bnorm = sqrt(tot[1]);
+        ks.res = sqrt(tot[0]);
+        thr = tol * ks.bnorm;
+        ks.rho = tot[0];
+        ks.alpha = 1.0;
+        ks.omega = 1.0;
+        ks.beta = (T)ks.rho;                      // (rho / 1) (1 / 1); p = v = 0, so p = r
+        ks.om = T(1);
+        ks.conv = ks.res <= thr;
+        ks.state = (ks.bnorm == 0.0 || ks.conv || max_it <= 0 || !isfinite(ks.res)) ? 2 : 0;
+      }))
+    return false;
+  out.bnorm = ks.bnorm;
   out.it = 0;
   if (out.bnorm == 0.0) {
     if (!zero_x0)
@@ -135,14 +158,10 @@ __device__ bool bcg_core(const Planes<T>& a, int n, int sy, int sz, int has_z, c
     out.res = 0.0;
     return true;
   }
-  const double thr = tol * out.bnorm;
-  double rho = tot.v[0], rho_old = 1.0, alpha = 1.0, omega = 1.0;
   int it = 0;
-  bool conv = res <= thr;
-  while (!conv && it < max_it && isfinite(res)) {
+  while (ks.state == 0) {
     ++it;
-    const T beta = (T)((rho / rho_old) * (alpha / omega));
-    const T om = (T)omega;
+    const T beta = ks.beta, om = ks.om;
     for (int i = t0; i < n; i += gs) {          // p = r + beta (p - omega v); y = M^-1 p
       const T pi = r[i] + beta * (p[i] - om * v[i]);
       p[i] = pi;
@@ -155,10 +174,12 @@ __device__ bool bcg_core(const Planes<T>& a, int n, int sy, int sz, int has_z, c
       v[i] = vi;
       s1 += rh[i] * vi;
     }
-    Vec<1> o1, d1 = {{(double)s1}};
-    if (!team_sum<1>(d1, tm, max_blocks, 0, st, epoch, o1)) return false;
-    alpha = rho / o1.v[0];
-    const T al = (T)alpha;
+    if (!team_sum_post<1>(Vec<1>{{(double)s1}}, tm, max_blocks, 0, st, epoch, [&](const double* tot) {
+          ks.alpha = ks.rho / tot[0];
+          ks.al = (T)ks.alpha;
+        }))
+      return false;
+    const T al = ks.al;
     T s2 = T(0);
     for (int i = t0; i < n; i += gs) {          // s = r - alpha v (in r); z = M^-1 s
       const T si = r[i] - al * v[i];
@@ -166,12 +187,17 @@ __device__ bool bcg_core(const Planes<T>& a, int n, int sy, int sz, int has_z, c
       z[i] = __ldg(a.idiag + i) * si;
       s2 += si * si;
     }
-    Vec<1> o2, d2 = {{(double)s2}};
-    if (!team_sum<1>(d2, tm, max_blocks, 1, st, epoch, o2)) return false;
-    if (sqrt(o2.v[0]) <= thr) {                  // early exit on the half step
+    if (!team_sum_post<1>(Vec<1>{{(double)s2}}, tm, max_blocks, 1, st, epoch, [&](const double* tot) {
+          const double rs = sqrt(tot[0]);
+          if (rs <= thr) {                        // early exit on the half step
+            ks.res = rs;
+            ks.conv = 1;
+            ks.state = 1;
+          }
+        }))
+      return false;
+    if (ks.state == 1) {
       for (int i = t0; i < n; i += gs) x[i] += al * y[i];
-      res = sqrt(o2.v[0]);
-      conv = true;
       break;
     }
     T s3 = T(0), s4 = T(0);
@@ -181,10 +207,12 @@ __device__ bool bcg_core(const Planes<T>& a, int n, int sy, int sz, int has_z, c
       s3 += ti * r[i];
       s4 += ti * ti;
     }
-    Vec<2> o3, d3 = {{(double)s3, (double)s4}};
-    if (!team_sum<2>(d3, tm, max_blocks, 2, st, epoch, o3)) return false;
-    omega = (o3.v[1] > 0.0) ? o3.v[0] / o3.v[1] : 0.0;
-    const T omn = (T)omega;
+    if (!team_sum_post<2>(Vec<2>{{(double)s3, (double)s4}}, tm, max_blocks, 2, st, epoch, [&](const double* tot) {
+          ks.omega = (tot[1] > 0.0) ? tot[0] / tot[1] : 0.0;
+          ks.omn = (T)ks.omega;
+        }))
+      return false;
+    const T omn = ks.omn;
     T s5 = T(0), s6 = T(0);
     for (int i = t0; i < n; i += gs) {          // x += alpha y + omega z; r = s - omega t
       x[i] += al * y[i] + omn * z[i];
@@ -193,23 +221,28 @@ __device__ bool bcg_core(const Planes<T>& a, int n, int sy, int sz, int has_z, c
       s5 += rh[i] * ri;
       s6 += ri * ri;
     }
-    Vec<2> o4, d4 = {{(double)s5, (double)s6}};
-    if (!team_sum<2>(d4, tm, max_blocks, 4, st, epoch, o4)) return false;
-    res = sqrt(o4.v[1]);
-    conv = res <= thr;
-    rho_old = rho;
-    rho = o4.v[0];
-    if (rho == 0.0 || omega == 0.0) break;   // breakdown: report the current iterate
+    if (!team_sum_post<2>(Vec<2>{{(double)s5, (double)s6}}, tm, max_blocks, 4, st, epoch, [&](const double* tot) {
+          ks.res = sqrt(tot[1]);
+          ks.conv = ks.res <= thr;
+          const double rho_old = ks.rho;
+          ks.rho = tot[0];
+          ks.beta = (T)((ks.rho / rho_old) * (ks.alpha / ks.omega));
+          ks.om = (T)ks.omega;
+          // stop on convergence, the iteration cap, a non-finite residual or
+          // a breakdown (rho = 0 or omega = 0: the current iterate is reported)
+          ks.state = (ks.conv || it >= max_it || !isfinite(ks.res) || ks.rho == 0.0 || ks.omega == 0.0) ? 2 : 0;
+        }))
+      return false;
   }
   out.it = it;
-  out.conv = conv;
-  out.res = res;
+  out.conv = ks.conv != 0;
+  out.res = ks.res;
   return true;
 }
 
 // ---- FP32 inner solve with three grid-wide synchronisations per iteration.
 //
-// The same Jacobi-preconditioned BiCGSTAB as bcg_core<float>, with the
+// The same Jacobi-preconditioned BiCGSTAB as bcg_core, in FP32, with the
 // preconditioned vectors never stored: y = D^-1 (r + beta (p - omega v)) and
 // z = D^-1 (r - alpha v) are formed wherever the SpMV needs them (the row and
 // its six neighbours), from vectors that are complete after the previous
@@ -300,38 +333,35 @@ __device__ bool bcg_fused(const Planes<float>& a, int n, int sy, int sz, int has
   float *R = V.r0, *S = V.r1, *Po = V.p0, *Pn = V.p1, *Vo = V.v0, *Vn = V.v1;
   const float* rh = V.rh;
   const float* dg = a.idiag;
-  Vec<2> acc = {{0.0, 0.0}};
-  {
-    float a0 = 0.f;
-    for (int i = t0; i < n; i += gs) {            // x = 0, rhat = r, p = v = 0
-      const float ri = R[i];
-      x[i] = 0.f;
-      V.rh[i] = ri;
-      Po[i] = 0.f;
-      Vo[i] = 0.f;
-      a0 += ri * ri;
-    }
-    acc.v[0] = (double)a0;
-    acc.v[1] = (double)a0;
+  __shared__ BcgScalars<float> ks;
+  float a0 = 0.f;
+  for (int i = t0; i < n; i += gs) {              // x = 0, rhat = r, p = v = 0
+    const float ri = R[i];
+    x[i] = 0.f;
+    V.rh[i] = ri;
+    Po[i] = 0.f;
+    Vo[i] = 0.f;
+    a0 += ri * ri;
   }
-  Vec<2> tot;
-  if (!team_sum<2>(acc, tm, max_blocks, 6, st, epoch, tot)) return false;
-  out.bnorm = sqrt(tot.v[1]);
-  double res = sqrt(tot.v[0]);
-  out.it = 0;
-  if (out.bnorm == 0.0) {
-    out.conv = true;
-    out.res = 0.0;
-    return true;
-  }
-  const double thr = tol * out.bnorm;
-  double rho = tot.v[0], rho_old = 1.0, alpha = 1.0, omega = 1.0;
+  double thr = 0.0;                               // read by thread 0 only
   int it = 0;
-  bool conv = res <= thr;
-  while (!conv && it < max_it && isfinite(res)) {
+  if (!team_sum_post<1>(VecF<1>{{a0}}, tm, max_blocks, 6, st, epoch, [&](const double* tot) {
+        ks.bnorm = sqrt(tot[0]);
+        ks.res = ks.bnorm;
+        thr = tol * ks.bnorm;
+        ks.rho = tot[0];
+        ks.alpha = 1.0;
+        ks.omega = 1.0;
+        ks.beta = (float)ks.rho;                    // (rho / 1) (1 / 1); p = v = 0, so p' = r
+        ks.om = 1.f;
+        ks.conv = ks.bnorm == 0.0 || ks.res <= thr;
+        ks.state = (ks.conv || max_it <= 0 || !isfinite(ks.res)) ? 2 : 0;
+      }))
+    return false;
+  out.bnorm = ks.bnorm;
+  while (ks.state == 0) {
     ++it;
-    const float beta = (float)((rho / rho_old) * (alpha / omega));
-    const float om = (float)omega;
+    const float beta = ks.beta, om = ks.om;
     // pass 1: p' = r + beta (p - om v) (stored), v' = A D^-1 p', (rhat, v')
     const YDir yd{R, Po, Vo, dg, beta, om};
     float s1 = 0.f;
@@ -353,10 +383,12 @@ __device__ bool bcg_fused(const Planes<float>& a, int n, int sy, int sz, int has
       Vn[i] = vn;
       s1 += rh[i] * vn;
     }
-    Vec<1> o1, d1 = {{(double)s1}};
-    if (!team_sum<1>(d1, tm, max_blocks, 0, st, epoch, o1)) return false;
-    alpha = rho / o1.v[0];
-    const float al = (float)alpha;
+    if (!team_sum_post<1>(VecF<1>{{s1}}, tm, max_blocks, 0, st, epoch, [&](const double* tot) {
+          ks.alpha = ks.rho / tot[0];
+          ks.al = (float)ks.alpha;
+        }))
+      return false;
+    const float al = ks.al;
     // pass 2: s = r - al v' (stored beside r), t = A D^-1 s, (t,s), (t,t), (s,s)
     const ZDir zd{R, Vn, dg, al};
     float s3 = 0.f, s4 = 0.f, s2 = 0.f;
@@ -380,16 +412,23 @@ __device__ bool bcg_fused(const Planes<float>& a, int n, int sy, int sz, int has
       s4 += ti * ti;
       s2 += si * si;
     }
-    Vec<3> o3, d3 = {{(double)s3, (double)s4, (double)s2}};
-    if (!team_sum<3>(d3, tm, max_blocks, 2, st, epoch, o3)) return false;
-    if (sqrt(o3.v[2]) <= thr) {                  // converged on the half step: x += al D^-1 p'
+    if (!team_sum_post<3>(VecF<3>{{s3, s4, s2}}, tm, max_blocks, 2, st, epoch, [&](const double* tot) {
+          const double rs = sqrt(tot[2]);
+          if (rs <= thr) {                        // converged on the half step
+            ks.res = rs;
+            ks.conv = 1;
+            ks.state = 1;
+          } else {
+            ks.omega = (tot[1] > 0.0) ? tot[0] / tot[1] : 0.0;
+            ks.omn = (float)ks.omega;
+          }
+        }))
+      return false;
+    if (ks.state == 1) {                           // x += al D^-1 p'
       for (int i = t0; i < n; i += gs) x[i] += al * (__ldg(dg + i) * Pn[i]);
-      res = sqrt(o3.v[2]);
-      conv = true;
       break;
     }
-    omega = (o3.v[1] > 0.0) ? o3.v[0] / o3.v[1] : 0.0;
-    const float omn = (float)omega;
+    const float omn = ks.omn;
     // pass 3: x += al D^-1 p' + omn D^-1 s; r = s - omn t (over s); (rhat, r), (r, r)
     float s5 = 0.f, s6 = 0.f;
     for (int m = t0; m < n4; m += gs) {
@@ -411,20 +450,25 @@ __device__ bool bcg_fused(const Planes<float>& a, int n, int sy, int sz, int has
       s5 += rh[i] * ri;
       s6 += ri * ri;
     }
-    Vec<2> o4, d4 = {{(double)s5, (double)s6}};
-    if (!team_sum<2>(d4, tm, max_blocks, 4, st, epoch, o4)) return false;
-    res = sqrt(o4.v[1]);
-    conv = res <= thr;
-    rho_old = rho;
-    rho = o4.v[0];
+    if (!team_sum_post<2>(VecF<2>{{s5, s6}}, tm, max_blocks, 4, st, epoch, [&](const double* tot) {
+          ks.res = sqrt(tot[1]);
+          ks.conv = ks.res <= thr;
+          const double rho_old = ks.rho;
+          ks.rho = tot[0];
+          ks.beta = (float)((ks.rho / rho_old) * (ks.alpha / ks.omega));
+          ks.om = (float)ks.omega;
+          // stop on convergence, the iteration cap, a non-finite residual or
+          // a breakdown (rho = 0 or omega = 0: the current iterate is reported)
+          ks.state = (ks.conv || it >= max_it || !isfinite(ks.res) || ks.rho == 0.0 || ks.omega == 0.0) ? 2 : 0;
+        }))
+      return false;
     float* tmp = R; R = S; S = tmp;               // the new r lives in S
     tmp = Po; Po = Pn; Pn = tmp;
     tmp = Vo; Vo = Vn; Vn = tmp;
-    if (rho == 0.0 || omega == 0.0) break;       // breakdown: report the current iterate
   }
   out.it = it;
-  out.conv = conv;
-  out.res = res;
+  out.conv = ks.conv != 0;
+  out.res = ks.res;
   return true;
 }
 
@@ -465,16 +509,27 @@ __device__ __forceinline__ void ir_solve(const BcgArgs& A, const Team& tm) {
     acc.v[0] += ri * ri;
     acc.v[1] += b[i] * b[i];
   }
-  Vec<2> tot;
-  if (!team_sum<2>(acc, tm, A.max_blocks, 13, A.st, epoch, tot)) return;
-  const double bnorm = sqrt(tot.v[1]);
-  double rn = sqrt(tot.v[0]);
-  const double thr = A.tol * bnorm;
+  // scalars formed by thread 0 of each block after each reduction
+  __shared__ struct {
+    double bnorm, rn, inv, rel;
+    int conv, go;
+  } is;
+  double thr = 0.0;                               // read by thread 0 only
+  if (!team_sum_post<2>(acc, tm, A.max_blocks, 13, A.st, epoch, [&](const double* tot) {
+        is.bnorm = sqrt(tot[1]);
+        is.rn = sqrt(tot[0]);
+        thr = A.tol * is.bnorm;
+        is.inv = 1.0 / is.rn;
+        is.conv = is.bnorm == 0.0 || is.rn <= thr;
+        is.go = is.bnorm > 0.0 && is.rn > thr && isfinite(is.rn);
+        is.rel = is.bnorm > 0.0 ? is.rn / is.bnorm : 0.0;
+      }))
+    return;
   int total = 0, ref = 0;
-  while (bnorm > 0.0 && rn > thr && ref < kMaxRefine && total < A.max_it && isfinite(rn)) {
+  while (is.go && ref < kMaxRefine && total < A.max_it) {
     ++ref;
     // the inner solve sees the residual scaled to unit norm (no FP32 under- or overflow)
-    const double inv = 1.0 / rn;
+    const double rn = is.rn, inv = is.inv;
     // (bcg_fused first reads r0 on the rows this thread wrote; the reduction
     // that follows orders it before any neighbour read)
     for (int i = t0; i < n; i += gs) A.f32.r0[i] = (float)(r64[i] * inv);
@@ -492,12 +547,17 @@ __device__ __forceinline__ void ir_solve(const BcgArgs& A, const Team& tm) {
       r64[i] = ri;
       s1.v[0] += ri * ri;
     }
-    Vec<1> o1;
-    if (!team_sum<1>(s1, tm, A.max_blocks, 15, A.st, epoch, o1)) return;
-    rn = sqrt(o1.v[0]);
-    if (o.it == 0 && !(rn <= thr)) break;      // the inner solve made no progress
+    if (!team_sum_post<1>(s1, tm, A.max_blocks, 15, A.st, epoch, [&](const double* tot) {
+          is.rn = sqrt(tot[0]);
+          is.inv = 1.0 / is.rn;
+          is.conv = is.rn <= thr;
+          is.go = is.rn > thr && isfinite(is.rn);
+          is.rel = is.rn / is.bnorm;
+        }))
+      return;
+    if (o.it == 0 && !is.conv) break;          // the inner solve made no progress
   }
-  record(A.st, tm.rank == 0, A.stat_index, total, ref, bnorm == 0.0 || rn <= thr, bnorm > 0.0 ? rn / bnorm : 0.0);
+  record(A.st, tm.rank == 0, A.stat_index, total, ref, is.conv != 0, is.rel);
 }
 
 // Up to kMaxTeams independent systems in one cooperative launch: team s is

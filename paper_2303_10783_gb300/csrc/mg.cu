@@ -645,6 +645,22 @@ struct PcgOut {
   double res, bnorm;
 };
 
+// The CG scalars, formed by thread 0 of each block after each reduction
+// (every block forms the same values from the same totals).
+template <typename TV>
+struct PcgScalars {
+  double rz, res, bnorm, inv_n;
+  TV alpha, beta, mz;
+  int state;   // 0: iterate on; 2: stop
+  int conv;
+};
+
+// Reduction input: FP32 partial sums reduce in FP32 within a block.
+template <typename TV, int K>
+struct RedIn { using type = Vec<K>; };
+template <int K>
+struct RedIn<float, K> { using type = VecF<K>; };
+
 // CG with the V-cycle preconditioner on A x = bscale * (b - bshift) (b is FP64), vectors
 // of type TV (double: FP64 path; float: inner solve of the mixed path), x
 // from 0. The fine-grid operator uses coefficients (cx, cy, cz) and the
@@ -680,16 +696,24 @@ __device__ __noinline__ bool pcg(const Ctx& X, const Level<TP>* glev, const Leve
   if (!vcycle(X, glev, slev, tb, epoch)) return false;
   TV a0 = TV(0), a1 = TV(0), a2 = TV(0), a3 = TV(0);
   zr_sums(L0, r, t0, gsz, a0, a1, a2, a3);
-  Vec<4> o0, s0 = {{(double)a0, (double)a1, (double)a2, (double)a3}};
-  if (!grid_sum<4>(s0, X.partial, X.max_blocks, 0, X.st, epoch, o0)) return false;
-  const double inv_n = 1.0 / (double)n;
-  double mz = o0.v[2] * inv_n;
-  out.bnorm = sqrt(o0.v[1]);
-  double rz = o0.v[0] - mz * o0.v[3], res = out.bnorm;
-  const double thr = tol * out.bnorm;
+  __shared__ PcgScalars<TV> ps;
+  double thr = 0.0;                               // read by thread 0 only
   int it = 0;
-  bool conv = (out.bnorm == 0.0);
-  TV beta = TV(0);
+  if (!grid_sum_post<4>(typename RedIn<TV, 4>::type{{a0, a1, a2, a3}}, X.partial, X.max_blocks, 0, X.st, epoch,
+                        [&](const double* tot) {
+                          ps.inv_n = 1.0 / (double)n;
+                          const double mz = tot[2] * ps.inv_n;
+                          ps.bnorm = sqrt(tot[1]);
+                          ps.rz = tot[0] - mz * tot[3];
+                          ps.res = ps.bnorm;
+                          thr = tol * ps.bnorm;
+                          ps.mz = (TV)mz;
+                          ps.beta = TV(0);
+                          ps.conv = ps.bnorm == 0.0;
+                          ps.state = (ps.conv || max_it <= 0 || !isfinite(ps.res)) ? 2 : 0;
+                        }))
+    return false;
+  out.bnorm = ps.bnorm;
   TV* p_old = p_a;
   TV* p = p_b;
   const bool v4 = (sizeof(TV) == 4) && L0.v4;
@@ -698,11 +722,12 @@ __device__ __noinline__ bool pcg(const Ctx& X, const Level<TP>* glev, const Leve
   // path keeps p' in a pass of its own (and one more barrier).
   constexpr bool kFused = sizeof(TV) == 4;
   if constexpr (!kFused) {
-    for (int c = t0; c < n; c += gsz) p[c] = (TV)L0.t[c] - (TV)mz;
+    const TV mz = ps.mz;
+    for (int c = t0; c < n; c += gsz) p[c] = (TV)L0.t[c] - mz;
     if (!grid_barrier(X.st, gridDim.x, epoch)) return false;
   }
-  while (!conv && it < max_it && isfinite(res)) {
-    const Dir<TV> dir{(const TV*)L0.t, p_old, (TV)mz, beta, it == 0};
+  while (ps.state == 0) {
+    const Dir<TV> dir{(const TV*)L0.t, p_old, ps.mz, ps.beta, it == 0};
     ++it;
     TV s1 = TV(0);
     if constexpr (sizeof(TV) == 4) {
@@ -743,9 +768,10 @@ __device__ __noinline__ bool pcg(const Ctx& X, const Level<TP>* glev, const Leve
         }
       }
     }
-    Vec<1> o1, d1 = {{(double)s1}};
-    if (!grid_sum<1>(d1, X.partial, X.max_blocks, 4, X.st, epoch, o1)) return false;
-    const TV alpha = (TV)(rz / o1.v[0]);
+    if (!grid_sum_post<1>(typename RedIn<TV, 1>::type{{s1}}, X.partial, X.max_blocks, 4, X.st, epoch,
+                          [&](const double* tot) { ps.alpha = (TV)(ps.rz / tot[0]); }))
+      return false;
+    const TV alpha = ps.alpha;
     if constexpr (sizeof(TV) == 4) {
       if (v4) {
         for (int m = t0; m < (n >> 2); m += gsz) {    // x += alpha p; r -= alpha q; first V-cycle sweep
@@ -795,28 +821,36 @@ __device__ __noinline__ bool pcg(const Ctx& X, const Level<TP>* glev, const Leve
     if (!vcycle(X, glev, slev, tb, epoch)) return false;
     TV s2 = TV(0), s3 = TV(0), s4 = TV(0), s5 = TV(0);
     zr_sums(L0, r, t0, gsz, s2, s3, s4, s5);
-    Vec<4> o2, d2 = {{(double)s2, (double)s3, (double)s4, (double)s5}};
-    if (!grid_sum<4>(d2, X.partial, X.max_blocks, 8, X.st, epoch, o2)) return false;
-    res = sqrt(o2.v[1]);
-    conv = res <= thr;
-    if (conv) break;
-    mz = o2.v[2] * inv_n;
-    const double rz_new = o2.v[0] - mz * o2.v[3];
-    beta = (TV)(rz_new / rz);
-    rz = rz_new;
+    if (!grid_sum_post<4>(typename RedIn<TV, 4>::type{{s2, s3, s4, s5}}, X.partial, X.max_blocks, 8, X.st, epoch,
+                          [&](const double* tot) {
+                            ps.res = sqrt(tot[1]);
+                            ps.conv = ps.res <= thr;
+                            if (ps.conv) {
+                              ps.state = 2;
+                              return;
+                            }
+                            const double mz = tot[2] * ps.inv_n;
+                            const double rz_new = tot[0] - mz * tot[3];
+                            ps.beta = (TV)(rz_new / ps.rz);
+                            ps.rz = rz_new;
+                            ps.mz = (TV)mz;
+                            ps.state = (it >= max_it || !isfinite(ps.res)) ? 2 : 0;
+                          }))
+      return false;
+    if (ps.state != 0) break;
     if constexpr (kFused) {
       TV* tmp = p_old;  // this iteration's p' is the next iteration's old p
       p_old = p;
       p = tmp;
     } else {
-      const TV mzt = (TV)mz;
+      const TV mzt = ps.mz, beta = ps.beta;
       for (int c = t0; c < n; c += gsz) p[c] = ((TV)L0.t[c] - mzt) + beta * p[c];
       if (!grid_barrier(X.st, gridDim.x, epoch)) return false;
     }
   }
   out.it = it;
-  out.conv = conv;
-  out.res = res;
+  out.conv = ps.conv != 0;
+  out.res = ps.res;
   return true;
 }
 
@@ -863,17 +897,24 @@ __global__ void __launch_bounds__(kBlock, 1) k_pcg_mg(MGArgs<TP> A) {
   double* x = A.x;
   double* r = A.r;
 
+  // Scalars of this driver, formed by thread 0 of each block after each
+  // reduction (divisions and square roots once per block, not per thread).
+  __shared__ struct {
+    double mean, bn, rn, rmean, inv;
+    int conv;
+  } ds;
   // consistency: remove the mean of the right-hand side (Neumann null space)
   Vec<1> sb = {{0.0}};
   for (int c = t0; c < n; c += gsz) sb.v[0] += b[c];
-  Vec<1> ob;
-  if (!grid_sum<1>(sb, X.partial, X.max_blocks, 12, X.st, epoch, ob)) return;
-  const double mean_b = ob.v[0] / (double)n;
+  if (!grid_sum_post<1>(sb, X.partial, X.max_blocks, 12, X.st, epoch,
+                        [&](const double* tot) { ds.mean = tot[0] / (double)n; }))
+    return;
+  const double mean_b = ds.mean;
   for (int c = t0; c < n; c += gsz) b[c] -= mean_b;
 
   int iters = 0, refs = 0;
   bool conv = false;
-  double rel = 0.0;
+  double res = 0.0, bnorm = 0.0;   // relative residual res / bnorm
   // TP = double: the FP64 path; TP = float: the mixed path (refinement)
   if constexpr (sizeof(TP) == 8) {
     PcgOut o;
@@ -882,7 +923,8 @@ __global__ void __launch_bounds__(kBlock, 1) k_pcg_mg(MGArgs<TP> A) {
       return;
     iters = o.it;
     conv = o.conv;
-    rel = o.bnorm > 0.0 ? o.res / o.bnorm : 0.0;
+    res = o.res;
+    bnorm = o.bnorm;
   } else {
     Vec<1> s = {{0.0}};
     for (int c = t0; c < n; c += gsz) {
@@ -891,15 +933,20 @@ __global__ void __launch_bounds__(kBlock, 1) k_pcg_mg(MGArgs<TP> A) {
       r[c] = bc;
       s.v[0] += bc * bc;
     }
-    Vec<1> o;
-    if (!grid_sum<1>(s, X.partial, X.max_blocks, 13, X.st, epoch, o)) return;
-    const double bn = sqrt(o.v[0]);
-    double rn = bn;
-    double rmean = 0.0;   // b is mean-free
-    const double thr = A.tol * bn;
+    double thr = 0.0;                             // read by thread 0 only
+    if (!grid_sum_post<1>(s, X.partial, X.max_blocks, 13, X.st, epoch, [&](const double* tot) {
+          ds.bn = sqrt(tot[0]);
+          ds.rn = ds.bn;
+          ds.inv = 1.0 / ds.rn;
+          ds.rmean = 0.0;                         // b is mean-free
+          thr = A.tol * ds.bn;
+          ds.conv = ds.bn == 0.0;
+        }))
+      return;
     const double cx = A.cx, cy = A.cy, cz = A.cz;
-    conv = (bn == 0.0);
-    while (!conv && refs < kMaxRefineP && iters < A.max_it && isfinite(rn)) {
+    conv = ds.conv != 0;
+    while (!conv && refs < kMaxRefineP && iters < A.max_it && isfinite(ds.rn)) {
+      const double rn = ds.rn;
       ++refs;
       // The inner solve sees the residual without its mean and scaled to unit
       // norm (no FP32 under- or overflow). The mean is the part of the FP64
@@ -908,7 +955,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_pcg_mg(MGArgs<TP> A) {
       // side it would stall the inner iteration once the rest falls below it.
       PcgOut io;
       const int cap = (A.max_it - iters < kMaxInnerP) ? A.max_it - iters : kMaxInnerP;
-      if (!pcg<TP, TP>(X, glev, slev, tb, r, rmean, 1.0 / rn, A.di, A.ri, A.pi, A.pi2, A.qi, L0.ax, L0.ay, L0.az,
+      if (!pcg<TP, TP>(X, glev, slev, tb, r, ds.rmean, ds.inv, A.di, A.ri, A.pi, A.pi2, A.qi, L0.ax, L0.ay, L0.az,
                        tb.diag[0], A.inner_tol, cap, epoch, io))
         return;
       iters += io.it;
@@ -923,24 +970,30 @@ __global__ void __launch_bounds__(kBlock, 1) k_pcg_mg(MGArgs<TP> A) {
         s2.v[0] += rc * rc;
         s2.v[1] += rc;
       }
-      Vec<2> o2;
-      if (!grid_sum<2>(s2, X.partial, X.max_blocks, 14, X.st, epoch, o2)) return;
-      // norm of the residual's range part: sum (r - mean)^2 = sum r^2 - n mean^2
-      rmean = o2.v[1] / (double)n;
-      rn = sqrt(fmax(o2.v[0] - (double)n * rmean * rmean, 0.0));
-      conv = rn <= thr;
+      if (!grid_sum_post<2>(s2, X.partial, X.max_blocks, 14, X.st, epoch, [&](const double* tot) {
+            // norm of the residual's range part: sum (r - mean)^2 = sum r^2 - n mean^2
+            ds.rmean = tot[1] / (double)n;
+            ds.rn = sqrt(fmax(tot[0] - (double)n * ds.rmean * ds.rmean, 0.0));
+            ds.inv = 1.0 / ds.rn;
+            ds.conv = ds.rn <= thr;
+          }))
+        return;
+      conv = ds.conv != 0;
       if (io.it == 0) break;                     // the inner solve made no progress
     }
-    rel = bn > 0.0 ? rn / bn : 0.0;
+    res = ds.rn;
+    bnorm = ds.bn;
   }
   // gauge: zero-mean correction
   Vec<1> sx = {{0.0}};
   for (int c = t0; c < n; c += gsz) sx.v[0] += x[c];
-  Vec<1> ox;
-  if (!grid_sum<1>(sx, X.partial, X.max_blocks, 15, X.st, epoch, ox)) return;
-  const double mean_x = ox.v[0] / (double)n;
+  if (!grid_sum_post<1>(sx, X.partial, X.max_blocks, 15, X.st, epoch,
+                        [&](const double* tot) { ds.mean = tot[0] / (double)n; }))
+    return;
+  const double mean_x = ds.mean;
   for (int c = t0; c < n; c += gsz) x[c] -= mean_x;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
+    const double rel = bnorm > 0.0 ? res / bnorm : 0.0;
     SolveStat& st = A.st->stat[A.stat_index];
     st.iters = iters;
     st.iters_total += iters;

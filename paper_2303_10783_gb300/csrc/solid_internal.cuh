@@ -202,22 +202,44 @@ __device__ __forceinline__ Vec<K> block_sum0(Vec<K> x) {
   return r;
 }
 
-// Deterministic reduction of K doubles over a team: every block writes its
-// partial sums to slots [slot, slot+K), passes the team barrier, then warp q
-// of every block sums slot q's partials in block order (the same order
-// everywhere, so all blocks get bit-identical totals). Returns false if the
-// barrier gave up.
 template <int K>
-__device__ __forceinline__ bool team_sum(Vec<K> x, const Team& t, int max_blocks, int slot, DevStatus* st,
-                                         unsigned int& epoch, Vec<K>& out) {
-  static_assert(K <= kBlock / 32, "one warp per reduced value");
-  Vec<K> b = block_sum0<K>(x);
-  if (threadIdx.x == 0) {
+struct VecF { float v[K]; };
+
+// Block-wide sum of K floats, returned as doubles in thread 0. The warp sums
+// and the sum of the 16 warp sums are formed in FP32: the inputs are FP32
+// partial sums of FP32 vectors, and an FP64 shuffle tree would cost each
+// warp 16 clocks of the SM's two-lane FP64 pipe per step.
+template <int K>
+__device__ __forceinline__ Vec<K> block_sum0(VecF<K> x) {
+  static_assert(kBlock / 32 <= 32 && (kBlock & (kBlock - 1)) == 0, "one warp holds the warp sums");
+  __shared__ float shf[K][kBlock / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
-    for (int q = 0; q < K; ++q) t.partial[(size_t)(slot + q) * max_blocks + t.rank] = b.v[q];
+  for (int q = 0; q < K; ++q) {
+    float s = x.v[q];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) shf[q][wid] = s;
   }
-  if (!team_barrier(st, t, epoch)) return false;
-  __shared__ double tot[K];
+  __syncthreads();
+  Vec<K> r;
+  if (wid == 0) {
+#pragma unroll
+    for (int q = 0; q < K; ++q) {
+      float s = lane < kBlock / 32 ? shf[q][lane] : 0.f;
+#pragma unroll
+      for (int o = kBlock / 64; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+      r.v[q] = (double)s;
+    }
+  }
+  return r;
+}
+
+// Second half of a team reduction: after the barrier, warp q of every block
+// sums slot q's partials in block order (the same order everywhere, so all
+// blocks get bit-identical totals) into tot[q]; valid after a __syncthreads.
+template <int K>
+__device__ __forceinline__ void team_total(const Team& t, int max_blocks, int slot, double* tot) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   if (wid < K) {
     const double* pp = t.partial + (size_t)(slot + wid) * max_blocks;
@@ -236,9 +258,50 @@ __device__ __forceinline__ bool team_sum(Vec<K> x, const Team& t, int max_blocks
     for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
     if (lane == 0) tot[wid] = s;
   }
+}
+
+// Deterministic reduction of K values over a team: every block writes its
+// partial sums to slots [slot, slot+K), passes the team barrier, and forms
+// the totals with team_total. Returns false if the barrier gave up.
+template <int K>
+__device__ __forceinline__ bool team_sum(Vec<K> x, const Team& t, int max_blocks, int slot, DevStatus* st,
+                                         unsigned int& epoch, Vec<K>& out) {
+  static_assert(K <= kBlock / 32, "one warp per reduced value");
+  Vec<K> b = block_sum0<K>(x);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int q = 0; q < K; ++q) t.partial[(size_t)(slot + q) * max_blocks + t.rank] = b.v[q];
+  }
+  if (!team_barrier(st, t, epoch)) return false;
+  __shared__ double tot[K];
+  team_total<K>(t, max_blocks, slot, tot);
   __syncthreads();
 #pragma unroll
   for (int q = 0; q < K; ++q) out.v[q] = tot[q];
+  __syncthreads();
+  return true;
+}
+
+// The same reduction (x a Vec<K> of doubles or a VecF<K> of floats), with
+// the totals handed to post(const double* tot), run by thread 0 of each
+// block: the Krylov scalars (divisions, square roots, stopping tests) are
+// formed once per block instead of once per thread, which on this GPU's
+// narrow FP64 pipe costs microseconds per iteration. What post writes to
+// shared memory is visible to every thread of the block on return.
+template <int K, class In, class Post>
+__device__ __forceinline__ bool team_sum_post(const In& x, const Team& t, int max_blocks, int slot, DevStatus* st,
+                                              unsigned int& epoch, Post&& post) {
+  static_assert(K <= kBlock / 32, "one warp per reduced value");
+  const Vec<K> b = block_sum0(x);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int q = 0; q < K; ++q) t.partial[(size_t)(slot + q) * max_blocks + t.rank] = b.v[q];
+  }
+  if (!team_barrier(st, t, epoch)) return false;
+  __shared__ double tot[K];
+  team_total<K>(t, max_blocks, slot, tot);
+  __syncthreads();
+  if (threadIdx.x == 0) post(static_cast<const double*>(tot));
   __syncthreads();
   return true;
 }
@@ -249,6 +312,13 @@ __device__ __forceinline__ bool grid_sum(Vec<K> x, double* partial, int max_bloc
                                          unsigned int& epoch, Vec<K>& out) {
   const Team t{(int)blockIdx.x, (int)gridDim.x, &st->barrier, partial};
   return team_sum<K>(x, t, max_blocks, slot, st, epoch, out);
+}
+
+template <int K, class In, class Post>
+__device__ __forceinline__ bool grid_sum_post(const In& x, double* partial, int max_blocks, int slot, DevStatus* st,
+                                              unsigned int& epoch, Post&& post) {
+  const Team t{(int)blockIdx.x, (int)gridDim.x, &st->barrier, partial};
+  return team_sum_post<K>(x, t, max_blocks, slot, st, epoch, post);
 }
 
 // Division by a runtime constant d >= 1 for 0 <= n < 2^31 with a multiply-high
