@@ -334,11 +334,18 @@ struct Phase {
 __device__ __forceinline__ Phase phase_of(const Params& pr, double C, double g) {
   Phase o;
   const double s = 1.0 - g;
-  // g + kp (1 - g) = 1 - (1 - kp)(1 - g): the denominator of Eq. 3.18 is 1/A_g (Eq. 3.8)
-  o.Ag = 1.0 / (1.0 - pr.lev_a * s);                 // Eq. 3.8, for the next solute step
-  o.Cl = C * o.Ag;                                   // Eq. 3.18
+  if (s == 0.0) {
+    // fully liquid: the two divisions below give exactly A_g = 1 and K^-1 = 0
+    o.Ag = 1.0;
+    o.Cl = C;
+    o.Kinv = 0.0;
+  } else {
+    // g + kp (1 - g) = 1 - (1 - kp)(1 - g): the denominator of Eq. 3.18 is 1/A_g (Eq. 3.8)
+    o.Ag = 1.0 / (1.0 - pr.lev_a * s);               // Eq. 3.8, for the next solute step
+    o.Cl = C * o.Ag;                                 // Eq. 3.18
+    o.Kinv = s * s / (pr.K0 * (g * g * g + pr.eps));  // Eq. 2.8, regularised
+  }
   if (pr.has_eutectic) o.Cl = fmin(o.Cl, pr.Ce);
-  o.Kinv = s * s / (pr.K0 * (g * g * g + pr.eps));  // Eq. 2.8, regularised
   return o;
 }
 

@@ -814,6 +814,13 @@ cudaError_t launch_bicgstab_multi(const Sys* const* sys, int nsys, int has_z, co
       --want[big];
       --total;
     }
+    while (total < lim) {                      // and hand what rounding left to the team with most rows per block
+      int most = 0;
+      for (int q = 1; q < nsys; ++q)
+        if ((double)sys[q]->d.n / (double)want[q] > (double)sys[most]->d.n / (double)want[most]) most = q;
+      ++want[most];
+      ++total;
+    }
   }
   M.first[0] = 0;
   for (int q = 0; q < nsys; ++q) M.first[q + 1] = M.first[q] + (int)want[q];
