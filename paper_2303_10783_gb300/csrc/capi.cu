@@ -442,8 +442,8 @@ ss_status stage_lever(ss_case* c) {
 
 // The u*, v*, w* systems of Eq. 3.3 are independent (each uses u^n only):
 // one cooperative launch solves all of them, one team of blocks per
-// component. Its time and its launch are counted under solve_u. Used for
-// cases up to kJointMomentumMaxCells.
+// component. Its time and its launch are counted under solve_u. Used where
+// joint_momentum() says so.
 ss_status stage_solve_momentum(ss_case* c) {
   StageTimer tm(c, SS_PROF_SOLVE + SS_SYS_U, 1);
   const int ncomp = c->pr.dim;
@@ -465,16 +465,24 @@ ss_status stage_solve_momentum(ss_case* c) {
   return SS_OK;
 }
 
-// Largest case (cells) whose momentum systems are solved in one joint launch.
-// Measured: at 1.2 M cells the joint launch is 7% faster than three
-// sequential solves (each solve alone is latency-bound); at 25 M cells it is
-// 15% slower (each team streams its own vectors from HBM on a third of the
-// SMs, and the team with the most iterations sets the time).
-constexpr long long kJointMomentumMaxCells = 1LL << 22;
+// When the momentum systems are solved in one joint launch. Measured on the
+// 1.2 M-cell box: three sequential solves take 0.76 ms against 0.79 ms for
+// the joint launch (the three working sets exceed L2 together, one at a time
+// they do not), while a case under a solver block cap (a batch or a server
+// running cases side by side) gains ~10% from the joint launch, and so does
+// a small case, whose solves are latency-bound. At 25 M cells the joint
+// launch is 15% slower (each team streams its own vectors from HBM on a third
+// of the SMs, and the team with the most iterations sets the time).
+constexpr long long kJointMomentumMaxCells = 1LL << 22;        // capped cases
+constexpr long long kJointMomentumMaxCellsUncapped = 1LL << 20;
+
+bool joint_momentum(const ss_case* c) {
+  return c->n_cell <= (c->block_cap > 0 ? kJointMomentumMaxCells : kJointMomentumMaxCellsUncapped);
+}
 
 ss_status one_step(ss_case* c) {
   const int ncomp = c->pr.dim;
-  if (c->n_cell <= kJointMomentumMaxCells) {  // 1: intermediate velocity (Eq. 3.3)
+  if (joint_momentum(c)) {  // 1: intermediate velocity (Eq. 3.3)
     for (int a = 0; a < ncomp; ++a) STAGE_TRY(stage_assemble(c, a));
     STAGE_TRY(stage_solve_momentum(c));
   } else {
