@@ -32,7 +32,6 @@ if ROOT not in sys.path:
 
 from paper_2303_10783_gb300 import cases  # noqa: E402
 
-WORKLOAD = "box_3d_128x96x96"
 # Algorithmic work of the multigrid-preconditioned pressure solve (k_pcg_mg), per fine cell:
 #   one CG iteration with a V(2,2)-cycle moves, at the fine level, A p (8 B in FP32), the x/r
 #   update with the first smoothing sweep (32), second pre-sweep (12), residual (12),
@@ -80,11 +79,33 @@ def dist_env():
     return rank, world, local
 
 
-def workload(args, rank=0):
-    """The benchmark case; rank r gets seed 1 + r (independent replica)."""
+def workload(args, rank=0, k=1):
+    """The benchmark case; rank r gets seed 1 + r (independent replica). k > 1:
+    the same case at 1/k of the resolution per axis (a bounded oracle sample)."""
+    nx, ny, nz = max(args.nx // k, 2), max(args.ny // k, 2), max(args.nz // k, 2)
     if getattr(args, "workload", "box") == "ingot":
-        return cases.ingot_3d(args.nx, args.ny, args.nz, seed=4 + rank)
-    return cases.box_3d(args.nx, args.ny, args.nz, seed=1 + rank)
+        return cases.ingot_3d(nx, ny, nz, seed=4 + rank)
+    return cases.box_3d(nx, ny, nz, seed=1 + rank)
+
+
+def workload_name(args):
+    kind = "ingot" if getattr(args, "workload", "box") == "ingot" else "box"
+    return "%s_3d_%dx%dx%d" % (kind, args.nx, args.ny, args.nz)
+
+
+# Oracle samples are bounded: the workload's own case at the smallest
+# per-axis reduction k that keeps it within a cell budget (the oracle runs
+# ~1e5 cell-steps/s on one host core, so 1.3 M cells is ~12 s per step).
+CPU_BASELINE_MAX_CELLS = 1_300_000     # one step (cpu_baseline leg)
+REFERENCE_MAX_CELLS = 160_000          # warm-up + timed steps (--impl reference)
+
+
+def sample_case(args, max_cells):
+    """(case, k): the workload at 1/k resolution per axis, k the smallest with <= max_cells cells."""
+    k = 1
+    while max(args.nx // k, 2) * max(args.ny // k, 2) * max(args.nz // k, 2) > max_cells:
+        k += 1
+    return workload(args, k=k), k
 
 
 def init_group(world):
@@ -187,16 +208,17 @@ def kernel_source_sha():
     return h.hexdigest()
 
 
-def kernel_traffic(kernel):
+def kernel_traffic(kernel, workload):
     """DRAM bytes per launch of `kernel` from the committed ncu summary, if the
-    summary was taken on the current source (its sha256 matches); else None."""
+    summary was taken on the current source (its sha256 matches) and on this
+    workload; else None."""
     path = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(path):
         return None
     sha = kernel_source_sha()
     for line in open(path):
         m = re.match(r"\s*(\S+)\s+sha256=(\w+)\s+bytes_per_launch=([0-9.eE+]+)\s+workload=(\S+)", line)
-        if m and m.group(1) == kernel and m.group(2) == sha:
+        if m and m.group(1) == kernel and m.group(2) == sha and m.group(4) == workload:
             return float(m.group(3)), m.group(4)
     return None
 
@@ -204,16 +226,17 @@ def kernel_traffic(kernel):
 def cpu_baseline(args):
     """The FP64 oracle as it stands, one full step of the same workload on the host."""
     import oracle
-    case = workload(args)
+    case, k = sample_case(args, CPU_BASELINE_MAX_CELLS)
     f = cases.initial_fields(case)
     g = oracle.Grid(case)
     st = oracle.initial_state(case, f["T"], f["C"])
     t = time.perf_counter()
     oracle.step(g, st, case)
     dt = time.perf_counter() - t
+    res = "" if k == 1 else " at 1/%d resolution per axis (%dx%dx%d)" % (k, g.n[0], g.n[1], g.n[2])
     return {"value": g.ncell / dt, "unit": "cell-steps/s", "cores": 1, "kind": "oracle",
-            "sample": "one full time step of %s (%d cells) from the seeded initial state, numpy/scipy FP64, "
-                      "single thread, %.1f s" % (WORKLOAD, g.ncell, dt)}
+            "sample": "one full time step of %s%s (%d cells) from the seeded initial state, numpy/scipy FP64, "
+                      "single thread, %.1f s" % (workload_name(args), res, g.ncell, dt)}
 
 
 def run_reference(args):
@@ -221,8 +244,8 @@ def run_reference(args):
     if rank != 0:
         return 0
     import oracle
-    # bounded sample of the workload: the same box at half resolution per axis
-    case = cases.box_3d(max(args.nx // 2, 2), max(args.ny // 2, 2), max(args.nz // 2, 2), seed=1)
+    # bounded sample of the workload: the same case at reduced resolution per axis
+    case, k = sample_case(args, REFERENCE_MAX_CELLS)
     f = cases.initial_fields(case)
     g = oracle.Grid(case)
     st = oracle.initial_state(case, f["T"], f["C"])
@@ -233,13 +256,13 @@ def run_reference(args):
         st = oracle.step(g, st, case)
     dt = time.perf_counter() - t
     value = g.ncell * args.steps / dt
-    sample = ("the %s workload's box at half resolution per axis (%dx%dx%d = %d cells), %d timed steps after %d "
-              "warm-up, numpy/scipy FP64, single thread" % (WORKLOAD, g.n[0], g.n[1], g.n[2], g.ncell, args.steps,
-                                                            args.warmup))
+    sample = ("the %s workload at 1/%d resolution per axis (%dx%dx%d = %d cells), %d timed steps after %d "
+              "warm-up, numpy/scipy FP64, single thread" % (workload_name(args), k, g.n[0], g.n[1], g.n[2], g.ncell,
+                                                            args.steps, args.warmup))
     out = {"metric": "cell-steps/s", "value": value, "unit": "cell-steps/s", "n_gpus": args.gpus, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-           "config": {"workload": WORKLOAD, "sample_cells": g.ncell, "precision": "fp64"},
+           "config": {"workload": workload_name(args), "sample_cells": g.ncell, "precision": "fp64"},
            "cpu_baseline": {"value": value, "unit": "cell-steps/s", "cores": 1, "kind": "oracle", "sample": sample},
            "e2e": {"value": value, "unit": "cell-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
@@ -352,7 +375,7 @@ def field_errors(a, b, dim):
     return out
 
 
-def roofline(precision_name, m, ncell, steps):
+def roofline(precision_name, m, ncell, steps, wname):
     """Roofline of the dominant stage (device time from the library's events on the case stream)."""
     stage_ms = m["prof"]["ms"]
     top = max(stage_ms, key=stage_ms.get)
@@ -379,7 +402,7 @@ def roofline(precision_name, m, ncell, steps):
                    peak_basis="FP64 pipe: 4 flop/clk/SM x 152 SMs x %.0f MHz median SM clock under load" % sm_mhz,
                    hbm_achieved_GBps=bytes_ / t_launch / 1e9)
         out["algorithmic_per_launch"]["flops"] = flops
-    tr = kernel_traffic(out["kernel"])
+    tr = kernel_traffic(out["kernel"], wname)
     out["traffic"] = tr[0] if tr else None
     if top != "solve_p":
         # per-unit counts are defined for the pressure solve; say when another stage took longer
@@ -418,7 +441,7 @@ def run_ours(args):
         "metric": "cell-steps/s", "value": h["value"], "unit": "cell-steps/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": h["ms_max"] / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64" if head == "mixed" else "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD if args.workload == "box" else "ingot_3d_%dx%dx%d" % (args.nx, args.ny, args.nz),
+        "config": {"workload": workload_name(args),
                    "cells": ncell, "precision": head, "tol_p": case["tol_p"],
                    "tol_t": case["tol_t"], "dt": case["dt"], "pressure_preconditioner": case.get("precond_p", "mg"),
                    "parallelism": "replicas" if world > 1 else "single",
@@ -432,7 +455,7 @@ def run_ours(args):
                          "ss_set_fields(device) + ss_step(1) + ss_get_fields(device), device buffer -> pinned "
                          "host (side stream, during the next step)"} if h["e2e"] else None),
         "gpu_launches": h["prof"]["kernels"],
-        "roofline": roofline(head, h, ncell, args.steps),
+        "roofline": roofline(head, h, ncell, args.steps, workload_name(args)),
         "stage_ms_per_step": {k: v / args.steps for k, v in h["prof"]["ms"].items() if v > 0},
         "iters_per_step": {k: v / args.steps for k, v in h["prof"]["iters"].items()},
         "refinements_last_step": dict(h["stats"]["refinements"]),
@@ -442,7 +465,7 @@ def run_ours(args):
         out[name] = {"value": m["value"], "ms_per_step": m["ms_max"] / args.steps, "status": m["status"],
                      "dtype": "f64" if name == "fp64" else "f32+f64",
                      "e2e_value": m.get("e2e_value"), "gpu_launches": m["prof"]["kernels"],
-                     "roofline": roofline(name, m, ncell, args.steps),
+                     "roofline": roofline(name, m, ncell, args.steps, workload_name(args)),
                      "stage_ms_per_step": {k: v / args.steps for k, v in m["prof"]["ms"].items() if v > 0},
                      "iters_per_step": {k: v / args.steps for k, v in m["prof"]["iters"].items()}}
     if "mixed" in res and "fp64" in res:
@@ -524,14 +547,14 @@ def run_serving(args):
 
 def main():
     args = parse()
+    if args.workload == "ingot" and (args.nx, args.ny, args.nz) == (128, 96, 96):
+        args.nx, args.ny, args.nz = 384, 256, 256     # the ingot's own size unless given
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batched":
         return run_batched(args)
     if args.workload == "serving":
         return run_serving(args)
-    if args.workload == "ingot":
-        args.nx, args.ny, args.nz = 384, 256, 256
     return run_ours(args)
 
 
