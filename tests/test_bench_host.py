@@ -1,0 +1,54 @@
+"""Host logic of bench.py that needs no GPU: workload names, the bounded
+oracle samples and the lookup of committed DRAM traffic."""
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+
+def _args(kind, nx, ny, nz):
+    return type("A", (), {"workload": kind, "nx": nx, "ny": ny, "nz": nz})()
+
+
+def test_workload_name_follows_sizes():
+    assert bench.workload_name(_args("box", 128, 96, 96)) == "box_3d_128x96x96"
+    assert bench.workload_name(_args("ingot", 384, 256, 256)) == "ingot_3d_384x256x256"
+    assert bench.workload_name(_args("box", 64, 48, 32)) == "box_3d_64x48x32"
+
+
+def test_oracle_samples_are_bounded_and_keep_the_case():
+    for kind, n in (("box", (128, 96, 96)), ("ingot", (384, 256, 256))):
+        a = _args(kind, *n)
+        for budget in (bench.CPU_BASELINE_MAX_CELLS, bench.REFERENCE_MAX_CELLS):
+            case, k = bench.sample_case(a, budget)
+            cells = case["nx"] * case["ny"] * case["nz"]
+            assert cells <= budget
+            # k is the smallest reduction that fits
+            if k > 1:
+                prev = max(n[0] // (k - 1), 2) * max(n[1] // (k - 1), 2) * max(n[2] // (k - 1), 2)
+                assert prev > budget
+            assert (case["nx"], case["ny"], case["nz"]) == tuple(max(v // k, 2) for v in n)
+            # the sample is the workload's own case (domain and cooling), only coarser
+            full = bench.workload(a)
+            assert case["lx"] == full["lx"] and case["ly"] == full["ly"] and case["lz"] == full["lz"]
+            assert case["dt"] == full["dt"]
+    # the box workload's one-step CPU baseline runs at full size
+    assert bench.sample_case(_args("box", 128, 96, 96), bench.CPU_BASELINE_MAX_CELLS)[1] == 1
+
+
+def test_traffic_record_is_keyed_by_workload():
+    rec = None
+    for line in open(os.path.join(ROOT, "profiles", "traffic.txt")):
+        if line.startswith("k_pcg_mg<float>"):
+            rec = dict(f.split("=", 1) for f in line.split()[1:])
+    assert rec is not None
+    got = bench.kernel_traffic("k_pcg_mg<float>", rec["workload"])
+    if rec["sha256"] == bench.kernel_source_sha():
+        assert got is not None and got[0] == float(rec["bytes_per_launch"])
+    else:
+        assert got is None
+    assert bench.kernel_traffic("k_pcg_mg<float>", "some_other_workload") is None
