@@ -194,7 +194,11 @@ ss_status ss_sync(ss_case* c);
 ss_status ss_get_fields(ss_case* c, unsigned mask, void* const* dst, int dst_is_device);
 
 /* Overwrite the fields selected by `mask` from src[id] (restart, or seeded
- * initial noise). Other fields are left as they are. */
+ * initial noise). Other fields are left as they are. In a mixed-precision
+ * case with the multigrid pressure solver, each step's pressure correction
+ * (Eq. 3.4) starts from the previous step's correction; this call clears
+ * that warm start, so the next step depends on the case's state alone and a
+ * restarted case gives the same fields as a new case from the same state. */
 ss_status ss_set_fields(ss_case* c, unsigned mask, const void* const* src, int src_is_device);
 
 /* Recompute g_l, C_l and C_s from the current T and C in equilibrium: g_l = 1
@@ -252,8 +256,10 @@ const char* ss_last_error(void);
  *   SS_SYS_C: solute system (Eq. 3.10) advected by the current u;
  *   SS_SYS_T: T* system (Eq. 3.12) advected by the current u.
  * ss_solve(c, sys): solve the assembled system (initial guess: the current
- *   field for U/V/W/C/T, 0 for P) into the system's solution vector; returns
- *   the solve's outcome.
+ *   field for U/V/W/C/T; for P the previous pressure correction in a
+ *   mixed-precision case with the multigrid solver, 0 in a new case, after
+ *   ss_set_fields and on the other paths) into the system's solution vector;
+ *   returns the solve's outcome.
  * ss_get_system(c, sys, dst, dst_is_device): copy planes and vectors of the
  *   system into dst[0..8] = P, W, E, S, N, B, T (DIA planes, Eq. 4.1), b
  *   (right-hand side), x (solution); NULL entries are skipped. SS_SYS_P has

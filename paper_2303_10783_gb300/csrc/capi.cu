@@ -402,6 +402,10 @@ ss_status stage_solve(ss_case* c, int sys) {
   if (sys == SS_SYS_P) {
     ctl.tol = c->g.tol_p;
     ctl.max_it = c->g.max_it_p;
+    // the correction of the previous step (zero in a new case and after
+    // ss_set_fields) starts the mixed multigrid solve; the Jacobi and FP64
+    // solves start from zero
+    ctl.warm_start = 1;
     if (c->g.precond_p == SS_PRECOND_MG)
       e = launch_pcg_mg(c->mg, c->pr, c->pb, c->pc, ctl, c->sc[0], c->st, c->stream);
     else
@@ -709,6 +713,9 @@ ss_status ss_set_fields(ss_case* c, unsigned mask, const void* const* src, int s
     CUDA_TRY(cudaMemcpyAsync(field_ptr(c, id), src[id], field_len(c, id) * sizeof(double),
                              src_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
   }
+  // a new state clears the pressure solve's warm start, so the next step
+  // depends on the state alone (as in a new case)
+  CUDA_TRY(cudaMemsetAsync(c->pc, 0, c->n_cell * sizeof(double), c->stream));
   if ((mask & (1u << SS_GL)) && c->alloy_set) {
     // keep K^{-1} and A_g consistent with the new g_l; C_l and C_s stay as they are
     cudaError_t e = launch_equilibrate(c->pr, c->T, c->C, c->gl, c->Cl, c->Cs, c->Kinv, c->Ag, 0, 0, c->stream);

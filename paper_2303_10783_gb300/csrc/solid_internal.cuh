@@ -392,6 +392,7 @@ struct SolverCtl {
   int stat_index;        // SS_SYS_* slot of DevStatus::stat
   double inner_tol;      // relative tolerance of each FP32 inner solve (mixed path)
   int block_cap;         // > 0: at most this many blocks in the cooperative launch
+  int warm_start = 0;    // 1: the solution buffer holds the initial guess (multigrid pressure, mixed path)
 };
 cudaError_t launch_bicgstab(const Sys& sys, int has_z, const SolverCtl& ctl, Scratch& sc, DevStatus* st,
                             cudaStream_t s);
