@@ -21,7 +21,7 @@ Linear systems are stored as seven DIA planes on the grid of their unknowns
 the matrix reads  P[r] x[r] + W[r] x[r-1] + E[r] x[r+1] + S[r] x[r-m_x] + ...
 A plane holds 0 wherever the neighbour is not an unknown of the system.
 
-Readings of points the paper leaves open (each restated in the design doc):
+Readings of points the paper leaves open:
 * flux-form upwind convection everywhere (Eq. 3.28-3.29), with the advecting
   velocity u^n in the momentum step and u^{n+1} in the C and T steps;
 * advecting velocities on staggered control-volume faces are arithmetic

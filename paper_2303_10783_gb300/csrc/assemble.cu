@@ -61,7 +61,7 @@ __device__ __forceinline__ int fidx(const Params& pr, int d, int i, int j, int k
 __device__ __forceinline__ int cidx(const Params& pr, int i, int j, int k) { return i + pr.nx * (j + pr.ny * k); }
 
 // These kernels are bound by the FP64 pipe (a small fraction of the FP32
-// rate on this GPU), so work that needs no FP64 arithmetic is done on the
+// rate on GB300), so work that needs no FP64 arithmetic is done on the
 // integer pipes: the sign split of an advecting velocity and the FP64 -> FP32
 // rounding of the plane copies.
 

@@ -285,8 +285,8 @@ __device__ __forceinline__ bool team_sum(Vec<K> x, const Team& t, int max_blocks
 // The same reduction (x a Vec<K> of doubles or a VecF<K> of floats), with
 // the totals handed to post(const double* tot), run by thread 0 of each
 // block: the Krylov scalars (divisions, square roots, stopping tests) are
-// formed once per block instead of once per thread, which on this GPU's
-// narrow FP64 pipe costs microseconds per iteration. What post writes to
+// formed once per block instead of once per thread, which on GB300's narrow
+// FP64 pipe (two lanes per clock per SM) costs microseconds per iteration. What post writes to
 // shared memory is visible to every thread of the block on return.
 template <int K, class In, class Post>
 __device__ __forceinline__ bool team_sum_post(const In& x, const Team& t, int max_blocks, int slot, DevStatus* st,

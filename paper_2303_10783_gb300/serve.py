@@ -56,7 +56,7 @@ class Server:
     def _cap_for(r):
         """Blocks per solver launch in proportion to the request's size: one
         per 8192 cells, at least 16; no cap once that reaches 152 (one block
-        per SM of this GPU)."""
+        per SM of a GB300)."""
         cap = max(16, r.cells // 8192)
         return 0 if cap >= 152 else cap
 
