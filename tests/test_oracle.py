@@ -550,3 +550,39 @@ def test_manufactured_advection_diffusion_first_order():
     e3 = _mms_error(64, 40)
     assert e3 < e2 < e1
     assert np.log2(e2 / e3) > 0.7
+
+
+# ---------------------------------------------------------------- Darcy drag (Eq. 2.8 in Eq. 3.3)
+
+@pytest.mark.parametrize("g", [0.5, 0.8, 0.95])
+def test_darcy_damping_of_uniform_flow_closed_form(g):
+    """A uniform x-velocity U in a uniform mushy zone (g_l = g), with no
+    pressure gradient and the gravity along z, keeps convection and diffusion
+    in balance away from the walls, so the implicit drag alone acts:
+    u* (1/dt + nu K^-1) = U / dt, i.e. u* = U / (1 + dt nu K^-1) with
+    K^-1 = (1 - g)^2 / (K0 (g^3 + eps)). The wall rows' influence decays by
+    ~dt nu / h^2 (~1e-4 here) per cell, so faces four cells in meet the closed
+    form to rounding. A dropped or sign-flipped drag, or a drag on the wrong
+    face average, fails by orders of magnitude (dt nu K^-1 = 7.9, 0.31, 0.012).
+    Along x the x-walls' disturbance is carried by the upwind convection and
+    decays only by ~U dt / h (~0.02) per cell, so the check keeps to the middle
+    of the x range, more than eight cells from either x-wall."""
+    case = cases.box_3d(24, 16, 16)
+    al = case["alloy"]
+    grid = oracle.Grid(case)
+    assert grid.vert == 2
+    U = 0.01
+    u = np.zeros(grid.faces(0))                   # (z, y, x) order
+    u[..., 1:-1] = U                              # interior x-faces; the walls hold 0
+    st = State([u, np.zeros(grid.faces(1)), np.zeros(grid.faces(2))], np.zeros(grid.cells),
+               np.full(grid.cells, case["T0"]), np.full(grid.cells, al["C0"]), np.full(grid.cells, g),
+               np.full(grid.cells, al["C0"]), np.full(grid.cells, al["kp"] * al["C0"]))
+    sysm = oracle.assemble_momentum(grid, st, case, 0)
+    ustar = oracle.solve_system(sysm, x0=st.vel[0], method="direct", rtol=1e-14).reshape(grid.faces(0))
+    nu = al["mu"] / al["rho"]
+    kinv = (1.0 - g) ** 2 / (al["K0"] * (g ** 3 + al["darcy_eps"]))
+    expect = U / (1.0 + case["dt"] * nu * kinv)
+    core = ustar[4:-4, 4:-4, 10:16]
+    assert np.abs(core - expect).max() <= 1e-13 * expect, (np.abs(core - expect).max(), expect)
+    # and the drag matters: the undamped value is far off
+    assert abs(U - expect) > 1e-2 * U
