@@ -586,3 +586,38 @@ def test_darcy_damping_of_uniform_flow_closed_form(g):
     assert np.abs(core - expect).max() <= 1e-13 * expect, (np.abs(core - expect).max(), expect)
     # and the drag matters: the undamped value is far off
     assert abs(U - expect) > 1e-2 * U
+
+
+# ---------------------------------------------------------------- Boussinesq force (Eq. 2.9 in Eq. 3.3)
+
+@pytest.mark.parametrize("dT,dC,g", [(2.0, 0.0, 1.0), (0.0, 0.5, 1.0), (1.5, -0.3, 0.8)])
+def test_buoyancy_of_a_resting_melt_closed_form(dT, dC, g):
+    """A resting melt (u = 0, p = 0) with uniform T = T_ref + dT and
+    C_l = C_ref + dC feels f = g (1 - beta_T dT - beta_c dC) with g pointing
+    down; the constant part is hydrostatic, so the intermediate vertical
+    velocity away from the walls is w* = dt |g| (beta_T dT + beta_c dC) /
+    (1 + dt nu K^-1): a warmer melt (beta_T > 0) rises and a melt richer in
+    the heavier component (beta_c < 0 here) sinks; the horizontal components
+    stay at rest. The wall rows' influence decays by ~dt nu / h^2 per cell."""
+    case = cases.box_3d(24, 16, 16)
+    al = case["alloy"]
+    grid = oracle.Grid(case)
+    assert grid.vert == 2 and al["betaT"] > 0 and al["betaC"] < 0 and al["gravity"] > 0
+    zero = [np.zeros(grid.faces(a)) for a in range(3)]
+    Cl = al["C0"] + dC
+    st = State(zero, np.zeros(grid.cells), np.full(grid.cells, case["T0"] + dT), np.full(grid.cells, al["C0"]),
+               np.full(grid.cells, g), np.full(grid.cells, Cl), np.full(grid.cells, al["kp"] * Cl))
+    out = []
+    for a in range(3):
+        sysm = oracle.assemble_momentum(grid, st, case, a)
+        out.append(oracle.solve_system(sysm, x0=st.vel[a], method="direct", rtol=1e-14).reshape(grid.faces(a)))
+    nu = al["mu"] / al["rho"]
+    kinv = (1.0 - g) ** 2 / (al["K0"] * (g ** 3 + al["darcy_eps"]))
+    expect = case["dt"] * al["gravity"] * (al["betaT"] * dT + al["betaC"] * dC) / (1.0 + case["dt"] * nu * kinv)
+    core = out[2][4:-4, 4:-4, 4:-4]
+    assert np.abs(core - expect).max() <= 1e-12 * abs(expect), (np.abs(core - expect).max(), expect)
+    if dC == 0.0:
+        assert expect > 0                         # warmer than the reference: rises
+    if dT == 0.0:
+        assert expect < 0                         # richer in the heavier component: sinks
+    assert np.abs(out[0]).max() == 0.0 and np.abs(out[1]).max() == 0.0
