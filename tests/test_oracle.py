@@ -621,3 +621,38 @@ def test_buoyancy_of_a_resting_melt_closed_form(dT, dC, g):
     if dT == 0.0:
         assert expect < 0                         # richer in the heavier component: sinks
     assert np.abs(out[0]).max() == 0.0 and np.abs(out[1]).max() == 0.0
+
+
+# ---------------------------------------------------------------- pressure gradient (Eq. 3.3, explicit -grad p^n / rho)
+
+@pytest.mark.parametrize("axis", [0, 1])
+def test_linear_pressure_accelerates_a_resting_liquid(axis):
+    """A resting liquid (g_l = 1, so no drag; T and C_l at their reference
+    values, so no buoyancy) under the linear pressure p^n = G x_axis takes
+    u*_axis = -dt G / rho away from the walls: the face difference of p
+    across one cell is G h exactly, and the other components stay at rest.
+    A wrong sign, a missing 1/rho or 1/h, or a gradient on the wrong axis
+    fails it."""
+    case = cases.box_3d(24, 16, 16)
+    al = case["alloy"]
+    grid = oracle.Grid(case)
+    G = 250.0                                     # Pa/m
+    # cell centres along the axis; cells are (z, y, x) ordered
+    n = grid.n[axis]
+    xc = (np.arange(n) + 0.5) * grid.h[axis]
+    shape = [1, 1, 1]
+    shape[2 - axis] = n
+    p = np.broadcast_to(G * xc.reshape(shape), grid.cells).copy()
+    zero = [np.zeros(grid.faces(a)) for a in range(3)]
+    st = State(zero, p, np.full(grid.cells, case["T0"]), np.full(grid.cells, al["C0"]),
+               np.full(grid.cells, 1.0), np.full(grid.cells, al["C0"]), np.full(grid.cells, al["kp"] * al["C0"]))
+    out = []
+    for a in range(3):
+        sysm = oracle.assemble_momentum(grid, st, case, a)
+        out.append(oracle.solve_system(sysm, x0=st.vel[a], method="direct", rtol=1e-14).reshape(grid.faces(a)))
+    expect = -case["dt"] * G / al["rho"]
+    core = out[axis][4:-4, 4:-4, 4:-4]
+    assert np.abs(core - expect).max() <= 1e-12 * abs(expect), (np.abs(core - expect).max(), expect)
+    for a in range(3):
+        if a != axis:
+            assert np.abs(out[a]).max() == 0.0
