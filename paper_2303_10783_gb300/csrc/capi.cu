@@ -470,18 +470,21 @@ ss_status stage_solve_momentum(ss_case* c) {
 }
 
 // When the momentum systems are solved in one joint launch. Measured on the
-// 1.2 M-cell box: three sequential solves take 0.76 ms against 0.79 ms for
-// the joint launch (the three working sets exceed L2 together, one at a time
-// they do not), while a case under a solver block cap (a batch or a server
-// running cases side by side) gains ~10% from the joint launch, and so does
-// a small case, whose solves are latency-bound. At 25 M cells the joint
-// launch is 15% slower (each team streams its own vectors from HBM on a third
-// of the SMs, and the team with the most iterations sets the time).
-constexpr long long kJointMomentumMaxCells = 1LL << 22;        // capped cases
+// 1.2 M-cell box, mixed precision: three sequential solves take 0.76 ms
+// against 0.79 ms for the joint launch (the three FP32 working sets exceed L2
+// together, one at a time they do not); in FP64 the joint launch wins (0.77
+// against 0.97 ms: those solves are bound by the FP64 pipe, not by L2). A
+// case under a solver block cap (a batch or a server running cases side by
+// side) gains ~10% from the joint launch, and so does a small case, whose
+// solves are latency-bound. At 25 M cells the joint launch is 15% slower
+// (each team streams its own vectors from HBM on a third of the SMs, and the
+// team with the most iterations sets the time).
+constexpr long long kJointMomentumMaxCells = 1LL << 22;        // capped or FP64 cases
 constexpr long long kJointMomentumMaxCellsUncapped = 1LL << 20;
 
 bool joint_momentum(const ss_case* c) {
-  return c->n_cell <= (c->block_cap > 0 ? kJointMomentumMaxCells : kJointMomentumMaxCellsUncapped);
+  const bool wide = c->block_cap > 0 || c->g.precision == SS_FP64;
+  return c->n_cell <= (wide ? kJointMomentumMaxCells : kJointMomentumMaxCellsUncapped);
 }
 
 ss_status one_step(ss_case* c) {
