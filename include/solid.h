@@ -22,8 +22,10 @@
  *     w nx*ny*(nz+1); faces 0 and n along their own axis are walls.
  *     2D cases have nz = 1 and no w.
  *   - The vertical axis is y in 2D and z in 3D; gravity points along minus it.
- *   - All walls are rigid, no-slip and impermeable to solute; each wall is
- *     adiabatic or Robin-cooled (heat flux U (T - T_ext), U = 1/(1/h + dx/(2k))).
+ *   - All walls are rigid and impermeable to flow and solute. Each wall is
+ *     no-slip or free-slip for the tangential velocity, and thermally
+ *     adiabatic, Robin-cooled (heat flux U (T - T_ext), U = 1/(1/h + dx/(2k)))
+ *     or held at a temperature that changes linearly in time (see ss_bc).
  *   - Device memory: the caller allocates one workspace of ss_workspace_bytes()
  *     bytes (any device allocator, e.g. torch) and keeps it alive until
  *     ss_destroy(); the library carves every field, DIA plane and solver
@@ -292,6 +294,25 @@ ss_status ss_assemble_forward(ss_case* c, int sys);
 ss_status ss_project(ss_case* c);
 ss_status ss_lever(ss_case* c);
 
+/* ---- Device-side waits.
+ *
+ * Every wait inside a kernel of a case (the barriers of the cooperative
+ * solvers) polls a bounded number of times; a wait that runs out sets a
+ * sticky error, every block of the launch returns, and the next ss_sync /
+ * ss_get_stats reports SS_ETIMEOUT (and clears it). The context stays
+ * usable.
+ *
+ * ss_set_wait_limit(c, polls): polls per wait before giving up, for the
+ *   case's later launches (stream-ordered); 0 restores the default (about a
+ *   second). SS_EINVAL outside [0, 2^24].
+ * ss_wait_selftest(c): enqueue one block that waits at a barrier no other
+ *   block ever reaches, so the wait runs out after the case's limit; the
+ *   next ss_sync then returns SS_ETIMEOUT. It exercises the timeout path
+ *   without a fault or a hang; call ss_sync before stepping again (the
+ *   sticky error would otherwise stop the next solves). */
+ss_status ss_set_wait_limit(ss_case* c, long long polls);
+ss_status ss_wait_selftest(ss_case* c);
+
 /* ---- Pressure-correction solve that allocates nothing.
  *
  * The paper has no counterpart to this call; it exists for callers that
@@ -299,10 +320,11 @@ ss_status ss_lever(ss_case* c);
  * the whole GPU and rejects allocations it did not make, a loop with a hard
  * latency budget where a cudaMalloc (which may synchronise the device) is
  * not acceptable, or a plugin that is handed only a stream and device
- * pointers. It solves A p' = b - mean(b), A = -L the Neumann Laplacian of
- * Eq. 3.4 on an nx*ny*nz cell grid (x fastest; nz ignored when dim == 2)
- * with spacings hx, hy, hz, by the same Jacobi-preconditioned CG as ss_solve
- * (SS_SYS_P), and writes the zero-mean p' to x.
+ * pointers. It solves A p = b - mean(b) for the zero-mean p, where A is the
+ * negated 7-point (5-point in 2D) Laplacian on cells with zero-flux walls,
+ * on an nx*ny*nz cell grid (x fastest; nz ignored when dim == 2) with
+ * spacings hx, hy, hz, by the same Jacobi-preconditioned CG as ss_solve on
+ * the pressure system with SS_PRECOND_JACOBI, and writes p to x.
  *
  *   b, x      device pointers to nx*ny*nz doubles (b is not modified; the
  *             caller owns both)
@@ -320,9 +342,16 @@ ss_status ss_lever(ss_case* c);
  * call's contents (each call clears what must start at zero), so calls that
  * overlap on the GPU -- on different streams or from different threads --
  * race and must not be issued. The first call on each device looks up the
- * array's device address (cudaGetSymbolAddress) with that device current;
- * make that first call before any stream capture. No cudaMalloc, cudaFree
- * or allocating library routine is called. */
+ * array's device address (cudaGetSymbolAddress) with that device current
+ * and caches it; devices with an index of 64 or more are refused
+ * (SS_ECUDA, invalid device). Make that first call before any stream
+ * capture. When iters and relres are both NULL the call only enqueues the
+ * work: it then reports no solver outcome at all (no iteration cap, no
+ * non-finite residual, no barrier timeout), because that outcome lives in the
+ * shared array and the next call clears it. A call made while its stream is
+ * being captured must pass iters = relres = NULL (the other form copies the
+ * outcome back and waits for the stream). No cudaMalloc, cudaFree or
+ * allocating library routine is called. */
 ss_status ss_poisson_solve_noalloc(int dim, int nx, int ny, int nz, double hx, double hy, double hz,
                                    const double* b, double* x, double tol, int max_it, int* iters,
                                    double* relres, void* stream);

@@ -37,6 +37,17 @@ __global__ void k_fill(double* x, double v, long long n) {
     x[i] = v;
 }
 
+__global__ void k_set_spin_limit(DevStatus* st, long long polls) { st->spin_limit = polls; }
+
+// One block waits at a barrier of a two-block team whose other member is
+// never launched: nothing ever completes the count, so the wait runs until
+// the case's poll limit, then sets the sticky barrier error and returns.
+__global__ void k_wait_selftest(DevStatus* st) {
+  unsigned int epoch = 0;
+  const Team t{0, 2, &st->selftest_counter, nullptr};
+  team_barrier(st, t, epoch);
+}
+
 // Workspace planner: the same walk computes the size and the pointers.
 struct Planner {
   char* base;
@@ -472,7 +483,7 @@ ss_status stage_solve_momentum(ss_case* c) {
 // When the momentum systems are solved in one joint launch. Measured on the
 // 1.2 M-cell box, mixed precision: three sequential solves take 0.76 ms
 // against 0.79 ms for the joint launch (the three FP32 working sets exceed L2
-// together, one at a time they do not); in FP64 the joint launch wins (0.77
+// together, one at a time they do not); in FP64 the joint launch wins (0.79
 // against 0.97 ms: those solves are bound by the FP64 pipe, not by L2). A
 // case under a solver block cap (a batch or a server running cases side by
 // side) gains ~10% from the joint launch, and so does a small case, whose
@@ -906,6 +917,23 @@ ss_status ss_convert_f64_to_f32(const double* src, float* dst, long long n, void
   if (n == 0) return SS_OK;
   cudaError_t e = launch_to_f32(src, dst, n, (cudaStream_t)stream);
   if (e != cudaSuccess) return fail(SS_ECUDA, "convert: %s", cudaGetErrorString(e));
+  return SS_OK;
+}
+
+ss_status ss_set_wait_limit(ss_case* c, long long polls) {
+  STAGE_TRY(check_case(c));
+  if (polls < 0 || polls > kMaxSpinLimit)
+    return fail(SS_EINVAL, "polls must be in [0, %lld] (0: the default)", kMaxSpinLimit);
+  k_set_spin_limit<<<1, 1, 0, c->stream>>>(c->st, polls);
+  CUDA_TRY(cudaGetLastError());
+  return SS_OK;
+}
+
+ss_status ss_wait_selftest(ss_case* c) {
+  STAGE_TRY(check_case(c));
+  CUDA_TRY(cudaMemsetAsync(&c->st->selftest_counter, 0, sizeof(unsigned int), c->stream));
+  k_wait_selftest<<<1, 32, 0, c->stream>>>(c->st);
+  CUDA_TRY(cudaGetLastError());
   return SS_OK;
 }
 

@@ -20,7 +20,8 @@ namespace solid {
 
 constexpr int kBlock = 512;              // threads per block of every kernel
 constexpr int kMaxRedSlots = 16;         // reduction slots (one per reduction site)
-constexpr long long kSpinLimit = 1LL << 21;  // grid-barrier polls before giving up (about a second)
+constexpr long long kSpinLimit = 1LL << 21;  // default barrier polls before giving up (about a second)
+constexpr long long kMaxSpinLimit = 1LL << 24;  // largest limit a caller may set (several seconds)
 
 // device-side error codes (sticky word in DevStatus::err)
 enum : int { kErrNone = 0, kErrBarrier = 1 };
@@ -54,6 +55,8 @@ struct DevStatus {
   double scal[kMaxRedSlots * 4]; // broadcast scalars (unused by the all-blocks reduction)
   double time;                   // simulated time of the fields; k_lever advances it by dt
   unsigned int team_arrivals[kMaxTeams]; // barrier counters of the teams of a multi-system solve
+  unsigned int selftest_counter; // counter of the wait self-test (ss_wait_selftest)
+  long long spin_limit;          // polls a barrier waits before giving up (0: kSpinLimit)
 };
 
 template <typename T>
@@ -138,10 +141,11 @@ struct Team {
 
 // Barrier over the blocks of a team. `epoch` counts barriers passed by this
 // block. Thread 0 arrives with an acq_rel atomic (publishing the block's
-// writes) and polls with acquire loads. A poll limit bounds the wait: on
-// expiry the sticky error is set and every block returns false from then
-// on, so the kernel unwinds instead of hanging. The error flag is shared by
-// all teams, so one team's failure unwinds every team.
+// writes) and polls with acquire loads. A poll limit bounds the wait (the
+// case's st->spin_limit, read once a block has polled 256 times; 0 means
+// kSpinLimit): on expiry the sticky error is set and every block returns
+// false from then on, so the kernel unwinds instead of hanging. The error
+// flag is shared by all teams, so one team's failure unwinds every team.
 __device__ __forceinline__ bool team_barrier(DevStatus* st, const Team& t, unsigned int& epoch) {
   __shared__ int s_ok;
   __syncthreads();
@@ -152,11 +156,15 @@ __device__ __forceinline__ bool team_barrier(DevStatus* st, const Team& t, unsig
     const unsigned int old = atom_add_acq_rel_u32(t.counter, 1u);
     int ok = 1;
     if (old + 1u != target) {
-      long long spins = 0;
+      long long spins = 0, limit = 0;
       while (ld_acquire_u32(t.counter) < target) {
         if ((++spins & 255) == 0) {
           if (*(volatile int*)&st->err != kErrNone) { ok = 0; break; }
-          if (spins > kSpinLimit) { atomicExch(&st->err, kErrBarrier); ok = 0; break; }
+          if (limit == 0) {
+            const long long l = st->spin_limit;
+            limit = (l > 0 && l <= kMaxSpinLimit) ? l : kSpinLimit;
+          }
+          if (spins >= limit) { atomicExch(&st->err, kErrBarrier); ok = 0; break; }
         }
       }
     }

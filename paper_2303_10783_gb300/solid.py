@@ -96,6 +96,8 @@ def _declare(lib):
         "ss_lever": [P],
         "ss_set_profiling": [P, ctypes.c_int],
         "ss_get_profile": [P, ctypes.POINTER(Profile)],
+        "ss_set_wait_limit": [P, ctypes.c_longlong],
+        "ss_wait_selftest": [P],
         "ss_poisson_solve_noalloc": [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                      ctypes.c_double, ctypes.c_double, P, P, ctypes.c_double, ctypes.c_int,
                                      ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double), P],
@@ -195,6 +197,14 @@ class Case:
     def set_block_cap(self, max_blocks):
         """At most ``max_blocks`` blocks per cooperative solver launch (0: no cap)."""
         check(self.lib.ss_set_block_cap(self.h, int(max_blocks)))
+
+    def set_wait_limit(self, polls):
+        """Polls per device-side wait before it gives up (0: the default, about a second)."""
+        check(self.lib.ss_set_wait_limit(self.h, int(polls)))
+
+    def wait_selftest(self):
+        """Enqueue a wait that nothing completes; the next sync reports SS_ETIMEOUT."""
+        check(self.lib.ss_wait_selftest(self.h))
 
     def set_time(self, t):
         check(self.lib.ss_set_time(self.h, float(t)))

@@ -328,6 +328,33 @@ def test_iteration_cap_is_reported(lib):
     c.close()
 
 
+def test_device_wait_runs_out_and_the_case_recovers(lib):
+    """A device-side wait that nothing completes gives up after the case's
+    poll limit: the kernel returns, the next sync reports SS_ETIMEOUT (once),
+    and the case then steps normally and matches the oracle."""
+    case = _tight(cases.cavity_2d(20, 12))
+    f = cases.initial_fields(case)
+    c = solid.Case(case)
+    c.initialize(f["T"] - 0.8, f["C"])
+    c.set_wait_limit(4096)
+    c.wait_selftest()
+    assert c.sync(allow=(solid.SS_ETIMEOUT,)) == solid.SS_ETIMEOUT
+    assert b"timed out" in lib.ss_last_error()
+    assert c.sync() == solid.SS_OK              # the sticky error was cleared by the read
+    assert lib.ss_set_wait_limit(c.h, -1) == solid.SS_EINVAL
+    assert lib.ss_set_wait_limit(c.h, 1 << 30) == solid.SS_EINVAL
+    c.set_wait_limit(0)
+    c.step(3)
+    assert c.sync() == solid.SS_OK
+    gpu = c.get_fields(("T", "gl"))
+    c.close()
+    g = oracle.Grid(case)
+    st = oracle.initial_state(case, f["T"] - 0.8, f["C"])
+    for _ in range(3):
+        st = oracle.step(g, st, case)
+    assert _rel(gpu["T"], st.T) < STEP_TOL and np.abs(gpu["gl"] - st.gl).max() < STEP_TOL
+
+
 def test_bad_arguments(lib):
     import ctypes
     case = cases.cavity_2d(10, 8)
@@ -414,6 +441,52 @@ def test_full_size_steps_keep_invariants(lib, full):
     c.close()
 
 
+FULL_STEPS = 3
+FULL_BOUND = 1e-6     # relative L-inf bound on T, C and g_l of the mixed path (and checked on p and u here)
+
+
+@pytest.fixture(scope="module")
+def full_oracle(full):
+    """FULL_STEPS oracle steps of the 128x96x96 benchmark workload, started
+    inside the mushy range so that the lever rule and the Darcy terms act,
+    with the oracle's iterative solves at their 1e-13 floor."""
+    case = dict(full)
+    f = cases.initial_fields(case)
+    T0 = f["T"] - 0.8
+    g = oracle.Grid(case)
+    st = oracle.initial_state(case, T0, f["C"])
+    for _ in range(FULL_STEPS):
+        st = oracle.step(g, st, case, method="iterative")
+    return case, T0, f["C"], st
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_full_size_steps_match_oracle(lib, full_oracle, prec):
+    """The benchmarked path at the benchmark size and tolerances (128x96x96,
+    pressure tol 1e-10, transport tol 1e-12), element by element against the
+    oracle after FULL_STEPS steps. The mixed case takes the one-after-another
+    momentum solves and the full pressure hierarchy that the benchmark runs;
+    the FP64 case the joint momentum launch. T, C and g_l must be within the
+    1e-6 bound of the mixed path; so must p and the velocity (one vector
+    field, judged against its largest component)."""
+    case, T0, C0, ref = full_oracle
+    c = solid.Case(case, precision=PREC[prec])
+    c.initialize(T0, C0)
+    c.step(FULL_STEPS)
+    s = c.stats()
+    assert s["status"] == solid.SS_OK, s
+    gpu = c.get_fields()
+    c.close()
+    errs = {k: _rel(gpu[k], getattr(ref, k)) for k in ("p", "T", "C", "gl", "Cl", "Cs")}
+    vmax = max(np.abs(x).max() for x in ref.vel)
+    errs["velocity"] = max(np.abs(gpu[k] - ref.vel[a]).max() for a, k in enumerate("uvw")) / vmax
+    print("full-size %s vs oracle after %d steps: %s" % (prec, FULL_STEPS,
+                                                          ", ".join("%s %.2e" % kv for kv in errs.items())))
+    for k, e in errs.items():
+        assert e < FULL_BOUND, (k, e)
+    assert ref.gl.min() < 1.0
+
+
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_tiny_right_hand_side(lib, prec):
     """A nearly solenoidal u* gives a pressure right-hand side near the
@@ -485,6 +558,31 @@ FORWARD_CASES = [
     cases.cavity_2d(61, 37, robin={"x-": (400.0, 298.0), "y+": (60.0, 300.0)}),
     cases.box_3d(),
 ]
+
+
+@pytest.mark.parametrize("case", FORWARD_CASES[:2], ids=["3d-27x19x13-walls", "2d-61x37"])
+def test_forward_assembly_matches_oracle_forward(lib, case):
+    """The GPU forward assembly (Sec. 4, Eq. 4.5-4.7) against the oracle's own
+    forward assembly, written separately from the paper: every plane and
+    right-hand side of every system, with no-slip, free-slip, Robin and
+    time-linear Dirichlet walls."""
+    from oracle import forward as oforward
+    c, f = _random_case(case, 31)
+    c.set_time(1.25)
+    g = oracle.Grid(case)
+    st = _oracle_state(f)
+    refs = {name: oforward.forward_momentum(g, st, case, a) for a, name in enumerate("uvw"[: case["dim"]])}
+    refs["C"] = oforward.forward_solute(g, st.vel, st.gl, st.C, case)
+    refs["T"] = oforward.forward_temperature(g, st.vel, st.T, case, t=1.25 + case["dt"])
+    for name, ref in refs.items():
+        c.assemble_forward(name)
+        fw = c.get_system(name)
+        scale = np.abs(ref["P"]).max()
+        for k in oracle.PLANES:
+            assert np.abs(fw[k] - ref[k]).max() <= PLANE_TOL * scale, (name, k)
+        bs = max(np.abs(ref["b"]).max(), 1e-300)
+        assert np.abs(fw["b"] - ref["b"]).max() <= PLANE_TOL * bs, (name, "b")
+    c.close()
 
 
 @pytest.mark.parametrize("case", FORWARD_CASES, ids=["3d-27x19x13-walls", "2d-61x37", "3d-128x96x96"])
