@@ -67,6 +67,8 @@ def parse():
     ap.add_argument("--block-cap", type=int, default=-1,
                     help="serving: blocks per cooperative solver launch of each request (0: no cap; "
                          "-1: in proportion to the request's cells)")
+    ap.add_argument("--precond", choices=("dct", "mg", "jacobi"), default=None,
+                    help="pressure solver (default: the workload's own)")
     ap.add_argument("--nx", type=int, default=128)
     ap.add_argument("--ny", type=int, default=96)
     ap.add_argument("--nz", type=int, default=96)
@@ -85,8 +87,12 @@ def workload(args, rank=0, k=1):
     the same case at 1/k of the resolution per axis (a bounded oracle sample)."""
     nx, ny, nz = max(args.nx // k, 2), max(args.ny // k, 2), max(args.nz // k, 2)
     if getattr(args, "workload", "box") == "ingot":
-        return cases.ingot_3d(nx, ny, nz, seed=4 + rank)
-    return cases.box_3d(nx, ny, nz, seed=1 + rank)
+        case = cases.ingot_3d(nx, ny, nz, seed=4 + rank)
+    else:
+        case = cases.box_3d(nx, ny, nz, seed=1 + rank)
+    if getattr(args, "precond", None):
+        case["precond_p"] = args.precond
+    return case
 
 
 def workload_name(args):

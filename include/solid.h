@@ -64,7 +64,7 @@ typedef enum {
 } ss_status;
 
 enum { SS_FP64 = 0, SS_MIXED = 1 };                  /* ss_grid.precision */
-enum { SS_PRECOND_MG = 0, SS_PRECOND_JACOBI = 1 };   /* ss_grid.precond_p */
+enum { SS_PRECOND_MG = 0, SS_PRECOND_JACOBI = 1, SS_PRECOND_DCT = 2 };   /* ss_grid.precond_p */
 enum { SS_ADIABATIC = 0, SS_ROBIN = 1, SS_DIRICHLET = 2 };  /* ss_bc.thermal */
 enum { SS_NOSLIP = 0, SS_FREESLIP = 1 };             /* ss_bc.flow */
 enum { SS_XM = 0, SS_XP = 1, SS_YM = 2, SS_YP = 3, SS_ZM = 4, SS_ZP = 5 };  /* walls */
@@ -88,8 +88,12 @@ typedef struct {
   double tol_p;              /* relative 2-norm residual tolerance, pressure solve */
   double tol_t;              /* same for the transport solves (u, v, w, C, T) */
   int max_it_p, max_it_t;    /* iteration caps (>= 1) */
-  int precond_p;             /* pressure preconditioner: SS_PRECOND_MG (geometric multigrid
-                                V-cycle, default) or SS_PRECOND_JACOBI */
+  int precond_p;             /* pressure solver (Eq. 3.4): SS_PRECOND_MG, CG preconditioned by a
+                                geometric-multigrid V-cycle; SS_PRECOND_JACOBI, Jacobi-
+                                preconditioned CG; SS_PRECOND_DCT, FP64 iterative refinement
+                                around the exact inverse of the operator by cosine transforms
+                                along x (and y in 3D) and tridiagonal solves along the last
+                                axis, in FP32 (SS_MIXED) or FP64 */
 } ss_grid;
 
 /* Alloy and model data (Table 1 style). C is the mass fraction of the
@@ -200,7 +204,9 @@ ss_status ss_get_fields(ss_case* c, unsigned mask, void* const* dst, int dst_is_
  * case with the multigrid pressure solver, each step's pressure correction
  * (Eq. 3.4) starts from the previous step's correction; this call clears
  * that warm start, so the next step depends on the case's state alone and a
- * restarted case gives the same fields as a new case from the same state. */
+ * restarted case gives the same fields as a new case from the same state.
+ * It clears the stored T* increment of the T* initial guess for the same
+ * reason. */
 ss_status ss_set_fields(ss_case* c, unsigned mask, const void* const* src, int src_is_device);
 
 /* Recompute g_l, C_l and C_s from the current T and C in equilibrium: g_l = 1
@@ -256,7 +262,10 @@ const char* ss_last_error(void);
  *   SS_SYS_P: pressure-correction right-hand side -(rho/dt) div u* (Eq. 3.4),
  *             mean removed, with u* the last solved momentum components;
  *   SS_SYS_C: solute system (Eq. 3.10) advected by the current u;
- *   SS_SYS_T: T* system (Eq. 3.12) advected by the current u.
+ *   SS_SYS_T: T* system (Eq. 3.12) advected by the current u; T is replaced
+ *             by the solve's initial guess: T^n + (T* - T^{n-1}) of the
+ *             previous step when that step ran its T* assembly and lever
+ *             stage, else T^n unchanged.
  * ss_solve(c, sys): solve the assembled system (initial guess: the current
  *   field for U/V/W/C/T; for P the previous pressure correction in a
  *   mixed-precision case with the multigrid solver, 0 in a new case, after

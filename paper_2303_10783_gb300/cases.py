@@ -28,7 +28,9 @@ A case is a plain ``dict``:
 ``tol_p, tol_t``        relative residual tolerances (2-norm) of the pressure
                         and transport solves
 ``max_it_p, max_it_t``  iteration caps of those solves
-``precond_p``           pressure preconditioner of the CUDA path: "mg" or "jacobi"
+``precond_p``           pressure solver of the CUDA path: "mg" (multigrid-preconditioned CG),
+                        "jacobi" (Jacobi-preconditioned CG) or "dct" (refinement around the
+                        cosine-transform inverse)
 ``steps``               number of time steps the workload runs
 
 The vertical axis is y in 2D and z in 3D; gravity points along minus that

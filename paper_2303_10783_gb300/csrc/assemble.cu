@@ -208,14 +208,19 @@ __global__ void __launch_bounds__(kBlockA) k_assemble_momentum(Params pr, Sys s,
 // false: T* (Eq. 3.12) with diffusivity k/(rho c_p) and cooled walls, whose
 // temperature is taken at the new time level *time + dt.
 // `Ag` holds A_g per cell (kept current by k_lever / k_equilibrate).
+// T* only (Tinc non-null): the solve's initial guess replaces T^n in place,
+// T^n + Tinc (the previous step's T* - T^{n-1}, or 0) when use_guess, else
+// T^n; Tinc then holds -T^n, which the lever stage completes to T* - T^n.
+// Each row reads and writes T and Tinc only at itself.
 template <bool SOLUTE>
 __global__ void __launch_bounds__(kBlockA) k_assemble_cells(Params pr, Sys s, const double* __restrict__ u,
                                                            const double* __restrict__ v,
                                                            const double* __restrict__ w,
-                                                           const double* __restrict__ phi_n,
+                                                           double* phi_n,
                                                            const double* __restrict__ gl,
                                                            const double* __restrict__ Ag,
-                                                           const double* __restrict__ time) {
+                                                           const double* __restrict__ time, double* Tinc,
+                                                           int use_guess) {
   const Axes ax = axes_of(pr);
   const double* vel[3] = {u, v, w};
   const int nx = pr.nx, ny = pr.ny;
@@ -252,7 +257,13 @@ __global__ void __launch_bounds__(kBlockA) k_assemble_cells(Params pr, Sys s, co
       nbB[a] = cb;
       nbF[a] = cf;
     }
-    double P, b = phi_n[r] * idt;
+    const double phi = phi_n[r];
+    double P, b = phi * idt;
+    if (!SOLUTE && Tinc) {
+      const double inc = Tinc[r];
+      phi_n[r] = use_guess ? phi + inc : phi;
+      Tinc[r] = -phi;
+    }
     if (SOLUTE) {
       P = idt + m0 * Ag[r];
     } else {
@@ -350,9 +361,11 @@ __device__ __forceinline__ Phase phase_of(const Params& pr, double C, double g) 
 }
 
 // The lever update closes a step: it also advances the case's time by dt.
+// Tinc (may be null): T* - T^n for the next step's initial guess when
+// form_inc (Tinc holds -T^n from this step's T* assembly), else 0.
 __global__ void __launch_bounds__(kBlockA) k_lever(Params pr, double* time, double* T, double* gl,
                                                   const double* __restrict__ C, double* Cl, double* Cs, double* Kinv,
-                                                  double* Ag, int n) {
+                                                  double* Ag, int n, double* Tinc, int form_inc) {
   if (blockIdx.x == 0 && threadIdx.x == 0) *time += pr.dt;
   const double kp = pr.kp, Tm = pr.Tm;
   const double cpL = pr.cpL, Lcp = pr.Lcp;
@@ -374,6 +387,7 @@ __global__ void __launch_bounds__(kBlockA) k_lever(Params pr, double* time, doub
       else { g = 0.0; Tn = Ts + Lcp * gn; }
     }
     const Phase ph = phase_of(pr, Cn, g);
+    if (Tinc) Tinc[r] = form_inc ? Ts + Tinc[r] : 0.0;
     T[r] = Tn;
     gl[r] = g;
     Cl[r] = ph.Cl;
@@ -623,14 +637,16 @@ cudaError_t launch_assemble_momentum(int comp, const Params& pr, const Sys& sys,
 
 cudaError_t launch_assemble_solute(const Params& pr, const Sys& sys, const double* const vel[3], const double* gl,
                                    const double* C, const double* Ag, cudaStream_t st) {
-  k_assemble_cells<true><<<grid_for(sys.d.n), kBlockA, 0, st>>>(pr, sys, vel[0], vel[1], vel[2], C, gl, Ag, nullptr);
+  k_assemble_cells<true><<<grid_for(sys.d.n), kBlockA, 0, st>>>(pr, sys, vel[0], vel[1], vel[2], const_cast<double*>(C),
+                                                                gl, Ag, nullptr, nullptr, 0);
   return cudaGetLastError();
 }
 
 cudaError_t launch_assemble_temperature(const Params& pr, const Sys& sys, const double* const vel[3],
-                                        const double* time, const double* T, cudaStream_t st) {
+                                        const double* time, double* T, double* Tinc, int use_guess,
+                                        cudaStream_t st) {
   k_assemble_cells<false><<<grid_for(sys.d.n), kBlockA, 0, st>>>(pr, sys, vel[0], vel[1], vel[2], T, nullptr,
-                                                                 nullptr, time);
+                                                                 nullptr, time, Tinc, use_guess);
   return cudaGetLastError();
 }
 
@@ -649,9 +665,9 @@ cudaError_t launch_project(const Params& pr, double* const vel[3], const double*
 }
 
 cudaError_t launch_lever(const Params& pr, double* time, double* T, double* gl, const double* C, double* Cl,
-                         double* Cs, double* Kinv, double* Ag, cudaStream_t st) {
+                         double* Cs, double* Kinv, double* Ag, double* Tinc, int form_inc, cudaStream_t st) {
   const int n = pr.nx * pr.ny * pr.nz;
-  k_lever<<<grid_for(n), kBlockA, 0, st>>>(pr, time, T, gl, C, Cl, Cs, Kinv, Ag, n);
+  k_lever<<<grid_for(n), kBlockA, 0, st>>>(pr, time, T, gl, C, Cl, Cs, Kinv, Ag, n, Tinc, form_inc);
   return cudaGetLastError();
 }
 

@@ -89,8 +89,11 @@ struct ss_case {
   size_t ws_bytes;
   double *u, *v, *w, *p, *T, *C, *gl, *Cl, *Cs, *Kinv, *Ag;
   double *ustar[3], *pc, *pb;
+  double* Tinc;              // T* - T^n of the last step (initial guess of the next T* solve), or 0
+  int tinc_pending;          // the last T* assembly left -T^n in Tinc for the lever stage
   Sys sys[SS_NSYS];
   MGPlan mg;
+  DctPlan dct;
   Scratch sc[kMaxTeams];   // Krylov scratch per team of a joint solve (set 0 for every other solve)
   DevStatus* st;
   int alloy_set;
@@ -125,7 +128,7 @@ bool grid_ok(const ss_grid* g, char* why, size_t len) {
   if (g->precision != SS_FP64 && g->precision != SS_MIXED) { snprintf(why, len, "unknown precision %d", g->precision); return false; }
   if (!(g->tol_p > 0) || !(g->tol_t > 0)) { snprintf(why, len, "tolerances must be > 0"); return false; }
   if (g->max_it_p < 1 || g->max_it_t < 1) { snprintf(why, len, "iteration caps must be >= 1"); return false; }
-  if (g->precond_p != SS_PRECOND_MG && g->precond_p != SS_PRECOND_JACOBI) {
+  if (g->precond_p != SS_PRECOND_MG && g->precond_p != SS_PRECOND_JACOBI && g->precond_p != SS_PRECOND_DCT) {
     snprintf(why, len, "unknown pressure preconditioner %d", g->precond_p);
     return false;
   }
@@ -156,6 +159,7 @@ void plan(ss_case* c, Planner& pl) {
   for (int a = 0; a < 3; ++a) c->ustar[a] = pl.vec<double>(c->n_face[a]);
   c->pc = pl.vec<double>(c->n_cell);
   c->pb = pl.vec<double>(c->n_cell);
+  c->Tinc = pl.vec<double>(c->n_cell);
   // DIA planes: one set per momentum component, so that u*, v*, w* can be
   // solved together (one launch, one team of blocks each); the C and T
   // systems reuse the u* set, each assembled right before its solve (Sec. 4
@@ -210,6 +214,14 @@ void plan(ss_case* c, Planner& pl) {
     c->cinv_n = coarse_pseudo_inverse(c->mg, c->g.dim, c->cinv_host);
     if (c->cinv_n > 0)
       c->mg.cinv = pl.raw<char>((size_t)c->cinv_n * c->cinv_n * (c->mg.fp32 ? sizeof(float) : sizeof(double)));
+  }
+  if (c->g.precond_p == SS_PRECOND_DCT) {
+    fill_params(c, nullptr);
+    plan_dct(c->pr, c->dct, mixed);
+    const size_t esz = mixed ? sizeof(float) : sizeof(double);
+    c->dct.T1 = mixed ? (void*)pl.vec<float>(c->n_cell) : (void*)pl.vec<double>(c->n_cell);
+    c->dct.T2 = mixed ? (void*)pl.vec<float>(c->n_cell) : (void*)pl.vec<double>(c->n_cell);
+    c->dct.tables = pl.raw<char>(dct_table_elems(c->dct) * esz);
   }
   // Krylov scratch: set 0 serves every solve (multigrid included); sets 1, 2
   // serve the v* and w* teams of the joint momentum solve, with only the
@@ -384,7 +396,13 @@ ss_status stage_assemble(ss_case* c, int sys) {
       break;
     }
     case SS_SYS_C: e = launch_assemble_solute(c->pr, c->sys[sys], vel, c->gl, c->C, c->Ag, c->stream); break;
-    case SS_SYS_T: e = launch_assemble_temperature(c->pr, c->sys[sys], vel, &c->st->time, c->T, c->stream); break;
+    case SS_SYS_T:
+      // the solve starts from T^n + (T* - T^{n-1}) of the previous step; a
+      // second assembly before the lever stage starts from T^n
+      e = launch_assemble_temperature(c->pr, c->sys[sys], vel, &c->st->time, c->T, c->Tinc, !c->tinc_pending,
+                                      c->stream);
+      c->tinc_pending = 1;
+      break;
     default: return fail(SS_EINVAL, "unknown system %d", sys);
   }
   if (e != cudaSuccess) return fail(SS_ECUDA, "assembly of system %d: %s", sys, cudaGetErrorString(e));
@@ -419,6 +437,8 @@ ss_status stage_solve(ss_case* c, int sys) {
     ctl.warm_start = 1;
     if (c->g.precond_p == SS_PRECOND_MG)
       e = launch_pcg_mg(c->mg, c->pr, c->pb, c->pc, ctl, c->sc[0], c->st, c->stream);
+    else if (c->g.precond_p == SS_PRECOND_DCT)
+      e = launch_poisson_dct(c->dct, c->pr, c->pb, c->pc, ctl, c->sc[0], c->st, c->stream);
     else
       e = launch_pcg_poisson(c->pr, c->pb, c->pc, ctl, c->sc[0], c->st, c->stream);
   } else if (sys >= 0 && sys < SS_NSYS) {
@@ -444,7 +464,9 @@ ss_status stage_project(ss_case* c) {
 
 ss_status stage_lever(ss_case* c) {
   StageTimer tm(c, SS_PROF_LEVER, 1);
-  cudaError_t e = launch_lever(c->pr, &c->st->time, c->T, c->gl, c->C, c->Cl, c->Cs, c->Kinv, c->Ag, c->stream);
+  cudaError_t e = launch_lever(c->pr, &c->st->time, c->T, c->gl, c->C, c->Cl, c->Cs, c->Kinv, c->Ag, c->Tinc,
+                               c->tinc_pending, c->stream);
+  c->tinc_pending = 0;
   if (e != cudaSuccess) return fail(SS_ECUDA, "lever update: %s", cudaGetErrorString(e));
   return SS_OK;
 }
@@ -599,6 +621,21 @@ ss_status ss_create_case(const ss_grid* grid, void* workspace, size_t workspace_
                         c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   }
+  if (e == cudaSuccess && c->dct.tables) {
+    // cosine matrices and eigenvalues of the transform solver, formed in FP64 on the host
+    std::vector<double> tab(dct_table_elems(c->dct));
+    dct_tables(c->dct, c->pr, tab.data());
+    std::vector<float> tab32;
+    const void* src = tab.data();
+    size_t bytes = tab.size() * sizeof(double);
+    if (c->dct.fp32) {
+      tab32.assign(tab.begin(), tab.end());
+      src = tab32.data();
+      bytes = tab32.size() * sizeof(float);
+    }
+    e = cudaMemcpyAsync(c->dct.tables, src, bytes, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  }
   if (e != cudaSuccess) {
     delete c->pool;
     delete c->pending;
@@ -625,6 +662,8 @@ ss_status ss_set_alloy(ss_case* c, const ss_alloy* al) {
   CUDA_TRY(cudaMemsetAsync(c->v, 0, nf[1] * sizeof(double), c->stream));
   CUDA_TRY(cudaMemsetAsync(c->w, 0, nf[2] * sizeof(double), c->stream));
   CUDA_TRY(cudaMemsetAsync(c->p, 0, c->n_cell * sizeof(double), c->stream));
+  CUDA_TRY(cudaMemsetAsync(c->Tinc, 0, c->n_cell * sizeof(double), c->stream));
+  c->tinc_pending = 0;
   k_fill<<<256, 256, 0, c->stream>>>(c->T, al->Tref, c->n_cell);
   k_fill<<<256, 256, 0, c->stream>>>(c->C, al->C0, c->n_cell);
   CUDA_TRY(cudaGetLastError());
@@ -730,6 +769,9 @@ ss_status ss_set_fields(ss_case* c, unsigned mask, const void* const* src, int s
   // a new state clears the pressure solve's warm start, so the next step
   // depends on the state alone (as in a new case)
   CUDA_TRY(cudaMemsetAsync(c->pc, 0, c->n_cell * sizeof(double), c->stream));
+  // and the T* initial guess's increment, for the same reason
+  CUDA_TRY(cudaMemsetAsync(c->Tinc, 0, c->n_cell * sizeof(double), c->stream));
+  c->tinc_pending = 0;
   if ((mask & (1u << SS_GL)) && c->alloy_set) {
     // keep K^{-1} and A_g consistent with the new g_l; C_l and C_s stay as they are
     cudaError_t e = launch_equilibrate(c->pr, c->T, c->C, c->gl, c->Cl, c->Cs, c->Kinv, c->Ag, 0, 0, c->stream);

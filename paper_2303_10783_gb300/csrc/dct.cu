@@ -1,0 +1,549 @@
+// Pressure-correction solve (Eq. 3.4) by cosine transforms.
+//
+// The operator of Eq. 3.4 is the Laplacian with constant coefficients per
+// axis and zero-flux walls on a box of cells (the term-wise strategy of
+// Sec. 4 keeps it fixed for the whole run). Such an operator is diagonalised
+// by the orthonormal DCT-II basis along each axis: along an axis of n cells
+// and spacing h, the 1D operator (-p_{i-1} + 2 p_i - p_{i+1})/h^2, with the
+// missing neighbour dropped at a wall, has the eigenvectors
+// v_k(i) = s_k cos(pi k (i + 1/2) / n) and the eigenvalues
+// lambda_k = (4/h^2) sin^2(pi k / (2n)). So A = -L is inverted exactly by
+//   transform along x and y (3D) or x (2D),
+//   for every transformed column, a tridiagonal solve along the last axis
+//     (T_t + (lambda_x + lambda_y) I) p = f  (Thomas algorithm; the one
+//     column with lambda_x + lambda_y = 0 is the Neumann null space: its last
+//     unknown is pinned to 0, then its mean is removed),
+//   transform back.
+// The transforms are dense products with the n x n cosine matrices: GEMMs,
+// computed by tiles in shared memory. Their cost is arithmetic, not
+// synchronisation: one application has three passes and two grid barriers.
+//
+// The solve is FP64 iterative refinement around that inverse: each sweep
+// forms the FP64 residual r = b - A x (and its norm), applies the inverse in
+// the precision TP of the transforms, and adds the correction to x. TP =
+// float on the mixed path (the inverse is then exact to FP32 rounding, and a
+// sweep reduces the residual by 1e-4 to 1e-7), TP = double on the FP64 path.
+// The stopping test is the same as the other pressure solvers': the FP64
+// residual (its part outside the constants) below tol * |b|.
+//
+// Data flow of one application (Mx, My, Mt: cells along the transform axes x
+// and y and along the tridiagonal axis; My = 1 in 2D; R = My * Mt lines
+// along x; a line's index is row = j + My * t):
+//   pass A   T1[kx][row] = sum_i Cx[kx][i] r[i + Mx row]          (tiles over kx, row)
+//   pass B   per kx: T2[kx][t][ky] = sum_j Cy[ky][j] T1[kx][j + My t];
+//            tridiagonal solves along t for every ky (in shared memory);
+//            T1[kx][j + My t] = sum_ky Cy[ky][j] T2[kx][t][ky]   (one block per kx)
+//            (2D: the tridiagonal solves run on T1 directly)
+//   pass C   d[i + Mx row] = sum_kx Cx[kx][i] T1[kx][row]; x += |r| d
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "solid_internal.cuh"
+
+namespace solid {
+namespace {
+
+// GEMM tile: BM x BN outputs per block, K in chunks of BK; each of the 512
+// threads owns 4 x 4 outputs. Shared-memory rows are padded by 4 elements
+// (fewer bank conflicts on the transposing stores, 16-byte aligned rows).
+constexpr int BM = 64, BN = 128, BK = 16;
+constexpr int AS = BM + 4, BS = BN + 4;
+constexpr int kGemmSmemElems = 2 * BK * AS + 2 * BK * BS;
+static_assert(kBlock == 512, "the GEMM tile assumes 512 threads");
+constexpr int kMaxSweeps = 20;
+// shared memory for the tridiagonal solves of one chunk of columns
+constexpr size_t kThomasSmemBytes = 96 * 1024;
+
+template <typename TP>
+struct DctArgs {
+  int Mx, My, Mt, R, dim;
+  int nx, ny, nz, n;
+  FastDiv fx, fy;
+  double cx, cy, cz;        // FP64 1/h^2 per axis (the residual's stencil)
+  TP at;                    // 1/h^2 along the tridiagonal axis
+  const TP* Cx;             // [Mx][Mx] cosine matrix (row k: mode k)
+  const TP* Cy;             // [My][My]
+  const TP* lx;             // [Mx] eigenvalues along x
+  const TP* ly;             // [My] eigenvalues along y
+  TP* T1;                   // [Mx][R]
+  TP* T2;                   // [Mx][Mt][My]
+  double* b;                // right-hand side (mean removed in place)
+  double* x;                // solution
+  double* r;                // FP64 residual
+  double tol;
+  int max_sweeps;
+  int stat_index;
+  int thomas_cols;          // columns per shared-memory chunk of the tridiagonal solves
+  double* partial;
+  int max_blocks;
+  DevStatus* st;
+};
+
+template <typename T>
+__device__ __forceinline__ void lds4(const T* p, T v[4]);
+template <>
+__device__ __forceinline__ void lds4<float>(const float* p, float v[4]) {
+  const float4 q = *reinterpret_cast<const float4*>(p);
+  v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+}
+template <>
+__device__ __forceinline__ void lds4<double>(const double* p, double v[4]) {
+  const double2 a = *reinterpret_cast<const double2*>(p), b = *reinterpret_cast<const double2*>(p + 2);
+  v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+
+// One BM x BN tile of C(m, n) = sum_k A(m, k) B(k, n), m in [m0, m0+BM) and
+// n in [n0, n0+BN), entries beyond M, N, K taken as 0. la(m, k) and lb(k, n)
+// load one operand element; st(m, n, v) stores one result. *_k_fast say
+// whether consecutive k are adjacent in memory (else consecutive m or n),
+// and out_m_fast whether consecutive m of the result are: the thread
+// mappings of the loads and of the outputs follow, so that neighbouring
+// threads touch neighbouring addresses. Chunk k+1 is fetched into registers
+// while chunk k is multiplied (two shared-memory buffers).
+template <typename TP, class LA, class LB, class ST>
+__device__ __forceinline__ void gemm_tile(int M, int N, int K, int m0, int n0, LA la, bool a_k_fast, LB lb,
+                                          bool b_k_fast, ST st, bool out_m_fast, TP* sm) {
+  TP* As = sm;                   // [2][BK][AS]
+  TP* Bs = sm + 2 * BK * AS;     // [2][BK][BS]
+  const int tid = threadIdx.x;
+  const int tm = out_m_fast ? (tid & 15) : (tid >> 5);
+  const int tn = out_m_fast ? (tid >> 4) : (tid & 31);
+  TP acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = TP(0);
+  TP ra[2], rb[4];
+  auto fetch = [&](int k0) {
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int e = tid + q * kBlock;
+      const int m = a_k_fast ? (e >> 4) : (e & (BM - 1));
+      const int k = a_k_fast ? (e & (BK - 1)) : (e >> 6);
+      const int gm = m0 + m, gk = k0 + k;
+      ra[q] = (gm < M && gk < K) ? la(gm, gk) : TP(0);
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int e = tid + q * kBlock;
+      const int n = b_k_fast ? (e >> 4) : (e & (BN - 1));
+      const int k = b_k_fast ? (e & (BK - 1)) : (e >> 7);
+      const int gn = n0 + n, gk = k0 + k;
+      rb[q] = (gn < N && gk < K) ? lb(gk, gn) : TP(0);
+    }
+  };
+  auto stash = [&](int buf) {
+    TP* as = As + buf * BK * AS;
+    TP* bs = Bs + buf * BK * BS;
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int e = tid + q * kBlock;
+      const int m = a_k_fast ? (e >> 4) : (e & (BM - 1));
+      const int k = a_k_fast ? (e & (BK - 1)) : (e >> 6);
+      as[k * AS + m] = ra[q];
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int e = tid + q * kBlock;
+      const int n = b_k_fast ? (e >> 4) : (e & (BN - 1));
+      const int k = b_k_fast ? (e & (BK - 1)) : (e >> 7);
+      bs[k * BS + n] = rb[q];
+    }
+  };
+  fetch(0);
+  stash(0);
+  __syncthreads();
+  const int nk = (K + BK - 1) / BK;
+  for (int c = 0; c < nk; ++c) {
+    const int buf = c & 1;
+    if (c + 1 < nk) fetch((c + 1) * BK);
+    const TP* as = As + buf * BK * AS + tm * 4;
+    const TP* bs = Bs + buf * BK * BS + tn * 4;
+#pragma unroll
+    for (int k = 0; k < BK; ++k) {
+      TP a[4], bv[4];
+      lds4(as + k * AS, a);
+      lds4(bs + k * BS, bv);
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], bv[j], acc[i][j]);
+    }
+    if (c + 1 < nk) stash(buf ^ 1);
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int gm = m0 + tm * 4 + i;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int gn = n0 + tn * 4 + j;
+      if (gm < M && gn < N) st(gm, gn, acc[i][j]);
+    }
+  }
+}
+
+// Tridiagonal solves along t for the columns [c0, c0 + w) of one group:
+// column c's entry t is at buf[t * st + c * sc], its shift is sig(c) and it
+// is the singular (null-space) column when sing(c). Staged in shared memory:
+// values ys[c][t] and the eliminated super-diagonal cs[c][t], rows of odd
+// length P (conflict-free column walks).
+template <typename TP, class SIG, class SING>
+__device__ void thomas_chunk(TP* buf, long long st, long long sc, int Mt, int c0, int w, TP at, SIG sig, SING sing,
+                             TP* sm) {
+  const int P = (Mt & 1) ? Mt : Mt + 1;
+  TP* ys = sm;
+  TP* cs = sm + (size_t)w * P;
+  const int tot = w * Mt;
+  const bool t_fast = (st == 1);
+  for (int e = threadIdx.x; e < tot; e += blockDim.x) {
+    const int t = t_fast ? e % Mt : e / w;
+    const int c = t_fast ? e / Mt : e % w;
+    ys[c * P + t] = buf[(long long)t * st + (long long)(c0 + c) * sc];
+  }
+  __syncthreads();
+  for (int c = threadIdx.x; c < w; c += blockDim.x) {
+    TP* y = ys + c * P;
+    TP* cp = cs + c * P;
+    const TP s = sig(c0 + c);
+    const bool singular = sing(c0 + c);
+    // the singular column solves its first Mt - 1 rows with the last unknown
+    // pinned to 0 (the system is consistent: its right-hand side sums to 0)
+    const int m = singular ? Mt - 1 : Mt;
+    if (m <= 0) {
+      y[0] = TP(0);
+    } else {
+      TP prev_c = TP(0), prev_y = TP(0);
+      for (int t = 0; t < m; ++t) {
+        const TP nb = TP((t > 0) + (t < Mt - 1));
+        const TP d = fma(at, prev_c, fma(at, nb, s));   // a nb + s + a c'_{t-1} (c' <= 0)
+        const TP inv = TP(1) / d;
+        prev_y = fma(at, prev_y, y[t]) * inv;
+        prev_c = -at * inv;
+        y[t] = prev_y;
+        cp[t] = prev_c;
+      }
+      TP next = TP(0);
+      if (singular) y[Mt - 1] = TP(0);
+      for (int t = m - 1; t >= 0; --t) {
+        next = y[t] - cp[t] * next;
+        y[t] = next;
+      }
+      if (singular) {
+        TP sum = TP(0);
+        for (int t = 0; t < Mt; ++t) sum += y[t];
+        const TP mean = sum / TP(Mt);
+        for (int t = 0; t < Mt; ++t) y[t] -= mean;
+      }
+    }
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < tot; e += blockDim.x) {
+    const int t = t_fast ? e % Mt : e / w;
+    const int c = t_fast ? e / Mt : e % w;
+    buf[(long long)t * st + (long long)(c0 + c) * sc] = ys[c * P + t];
+  }
+  __syncthreads();
+}
+
+// (A v)_c, A = -L with zero-flux walls (FP64, the refinement residual)
+__device__ __forceinline__ double lap64(const double* v, int c, int i, int j, int k, int nx, int ny, int nz,
+                                        double ax, double ay, double az, double diag) {
+  const int sy = nx, sz = nx * ny;
+  double acc = diag * v[c];
+  acc = fma(-ax, (i > 0 ? v[c - 1] : 0.0) + (i < nx - 1 ? v[c + 1] : 0.0), acc);
+  acc = fma(-ay, (j > 0 ? v[c - sy] : 0.0) + (j < ny - 1 ? v[c + sy] : 0.0), acc);
+  if (nz > 1) acc = fma(-az, (k > 0 ? v[c - sz] : 0.0) + (k < nz - 1 ? v[c + sz] : 0.0), acc);
+  return acc;
+}
+
+// Pass A: T1 = (Cx ⊗ I) ((src - shift) * scale)
+template <typename TP>
+__device__ void pass_a(const DctArgs<TP>& A, const double* src, double shift, double scale, TP* sm) {
+  const int Mx = A.Mx, R = A.R;
+  const int mt = (Mx + BM - 1) / BM, nt = (R + BN - 1) / BN;
+  const TP* Cx = A.Cx;
+  TP* T1 = A.T1;
+  for (int tile = blockIdx.x; tile < mt * nt; tile += gridDim.x) {
+    const int m0 = (tile % mt) * BM, n0 = (tile / mt) * BN;
+    gemm_tile<TP>(
+        Mx, R, Mx, m0, n0, [&](int m, int k) { return Cx[(size_t)m * Mx + k]; }, true,
+        [&](int k, int n) { return (TP)((src[(size_t)n * Mx + k] - shift) * scale); }, true,
+        [&](int m, int n, TP v) { T1[(size_t)m * R + n] = v; }, false, sm);
+  }
+}
+
+// Pass B: per mode kx, the transform along y, the tridiagonal solves along t
+// and the inverse transform along y (3D); in 2D only the tridiagonal solves.
+template <typename TP>
+__device__ void pass_b(const DctArgs<TP>& A, TP* sm) {
+  const int Mx = A.Mx, My = A.My, Mt = A.Mt, R = A.R;
+  const TP* lx = A.lx;
+  const TP* ly = A.ly;
+  const TP* Cy = A.Cy;
+  const TP at = A.at;
+  const int w = A.thomas_cols;
+  if (A.dim == 2) {
+    // columns are the modes kx, each a contiguous line of Mt values in T1
+    for (int c0 = blockIdx.x * w; c0 < Mx; c0 += gridDim.x * w) {
+      const int cw = (Mx - c0 < w) ? Mx - c0 : w;
+      thomas_chunk<TP>(
+          A.T1, 1, R, Mt, c0, cw, at, [&](int c) { return lx[c]; }, [&](int c) { return c == 0; }, sm);
+    }
+    return;
+  }
+  const int mt = (My + BM - 1) / BM, nt = (Mt + BN - 1) / BN;
+  for (int kx = blockIdx.x; kx < Mx; kx += gridDim.x) {
+    TP* S1 = A.T1 + (size_t)kx * R;   // [t][j]
+    TP* S2 = A.T2 + (size_t)kx * R;   // [t][ky]
+    for (int tile = 0; tile < mt * nt; ++tile) {
+      const int m0 = (tile % mt) * BM, n0 = (tile / mt) * BN;
+      gemm_tile<TP>(
+          My, Mt, My, m0, n0, [&](int m, int k) { return Cy[(size_t)m * My + k]; }, true,
+          [&](int k, int n) { return S1[(size_t)n * My + k]; }, true,
+          [&](int m, int n, TP v) { S2[(size_t)n * My + m] = v; }, true, sm);
+    }
+    __syncthreads();
+    const TP sx = lx[kx];
+    for (int c0 = 0; c0 < My; c0 += w) {
+      const int cw = (My - c0 < w) ? My - c0 : w;
+      thomas_chunk<TP>(
+          S2, My, 1, Mt, c0, cw, at, [&](int c) { return sx + ly[c]; }, [&](int c) { return kx == 0 && c == 0; },
+          sm);
+    }
+    for (int tile = 0; tile < mt * nt; ++tile) {
+      const int m0 = (tile % mt) * BM, n0 = (tile / mt) * BN;
+      gemm_tile<TP>(
+          My, Mt, My, m0, n0, [&](int m, int k) { return Cy[(size_t)k * My + m]; }, false,
+          [&](int k, int n) { return S2[(size_t)n * My + k]; }, true,
+          [&](int m, int n, TP v) { S1[(size_t)n * My + m] = v; }, true, sm);
+    }
+    __syncthreads();
+  }
+}
+
+// Pass C: x += rn * (Cx^T ⊗ I) T1
+template <typename TP>
+__device__ void pass_c(const DctArgs<TP>& A, double rn, TP* sm) {
+  const int Mx = A.Mx, R = A.R;
+  const int mt = (Mx + BM - 1) / BM, nt = (R + BN - 1) / BN;
+  const TP* Cx = A.Cx;
+  const TP* T1 = A.T1;
+  double* x = A.x;
+  for (int tile = blockIdx.x; tile < mt * nt; tile += gridDim.x) {
+    const int m0 = (tile % mt) * BM, n0 = (tile / mt) * BN;
+    gemm_tile<TP>(
+        Mx, R, Mx, m0, n0, [&](int m, int k) { return Cx[(size_t)k * Mx + m]; }, false,
+        [&](int k, int n) { return T1[(size_t)k * R + n]; }, false,
+        [&](int m, int n, TP v) {
+          const size_t c = (size_t)n * Mx + m;
+          x[c] = fma(rn, (double)v, x[c]);
+        },
+        true, sm);
+  }
+}
+
+template <typename TP>
+__global__ void __launch_bounds__(kBlock, 1) k_poisson_dct(DctArgs<TP> A) {
+  extern __shared__ __align__(16) unsigned char dsm[];
+  TP* sm = reinterpret_cast<TP*>(dsm);
+  __shared__ double s_diag[27];
+  if (threadIdx.x < 27) {
+    const int c = threadIdx.x;
+    s_diag[c] = (c % 3) * A.cx + ((c / 3) % 3) * A.cy + (c / 9) * A.cz;
+  }
+  __syncthreads();
+  unsigned int epoch = 0;
+  const int n = A.n;
+  const int t0 = blockIdx.x * blockDim.x + threadIdx.x, gsz = gridDim.x * blockDim.x;
+  double* b = A.b;
+  double* x = A.x;
+  double* r = A.r;
+  __shared__ struct {
+    double mean, bn, rn, rmean, inv;
+    int go, conv;
+  } ds;
+  double thr = 0.0;   // read by thread 0 only
+  // consistency: remove the mean of the right-hand side (Neumann null space)
+  Vec<1> sb = {{0.0}};
+  for (int c = t0; c < n; c += gsz) sb.v[0] += b[c];
+  if (!grid_sum_post<1>(sb, A.partial, A.max_blocks, 0, A.st, epoch,
+                        [&](const double* tot) { ds.mean = tot[0] / (double)n; }))
+    return;
+  const double mean_b = ds.mean;
+  Vec<1> s2 = {{0.0}};
+  for (int c = t0; c < n; c += gsz) {
+    const double bc = b[c] - mean_b;
+    b[c] = bc;
+    x[c] = 0.0;
+    s2.v[0] += bc * bc;
+  }
+  if (!grid_sum_post<1>(s2, A.partial, A.max_blocks, 1, A.st, epoch, [&](const double* tot) {
+        ds.bn = sqrt(tot[0]);
+        ds.rn = ds.bn;
+        ds.rmean = 0.0;
+        ds.inv = 1.0 / ds.bn;
+        thr = A.tol * ds.bn;
+        ds.conv = ds.bn == 0.0;
+        ds.go = ds.bn > 0.0 && isfinite(ds.bn);
+      }))
+    return;
+  int sweeps = 0;
+  const double* src = b;   // x = 0: the first residual is b itself
+  while (ds.go && sweeps < A.max_sweeps) {
+    ++sweeps;
+    const double shift = ds.rmean, scale = ds.inv, rn = ds.rn;
+    pass_a<TP>(A, src, shift, scale, sm);
+    if (!grid_barrier(A.st, gridDim.x, epoch)) return;
+    pass_b<TP>(A, sm);
+    if (!grid_barrier(A.st, gridDim.x, epoch)) return;
+    pass_c<TP>(A, rn, sm);
+    if (!grid_barrier(A.st, gridDim.x, epoch)) return;
+    Vec<2> s = {{0.0, 0.0}};
+    for (int c = t0; c < n; c += gsz) {
+      int i, j, k;
+      decompose3(c, A.fx, A.fy, i, j, k);
+      const int code = ((i > 0) + (i < A.nx - 1)) + 3 * ((j > 0) + (j < A.ny - 1)) + 9 * ((k > 0) + (k < A.nz - 1));
+      const double rc = b[c] - lap64(x, c, i, j, k, A.nx, A.ny, A.nz, A.cx, A.cy, A.cz, s_diag[code]);
+      r[c] = rc;
+      s.v[0] += rc;
+      s.v[1] += rc * rc;
+    }
+    if (!grid_sum_post<2>(s, A.partial, A.max_blocks, 2, A.st, epoch, [&](const double* tot) {
+          // norm of the part of r outside the constants: sum (r - mean)^2
+          const double rmean = tot[0] / (double)n;
+          const double rn_new = sqrt(fmax(tot[1] - (double)n * rmean * rmean, 0.0));
+          ds.conv = rn_new <= thr;
+          // stop when a sweep no longer halves the residual (rounding floor)
+          ds.go = !ds.conv && isfinite(rn_new) && rn_new < 0.5 * ds.rn;
+          ds.rn = rn_new;
+          ds.rmean = rmean;
+          ds.inv = 1.0 / rn_new;
+        }))
+      return;
+    src = r;
+  }
+  // gauge: zero-mean correction
+  Vec<1> sx = {{0.0}};
+  for (int c = t0; c < n; c += gsz) sx.v[0] += x[c];
+  if (!grid_sum_post<1>(sx, A.partial, A.max_blocks, 3, A.st, epoch,
+                        [&](const double* tot) { ds.mean = tot[0] / (double)n; }))
+    return;
+  const double mean_x = ds.mean;
+  for (int c = t0; c < n; c += gsz) x[c] -= mean_x;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    const double rel = ds.bn > 0.0 ? ds.rn / ds.bn : 0.0;
+    SolveStat& so = A.st->stat[A.stat_index];
+    so.iters = sweeps;
+    so.iters_total += sweeps;
+    so.refinements = sweeps;
+    so.converged = ds.conv ? 1 : 0;
+    so.nonfinite = isfinite(rel) ? 0 : 1;
+    so.relres = rel;
+    if (!isfinite(rel)) atomicExch(&A.st->sticky, (int)SS_ENAN);
+    else if (!ds.conv) atomicCAS(&A.st->sticky, (int)SS_OK, (int)SS_ENOTCONV);
+  }
+}
+
+template <typename TP>
+size_t smem_bytes(const DctPlan& pl, int* cols) {
+  const int P = (pl.Mt & 1) ? pl.Mt : pl.Mt + 1;
+  const int ncols = pl.dim == 3 ? pl.My : pl.Mx;
+  long long w = (long long)(kThomasSmemBytes / (2 * (size_t)P * sizeof(TP)));
+  if (w > ncols) w = ncols;
+  if (w > 4 * kBlock) w = 4 * kBlock;
+  if (w < 1) w = 1;
+  *cols = (int)w;
+  const size_t thomas = 2 * (size_t)w * P * sizeof(TP);
+  const size_t gemm = (size_t)kGemmSmemElems * sizeof(TP);
+  return thomas > gemm ? thomas : gemm;
+}
+
+template <typename TP>
+cudaError_t launch_t(const DctPlan& pl, const Params& pr, double* b, double* x, const SolverCtl& ctl, Scratch& sc,
+                     DevStatus* st, cudaStream_t s) {
+  DctArgs<TP> A;
+  memset(&A, 0, sizeof A);
+  A.Mx = pl.Mx; A.My = pl.My; A.Mt = pl.Mt; A.R = pl.My * pl.Mt; A.dim = pl.dim;
+  A.nx = pr.nx; A.ny = pr.ny; A.nz = pr.nz; A.n = pr.nx * pr.ny * pr.nz;
+  A.fx = make_fastdiv(pr.nx);
+  A.fy = make_fastdiv(pr.ny);
+  A.cx = 1.0 / (pr.hx * pr.hx);
+  A.cy = 1.0 / (pr.hy * pr.hy);
+  A.cz = pr.dim == 3 ? 1.0 / (pr.hz * pr.hz) : 0.0;
+  const double ht = pr.dim == 3 ? pr.hz : pr.hy;
+  A.at = (TP)(1.0 / (ht * ht));
+  const TP* tab = (const TP*)pl.tables;
+  A.Cx = tab;
+  A.Cy = tab + (size_t)pl.Mx * pl.Mx;
+  A.lx = A.Cy + (size_t)pl.My * pl.My;
+  A.ly = A.lx + pl.Mx;
+  A.T1 = (TP*)pl.T1;
+  A.T2 = (TP*)pl.T2;
+  A.b = b; A.x = x; A.r = sc.v[0];
+  A.tol = ctl.tol;
+  A.max_sweeps = ctl.max_it < kMaxSweeps ? ctl.max_it : kMaxSweeps;
+  A.stat_index = ctl.stat_index;
+  A.partial = sc.partial;
+  A.max_blocks = sc.max_blocks;
+  A.st = st;
+  const size_t smem = smem_bytes<TP>(pl, &A.thomas_cols);
+  const void* kern = (const void*)k_poisson_dct<TP>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int cap = ctl.block_cap > 0 && ctl.block_cap < sc.max_blocks ? ctl.block_cap : sc.max_blocks;
+  const int nb = coop_blocks_for_smem(kern, 1LL << 40, cap, smem);
+  if ((e = cudaMemsetAsync(&st->barrier, 0, sizeof(unsigned int), s)) != cudaSuccess) return e;
+  void* args[] = {&A};
+  return cudaLaunchCooperativeKernel(kern, dim3(nb), dim3(kBlock), args, smem, s);
+}
+
+}  // namespace
+
+void plan_dct(const Params& pr, DctPlan& pl, int fp32) {
+  memset(&pl, 0, sizeof pl);
+  pl.dim = pr.dim;
+  pl.Mx = pr.nx;
+  pl.My = pr.dim == 3 ? pr.ny : 1;
+  pl.Mt = pr.dim == 3 ? pr.nz : pr.ny;
+  pl.fp32 = fp32;
+}
+
+size_t dct_table_elems(const DctPlan& pl) {
+  return (size_t)pl.Mx * pl.Mx + (size_t)pl.My * pl.My + pl.Mx + pl.My;
+}
+
+// Orthonormal DCT-II matrices and the eigenvalues of the 1D operators, in
+// FP64 on the host: C[k][i] = s_k cos(pi k (2i + 1) / (2n)), s_0 = sqrt(1/n),
+// s_k = sqrt(2/n); lambda_k = (4/h^2) sin^2(pi k / (2n)).
+void dct_tables(const DctPlan& pl, const Params& pr, double* out) {
+  const double pi = 3.14159265358979323846;
+  auto fill = [&](int nn, double h, double* C, double* lam) {
+    for (int k = 0; k < nn; ++k) {
+      const double s = std::sqrt((k == 0 ? 1.0 : 2.0) / nn);
+      for (int i = 0; i < nn; ++i) C[(size_t)k * nn + i] = s * std::cos(pi * k * (2.0 * i + 1.0) / (2.0 * nn));
+      const double sn = std::sin(pi * k / (2.0 * nn));
+      lam[k] = 4.0 * sn * sn / (h * h);
+    }
+  };
+  double* Cx = out;
+  double* Cy = Cx + (size_t)pl.Mx * pl.Mx;
+  double* lx = Cy + (size_t)pl.My * pl.My;
+  double* ly = lx + pl.Mx;
+  fill(pl.Mx, pr.hx, Cx, lx);
+  if (pl.dim == 3) {
+    fill(pl.My, pr.hy, Cy, ly);
+  } else {
+    Cy[0] = 1.0;
+    ly[0] = 0.0;
+  }
+}
+
+cudaError_t launch_poisson_dct(const DctPlan& pl, const Params& pr, double* b, double* x, const SolverCtl& ctl,
+                               Scratch& sc, DevStatus* st, cudaStream_t s) {
+  if (pl.fp32) return launch_t<float>(pl, pr, b, x, ctl, sc, st, s);
+  return launch_t<double>(pl, pr, b, x, ctl, sc, st, s);
+}
+
+}  // namespace solid

@@ -372,14 +372,18 @@ cudaError_t launch_assemble_momentum(int comp, const Params& pr, const Sys& sys,
                                      const double* Kinv, cudaStream_t s);
 cudaError_t launch_assemble_solute(const Params& pr, const Sys& sys, const double* const vel[3], const double* gl,
                                    const double* C, const double* Ag, cudaStream_t s);
+// T is replaced in place by the solve's initial guess (T + Tinc when
+// use_guess, else T) and Tinc by -T (see k_assemble_cells).
 cudaError_t launch_assemble_temperature(const Params& pr, const Sys& sys, const double* const vel[3],
-                                        const double* time, const double* T, cudaStream_t s);
+                                        const double* time, double* T, double* Tinc, int use_guess,
+                                        cudaStream_t s);
 cudaError_t launch_poisson_rhs(const Params& pr, const double* const ustar[3], double* b, cudaStream_t s);
 cudaError_t launch_project(const Params& pr, double* const vel[3], const double* const ustar[3], const double* pc,
                            double* p, cudaStream_t s);
-// `time` is advanced by dt (the lever update closes a step).
+// `time` is advanced by dt (the lever update closes a step); Tinc becomes
+// T* - T^n when form_inc, else 0.
 cudaError_t launch_lever(const Params& pr, double* time, double* T, double* gl, const double* C, double* Cl,
-                         double* Cs, double* Kinv, double* Ag, cudaStream_t s);
+                         double* Cs, double* Kinv, double* Ag, double* Tinc, int form_inc, cudaStream_t s);
 // from_T: recompute g_l from (T, C) in equilibrium; write_cl: recompute C_l, C_s.
 // K^{-1} and A_g are always refreshed from g_l.
 // Forward (residual-probing) assembly of system sys into its planes (validation mode).
@@ -440,5 +444,22 @@ void plan_multigrid(const Params& pr, MGPlan& pl, int fp32);
 int coarse_pseudo_inverse(const MGPlan& pl, int dim, double* out);
 cudaError_t launch_pcg_mg(const MGPlan& pl, const Params& pr, double* b, double* x, const SolverCtl& ctl,
                           Scratch& sc, DevStatus* st, cudaStream_t s);
+
+// dct.cu: the pressure correction by cosine transforms along x (and y in 3D)
+// and tridiagonal solves along the last axis, inside FP64 refinement
+struct DctPlan {
+  int dim;
+  int Mx, My, Mt;        // cells along x, along y (1 in 2D) and along the tridiagonal axis
+  int fp32;              // transforms in FP32 (mixed cases) or FP64
+  void* T1;              // work arrays of Mx*My*Mt elements (float or double)
+  void* T2;
+  void* tables;          // cosine matrices Cx [Mx][Mx], Cy [My][My], eigenvalues lx [Mx], ly [My]
+};
+void plan_dct(const Params& pr, DctPlan& pl, int fp32);
+size_t dct_table_elems(const DctPlan& pl);
+// the tables in FP64, packed as above, into out[dct_table_elems]
+void dct_tables(const DctPlan& pl, const Params& pr, double* out);
+cudaError_t launch_poisson_dct(const DctPlan& pl, const Params& pr, double* b, double* x, const SolverCtl& ctl,
+                               Scratch& sc, DevStatus* st, cudaStream_t s);
 
 }  // namespace solid

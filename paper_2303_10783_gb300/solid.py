@@ -17,7 +17,7 @@ SS_OK, SS_EINVAL, SS_ENOMEM, SS_ENOTCONV, SS_ENAN, SS_ECUDA, SS_ESTATE, SS_ETIME
 STATUS_NAMES = {0: "SS_OK", 1: "SS_EINVAL", 2: "SS_ENOMEM", 3: "SS_ENOTCONV", 4: "SS_ENAN", 5: "SS_ECUDA",
                 6: "SS_ESTATE", 7: "SS_ETIMEOUT"}
 SS_FP64, SS_MIXED = 0, 1
-SS_PRECOND_MG, SS_PRECOND_JACOBI = 0, 1
+SS_PRECOND_MG, SS_PRECOND_JACOBI, SS_PRECOND_DCT = 0, 1, 2
 SS_ADIABATIC, SS_ROBIN, SS_DIRICHLET = 0, 1, 2
 SS_NOSLIP, SS_FREESLIP = 0, 1
 FIELDS = ("u", "v", "w", "p", "T", "C", "gl", "Cl", "Cs")
@@ -131,7 +131,8 @@ def grid_struct(case, precision=SS_FP64):
     return Grid(case["dim"], case["nx"], case["ny"], case["nz"] if case["dim"] == 3 else 1,
                 case["lx"], case["ly"], case["lz"], case["dt"], precision,
                 case["tol_p"], case["tol_t"], case["max_it_p"], case["max_it_t"],
-                {"mg": SS_PRECOND_MG, "jacobi": SS_PRECOND_JACOBI}[case.get("precond_p", "mg")])
+                {"mg": SS_PRECOND_MG, "jacobi": SS_PRECOND_JACOBI,
+                 "dct": SS_PRECOND_DCT}[case.get("precond_p", "mg")])
 
 
 def alloy_struct(case):

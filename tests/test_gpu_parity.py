@@ -32,6 +32,10 @@ def _tight(case):
     case["tol_t"] = 1e-14
     case["max_it_p"] = 50000
     case["max_it_t"] = 5000
+    if case.get("precond_p") == "dct":
+        # the transform solver tests the true FP64 residual of its refinement,
+        # whose rounding floor can sit above 1e-14 (a CG tests its recursive one)
+        case["tol_p"] = 1e-13
     return case
 
 
@@ -41,7 +45,7 @@ SMALL = CASES_2D + CASES_3D
 # sizes whose multigrid hierarchy has several levels (the ragged ones above have one)
 MULTILEVEL = [cases.cavity_2d(64, 40, robin={"x-": (400.0, 298.0), "y+": (60.0, 300.0)}),
               cases.box_3d(32, 24, 16, robin={"x-": (400.0, 298.0), "z+": (60.0, 300.0)})]
-SOLVE_CASES = [(c, prec, pre) for c in SMALL + MULTILEVEL for prec in ("fp64", "mixed") for pre in ("mg", "jacobi")]
+SOLVE_CASES = [(c, prec, pre) for c in SMALL + MULTILEVEL for prec in ("fp64", "mixed") for pre in ("mg", "jacobi", "dct")]
 SOLVE_IDS = ["%s-%dx%dx%d-%s-%s" % ("2d" if c["dim"] == 2 else "3d", c["nx"], c["ny"], c["nz"], prec, pre)
              for c, prec, pre in SOLVE_CASES]
 PREC = {"fp64": solid.SS_FP64, "mixed": solid.SS_MIXED}
@@ -174,17 +178,22 @@ def _run_pair(case, nsteps, T0shift=-0.8, precision=solid.SS_FP64):
     return gpu, st, stats
 
 
-STEP_CASES = [(cases.cavity_2d(), "fp64"), (cases.box_3d(19, 13, 11), "fp64"), (cases.box_3d(24, 16, 12), "fp64"),
-              (cases.cavity_2d(), "mixed"), (cases.box_3d(24, 16, 12), "mixed")]
+STEP_CASES = [(cases.cavity_2d(), "fp64", "mg"), (cases.box_3d(19, 13, 11), "fp64", "mg"),
+              (cases.box_3d(24, 16, 12), "fp64", "mg"), (cases.cavity_2d(), "mixed", "mg"),
+              (cases.box_3d(24, 16, 12), "mixed", "mg"),
+              (cases.cavity_2d(), "fp64", "dct"), (cases.box_3d(19, 13, 11), "fp64", "dct"),
+              (cases.cavity_2d(), "mixed", "dct"), (cases.box_3d(24, 16, 12), "mixed", "dct"),
+              (cases.box_3d(19, 13, 11), "mixed", "dct")]
 
 
-@pytest.mark.parametrize("case,prec", STEP_CASES,
-                         ids=["2d-50x30-fp64", "3d-19x13x11-fp64", "3d-24x16x12-fp64", "2d-50x30-mixed",
-                              "3d-24x16x12-mixed"])
-def test_step_parity_100_steps(lib, case, prec):
+@pytest.mark.parametrize("case,prec,precond", STEP_CASES,
+                         ids=["%s-%dx%dx%d-%s-%s" % ("2d" if c["dim"] == 2 else "3d", c["nx"], c["ny"], c["nz"], p, q)
+                              for c, p, q in STEP_CASES])
+def test_step_parity_100_steps(lib, case, prec, precond):
     """The GPU step matches the oracle to 1e-9 relative L-inf on every field after 100 steps
-    (the mixed path reaches the same bound: its outer iterations and residuals are FP64)."""
-    case = _tight(dict(case))
+    (the mixed path reaches the same bound: its outer iterations and residuals are FP64),
+    with the multigrid and with the cosine-transform pressure solver."""
+    case = _tight(dict(case, precond_p=precond))
     if prec == "mixed":
         # the mixed path stops on the true FP64 residual, which rounding keeps
         # above 1e-14 on some systems (the FP64 path tests its recursive one)
@@ -460,8 +469,8 @@ def full_oracle(full):
     return case, T0, f["C"], st
 
 
-@pytest.mark.parametrize("prec", ["mixed", "fp64"])
-def test_full_size_steps_match_oracle(lib, full_oracle, prec):
+@pytest.mark.parametrize("prec,precond", [("mixed", "mg"), ("fp64", "mg"), ("mixed", "dct"), ("fp64", "dct")])
+def test_full_size_steps_match_oracle(lib, full_oracle, prec, precond):
     """The benchmarked path at the benchmark size and tolerances (128x96x96,
     pressure tol 1e-10, transport tol 1e-12), element by element against the
     oracle after FULL_STEPS steps. The mixed case takes the one-after-another
@@ -470,29 +479,30 @@ def test_full_size_steps_match_oracle(lib, full_oracle, prec):
     1e-6 bound of the mixed path; so must p and the velocity (one vector
     field, judged against its largest component)."""
     case, T0, C0, ref = full_oracle
-    c = solid.Case(case, precision=PREC[prec])
+    c = solid.Case(dict(case, precond_p=precond), precision=PREC[prec])
     c.initialize(T0, C0)
     c.step(FULL_STEPS)
     s = c.stats()
     assert s["status"] == solid.SS_OK, s
     gpu = c.get_fields()
     c.close()
+    assert s["iters"]["p"] > 0
     errs = {k: _rel(gpu[k], getattr(ref, k)) for k in ("p", "T", "C", "gl", "Cl", "Cs")}
     vmax = max(np.abs(x).max() for x in ref.vel)
     errs["velocity"] = max(np.abs(gpu[k] - ref.vel[a]).max() for a, k in enumerate("uvw")) / vmax
-    print("full-size %s vs oracle after %d steps: %s" % (prec, FULL_STEPS,
+    print("full-size %s %s vs oracle after %d steps: %s" % (prec, precond, FULL_STEPS,
                                                           ", ".join("%s %.2e" % kv for kv in errs.items())))
     for k, e in errs.items():
         assert e < FULL_BOUND, (k, e)
     assert ref.gl.min() < 1.0
 
 
-@pytest.mark.parametrize("prec", ["fp64", "mixed"])
-def test_tiny_right_hand_side(lib, prec):
+@pytest.mark.parametrize("prec,precond", [("fp64", "mg"), ("mixed", "mg"), ("fp64", "dct"), ("mixed", "dct")])
+def test_tiny_right_hand_side(lib, prec, precond):
     """A nearly solenoidal u* gives a pressure right-hand side near the
     rounding level; the solves must neither underflow (the mixed path scales
     its FP32 inner problem) nor lose accuracy."""
-    case = _tight(dict(cases.box_3d(32, 24, 16)))
+    case = _tight(dict(cases.box_3d(32, 24, 16), precond_p=precond))
     c = solid.Case(case, precision=PREC[prec])
     f = cases.random_state(case, 31, vel_scale=1e-22)
     c.set_fields(f)
