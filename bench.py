@@ -33,19 +33,49 @@ if ROOT not in sys.path:
 
 from paper_2303_10783_gb300 import cases  # noqa: E402
 
-# Algorithmic work of the multigrid-preconditioned pressure solve (k_pcg_mg), per fine cell:
+# Algorithmic work per unit of the kernels whose roofline the line reports (the
+# dominant stage of a step). Bytes are what the method must move per cell or row;
+# flops are arithmetic operations (FMA = 2) in the kernel's own precision.
+#
+# k_pcg_mg (multigrid-preconditioned CG), per fine cell:
 #   one CG iteration with a V(2,2)-cycle moves, at the fine level, A p (8 B in FP32), the x/r
 #   update with the first smoothing sweep (32), second pre-sweep (12), residual (12),
 #   restriction (5), prolongation (8.5), two post-sweeps (24), the dot products (8) and the
 #   p update (12) = 121.5 B, plus ~10 B on the coarser levels -> 131 B in FP32, 262 B in FP64.
 #   One FP64 refinement sweep of the mixed path adds 44 B (r = b - A x: 24, x += d: 20).
-#   FP64 flops per CG iteration (FMA = 2): A p and (p,q) 12, updates 5, pre-sweep 13, residual 11,
+#   FP64 flops per CG iteration: A p and (p,q) 12, updates 5, pre-sweep 13, residual 11,
 #   restriction 21, prolongation 15, post-sweeps 26, dots 6, p update 3 = 112, coarse levels
 #   ~13 -> 125.
 MG_BYTES_PER_CELL_IT = {"mixed": 131.0, "fp64": 262.0}
 MG_BYTES_PER_CELL_REFINE = 44.0
 MG_FLOPS_PER_CELL_IT = 125.0
-FP64_FLOP_PER_CLK_PER_SM = 4.0   # 2 DFMA per clock per SM (1.25 TFLOP/s nominal at 2070 MHz, 152 SMs)
+# k_poisson_dct (cosine-transform solver in FP64 refinement), per cell, with E the size in
+# bytes of the transform type (4 mixed, 8 FP64):
+#   per sweep: pass A reads the FP64 residual (8) and writes T1 (E); pass B reads T1 (E),
+#   writes T2 (E), reads and writes it in the tridiagonal solves (2E), reads it (E) and writes
+#   T1 (E); pass C reads T1 (E) and reads and writes x (16); the FP64 residual reads x and b
+#   and writes r (24): 48 + 8E B. Once per launch: the mean of b (8), b and x set (24), the
+#   gauge (24): 56 B.
+#   flops per sweep: the forward and inverse transforms are 2 (Mx + My) multiply-adds
+#   (4 (Mx + My) flops, My = 0 in 2D) and the tridiagonal solve ~8, in the transform type;
+#   the FP64 residual ~16.
+DCT_BYTES_PER_CELL_SWEEP_BASE = 48.0
+DCT_BYTES_PER_CELL_LAUNCH = 56.0
+DCT_THOMAS_FLOPS = 8.0
+# k_bicgstab_ir (mixed transport: FP32 BiCGSTAB in FP64 refinement), per row:
+#   the first FP64 residual reads 7 FP64 planes, x and b and writes r (80); each sweep
+#   converts r (12), sets up the inner vectors (20), adds the correction (20) and forms the
+#   next FP64 residual (80): 132; each inner iteration moves 7 FP32 planes twice (56) and
+#   ~80 B of FP32 vectors: 136.
+BCG_IR_BYTES_ROW = 80.0
+BCG_IR_BYTES_ROW_SWEEP = 132.0
+BCG_IR_BYTES_ROW_IT = 136.0
+# k_bicgstab (FP64 transport), per row and iteration: two SpMVs over 7 FP64 planes (2 x 72)
+# and the vector updates (~156 B): 300 B; 2 x 13 + 20 = 46 FP64 flops.
+BCG_BYTES_ROW_IT = 300.0
+BCG_FLOPS_ROW_IT = 46.0
+FP64_FLOP_PER_CLK_PER_SM = 4.0    # 2 DFMA per clock per SM (1.26 TFLOP/s at 2070 MHz, 152 SMs)
+FP32_FLOP_PER_CLK_PER_SM = 256.0  # 128 FP32 FMA per clock per SM (80.6 TFLOP/s at 2070 MHz)
 NUM_SMS = 152
 
 
@@ -62,8 +92,10 @@ def parse():
     ap.add_argument("--workload", choices=("box", "batched", "serving", "ingot"), default="box",
                     help="box: the 128x96x96 headline; batched: 64 independent cavities; serving: request stream; "
                          "ingot: 384x256x256")
-    ap.add_argument("--requests", type=int, default=24, help="serving: requests in the sample")
-    ap.add_argument("--request-steps", type=int, default=100, help="serving: steps per request in the sample")
+    ap.add_argument("--requests", type=int, default=120, help="serving: requests in the sample")
+    ap.add_argument("--request-steps", type=int, default=50, help="serving: steps per request in the sample")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="box workload only: skip the cavity, ingot, batched and serving legs of the default line")
     ap.add_argument("--block-cap", type=int, default=-1,
                     help="serving: blocks per cooperative solver launch of each request (0: no cap; "
                          "-1: in proportion to the request's cells)")
@@ -207,10 +239,15 @@ def measured_peaks():
         return {}
 
 
-def kernel_source_sha():
-    """sha256 over the sources of the pressure-solve kernel (mg.cu and the shared header)."""
+KERNEL_SOURCES = {"k_pcg_mg": "mg.cu", "k_poisson_dct": "dct.cu", "k_bicgstab_ir": "krylov.cu",
+                  "k_bicgstab": "krylov.cu", "k_pcg_poisson": "krylov.cu"}
+
+
+def kernel_source_sha(kernel="k_pcg_mg"):
+    """sha256 over the source file of `kernel` and the shared header."""
     h = hashlib.sha256()
-    for f in ("mg.cu", "solid_internal.cuh"):
+    base = kernel.split("<")[0]
+    for f in (KERNEL_SOURCES.get(base, "mg.cu"), "solid_internal.cuh"):
         h.update(open(os.path.join(ROOT, "paper_2303_10783_gb300", "csrc", f), "rb").read())
     return h.hexdigest()
 
@@ -222,7 +259,7 @@ def kernel_traffic(kernel, workload):
     path = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(path):
         return None
-    sha = kernel_source_sha()
+    sha = kernel_source_sha(kernel)
     for line in open(path):
         m = re.match(r"\s*(\S+)\s+sha256=(\w+)\s+bytes_per_launch=([0-9.eE+]+)\s+workload=(\S+)", line)
         if m and m.group(1) == kernel and m.group(2) == sha and m.group(4) == workload:
@@ -244,6 +281,59 @@ def cpu_baseline(args):
     return {"value": g.ncell / dt, "unit": "cell-steps/s", "cores": 1, "kind": "oracle",
             "sample": "one full time step of %s%s (%d cells) from the seeded initial state, numpy/scipy FP64, "
                       "single thread, %.1f s" % (workload_name(args), res, g.ncell, dt)}
+
+
+def _oracle_step_at(job):
+    """One oracle step of the box workload at (nx, ny, nz), started at wall time
+    `start` (so that every process steps at once); returns (cells, begin, end)."""
+    nx, ny, nz, seed, start = job
+    import oracle
+    from paper_2303_10783_gb300 import cases as cs
+    case = cs.box_3d(nx, ny, nz, seed=seed)
+    f = cs.initial_fields(case)
+    g = oracle.Grid(case)
+    st = oracle.initial_state(case, f["T"], f["C"])
+    while time.time() < start:
+        time.sleep(0.01)
+    t0 = time.time()
+    oracle.step(g, st, case)
+    return g.ncell, t0, time.time()
+
+
+def cpu_all_cores(args, delay=8.0):
+    """The oracle as it stands on every host core at once: one independent
+    replica per core (spawned processes, one thread each), each taking one
+    step of the workload at half its resolution per axis; throughput = the
+    replicas' cells over the span from the first start to the last end."""
+    import multiprocessing as mp
+    ncores = os.cpu_count() or 1
+    nx, ny, nz = max(args.nx // 2, 2), max(args.ny // 2, 2), max(args.nz // 2, 2)
+    env = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+    for k in env:
+        os.environ[k] = "1"
+    try:
+        ctx = mp.get_context("spawn")
+        start = time.time() + delay        # after every process has imported numpy and scipy
+        with ctx.Pool(ncores) as pool:
+            res = pool.map(_oracle_step_at, [(nx, ny, nz, 100 + q, start) for q in range(ncores)])
+    finally:
+        for k, v in env.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    cells = sum(r[0] for r in res)
+    span = max(r[2] for r in res) - min(r[1] for r in res)
+    try:
+        import platform
+        model = platform.processor() or platform.machine()
+    except Exception:
+        model = "unknown"
+    return {"value": cells / span, "unit": "cell-steps/s", "cores": ncores, "kind": "oracle",
+            "cpu": model,
+            "sample": "%d independent replicas (one per core, one thread each), one step each of %s at 1/2 "
+                      "resolution per axis (%dx%dx%d), numpy/scipy FP64, %.1f s span"
+                      % (ncores, workload_name(args), nx, ny, nz, span)}
 
 
 def run_reference(args):
@@ -382,38 +472,86 @@ def field_errors(a, b, dim):
     return out
 
 
-def roofline(precision_name, m, ncell, steps, wname):
-    """Roofline of the dominant stage (device time from the library's events on the case stream)."""
+def _rows(case, sysname):
+    nx, ny, nz = case["nx"], case["ny"], case["nz"] if case["dim"] == 3 else 1
+    return {"u": (nx + 1) * ny * nz, "v": nx * (ny + 1) * nz, "w": nx * ny * (nz + 1)}.get(sysname, nx * ny * nz)
+
+
+def kernel_work(stage, precision_name, case, prof, stats):
+    """Algorithmic work of one launch of the solve kernel of `stage` (from the
+    per-unit figures above and the measured iterations): (kernel, launches,
+    bytes per launch, flops per launch, flop type, counts)."""
+    mixed = precision_name == "mixed"
+    launches = max(prof["launches"][stage], 1)
+    sysname = stage.split("_", 1)[1]
+    ncell = _rows(case, "p")
+    precond = case.get("precond_p", "dct")
+    if sysname == "p":
+        its = prof["iters"]["p"] / launches
+        if precond == "dct":
+            E = 4.0 if mixed else 8.0
+            My = case["ny"] if case["dim"] == 3 else 0
+            nbytes = ncell * (DCT_BYTES_PER_CELL_LAUNCH + its * (DCT_BYTES_PER_CELL_SWEEP_BASE + 8.0 * E))
+            flops = ncell * its * (4.0 * (case["nx"] + My) + DCT_THOMAS_FLOPS)
+            kern = "k_poisson_dct<%s>" % ("float" if mixed else "double")
+            return kern, launches, nbytes, flops, "fp32" if mixed else "fp64", {"sweeps": its, "cells": ncell}
+        refs = stats["refinements"]["p"]
+        nbytes = ncell * (MG_BYTES_PER_CELL_IT[precision_name] * its + MG_BYTES_PER_CELL_REFINE * refs)
+        flops = MG_FLOPS_PER_CELL_IT * ncell * its
+        kern = "k_pcg_mg<%s>" % ("float" if mixed else "double")
+        return kern, launches, nbytes, flops, "fp64", {"iterations": its, "refinements": refs, "cells": ncell}
+    systems = [sysname]
+    if stage == "solve_u" and prof["launches"].get("solve_v", 0) == 0:
+        systems = list("uvw"[: case["dim"]])     # the joint momentum launch, counted under solve_u
+    nbytes = flops = 0.0
+    counts = {}
+    for q in systems:
+        rows = _rows(case, q)
+        its = prof["iters"][q] / launches
+        if mixed:
+            sweeps = stats["refinements"][q]
+            nbytes += rows * (BCG_IR_BYTES_ROW + BCG_IR_BYTES_ROW_SWEEP * sweeps + BCG_IR_BYTES_ROW_IT * its)
+            counts[q] = {"rows": rows, "inner_iterations": its, "sweeps": sweeps}
+        else:
+            nbytes += rows * BCG_BYTES_ROW_IT * its
+            flops += rows * BCG_FLOPS_ROW_IT * its
+            counts[q] = {"rows": rows, "iterations": its}
+    return ("k_bicgstab_ir" if mixed else "k_bicgstab"), launches, nbytes, flops, "fp64", counts
+
+
+def roofline(precision_name, m, case, steps, wname):
+    """Roofline of the dominant solve stage of a step: its kernel's algorithmic
+    bytes and flops per launch over the launch's device time (CUDA events on
+    the case stream), against the measured HBM copy bandwidth and the FP32 or
+    FP64 pipe's peak at the median SM clock sampled during the timed region;
+    the bound is whichever resource takes longer at its peak."""
     stage_ms = m["prof"]["ms"]
-    top = max(stage_ms, key=stage_ms.get)
+    solves = {k: v for k, v in stage_ms.items() if k.startswith("solve_") and m["prof"]["launches"].get(k, 0) > 0}
+    top = max(solves, key=solves.get)
     peaks = measured_peaks()
     sm_mhz = m["clocks"].get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
-    launches = max(m["prof"]["launches"]["solve_p"], 1)
-    t_launch = stage_ms["solve_p"] * 1e-3 / launches
-    its = m["prof"]["iters"]["p"] / launches
-    refs = m["stats"]["refinements"]["p"]
-    bytes_ = ncell * (MG_BYTES_PER_CELL_IT[precision_name] * its + MG_BYTES_PER_CELL_REFINE * refs)
+    kern, launches, nbytes, flops, ftype, counts = kernel_work(top, precision_name, case, m["prof"], m["stats"])
+    t_launch = stage_ms[top] * 1e-3 / launches
     hbm = peaks.get("hbm_gbs", 6687.1)
-    out = {"kernel": "k_pcg_mg<%s>" % ("float" if precision_name == "mixed" else "double"),
-           "launch_ms": t_launch * 1e3, "algorithmic_per_launch": {"bytes": bytes_, "iterations": its,
-                                                                    "refinements": refs, "cells": ncell}}
-    if precision_name == "mixed":
-        ach = bytes_ / t_launch / 1e9
+    per_clk = FP32_FLOP_PER_CLK_PER_SM if ftype == "fp32" else FP64_FLOP_PER_CLK_PER_SM
+    fpeak = per_clk * NUM_SMS * sm_mhz * 1e6 / 1e12
+    out = {"kernel": kern, "stage": top, "launch_ms": t_launch * 1e3,
+           "algorithmic_per_launch": {"bytes": nbytes, "flops": flops, "flop_type": ftype, "counts": counts},
+           "hbm_frac": nbytes / t_launch / 1e9 / hbm, "alu_frac": flops / t_launch / 1e12 / fpeak}
+    if nbytes / (hbm * 1e9) >= flops / (fpeak * 1e12):
+        ach = nbytes / t_launch / 1e9
         out.update(bound="hbm", achieved=ach, peak=hbm, unit="GB/s", frac=ach / hbm,
                    peak_basis="measured HBM copy bandwidth (MEASURED_PEAKS.json)")
     else:
-        flops = MG_FLOPS_PER_CELL_IT * ncell * its
-        peak = FP64_FLOP_PER_CLK_PER_SM * NUM_SMS * sm_mhz * 1e6 / 1e12
         ach = flops / t_launch / 1e12
-        out.update(bound="alu", achieved=ach, peak=peak, unit="TFLOP/s", frac=ach / peak,
-                   peak_basis="FP64 pipe: 4 flop/clk/SM x 152 SMs x %.0f MHz median SM clock under load" % sm_mhz,
-                   hbm_achieved_GBps=bytes_ / t_launch / 1e9)
-        out["algorithmic_per_launch"]["flops"] = flops
-    tr = kernel_traffic(out["kernel"], wname)
+        out.update(bound="alu", achieved=ach, peak=fpeak, unit="TFLOP/s", frac=ach / fpeak,
+                   peak_basis="%s pipe: %.0f flop/clk/SM x %d SMs x %.0f MHz median SM clock under load"
+                              % (ftype.upper(), per_clk, NUM_SMS, sm_mhz))
+    tr = kernel_traffic(kern, wname)
     out["traffic"] = tr[0] if tr else None
-    if top != "solve_p":
-        # per-unit counts are defined for the pressure solve; say when another stage took longer
-        out["dominant_stage"] = top
+    top_all = max(stage_ms, key=stage_ms.get)
+    if top_all != top:
+        out["dominant_stage"] = top_all
     return out
 
 
@@ -450,7 +588,7 @@ def run_ours(args):
         "vs_baseline": None, "dtype": "f32+f64" if head == "mixed" else "f64", "data": "synthetic",
         "config": {"workload": workload_name(args),
                    "cells": ncell, "precision": head, "tol_p": case["tol_p"],
-                   "tol_t": case["tol_t"], "dt": case["dt"], "pressure_preconditioner": case.get("precond_p", "mg"),
+                   "tol_t": case["tol_t"], "dt": case["dt"], "pressure_preconditioner": case.get("precond_p", "dct"),
                    "parallelism": "replicas" if world > 1 else "single",
                    "l2": "inputs larger than L2: each step streams ~0.5 GB of fields and DIA planes (L2 129 MB); "
                          "no flush"},
@@ -462,7 +600,7 @@ def run_ours(args):
                          "ss_set_fields(device) + ss_step(1) + ss_get_fields(device), device buffer -> pinned "
                          "host (side stream, during the next step)"} if h["e2e"] else None),
         "gpu_launches": h["prof"]["kernels"],
-        "roofline": roofline(head, h, ncell, args.steps, workload_name(args)),
+        "roofline": roofline(head, h, case, args.steps, workload_name(args)),
         "stage_ms_per_step": {k: v / args.steps for k, v in h["prof"]["ms"].items() if v > 0},
         "iters_per_step": {k: v / args.steps for k, v in h["prof"]["iters"].items()},
         "refinements_last_step": dict(h["stats"]["refinements"]),
@@ -472,83 +610,192 @@ def run_ours(args):
         out[name] = {"value": m["value"], "ms_per_step": m["ms_max"] / args.steps, "status": m["status"],
                      "dtype": "f64" if name == "fp64" else "f32+f64",
                      "e2e_value": m.get("e2e_value"), "gpu_launches": m["prof"]["kernels"],
-                     "roofline": roofline(name, m, ncell, args.steps, workload_name(args)),
+                     "roofline": roofline(name, m, case, args.steps, workload_name(args)),
                      "stage_ms_per_step": {k: v / args.steps for k, v in m["prof"]["ms"].items() if v > 0},
                      "iters_per_step": {k: v / args.steps for k, v in m["prof"]["iters"].items()}}
     if "mixed" in res and "fp64" in res:
         out["mixed_vs_fp64"] = {"after_steps": args.warmup + args.steps, "bound": 1e-6, "bounded_fields": ["T", "C", "gl"],
                                 "rel_linf": field_errors(res["mixed"]["fields"], res["fp64"]["fields"], case["dim"])}
+    if world == 1 and not args.no_extras and args.workload == "box":
+        for leg in (cavity_leg, ingot_leg, batched_leg, serving_leg):
+            name, val = leg(args, local)
+            out[name] = val
+            torch.cuda.empty_cache()
     if world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args)
+        out["cpu_baseline"]["all_cores"] = cpu_all_cores(args)
     print(json.dumps(out))
     if dist is not None:
         dist.destroy_process_group()
     return 0
 
 
-def run_batched(args):
-    """64 independent cavities stepped side by side (one stream each, graph-replayed steps)."""
+def _time_case(case, precision, steps, warmup, local):
+    """Warm up, then time `steps` steps of one case on its own stream (CUDA
+    events on that stream); returns (ms, status, profile, stats, clocks)."""
     import torch
     from paper_2303_10783_gb300 import solid
+    f = cases.initial_fields(case)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        c = solid.Case(case, precision=solid.SS_MIXED if precision == "mixed" else solid.SS_FP64, stream=stream)
+        c.initialize(f["T"], f["C"])
+        c.step(warmup)
+        c.sync()
+        c.get_profile()
+        c.set_profiling(True)
+        sampler = ClockSampler(local)
+        stream.synchronize()
+        sampler.start()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        c.step(steps)
+        e1.record(stream)
+        stream.synchronize()
+        clocks = sampler.stop()
+        ms = e0.elapsed_time(e1)
+        status = c.sync(allow=(solid.SS_ENOTCONV,))
+        prof = c.get_profile()
+        stats = c.stats()
+        c.close()
+    return ms, solid.STATUS_NAMES.get(status, status), prof, stats, clocks
+
+
+def cavity_leg(args, local):
+    """The 2D cavity (0.10 x 0.06 m, 50 x 30 cells, FP64 plain scheme), 300 steps."""
+    case = cases.cavity_2d()
+    if args.precond:
+        case["precond_p"] = args.precond
+    ms, status, prof, _, clocks = _time_case(case, "fp64", 300, 3, local)
+    n = case["nx"] * case["ny"]
+    return "cavity", {"workload": "cavity_2d_50x30", "precision": "fp64", "steps": 300, "warmup": 3,
+                      "value": n * 300 / (ms * 1e-3), "unit": "cell-steps/s", "ms_per_step": ms / 300,
+                      "status": status, "gpu_launches": prof["kernels"], "clocks": clocks,
+                      "note": "1500 cells: latency-bound, no roofline claimed"}
+
+
+def ingot_leg(args, local):
+    """The 3D ingot (0.2 x 0.1 x 0.1 m, 384 x 256 x 256 = 25.2 M cells, Fe-C-like
+    alloy, bottom cooling), mixed and FP64, each with the roofline of its
+    dominant solve: at this size the vectors do not fit L2."""
+    out = {"workload": "ingot_3d_384x256x256", "cells": 384 * 256 * 256}
+    steps, warmup = 5, 2
+    for prec in ("mixed", "fp64"):
+        case = cases.ingot_3d(seed=4)
+        if args.precond:
+            case["precond_p"] = args.precond
+        ms, status, prof, stats, clocks = _time_case(case, prec, steps, warmup, local)
+        m = {"prof": prof, "stats": stats, "clocks": clocks}
+        out[prec] = {"value": out["cells"] * steps / (ms * 1e-3), "unit": "cell-steps/s", "ms_per_step": ms / steps,
+                     "steps": steps, "warmup": warmup, "status": status, "gpu_launches": prof["kernels"],
+                     "clocks": clocks, "pressure_solver": case.get("precond_p", "dct"),
+                     "roofline": roofline(prec, m, case, steps, "ingot_3d_384x256x256"),
+                     "stage_ms_per_step": {k: v / steps for k, v in prof["ms"].items() if v > 0},
+                     "iters_per_step": {k: v / steps for k, v in prof["iters"].items()}}
+    return "ingot", out
+
+
+def batched_leg(args, local, steps=5, warmup=2):
+    """64 independent cavities stepped side by side; see run_batched."""
+    return "batched", _batched(args, local, steps, warmup, None)
+
+
+def serving_leg(args, local):
+    """A bounded sample of the request stream served under the 150 GB budget; see run_serving."""
+    return "serving", _serving(args)
+
+
+def _batched(args, local, steps, warmup, dist):
+    """64 independent cavities (2D and 3D, uneven sizes) stepped side by side:
+    one stream and one captured step graph per case, solver block cap chosen
+    by the batch autotuner from a saved and restored state (outside the timed
+    region). Returns the measured quantities (rank-local)."""
+    from paper_2303_10783_gb300 import solid
     from paper_2303_10783_gb300.batch import Batch
-    rank, world, local = dist_env()
-    dist = init_group(world)
-    torch.cuda.set_device(local)
+    rank = dist_env()[0]
     cs = cases.batch_cases(64, seed=2 + 100 * rank)
+    if args.precond:
+        cs = [dict(c, precond_p=args.precond) for c in cs]
     b = Batch(cs, precision=solid.SS_MIXED)
     sampler = ClockSampler(local)
-    b.step(args.warmup)
+    b.step(warmup)
     b.sync()
-    # project autotuner: the solver block cap that steps this batch fastest
-    # (trials run from a saved state that is restored, outside the timed region)
     cap, trials = b.autotune()
     for _, c, _ in b.members:
         c.get_profile()   # count launches of the timed region only
     barrier(dist)
     sampler.start()
-    dt, _ = b.run(args.steps)
+    dt, _ = b.run(steps)
     clocks = sampler.stop()
     dt = max_over_ranks(dist, dt)
-    total = sum_over_ranks(dist, b.cells * args.steps)
+    total = sum_over_ranks(dist, b.cells * steps)
     status = b.sync()
     kernels = sum(c.get_profile()["kernels"] for _, c, _ in b.members)
     cells = b.cells
     b.close()
+    return {"workload": "batched_64_cavities", "value": total / dt, "unit": "cell-steps/s",
+            "ms_per_step": 1e3 * dt / steps, "steps": steps, "warmup": warmup, "cases": len(cs), "cells": cells,
+            "precision": "mixed", "pressure_solver": cs[0].get("precond_p", "dct"),
+            "status": solid.STATUS_NAMES.get(status, status), "streams": len(cs), "graphs": True,
+            "block_cap": cap, "autotune_ms_per_step": {str(k): 1e3 * v for k, v in trials.items()},
+            "timing": "host wall clock over the steps of all cases (enqueue to last stream synchronised)",
+            "clocks": clocks, "gpu_launches": kernels}
+
+
+def run_batched(args):
+    """64 independent cavities stepped side by side (one stream each, graph-replayed steps)."""
+    import torch
+    rank, world, local = dist_env()
+    dist = init_group(world)
+    torch.cuda.set_device(local)
+    r = _batched(args, local, args.steps, args.warmup, dist)
     if rank == 0:
-        print(json.dumps({"metric": "cell-steps/s", "value": total / dt, "unit": "cell-steps/s", "n_gpus": world,
-                          "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        print(json.dumps({"metric": "cell-steps/s", "value": r["value"], "unit": "cell-steps/s", "n_gpus": world,
+                          "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms_per_step"],
                           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
-                          "data": "synthetic", "status": solid.STATUS_NAMES.get(status, status),
-                          "config": {"workload": "batched_64_cavities", "cases": len(cs), "cells": cells,
-                                     "precision": "mixed", "streams": len(cs), "graphs": True,
-                                     "block_cap": cap,
-                                     "autotune_ms_per_step": {str(k): 1e3 * v for k, v in trials.items()}},
-                          "clocks": clocks, "gpu_launches": kernels}))
+                          "data": "synthetic", "status": r["status"],
+                          "config": {k: r[k] for k in ("workload", "cases", "cells", "precision", "streams",
+                                                        "graphs", "block_cap", "autotune_ms_per_step",
+                                                        "pressure_solver")},
+                          "clocks": r["clocks"], "gpu_launches": r["gpu_launches"]}))
     return 0
+
+
+def _serving(args):
+    """The first `args.requests` requests of the seeded stream (Poisson arrivals
+    at 20/s, grids 32^3..192^3), `args.request_steps` steps each, served under
+    the 150 GB budget with continuous batching."""
+    from paper_2303_10783_gb300.serve import Server
+    reqs = cases.serving_requests(n=args.requests, steps=args.request_steps)
+    srv = Server(budget_bytes=150 * 10 ** 9, chunk=10, block_cap=args.block_cap, precond=args.precond)
+    rep = srv.run(reqs)
+    waits = sorted(p["admitted"] - p["arrival"] for p in rep["per_request"])
+    return {"workload": "serving_requests", "value": rep["cell_steps_per_s"], "unit": "cell-steps/s",
+            "requests": rep["requests"], "steps_per_request": args.request_steps, "arrival_rate_per_s": 20.0,
+            "budget_bytes": rep["budget_bytes"],
+            "sample": "first %d requests of the seeded stream (grids 32^3..192^3), %d steps each"
+                      % (args.requests, args.request_steps),
+            "p50_ms_per_100_steps": rep["p50_ms_per_100_steps"], "p99_ms_per_100_steps": rep["p99_ms_per_100_steps"],
+            "p50_queue_s": rep["p50_queue_s"], "p99_queue_s": rep["p99_queue_s"],
+            "requests_that_waited": sum(1 for w in waits if w > 0.05),
+            "max_active": rep["max_active"], "max_used_bytes": rep["max_used_bytes"], "wall_s": rep["wall_s"],
+            "pressure_solver": srv.precond or reqs[0][1].get("precond_p", "dct")}
 
 
 def run_serving(args):
     """A bounded sample of the request stream served under the 150 GB budget."""
     import torch
-    from paper_2303_10783_gb300 import solid
-    from paper_2303_10783_gb300.serve import Server
     torch.cuda.set_device(0)
-    reqs = cases.serving_requests(n=args.requests, steps=args.request_steps)
-    srv = Server(budget_bytes=150 * 10 ** 9, chunk=10, block_cap=args.block_cap)
-    rep = srv.run(reqs)
-    print(json.dumps({"metric": "cell-steps/s", "value": rep["cell_steps_per_s"], "unit": "cell-steps/s",
+    r = _serving(args)
+    print(json.dumps({"metric": "cell-steps/s", "value": r["value"], "unit": "cell-steps/s",
                       "n_gpus": 1, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                       "dtype": "f32+f64", "data": "synthetic",
-                      "config": {"workload": "serving_requests", "requests": rep["requests"],
-                                 "steps_per_request": args.request_steps, "arrival_rate_per_s": 20.0,
-                                 "budget_bytes": rep["budget_bytes"],
-                                 "sample": "first %d requests of the seeded stream (grids 32^3..192^3), %d steps each"
-                                           % (args.requests, args.request_steps)},
-                      "p50_ms_per_100_steps": rep["p50_ms_per_100_steps"],
-                      "p99_ms_per_100_steps": rep["p99_ms_per_100_steps"],
-                      "p50_queue_s": rep["p50_queue_s"], "p99_queue_s": rep["p99_queue_s"],
-                      "max_active": rep["max_active"], "max_used_bytes": rep["max_used_bytes"],
-                      "wall_s": rep["wall_s"]}))
+                      "config": {k: r[k] for k in ("workload", "requests", "steps_per_request", "arrival_rate_per_s",
+                                                    "budget_bytes", "sample", "pressure_solver")},
+                      **{k: r[k] for k in ("p50_ms_per_100_steps", "p99_ms_per_100_steps", "p50_queue_s",
+                                           "p99_queue_s", "requests_that_waited", "max_active", "max_used_bytes",
+                                           "wall_s")}}))
     return 0
 
 

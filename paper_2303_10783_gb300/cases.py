@@ -71,7 +71,7 @@ def fe_c_alloy():
 
 
 def make_case(dim, nx, ny, nz, lx, ly, lz, dt, alloy=None, robin=None, T0=499.0, noise=1.0e-3, seed=0,
-              tol_p=1.0e-10, tol_t=1.0e-12, max_it_p=20000, max_it_t=2000, steps=100, precond_p="mg",
+              tol_p=1.0e-10, tol_t=1.0e-12, max_it_p=20000, max_it_t=2000, steps=100, precond_p="dct",
               dirichlet=None, slip=(), perturb=None):
     if dim == 2:
         nz, lz = 1, 1.0

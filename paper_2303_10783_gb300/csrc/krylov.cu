@@ -493,6 +493,12 @@ constexpr int kMaxRefine = 12;
 // Inner iterations per refinement sweep: bounds a sweep whose FP32 iteration
 // stalls (the outer FP64 loop then continues from the best iterate).
 constexpr int kMaxInner = 200;
+// A sweep's inner solve need not reduce its residual further than the outer
+// tolerance still asks: it stops at max(inner_tol, kSweepMargin * thr / rn),
+// thr the outer target and rn the current FP64 residual norm. The margin
+// covers the FP32 operator's rounding, which the FP64 residual sees and the
+// inner one does not.
+constexpr double kSweepMargin = 0.1;
 
 __device__ __forceinline__ void ir_solve(const BcgArgs& A, const Team& tm) {
   unsigned int epoch = 0;
@@ -511,7 +517,7 @@ __device__ __forceinline__ void ir_solve(const BcgArgs& A, const Team& tm) {
   }
   // scalars formed by thread 0 of each block after each reduction
   __shared__ struct {
-    double bnorm, rn, inv, rel;
+    double bnorm, rn, inv, rel, itol;
     int conv, go;
   } is;
   double thr = 0.0;                               // read by thread 0 only
@@ -523,6 +529,7 @@ __device__ __forceinline__ void ir_solve(const BcgArgs& A, const Team& tm) {
         is.conv = is.bnorm == 0.0 || is.rn <= thr;
         is.go = is.bnorm > 0.0 && is.rn > thr && isfinite(is.rn);
         is.rel = is.bnorm > 0.0 ? is.rn / is.bnorm : 0.0;
+        is.itol = fmax(A.inner_tol, kSweepMargin * thr / is.rn);
       }))
     return;
   int total = 0, ref = 0;
@@ -535,8 +542,7 @@ __device__ __forceinline__ void ir_solve(const BcgArgs& A, const Team& tm) {
     for (int i = t0; i < n; i += gs) A.f32.r0[i] = (float)(r64[i] * inv);
     CoreOut o;
     const int cap = (A.max_it - total < kMaxInner) ? A.max_it - total : kMaxInner;
-    if (!bcg_fused(A.sys.af, n, sy, sz, A.has_z, A.d32, A.f32, A.inner_tol, cap, tm, A.max_blocks, A.st, epoch,
-                   o))
+    if (!bcg_fused(A.sys.af, n, sy, sz, A.has_z, A.d32, A.f32, is.itol, cap, tm, A.max_blocks, A.st, epoch, o))
       return;
     total += o.it;
     for (int i = t0; i < n; i += gs) x[i] += rn * (double)A.d32[i];
@@ -553,6 +559,7 @@ __device__ __forceinline__ void ir_solve(const BcgArgs& A, const Team& tm) {
           is.conv = is.rn <= thr;
           is.go = is.rn > thr && isfinite(is.rn);
           is.rel = is.rn / is.bnorm;
+          is.itol = fmax(A.inner_tol, kSweepMargin * thr / is.rn);
         }))
       return;
     if (o.it == 0 && !is.conv) break;          // the inner solve made no progress

@@ -132,7 +132,7 @@ def grid_struct(case, precision=SS_FP64):
                 case["lx"], case["ly"], case["lz"], case["dt"], precision,
                 case["tol_p"], case["tol_t"], case["max_it_p"], case["max_it_t"],
                 {"mg": SS_PRECOND_MG, "jacobi": SS_PRECOND_JACOBI,
-                 "dct": SS_PRECOND_DCT}[case.get("precond_p", "mg")])
+                 "dct": SS_PRECOND_DCT}[case.get("precond_p", "dct")])
 
 
 def alloy_struct(case):

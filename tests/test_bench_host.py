@@ -72,3 +72,11 @@ def test_reference_arm_prints_the_contract_line():
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
     assert d["config"]["workload"] == "box_3d_16x12x12"
+
+
+def test_all_core_oracle_timing_runs_one_replica_per_core():
+    """The all-core oracle leg spawns one single-threaded replica per host core
+    and reports their combined throughput with the core count."""
+    d = bench.cpu_all_cores(_args("box", 16, 12, 12), delay=4.0)
+    assert d["cores"] == (os.cpu_count() or 1) and d["kind"] == "oracle" and d["value"] > 0
+    assert "8x6x6" in d["sample"]

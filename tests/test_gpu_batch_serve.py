@@ -74,6 +74,28 @@ def test_server_budget_and_isolation(lib):
     assert one > 0
 
 
+def test_server_admits_and_retires_continuously(lib):
+    """Continuous batching: a small request that arrives while a large one is
+    running is admitted at once and finishes first; a second large request
+    that does not fit the budget beside the first waits and is admitted as
+    soon as memory frees; every result equals the request run alone."""
+    big = dict(cases.box_3d(64, 48, 48, seed=11), steps=80)
+    small = dict(cases.box_3d(16, 16, 16, seed=13), steps=10)
+    big2 = dict(cases.box_3d(64, 48, 48, seed=12), steps=10)
+    reqs = [(0.0, big), (0.002, small), (0.004, big2)]
+    wb = solid.workspace_bytes(big, solid.SS_MIXED)
+    ws = solid.workspace_bytes(small, solid.SS_MIXED)
+    srv = Server(budget_bytes=wb + ws + ws // 2, chunk=5, keep_results=True)
+    rep = srv.run(reqs)
+    per = {p["rid"]: p for p in rep["per_request"]}
+    assert per[1]["arrival"] > per[0]["arrival"] and per[1]["finished"] < per[0]["finished"]
+    assert per[1]["admitted"] < per[0]["finished"]                 # admitted while the large one ran
+    assert per[2]["admitted"] >= per[0]["finished"]                # waited for the large one's memory
+    assert rep["max_used_bytes"] <= rep["budget_bytes"] and rep["max_active"] == 2
+    for q, (_, cd) in enumerate(reqs):
+        assert _same(rep["results"][q], _alone(cd, cd["steps"])), q
+
+
 @pytest.mark.parametrize("prec", [solid.SS_FP64, solid.SS_MIXED], ids=["fp64", "mixed"])
 @pytest.mark.parametrize("dims", [(24, 16, 12), (64, 48, 48)])
 def test_steps_are_bit_reproducible(lib, prec, dims):
@@ -88,7 +110,7 @@ def test_mixed_pressure_refinement_does_not_stall(lib):
     not reach the FP32 inner solve: on this 96x128 batch case it once made the
     inner CG run to the iteration cap at steps 6 and 7. Every step must stay
     at a few V-cycle iterations and meet the tolerance."""
-    case = cases.batch_cases(n=64)[48]
+    case = dict(cases.batch_cases(n=64)[48], precond_p="mg")
     assert (case["dim"], case["nx"], case["ny"]) == (2, 96, 128)
     c = solid.Case(case, precision=solid.SS_MIXED)
     f = cases.initial_fields(case)

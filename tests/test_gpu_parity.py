@@ -322,16 +322,17 @@ def test_fully_solid_and_fully_liquid(lib):
             assert np.abs(gpu[k] - getattr(st, k)).max() <= 1e-9 * max(np.abs(getattr(st, k)).max(), 1e-12), (shift, k)
 
 
-def test_iteration_cap_is_reported(lib):
+@pytest.mark.parametrize("precond,tol", [("mg", 1e-14), ("dct", 1e-30)])
+def test_iteration_cap_is_reported(lib, precond, tol):
     """A solve that hits its cap records SS_ENOTCONV (sticky) and keeps its iterate; nothing traps."""
-    case = cases.cavity_2d(30, 20, tol_p=1e-14, max_it_p=2)
+    case = cases.cavity_2d(30, 20, tol_p=tol, max_it_p=2, precond_p=precond)
     f = cases.initial_fields(case)
     c = solid.Case(case)
     c.initialize(f["T"] - 0.8, f["C"])
     c.step(2)
     assert c.sync(allow=(solid.SS_ENOTCONV,)) == solid.SS_ENOTCONV
     s = c.stats()
-    assert s["iters"]["p"] == 2
+    assert s["iters"]["p"] == 2 if precond == "mg" else 1 <= s["iters"]["p"] <= 2
     assert c.sync() == solid.SS_OK       # cleared by the read
     assert np.all(np.isfinite(c.get_fields(("u", "T"))["u"]))
     c.close()
