@@ -146,7 +146,9 @@ typedef struct {
  * pair on the case's stream around every stage; ss_get_profile returns the
  * accumulated device time per stage (ms) and the number of library kernels
  * launched per stage since the previous ss_get_profile call (launch counts
- * are kept whether or not profiling is on). */
+ * are kept whether or not profiling is on). With SS_PRECOND_DCT the pressure
+ * solve of a step ends with the projection (Eq. 3.5): its time and launch
+ * count under the pressure solve, and the projection stage stays at 0. */
 enum { SS_PROF_ASSEMBLE = 0,   /* + SS_SYS_*: assembly of that system */
        SS_PROF_SOLVE = 6,      /* + SS_SYS_*: its solve */
        SS_PROF_PROJECT = 12, SS_PROF_LEVER = 13, SS_NPROF = 14 };
@@ -201,7 +203,8 @@ ss_status ss_get_fields(ss_case* c, unsigned mask, void* const* dst, int dst_is_
 
 /* Overwrite the fields selected by `mask` from src[id] (restart, or seeded
  * initial noise). Other fields are left as they are. In a mixed-precision
- * case with the multigrid pressure solver, each step's pressure correction
+ * case with the multigrid or the cosine-transform pressure solver, each
+ * step's pressure correction
  * (Eq. 3.4) starts from the previous step's correction; this call clears
  * that warm start, so the next step depends on the case's state alone and a
  * restarted case gives the same fields as a new case from the same state.
@@ -268,8 +271,9 @@ const char* ss_last_error(void);
  *             stage, else T^n unchanged.
  * ss_solve(c, sys): solve the assembled system (initial guess: the current
  *   field for U/V/W/C/T; for P the previous pressure correction in a
- *   mixed-precision case with the multigrid solver, 0 in a new case, after
- *   ss_set_fields and on the other paths) into the system's solution vector;
+ *   mixed-precision case with the multigrid or cosine-transform solver, 0 in
+ *   a new case, after ss_set_fields and on the other paths) into the system's
+ *   solution vector;
  *   returns the solve's outcome.
  * ss_get_system(c, sys, dst, dst_is_device): copy planes and vectors of the
  *   system into dst[0..8] = P, W, E, S, N, B, T (DIA planes, Eq. 4.1), b
@@ -302,6 +306,56 @@ ss_status ss_get_system_f32(ss_case* c, int sys, void* const* dst, int dst_is_de
 ss_status ss_assemble_forward(ss_case* c, int sys);
 ss_status ss_project(ss_case* c);
 ss_status ss_lever(ss_case* c);
+
+/* ---- Packed batches of cases.
+ *
+ * The paper steps one case at a time; a packed batch steps many independent
+ * cases (each a case created as above, with its own workspace and fields)
+ * with one launch per stage of Algorithm 1 for all of them: the assembly and
+ * pointwise stages (Eq. 3.3 and 3.4 right-hand sides, Eq. 3.10, Eq. 3.12,
+ * Eq. 3.13-3.19) process a packed list of (case, row tile) items, and each
+ * solve (Eq. 3.3, 3.4, 3.10, 3.12) is one cooperative launch in which every
+ * case is solved by its own team of blocks, so uneven cases run side by side
+ * without a launch per case; the pressure solve ends with the projection
+ * (Eq. 3.5). Nine launches per batch step; on a non-default stream they are
+ * captured once into a CUDA graph and replayed.
+ * A member's fields agree with the same case stepped alone to rounding (the
+ * reductions of a team of k blocks are ordered like a launch of k blocks);
+ * the batch is deterministic for a given schedule.
+ *
+ * ss_batch_workspace_bytes(cases, n, bytes): device bytes the batch's tables
+ *   need (descriptions of the n cases, solver arguments, team and tile tables).
+ *   Every case must be SS_MIXED with the SS_PRECOND_DCT pressure solver and
+ *   have its alloy set; a case may appear once (SS_EINVAL / SS_ESTATE else).
+ * ss_batch_create(cases, n, workspace, bytes, stream, out): the batch over
+ *   the n cases, its tables in `workspace` (device, 256-byte aligned, owned by
+ *   the caller, alive until ss_batch_destroy), launched on `stream`. It waits
+ *   for the cases' own streams once. While the batch steps them, the cases
+ *   must not be used on their own streams; after ss_batch_sync they can be
+ *   read (ss_get_fields, ss_get_stats) and stepped alone again. SS_EINVAL when
+ *   the cases need more teams than one launch keeps resident (one block per
+ *   case at least). The schedule starts at gamma = 1, tile_rows = 4096.
+ * ss_batch_set_schedule(b, gamma, tile_rows): team sizes in proportion to
+ *   cells^gamma (gamma in [0, 2]; at least one block, at most one per 512
+ *   cells, all teams together the resident limit) and rows per tile of the
+ *   packed stages (256 .. 2^24). Drops the captured graph. Changing it changes
+ *   the reduction order of the solves, hence the fields at rounding level.
+ * ss_batch_get_teams(b, blocks): blocks[q] = team size of case q.
+ * ss_batch_step(b, n): enqueue n batch steps and return.
+ * ss_batch_sync(b, launches): wait for the batch's stream, then read and
+ *   clear every case's sticky solver status; returns the worst one.
+ *   *launches (if not NULL) = library kernels launched by the batch so far.
+ * ss_batch_destroy(b): wait for the stream and free the host side; the
+ *   workspace and the cases are the caller's. */
+typedef struct ss_batch ss_batch;
+ss_status ss_batch_workspace_bytes(ss_case* const* cases, int n, size_t* bytes);
+ss_status ss_batch_create(ss_case* const* cases, int n, void* workspace, size_t workspace_bytes, void* stream,
+                          ss_batch** out);
+ss_status ss_batch_set_schedule(ss_batch* b, double gamma, int tile_rows);
+ss_status ss_batch_get_teams(ss_batch* b, int* blocks);
+ss_status ss_batch_step(ss_batch* b, int n);
+ss_status ss_batch_sync(ss_batch* b, long long* launches);
+ss_status ss_batch_destroy(ss_batch* b);
 
 /* ---- Device-side waits.
  *

@@ -75,27 +75,7 @@ __device__ __forceinline__ Split split(double F) {
   return {negative ? 0.0 : F, negative ? F : 0.0};
 }
 
-// IEEE-754 binary64 -> binary32 rounding to nearest, ties to even, on the
-// integer pipes for values whose result is a normal float (exponent of d in
-// [-126, 127]) and for zeros; other values (subnormal, overflowing, non-finite
-// results) take the hardware conversion. The 52-bit fraction keeps its top 23
-// bits; the 29 dropped bits decide the rounding; a carry out of the fraction
-// correctly increments the exponent (up to infinity).
-__device__ __forceinline__ float to_f32(double d) {
-  const unsigned long long u = (unsigned long long)__double_as_longlong(d);
-  const unsigned hi = (unsigned)(u >> 32), lo = (unsigned)u;
-  const unsigned e = (hi >> 20) & 0x7FFu;
-  const unsigned sign = hi & 0x80000000u;
-  if (e - 897u <= 253u) {
-    const unsigned m = ((hi & 0xFFFFFu) << 3) | (lo >> 29);
-    const unsigned rest = lo & 0x1FFFFFFFu;
-    unsigned bits = sign | ((e - 896u) << 23) | m;
-    bits += (rest > 0x10000000u || (rest == 0x10000000u && (m & 1u))) ? 1u : 0u;
-    return __uint_as_float(bits);
-  }
-  if ((u << 1) == 0ull) return __uint_as_float(sign);
-  return __double2float_rn(d);
-}
+// to_f32 (solid_internal.cuh): the FP64 -> FP32 rounding on the integer pipes.
 
 // The mixed path's FP64 residual never reads the FP64 inverse diagonal: it is
 // written on the FP64 path only, and the FP32 one is an FP32 reciprocal
@@ -129,21 +109,22 @@ __device__ __forceinline__ void write_row(const Sys& s, int r, int dim, double P
   }
 }
 
+// Rows first, first + stride, ... below end of the momentum system of
+// component A (the bodies below take a row range so that one launch can also
+// serve many cases of a packed batch).
 template <int A>
-__global__ void __launch_bounds__(kBlockA) k_assemble_momentum(Params pr, Sys s, const double* __restrict__ u,
-                                                              const double* __restrict__ v,
-                                                              const double* __restrict__ w, double* ustar,
-                                                              const double* __restrict__ p,
-                                                              const double* __restrict__ T,
-                                                              const double* __restrict__ Cl,
-                                                              const double* __restrict__ Kinv) {
+__device__ __forceinline__ void assemble_momentum_rows(const Params& pr, const Sys& s, const double* __restrict__ u,
+                                                       const double* __restrict__ v, const double* __restrict__ w,
+                                                       double* ustar, const double* __restrict__ p,
+                                                       const double* __restrict__ T, const double* __restrict__ Cl,
+                                                       const double* __restrict__ Kinv, int first, int stride,
+                                                       int end) {
   const Axes ax = axes_of(pr);
   const double* vel[3] = {u, v, w};
   const int mx = s.d.mx, my = s.d.my;
-  const int n = (int)s.d.n;
   const int sA = (A == 0) ? 1 : (A == 1) ? mx : mx * my;    // stride of axis A in the row grid
   const double idt = pr.idt;
-  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+  for (int r = first; r < end; r += stride) {
     const int i = r % mx, t = r / mx, j = t % my, k = t / my;
     const int idx[3] = {i, j, k};
     const int f = idx[A];
@@ -203,6 +184,18 @@ __global__ void __launch_bounds__(kBlockA) k_assemble_momentum(Params pr, Sys s,
   }
 }
 
+template <int A>
+__global__ void __launch_bounds__(kBlockA) k_assemble_momentum(Params pr, Sys s, const double* __restrict__ u,
+                                                              const double* __restrict__ v,
+                                                              const double* __restrict__ w, double* ustar,
+                                                              const double* __restrict__ p,
+                                                              const double* __restrict__ T,
+                                                              const double* __restrict__ Cl,
+                                                              const double* __restrict__ Kinv) {
+  assemble_momentum_rows<A>(pr, s, u, v, w, ustar, p, T, Cl, Kinv, blockIdx.x * blockDim.x + threadIdx.x,
+                            gridDim.x * blockDim.x, (int)s.d.n);
+}
+
 // Cell-centred systems. SOLUTE = true: solute (Eq. 3.10) with diffusivity
 // g_l^n D_l on faces and column scaling by A_g = 1/(1 - (1-k_p)(1-g_l^n));
 // false: T* (Eq. 3.12) with diffusivity k/(rho c_p) and cooled walls, whose
@@ -213,21 +206,17 @@ __global__ void __launch_bounds__(kBlockA) k_assemble_momentum(Params pr, Sys s,
 // T^n; Tinc then holds -T^n, which the lever stage completes to T* - T^n.
 // Each row reads and writes T and Tinc only at itself.
 template <bool SOLUTE>
-__global__ void __launch_bounds__(kBlockA) k_assemble_cells(Params pr, Sys s, const double* __restrict__ u,
-                                                           const double* __restrict__ v,
-                                                           const double* __restrict__ w,
-                                                           double* phi_n,
-                                                           const double* __restrict__ gl,
-                                                           const double* __restrict__ Ag,
-                                                           const double* __restrict__ time, double* Tinc,
-                                                           int use_guess) {
+__device__ __forceinline__ void assemble_cells_rows(const Params& pr, const Sys& s, const double* __restrict__ u,
+                                                    const double* __restrict__ v, const double* __restrict__ w,
+                                                    double* phi_n, const double* __restrict__ gl,
+                                                    const double* __restrict__ Ag, const double* __restrict__ time,
+                                                    double* Tinc, int use_guess, int first, int rstride, int end) {
   const Axes ax = axes_of(pr);
   const double* vel[3] = {u, v, w};
   const int nx = pr.nx, ny = pr.ny;
-  const int n = (int)s.d.n;
   const int stride[3] = {1, nx, nx * ny};
   const double idt = pr.idt;
-  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+  for (int r = first; r < end; r += rstride) {
     const int i = r % nx, t = r / nx, j = t % ny, k = t / ny;
     const int idx[3] = {i, j, k};
     double m0 = 0.0, nbB[3] = {0.0, 0.0, 0.0}, nbF[3] = {0.0, 0.0, 0.0};
@@ -285,14 +274,26 @@ __global__ void __launch_bounds__(kBlockA) k_assemble_cells(Params pr, Sys s, co
   }
 }
 
-__global__ void __launch_bounds__(kBlockA) k_poisson_rhs(Params pr, const double* __restrict__ us,
-                                                        const double* __restrict__ vs,
-                                                        const double* __restrict__ ws, double* b) {
+template <bool SOLUTE>
+__global__ void __launch_bounds__(kBlockA) k_assemble_cells(Params pr, Sys s, const double* __restrict__ u,
+                                                           const double* __restrict__ v,
+                                                           const double* __restrict__ w,
+                                                           double* phi_n,
+                                                           const double* __restrict__ gl,
+                                                           const double* __restrict__ Ag,
+                                                           const double* __restrict__ time, double* Tinc,
+                                                           int use_guess) {
+  assemble_cells_rows<SOLUTE>(pr, s, u, v, w, phi_n, gl, Ag, time, Tinc, use_guess,
+                              blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x, (int)s.d.n);
+}
+
+__device__ __forceinline__ void poisson_rhs_rows(const Params& pr, const double* __restrict__ us,
+                                                 const double* __restrict__ vs, const double* __restrict__ ws,
+                                                 double* b, int first, int stride, int end) {
   const Axes ax = axes_of(pr);
   const int nx = pr.nx, ny = pr.ny;
-  const int n = pr.nx * pr.ny * pr.nz;
   const double scale = pr.rhs_scale;
-  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+  for (int r = first; r < end; r += stride) {
     const int i = r % nx, t = r / nx, j = t % ny, k = t / ny;
     double div = (us[fidx(pr, 0, i + 1, j, k)] - us[fidx(pr, 0, i, j, k)]) * ax.ih[0] +
                  (vs[fidx(pr, 1, i, j + 1, k)] - vs[fidx(pr, 1, i, j, k)]) * ax.ih[1];
@@ -301,18 +302,27 @@ __global__ void __launch_bounds__(kBlockA) k_poisson_rhs(Params pr, const double
   }
 }
 
-// Faces of u, v, w then cells of p, one flat index space.
-__global__ void __launch_bounds__(kBlockA) k_project(Params pr, double* u, double* v, double* w,
-                                                    const double* __restrict__ us,
-                                                    const double* __restrict__ vs,
-                                                    const double* __restrict__ ws,
-                                                    const double* __restrict__ pc, double* p) {
+__global__ void __launch_bounds__(kBlockA) k_poisson_rhs(Params pr, const double* __restrict__ us,
+                                                        const double* __restrict__ vs,
+                                                        const double* __restrict__ ws, double* b) {
+  poisson_rhs_rows(pr, us, vs, ws, b, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x,
+                   pr.nx * pr.ny * pr.nz);
+}
+
+// Faces of u, v, w then cells of p, one flat index space of project_size() entries.
+__host__ __device__ __forceinline__ int project_size(const Params& pr) {
+  const int nx = pr.nx, ny = pr.ny, nz = pr.nz;
+  return (nx + 1) * ny * nz + nx * (ny + 1) * nz + ((pr.dim == 3) ? nx * ny * (nz + 1) : 0) + nx * ny * nz;
+}
+
+__device__ __forceinline__ void project_rows(const Params& pr, double* u, double* v, double* w,
+                                             const double* __restrict__ us, const double* __restrict__ vs,
+                                             const double* __restrict__ ws, const double* __restrict__ pc, double* p,
+                                             int first, int stride, int total) {
   const int nx = pr.nx, ny = pr.ny, nz = pr.nz;
   const int nu_ = (nx + 1) * ny * nz, nv = nx * (ny + 1) * nz, nw = (pr.dim == 3) ? nx * ny * (nz + 1) : 0;
-  const int nc = nx * ny * nz;
-  const int total = nu_ + nv + nw + nc;
   const double kk = pr.proj_k;
-  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < total; q += gridDim.x * blockDim.x) {
+  for (int q = first; q < total; q += stride) {
     if (q < nu_ + nv + nw) {
       int d, r;
       if (q < nu_) { d = 0; r = q; }
@@ -338,6 +348,15 @@ __global__ void __launch_bounds__(kBlockA) k_project(Params pr, double* u, doubl
   }
 }
 
+__global__ void __launch_bounds__(kBlockA) k_project(Params pr, double* u, double* v, double* w,
+                                                    const double* __restrict__ us,
+                                                    const double* __restrict__ vs,
+                                                    const double* __restrict__ ws,
+                                                    const double* __restrict__ pc, double* p) {
+  project_rows(pr, u, v, w, us, vs, ws, pc, p, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x,
+               project_size(pr));
+}
+
 struct Phase {
   double Cl, Kinv, Ag;
 };
@@ -360,18 +379,19 @@ __device__ __forceinline__ Phase phase_of(const Params& pr, double C, double g) 
   return o;
 }
 
-// The lever update closes a step: it also advances the case's time by dt.
+// The lever update closes a step: it also advances the case's time by dt
+// (done by the thread whose first row is 0).
 // Tinc (may be null): T* - T^n for the next step's initial guess when
 // form_inc (Tinc holds -T^n from this step's T* assembly), else 0.
-__global__ void __launch_bounds__(kBlockA) k_lever(Params pr, double* time, double* T, double* gl,
-                                                  const double* __restrict__ C, double* Cl, double* Cs, double* Kinv,
-                                                  double* Ag, int n, double* Tinc, int form_inc) {
-  if (blockIdx.x == 0 && threadIdx.x == 0) *time += pr.dt;
+__device__ __forceinline__ void lever_rows(const Params& pr, double* time, double* T, double* gl,
+                                           const double* __restrict__ C, double* Cl, double* Cs, double* Kinv,
+                                           double* Ag, double* Tinc, int form_inc, int first, int stride, int n) {
+  if (first == 0) *time += pr.dt;
   const double kp = pr.kp, Tm = pr.Tm;
   const double cpL = pr.cpL, Lcp = pr.Lcp;
   const double a = pr.lev_a;
   const double Te = pr.Te;
-  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+  for (int r = first; r < n; r += stride) {
     const double Ts = T[r], gn = gl[r], Cn = C[r];
     const double Tl = Tm + pr.m * Cn;                                       // Eq. 3.14
     const double b = kp - gn * a + pr.lev_cpLa * (Tm - Ts);                // Eq. 3.17
@@ -395,6 +415,13 @@ __global__ void __launch_bounds__(kBlockA) k_lever(Params pr, double* time, doub
     Kinv[r] = ph.Kinv;
     Ag[r] = ph.Ag;
   }
+}
+
+__global__ void __launch_bounds__(kBlockA) k_lever(Params pr, double* time, double* T, double* gl,
+                                                  const double* __restrict__ C, double* Cl, double* Cs, double* Kinv,
+                                                  double* Ag, int n, double* Tinc, int form_inc) {
+  lever_rows(pr, time, T, gl, C, Cl, Cs, Kinv, Ag, Tinc, form_inc, blockIdx.x * blockDim.x + threadIdx.x,
+             gridDim.x * blockDim.x, n);
 }
 
 __global__ void __launch_bounds__(kBlockA) k_equilibrate(Params pr, const double* __restrict__ T,
@@ -594,12 +621,79 @@ __global__ void __launch_bounds__(kBlockA) k_forward_cells(Params pr, Sys s, con
   }
 }
 
+// One launch of a packed stage: block b takes tiles[b], stages its case's
+// description in shared memory and runs the stage's rows of that tile. The
+// assembly stages also zero the barrier counters of their case for the
+// solve launch that follows them.
+template <int STAGE>
+__global__ void __launch_bounds__(kBlockA) k_packed_rows(const CaseRows* __restrict__ cases,
+                                                        const PackedTile* __restrict__ tiles) {
+  __shared__ __align__(16) unsigned long long buf[(sizeof(CaseRows) + 7) / 8];
+  const PackedTile t = tiles[blockIdx.x];
+  const unsigned long long* src = reinterpret_cast<const unsigned long long*>(cases + t.c);
+  for (int q = threadIdx.x; q < (int)(sizeof(CaseRows) / 8); q += blockDim.x) buf[q] = src[q];
+  __syncthreads();
+  const CaseRows& cs = *reinterpret_cast<const CaseRows*>(buf);
+  const int first = t.r0 + threadIdx.x, stride = blockDim.x, end = t.r1;
+  if (STAGE == kStageMomentum) {
+    if (t.part == 0)
+      assemble_momentum_rows<0>(cs.pr, cs.sys[0], cs.u, cs.v, cs.w, cs.ustar[0], cs.p, cs.T, cs.Cl, cs.Kinv, first,
+                                stride, end);
+    else if (t.part == 1)
+      assemble_momentum_rows<1>(cs.pr, cs.sys[1], cs.u, cs.v, cs.w, cs.ustar[1], cs.p, cs.T, cs.Cl, cs.Kinv, first,
+                                stride, end);
+    else
+      assemble_momentum_rows<2>(cs.pr, cs.sys[2], cs.u, cs.v, cs.w, cs.ustar[2], cs.p, cs.T, cs.Cl, cs.Kinv, first,
+                                stride, end);
+  } else if (STAGE == kStageRhs) {
+    poisson_rhs_rows(cs.pr, cs.ustar[0], cs.ustar[1], cs.ustar[2], cs.pb, first, stride, end);
+  } else if (STAGE == kStageProject) {
+    project_rows(cs.pr, cs.u, cs.v, cs.w, cs.ustar[0], cs.ustar[1], cs.ustar[2], cs.pc, cs.p, first, stride, end);
+  } else if (STAGE == kStageSolute) {
+    assemble_cells_rows<true>(cs.pr, cs.sys[SS_SYS_C], cs.u, cs.v, cs.w, cs.C, cs.gl, cs.Ag, nullptr, nullptr, 0, first,
+                              stride, end);
+  } else if (STAGE == kStageTemperature) {
+    assemble_cells_rows<false>(cs.pr, cs.sys[SS_SYS_T], cs.u, cs.v, cs.w, cs.T, nullptr, nullptr, &cs.st->time,
+                               cs.Tinc, 1, first, stride, end);
+  } else {
+    lever_rows(cs.pr, &cs.st->time, cs.T, cs.gl, cs.C, cs.Cl, cs.Cs, cs.Kinv, cs.Ag, cs.Tinc, 1, first, stride, end);
+  }
+  if (STAGE != kStageProject && STAGE != kStageLever && t.part == 0 && t.r0 == 0 && threadIdx.x == 0) {
+    cs.st->barrier = 0u;
+    for (int q = 0; q < kMaxTeams; ++q) cs.st->team_arrivals[q] = 0u;
+  }
+}
+
 __global__ void __launch_bounds__(kBlockA) k_to_f32(const double* __restrict__ src, float* dst, long long n) {
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x)
     dst[q] = to_f32(src[q]);
 }
 
 }  // namespace
+
+long long packed_stage_rows(int stage, const Params& pr, int part) {
+  const long long nx = pr.nx, ny = pr.ny, nz = pr.nz;
+  switch (stage) {
+    case kStageMomentum:
+      return part == 0 ? (nx + 1) * ny * nz : part == 1 ? nx * (ny + 1) * nz : nx * ny * (nz + 1);
+    case kStageProject: return project_size(pr);
+    default: return nx * ny * nz;
+  }
+}
+
+cudaError_t launch_packed_rows(int stage, const CaseRows* cases, const PackedTile* tiles, int ntiles, cudaStream_t st) {
+  if (ntiles <= 0) return cudaSuccess;
+  switch (stage) {
+    case kStageMomentum: k_packed_rows<kStageMomentum><<<ntiles, kBlockA, 0, st>>>(cases, tiles); break;
+    case kStageRhs: k_packed_rows<kStageRhs><<<ntiles, kBlockA, 0, st>>>(cases, tiles); break;
+    case kStageProject: k_packed_rows<kStageProject><<<ntiles, kBlockA, 0, st>>>(cases, tiles); break;
+    case kStageSolute: k_packed_rows<kStageSolute><<<ntiles, kBlockA, 0, st>>>(cases, tiles); break;
+    case kStageTemperature: k_packed_rows<kStageTemperature><<<ntiles, kBlockA, 0, st>>>(cases, tiles); break;
+    case kStageLever: k_packed_rows<kStageLever><<<ntiles, kBlockA, 0, st>>>(cases, tiles); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
 
 cudaError_t launch_to_f32(const double* src, float* dst, long long n, cudaStream_t st) {
   k_to_f32<<<grid_for(n), kBlockA, 0, st>>>(src, dst, n);
@@ -658,8 +752,7 @@ cudaError_t launch_poisson_rhs(const Params& pr, const double* const ustar[3], d
 
 cudaError_t launch_project(const Params& pr, double* const vel[3], const double* const ustar[3], const double* pc,
                            double* p, cudaStream_t st) {
-  const long long nx = pr.nx, ny = pr.ny, nz = pr.nz;
-  const long long total = (nx + 1) * ny * nz + nx * (ny + 1) * nz + (pr.dim == 3 ? nx * ny * (nz + 1) : 0) + nx * ny * nz;
+  const long long total = project_size(pr);
   k_project<<<grid_for(total), kBlockA, 0, st>>>(pr, vel[0], vel[1], vel[2], ustar[0], ustar[1], ustar[2], pc, p);
   return cudaGetLastError();
 }

@@ -420,7 +420,7 @@ constexpr double kInnerTolPressure = 3.0e-6;
 constexpr double kInnerTolEnergy = 1.0e-4;
 constexpr double kInnerTolTransport = 1.0e-5;
 
-ss_status stage_solve(ss_case* c, int sys) {
+ss_status stage_solve(ss_case* c, int sys, bool fuse_project = false) {
   StageTimer tm(c, SS_PROF_SOLVE + (sys >= 0 && sys < SS_NSYS ? sys : 0), 1);
   SolverCtl ctl;
   ctl.mixed = c->g.precision == SS_MIXED;
@@ -434,11 +434,16 @@ ss_status stage_solve(ss_case* c, int sys) {
     // the correction of the previous step (zero in a new case and after
     // ss_set_fields) starts the mixed multigrid solve; the Jacobi and FP64
     // solves start from zero
-    ctl.warm_start = 1;
+    // (the FP64 transform solve converges in one sweep: a warm start would
+    // only add a residual pass)
+    ctl.warm_start = !(c->g.precond_p == SS_PRECOND_DCT && c->g.precision == SS_FP64);
     if (c->g.precond_p == SS_PRECOND_MG)
       e = launch_pcg_mg(c->mg, c->pr, c->pb, c->pc, ctl, c->sc[0], c->st, c->stream);
-    else if (c->g.precond_p == SS_PRECOND_DCT)
-      e = launch_poisson_dct(c->dct, c->pr, c->pb, c->pc, ctl, c->sc[0], c->st, c->stream);
+    else if (c->g.precond_p == SS_PRECOND_DCT) {
+      ProjectPtrs pj{{c->u, c->v, c->w}, {c->ustar[0], c->ustar[1], c->ustar[2]}, c->p};
+      e = launch_poisson_dct(c->dct, c->pr, c->pb, c->pc, ctl, c->sc[0], c->st, fuse_project ? &pj : nullptr,
+                             c->stream);
+    }
     else
       e = launch_pcg_poisson(c->pr, c->pb, c->pc, ctl, c->sc[0], c->st, c->stream);
   } else if (sys >= 0 && sys < SS_NSYS) {
@@ -532,8 +537,12 @@ ss_status one_step(ss_case* c) {
     }
   }
   STAGE_TRY(stage_assemble(c, SS_SYS_P));     // 2: pressure correction (Eq. 3.4)
-  STAGE_TRY(stage_solve(c, SS_SYS_P));
-  STAGE_TRY(stage_project(c));                // 3: projection (Eq. 3.5)
+  if (c->g.precond_p == SS_PRECOND_DCT) {
+    STAGE_TRY(stage_solve(c, SS_SYS_P, true)); // 3: the transform solve ends with the projection (Eq. 3.5)
+  } else {
+    STAGE_TRY(stage_solve(c, SS_SYS_P));
+    STAGE_TRY(stage_project(c));              // 3: projection (Eq. 3.5)
+  }
   STAGE_TRY(stage_assemble(c, SS_SYS_C));     // 4: solute (Eq. 3.10)
   STAGE_TRY(stage_solve(c, SS_SYS_C));
   STAGE_TRY(stage_assemble(c, SS_SYS_T));     // 5-6: T* (Eq. 3.12); T_l is formed in the lever stage
@@ -558,6 +567,176 @@ ss_status read_status(ss_case* c, DevStatus* host) {
   if (host->sticky == SS_ENAN) return fail(SS_ENAN, "a non-finite residual appeared in a solve");
   if (host->sticky == SS_ENOTCONV) return fail(SS_ENOTCONV, "a solve reached its iteration cap");
   return SS_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- packed batches
+//
+// A batch steps many cases with one launch per stage of Algorithm 1: the
+// assembly and pointwise stages take a packed list of (case, row tile) items,
+// the solves one cooperative launch in which each case is solved by its own
+// team of blocks (sized from its cells by the schedule). The batch's device
+// tables live in a workspace the caller provides; the cases keep their own.
+struct ss_batch {
+  std::vector<ss_case*>* cases;
+  cudaStream_t stream;
+  char* ws;
+  size_t ws_bytes;
+  CaseRows* rows;                             // [n]
+  char* bcg[3];                               // PackedBcgTeam [n]: momentum, solute, temperature
+  char* dct;                                  // DctArgs<float> [n]
+  int* first;                                 // [n + 1] first block of each team
+  PackedTile* tiles[kNumPackedStages];
+  int ntiles[kNumPackedStages];
+  int cap_tiles[kNumPackedStages];
+  std::vector<int>* team_blocks;              // host copy of the team sizes
+  int max_blocks;                             // blocks one packed solve launch may keep resident
+  int nblocks;                                // blocks of the packed solve launches
+  size_t dct_smem;
+  double gamma;                               // team size ~ cells^gamma
+  int tile_rows;                              // rows per tile of the packed stages
+  cudaGraphExec_t graph;
+  long long launches;
+};
+
+namespace {
+
+constexpr int kMinTileRows = 256;
+constexpr int kPackedLaunchesPerStep = 9;
+constexpr int kMaxTileRows = 1 << 24;
+
+int stage_parts(int stage, const ss_case* c) { return stage == kStageMomentum ? c->pr.dim : 1; }
+
+long long stage_tiles(int stage, const ss_case* c, int tile_rows) {
+  long long t = 0;
+  for (int part = 0; part < stage_parts(stage, c); ++part)
+    t += (packed_stage_rows(stage, c->pr, part) + tile_rows - 1) / tile_rows;
+  return t;
+}
+
+// Walk of the batch workspace (the same walk sizes it and places the tables).
+template <class F>
+size_t batch_layout(ss_case* const* cs, int n, char* base, F&& place) {
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    char* p = base ? base + off : nullptr;
+    off += (bytes + 255) & ~(size_t)255;
+    return p;
+  };
+  place(0, take((size_t)n * sizeof(CaseRows)));
+  for (int q = 0; q < 3; ++q) place(1 + q, take((size_t)n * packed_bcg_team_bytes()));
+  place(4, take((size_t)n * packed_dct_args_bytes()));
+  place(5, take((size_t)(n + 1) * sizeof(int)));
+  for (int st = 0; st < kNumPackedStages; ++st) {
+    long long t = 0;
+    for (int q = 0; q < n && st != kStageProject; ++q) t += stage_tiles(st, cs[q], kMinTileRows);
+    place(6 + st, take((size_t)t * sizeof(PackedTile)));
+  }
+  return off;
+}
+
+ss_status batch_check(ss_case* const* cs, int n) {
+  if (!cs || n < 1) return fail(SS_EINVAL, "a batch needs at least one case");
+  for (int q = 0; q < n; ++q) {
+    const ss_case* c = cs[q];
+    if (!c) return fail(SS_EINVAL, "case %d is NULL", q);
+    if (!c->alloy_set) return fail(SS_ESTATE, "case %d: set_alloy first", q);
+    if (c->g.precision != SS_MIXED || c->g.precond_p != SS_PRECOND_DCT)
+      return fail(SS_EINVAL, "case %d: packed batches take SS_MIXED cases with the SS_PRECOND_DCT pressure solver", q);
+    for (int r = 0; r < q; ++r)
+      if (cs[r] == c) return fail(SS_EINVAL, "case %d appears twice", q);
+  }
+  return SS_OK;
+}
+
+// Team sizes (blocks per case) and row tiles for the current schedule, uploaded.
+ss_status batch_schedule(ss_batch* b) {
+  std::vector<ss_case*>& cs = *b->cases;
+  const int n = (int)cs.size();
+  std::vector<double> w(n);
+  std::vector<long long> want(n);
+  double wsum = 0.0;
+  for (int q = 0; q < n; ++q) {
+    w[q] = std::pow((double)cs[q]->n_cell, b->gamma);
+    wsum += w[q];
+    want[q] = blocks_wanted(cs[q]->n_cell);
+  }
+  std::vector<int>& blk = *b->team_blocks;
+  blk.assign(n, 1);
+  long long tot = 0;
+  for (int q = 0; q < n; ++q) {
+    long long v = (long long)std::floor((double)b->max_blocks * w[q] / wsum);
+    blk[q] = (int)std::max(1LL, std::min(v, want[q]));
+    tot += blk[q];
+  }
+  while (tot > b->max_blocks) {            // the floor of 1 block per case can overshoot
+    int big = 0;
+    for (int q = 1; q < n; ++q) if (blk[q] > blk[big]) big = q;
+    if (blk[big] <= 1) return fail(SS_EINVAL, "%d cases exceed the %d resident blocks of a packed launch", n,
+                                   b->max_blocks);
+    --blk[big];
+    --tot;
+  }
+  while (tot < b->max_blocks) {            // hand spare blocks to the case with most cells per block
+    int best = -1;
+    for (int q = 0; q < n; ++q)
+      if (blk[q] < want[q] && (best < 0 || (double)cs[q]->n_cell / blk[q] > (double)cs[best]->n_cell / blk[best]))
+        best = q;
+    if (best < 0) break;
+    ++blk[best];
+    ++tot;
+  }
+  std::vector<int> first(n + 1, 0);
+  for (int q = 0; q < n; ++q) first[q + 1] = first[q] + blk[q];
+  b->nblocks = first[n];
+  CUDA_TRY(cudaMemcpyAsync(b->first, first.data(), (n + 1) * sizeof(int), cudaMemcpyHostToDevice, b->stream));
+  for (int st = 0; st < kNumPackedStages; ++st) {
+    std::vector<PackedTile> t;
+    for (int q = 0; q < n && st != kStageProject; ++q)   // the pressure solve projects
+      for (int part = 0; part < stage_parts(st, cs[q]); ++part) {
+        const long long rows = packed_stage_rows(st, cs[q]->pr, part);
+        for (long long r0 = 0; r0 < rows; r0 += b->tile_rows)
+          t.push_back({q, part, (int)r0, (int)std::min(rows, r0 + (long long)b->tile_rows)});
+      }
+    if ((int)t.size() > b->cap_tiles[st]) return fail(SS_EINVAL, "tile table of stage %d overflows", st);
+    b->ntiles[st] = (int)t.size();
+    if (!t.empty())
+      CUDA_TRY(cudaMemcpyAsync(b->tiles[st], t.data(), t.size() * sizeof(PackedTile), cudaMemcpyHostToDevice,
+                               b->stream));
+  }
+  CUDA_TRY(cudaStreamSynchronize(b->stream));
+  return SS_OK;
+}
+
+ss_status batch_one_step(ss_batch* b) {
+  const int n = (int)b->cases->size();
+  cudaStream_t s = b->stream;
+  cudaError_t e;
+#define PACKED_TRY(expr)                                                              \
+  do {                                                                                \
+    if ((e = (expr)) != cudaSuccess) return fail(SS_ECUDA, "%s: %s", #expr, cudaGetErrorString(e)); \
+  } while (0)
+  PACKED_TRY(launch_packed_rows(kStageMomentum, b->rows, b->tiles[kStageMomentum], b->ntiles[kStageMomentum], s));
+  PACKED_TRY(launch_bicgstab_packed(b->bcg[0], b->first, n, b->nblocks, s));
+  PACKED_TRY(launch_packed_rows(kStageRhs, b->rows, b->tiles[kStageRhs], b->ntiles[kStageRhs], s));
+  PACKED_TRY(launch_poisson_dct_packed(b->dct, b->first, n, b->nblocks, b->dct_smem, s));   // ends with Eq. 3.5
+  PACKED_TRY(launch_packed_rows(kStageSolute, b->rows, b->tiles[kStageSolute], b->ntiles[kStageSolute], s));
+  PACKED_TRY(launch_bicgstab_packed(b->bcg[1], b->first, n, b->nblocks, s));
+  PACKED_TRY(launch_packed_rows(kStageTemperature, b->rows, b->tiles[kStageTemperature],
+                                b->ntiles[kStageTemperature], s));
+  PACKED_TRY(launch_bicgstab_packed(b->bcg[2], b->first, n, b->nblocks, s));
+  PACKED_TRY(launch_packed_rows(kStageLever, b->rows, b->tiles[kStageLever], b->ntiles[kStageLever], s));
+#undef PACKED_TRY
+  b->launches += kPackedLaunchesPerStep;
+  return SS_OK;
+}
+
+void batch_drop_graph(ss_batch* b) {
+  if (b->graph) {
+    cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+  }
 }
 
 }  // namespace
@@ -976,6 +1155,197 @@ ss_status ss_wait_selftest(ss_case* c) {
   CUDA_TRY(cudaMemsetAsync(&c->st->selftest_counter, 0, sizeof(unsigned int), c->stream));
   k_wait_selftest<<<1, 32, 0, c->stream>>>(c->st);
   CUDA_TRY(cudaGetLastError());
+  return SS_OK;
+}
+
+ss_status ss_batch_workspace_bytes(ss_case* const* cases, int n, size_t* bytes) {
+  if (!bytes) return fail(SS_EINVAL, "bytes is NULL");
+  STAGE_TRY(batch_check(cases, n));
+  *bytes = batch_layout(cases, n, nullptr, [](int, char*) {});
+  return SS_OK;
+}
+
+ss_status ss_batch_create(ss_case* const* cases, int n, void* workspace, size_t workspace_bytes, void* stream,
+                          ss_batch** out) {
+  if (!out) return fail(SS_EINVAL, "out is NULL");
+  *out = nullptr;
+  size_t need = 0;
+  STAGE_TRY(ss_batch_workspace_bytes(cases, n, &need));
+  if (!workspace) return fail(SS_EINVAL, "workspace is NULL");
+  if (((uintptr_t)workspace & 255) != 0) return fail(SS_EINVAL, "workspace must be 256-byte aligned");
+  if (workspace_bytes < need) return fail(SS_ENOMEM, "batch workspace has %zu bytes, needs %zu", workspace_bytes, need);
+  ss_batch* b = new (std::nothrow) ss_batch;
+  if (!b) return fail(SS_ENOMEM, "host allocation failed");
+  memset(b, 0, sizeof *b);
+  b->cases = new (std::nothrow) std::vector<ss_case*>(cases, cases + n);
+  b->team_blocks = new (std::nothrow) std::vector<int>();
+  if (!b->cases || !b->team_blocks) {
+    delete b->cases;
+    delete b->team_blocks;
+    delete b;
+    return fail(SS_ENOMEM, "host allocation failed");
+  }
+  b->stream = (cudaStream_t)stream;
+  b->ws = (char*)workspace;
+  b->ws_bytes = workspace_bytes;
+  b->gamma = 1.0;
+  b->tile_rows = 4096;
+  char* slot[6 + kNumPackedStages] = {nullptr};
+  batch_layout(cases, n, b->ws, [&](int k, char* p) { slot[k] = p; });
+  b->rows = reinterpret_cast<CaseRows*>(slot[0]);
+  for (int q = 0; q < 3; ++q) b->bcg[q] = slot[1 + q];
+  b->dct = slot[4];
+  b->first = reinterpret_cast<int*>(slot[5]);
+  for (int st = 0; st < kNumPackedStages; ++st) {
+    b->tiles[st] = reinterpret_cast<PackedTile*>(slot[6 + st]);
+    long long t = 0;
+    for (int q = 0; q < n && st != kStageProject; ++q) t += stage_tiles(st, cases[q], kMinTileRows);
+    b->cap_tiles[st] = (int)t;
+  }
+  // per-case descriptions and solver arguments, built on the host once
+  const size_t bt = packed_bcg_team_bytes(), da = packed_dct_args_bytes();
+  std::vector<CaseRows> rows(n);
+  std::vector<char> bcg(3 * (size_t)n * bt), dct((size_t)n * da);
+  b->dct_smem = 0;
+  for (int q = 0; q < n; ++q) {
+    ss_case* c = cases[q];
+    CaseRows& r = rows[q];
+    memset(&r, 0, sizeof r);
+    r.pr = c->pr;
+    for (int k = 0; k < SS_NSYS; ++k) r.sys[k] = c->sys[k];
+    r.u = c->u; r.v = c->v; r.w = c->w; r.p = c->p; r.T = c->T; r.C = c->C; r.gl = c->gl; r.Cl = c->Cl;
+    r.Cs = c->Cs; r.Kinv = c->Kinv; r.Ag = c->Ag; r.pc = c->pc; r.pb = c->pb; r.Tinc = c->Tinc;
+    for (int a = 0; a < 3; ++a) r.ustar[a] = c->ustar[a];
+    r.st = c->st;
+    SolverCtl ctl[3];
+    const Sys* sys[3];
+    for (int a = 0; a < c->pr.dim; ++a) {
+      ctl[a].mixed = 1; ctl[a].block_cap = 0; ctl[a].stat_index = a; ctl[a].inner_tol = kInnerTolTransport;
+      ctl[a].tol = c->g.tol_t; ctl[a].max_it = c->g.max_it_t;
+      sys[a] = &c->sys[a];
+    }
+    fill_packed_bcg_team(&bcg[(0 * (size_t)n + q) * bt], sys, c->pr.dim, c->pr.dim == 3, ctl, c->sc[0], c->st);
+    SolverCtl cc = ctl[0];
+    cc.stat_index = SS_SYS_C;
+    sys[0] = &c->sys[SS_SYS_C];
+    fill_packed_bcg_team(&bcg[(1 * (size_t)n + q) * bt], sys, 1, c->pr.dim == 3, &cc, c->sc[0], c->st);
+    SolverCtl ct = ctl[0];
+    ct.stat_index = SS_SYS_T;
+    ct.inner_tol = kInnerTolEnergy;
+    sys[0] = &c->sys[SS_SYS_T];
+    fill_packed_bcg_team(&bcg[(2 * (size_t)n + q) * bt], sys, 1, c->pr.dim == 3, &ct, c->sc[0], c->st);
+    SolverCtl cp;
+    cp.mixed = 1; cp.block_cap = 0; cp.stat_index = SS_SYS_P; cp.inner_tol = kInnerTolPressure;
+    cp.warm_start = 1;
+    cp.tol = c->g.tol_p; cp.max_it = c->g.max_it_p;
+    ProjectPtrs pj{{c->u, c->v, c->w}, {c->ustar[0], c->ustar[1], c->ustar[2]}, c->p};
+    const size_t sm = fill_packed_dct_args(&dct[(size_t)q * da], c->dct, c->pr, c->pb, c->pc, cp, c->sc[0], c->st, &pj);
+    b->dct_smem = std::max(b->dct_smem, sm);
+  }
+  const int lim_d = packed_dct_max_blocks(b->dct_smem);
+  b->max_blocks = std::min(packed_bcg_max_blocks(), lim_d);
+  for (int q = 0; q < n; ++q) b->max_blocks = std::min(b->max_blocks, cases[q]->sc[0].max_blocks);
+  cudaError_t e = cudaSuccess;
+  for (int q = 0; q < n && e == cudaSuccess; ++q) e = cudaStreamSynchronize(cases[q]->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(b->rows, rows.data(), n * sizeof(CaseRows), cudaMemcpyHostToDevice, b->stream);
+  for (int q = 0; q < 3 && e == cudaSuccess; ++q)
+    e = cudaMemcpyAsync(b->bcg[q], &bcg[(size_t)q * n * bt], n * bt, cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(b->dct, dct.data(), n * da, cudaMemcpyHostToDevice, b->stream);
+  ss_status s = SS_OK;
+  if (e != cudaSuccess) s = fail(SS_ECUDA, "batch tables: %s", cudaGetErrorString(e));
+  else if (b->max_blocks < n) s = fail(SS_EINVAL, "%d cases exceed the %d resident blocks of a packed launch", n,
+                                       b->max_blocks);
+  else s = batch_schedule(b);
+  if (s != SS_OK) {
+    delete b->cases;
+    delete b->team_blocks;
+    delete b;
+    return s;
+  }
+  *out = b;
+  return SS_OK;
+}
+
+ss_status ss_batch_set_schedule(ss_batch* b, double gamma, int tile_rows) {
+  if (!b) return fail(SS_EINVAL, "batch is NULL");
+  if (!(gamma >= 0.0 && gamma <= 2.0)) return fail(SS_EINVAL, "gamma must be in [0, 2]");
+  if (tile_rows < kMinTileRows || tile_rows > kMaxTileRows)
+    return fail(SS_EINVAL, "tile_rows must be in [%d, %d]", kMinTileRows, kMaxTileRows);
+  CUDA_TRY(cudaStreamSynchronize(b->stream));
+  batch_drop_graph(b);
+  b->gamma = gamma;
+  b->tile_rows = tile_rows;
+  return batch_schedule(b);
+}
+
+ss_status ss_batch_get_teams(ss_batch* b, int* blocks) {
+  if (!b || !blocks) return fail(SS_EINVAL, "batch or blocks is NULL");
+  for (size_t q = 0; q < b->team_blocks->size(); ++q) blocks[q] = (*b->team_blocks)[q];
+  return SS_OK;
+}
+
+ss_status ss_batch_step(ss_batch* b, int n) {
+  if (!b) return fail(SS_EINVAL, "batch is NULL");
+  if (n < 0) return fail(SS_EINVAL, "n must be >= 0");
+  if (n == 0) return SS_OK;
+  if (b->stream == nullptr) {                  // the legacy default stream cannot be captured
+    for (int k = 0; k < n; ++k) STAGE_TRY(batch_one_step(b));
+  } else {
+    if (!b->graph) {
+      const long long before = b->launches;
+      CUDA_TRY(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+      ss_status s = batch_one_step(b);
+      cudaGraph_t g = nullptr;
+      cudaError_t e = cudaStreamEndCapture(b->stream, &g);
+      b->launches = before;                    // the capture launched nothing
+      if (s != SS_OK) {
+        if (g) cudaGraphDestroy(g);
+        return s;
+      }
+      if (e != cudaSuccess) return fail(SS_ECUDA, "batch capture: %s", cudaGetErrorString(e));
+      e = cudaGraphInstantiate(&b->graph, g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) {
+        b->graph = nullptr;
+        return fail(SS_ECUDA, "batch graph instantiate: %s", cudaGetErrorString(e));
+      }
+    }
+    for (int k = 0; k < n; ++k) CUDA_TRY(cudaGraphLaunch(b->graph, b->stream));
+    b->launches += (long long)kPackedLaunchesPerStep * n;
+  }
+  for (ss_case* c : *b->cases) {
+    c->steps += n;
+    c->tinc_pending = 0;
+  }
+  return SS_OK;
+}
+
+ss_status ss_batch_sync(ss_batch* b, long long* launches) {
+  if (!b) return fail(SS_EINVAL, "batch is NULL");
+  CUDA_TRY(cudaStreamSynchronize(b->stream));
+  if (launches) *launches = b->launches;
+  ss_status worst = SS_OK;
+  char msg[512] = "";
+  for (ss_case* c : *b->cases) {
+    DevStatus h;
+    ss_status s = read_status(c, &h);
+    if (s != SS_OK && (worst == SS_OK || s > worst)) {
+      worst = s;
+      snprintf(msg, sizeof msg, "%s", g_err);
+    }
+  }
+  if (worst != SS_OK) return fail(worst, "%s", msg);
+  return SS_OK;
+}
+
+ss_status ss_batch_destroy(ss_batch* b) {
+  if (!b) return SS_OK;
+  cudaError_t e = cudaStreamSynchronize(b->stream);
+  batch_drop_graph(b);
+  delete b->cases;
+  delete b->team_blocks;
+  delete b;
+  if (e != cudaSuccess) return fail(SS_ECUDA, "batch destroy: %s", cudaGetErrorString(e));
   return SS_OK;
 }
 

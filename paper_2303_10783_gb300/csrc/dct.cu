@@ -74,10 +74,18 @@ struct DctArgs {
   double tol;
   int max_sweeps;
   int stat_index;
+  int warm;                 // start from the x in place (else from 0)
   int thomas_cols;          // columns per shared-memory chunk of the tridiagonal solves
   double* partial;
   int max_blocks;
   DevStatus* st;
+  // projection (Eq. 3.5) after the solve, when p is not null:
+  // u^{n+1} = u* - (dt/rho) grad p' on the faces, p += p'
+  double* p;
+  double* vel[3];
+  const double* us[3];
+  double proj_k;
+  double ih[3];
 };
 
 template <typename T>
@@ -92,6 +100,16 @@ __device__ __forceinline__ void lds4<double>(const double* p, double v[4]) {
   const double2 a = *reinterpret_cast<const double2*>(p), b = *reinterpret_cast<const double2*>(p + 2);
   v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
 }
+
+// FP64 <-> transform type, the FP32 conversions on the integer pipes
+template <typename TP>
+__device__ __forceinline__ TP narrow(double v);
+template <>
+__device__ __forceinline__ float narrow<float>(double v) { return to_f32(v); }
+template <>
+__device__ __forceinline__ double narrow<double>(double v) { return v; }
+__device__ __forceinline__ double widen(float v) { return to_f64(v); }
+__device__ __forceinline__ double widen(double v) { return v; }
 
 // One BM x BN tile of C(m, n) = sum_k A(m, k) B(k, n), m in [m0, m0+BM) and
 // n in [n0, n0+BN), entries beyond M, N, K taken as 0. la(m, k) and lb(k, n)
@@ -260,16 +278,16 @@ __device__ __forceinline__ double lap64(const double* v, int c, int i, int j, in
 
 // Pass A: T1 = (Cx ⊗ I) ((src - shift) * scale)
 template <typename TP>
-__device__ void pass_a(const DctArgs<TP>& A, const double* src, double shift, double scale, TP* sm) {
+__device__ void pass_a(const DctArgs<TP>& A, const Team& tm, const double* src, double shift, double scale, TP* sm) {
   const int Mx = A.Mx, R = A.R;
   const int mt = (Mx + BM - 1) / BM, nt = (R + BN - 1) / BN;
   const TP* Cx = A.Cx;
   TP* T1 = A.T1;
-  for (int tile = blockIdx.x; tile < mt * nt; tile += gridDim.x) {
+  for (int tile = tm.rank; tile < mt * nt; tile += tm.size) {
     const int m0 = (tile % mt) * BM, n0 = (tile / mt) * BN;
     gemm_tile<TP>(
         Mx, R, Mx, m0, n0, [&](int m, int k) { return Cx[(size_t)m * Mx + k]; }, true,
-        [&](int k, int n) { return (TP)((src[(size_t)n * Mx + k] - shift) * scale); }, true,
+        [&](int k, int n) { return narrow<TP>(fma(src[(size_t)n * Mx + k], scale, -shift * scale)); }, true,
         [&](int m, int n, TP v) { T1[(size_t)m * R + n] = v; }, false, sm);
   }
 }
@@ -277,7 +295,7 @@ __device__ void pass_a(const DctArgs<TP>& A, const double* src, double shift, do
 // Pass B: per mode kx, the transform along y, the tridiagonal solves along t
 // and the inverse transform along y (3D); in 2D only the tridiagonal solves.
 template <typename TP>
-__device__ void pass_b(const DctArgs<TP>& A, TP* sm) {
+__device__ void pass_b(const DctArgs<TP>& A, const Team& tm, TP* sm) {
   const int Mx = A.Mx, My = A.My, Mt = A.Mt, R = A.R;
   const TP* lx = A.lx;
   const TP* ly = A.ly;
@@ -286,7 +304,7 @@ __device__ void pass_b(const DctArgs<TP>& A, TP* sm) {
   const int w = A.thomas_cols;
   if (A.dim == 2) {
     // columns are the modes kx, each a contiguous line of Mt values in T1
-    for (int c0 = blockIdx.x * w; c0 < Mx; c0 += gridDim.x * w) {
+    for (int c0 = tm.rank * w; c0 < Mx; c0 += tm.size * w) {
       const int cw = (Mx - c0 < w) ? Mx - c0 : w;
       thomas_chunk<TP>(
           A.T1, 1, R, Mt, c0, cw, at, [&](int c) { return lx[c]; }, [&](int c) { return c == 0; }, sm);
@@ -294,7 +312,7 @@ __device__ void pass_b(const DctArgs<TP>& A, TP* sm) {
     return;
   }
   const int mt = (My + BM - 1) / BM, nt = (Mt + BN - 1) / BN;
-  for (int kx = blockIdx.x; kx < Mx; kx += gridDim.x) {
+  for (int kx = tm.rank; kx < Mx; kx += tm.size) {
     TP* S1 = A.T1 + (size_t)kx * R;   // [t][j]
     TP* S2 = A.T2 + (size_t)kx * R;   // [t][ky]
     for (int tile = 0; tile < mt * nt; ++tile) {
@@ -325,29 +343,29 @@ __device__ void pass_b(const DctArgs<TP>& A, TP* sm) {
 
 // Pass C: x += rn * (Cx^T ⊗ I) T1
 template <typename TP>
-__device__ void pass_c(const DctArgs<TP>& A, double rn, TP* sm) {
+__device__ void pass_c(const DctArgs<TP>& A, const Team& tm, double rn, TP* sm) {
   const int Mx = A.Mx, R = A.R;
   const int mt = (Mx + BM - 1) / BM, nt = (R + BN - 1) / BN;
   const TP* Cx = A.Cx;
   const TP* T1 = A.T1;
   double* x = A.x;
-  for (int tile = blockIdx.x; tile < mt * nt; tile += gridDim.x) {
+  for (int tile = tm.rank; tile < mt * nt; tile += tm.size) {
     const int m0 = (tile % mt) * BM, n0 = (tile / mt) * BN;
     gemm_tile<TP>(
         Mx, R, Mx, m0, n0, [&](int m, int k) { return Cx[(size_t)k * Mx + m]; }, false,
         [&](int k, int n) { return T1[(size_t)k * R + n]; }, false,
         [&](int m, int n, TP v) {
           const size_t c = (size_t)n * Mx + m;
-          x[c] = fma(rn, (double)v, x[c]);
+          x[c] = fma(rn, widen(v), x[c]);
         },
         true, sm);
   }
 }
 
+// The whole solve by one team of blocks (a whole grid is one team); sm is the
+// block's dynamic shared memory. Returns false if a barrier gave up.
 template <typename TP>
-__global__ void __launch_bounds__(kBlock, 1) k_poisson_dct(DctArgs<TP> A) {
-  extern __shared__ __align__(16) unsigned char dsm[];
-  TP* sm = reinterpret_cast<TP*>(dsm);
+__device__ bool poisson_dct_team(const DctArgs<TP>& A, const Team& tm, TP* sm) {
   __shared__ double s_diag[27];
   if (threadIdx.x < 27) {
     const int c = threadIdx.x;
@@ -356,7 +374,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_poisson_dct(DctArgs<TP> A) {
   __syncthreads();
   unsigned int epoch = 0;
   const int n = A.n;
-  const int t0 = blockIdx.x * blockDim.x + threadIdx.x, gsz = gridDim.x * blockDim.x;
+  const int t0 = tm.rank * blockDim.x + threadIdx.x, gsz = tm.size * blockDim.x;
   double* b = A.b;
   double* x = A.x;
   double* r = A.r;
@@ -368,38 +386,57 @@ __global__ void __launch_bounds__(kBlock, 1) k_poisson_dct(DctArgs<TP> A) {
   // consistency: remove the mean of the right-hand side (Neumann null space)
   Vec<1> sb = {{0.0}};
   for (int c = t0; c < n; c += gsz) sb.v[0] += b[c];
-  if (!grid_sum_post<1>(sb, A.partial, A.max_blocks, 0, A.st, epoch,
+  if (!team_sum_post<1>(sb, tm, A.max_blocks, 0, A.st, epoch,
                         [&](const double* tot) { ds.mean = tot[0] / (double)n; }))
-    return;
+    return false;
   const double mean_b = ds.mean;
-  Vec<1> s2 = {{0.0}};
+  // Warm start: the x in place (the previous step's correction) is the first
+  // iterate and r = b - A x the first residual; cold start: x = 0 and the
+  // first residual is b itself.
+  const bool warm = A.warm != 0;
+  Vec<3> s2 = {{0.0, 0.0, 0.0}};
   for (int c = t0; c < n; c += gsz) {
     const double bc = b[c] - mean_b;
     b[c] = bc;
-    x[c] = 0.0;
     s2.v[0] += bc * bc;
+    if (warm) {
+      int i, j, k;
+      decompose3(c, A.fx, A.fy, i, j, k);
+      const int code = ((i > 0) + (i < A.nx - 1)) + 3 * ((j > 0) + (j < A.ny - 1)) + 9 * ((k > 0) + (k < A.nz - 1));
+      const double rc = bc - lap64(x, c, i, j, k, A.nx, A.ny, A.nz, A.cx, A.cy, A.cz, s_diag[code]);
+      r[c] = rc;
+      s2.v[1] += rc;
+      s2.v[2] += rc * rc;
+    } else {
+      x[c] = 0.0;
+    }
   }
-  if (!grid_sum_post<1>(s2, A.partial, A.max_blocks, 1, A.st, epoch, [&](const double* tot) {
+  if (!team_sum_post<3>(s2, tm, A.max_blocks, 1, A.st, epoch, [&](const double* tot) {
         ds.bn = sqrt(tot[0]);
-        ds.rn = ds.bn;
-        ds.rmean = 0.0;
-        ds.inv = 1.0 / ds.bn;
         thr = A.tol * ds.bn;
-        ds.conv = ds.bn == 0.0;
-        ds.go = ds.bn > 0.0 && isfinite(ds.bn);
+        if (warm) {   // the part of r outside the constants, as after each sweep
+          ds.rmean = tot[1] / (double)n;
+          ds.rn = sqrt(fmax(tot[2] - (double)n * ds.rmean * ds.rmean, 0.0));
+        } else {
+          ds.rmean = 0.0;
+          ds.rn = ds.bn;
+        }
+        ds.inv = 1.0 / ds.rn;
+        ds.conv = ds.bn == 0.0 || ds.rn <= thr;
+        ds.go = !ds.conv && isfinite(ds.rn);
       }))
-    return;
+    return false;
   int sweeps = 0;
-  const double* src = b;   // x = 0: the first residual is b itself
+  const double* src = warm ? r : b;
   while (ds.go && sweeps < A.max_sweeps) {
     ++sweeps;
     const double shift = ds.rmean, scale = ds.inv, rn = ds.rn;
-    pass_a<TP>(A, src, shift, scale, sm);
-    if (!grid_barrier(A.st, gridDim.x, epoch)) return;
-    pass_b<TP>(A, sm);
-    if (!grid_barrier(A.st, gridDim.x, epoch)) return;
-    pass_c<TP>(A, rn, sm);
-    if (!grid_barrier(A.st, gridDim.x, epoch)) return;
+    pass_a<TP>(A, tm, src, shift, scale, sm);
+    if (!team_barrier(A.st, tm, epoch)) return false;
+    pass_b<TP>(A, tm, sm);
+    if (!team_barrier(A.st, tm, epoch)) return false;
+    pass_c<TP>(A, tm, rn, sm);
+    if (!team_barrier(A.st, tm, epoch)) return false;
     Vec<2> s = {{0.0, 0.0}};
     for (int c = t0; c < n; c += gsz) {
       int i, j, k;
@@ -410,7 +447,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_poisson_dct(DctArgs<TP> A) {
       s.v[0] += rc;
       s.v[1] += rc * rc;
     }
-    if (!grid_sum_post<2>(s, A.partial, A.max_blocks, 2, A.st, epoch, [&](const double* tot) {
+    if (!team_sum_post<2>(s, tm, A.max_blocks, 2, A.st, epoch, [&](const double* tot) {
           // norm of the part of r outside the constants: sum (r - mean)^2
           const double rmean = tot[0] / (double)n;
           const double rn_new = sqrt(fmax(tot[1] - (double)n * rmean * rmean, 0.0));
@@ -421,18 +458,50 @@ __global__ void __launch_bounds__(kBlock, 1) k_poisson_dct(DctArgs<TP> A) {
           ds.rmean = rmean;
           ds.inv = 1.0 / rn_new;
         }))
-      return;
+      return false;
     src = r;
   }
   // gauge: zero-mean correction
   Vec<1> sx = {{0.0}};
   for (int c = t0; c < n; c += gsz) sx.v[0] += x[c];
-  if (!grid_sum_post<1>(sx, A.partial, A.max_blocks, 3, A.st, epoch,
+  if (!team_sum_post<1>(sx, tm, A.max_blocks, 3, A.st, epoch,
                         [&](const double* tot) { ds.mean = tot[0] / (double)n; }))
-    return;
+    return false;
   const double mean_x = ds.mean;
-  for (int c = t0; c < n; c += gsz) x[c] -= mean_x;
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
+  double* pp = A.p;
+  for (int c = t0; c < n; c += gsz) {
+    const double xc = x[c] - mean_x;
+    x[c] = xc;
+    if (pp) pp[c] += xc;
+  }
+  if (pp) {
+    // the projection: every face reads p' on both sides, written above by any block
+    if (!team_barrier(A.st, tm, epoch)) return false;
+    const int nx = A.nx, ny = A.ny, nz = A.nz;
+    const int nf[3] = {(nx + 1) * ny * nz, nx * (ny + 1) * nz, A.dim == 3 ? nx * ny * (nz + 1) : 0};
+    const double kk = A.proj_k;
+    for (int d = 0; d < 3; ++d) {
+      if (nf[d] == 0) continue;
+      const int fx = nx + (d == 0), fy = ny + (d == 1);
+      const int nd = (d == 0) ? nx : (d == 1) ? ny : nz;
+      const int sd = (d == 0) ? 1 : (d == 1) ? nx : nx * ny;
+      double* out = A.vel[d];
+      const double* in = A.us[d];
+      const double ih = A.ih[d];
+      for (int r = t0; r < nf[d]; r += gsz) {
+        const int i = r % fx, t = r / fx, j = t % fy, k = t / fy;
+        const int f = (d == 0) ? i : (d == 1) ? j : k;
+        if (f == 0 || f == nd) {
+          out[r] = 0.0;
+          continue;
+        }
+        const int c_hi = i + nx * (j + ny * k);
+        const double grad = (x[c_hi] - x[c_hi - sd]) * ih;
+        out[r] = in[r] - kk * grad;
+      }
+    }
+  }
+  if (tm.rank == 0 && threadIdx.x == 0) {
     const double rel = ds.bn > 0.0 ? ds.rn / ds.bn : 0.0;
     SolveStat& so = A.st->stat[A.stat_index];
     so.iters = sweeps;
@@ -444,6 +513,14 @@ __global__ void __launch_bounds__(kBlock, 1) k_poisson_dct(DctArgs<TP> A) {
     if (!isfinite(rel)) atomicExch(&A.st->sticky, (int)SS_ENAN);
     else if (!ds.conv) atomicCAS(&A.st->sticky, (int)SS_OK, (int)SS_ENOTCONV);
   }
+  return true;
+}
+
+template <typename TP>
+__global__ void __launch_bounds__(kBlock, 1) k_poisson_dct(DctArgs<TP> A) {
+  extern __shared__ __align__(16) unsigned char dsm[];
+  const Team tm{(int)blockIdx.x, (int)gridDim.x, &A.st->barrier, A.partial};
+  poisson_dct_team<TP>(A, tm, reinterpret_cast<TP*>(dsm));
 }
 
 template <typename TP>
@@ -460,11 +537,46 @@ size_t smem_bytes(const DctPlan& pl, int* cols) {
   return thomas > gemm ? thomas : gemm;
 }
 
+// A packed launch over the cases of a batch: team q (blocks first[q] ..
+// first[q+1]-1) solves case q's pressure correction with its own arguments
+// (staged in shared memory), barrier counter and reduction partials.
+__global__ void __launch_bounds__(kBlock, 1) k_poisson_dct_packed(const DctArgs<float>* __restrict__ args,
+                                                                 const int* __restrict__ first, int nteams) {
+  extern __shared__ __align__(16) unsigned char dsm[];
+  __shared__ int s_team;
+  if (threadIdx.x == 0) {
+    int lo = 0, hi = nteams - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (first[mid] <= (int)blockIdx.x) lo = mid; else hi = mid - 1;
+    }
+    s_team = lo;
+  }
+  __syncthreads();
+  const int q = s_team;
+  __shared__ __align__(16) unsigned long long buf[(sizeof(DctArgs<float>) + 7) / 8];
+  const unsigned long long* src = reinterpret_cast<const unsigned long long*>(args + q);
+  for (int w = threadIdx.x; w < (int)(sizeof(DctArgs<float>) / 8); w += blockDim.x) buf[w] = src[w];
+  __syncthreads();
+  const DctArgs<float>& A = *reinterpret_cast<const DctArgs<float>*>(buf);
+  const Team tm{(int)blockIdx.x - first[q], first[q + 1] - first[q], &A.st->barrier, A.partial};
+  poisson_dct_team<float>(A, tm, reinterpret_cast<float*>(dsm));
+}
+
+// The arguments of one solve; returns the dynamic shared memory it needs.
 template <typename TP>
-cudaError_t launch_t(const DctPlan& pl, const Params& pr, double* b, double* x, const SolverCtl& ctl, Scratch& sc,
-                     DevStatus* st, cudaStream_t s) {
-  DctArgs<TP> A;
+size_t make_args(DctArgs<TP>& A, const DctPlan& pl, const Params& pr, double* b, double* x, const SolverCtl& ctl,
+                 Scratch& sc, DevStatus* st, const ProjectPtrs* proj) {
   memset(&A, 0, sizeof A);
+  if (proj) {
+    A.p = proj->p;
+    for (int d = 0; d < 3; ++d) {
+      A.vel[d] = proj->vel[d];
+      A.us[d] = proj->us[d];
+      A.ih[d] = pr.ih[d];
+    }
+    A.proj_k = pr.proj_k;
+  }
   A.Mx = pl.Mx; A.My = pl.My; A.Mt = pl.Mt; A.R = pl.My * pl.Mt; A.dim = pl.dim;
   A.nx = pr.nx; A.ny = pr.ny; A.nz = pr.nz; A.n = pr.nx * pr.ny * pr.nz;
   A.fx = make_fastdiv(pr.nx);
@@ -483,17 +595,25 @@ cudaError_t launch_t(const DctPlan& pl, const Params& pr, double* b, double* x, 
   A.T2 = (TP*)pl.T2;
   A.b = b; A.x = x; A.r = sc.v[0];
   A.tol = ctl.tol;
+  A.warm = ctl.warm_start;
   A.max_sweeps = ctl.max_it < kMaxSweeps ? ctl.max_it : kMaxSweeps;
   A.stat_index = ctl.stat_index;
   A.partial = sc.partial;
   A.max_blocks = sc.max_blocks;
   A.st = st;
-  const size_t smem = smem_bytes<TP>(pl, &A.thomas_cols);
+  return smem_bytes<TP>(pl, &A.thomas_cols);
+}
+
+template <typename TP>
+cudaError_t launch_t(const DctPlan& pl, const Params& pr, double* b, double* x, const SolverCtl& ctl, Scratch& sc,
+                     DevStatus* st, const ProjectPtrs* proj, cudaStream_t s) {
+  DctArgs<TP> A;
+  const size_t smem = make_args<TP>(A, pl, pr, b, x, ctl, sc, st, proj);
   const void* kern = (const void*)k_poisson_dct<TP>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int cap = ctl.block_cap > 0 && ctl.block_cap < sc.max_blocks ? ctl.block_cap : sc.max_blocks;
-  const int nb = coop_blocks_for_smem(kern, 1LL << 40, cap, smem);
+  const int nb = coop_blocks_for_smem(kern, (long long)A.n, cap, smem);
   if ((e = cudaMemsetAsync(&st->barrier, 0, sizeof(unsigned int), s)) != cudaSuccess) return e;
   void* args[] = {&A};
   return cudaLaunchCooperativeKernel(kern, dim3(nb), dim3(kBlock), args, smem, s);
@@ -540,10 +660,32 @@ void dct_tables(const DctPlan& pl, const Params& pr, double* out) {
   }
 }
 
+size_t packed_dct_args_bytes() { return sizeof(DctArgs<float>); }
+
+size_t fill_packed_dct_args(void* out, const DctPlan& pl, const Params& pr, double* b, double* x, const SolverCtl& ctl,
+                            Scratch& sc, DevStatus* st, const ProjectPtrs* proj) {
+  return make_args<float>(*static_cast<DctArgs<float>*>(out), pl, pr, b, x, ctl, sc, st, proj);
+}
+
+int packed_dct_max_blocks(size_t smem) {
+  const void* kern = (const void*)k_poisson_dct_packed;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
+  return coop_blocks_for_smem(kern, 1LL << 40, 1 << 30, smem);
+}
+
+cudaError_t launch_poisson_dct_packed(const void* args, const int* first, int nteams, int nblocks, size_t smem,
+                                      cudaStream_t s) {
+  const void* kern = (const void*)k_poisson_dct_packed;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  void* a[] = {(void*)&args, (void*)&first, (void*)&nteams};
+  return cudaLaunchCooperativeKernel(kern, dim3(nblocks), dim3(kBlock), a, smem, s);
+}
+
 cudaError_t launch_poisson_dct(const DctPlan& pl, const Params& pr, double* b, double* x, const SolverCtl& ctl,
-                               Scratch& sc, DevStatus* st, cudaStream_t s) {
-  if (pl.fp32) return launch_t<float>(pl, pr, b, x, ctl, sc, st, s);
-  return launch_t<double>(pl, pr, b, x, ctl, sc, st, s);
+                               Scratch& sc, DevStatus* st, const ProjectPtrs* proj, cudaStream_t s) {
+  if (pl.fp32) return launch_t<float>(pl, pr, b, x, ctl, sc, st, proj, s);
+  return launch_t<double>(pl, pr, b, x, ctl, sc, st, proj, s);
 }
 
 }  // namespace solid

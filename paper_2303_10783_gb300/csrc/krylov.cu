@@ -472,8 +472,7 @@ __device__ bool bcg_fused(const Planes<float>& a, int n, int sy, int sz, int has
   return true;
 }
 
-__device__ __forceinline__ void fp64_solve(const BcgArgs& A, const Team& tm) {
-  unsigned int epoch = 0;
+__device__ __forceinline__ void fp64_solve(const BcgArgs& A, const Team& tm, unsigned int& epoch) {
   const int n = (int)A.sys.d.n;
   const int sy = A.sys.d.mx, sz = A.sys.d.mx * A.sys.d.my;
   CoreOut o;
@@ -500,8 +499,7 @@ constexpr int kMaxInner = 200;
 // inner one does not.
 constexpr double kSweepMargin = 0.1;
 
-__device__ __forceinline__ void ir_solve(const BcgArgs& A, const Team& tm) {
-  unsigned int epoch = 0;
+__device__ __forceinline__ void ir_solve(const BcgArgs& A, const Team& tm, unsigned int& epoch) {
   const int n = (int)A.sys.d.n;
   const int sy = A.sys.d.mx, sz = A.sys.d.mx * A.sys.d.my;
   const int t0 = tm.rank * blockDim.x + threadIdx.x, gs = tm.size * blockDim.x;
@@ -577,6 +575,14 @@ struct BcgMulti {
   int first[kMaxTeams + 1];
 };
 
+// The systems one team of a packed launch solves, one after another.
+struct PackedBcgTeam {
+  BcgArgs sys[kMaxTeams];
+  int nsys;
+};
+
+void fill_bcg_args(BcgArgs& A, const Sys& sys, int has_z, const SolverCtl& ctl, const Scratch& c, DevStatus* st);
+
 // The team of this block. Each system's arguments are named with a constant
 // index (no runtime indexing of the parameter block, which would copy it to
 // local memory).
@@ -587,21 +593,59 @@ __device__ __forceinline__ void solve_team(const BcgMulti& M) {
   const int f0 = s == 0 ? 0 : s == 1 ? M.first[1] : M.first[2];
   const int f1 = s == 0 ? M.first[1] : s == 1 ? M.first[2] : M.first[3];
   DevStatus* st = M.sys[0].st;
+  unsigned int epoch = 0;
   if (s == 0) {
     const Team tm{b - f0, f1 - f0, &st->team_arrivals[0], M.sys[0].partial};
-    if (MIXED) ir_solve(M.sys[0], tm); else fp64_solve(M.sys[0], tm);
+    if (MIXED) ir_solve(M.sys[0], tm, epoch); else fp64_solve(M.sys[0], tm, epoch);
   } else if (s == 1) {
     const Team tm{b - f0, f1 - f0, &st->team_arrivals[1], M.sys[1].partial};
-    if (MIXED) ir_solve(M.sys[1], tm); else fp64_solve(M.sys[1], tm);
+    if (MIXED) ir_solve(M.sys[1], tm, epoch); else fp64_solve(M.sys[1], tm, epoch);
   } else {
     const Team tm{b - f0, f1 - f0, &st->team_arrivals[2], M.sys[2].partial};
-    if (MIXED) ir_solve(M.sys[2], tm); else fp64_solve(M.sys[2], tm);
+    if (MIXED) ir_solve(M.sys[2], tm, epoch); else fp64_solve(M.sys[2], tm, epoch);
   }
 }
 
 __global__ void __launch_bounds__(kBlock, 2) k_bicgstab(BcgMulti M) { solve_team<false>(M); }
 
 __global__ void __launch_bounds__(kBlock, 1) k_bicgstab_ir(BcgMulti M) { solve_team<true>(M); }
+
+// The team of block b in a packed launch: the largest q with first[q] <= b.
+__device__ __forceinline__ int packed_team(const int* __restrict__ first, int nteams) {
+  __shared__ int s_team;
+  if (threadIdx.x == 0) {
+    int lo = 0, hi = nteams - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (first[mid] <= (int)blockIdx.x) lo = mid; else hi = mid - 1;
+    }
+    s_team = lo;
+  }
+  __syncthreads();
+  return s_team;
+}
+
+// A packed launch over the cases of a batch: team q (blocks first[q] ..
+// first[q+1]-1) solves the nsys systems of teams[q] one after another (the
+// FP32-inner, FP64-refined solve), with the case's own barrier counter and
+// reduction partials. Each system's arguments are staged in shared memory.
+__global__ void __launch_bounds__(kBlock, 1) k_bicgstab_ir_packed(const PackedBcgTeam* __restrict__ teams,
+                                                                 const int* __restrict__ first, int nteams) {
+  const int q = packed_team(first, nteams);
+  const int f0 = first[q], f1 = first[q + 1];
+  __shared__ __align__(16) unsigned long long buf[(sizeof(BcgArgs) + 7) / 8];
+  const int nsys = teams[q].nsys;
+  unsigned int epoch = 0;
+  for (int k = 0; k < nsys; ++k) {
+    __syncthreads();
+    const unsigned long long* src = reinterpret_cast<const unsigned long long*>(&teams[q].sys[k]);
+    for (int w = threadIdx.x; w < (int)(sizeof(BcgArgs) / 8); w += blockDim.x) buf[w] = src[w];
+    __syncthreads();
+    const BcgArgs& A = *reinterpret_cast<const BcgArgs*>(buf);
+    const Team tm{(int)blockIdx.x - f0, f1 - f0, &A.st->team_arrivals[0], A.partial};
+    ir_solve(A, tm, epoch);
+  }
+}
 
 struct PcgArgs {
   int nx, ny, nz, dim;
@@ -729,6 +773,21 @@ __global__ void __launch_bounds__(kBlock, 2) k_pcg_poisson(PcgArgs A) {
   record(A.st, blockIdx.x == 0, A.stat_index, it, 0, conv, bnorm > 0.0 ? res / bnorm : 0.0);
 }
 
+void fill_bcg_args(BcgArgs& A, const Sys& sys, int has_z, const SolverCtl& ctl, const Scratch& c, DevStatus* st) {
+  A.sys = sys;
+  A.has_z = has_z;
+  A.tol = ctl.tol;
+  A.max_it = ctl.max_it;
+  A.stat_index = ctl.stat_index;
+  A.inner_tol = ctl.inner_tol;
+  A.v64 = {c.v[0], c.v[1], c.v[2], c.v[3], c.v[4], c.v[5], c.v[6]};
+  A.f32 = {c.f[0], c.f[1], c.f[2], c.f[3], c.f[4], c.f[5], c.f[6], c.f[8]};
+  A.d32 = c.f[7];
+  A.partial = c.partial;
+  A.max_blocks = c.max_blocks;
+  A.st = st;
+}
+
 int g_num_sms = 0;
 
 int coop_limit(const void* kernel, size_t smem = 0) {
@@ -744,7 +803,7 @@ int coop_limit(const void* kernel, size_t smem = 0) {
 }
 
 int blocks_for(const void* kernel, long long rows, int max_blocks, size_t smem = 0) {
-  long long want = (rows + kBlock - 1) / kBlock;
+  long long want = blocks_wanted(rows);
   int lim = coop_limit(kernel, smem);
   if (lim > max_blocks) lim = max_blocks;
   if (want > lim) want = lim;
@@ -776,21 +835,8 @@ cudaError_t launch_bicgstab_multi(const Sys* const* sys, int nsys, int has_z, co
   M.nsys = nsys;
   bool mixed = true;
   for (int q = 0; q < nsys; ++q) {
-    BcgArgs& A = M.sys[q];
-    const Scratch& c = *sc[q];
-    A.sys = *sys[q];
-    A.has_z = has_z;
-    A.tol = ctl[q].tol;
-    A.max_it = ctl[q].max_it;
-    A.stat_index = ctl[q].stat_index;
-    A.inner_tol = ctl[q].inner_tol;
-    A.v64 = {c.v[0], c.v[1], c.v[2], c.v[3], c.v[4], c.v[5], c.v[6]};
-    A.f32 = {c.f[0], c.f[1], c.f[2], c.f[3], c.f[4], c.f[5], c.f[6], c.f[8]};
-    A.d32 = c.f[7];
-    A.partial = c.partial;
-    A.max_blocks = c.max_blocks;
-    A.st = st;
-    mixed = mixed && ctl[q].mixed && sys[q]->af.P != nullptr && c.f[0] != nullptr;
+    fill_bcg_args(M.sys[q], *sys[q], has_z, ctl[q], *sc[q], st);
+    mixed = mixed && ctl[q].mixed && sys[q]->af.P != nullptr && sc[q]->f[0] != nullptr;
   }
   const void* kern = mixed ? (const void*)k_bicgstab_ir : (const void*)k_bicgstab;
   // blocks per team: as many as the system's rows want, scaled down in
@@ -802,8 +848,7 @@ cudaError_t launch_bicgstab_multi(const Sys* const* sys, int nsys, int has_z, co
   long long want[kMaxTeams], rows = 0, total = 0;
   for (int q = 0; q < nsys; ++q) {
     if (lim > sc[q]->max_blocks) lim = sc[q]->max_blocks;
-    want[q] = (sys[q]->d.n + kBlock - 1) / kBlock;
-    if (want[q] < 1) want[q] = 1;
+    want[q] = blocks_wanted(sys[q]->d.n);
     rows += sys[q]->d.n;
     total += want[q];
   }
@@ -836,6 +881,23 @@ cudaError_t launch_bicgstab_multi(const Sys* const* sys, int nsys, int has_z, co
   if (e != cudaSuccess) return e;
   void* args[] = {&M};
   return cudaLaunchCooperativeKernel(kern, dim3(M.first[nsys]), dim3(kBlock), args, 0, s);
+}
+
+size_t packed_bcg_team_bytes() { return sizeof(PackedBcgTeam); }
+
+void fill_packed_bcg_team(void* out, const Sys* const* sys, int nsys, int has_z, const SolverCtl* ctl, Scratch& sc,
+                          DevStatus* st) {
+  PackedBcgTeam& T = *static_cast<PackedBcgTeam*>(out);
+  memset(&T, 0, sizeof T);
+  T.nsys = nsys;
+  for (int q = 0; q < nsys; ++q) fill_bcg_args(T.sys[q], *sys[q], has_z, ctl[q], sc, st);
+}
+
+int packed_bcg_max_blocks() { return coop_limit((const void*)k_bicgstab_ir_packed); }
+
+cudaError_t launch_bicgstab_packed(const void* teams, const int* first, int nteams, int nblocks, cudaStream_t s) {
+  void* args[] = {(void*)&teams, (void*)&first, (void*)&nteams};
+  return cudaLaunchCooperativeKernel((const void*)k_bicgstab_ir_packed, dim3(nblocks), dim3(kBlock), args, 0, s);
 }
 
 cudaError_t launch_bicgstab(const Sys& sys, int has_z, const SolverCtl& ctl, Scratch& sc, DevStatus* st,

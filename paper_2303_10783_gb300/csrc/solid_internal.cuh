@@ -23,6 +23,14 @@ constexpr int kMaxRedSlots = 16;         // reduction slots (one per reduction s
 constexpr long long kSpinLimit = 1LL << 21;  // default barrier polls before giving up (about a second)
 constexpr long long kMaxSpinLimit = 1LL << 24;  // largest limit a caller may set (several seconds)
 
+// Systems of at most this many rows are solved by one block: its barriers
+// are block barriers, which costs far less than the grid barriers that a few
+// blocks would need for a few rows each.
+constexpr long long kSingleBlockRows = 4096;
+inline long long blocks_wanted(long long rows) {
+  return rows <= kSingleBlockRows ? 1 : (rows + kBlock - 1) / kBlock;
+}
+
 // device-side error codes (sticky word in DevStatus::err)
 enum : int { kErrNone = 0, kErrBarrier = 1 };
 
@@ -147,6 +155,11 @@ struct Team {
 // false from then on, so the kernel unwinds instead of hanging. The error
 // flag is shared by all teams, so one team's failure unwinds every team.
 __device__ __forceinline__ bool team_barrier(DevStatus* st, const Team& t, unsigned int& epoch) {
+  if (t.size == 1) {   // a team of one block: a block barrier orders its own writes
+    __threadfence_block();
+    __syncthreads();
+    return true;
+  }
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -329,6 +342,43 @@ __device__ __forceinline__ bool grid_sum_post(const In& x, double* partial, int 
   return team_sum_post<K>(x, t, max_blocks, slot, st, epoch, post);
 }
 
+// IEEE-754 binary64 -> binary32 rounding to nearest, ties to even, on the
+// integer pipes for values whose result is a normal float (exponent of d in
+// [-126, 127]) and for zeros; other values (subnormal, overflowing, non-finite
+// results) take the hardware conversion. The 52-bit fraction keeps its top 23
+// bits; the 29 dropped bits decide the rounding; a carry out of the fraction
+// correctly increments the exponent (up to infinity). GB300's FP64 pipe is
+// narrow, so conversions that need no FP64 arithmetic stay off it.
+__device__ __forceinline__ float to_f32(double d) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(d);
+  const unsigned hi = (unsigned)(u >> 32), lo = (unsigned)u;
+  const unsigned e = (hi >> 20) & 0x7FFu;
+  const unsigned sign = hi & 0x80000000u;
+  if (e - 897u <= 253u) {
+    const unsigned m = ((hi & 0xFFFFFu) << 3) | (lo >> 29);
+    const unsigned rest = lo & 0x1FFFFFFFu;
+    unsigned bits = sign | ((e - 896u) << 23) | m;
+    bits += (rest > 0x10000000u || (rest == 0x10000000u && (m & 1u))) ? 1u : 0u;
+    return __uint_as_float(bits);
+  }
+  if ((u << 1) == 0ull) return __uint_as_float(sign);
+  return __double2float_rn(d);
+}
+
+// binary32 -> binary64 (exact) on the integer pipes for normal floats and
+// zeros: the exponent is rebiased (127 -> 1023) and the fraction shifted into
+// place; subnormal and non-finite values take the hardware conversion.
+__device__ __forceinline__ double to_f64(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned e = (u >> 23) & 0xFFu;
+  const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
+  if (e - 1u < 254u)
+    return __longlong_as_double((long long)(sign | ((unsigned long long)(e + 896u) << 52) |
+                                            ((unsigned long long)(u & 0x7FFFFFu) << 29)));
+  if ((u << 1) == 0u) return __longlong_as_double((long long)sign);
+  return (double)f;
+}
+
 // Division by a runtime constant d >= 1 for 0 <= n < 2^31 with a multiply-high
 // and a shift: q = (umulhi(n, m) + n) >> s, s = ceil(log2 d),
 // m = floor(2^32 (2^s - d) / d) + 1 (round-up method of Granlund & Montgomery).
@@ -445,6 +495,34 @@ int coarse_pseudo_inverse(const MGPlan& pl, int dim, double* out);
 cudaError_t launch_pcg_mg(const MGPlan& pl, const Params& pr, double* b, double* x, const SolverCtl& ctl,
                           Scratch& sc, DevStatus* st, cudaStream_t s);
 
+// ---- packed batches: one launch per stage for many cases
+//
+// The device-side description of one case of a packed batch: what the
+// assembly and pointwise stages of a step read and write.
+struct CaseRows {
+  Params pr;
+  Sys sys[SS_NSYS];
+  double *u, *v, *w, *p, *T, *C, *gl, *Cl, *Cs, *Kinv, *Ag, *pc, *pb, *Tinc;
+  double* ustar[3];
+  DevStatus* st;
+};
+// A work item of a packed stage: rows [r0, r1) of part `part` (the momentum
+// component; 0 otherwise) of case c.
+struct PackedTile {
+  int c, part, r0, r1;
+};
+enum { kStageMomentum = 0, kStageRhs = 1, kStageProject = 2, kStageSolute = 3, kStageTemperature = 4,
+       kStageLever = 5, kNumPackedStages = 6 };
+// Rows of case q that a packed stage covers (part: momentum component).
+long long packed_stage_rows(int stage, const Params& pr, int part);
+cudaError_t launch_packed_rows(int stage, const CaseRows* cases, const PackedTile* tiles, int ntiles, cudaStream_t s);
+// krylov.cu: the transport solves of a packed batch, one team of blocks per case
+size_t packed_bcg_team_bytes();
+void fill_packed_bcg_team(void* out, const Sys* const* sys, int nsys, int has_z, const SolverCtl* ctl, Scratch& sc,
+                          DevStatus* st);
+int packed_bcg_max_blocks();
+cudaError_t launch_bicgstab_packed(const void* teams, const int* first, int nteams, int nblocks, cudaStream_t s);
+
 // dct.cu: the pressure correction by cosine transforms along x (and y in 3D)
 // and tridiagonal solves along the last axis, inside FP64 refinement
 struct DctPlan {
@@ -459,7 +537,22 @@ void plan_dct(const Params& pr, DctPlan& pl, int fp32);
 size_t dct_table_elems(const DctPlan& pl);
 // the tables in FP64, packed as above, into out[dct_table_elems]
 void dct_tables(const DctPlan& pl, const Params& pr, double* out);
+// The fields of the projection (Eq. 3.5) that the transform solve can end with.
+struct ProjectPtrs {
+  double* vel[3];          // u^{n+1} (written)
+  const double* us[3];     // u*
+  double* p;               // p (p += p')
+};
+// proj: when not null, the solve ends with the projection (u^{n+1} from u* and
+// the zero-mean p', and p += p'), bit for bit what the projection stage gives.
 cudaError_t launch_poisson_dct(const DctPlan& pl, const Params& pr, double* b, double* x, const SolverCtl& ctl,
-                               Scratch& sc, DevStatus* st, cudaStream_t s);
+                               Scratch& sc, DevStatus* st, const ProjectPtrs* proj, cudaStream_t s);
+// the pressure solves of a packed batch (FP32 transforms), one team per case
+size_t packed_dct_args_bytes();
+size_t fill_packed_dct_args(void* out, const DctPlan& pl, const Params& pr, double* b, double* x, const SolverCtl& ctl,
+                            Scratch& sc, DevStatus* st, const ProjectPtrs* proj);
+int packed_dct_max_blocks(size_t smem);
+cudaError_t launch_poisson_dct_packed(const void* args, const int* first, int nteams, int nblocks, size_t smem,
+                                      cudaStream_t s);
 
 }  // namespace solid

@@ -96,6 +96,13 @@ def _declare(lib):
         "ss_lever": [P],
         "ss_set_profiling": [P, ctypes.c_int],
         "ss_get_profile": [P, ctypes.POINTER(Profile)],
+        "ss_batch_workspace_bytes": [ctypes.POINTER(P), ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)],
+        "ss_batch_create": [ctypes.POINTER(P), ctypes.c_int, P, ctypes.c_size_t, P, ctypes.POINTER(P)],
+        "ss_batch_set_schedule": [P, ctypes.c_double, ctypes.c_int],
+        "ss_batch_get_teams": [P, ctypes.POINTER(ctypes.c_int)],
+        "ss_batch_step": [P, ctypes.c_int],
+        "ss_batch_sync": [P, ctypes.POINTER(ctypes.c_longlong)],
+        "ss_batch_destroy": [P],
         "ss_set_wait_limit": [P, ctypes.c_longlong],
         "ss_wait_selftest": [P],
         "ss_poisson_solve_noalloc": [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
@@ -370,3 +377,52 @@ def convert_f64_to_f32(src):
     check(load().ss_convert_f64_to_f32(ctypes.c_void_p(src.data_ptr()), ctypes.c_void_p(dst.data_ptr()),
                                        src.numel(), ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)))
     return dst
+
+
+class PackedBatch:
+    """ss_batch: many cases stepped with one launch per stage (see include/solid.h).
+    ``members`` are :class:`Case` objects (SS_MIXED, "dct" pressure solver);
+    the batch's tables live in a torch uint8 workspace owned by this object."""
+
+    def __init__(self, members, stream=None):
+        import torch
+        self.lib = load()
+        self.members = list(members)
+        n = len(self.members)
+        arr = (ctypes.c_void_p * n)(*[m.h.value for m in self.members])
+        nb = ctypes.c_size_t(0)
+        check(self.lib.ss_batch_workspace_bytes(arr, n, ctypes.byref(nb)))
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        self.workspace = torch.empty(max(nb.value, 256), dtype=torch.uint8, device="cuda")
+        h = ctypes.c_void_p()
+        check(self.lib.ss_batch_create(arr, n, ctypes.c_void_p(self.workspace.data_ptr()), nb.value,
+                                       ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h)))
+        self.h = h
+
+    def set_schedule(self, gamma, tile_rows):
+        check(self.lib.ss_batch_set_schedule(self.h, float(gamma), int(tile_rows)))
+
+    def teams(self):
+        out = (ctypes.c_int * len(self.members))()
+        check(self.lib.ss_batch_get_teams(self.h, out))
+        return list(out)
+
+    def step(self, n=1):
+        check(self.lib.ss_batch_step(self.h, int(n)))
+
+    def sync(self, allow=()):
+        """Wait for the batch; returns (worst sticky status, kernels launched so far)."""
+        k = ctypes.c_longlong(0)
+        st = check(self.lib.ss_batch_sync(self.h, ctypes.byref(k)), allow)
+        return st, k.value
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            self.lib.ss_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

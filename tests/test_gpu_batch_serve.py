@@ -51,6 +51,99 @@ def test_batch_member_equals_alone(lib):
     b.close()
 
 
+def _tight_mixed(case):
+    return dict(case, tol_p=1e-13, tol_t=1e-13, max_it_p=50000, max_it_t=5000, precond_p="dct")
+
+
+PACKED_CASES = [_tight_mixed(cases.cavity_2d(40, 24, T0=498.2)), _tight_mixed(cases.box_3d(19, 13, 11, T0=498.2)),
+                _tight_mixed(cases.box_3d(16, 12, 8, seed=3, T0=498.2)), _tight_mixed(cases.cavity_2d(50, 30, T0=498.2))]
+
+
+def _packed_run(cs, nsteps, schedule=None):
+    b = Batch(cs, precision=solid.SS_MIXED, packed=True)
+    if schedule:
+        b.packed.set_schedule(*schedule)
+    b.step(nsteps)
+    assert b.sync() == solid.SS_OK
+    out = [b.fields(q) for q in range(len(cs))]
+    teams = b.packed.teams()
+    launches = b.kernels()
+    b.close()
+    return out, teams, launches
+
+
+def test_packed_batch_matches_oracle(lib):
+    """Uneven 2D and 3D cases stepped by the packed batch (one launch per stage
+    for all of them, each solve by a team of blocks per case) match the oracle
+    after 20 steps at the parity tolerances, starting inside the mushy range."""
+    import oracle
+    out, teams, launches = _packed_run(PACKED_CASES, 20)
+    assert len(teams) == len(PACKED_CASES) and min(teams) >= 1
+    assert launches == 20 * 9         # nine launches per batch step
+    for q, case in enumerate(PACKED_CASES):
+        f = cases.initial_fields(case)
+        g = oracle.Grid(case)
+        st = oracle.initial_state(case, f["T"], f["C"])
+        for _ in range(20):
+            st = oracle.step(g, st, case)
+        gpu = out[q]
+        for k in ("p", "T", "C", "gl", "Cl", "Cs"):
+            ref = getattr(st, k)
+            assert np.abs(gpu[k] - ref).max() <= 1e-9 * np.abs(ref).max(), (q, k)
+        vmax = max(np.abs(x).max() for x in st.vel)
+        for a, k in enumerate("uvw"[: case["dim"]]):
+            assert np.abs(gpu[k] - st.vel[a]).max() <= 1e-9 * vmax, (q, k)
+        assert st.gl.min() < 1.0
+
+
+def test_packed_batch_is_deterministic_and_agrees_with_alone(lib):
+    """Two packed runs with the same schedule agree bit for bit; another
+    schedule (other team sizes and tiles) and the case stepped alone agree to
+    rounding."""
+    cs = [dict(c, precond_p="dct") for c in (cases.cavity_2d(64, 40), cases.box_3d(32, 24, 16),
+                                              cases.box_3d(16, 16, 16, seed=7))]
+    a, ta, _ = _packed_run(cs, 6)
+    b, tb, _ = _packed_run(cs, 6)
+    assert ta == tb
+    for x, y in zip(a, b):
+        assert _same(x, y)
+    c2, tc, _ = _packed_run(cs, 6, schedule=(0.5, 1024))
+    for q, cd in enumerate(cs):
+        alone = _alone(cd, 6)
+        for other in (alone, c2[q]):
+            for k in ("T", "C", "gl", "p"):
+                assert np.abs(a[q][k] - other[k]).max() <= 1e-9 * np.abs(other[k]).max(), (q, k)
+
+
+def test_packed_autotune_restores_state_and_rejects_bad_cases(lib):
+    import ctypes
+    cs = [dict(cases.box_3d(20, 12, 10, seed=4), precond_p="dct"), dict(cases.cavity_2d(48, 32), precond_p="dct")]
+    bt = Batch(cs, precision=solid.SS_MIXED, packed=True)
+    bt.step(2)
+    bt.sync()
+    before = [bt.fields(q) for q in range(len(cs))]
+    best, timing = bt.autotune(steps=1, gammas=(0.5, 1.0), tiles=(1024, 4096))
+    assert best in timing and len(timing) == 4
+    after = [bt.fields(q) for q in range(len(cs))]
+    for x, y in zip(before, after):
+        assert _same(x, y)
+    assert lib.ss_batch_set_schedule(bt.packed.h, -1.0, 4096) == solid.SS_EINVAL
+    assert lib.ss_batch_set_schedule(bt.packed.h, 1.0, 16) == solid.SS_EINVAL
+    bt.close()
+    # FP64 cases, multigrid pressure solves and repeated cases are refused
+    for cd, prec in ((dict(cs[1], precond_p="dct"), solid.SS_FP64), (dict(cs[1], precond_p="mg"), solid.SS_MIXED)):
+        c = solid.Case(cd, precision=prec)
+        arr = (ctypes.c_void_p * 1)(c.h.value)
+        nb = ctypes.c_size_t(0)
+        assert lib.ss_batch_workspace_bytes(arr, 1, ctypes.byref(nb)) == solid.SS_EINVAL
+        c.close()
+    c = solid.Case(dict(cs[1], precond_p="dct"), precision=solid.SS_MIXED)
+    arr = (ctypes.c_void_p * 2)(c.h.value, c.h.value)
+    nb = ctypes.c_size_t(0)
+    assert lib.ss_batch_workspace_bytes(arr, 2, ctypes.byref(nb)) == solid.SS_EINVAL
+    c.close()
+
+
 def test_batched_workload_cases_are_valid():
     cs = cases.batch_cases(64)
     assert len(cs) == 64 and {c["dim"] for c in cs} == {2, 3}
