@@ -673,6 +673,8 @@ def cavity_leg(args, local):
     return "cavity", {"workload": "cavity_2d_50x30", "precision": "fp64", "steps": 300, "warmup": 3,
                       "value": n * 300 / (ms * 1e-3), "unit": "cell-steps/s", "ms_per_step": ms / 300,
                       "status": status, "gpu_launches": prof["kernels"], "clocks": clocks,
+                      "stage_ms_per_step": {k: v / 300 for k, v in prof["ms"].items() if v > 0},
+                      "iters_per_step": {k: v / 300 for k, v in prof["iters"].items()},
                       "note": "1500 cells: latency-bound, no roofline claimed"}
 
 
