@@ -76,6 +76,7 @@ struct DctArgs {
   int stat_index;
   int warm;                 // start from the x in place (else from 0)
   int thomas_cols;          // columns per shared-memory chunk of the tridiagonal solves
+  int slab_smem;            // 1: pass B keeps each slab in shared memory (FP32 slabs that fit)
   double* partial;
   int max_blocks;
   DevStatus* st;
@@ -86,6 +87,7 @@ struct DctArgs {
   const double* us[3];
   double proj_k;
   double ih[3];
+  FastDiv ffx[3], ffy[3];   // division by the face grid's extents along x and y, per component
 };
 
 template <typename T>
@@ -276,26 +278,159 @@ __device__ __forceinline__ double lap64(const double* v, int c, int i, int j, in
   return acc;
 }
 
-// Pass A: T1 = (Cx ⊗ I) ((src - shift) * scale)
+// Pass A: T1 = (Cx ⊗ I) (rs * sc + off): rs is the residual staged in T2 in
+// the transform type, scaled by a power of two (exactly) when it was formed;
+// sc and off turn it into (r - mean) / |r| (unit norm, no FP32 under- or
+// overflow) in the transform type, once per element and tile.
 template <typename TP>
-__device__ void pass_a(const DctArgs<TP>& A, const Team& tm, const double* src, double shift, double scale, TP* sm) {
+__device__ void pass_a(const DctArgs<TP>& A, const Team& tm, TP sc, TP off, TP* sm) {
   const int Mx = A.Mx, R = A.R;
   const int mt = (Mx + BM - 1) / BM, nt = (R + BN - 1) / BN;
   const TP* Cx = A.Cx;
+  const TP* rs = A.T2;
   TP* T1 = A.T1;
   for (int tile = tm.rank; tile < mt * nt; tile += tm.size) {
     const int m0 = (tile % mt) * BM, n0 = (tile / mt) * BN;
     gemm_tile<TP>(
         Mx, R, Mx, m0, n0, [&](int m, int k) { return Cx[(size_t)m * Mx + k]; }, true,
-        [&](int k, int n) { return narrow<TP>(fma(src[(size_t)n * Mx + k], scale, -shift * scale)); }, true,
+        [&](int k, int n) { return fma(rs[(size_t)n * Mx + k], sc, off); }, true,
         [&](int m, int n, TP v) { T1[(size_t)m * R + n] = v; }, false, sm);
   }
 }
 
 // Pass B: per mode kx, the transform along y, the tridiagonal solves along t
 // and the inverse transform along y (3D); in 2D only the tridiagonal solves.
+// Shared-memory GEMM of a whole slab: out(m, n) = sum_k a[k*lda + m] b[k*ldb + n]
+// (both operands k-major), 4 x 4 outputs per thread strided over the output.
+template <class ST>
+__device__ __forceinline__ void smem_gemm(int M, int N, int K, const float* a, int lda, const float* b, int ldb,
+                                          ST st) {
+  const int mb = (M + 3) >> 2, nb = (N + 3) >> 2;
+  const bool v4 = ((M | N | lda | ldb) & 3) == 0;
+  for (int o = threadIdx.x; o < mb * nb; o += blockDim.x) {
+    const int m0 = (o % mb) * 4, n0 = (o / mb) * 4;
+    float acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+    for (int k = 0; k < K; ++k) {
+      float av[4], bv[4];
+      if (v4) {
+        lds4(a + (size_t)k * lda + m0, av);
+        lds4(b + (size_t)k * ldb + n0, bv);
+      } else {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          av[i] = (m0 + i < M) ? a[(size_t)k * lda + m0 + i] : 0.f;
+          bv[i] = (n0 + i < N) ? b[(size_t)k * ldb + n0 + i] : 0.f;
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if (m0 + i < M && n0 + j < N) st(m0 + i, n0 + j, acc[i][j]);
+  }
+}
+
+// Shared memory (floats) of the slab-resident pass B: the slab and the cosine
+// matrix (rows padded by 4: 16-byte aligned, fewer bank conflicts in the
+// transposing copies), the transformed slab (rows of odd length) and the
+// eliminated super-diagonal of the tridiagonal solves.
+__host__ __device__ __forceinline__ size_t slab_smem_floats(int My, int Mt) {
+  const size_t P = (size_t)(My | 1);
+  return (size_t)My * (Mt + 4) + (size_t)My * (My + 4) + 2 * (size_t)Mt * P;
+}
+
+// Pass B with the whole slab in shared memory (FP32, 3D): the transform along
+// y, the tridiagonal solves along t and the inverse transform never wait on
+// global memory between their steps.
+__device__ void pass_b_slab(const DctArgs<float>& A, const Team& tm, float* sm) {
+  const int Mx = A.Mx, My = A.My, Mt = A.Mt, R = A.R;
+  const int P = My | 1;                           // odd row length of the transformed slab
+  const int LX = Mt + 4, LC = My + 4;             // padded rows of Xs and Cs
+  float* Xs = sm;                                 // [My][LX]: the slab, j-major; later the solution, ky-major
+  float* Cs = Xs + (size_t)My * LX;               // [My][LC]: Cy transposed (GEMM 1), then Cy (GEMM 2)
+  float* Ts = Cs + (size_t)My * LC;               // [Mt][P]: transformed slab, ky fastest
+  float* Ps = Ts + (size_t)Mt * P;                // [Mt][P]: c' of the tridiagonal solves
+  const float at = A.at;
+  for (int kx = tm.rank; kx < Mx; kx += tm.size) {
+    float* S1 = A.T1 + (size_t)kx * R;            // [t][j] in global memory
+    for (int e = threadIdx.x; e < My * Mt; e += blockDim.x) {
+      const int t = e / My, j = e - t * My;       // coalesced over j
+      Xs[(size_t)j * LX + t] = S1[e];
+    }
+    for (int e = threadIdx.x; e < My * My; e += blockDim.x) {
+      const int ky = e / My, j = e - ky * My;
+      Cs[(size_t)j * LC + ky] = A.Cy[e];          // Cy^T: k-major for GEMM 1
+    }
+    __syncthreads();
+    // GEMM 1: Ts[t][ky] = sum_j Cy[ky][j] S[t][j]
+    smem_gemm(My, Mt, My, Cs, LC, Xs, LX, [&](int ky, int t, float v) { Ts[(size_t)t * P + ky] = v; });
+    __syncthreads();
+    for (int e = threadIdx.x; e < My * My; e += blockDim.x) {
+      const int ky = e / My, j = e - ky * My;
+      Cs[(size_t)ky * LC + j] = A.Cy[e];          // Cy: k-major for GEMM 2
+    }
+    // tridiagonal solves along t, one column ky per thread
+    const float sx = A.lx[kx];
+    for (int c = threadIdx.x; c < My; c += blockDim.x) {
+      const float s = sx + A.ly[c];
+      const bool singular = kx == 0 && c == 0;
+      const int m = singular ? Mt - 1 : Mt;
+      if (m <= 0) {
+        Ts[c] = 0.f;
+      } else {
+        float prev_c = 0.f, prev_y = 0.f;
+        for (int t = 0; t < m; ++t) {
+          const float nb = (float)((t > 0) + (t < Mt - 1));
+          const float d = fmaf(at, prev_c, fmaf(at, nb, s));
+          const float inv = 1.f / d;
+          prev_y = fmaf(at, prev_y, Ts[(size_t)t * P + c]) * inv;
+          prev_c = -at * inv;
+          Ts[(size_t)t * P + c] = prev_y;
+          Ps[(size_t)t * P + c] = prev_c;
+        }
+        float next = 0.f;
+        if (singular) Ts[(size_t)(Mt - 1) * P + c] = 0.f;
+        for (int t = m - 1; t >= 0; --t) {
+          next = Ts[(size_t)t * P + c] - Ps[(size_t)t * P + c] * next;
+          Ts[(size_t)t * P + c] = next;
+        }
+        if (singular) {
+          float sum = 0.f;
+          for (int t = 0; t < Mt; ++t) sum += Ts[(size_t)t * P + c];
+          const float mean = sum / (float)Mt;
+          for (int t = 0; t < Mt; ++t) Ts[(size_t)t * P + c] -= mean;
+        }
+      }
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < My * Mt; e += blockDim.x) {
+      const int ky = e / Mt, t = e - ky * Mt;
+      Xs[(size_t)ky * LX + t] = Ts[(size_t)t * P + ky];   // the solution, ky-major for GEMM 2
+    }
+    __syncthreads();
+    // GEMM 2: S[t][j] = sum_ky Cy[ky][j] Xs[ky][t]
+    smem_gemm(My, Mt, My, Cs, LC, Xs, LX, [&](int j, int t, float v) { S1[(size_t)t * My + j] = v; });
+    __syncthreads();
+  }
+}
+
 template <typename TP>
 __device__ void pass_b(const DctArgs<TP>& A, const Team& tm, TP* sm) {
+  if constexpr (sizeof(TP) == 4) {
+    if (A.slab_smem) {
+      pass_b_slab(A, tm, sm);
+      return;
+    }
+  }
   const int Mx = A.Mx, My = A.My, Mt = A.Mt, R = A.R;
   const TP* lx = A.lx;
   const TP* ly = A.ly;
@@ -379,37 +514,51 @@ __device__ bool poisson_dct_team(const DctArgs<TP>& A, const Team& tm, TP* sm) {
   double* x = A.x;
   double* r = A.r;
   __shared__ struct {
-    double mean, bn, rn, rmean, inv;
+    double mean, bn, rn, rmean, sc, off, pscale;
     int go, conv;
   } ds;
   double thr = 0.0;   // read by thread 0 only
-  // consistency: remove the mean of the right-hand side (Neumann null space)
-  Vec<1> sb = {{0.0}};
-  for (int c = t0; c < n; c += gsz) sb.v[0] += b[c];
-  if (!team_sum_post<1>(sb, tm, A.max_blocks, 0, A.st, epoch,
-                        [&](const double* tot) { ds.mean = tot[0] / (double)n; }))
+  TP* rs = A.T2;       // the residual of the next sweep, staged in the transform type (T2 is free outside pass B)
+  // consistency: remove the mean of the right-hand side (Neumann null space);
+  // its norm, from the same sums, sets the power of two that scales the
+  // first staged residual
+  Vec<2> sb = {{0.0, 0.0}};
+  for (int c = t0; c < n; c += gsz) {
+    const double bc = b[c];
+    sb.v[0] += bc;
+    sb.v[1] += bc * bc;
+  }
+  if (!team_sum_post<2>(sb, tm, A.max_blocks, 0, A.st, epoch, [&](const double* tot) {
+        ds.mean = tot[0] / (double)n;
+        int e = 0;
+        frexp(sqrt(fmax(tot[1] - (double)n * ds.mean * ds.mean, 0.0)), &e);
+        ds.pscale = ldexp(1.0, -e);
+      }))
     return false;
   const double mean_b = ds.mean;
   // Warm start: the x in place (the previous step's correction) is the first
   // iterate and r = b - A x the first residual; cold start: x = 0 and the
   // first residual is b itself.
   const bool warm = A.warm != 0;
+  double ps = ds.pscale;   // the staged residual is r * ps (ps a power of two: exact)
   Vec<3> s2 = {{0.0, 0.0, 0.0}};
   for (int c = t0; c < n; c += gsz) {
     const double bc = b[c] - mean_b;
     b[c] = bc;
     s2.v[0] += bc * bc;
+    double rc = bc;
     if (warm) {
       int i, j, k;
       decompose3(c, A.fx, A.fy, i, j, k);
       const int code = ((i > 0) + (i < A.nx - 1)) + 3 * ((j > 0) + (j < A.ny - 1)) + 9 * ((k > 0) + (k < A.nz - 1));
-      const double rc = bc - lap64(x, c, i, j, k, A.nx, A.ny, A.nz, A.cx, A.cy, A.cz, s_diag[code]);
+      rc = bc - lap64(x, c, i, j, k, A.nx, A.ny, A.nz, A.cx, A.cy, A.cz, s_diag[code]);
       r[c] = rc;
       s2.v[1] += rc;
       s2.v[2] += rc * rc;
     } else {
       x[c] = 0.0;
     }
+    rs[c] = narrow<TP>(rc * ps);
   }
   if (!team_sum_post<3>(s2, tm, A.max_blocks, 1, A.st, epoch, [&](const double* tot) {
         ds.bn = sqrt(tot[0]);
@@ -421,17 +570,21 @@ __device__ bool poisson_dct_team(const DctArgs<TP>& A, const Team& tm, TP* sm) {
           ds.rmean = 0.0;
           ds.rn = ds.bn;
         }
-        ds.inv = 1.0 / ds.rn;
         ds.conv = ds.bn == 0.0 || ds.rn <= thr;
         ds.go = !ds.conv && isfinite(ds.rn);
+        ds.sc = 1.0 / (ds.pscale * ds.rn);
+        ds.off = -ds.rmean / ds.rn;
+        int e = 0;
+        frexp(ds.rn, &e);
+        ds.pscale = ldexp(1.0, -e);   // for the residual of the next sweep
       }))
     return false;
   int sweeps = 0;
-  const double* src = warm ? r : b;
   while (ds.go && sweeps < A.max_sweeps) {
     ++sweeps;
-    const double shift = ds.rmean, scale = ds.inv, rn = ds.rn;
-    pass_a<TP>(A, tm, src, shift, scale, sm);
+    const double rn = ds.rn;
+    ps = ds.pscale;
+    pass_a<TP>(A, tm, (TP)ds.sc, (TP)ds.off, sm);
     if (!team_barrier(A.st, tm, epoch)) return false;
     pass_b<TP>(A, tm, sm);
     if (!team_barrier(A.st, tm, epoch)) return false;
@@ -443,7 +596,7 @@ __device__ bool poisson_dct_team(const DctArgs<TP>& A, const Team& tm, TP* sm) {
       decompose3(c, A.fx, A.fy, i, j, k);
       const int code = ((i > 0) + (i < A.nx - 1)) + 3 * ((j > 0) + (j < A.ny - 1)) + 9 * ((k > 0) + (k < A.nz - 1));
       const double rc = b[c] - lap64(x, c, i, j, k, A.nx, A.ny, A.nz, A.cx, A.cy, A.cz, s_diag[code]);
-      r[c] = rc;
+      rs[c] = narrow<TP>(rc * ps);
       s.v[0] += rc;
       s.v[1] += rc * rc;
     }
@@ -456,10 +609,13 @@ __device__ bool poisson_dct_team(const DctArgs<TP>& A, const Team& tm, TP* sm) {
           ds.go = !ds.conv && isfinite(rn_new) && rn_new < 0.5 * ds.rn;
           ds.rn = rn_new;
           ds.rmean = rmean;
-          ds.inv = 1.0 / rn_new;
+          ds.sc = 1.0 / (ds.pscale * rn_new);
+          ds.off = -rmean / rn_new;
+          int e = 0;
+          frexp(rn_new, &e);
+          ds.pscale = ldexp(1.0, -e);
         }))
       return false;
-    src = r;
   }
   // gauge: zero-mean correction
   Vec<1> sx = {{0.0}};
@@ -482,14 +638,15 @@ __device__ bool poisson_dct_team(const DctArgs<TP>& A, const Team& tm, TP* sm) {
     const double kk = A.proj_k;
     for (int d = 0; d < 3; ++d) {
       if (nf[d] == 0) continue;
-      const int fx = nx + (d == 0), fy = ny + (d == 1);
       const int nd = (d == 0) ? nx : (d == 1) ? ny : nz;
       const int sd = (d == 0) ? 1 : (d == 1) ? nx : nx * ny;
       double* out = A.vel[d];
       const double* in = A.us[d];
       const double ih = A.ih[d];
+      const FastDiv ffx = A.ffx[d], ffy = A.ffy[d];
       for (int r = t0; r < nf[d]; r += gsz) {
-        const int i = r % fx, t = r / fx, j = t % fy, k = t / fy;
+        int i, j, k;
+        decompose3(r, ffx, ffy, i, j, k);
         const int f = (d == 0) ? i : (d == 1) ? j : k;
         if (f == 0 || f == nd) {
           out[r] = 0.0;
@@ -523,8 +680,11 @@ __global__ void __launch_bounds__(kBlock, 1) k_poisson_dct(DctArgs<TP> A) {
   poisson_dct_team<TP>(A, tm, reinterpret_cast<TP*>(dsm));
 }
 
+// Shared memory a block may give the slab-resident pass B.
+constexpr size_t kSlabSmemBytes = 200 * 1024;
+
 template <typename TP>
-size_t smem_bytes(const DctPlan& pl, int* cols) {
+size_t smem_bytes(const DctPlan& pl, int* cols, int* slab) {
   const int P = (pl.Mt & 1) ? pl.Mt : pl.Mt + 1;
   const int ncols = pl.dim == 3 ? pl.My : pl.Mx;
   long long w = (long long)(kThomasSmemBytes / (2 * (size_t)P * sizeof(TP)));
@@ -534,7 +694,11 @@ size_t smem_bytes(const DctPlan& pl, int* cols) {
   *cols = (int)w;
   const size_t thomas = 2 * (size_t)w * P * sizeof(TP);
   const size_t gemm = (size_t)kGemmSmemElems * sizeof(TP);
-  return thomas > gemm ? thomas : gemm;
+  size_t need = thomas > gemm ? thomas : gemm;
+  const size_t slab_bytes = slab_smem_floats(pl.My, pl.Mt) * sizeof(float);
+  *slab = sizeof(TP) == 4 && pl.dim == 3 && slab_bytes <= kSlabSmemBytes;
+  if (*slab && slab_bytes > need) need = slab_bytes;
+  return need;
 }
 
 // A packed launch over the cases of a batch: team q (blocks first[q] ..
@@ -574,6 +738,8 @@ size_t make_args(DctArgs<TP>& A, const DctPlan& pl, const Params& pr, double* b,
       A.vel[d] = proj->vel[d];
       A.us[d] = proj->us[d];
       A.ih[d] = pr.ih[d];
+      A.ffx[d] = make_fastdiv(pr.nx + (d == 0));
+      A.ffy[d] = make_fastdiv(pr.ny + (d == 1));
     }
     A.proj_k = pr.proj_k;
   }
@@ -601,7 +767,7 @@ size_t make_args(DctArgs<TP>& A, const DctPlan& pl, const Params& pr, double* b,
   A.partial = sc.partial;
   A.max_blocks = sc.max_blocks;
   A.st = st;
-  return smem_bytes<TP>(pl, &A.thomas_cols);
+  return smem_bytes<TP>(pl, &A.thomas_cols, &A.slab_smem);
 }
 
 template <typename TP>
