@@ -184,6 +184,120 @@ __device__ __forceinline__ void assemble_momentum_rows(const Params& pr, const S
   }
 }
 
+// ---- mixed-path assembly in double-float arithmetic
+//
+// The same rows as above with the plane coefficients computed in double-float
+// (about 48 significant bits on the FP32 pipe, inputs split on the integer
+// pipe) and converted to FP64 with one FP64 add per plane: GB300's FP64 pipe
+// bounds the FP64 kernels at ~30 FP64 operations per row. The right-hand side
+// stays FP64 (its pressure difference and Boussinesq deviations cancel). The
+// planes agree with the FP64 ones to ~1e-14 relative to the row's scale, and
+// the FP32 copies are their IEEE rounding as before.
+
+// max(F, 0) and min(F, 0) of a double-float by the sign of its leading part
+struct SplitDf {
+  dfl pos, neg;
+};
+__device__ __forceinline__ SplitDf split_df(dfl F) {
+  const dfl z = {0.f, 0.f};
+  const bool negative = __float_as_int(F.hi) < 0;
+  return {negative ? z : F, negative ? F : z};
+}
+
+__device__ __forceinline__ void write_row_df(const Sys& s, int r, int dim, dfl P, const dfl nbB[3], const dfl nbF[3],
+                                             double b) {
+  double nb[3], nf[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    nb[d] = d < dim ? df_to_f64(nbB[d]) : 0.0;
+    nf[d] = d < dim ? df_to_f64(nbF[d]) : 0.0;
+  }
+  write_row(s, r, dim, df_to_f64(P), nb, nf, b);
+}
+
+template <int A>
+__device__ __forceinline__ void assemble_momentum_rows_df(const Params& pr, const Sys& s, const double* __restrict__ u,
+                                                          const double* __restrict__ v, const double* __restrict__ w,
+                                                          double* ustar, const double* __restrict__ p,
+                                                          const double* __restrict__ T,
+                                                          const double* __restrict__ Cl,
+                                                          const double* __restrict__ Kinv, int first, int stride,
+                                                          int end) {
+  const Axes ax = axes_of(pr);
+  const double* vel[3] = {u, v, w};
+  const int mx = s.d.mx, my = s.d.my;
+  const int sA = (A == 0) ? 1 : (A == 1) ? mx : mx * my;
+  const double idt = pr.idt;
+  const dfl zero = {0.f, 0.f};
+  for (int r = first; r < end; r += stride) {
+    const int i = r % mx, t = r / mx, j = t % my, k = t / my;
+    const int idx[3] = {i, j, k};
+    const int f = idx[A];
+    const double own = vel[A][r];
+    ustar[r] = own;   // initial guess of the predictor solve: u^n
+    if (f == 0 || f == ax.n[A]) {   // wall face: identity row, datum 0
+      const double zb[3] = {0.0, 0.0, 0.0};
+      write_row(s, r, pr.dim, 1.0, zb, zb, 0.0);
+      continue;
+    }
+    int lo[3] = {i, j, k};
+    lo[A] -= 1;
+    const int c_lo = cidx(pr, lo[0], lo[1], lo[2]);
+    const int c_hi = cidx(pr, i, j, k);
+    const dfl own_d = df_from(own);
+    dfl P = df_add(pr.df_idt, df_mul(pr.df_half_nu, df_add(df_from(Kinv[c_lo]), df_from(Kinv[c_hi]))));
+    dfl nbB[3] = {zero, zero, zero}, nbF[3] = {zero, zero, zero};
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      if (d >= pr.dim) break;
+      dfl sb, sf, Db, Df;
+      bool hb, hf;
+      if (d == A) {
+        sb = df_add(df_from(vel[A][r - sA]), own_d);
+        sf = df_add(own_d, df_from(vel[A][r + sA]));
+        hb = (f - 1 >= 1);
+        hf = (f + 1 <= ax.n[A] - 1);
+        Db = pr.df_nu_ih2[d];
+        Df = pr.df_nu_ih2[d];
+      } else {
+        int lo_f[3] = {lo[0], lo[1], lo[2]}, hi_f[3] = {i, j, k};
+        lo_f[d] += 1;
+        hi_f[d] += 1;
+        sb = df_add(df_from(vel[d][fidx(pr, d, lo[0], lo[1], lo[2])]), df_from(vel[d][fidx(pr, d, i, j, k)]));
+        sf = df_add(df_from(vel[d][fidx(pr, d, lo_f[0], lo_f[1], lo_f[2])]),
+                    df_from(vel[d][fidx(pr, d, hi_f[0], hi_f[1], hi_f[2])]));
+        hb = (idx[d] >= 1);
+        hf = (idx[d] <= ax.n[d] - 2);
+        Db = hb ? pr.df_nu_ih2[d] : (pr.slip[2 * d] ? zero : pr.df_two_nu_ih2[d]);
+        Df = hf ? pr.df_nu_ih2[d] : (pr.slip[2 * d + 1] ? zero : pr.df_two_nu_ih2[d]);
+      }
+      const SplitDf b_ = split_df(sb), f_ = split_df(sf);
+      P = df_add(P, df_add(df_mul(df_sub(f_.pos, b_.neg), pr.df_hh[d]), df_add(Db, Df)));
+      if (hb) nbB[d] = df_neg(df_add(df_mul(b_.pos, pr.df_hh[d]), Db));
+      if (hf) nbF[d] = df_sub(df_mul(f_.neg, pr.df_hh[d]), Df);
+    }
+    double b = fma(own, idt, -(p[c_hi] - p[c_lo]) * pr.ih_irho[A]);
+    if (A == pr.vert) {
+      const double Tf = 0.5 * (T[c_lo] + T[c_hi]);
+      const double Cf = 0.5 * (Cl[c_lo] + Cl[c_hi]);
+      b += pr.gravity * (pr.betaT * (Tf - pr.Tref) + pr.betaC * (Cf - pr.C0));
+    }
+    write_row_df(s, r, pr.dim, P, nbB, nbF, b);
+  }
+}
+
+template <int A>
+__global__ void __launch_bounds__(kBlockA) k_assemble_momentum_df(Params pr, Sys s, const double* __restrict__ u,
+                                                                 const double* __restrict__ v,
+                                                                 const double* __restrict__ w, double* ustar,
+                                                                 const double* __restrict__ p,
+                                                                 const double* __restrict__ T,
+                                                                 const double* __restrict__ Cl,
+                                                                 const double* __restrict__ Kinv) {
+  assemble_momentum_rows_df<A>(pr, s, u, v, w, ustar, p, T, Cl, Kinv, blockIdx.x * blockDim.x + threadIdx.x,
+                               gridDim.x * blockDim.x, (int)s.d.n);
+}
+
 template <int A>
 __global__ void __launch_bounds__(kBlockA) k_assemble_momentum(Params pr, Sys s, const double* __restrict__ u,
                                                               const double* __restrict__ v,
@@ -272,6 +386,94 @@ __device__ __forceinline__ void assemble_cells_rows(const Params& pr, const Sys&
     }
     write_row(s, r, pr.dim, P, nbB, nbF, b);
   }
+}
+
+template <bool SOLUTE>
+__device__ __forceinline__ void assemble_cells_rows_df(const Params& pr, const Sys& s, const double* __restrict__ u,
+                                                       const double* __restrict__ v, const double* __restrict__ w,
+                                                       double* phi_n, const double* __restrict__ gl,
+                                                       const double* __restrict__ Ag,
+                                                       const double* __restrict__ time, double* Tinc, int use_guess,
+                                                       int first, int rstride, int end) {
+  const Axes ax = axes_of(pr);
+  const double* vel[3] = {u, v, w};
+  const int nx = pr.nx, ny = pr.ny;
+  const int stride[3] = {1, nx, nx * ny};
+  const double idt = pr.idt;
+  const dfl zero = {0.f, 0.f};
+  for (int r = first; r < end; r += rstride) {
+    const int i = r % nx, t = r / nx, j = t % ny, k = t / ny;
+    const int idx[3] = {i, j, k};
+    dfl m0 = zero, nbB[3] = {zero, zero, zero}, nbF[3] = {zero, zero, zero};
+    dfl g0 = zero, agc = zero;
+    if (SOLUTE) {
+      g0 = df_from(gl[r]);
+      agc = df_from(Ag[r]);
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      if (a >= pr.dim) break;
+      int fr[3] = {i, j, k};
+      fr[a] += 1;
+      const SplitDf b_ = split_df(df_from(vel[a][fidx(pr, a, i, j, k)]));
+      const SplitDf f_ = split_df(df_from(vel[a][fidx(pr, a, fr[0], fr[1], fr[2])]));
+      const bool hb = idx[a] >= 1, hf = idx[a] <= ax.n[a] - 2;
+      dfl Db = zero, Df = zero;   // diffusion coefficient / h^2 of the back and front faces
+      if (SOLUTE) {
+        if (hb) Db = df_mul(pr.df_half_Dl_ih2[a], df_add(df_from(gl[r - stride[a]]), g0));
+        if (hf) Df = df_mul(pr.df_half_Dl_ih2[a], df_add(g0, df_from(gl[r + stride[a]])));
+      } else {
+        if (hb) Db = pr.df_alpha_ih2[a];
+        if (hf) Df = pr.df_alpha_ih2[a];
+      }
+      m0 = df_add(m0, df_add(df_mul(df_sub(f_.pos, b_.neg), pr.df_ih[a]), df_add(Db, Df)));
+      dfl cb = zero, cf = zero;
+      if (hb) cb = df_neg(df_add(df_mul(b_.pos, pr.df_ih[a]), Db));
+      if (hf) cf = df_sub(df_mul(f_.neg, pr.df_ih[a]), Df);
+      if (SOLUTE) {
+        if (hb) cb = df_mul(cb, df_from(Ag[r - stride[a]]));
+        if (hf) cf = df_mul(cf, df_from(Ag[r + stride[a]]));
+      }
+      nbB[a] = cb;
+      nbF[a] = cf;
+    }
+    const double phi = phi_n[r];
+    double b = phi * idt;
+    if (!SOLUTE && Tinc) {
+      const double inc = Tinc[r];
+      phi_n[r] = use_guess ? phi + inc : phi;
+      Tinc[r] = -phi;
+    }
+    dfl P;
+    if (SOLUTE) {
+      P = df_add(pr.df_idt, df_mul(m0, agc));
+    } else {
+      P = df_add(m0, pr.df_idt);
+      const int wall[6] = {i == 0, i == nx - 1, j == 0, j == ny - 1, pr.dim == 3 && k == 0,
+                           pr.dim == 3 && k == pr.nz - 1};
+#pragma unroll
+      for (int q = 0; q < 6; ++q) {
+        if (wall[q] && ((pr.wall_mask >> q) & 1)) {   // boundary rows only
+          const double t_new = *time + pr.dt;
+          P = df_add(P, pr.df_wall_coef[q]);
+          b += pr.wall_coef[q] * (pr.wall_T0[q] + pr.wall_rate[q] * t_new);
+        }
+      }
+    }
+    write_row_df(s, r, pr.dim, P, nbB, nbF, b);
+  }
+}
+
+template <bool SOLUTE>
+__global__ void __launch_bounds__(kBlockA) k_assemble_cells_df(Params pr, Sys s, const double* __restrict__ u,
+                                                              const double* __restrict__ v,
+                                                              const double* __restrict__ w, double* phi_n,
+                                                              const double* __restrict__ gl,
+                                                              const double* __restrict__ Ag,
+                                                              const double* __restrict__ time, double* Tinc,
+                                                              int use_guess) {
+  assemble_cells_rows_df<SOLUTE>(pr, s, u, v, w, phi_n, gl, Ag, time, Tinc, use_guess,
+                                 blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x, (int)s.d.n);
 }
 
 template <bool SOLUTE>
@@ -636,25 +838,26 @@ __global__ void __launch_bounds__(kBlockA) k_packed_rows(const CaseRows* __restr
   const CaseRows& cs = *reinterpret_cast<const CaseRows*>(buf);
   const int first = t.r0 + threadIdx.x, stride = blockDim.x, end = t.r1;
   if (STAGE == kStageMomentum) {
+    // packed batches are mixed-precision: the double-float assembly
     if (t.part == 0)
-      assemble_momentum_rows<0>(cs.pr, cs.sys[0], cs.u, cs.v, cs.w, cs.ustar[0], cs.p, cs.T, cs.Cl, cs.Kinv, first,
-                                stride, end);
+      assemble_momentum_rows_df<0>(cs.pr, cs.sys[0], cs.u, cs.v, cs.w, cs.ustar[0], cs.p, cs.T, cs.Cl, cs.Kinv,
+                                   first, stride, end);
     else if (t.part == 1)
-      assemble_momentum_rows<1>(cs.pr, cs.sys[1], cs.u, cs.v, cs.w, cs.ustar[1], cs.p, cs.T, cs.Cl, cs.Kinv, first,
-                                stride, end);
+      assemble_momentum_rows_df<1>(cs.pr, cs.sys[1], cs.u, cs.v, cs.w, cs.ustar[1], cs.p, cs.T, cs.Cl, cs.Kinv,
+                                   first, stride, end);
     else
-      assemble_momentum_rows<2>(cs.pr, cs.sys[2], cs.u, cs.v, cs.w, cs.ustar[2], cs.p, cs.T, cs.Cl, cs.Kinv, first,
-                                stride, end);
+      assemble_momentum_rows_df<2>(cs.pr, cs.sys[2], cs.u, cs.v, cs.w, cs.ustar[2], cs.p, cs.T, cs.Cl, cs.Kinv,
+                                   first, stride, end);
   } else if (STAGE == kStageRhs) {
     poisson_rhs_rows(cs.pr, cs.ustar[0], cs.ustar[1], cs.ustar[2], cs.pb, first, stride, end);
   } else if (STAGE == kStageProject) {
     project_rows(cs.pr, cs.u, cs.v, cs.w, cs.ustar[0], cs.ustar[1], cs.ustar[2], cs.pc, cs.p, first, stride, end);
   } else if (STAGE == kStageSolute) {
-    assemble_cells_rows<true>(cs.pr, cs.sys[SS_SYS_C], cs.u, cs.v, cs.w, cs.C, cs.gl, cs.Ag, nullptr, nullptr, 0, first,
-                              stride, end);
+    assemble_cells_rows_df<true>(cs.pr, cs.sys[SS_SYS_C], cs.u, cs.v, cs.w, cs.C, cs.gl, cs.Ag, nullptr, nullptr, 0,
+                                 first, stride, end);
   } else if (STAGE == kStageTemperature) {
-    assemble_cells_rows<false>(cs.pr, cs.sys[SS_SYS_T], cs.u, cs.v, cs.w, cs.T, nullptr, nullptr, &cs.st->time,
-                               cs.Tinc, 1, first, stride, end);
+    assemble_cells_rows_df<false>(cs.pr, cs.sys[SS_SYS_T], cs.u, cs.v, cs.w, cs.T, nullptr, nullptr, &cs.st->time,
+                                  cs.Tinc, 1, first, stride, end);
   } else {
     lever_rows(cs.pr, &cs.st->time, cs.T, cs.gl, cs.C, cs.Cl, cs.Cs, cs.Kinv, cs.Ag, cs.Tinc, 1, first, stride, end);
   }
@@ -720,6 +923,15 @@ cudaError_t launch_assemble_momentum(int comp, const Params& pr, const Sys& sys,
                                      double* ustar, const double* p, const double* T, const double* Cl,
                                      const double* Kinv, cudaStream_t st) {
   const int g = grid_for(sys.d.n);
+  if (sys.af.P) {   // mixed path: double-float coefficients
+    if (comp == 0)
+      k_assemble_momentum_df<0><<<g, kBlockA, 0, st>>>(pr, sys, vel[0], vel[1], vel[2], ustar, p, T, Cl, Kinv);
+    else if (comp == 1)
+      k_assemble_momentum_df<1><<<g, kBlockA, 0, st>>>(pr, sys, vel[0], vel[1], vel[2], ustar, p, T, Cl, Kinv);
+    else
+      k_assemble_momentum_df<2><<<g, kBlockA, 0, st>>>(pr, sys, vel[0], vel[1], vel[2], ustar, p, T, Cl, Kinv);
+    return cudaGetLastError();
+  }
   if (comp == 0)
     k_assemble_momentum<0><<<g, kBlockA, 0, st>>>(pr, sys, vel[0], vel[1], vel[2], ustar, p, T, Cl, Kinv);
   else if (comp == 1)
@@ -731,16 +943,25 @@ cudaError_t launch_assemble_momentum(int comp, const Params& pr, const Sys& sys,
 
 cudaError_t launch_assemble_solute(const Params& pr, const Sys& sys, const double* const vel[3], const double* gl,
                                    const double* C, const double* Ag, cudaStream_t st) {
-  k_assemble_cells<true><<<grid_for(sys.d.n), kBlockA, 0, st>>>(pr, sys, vel[0], vel[1], vel[2], const_cast<double*>(C),
-                                                                gl, Ag, nullptr, nullptr, 0);
+  if (sys.af.P)
+    k_assemble_cells_df<true><<<grid_for(sys.d.n), kBlockA, 0, st>>>(pr, sys, vel[0], vel[1], vel[2],
+                                                                     const_cast<double*>(C), gl, Ag, nullptr,
+                                                                     nullptr, 0);
+  else
+    k_assemble_cells<true><<<grid_for(sys.d.n), kBlockA, 0, st>>>(pr, sys, vel[0], vel[1], vel[2],
+                                                                  const_cast<double*>(C), gl, Ag, nullptr, nullptr, 0);
   return cudaGetLastError();
 }
 
 cudaError_t launch_assemble_temperature(const Params& pr, const Sys& sys, const double* const vel[3],
                                         const double* time, double* T, double* Tinc, int use_guess,
                                         cudaStream_t st) {
-  k_assemble_cells<false><<<grid_for(sys.d.n), kBlockA, 0, st>>>(pr, sys, vel[0], vel[1], vel[2], T, nullptr,
-                                                                 nullptr, time, Tinc, use_guess);
+  if (sys.af.P)
+    k_assemble_cells_df<false><<<grid_for(sys.d.n), kBlockA, 0, st>>>(pr, sys, vel[0], vel[1], vel[2], T, nullptr,
+                                                                      nullptr, time, Tinc, use_guess);
+  else
+    k_assemble_cells<false><<<grid_for(sys.d.n), kBlockA, 0, st>>>(pr, sys, vel[0], vel[1], vel[2], T, nullptr,
+                                                                   nullptr, time, Tinc, use_guess);
   return cudaGetLastError();
 }
 

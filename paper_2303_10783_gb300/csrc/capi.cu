@@ -294,6 +294,16 @@ void fill_params(ss_case* c, const ss_alloy* al) {
       pr.half_Dl_ih2[a] = 0.5 * pr.Dl * pr.ih2[a];
     }
   }
+  for (int a = 0; a < 3; ++a) {
+    pr.df_hh[a] = df_const(pr.hh[a]);
+    pr.df_ih[a] = df_const(pr.ih[a]);
+    pr.df_nu_ih2[a] = df_const(pr.nu_ih2[a]);
+    pr.df_two_nu_ih2[a] = df_const(pr.two_nu_ih2[a]);
+    pr.df_alpha_ih2[a] = df_const(pr.alpha_ih2[a]);
+    pr.df_half_Dl_ih2[a] = df_const(pr.half_Dl_ih2[a]);
+  }
+  pr.df_idt = df_const(pr.idt);
+  pr.df_half_nu = df_const(pr.half_nu);
   pr.wall_mask = 0;
   for (int q = 0; q < 6; ++q) {
     const int axis = q / 2;
@@ -313,6 +323,7 @@ void fill_params(ss_case* c, const ss_alloy* al) {
       pr.wall_rate[q] = bc.dTdt;
     }
     if (pr.wall_coef[q] != 0.0) pr.wall_mask |= 1 << q;
+    pr.df_wall_coef[q] = df_const(pr.wall_coef[q]);
   }
 }
 

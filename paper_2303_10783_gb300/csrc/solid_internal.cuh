@@ -80,6 +80,11 @@ struct Sys {
   double* x;             // solution (aliases a field or a scratch vector)
 };
 
+// A double-float: the value hi + lo held as two FP32s (operations below).
+struct dfl {
+  float hi, lo;
+};
+
 // Physical and numerical parameters passed by value to kernels.
 struct Params {
   int dim, nx, ny, nz, vert;
@@ -113,6 +118,10 @@ struct Params {
   // lever rule (Eq. 3.16-3.17): a = 1 - kp and products of constants with it
   double lev_a, lev_cpLa, lev_aTm, lev_4a, lev_2a;
   double Te;                 // eutectic temperature Tm + m Ce
+  // the assembly constants as double-floats (mixed-path assembly)
+  dfl df_hh[3], df_ih[3], df_nu_ih2[3], df_two_nu_ih2[3], df_alpha_ih2[3], df_half_Dl_ih2[3];
+  dfl df_idt, df_half_nu;
+  dfl df_wall_coef[6];
 };
 
 // Krylov scratch: 8 FP64 vectors + 9 FP32 vectors, each of `nmax` rows with guards.
@@ -377,6 +386,64 @@ __device__ __forceinline__ double to_f64(float f) {
                                             ((unsigned long long)(u & 0x7FFFFFu) << 29)));
   if ((u << 1) == 0u) return __longlong_as_double((long long)sign);
   return (double)f;
+}
+
+// ---- double-float: a value hi + lo held as two FP32s (about 48 significant
+// bits; Dekker's exact sum and product, with the product's error from an
+// FMA). The rounding intrinsics keep the compiler from contracting or
+// reordering the error-free steps.
+// a + b = s + e exactly (Knuth's two-sum)
+__device__ __forceinline__ dfl df_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return {s, e};
+}
+
+__device__ __forceinline__ dfl df_add(dfl a, dfl b) {
+  const dfl s = df_two_sum(a.hi, b.hi);
+  return df_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+
+__device__ __forceinline__ dfl df_neg(dfl a) { return {-a.hi, -a.lo}; }
+
+__device__ __forceinline__ dfl df_sub(dfl a, dfl b) { return df_add(a, df_neg(b)); }
+
+__device__ __forceinline__ dfl df_mul(dfl a, dfl b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  const float e = __fmaf_rn(a.hi, b.hi, -p);
+  return df_two_sum(p, __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, e)));
+}
+
+// FP64 -> double-float on the integer pipes: hi keeps the top 24 bits of
+// the significand (truncated), lo the next 29 rounded to 24, so the pair is
+// within 2^-48 of x. Values outside FP32's normal range take to_f32 with
+// lo = 0, and lo is 0 where it would fall below FP32's normal range
+// (|x| < 2^-74): absolute errors there are below 2^-122.
+__device__ __forceinline__ dfl df_from(double x) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const unsigned hi32 = (unsigned)(u >> 32), lo32 = (unsigned)u;
+  const unsigned e = (hi32 >> 20) & 0x7FFu;
+  const unsigned sign = hi32 & 0x80000000u;
+  if (e - 897u <= 253u) {
+    const unsigned m23 = ((hi32 & 0xFFFFFu) << 3) | (lo32 >> 29);
+    const float h = __uint_as_float(sign | ((e - 896u) << 23) | m23);
+    const unsigned rest = lo32 & 0x1FFFFFFFu;        // rest * 2^(e - 1023 - 52)
+    float l = 0.f;
+    if (rest != 0u && e >= 949u)
+      l = __uint_as_float(__float_as_uint(__fmul_rn(__uint2float_rn(rest), __uint_as_float((e - 948u) << 23))) | sign);
+    return {h, l};
+  }
+  return {to_f32(x), 0.f};
+}
+
+// double-float -> FP64: both halves widened exactly, one FP64 add
+__device__ __forceinline__ double df_to_f64(dfl a) { return to_f64(a.hi) + to_f64(a.lo); }
+
+// an FP64 constant as a double-float, on the host
+inline dfl df_const(double c) {
+  const float hi = (float)c;
+  return {hi, (float)(c - (double)hi)};
 }
 
 // Division by a runtime constant d >= 1 for 0 <= n < 2^31 with a multiply-high

@@ -58,9 +58,13 @@ def _random_case(case, seed, precision=solid.SS_FP64):
     return c, f
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
 @pytest.mark.parametrize("case", SMALL, ids=["2d", "3d"])
-def test_assembly_planes_match_oracle(lib, case):
-    c, f = _random_case(case, 11)
+def test_assembly_planes_match_oracle(lib, case, prec):
+    """Every plane and right-hand side of every system against the oracle's
+    assembly: FP64 arithmetic on the FP64 path, double-float arithmetic for the
+    planes on the mixed path."""
+    c, f = _random_case(case, 11, PREC[prec])
     g = oracle.Grid(case)
     st = _oracle_state(f)
     for a, name in enumerate("uvw"[: case["dim"]]):
@@ -396,10 +400,11 @@ def full():
     return case
 
 
-def test_full_size_assembly_and_lever(lib, full):
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_full_size_assembly_and_lever(lib, full, prec):
     """128x96x96: every assembled row and every lever-rule cell equals the oracle's."""
     case = full
-    c, f = _random_case(case, 21)
+    c, f = _random_case(case, 21, PREC[prec])
     g = oracle.Grid(case)
     st = _oracle_state(f)
     for a, name in enumerate("uvw"):
