@@ -125,7 +125,8 @@ __device__ __forceinline__ void assemble_momentum_rows(const Params& pr, const S
   const int sA = (A == 0) ? 1 : (A == 1) ? mx : mx * my;    // stride of axis A in the row grid
   const double idt = pr.idt;
   for (int r = first; r < end; r += stride) {
-    const int i = r % mx, t = r / mx, j = t % my, k = t / my;
+    int i, j, k;
+    decompose3(r, s.d.fmx, s.d.fmy, i, j, k);
     const int idx[3] = {i, j, k};
     const int f = idx[A];
     const double own = vel[A][r];
@@ -230,7 +231,8 @@ __device__ __forceinline__ void assemble_momentum_rows_df(const Params& pr, cons
   const double idt = pr.idt;
   const dfl zero = {0.f, 0.f};
   for (int r = first; r < end; r += stride) {
-    const int i = r % mx, t = r / mx, j = t % my, k = t / my;
+    int i, j, k;
+    decompose3(r, s.d.fmx, s.d.fmy, i, j, k);
     const int idx[3] = {i, j, k};
     const int f = idx[A];
     const double own = vel[A][r];
@@ -331,7 +333,8 @@ __device__ __forceinline__ void assemble_cells_rows(const Params& pr, const Sys&
   const int stride[3] = {1, nx, nx * ny};
   const double idt = pr.idt;
   for (int r = first; r < end; r += rstride) {
-    const int i = r % nx, t = r / nx, j = t % ny, k = t / ny;
+    int i, j, k;
+    decompose3(r, pr.fnx, pr.fny, i, j, k);
     const int idx[3] = {i, j, k};
     double m0 = 0.0, nbB[3] = {0.0, 0.0, 0.0}, nbF[3] = {0.0, 0.0, 0.0};
 #pragma unroll
@@ -402,7 +405,8 @@ __device__ __forceinline__ void assemble_cells_rows_df(const Params& pr, const S
   const double idt = pr.idt;
   const dfl zero = {0.f, 0.f};
   for (int r = first; r < end; r += rstride) {
-    const int i = r % nx, t = r / nx, j = t % ny, k = t / ny;
+    int i, j, k;
+    decompose3(r, pr.fnx, pr.fny, i, j, k);
     const int idx[3] = {i, j, k};
     dfl m0 = zero, nbB[3] = {zero, zero, zero}, nbF[3] = {zero, zero, zero};
     dfl g0 = zero, agc = zero;
@@ -496,7 +500,8 @@ __device__ __forceinline__ void poisson_rhs_rows(const Params& pr, const double*
   const int nx = pr.nx, ny = pr.ny;
   const double scale = pr.rhs_scale;
   for (int r = first; r < end; r += stride) {
-    const int i = r % nx, t = r / nx, j = t % ny, k = t / ny;
+    int i, j, k;
+    decompose3(r, pr.fnx, pr.fny, i, j, k);
     double div = (us[fidx(pr, 0, i + 1, j, k)] - us[fidx(pr, 0, i, j, k)]) * ax.ih[0] +
                  (vs[fidx(pr, 1, i, j + 1, k)] - vs[fidx(pr, 1, i, j, k)]) * ax.ih[1];
     if (pr.dim == 3) div += (ws[fidx(pr, 2, i, j, k + 1)] - ws[fidx(pr, 2, i, j, k)]) * ax.ih[2];
@@ -596,13 +601,22 @@ __device__ __forceinline__ void lever_rows(const Params& pr, double* time, doubl
   for (int r = first; r < n; r += stride) {
     const double Ts = T[r], gn = gl[r], Cn = C[r];
     const double Tl = Tm + pr.m * Cn;                                       // Eq. 3.14
-    const double b = kp - gn * a + pr.lev_cpLa * (Tm - Ts);                // Eq. 3.17
-    const double c = -(gn + cpL * Ts) * kp + cpL * (Tl - pr.lev_aTm);
-    const double sq = sqrt(fmax(b * b - pr.lev_4a * c, 0.0));
-    // larger root of Eq. 3.16 (a > 0), in the form free of cancellation
-    double g = (b > 0.0) ? (2.0 * c) / (-b - sq) : (-b + sq) / pr.lev_2a;
-    g = fmin(fmax(g, 0.0), 1.0);
-    double Tn = Ts - Lcp * (g - gn);                                         // Eq. 3.13
+    double g, Tn;
+    if (gn == 1.0 && Ts >= Tl) {
+      // a fully liquid cell at or above its liquidus stays liquid: the lever
+      // solution is g = 1 and T = T* (the root of Eq. 3.16 is >= 1 and is
+      // clamped to 1, so Eq. 3.13 leaves T* unchanged)
+      g = 1.0;
+      Tn = Ts;
+    } else {
+      const double b = kp - gn * a + pr.lev_cpLa * (Tm - Ts);              // Eq. 3.17
+      const double c = -(gn + cpL * Ts) * kp + cpL * (Tl - pr.lev_aTm);
+      const double sq = sqrt(fmax(b * b - pr.lev_4a * c, 0.0));
+      // larger root of Eq. 3.16 (a > 0), in the form free of cancellation
+      g = (b > 0.0) ? (2.0 * c) / (-b - sq) : (-b + sq) / pr.lev_2a;
+      g = fmin(fmax(g, 0.0), 1.0);
+      Tn = Ts - Lcp * (g - gn);                                              // Eq. 3.13
+    }
     if (pr.has_eutectic && Tn < Te && g > 0.0) {   // isothermal eutectic plateau
       const double ge = gn - cpL * (Te - Ts);
       if (ge >= 0.0) { g = ge; Tn = Te; }

@@ -193,10 +193,10 @@ void plan(ss_case* c, Planner& pl) {
     S.af = af[set];
     S.b = b[set];
     if (s <= SS_SYS_W) {
-      S.d = {mdims[s][0], mdims[s][1], mdims[s][2], c->n_face[s]};
+      S.d = {mdims[s][0], mdims[s][1], mdims[s][2], c->n_face[s], make_fastdiv(mdims[s][0]), make_fastdiv(mdims[s][1])};
       S.x = c->ustar[s];
     } else {
-      S.d = {(int)nx, (int)ny, (int)nz, c->n_cell};
+      S.d = {(int)nx, (int)ny, (int)nz, c->n_cell, make_fastdiv((unsigned)nx), make_fastdiv((unsigned)ny)};
       S.x = (s == SS_SYS_C) ? c->C : (s == SS_SYS_T) ? c->T : c->pc;
     }
   }
@@ -254,6 +254,8 @@ void fill_params(ss_case* c, const ss_alloy* al) {
   pr.ny = c->g.ny;
   pr.nz = c->g.dim == 3 ? c->g.nz : 1;
   pr.vert = c->g.dim == 2 ? 1 : 2;
+  pr.fnx = make_fastdiv((unsigned)pr.nx);
+  pr.fny = make_fastdiv((unsigned)pr.ny);
   pr.hx = c->g.lx / c->g.nx;
   pr.hy = c->g.ly / c->g.ny;
   pr.hz = c->g.dim == 3 ? c->g.lz / c->g.nz : 1.0;

@@ -34,9 +34,15 @@ inline long long blocks_wanted(long long rows) {
 // device-side error codes (sticky word in DevStatus::err)
 enum : int { kErrNone = 0, kErrBarrier = 1 };
 
+// Division by a runtime constant (make_fastdiv / fdiv below).
+struct FastDiv {
+  unsigned int d, m, s;
+};
+
 struct Dims {
   int mx, my, mz;      // row grid of a system / field
   long long n;         // mx * my * mz
+  FastDiv fmx, fmy;    // division by mx and my (row -> i, j, k)
 };
 
 // Per-solve outcome written by the solver kernels.
@@ -95,6 +101,7 @@ struct Params {
   // T_w(t) = wall_T0 + wall_rate t (coef 0: adiabatic). Robin: coef = U/(rho cp h),
   // U = 1/(1/h_c + h/2k), rate 0; Dirichlet: coef = 2k/(rho cp h^2).
   double wall_coef[6], wall_T0[6], wall_rate[6];
+  FastDiv fnx, fny;          // division by nx and ny (cell -> i, j, k)
   int slip[6];   // 1: free-slip wall (tangential ghost = interior), 0: no-slip
   int wall_mask; // bit q set when wall q is cooled (wall_coef[q] != 0): an integer test per row
   // Launch constants formed once on the host (IEEE division rounds the same
@@ -449,10 +456,6 @@ inline dfl df_const(double c) {
 // Division by a runtime constant d >= 1 for 0 <= n < 2^31 with a multiply-high
 // and a shift: q = (umulhi(n, m) + n) >> s, s = ceil(log2 d),
 // m = floor(2^32 (2^s - d) / d) + 1 (round-up method of Granlund & Montgomery).
-struct FastDiv {
-  unsigned int d, m, s;
-};
-
 inline FastDiv make_fastdiv(unsigned int d) {
   FastDiv f;
   f.d = d;
