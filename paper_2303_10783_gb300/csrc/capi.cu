@@ -433,6 +433,24 @@ constexpr double kInnerTolPressure = 3.0e-6;
 constexpr double kInnerTolEnergy = 1.0e-4;
 constexpr double kInnerTolTransport = 1.0e-5;
 
+// The mixed T* solve starts with FP64 defect correction around the transform
+// inverse of its constant-coefficient part I/dt - alpha L when the terms that
+// inverse leaves out are small: every cooled wall's coefficient at most this
+// fraction of 1/dt (Robin films in the workloads: ~0.4%; the half-cell
+// Dirichlet walls of Example 2 are comparable to 1/dt and keep BiCGSTAB
+// alone). Measured on the oracle's T* system at 64x48x48, a sweep reduces
+// the residual by ~1.6e-3 (BiCGSTAB needed 16 inner iterations); three
+// sweeps reach the benchmark tolerance from the T* initial guess.
+constexpr double kHelmholtzWallFraction = 0.05;
+constexpr int kHelmholtzSweeps = 3;
+
+bool transform_energy_solve(const ss_case* c) {
+  if (c->g.precision != SS_MIXED || !c->dct.tables || !c->dct.fp32) return false;
+  for (int q = 0; q < 6; ++q)
+    if (c->pr.wall_coef[q] > kHelmholtzWallFraction * c->pr.idt) return false;
+  return true;
+}
+
 ss_status stage_solve(ss_case* c, int sys, bool fuse_project = false) {
   StageTimer tm(c, SS_PROF_SOLVE + (sys >= 0 && sys < SS_NSYS ? sys : 0), 1);
   SolverCtl ctl;
@@ -463,7 +481,13 @@ ss_status stage_solve(ss_case* c, int sys, bool fuse_project = false) {
     if (sys == SS_SYS_W && c->pr.dim != 3) return SS_OK;
     ctl.tol = c->g.tol_t;
     ctl.max_it = c->g.max_it_t;
-    e = launch_bicgstab(c->sys[sys], c->pr.dim == 3, ctl, c->sc[0], c->st, c->stream);
+    e = cudaSuccess;
+    if (sys == SS_SYS_T && transform_energy_solve(c)) {
+      e = launch_helmholtz_dct(c->dct, c->pr, c->sys[sys], c->pr.dim == 3, kHelmholtzSweeps, ctl, c->sc[0], c->st,
+                               c->stream);
+      c->launches[SS_PROF_SOLVE + sys] += 1;
+    }
+    if (e == cudaSuccess) e = launch_bicgstab(c->sys[sys], c->pr.dim == 3, ctl, c->sc[0], c->st, c->stream);
   } else {
     return fail(SS_EINVAL, "unknown system %d", sys);
   }

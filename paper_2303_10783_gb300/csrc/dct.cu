@@ -77,6 +77,10 @@ struct DctArgs {
   int warm;                 // start from the x in place (else from 0)
   int thomas_cols;          // columns per shared-memory chunk of the tridiagonal solves
   int slab_smem;            // 1: pass B keeps each slab in shared memory (FP32 slabs that fit)
+  // Helmholtz mode (the T* pre-solve): the transforms invert s0 I - L instead
+  // of -L (no null space), s0 = shift, for the operator I/dt - alpha L
+  double shift;
+  int helm;
   double* partial;
   int max_blocks;
   DevStatus* st;
@@ -381,8 +385,8 @@ __device__ void pass_b_slab(const DctArgs<float>& A, const Team& tm, float* sm) 
     // tridiagonal solves along t, one column ky per thread
     const float sx = A.lx[kx];
     for (int c = threadIdx.x; c < My; c += blockDim.x) {
-      const float s = sx + A.ly[c];
-      const bool singular = kx == 0 && c == 0;
+      const float s = sx + A.ly[c] + (float)A.shift;
+      const bool singular = !A.helm && kx == 0 && c == 0;
       const int m = singular ? Mt - 1 : Mt;
       if (m <= 0) {
         Ts[c] = 0.f;
@@ -442,7 +446,8 @@ __device__ void pass_b(const DctArgs<TP>& A, const Team& tm, TP* sm) {
     for (int c0 = tm.rank * w; c0 < Mx; c0 += tm.size * w) {
       const int cw = (Mx - c0 < w) ? Mx - c0 : w;
       thomas_chunk<TP>(
-          A.T1, 1, R, Mt, c0, cw, at, [&](int c) { return lx[c]; }, [&](int c) { return c == 0; }, sm);
+          A.T1, 1, R, Mt, c0, cw, at, [&](int c) { return lx[c] + (TP)A.shift; },
+          [&](int c) { return !A.helm && c == 0; }, sm);
     }
     return;
   }
@@ -462,7 +467,8 @@ __device__ void pass_b(const DctArgs<TP>& A, const Team& tm, TP* sm) {
     for (int c0 = 0; c0 < My; c0 += w) {
       const int cw = (My - c0 < w) ? My - c0 : w;
       thomas_chunk<TP>(
-          S2, My, 1, Mt, c0, cw, at, [&](int c) { return sx + ly[c]; }, [&](int c) { return kx == 0 && c == 0; },
+          S2, My, 1, Mt, c0, cw, at, [&](int c) { return sx + ly[c] + (TP)A.shift; },
+          [&](int c) { return !A.helm && kx == 0 && c == 0; },
           sm);
     }
     for (int tile = 0; tile < mt * nt; ++tile) {
@@ -673,6 +679,109 @@ __device__ bool poisson_dct_team(const DctArgs<TP>& A, const Team& tm, TP* sm) {
   return true;
 }
 
+// One row of a DIA system in FP64 (the guard bands make every neighbour
+// read valid; an absent neighbour's coefficient is 0).
+__device__ __forceinline__ double spmv64(const Planes<double>& a, const double* x, int r, int sy, int sz, int has_z) {
+  double acc = a.P[r] * x[r];
+  acc = fma(a.W[r], x[r - 1], acc);
+  acc = fma(a.E[r], x[r + 1], acc);
+  acc = fma(a.S[r], x[r - sy], acc);
+  acc = fma(a.N[r], x[r + sy], acc);
+  if (has_z) {
+    acc = fma(a.B[r], x[r - sz], acc);
+    acc = fma(a.T_[r], x[r + sz], acc);
+  }
+  return acc;
+}
+
+// The T* system (Eq. 3.12) by FP64 defect correction around the inverse of
+// its constant-coefficient part I/dt - alpha L (zero-flux walls), by the
+// same transforms with the shift 1/(alpha dt): each sweep forms the FP64
+// residual b - A x with the system's own FP64 planes (upwind convection and
+// cooled walls included), applies the inverse and adds the correction. The
+// parts the inverse leaves out are small beside 1/dt where this is used, so
+// a sweep reduces the residual by ~1e-3; the caller's BiCGSTAB refinement
+// follows and only has to confirm the tolerance. Sweeps add to the system's
+// iteration count. x holds the initial guess.
+__device__ bool helmholtz_team(const DctArgs<float>& A, const Sys& S, int has_z, double inv_alpha, int max_sweeps,
+                               const Team& tm, float* sm) {
+  unsigned int epoch = 0;
+  const int n = (int)S.d.n;
+  const int sy = S.d.mx, sz = S.d.mx * S.d.my;
+  const int t0 = tm.rank * blockDim.x + threadIdx.x, gsz = tm.size * blockDim.x;
+  const double* b = S.b;
+  double* x = S.x;
+  float* rs = A.T2;
+  __shared__ struct {
+    double rn, sc, pscale;
+    int go;
+  } hs;
+  double thr = 0.0;   // read by thread 0 only
+  double ps = 1.0;    // the first staged residual is not scaled (T* residuals are O(1) in K/s)
+  Vec<2> s0 = {{0.0, 0.0}};
+  for (int c = t0; c < n; c += gsz) {
+    const double rc = b[c] - spmv64(S.a, x, c, sy, sz, has_z);
+    rs[c] = to_f32(rc);
+    s0.v[0] += b[c] * b[c];
+    s0.v[1] += rc * rc;
+  }
+  if (!team_sum_post<2>(s0, tm, A.max_blocks, 0, A.st, epoch, [&](const double* tot) {
+        const double bn = sqrt(tot[0]);
+        hs.rn = sqrt(tot[1]);
+        thr = A.tol * bn;
+        hs.go = bn > 0.0 && hs.rn > thr && isfinite(hs.rn);
+        hs.sc = 1.0 / hs.rn;
+        int e = 0;
+        frexp(hs.rn, &e);
+        hs.pscale = ldexp(1.0, -e);
+      }))
+    return false;
+  int sweeps = 0;
+  while (hs.go && sweeps < max_sweeps) {
+    ++sweeps;
+    const double rn = hs.rn;
+    pass_a<float>(A, tm, (float)hs.sc, 0.f, sm);
+    if (!team_barrier(A.st, tm, epoch)) return false;
+    pass_b<float>(A, tm, sm);
+    if (!team_barrier(A.st, tm, epoch)) return false;
+    pass_c<float>(A, tm, rn * inv_alpha, sm);
+    if (!team_barrier(A.st, tm, epoch)) return false;
+    ps = hs.pscale;
+    Vec<1> s1 = {{0.0}};
+    for (int c = t0; c < n; c += gsz) {
+      const double rc = b[c] - spmv64(S.a, x, c, sy, sz, has_z);
+      rs[c] = to_f32(rc * ps);
+      s1.v[0] += rc * rc;
+    }
+    if (!team_sum_post<1>(s1, tm, A.max_blocks, 1, A.st, epoch, [&](const double* tot) {
+          const double rn_new = sqrt(tot[0]);
+          hs.go = rn_new > thr && isfinite(rn_new) && rn_new < 0.5 * hs.rn;
+          hs.sc = 1.0 / (hs.pscale * rn_new);
+          hs.rn = rn_new;
+          int e = 0;
+          frexp(rn_new, &e);
+          hs.pscale = ldexp(1.0, -e);
+        }))
+      return false;
+  }
+  if (tm.rank == 0 && threadIdx.x == 0) A.st->stat[A.stat_index].iters_total += sweeps;
+  return true;
+}
+
+struct HelmArgs {
+  DctArgs<float> dct;
+  Sys sys;
+  int has_z;
+  double inv_alpha;
+  int max_sweeps;
+};
+
+__global__ void __launch_bounds__(kBlock, 1) k_helmholtz_dct(HelmArgs H) {
+  extern __shared__ __align__(16) unsigned char dsm[];
+  const Team tm{(int)blockIdx.x, (int)gridDim.x, &H.dct.st->barrier, H.dct.partial};
+  helmholtz_team(H.dct, H.sys, H.has_z, H.inv_alpha, H.max_sweeps, tm, reinterpret_cast<float*>(dsm));
+}
+
 template <typename TP>
 __global__ void __launch_bounds__(kBlock, 1) k_poisson_dct(DctArgs<TP> A) {
   extern __shared__ __align__(16) unsigned char dsm[];
@@ -824,6 +933,28 @@ void dct_tables(const DctPlan& pl, const Params& pr, double* out) {
     Cy[0] = 1.0;
     ly[0] = 0.0;
   }
+}
+
+cudaError_t launch_helmholtz_dct(const DctPlan& pl, const Params& pr, const Sys& sys, int has_z, int max_sweeps,
+                                 const SolverCtl& ctl, Scratch& sc, DevStatus* st, cudaStream_t s) {
+  if (!pl.fp32) return cudaErrorInvalidValue;
+  HelmArgs H;
+  memset(&H, 0, sizeof H);
+  const size_t smem = make_args<float>(H.dct, pl, pr, sys.b, sys.x, ctl, sc, st, nullptr);
+  H.dct.helm = 1;
+  H.dct.shift = 1.0 / (pr.alphaT * pr.dt);   // 1/(alpha dt), in the 1/h^2 units of the transforms
+  H.sys = sys;
+  H.has_z = has_z;
+  H.inv_alpha = 1.0 / pr.alphaT;
+  H.max_sweeps = max_sweeps;
+  const void* kern = (const void*)k_helmholtz_dct;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int cap = ctl.block_cap > 0 && ctl.block_cap < sc.max_blocks ? ctl.block_cap : sc.max_blocks;
+  const int nb = coop_blocks_for_smem(kern, (long long)sys.d.n, cap, smem);
+  if ((e = cudaMemsetAsync(&st->barrier, 0, sizeof(unsigned int), s)) != cudaSuccess) return e;
+  void* args[] = {&H};
+  return cudaLaunchCooperativeKernel(kern, dim3(nb), dim3(kBlock), args, smem, s);
 }
 
 size_t packed_dct_args_bytes() { return sizeof(DctArgs<float>); }

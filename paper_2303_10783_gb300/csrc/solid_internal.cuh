@@ -617,6 +617,11 @@ struct ProjectPtrs {
 // the zero-mean p', and p += p'), bit for bit what the projection stage gives.
 cudaError_t launch_poisson_dct(const DctPlan& pl, const Params& pr, double* b, double* x, const SolverCtl& ctl,
                                Scratch& sc, DevStatus* st, const ProjectPtrs* proj, cudaStream_t s);
+// The T* system (mixed path) by FP64 defect correction around the FP32
+// transform inverse of I/dt - alpha L, at most max_sweeps sweeps, starting
+// from the x in place; the BiCGSTAB refinement follows it.
+cudaError_t launch_helmholtz_dct(const DctPlan& pl, const Params& pr, const Sys& sys, int has_z, int max_sweeps,
+                                 const SolverCtl& ctl, Scratch& sc, DevStatus* st, cudaStream_t s);
 // the pressure solves of a packed batch (FP32 transforms), one team per case
 size_t packed_dct_args_bytes();
 size_t fill_packed_dct_args(void* out, const DctPlan& pl, const Params& pr, double* b, double* x, const SolverCtl& ctl,
