@@ -70,6 +70,12 @@ DCT_THOMAS_FLOPS = 8.0
 BCG_IR_BYTES_ROW = 80.0
 BCG_IR_BYTES_ROW_SWEEP = 132.0
 BCG_IR_BYTES_ROW_IT = 136.0
+# k_helmholtz_dct (the T* pre-solve of the mixed path), per cell: the first FP64 residual with
+#   the system's 7 FP64 planes, x and b, staged in FP32 (76 B); per sweep the transforms move
+#   the staged residual and T1 (4 + 4 + 8 in passes A and B), pass C reads T1 and reads and
+#   writes x (20), the FP64 residual again (76): 112 B; 4 (n_x + n_y) + 8 FP32 flop per sweep.
+HELM_BYTES_PER_CELL = 76.0
+HELM_BYTES_PER_CELL_SWEEP = 112.0
 # k_bicgstab (FP64 transport), per row and iteration: two SpMVs over 7 FP64 planes (2 x 72)
 # and the vector updates (~156 B): 300 B; 2 x 13 + 20 = 46 FP64 flops.
 BCG_BYTES_ROW_IT = 300.0
@@ -241,7 +247,7 @@ def measured_peaks():
 
 
 KERNEL_SOURCES = {"k_pcg_mg": "mg.cu", "k_poisson_dct": "dct.cu", "k_bicgstab_ir": "krylov.cu",
-                  "k_bicgstab": "krylov.cu", "k_pcg_poisson": "krylov.cu"}
+                  "k_bicgstab": "krylov.cu", "k_pcg_poisson": "krylov.cu", "k_helmholtz_dct": "dct.cu"}
 
 
 def kernel_source_sha(kernel="k_pcg_mg"):
@@ -479,28 +485,33 @@ def _rows(case, sysname):
 
 
 def kernel_work(stage, precision_name, case, prof, stats):
-    """Algorithmic work of one launch of the solve kernel of `stage` (from the
+    """Algorithmic work of the launches of `stage` in the timed steps (from the
     per-unit figures above and the measured iterations): (kernel, launches,
-    bytes per launch, flops per launch, flop type, counts)."""
+    bytes, flops, flop type, counts), bytes and flops summed over its launches."""
     mixed = precision_name == "mixed"
-    launches = max(prof["launches"][stage], 1)
-    sysname = stage.split("_", 1)[1]
+    launches = prof["launches"][stage]
     ncell = _rows(case, "p")
     precond = case.get("precond_p", "dct")
+    modes = case["nx"] + (case["ny"] if case["dim"] == 3 else 0)
+    if stage == "presolve_T":
+        sweeps = prof.get("presolve_sweeps", 0)
+        nbytes = ncell * (HELM_BYTES_PER_CELL * launches + HELM_BYTES_PER_CELL_SWEEP * sweeps)
+        flops = ncell * sweeps * (4.0 * modes + DCT_THOMAS_FLOPS)
+        return "k_helmholtz_dct", launches, nbytes, flops, "fp32", {"sweeps": sweeps, "cells": ncell}
+    sysname = stage.split("_", 1)[1]
     if sysname == "p":
-        its = prof["iters"]["p"] / launches
+        its = prof["iters"]["p"]
         if precond == "dct":
             E = 4.0 if mixed else 8.0
-            My = case["ny"] if case["dim"] == 3 else 0
-            nbytes = ncell * (DCT_BYTES_PER_CELL_LAUNCH + its * (DCT_BYTES_PER_CELL_SWEEP_BASE + 8.0 * E))
-            flops = ncell * its * (4.0 * (case["nx"] + My) + DCT_THOMAS_FLOPS)
+            nbytes = ncell * (DCT_BYTES_PER_CELL_LAUNCH * launches + its * (DCT_BYTES_PER_CELL_SWEEP_BASE + 8.0 * E))
+            flops = ncell * its * (4.0 * modes + DCT_THOMAS_FLOPS)
             kern = "k_poisson_dct<%s>" % ("float" if mixed else "double")
             return kern, launches, nbytes, flops, "fp32" if mixed else "fp64", {"sweeps": its, "cells": ncell}
-        refs = stats["refinements"]["p"]
+        refs = stats["refinements"]["p"] * launches
         nbytes = ncell * (MG_BYTES_PER_CELL_IT[precision_name] * its + MG_BYTES_PER_CELL_REFINE * refs)
         flops = MG_FLOPS_PER_CELL_IT * ncell * its
         kern = "k_pcg_mg<%s>" % ("float" if mixed else "double")
-        return kern, launches, nbytes, flops, "fp64", {"iterations": its, "refinements": refs, "cells": ncell}
+        return kern, launches, nbytes, flops, "fp64", {"iterations": its, "cells": ncell}
     systems = [sysname]
     if stage == "solve_u" and prof["launches"].get("solve_v", 0) == 0:
         systems = list("uvw"[: case["dim"]])     # the joint momentum launch, counted under solve_u
@@ -508,10 +519,10 @@ def kernel_work(stage, precision_name, case, prof, stats):
     counts = {}
     for q in systems:
         rows = _rows(case, q)
-        its = prof["iters"][q] / launches
+        its = prof["iters"][q]
         if mixed:
-            sweeps = stats["refinements"][q]
-            nbytes += rows * (BCG_IR_BYTES_ROW + BCG_IR_BYTES_ROW_SWEEP * sweeps + BCG_IR_BYTES_ROW_IT * its)
+            sweeps = stats["refinements"][q] * launches    # sweeps of the last step, for each launch
+            nbytes += rows * (BCG_IR_BYTES_ROW * launches + BCG_IR_BYTES_ROW_SWEEP * sweeps + BCG_IR_BYTES_ROW_IT * its)
             counts[q] = {"rows": rows, "inner_iterations": its, "sweeps": sweeps}
         else:
             nbytes += rows * BCG_BYTES_ROW_IT * its
@@ -521,38 +532,54 @@ def kernel_work(stage, precision_name, case, prof, stats):
 
 
 def roofline(precision_name, m, case, steps, wname):
-    """Roofline of the dominant solve stage of a step: its kernel's algorithmic
-    bytes and flops per launch over the launch's device time (CUDA events on
-    the case stream), against the measured HBM copy bandwidth and the FP32 or
-    FP64 pipe's peak at the median SM clock sampled during the timed region;
-    the bound is whichever resource takes longer at its peak."""
-    stage_ms = m["prof"]["ms"]
-    solves = {k: v for k, v in stage_ms.items() if k.startswith("solve_") and m["prof"]["launches"].get(k, 0) > 0}
-    top = max(solves, key=solves.get)
+    """Roofline of the step's dominant kernel: the solver kernel with the most
+    device time per step, its launches summed over the stages that run it.
+    Achieved = its algorithmic bytes (or flops, when those take longer at
+    their peak) over its device time (CUDA events on the case stream), against
+    the measured HBM copy bandwidth or the FP32 / FP64 pipe's peak at the
+    median SM clock sampled during the timed region."""
+    prof = m["prof"]
+    stage_ms = prof["ms"]
     peaks = measured_peaks()
     sm_mhz = m["clocks"].get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
-    kern, launches, nbytes, flops, ftype, counts = kernel_work(top, precision_name, case, m["prof"], m["stats"])
-    t_launch = stage_ms[top] * 1e-3 / launches
     hbm = peaks.get("hbm_gbs", 6687.1)
-    per_clk = FP32_FLOP_PER_CLK_PER_SM if ftype == "fp32" else FP64_FLOP_PER_CLK_PER_SM
-    fpeak = per_clk * NUM_SMS * sm_mhz * 1e6 / 1e12
-    out = {"kernel": kern, "stage": top, "launch_ms": t_launch * 1e3,
-           "algorithmic_per_launch": {"bytes": nbytes, "flops": flops, "flop_type": ftype, "counts": counts},
-           "hbm_frac": nbytes / t_launch / 1e9 / hbm, "alu_frac": flops / t_launch / 1e12 / fpeak}
-    if nbytes / (hbm * 1e9) >= flops / (fpeak * 1e12):
-        ach = nbytes / t_launch / 1e9
-        out.update(bound="hbm", achieved=ach, peak=hbm, unit="GB/s", frac=ach / hbm,
-                   peak_basis="measured HBM copy bandwidth (MEASURED_PEAKS.json)")
-    else:
-        ach = flops / t_launch / 1e12
-        out.update(bound="alu", achieved=ach, peak=fpeak, unit="TFLOP/s", frac=ach / fpeak,
-                   peak_basis="%s pipe: %.0f flop/clk/SM x %d SMs x %.0f MHz median SM clock under load"
-                              % (ftype.upper(), per_clk, NUM_SMS, sm_mhz))
-    tr = kernel_traffic(kern, wname)
-    out["traffic"] = tr[0] if tr else None
-    top_all = max(stage_ms, key=stage_ms.get)
-    if top_all != top:
-        out["dominant_stage"] = top_all
+    kernels = {}
+    for st in stage_ms:
+        if not (st.startswith("solve_") or st == "presolve_T") or prof["launches"].get(st, 0) <= 0:
+            continue
+        kern, launches, nbytes, flops, ftype, counts = kernel_work(st, precision_name, case, prof, m["stats"])
+        k = kernels.setdefault(kern, {"ms": 0.0, "launches": 0, "bytes": 0.0, "flops": 0.0, "flop_type": ftype,
+                                      "stages": {}})
+        k["ms"] += stage_ms[st]
+        k["launches"] += launches
+        k["bytes"] += nbytes
+        k["flops"] += flops
+        k["stages"][st] = counts
+    top = max(kernels, key=lambda q: kernels[q]["ms"])
+    detail = {}
+    for kern, k in kernels.items():
+        t = k["ms"] * 1e-3
+        per_clk = FP32_FLOP_PER_CLK_PER_SM if k["flop_type"] == "fp32" else FP64_FLOP_PER_CLK_PER_SM
+        fpeak = per_clk * NUM_SMS * sm_mhz * 1e6 / 1e12
+        d = {"ms_per_step": k["ms"] / steps, "launch_ms": k["ms"] / max(k["launches"], 1),
+             "bytes_per_launch": k["bytes"] / max(k["launches"], 1), "flops_per_launch": k["flops"] / max(k["launches"], 1),
+             "flop_type": k["flop_type"], "hbm_frac": k["bytes"] / t / 1e9 / hbm,
+             "alu_frac": k["flops"] / t / 1e12 / fpeak, "stages": k["stages"]}
+        if k["bytes"] / (hbm * 1e9) >= k["flops"] / (fpeak * 1e12):
+            ach = k["bytes"] / t / 1e9
+            d.update(bound="hbm", achieved=ach, peak=hbm, unit="GB/s", frac=ach / hbm,
+                     peak_basis="measured HBM copy bandwidth (MEASURED_PEAKS.json)")
+        else:
+            ach = k["flops"] / t / 1e12
+            d.update(bound="alu", achieved=ach, peak=fpeak, unit="TFLOP/s", frac=ach / fpeak,
+                     peak_basis="%s pipe: %.0f flop/clk/SM x %d SMs x %.0f MHz median SM clock under load"
+                                % (k["flop_type"].upper(), per_clk, NUM_SMS, sm_mhz))
+        tr = kernel_traffic(kern, wname)
+        d["traffic"] = tr[0] if tr else None
+        detail[kern] = d
+    out = dict(detail[top])
+    out["kernel"] = top
+    out["all_kernels"] = {k: {q: v for q, v in d.items() if q != "stages"} for k, d in detail.items() if k != top}
     return out
 
 

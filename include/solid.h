@@ -151,12 +151,16 @@ typedef struct {
  * count under the pressure solve, and the projection stage stays at 0. */
 enum { SS_PROF_ASSEMBLE = 0,   /* + SS_SYS_*: assembly of that system */
        SS_PROF_SOLVE = 6,      /* + SS_SYS_*: its solve */
-       SS_PROF_PROJECT = 12, SS_PROF_LEVER = 13, SS_NPROF = 14 };
+       SS_PROF_PROJECT = 12, SS_PROF_LEVER = 13,
+       SS_PROF_PRESOLVE_T = 14, /* the transform pre-solve of a mixed T* solve */
+       SS_NPROF = 15 };
 typedef struct {
   double ms[SS_NPROF];
   long long launches[SS_NPROF];
   long long kernels;        /* total library kernel launches */
-  long long iters[SS_NSYS]; /* Krylov iterations summed over the solves of each system */
+  long long iters[SS_NSYS]; /* Krylov iterations summed over the solves of each system
+                               (refinement sweeps for the transform pressure solver) */
+  long long presolve_sweeps;/* sweeps of the T* transform pre-solve */
 } ss_profile;
 
 /* Bytes of device workspace a case of this grid needs (256-byte aligned
@@ -317,8 +321,9 @@ ss_status ss_lever(ss_case* c);
  * solve (Eq. 3.3, 3.4, 3.10, 3.12) is one cooperative launch in which every
  * case is solved by its own team of blocks, so uneven cases run side by side
  * without a launch per case; the pressure solve ends with the projection
- * (Eq. 3.5). Nine launches per batch step; on a non-default stream they are
- * captured once into a CUDA graph and replayed.
+ * (Eq. 3.5), and the T* solve starts, where ss_step's does, with the
+ * transform pre-solve. Ten launches per batch step; on a non-default stream
+ * they are captured once into a CUDA graph and replayed.
  * A member's fields agree with the same case stepped alone to rounding (the
  * reductions of a team of k blocks are ordered like a launch of k blocks);
  * the batch is deterministic for a given schedule.

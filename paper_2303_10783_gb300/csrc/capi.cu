@@ -443,16 +443,21 @@ constexpr double kInnerTolTransport = 1.0e-5;
 // sweeps reach the benchmark tolerance from the T* initial guess.
 constexpr double kHelmholtzWallFraction = 0.05;
 constexpr int kHelmholtzSweeps = 3;
+// The transforms cost 2 (n_x + n_y) multiply-adds per cell and sweep: beyond
+// this many modes three sweeps cost more than the BiCGSTAB iterations they
+// replace (measured: 128 + 96 on the box, 0.58 -> 0.36 ms; 384 + 256 on the
+// ingot, 8.1 -> 11.9 ms).
+constexpr int kHelmholtzMaxModes = 320;
 
 bool transform_energy_solve(const ss_case* c) {
   if (c->g.precision != SS_MIXED || !c->dct.tables || !c->dct.fp32) return false;
+  if (c->pr.nx + (c->pr.dim == 3 ? c->pr.ny : 0) > kHelmholtzMaxModes) return false;
   for (int q = 0; q < 6; ++q)
     if (c->pr.wall_coef[q] > kHelmholtzWallFraction * c->pr.idt) return false;
   return true;
 }
 
 ss_status stage_solve(ss_case* c, int sys, bool fuse_project = false) {
-  StageTimer tm(c, SS_PROF_SOLVE + (sys >= 0 && sys < SS_NSYS ? sys : 0), 1);
   SolverCtl ctl;
   ctl.mixed = c->g.precision == SS_MIXED;
   ctl.block_cap = c->block_cap;
@@ -468,6 +473,7 @@ ss_status stage_solve(ss_case* c, int sys, bool fuse_project = false) {
     // (the FP64 transform solve converges in one sweep: a warm start would
     // only add a residual pass)
     ctl.warm_start = !(c->g.precond_p == SS_PRECOND_DCT && c->g.precision == SS_FP64);
+    StageTimer tm(c, SS_PROF_SOLVE + sys, 1);
     if (c->g.precond_p == SS_PRECOND_MG)
       e = launch_pcg_mg(c->mg, c->pr, c->pb, c->pc, ctl, c->sc[0], c->st, c->stream);
     else if (c->g.precond_p == SS_PRECOND_DCT) {
@@ -483,11 +489,14 @@ ss_status stage_solve(ss_case* c, int sys, bool fuse_project = false) {
     ctl.max_it = c->g.max_it_t;
     e = cudaSuccess;
     if (sys == SS_SYS_T && transform_energy_solve(c)) {
+      StageTimer pre(c, SS_PROF_PRESOLVE_T, 1);
       e = launch_helmholtz_dct(c->dct, c->pr, c->sys[sys], c->pr.dim == 3, kHelmholtzSweeps, ctl, c->sc[0], c->st,
                                c->stream);
-      c->launches[SS_PROF_SOLVE + sys] += 1;
     }
-    if (e == cudaSuccess) e = launch_bicgstab(c->sys[sys], c->pr.dim == 3, ctl, c->sc[0], c->st, c->stream);
+    if (e == cudaSuccess) {
+      StageTimer tm(c, SS_PROF_SOLVE + sys, 1);
+      e = launch_bicgstab(c->sys[sys], c->pr.dim == 3, ctl, c->sc[0], c->st, c->stream);
+    }
   } else {
     return fail(SS_EINVAL, "unknown system %d", sys);
   }
@@ -623,6 +632,7 @@ struct ss_batch {
   CaseRows* rows;                             // [n]
   char* bcg[3];                               // PackedBcgTeam [n]: momentum, solute, temperature
   char* dct;                                  // DctArgs<float> [n]
+  char* helm;                                 // the T* pre-solve's arguments [n]
   int* first;                                 // [n + 1] first block of each team
   PackedTile* tiles[kNumPackedStages];
   int ntiles[kNumPackedStages];
@@ -640,7 +650,7 @@ struct ss_batch {
 namespace {
 
 constexpr int kMinTileRows = 256;
-constexpr int kPackedLaunchesPerStep = 9;
+constexpr int kPackedLaunchesPerStep = 10;
 constexpr int kMaxTileRows = 1 << 24;
 
 int stage_parts(int stage, const ss_case* c) { return stage == kStageMomentum ? c->pr.dim : 1; }
@@ -670,6 +680,7 @@ size_t batch_layout(ss_case* const* cs, int n, char* base, F&& place) {
     for (int q = 0; q < n && st != kStageProject; ++q) t += stage_tiles(st, cs[q], kMinTileRows);
     place(6 + st, take((size_t)t * sizeof(PackedTile)));
   }
+  place(6 + kNumPackedStages, take((size_t)n * packed_helm_args_bytes()));
   return off;
 }
 
@@ -762,6 +773,7 @@ ss_status batch_one_step(ss_batch* b) {
   PACKED_TRY(launch_bicgstab_packed(b->bcg[1], b->first, n, b->nblocks, s));
   PACKED_TRY(launch_packed_rows(kStageTemperature, b->rows, b->tiles[kStageTemperature],
                                 b->ntiles[kStageTemperature], s));
+  PACKED_TRY(launch_helmholtz_dct_packed(b->helm, b->first, n, b->nblocks, b->dct_smem, s));
   PACKED_TRY(launch_bicgstab_packed(b->bcg[2], b->first, n, b->nblocks, s));
   PACKED_TRY(launch_packed_rows(kStageLever, b->rows, b->tiles[kStageLever], b->ntiles[kStageLever], s));
 #undef PACKED_TRY
@@ -1074,6 +1086,8 @@ ss_status ss_get_profile(ss_case* c, ss_profile* out) {
     out->iters[s] = h.stat[s].iters_total;
     CUDA_TRY(cudaMemsetAsync(&c->st->stat[s].iters_total, 0, sizeof(long long), c->stream));
   }
+  out->presolve_sweeps = h.presolve_sweeps;
+  CUDA_TRY(cudaMemsetAsync(&c->st->presolve_sweeps, 0, sizeof(long long), c->stream));
   CUDA_TRY(cudaStreamSynchronize(c->stream));
   return SS_OK;
 }
@@ -1227,11 +1241,12 @@ ss_status ss_batch_create(ss_case* const* cases, int n, void* workspace, size_t 
   b->ws_bytes = workspace_bytes;
   b->gamma = 1.0;
   b->tile_rows = 4096;
-  char* slot[6 + kNumPackedStages] = {nullptr};
+  char* slot[7 + kNumPackedStages] = {nullptr};
   batch_layout(cases, n, b->ws, [&](int k, char* p) { slot[k] = p; });
   b->rows = reinterpret_cast<CaseRows*>(slot[0]);
   for (int q = 0; q < 3; ++q) b->bcg[q] = slot[1 + q];
   b->dct = slot[4];
+  b->helm = slot[6 + kNumPackedStages];
   b->first = reinterpret_cast<int*>(slot[5]);
   for (int st = 0; st < kNumPackedStages; ++st) {
     b->tiles[st] = reinterpret_cast<PackedTile*>(slot[6 + st]);
@@ -1242,7 +1257,8 @@ ss_status ss_batch_create(ss_case* const* cases, int n, void* workspace, size_t 
   // per-case descriptions and solver arguments, built on the host once
   const size_t bt = packed_bcg_team_bytes(), da = packed_dct_args_bytes();
   std::vector<CaseRows> rows(n);
-  std::vector<char> bcg(3 * (size_t)n * bt), dct((size_t)n * da);
+  const size_t ha = packed_helm_args_bytes();
+  std::vector<char> bcg(3 * (size_t)n * bt), dct((size_t)n * da), helm((size_t)n * ha);
   b->dct_smem = 0;
   for (int q = 0; q < n; ++q) {
     ss_case* c = cases[q];
@@ -1278,8 +1294,11 @@ ss_status ss_batch_create(ss_case* const* cases, int n, void* workspace, size_t 
     ProjectPtrs pj{{c->u, c->v, c->w}, {c->ustar[0], c->ustar[1], c->ustar[2]}, c->p};
     const size_t sm = fill_packed_dct_args(&dct[(size_t)q * da], c->dct, c->pr, c->pb, c->pc, cp, c->sc[0], c->st, &pj);
     b->dct_smem = std::max(b->dct_smem, sm);
+    const size_t hm = fill_packed_helm_args(&helm[(size_t)q * ha], c->dct, c->pr, c->sys[SS_SYS_T], c->pr.dim == 3,
+                                            transform_energy_solve(c) ? kHelmholtzSweeps : 0, ct, c->sc[0], c->st);
+    b->dct_smem = std::max(b->dct_smem, hm);
   }
-  const int lim_d = packed_dct_max_blocks(b->dct_smem);
+  const int lim_d = std::min(packed_dct_max_blocks(b->dct_smem), packed_helm_max_blocks(b->dct_smem));
   b->max_blocks = std::min(packed_bcg_max_blocks(), lim_d);
   for (int q = 0; q < n; ++q) b->max_blocks = std::min(b->max_blocks, cases[q]->sc[0].max_blocks);
   cudaError_t e = cudaSuccess;
@@ -1288,6 +1307,7 @@ ss_status ss_batch_create(ss_case* const* cases, int n, void* workspace, size_t 
   for (int q = 0; q < 3 && e == cudaSuccess; ++q)
     e = cudaMemcpyAsync(b->bcg[q], &bcg[(size_t)q * n * bt], n * bt, cudaMemcpyHostToDevice, b->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(b->dct, dct.data(), n * da, cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(b->helm, helm.data(), n * ha, cudaMemcpyHostToDevice, b->stream);
   ss_status s = SS_OK;
   if (e != cudaSuccess) s = fail(SS_ECUDA, "batch tables: %s", cudaGetErrorString(e));
   else if (b->max_blocks < n) s = fail(SS_EINVAL, "%d cases exceed the %d resident blocks of a packed launch", n,

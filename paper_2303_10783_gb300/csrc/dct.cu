@@ -701,8 +701,8 @@ __device__ __forceinline__ double spmv64(const Planes<double>& a, const double* 
 // cooled walls included), applies the inverse and adds the correction. The
 // parts the inverse leaves out are small beside 1/dt where this is used, so
 // a sweep reduces the residual by ~1e-3; the caller's BiCGSTAB refinement
-// follows and only has to confirm the tolerance. Sweeps add to the system's
-// iteration count. x holds the initial guess.
+// follows and only has to confirm the tolerance. The sweeps are counted in
+// the status block's pre-solve counter. x holds the initial guess.
 __device__ bool helmholtz_team(const DctArgs<float>& A, const Sys& S, int has_z, double inv_alpha, int max_sweeps,
                                const Team& tm, float* sm) {
   unsigned int epoch = 0;
@@ -764,7 +764,7 @@ __device__ bool helmholtz_team(const DctArgs<float>& A, const Sys& S, int has_z,
         }))
       return false;
   }
-  if (tm.rank == 0 && threadIdx.x == 0) A.st->stat[A.stat_index].iters_total += sweeps;
+  if (tm.rank == 0 && threadIdx.x == 0) A.st->presolve_sweeps += sweeps;
   return true;
 }
 
@@ -779,6 +779,32 @@ struct HelmArgs {
 __global__ void __launch_bounds__(kBlock, 1) k_helmholtz_dct(HelmArgs H) {
   extern __shared__ __align__(16) unsigned char dsm[];
   const Team tm{(int)blockIdx.x, (int)gridDim.x, &H.dct.st->barrier, H.dct.partial};
+  helmholtz_team(H.dct, H.sys, H.has_z, H.inv_alpha, H.max_sweeps, tm, reinterpret_cast<float*>(dsm));
+}
+
+// The T* pre-solve of a packed batch: team q runs case q's sweeps (none
+// where the case's walls or size rule it out: max_sweeps = 0).
+__global__ void __launch_bounds__(kBlock, 1) k_helmholtz_dct_packed(const HelmArgs* __restrict__ args,
+                                                                   const int* __restrict__ first, int nteams) {
+  extern __shared__ __align__(16) unsigned char dsm[];
+  __shared__ int s_team;
+  if (threadIdx.x == 0) {
+    int lo = 0, hi = nteams - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (first[mid] <= (int)blockIdx.x) lo = mid; else hi = mid - 1;
+    }
+    s_team = lo;
+  }
+  __syncthreads();
+  const int q = s_team;
+  __shared__ __align__(16) unsigned long long buf[(sizeof(HelmArgs) + 7) / 8];
+  const unsigned long long* src = reinterpret_cast<const unsigned long long*>(args + q);
+  for (int w = threadIdx.x; w < (int)(sizeof(HelmArgs) / 8); w += blockDim.x) buf[w] = src[w];
+  __syncthreads();
+  const HelmArgs& H = *reinterpret_cast<const HelmArgs*>(buf);
+  if (H.max_sweeps <= 0) return;
+  const Team tm{(int)blockIdx.x - first[q], first[q + 1] - first[q], &H.dct.st->barrier, H.dct.partial};
   helmholtz_team(H.dct, H.sys, H.has_z, H.inv_alpha, H.max_sweeps, tm, reinterpret_cast<float*>(dsm));
 }
 
@@ -935,10 +961,9 @@ void dct_tables(const DctPlan& pl, const Params& pr, double* out) {
   }
 }
 
-cudaError_t launch_helmholtz_dct(const DctPlan& pl, const Params& pr, const Sys& sys, int has_z, int max_sweeps,
-                                 const SolverCtl& ctl, Scratch& sc, DevStatus* st, cudaStream_t s) {
-  if (!pl.fp32) return cudaErrorInvalidValue;
-  HelmArgs H;
+namespace {
+size_t make_helm_args(HelmArgs& H, const DctPlan& pl, const Params& pr, const Sys& sys, int has_z, int max_sweeps,
+                      const SolverCtl& ctl, Scratch& sc, DevStatus* st) {
   memset(&H, 0, sizeof H);
   const size_t smem = make_args<float>(H.dct, pl, pr, sys.b, sys.x, ctl, sc, st, nullptr);
   H.dct.helm = 1;
@@ -947,6 +972,42 @@ cudaError_t launch_helmholtz_dct(const DctPlan& pl, const Params& pr, const Sys&
   H.has_z = has_z;
   H.inv_alpha = 1.0 / pr.alphaT;
   H.max_sweeps = max_sweeps;
+  return smem;
+}
+}  // namespace
+
+size_t packed_helm_args_bytes() { return sizeof(HelmArgs); }
+
+size_t fill_packed_helm_args(void* out, const DctPlan& pl, const Params& pr, const Sys& sys, int has_z,
+                             int max_sweeps, const SolverCtl& ctl, Scratch& sc, DevStatus* st) {
+  HelmArgs& H = *static_cast<HelmArgs*>(out);
+  if (!pl.fp32 || !pl.tables) {
+    memset(&H, 0, sizeof H);
+    return 0;
+  }
+  return make_helm_args(H, pl, pr, sys, has_z, max_sweeps, ctl, sc, st);
+}
+
+cudaError_t launch_helmholtz_dct_packed(const void* args, const int* first, int nteams, int nblocks, size_t smem,
+                                        cudaStream_t s) {
+  const void* kern = (const void*)k_helmholtz_dct_packed;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  void* a[] = {(void*)&args, (void*)&first, (void*)&nteams};
+  return cudaLaunchCooperativeKernel(kern, dim3(nblocks), dim3(kBlock), a, smem, s);
+}
+
+int packed_helm_max_blocks(size_t smem) {
+  const void* kern = (const void*)k_helmholtz_dct_packed;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
+  return coop_blocks_for_smem(kern, 1LL << 40, 1 << 30, smem);
+}
+
+cudaError_t launch_helmholtz_dct(const DctPlan& pl, const Params& pr, const Sys& sys, int has_z, int max_sweeps,
+                                 const SolverCtl& ctl, Scratch& sc, DevStatus* st, cudaStream_t s) {
+  if (!pl.fp32) return cudaErrorInvalidValue;
+  HelmArgs H;
+  const size_t smem = make_helm_args(H, pl, pr, sys, has_z, max_sweeps, ctl, sc, st);
   const void* kern = (const void*)k_helmholtz_dct;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;

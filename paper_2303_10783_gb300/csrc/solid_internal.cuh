@@ -70,6 +70,7 @@ struct DevStatus {
   double time;                   // simulated time of the fields; k_lever advances it by dt
   unsigned int team_arrivals[kMaxTeams]; // barrier counters of the teams of a multi-system solve
   unsigned int selftest_counter; // counter of the wait self-test (ss_wait_selftest)
+  long long presolve_sweeps;     // T* transform pre-solve sweeps since the host last read them
   long long spin_limit;          // polls a barrier waits before giving up (0: kSpinLimit)
 };
 
@@ -622,6 +623,13 @@ cudaError_t launch_poisson_dct(const DctPlan& pl, const Params& pr, double* b, d
 // from the x in place; the BiCGSTAB refinement follows it.
 cudaError_t launch_helmholtz_dct(const DctPlan& pl, const Params& pr, const Sys& sys, int has_z, int max_sweeps,
                                  const SolverCtl& ctl, Scratch& sc, DevStatus* st, cudaStream_t s);
+// the same for a packed batch, one team per case (max_sweeps = 0: none)
+size_t packed_helm_args_bytes();
+size_t fill_packed_helm_args(void* out, const DctPlan& pl, const Params& pr, const Sys& sys, int has_z,
+                             int max_sweeps, const SolverCtl& ctl, Scratch& sc, DevStatus* st);
+int packed_helm_max_blocks(size_t smem);
+cudaError_t launch_helmholtz_dct_packed(const void* args, const int* first, int nteams, int nblocks, size_t smem,
+                                        cudaStream_t s);
 // the pressure solves of a packed batch (FP32 transforms), one team per case
 size_t packed_dct_args_bytes();
 size_t fill_packed_dct_args(void* out, const DctPlan& pl, const Params& pr, double* b, double* x, const SolverCtl& ctl,

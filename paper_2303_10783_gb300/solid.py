@@ -51,12 +51,13 @@ class Stats(ctypes.Structure):
                 ("relres", ctypes.c_double * 6), ("status", ctypes.c_int)]
 
 
-PROF_NAMES = tuple("assemble_" + s for s in SYSTEMS) + tuple("solve_" + s for s in SYSTEMS) + ("project", "lever")
+PROF_NAMES = (tuple("assemble_" + s for s in SYSTEMS) + tuple("solve_" + s for s in SYSTEMS) +
+              ("project", "lever", "presolve_T"))
 
 
 class Profile(ctypes.Structure):
-    _fields_ = [("ms", ctypes.c_double * 14), ("launches", ctypes.c_longlong * 14), ("kernels", ctypes.c_longlong),
-                ("iters", ctypes.c_longlong * 6)]
+    _fields_ = [("ms", ctypes.c_double * 15), ("launches", ctypes.c_longlong * 15), ("kernels", ctypes.c_longlong),
+                ("iters", ctypes.c_longlong * 6), ("presolve_sweeps", ctypes.c_longlong)]
 
 
 class SolidError(RuntimeError):
@@ -355,7 +356,7 @@ class Case:
         check(self.lib.ss_get_profile(self.h, ctypes.byref(p)))
         return dict(ms={k: p.ms[i] for i, k in enumerate(PROF_NAMES)},
                     launches={k: p.launches[i] for i, k in enumerate(PROF_NAMES)}, kernels=p.kernels,
-                    iters={k: p.iters[i] for i, k in enumerate(SYSTEMS)})
+                    iters={k: p.iters[i] for i, k in enumerate(SYSTEMS)}, presolve_sweeps=p.presolve_sweeps)
 
     def close(self):
         if getattr(self, "h", None):

@@ -79,7 +79,7 @@ def test_packed_batch_matches_oracle(lib):
     import oracle
     out, teams, launches = _packed_run(PACKED_CASES, 20)
     assert len(teams) == len(PACKED_CASES) and min(teams) >= 1
-    assert launches == 20 * 9         # nine launches per batch step
+    assert launches == 20 * 10        # ten launches per batch step
     for q, case in enumerate(PACKED_CASES):
         f = cases.initial_fields(case)
         g = oracle.Grid(case)
