@@ -63,12 +63,13 @@ DCT_BYTES_PER_CELL_SWEEP_BASE = 48.0
 DCT_BYTES_PER_CELL_LAUNCH = 56.0
 DCT_THOMAS_FLOPS = 8.0
 # k_bicgstab_ir (mixed transport: FP32 BiCGSTAB in FP64 refinement), per row:
-#   the first FP64 residual reads 7 FP64 planes, x and b and writes r (80); each sweep
-#   converts r (12), sets up the inner vectors (20), adds the correction (20) and forms the
-#   next FP64 residual (80): 132; each inner iteration moves 7 FP32 planes twice (56) and
-#   ~80 B of FP32 vectors: 136.
-BCG_IR_BYTES_ROW = 80.0
-BCG_IR_BYTES_ROW_SWEEP = 132.0
+#   the first FP64 residual reads 7 FP64 planes, x and b and writes r and its FP32 copy (84);
+#   each sweep's update pass reads the 7 FP64 planes, the correction, r and x and writes r, x
+#   and the FP32 copy (96), and its first inner pass stages r, rhat and p from the copy
+#   (4 B fewer than a later pass 1) and its first pass 3 does not read x (4): 88; each inner
+#   iteration moves 7 FP32 planes twice (56) and ~80 B of FP32 vectors: 136.
+BCG_IR_BYTES_ROW = 84.0
+BCG_IR_BYTES_ROW_SWEEP = 88.0
 BCG_IR_BYTES_ROW_IT = 136.0
 # k_helmholtz_dct (the T* pre-solve of the mixed path), per cell: the first FP64 residual with
 #   the system's 7 FP64 planes, x and b, staged in FP32 (76 B); per sweep the transforms move

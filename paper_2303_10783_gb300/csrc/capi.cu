@@ -489,6 +489,7 @@ ss_status stage_solve(ss_case* c, int sys, bool fuse_project = false) {
     ctl.max_it = c->g.max_it_t;
     e = cudaSuccess;
     if (sys == SS_SYS_T && transform_energy_solve(c)) {
+      ctl.after_presolve = 1;
       StageTimer pre(c, SS_PROF_PRESOLVE_T, 1);
       e = launch_helmholtz_dct(c->dct, c->pr, c->sys[sys], c->pr.dim == 3, kHelmholtzSweeps, ctl, c->sc[0], c->st,
                                c->stream);
@@ -1285,6 +1286,7 @@ ss_status ss_batch_create(ss_case* const* cases, int n, void* workspace, size_t 
     SolverCtl ct = ctl[0];
     ct.stat_index = SS_SYS_T;
     ct.inner_tol = kInnerTolEnergy;
+    ct.after_presolve = transform_energy_solve(c) ? 1 : 0;
     sys[0] = &c->sys[SS_SYS_T];
     fill_packed_bcg_team(&bcg[(2 * (size_t)n + q) * bt], sys, 1, c->pr.dim == 3, &ct, c->sc[0], c->st);
     SolverCtl cp;

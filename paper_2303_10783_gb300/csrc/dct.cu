@@ -700,9 +700,11 @@ __device__ __forceinline__ double spmv64(const Planes<double>& a, const double* 
 // residual b - A x with the system's own FP64 planes (upwind convection and
 // cooled walls included), applies the inverse and adds the correction. The
 // parts the inverse leaves out are small beside 1/dt where this is used, so
-// a sweep reduces the residual by ~1e-3; the caller's BiCGSTAB refinement
-// follows and only has to confirm the tolerance. The sweeps are counted in
-// the status block's pre-solve counter. x holds the initial guess.
+// a sweep reduces the residual by ~1e-3. The caller's BiCGSTAB refinement
+// follows: when the sweeps met the tolerance on the true FP64 residual
+// (status block: presolve_done, presolve_rel) it only records that, else it
+// continues from x. The sweeps are counted in the status block's pre-solve
+// counter. x holds the initial guess.
 __device__ bool helmholtz_team(const DctArgs<float>& A, const Sys& S, int has_z, double inv_alpha, int max_sweeps,
                                const Team& tm, float* sm) {
   unsigned int epoch = 0;
@@ -713,11 +715,12 @@ __device__ bool helmholtz_team(const DctArgs<float>& A, const Sys& S, int has_z,
   double* x = S.x;
   float* rs = A.T2;
   __shared__ struct {
-    double rn, sc, pscale;
-    int go;
+    double rn, bn, sc, pscale;
+    int go, conv;
   } hs;
   double thr = 0.0;   // read by thread 0 only
   double ps = 1.0;    // the first staged residual is not scaled (T* residuals are O(1) in K/s)
+  if (tm.rank == 0 && threadIdx.x == 0) A.st->presolve_done = 0;
   Vec<2> s0 = {{0.0, 0.0}};
   for (int c = t0; c < n; c += gsz) {
     const double rc = b[c] - spmv64(S.a, x, c, sy, sz, has_z);
@@ -727,8 +730,10 @@ __device__ bool helmholtz_team(const DctArgs<float>& A, const Sys& S, int has_z,
   }
   if (!team_sum_post<2>(s0, tm, A.max_blocks, 0, A.st, epoch, [&](const double* tot) {
         const double bn = sqrt(tot[0]);
+        hs.bn = bn;
         hs.rn = sqrt(tot[1]);
         thr = A.tol * bn;
+        hs.conv = bn == 0.0 || hs.rn <= thr;
         hs.go = bn > 0.0 && hs.rn > thr && isfinite(hs.rn);
         hs.sc = 1.0 / hs.rn;
         int e = 0;
@@ -755,6 +760,7 @@ __device__ bool helmholtz_team(const DctArgs<float>& A, const Sys& S, int has_z,
     }
     if (!team_sum_post<1>(s1, tm, A.max_blocks, 1, A.st, epoch, [&](const double* tot) {
           const double rn_new = sqrt(tot[0]);
+          hs.conv = rn_new <= thr;
           hs.go = rn_new > thr && isfinite(rn_new) && rn_new < 0.5 * hs.rn;
           hs.sc = 1.0 / (hs.pscale * rn_new);
           hs.rn = rn_new;
@@ -764,7 +770,11 @@ __device__ bool helmholtz_team(const DctArgs<float>& A, const Sys& S, int has_z,
         }))
       return false;
   }
-  if (tm.rank == 0 && threadIdx.x == 0) A.st->presolve_sweeps += sweeps;
+  if (tm.rank == 0 && threadIdx.x == 0) {
+    A.st->presolve_sweeps += sweeps;
+    A.st->presolve_rel = hs.bn > 0.0 ? hs.rn / hs.bn : 0.0;
+    A.st->presolve_done = hs.conv;
+  }
   return true;
 }
 

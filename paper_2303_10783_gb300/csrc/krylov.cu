@@ -51,6 +51,7 @@ struct BcgArgs {
   double* partial;
   int max_blocks;
   DevStatus* st;
+  int after_presolve;      // 1: the T* pre-solve ran before this launch and may have met tol
 };
 
 template <typename T>
@@ -93,6 +94,11 @@ struct CoreOut {
   int it;
   bool conv;
   double res, bnorm;
+  // bcg_fused only: the solve stopped on the half step, and its correction is
+  // x + al D^-1 p (x read as 0 when it == 1), formed where the caller reads it
+  bool half = false;
+  float al = 0.f;
+  const float* p = nullptr;
 };
 
 // The BiCGSTAB scalars, formed by thread 0 of each block after each
@@ -265,6 +271,16 @@ struct YDir {   // y = D^-1 (r + beta (p - om v))
   }
 };
 
+struct Y1Dir {  // the first direction y = D^-1 r0, r0 = sc r32 (p = v = 0)
+  const float *r, *d;
+  float sc;
+  __device__ __forceinline__ float at(int q) const { return d[q] * (r[q] * sc); }
+  __device__ __forceinline__ float4 at4(int q) const {
+    const float4 a = *reinterpret_cast<const float4*>(r + q), e = __ldg(reinterpret_cast<const float4*>(d + q));
+    return make_float4(e.x * (a.x * sc), e.y * (a.y * sc), e.z * (a.z * sc), e.w * (a.w * sc));
+  }
+};
+
 struct ZDir {   // z = D^-1 (r - al v)
   const float *r, *v, *d;
   float al;
@@ -323,8 +339,16 @@ __device__ __forceinline__ float spmv_dir(const Planes<float>& a, const F& f, fl
 
 __device__ __forceinline__ float dot4(float4 a, float4 b) { return (a.x * b.x + a.y * b.y) + (a.z * b.z + a.w * b.w); }
 
-// A x = b from x = 0 in FP32 (b in V.r0). Reduction slots 0..7, like bcg_core.
-__device__ bool bcg_fused(const Planes<float>& a, int n, int sy, int sz, int has_z, float* x, FusedVec V,
+// A x = r0 from x = 0 in FP32, r0 = sc r32 with r32 the caller's FP32 copy
+// of its residual in V.t (read only by the first pass; pass 2 reuses V.t).
+// The first iteration starts from p = v = 0, so its pass 1 also stages r0,
+// rhat and p' = r0 and reduces (r0, r0) beside (rhat, v'): no separate
+// initialisation pass or reduction, and x is first written (not updated) in
+// its pass 3. A solve that converges on the half step leaves its last update
+// x + al D^-1 p' to the caller (out.half, out.al, out.p). out.it == 0 means
+// the correction is zero (already converged, or no iterations allowed).
+// Reduction slots 0..7, like bcg_core.
+__device__ bool bcg_fused(const Planes<float>& a, int n, int sy, int sz, int has_z, float* x, FusedVec V, float sc,
                           double tol, int max_it, const Team& tm, int max_blocks, DevStatus* st,
                           unsigned int& epoch, CoreOut& out) {
   const int t0 = tm.rank * blockDim.x + threadIdx.x, gs = tm.size * blockDim.x;
@@ -334,60 +358,86 @@ __device__ bool bcg_fused(const Planes<float>& a, int n, int sy, int sz, int has
   const float* rh = V.rh;
   const float* dg = a.idiag;
   __shared__ BcgScalars<float> ks;
-  float a0 = 0.f;
-  for (int i = t0; i < n; i += gs) {              // x = 0, rhat = r, p = v = 0
-    const float ri = R[i];
-    x[i] = 0.f;
-    V.rh[i] = ri;
-    Po[i] = 0.f;
-    Vo[i] = 0.f;
-    a0 += ri * ri;
-  }
   double thr = 0.0;                               // read by thread 0 only
-  int it = 0;
-  if (!team_sum_post<1>(VecF<1>{{a0}}, tm, max_blocks, 6, st, epoch, [&](const double* tot) {
-        ks.bnorm = sqrt(tot[0]);
-        ks.res = ks.bnorm;
-        thr = tol * ks.bnorm;
-        ks.rho = tot[0];
-        ks.alpha = 1.0;
-        ks.omega = 1.0;
-        ks.beta = (float)ks.rho;                    // (rho / 1) (1 / 1); p = v = 0, so p' = r
-        ks.om = 1.f;
-        ks.conv = ks.bnorm == 0.0 || ks.res <= thr;
-        ks.state = (ks.conv || max_it <= 0 || !isfinite(ks.res)) ? 2 : 0;
-      }))
-    return false;
-  out.bnorm = ks.bnorm;
-  while (ks.state == 0) {
-    ++it;
-    const float beta = ks.beta, om = ks.om;
-    // pass 1: p' = r + beta (p - om v) (stored), v' = A D^-1 p', (rhat, v')
-    const YDir yd{R, Po, Vo, dg, beta, om};
-    float s1 = 0.f;
+  {
+    // pass 1 of iteration 1: r0 = sc r32, rhat = p' = r0, v' = A D^-1 p', (rhat, v'), (r0, r0)
+    const float* r32 = V.t;
+    const Y1Dir yd{r32, dg, sc};
+    float s1 = 0.f, a0 = 0.f;
     for (int m = t0; m < n4; m += gs) {
-      const float4 rv = ld4(R, m), pv = ld4(Po, m), vv = ld4(Vo, m), dv = ldg4(dg, m);
-      float4 pn;
-      pn.x = rv.x + beta * (pv.x - om * vv.x); pn.y = rv.y + beta * (pv.y - om * vv.y);
-      pn.z = rv.z + beta * (pv.z - om * vv.z); pn.w = rv.w + beta * (pv.w - om * vv.w);
-      st4(Pn, m, pn);
-      const float4 yc = make_float4(dv.x * pn.x, dv.y * pn.y, dv.z * pn.z, dv.w * pn.w);
+      const float4 q = ld4(r32, m), dv = ldg4(dg, m);
+      const float4 rv = make_float4(q.x * sc, q.y * sc, q.z * sc, q.w * sc);
+      st4(R, m, rv);
+      st4(V.rh, m, rv);
+      st4(Pn, m, rv);
+      const float4 yc = make_float4(dv.x * rv.x, dv.y * rv.y, dv.z * rv.z, dv.w * rv.w);
       const float4 vn = spmv4_dir(a, yd, yc, m, sy, sz, has_z, ay, az);
       st4(Vn, m, vn);
-      s1 += dot4(ld4(rh, m), vn);
+      s1 += dot4(rv, vn);
+      a0 += dot4(rv, rv);
     }
     for (int i = tail + t0; i < n; i += gs) {
-      const float pn = R[i] + beta * (Po[i] - om * Vo[i]);
-      Pn[i] = pn;
-      const float vn = spmv_dir(a, yd, __ldg(dg + i) * pn, i, sy, sz, has_z);
+      const float ri = r32[i] * sc;
+      R[i] = ri;
+      V.rh[i] = ri;
+      Pn[i] = ri;
+      const float vn = spmv_dir(a, yd, __ldg(dg + i) * ri, i, sy, sz, has_z);
       Vn[i] = vn;
-      s1 += rh[i] * vn;
+      s1 += ri * vn;
+      a0 += ri * ri;
     }
-    if (!team_sum_post<1>(VecF<1>{{s1}}, tm, max_blocks, 0, st, epoch, [&](const double* tot) {
+    if (!team_sum_post<2>(VecF<2>{{s1, a0}}, tm, max_blocks, 6, st, epoch, [&](const double* tot) {
+          ks.bnorm = sqrt(tot[1]);
+          ks.res = ks.bnorm;
+          thr = tol * ks.bnorm;
+          ks.rho = tot[1];
+          ks.omega = 1.0;
+          ks.conv = ks.bnorm == 0.0 || ks.res <= thr;
+          ks.state = (ks.conv || max_it <= 0 || !isfinite(ks.res)) ? 2 : 0;
           ks.alpha = ks.rho / tot[0];
           ks.al = (float)ks.alpha;
         }))
       return false;
+  }
+  out.bnorm = ks.bnorm;
+  out.half = false;
+  if (ks.state != 0) {
+    out.it = 0;
+    out.conv = ks.conv != 0;
+    out.res = ks.res;
+    return true;
+  }
+  int it = 1;
+  while (true) {
+    if (it > 1) {
+      const float beta = ks.beta, om = ks.om;
+      // pass 1: p' = r + beta (p - om v) (stored), v' = A D^-1 p', (rhat, v')
+      const YDir yd{R, Po, Vo, dg, beta, om};
+      float s1 = 0.f;
+      for (int m = t0; m < n4; m += gs) {
+        const float4 rv = ld4(R, m), pv = ld4(Po, m), vv = ld4(Vo, m), dv = ldg4(dg, m);
+        float4 pn;
+        pn.x = rv.x + beta * (pv.x - om * vv.x); pn.y = rv.y + beta * (pv.y - om * vv.y);
+        pn.z = rv.z + beta * (pv.z - om * vv.z); pn.w = rv.w + beta * (pv.w - om * vv.w);
+        st4(Pn, m, pn);
+        const float4 yc = make_float4(dv.x * pn.x, dv.y * pn.y, dv.z * pn.z, dv.w * pn.w);
+        const float4 vn = spmv4_dir(a, yd, yc, m, sy, sz, has_z, ay, az);
+        st4(Vn, m, vn);
+        s1 += dot4(ld4(rh, m), vn);
+      }
+      for (int i = tail + t0; i < n; i += gs) {
+        const float pn = R[i] + beta * (Po[i] - om * Vo[i]);
+        Pn[i] = pn;
+        const float vn = spmv_dir(a, yd, __ldg(dg + i) * pn, i, sy, sz, has_z);
+        Vn[i] = vn;
+        s1 += rh[i] * vn;
+      }
+      if (!team_sum_post<1>(VecF<1>{{s1}}, tm, max_blocks, 0, st, epoch, [&](const double* tot) {
+            ks.alpha = ks.rho / tot[0];
+            ks.al = (float)ks.alpha;
+          }))
+        return false;
+    }
     const float al = ks.al;
     // pass 2: s = r - al v' (stored beside r), t = A D^-1 s, (t,s), (t,t), (s,s)
     const ZDir zd{R, Vn, dg, al};
@@ -424,18 +474,25 @@ __device__ bool bcg_fused(const Planes<float>& a, int n, int sy, int sz, int has
           }
         }))
       return false;
-    if (ks.state == 1) {                           // x += al D^-1 p'
-      for (int i = t0; i < n; i += gs) x[i] += al * (__ldg(dg + i) * Pn[i]);
+    if (ks.state == 1) {                           // x + al D^-1 p', formed by the caller
+      out.half = true;
+      out.al = al;
+      out.p = Pn;
       break;
     }
     const float omn = ks.omn;
-    // pass 3: x += al D^-1 p' + omn D^-1 s; r = s - omn t (over s); (rhat, r), (r, r)
+    // pass 3: x += al D^-1 p' + omn D^-1 s (x = ... on iteration 1); r = s - omn t (over s);
+    // (rhat, r), (r, r)
+    const bool first = it == 1;
     float s5 = 0.f, s6 = 0.f;
     for (int m = t0; m < n4; m += gs) {
-      const float4 xv = ld4(x, m), pv = ld4(Pn, m), sv = ld4(S, m), tv = ld4(V.t, m), dv = ldg4(dg, m);
+      const float4 xv = first ? make_float4(0.f, 0.f, 0.f, 0.f) : ld4(x, m);
+      const float4 pv = ld4(Pn, m), sv = ld4(S, m), tv = ld4(V.t, m), dv = ldg4(dg, m);
       float4 xo, ro;
-      xo.x = xv.x + al * (dv.x * pv.x) + omn * (dv.x * sv.x); xo.y = xv.y + al * (dv.y * pv.y) + omn * (dv.y * sv.y);
-      xo.z = xv.z + al * (dv.z * pv.z) + omn * (dv.z * sv.z); xo.w = xv.w + al * (dv.w * pv.w) + omn * (dv.w * sv.w);
+      xo.x = fmaf(omn, dv.x * sv.x, fmaf(al, dv.x * pv.x, xv.x));
+      xo.y = fmaf(omn, dv.y * sv.y, fmaf(al, dv.y * pv.y, xv.y));
+      xo.z = fmaf(omn, dv.z * sv.z, fmaf(al, dv.z * pv.z, xv.z));
+      xo.w = fmaf(omn, dv.w * sv.w, fmaf(al, dv.w * pv.w, xv.w));
       ro.x = sv.x - omn * tv.x; ro.y = sv.y - omn * tv.y; ro.z = sv.z - omn * tv.z; ro.w = sv.w - omn * tv.w;
       st4(x, m, xo);
       st4(S, m, ro);
@@ -444,7 +501,7 @@ __device__ bool bcg_fused(const Planes<float>& a, int n, int sy, int sz, int has
     }
     for (int i = tail + t0; i < n; i += gs) {
       const float di = __ldg(dg + i);
-      x[i] += al * (di * Pn[i]) + omn * (di * S[i]);
+      x[i] = fmaf(omn, di * S[i], fmaf(al, di * Pn[i], first ? 0.f : x[i]));
       const float ri = S[i] - omn * V.t[i];
       S[i] = ri;
       s5 += rh[i] * ri;
@@ -462,9 +519,11 @@ __device__ bool bcg_fused(const Planes<float>& a, int n, int sy, int sz, int has
           ks.state = (ks.conv || it >= max_it || !isfinite(ks.res) || ks.rho == 0.0 || ks.omega == 0.0) ? 2 : 0;
         }))
       return false;
+    if (ks.state != 0) break;
     float* tmp = R; R = S; S = tmp;               // the new r lives in S
     tmp = Po; Po = Pn; Pn = tmp;
     tmp = Vo; Vo = Vn; Vn = tmp;
+    ++it;
   }
   out.it = it;
   out.conv = ks.conv != 0;
@@ -483,11 +542,13 @@ __device__ __forceinline__ void fp64_solve(const BcgArgs& A, const Team& tm, uns
 }
 
 // Mixed precision: FP64 iterative refinement around an FP32 BiCGSTAB on the
-// FP32 copies of the planes. Each sweep forms the FP64 residual
-// r = b - A x with the FP64 planes, solves A d = r in FP32 to the relative
-// inner tolerance chosen per system by the caller, and adds d to the FP64
-// iterate; it stops when the FP64 residual meets tol (the same test as the
-// FP64 path).
+// FP32 copies of the planes. Each sweep solves A d = r / |r| in FP32 to the
+// relative inner tolerance chosen per system by the caller, adds |r| d to the
+// FP64 iterate, and updates the FP64 residual r -= |r| A d with the FP64
+// planes (b - A x in exact arithmetic; the launch starts from the true
+// residual of its initial guess). It stops when the FP64 residual meets tol
+// (the same test as the FP64 path). The pass that forms the residual also
+// stores its FP32 copy, which the inner solve scales by 1/|r| as it reads it.
 constexpr int kMaxRefine = 12;
 // Inner iterations per refinement sweep: bounds a sweep whose FP32 iteration
 // stalls (the outer FP64 loop then continues from the best iterate).
@@ -498,6 +559,39 @@ constexpr int kMaxInner = 200;
 // covers the FP32 operator's rounding, which the FP64 residual sees and the
 // inner one does not.
 constexpr double kSweepMargin = 0.1;
+// The FP32 residual copy is scaled by 1/|r| in FP32 when |r| lies in
+// [2^-60, 2^60]: no entry then overflows, and entries that fall below FP32's
+// normal range are below 2^-66 |r|. Outside that range a pass restages the
+// copy from the FP64 residual, scaled in FP64.
+constexpr double kStageLo = 0x1p-60, kStageHi = 0x1p60;
+
+// The inner correction d at row q as the update pass reads it (see CoreOut).
+struct DCorr {
+  const float *x, *d, *p;
+  float al;
+  int mode;   // 0: x; 1: al D^-1 p; 2: x + al D^-1 p
+  __device__ __forceinline__ float at(int q) const {
+    if (mode == 0) return x[q];
+    const float y = d[q] * p[q];
+    return mode == 1 ? al * y : fmaf(al, y, x[q]);
+  }
+};
+
+// (A d)_r in FP64 with the FP64 planes, d widened exactly (same order of
+// operations as spmv_row)
+__device__ __forceinline__ double spmv64_corr(const Planes<double>& a, const DCorr& f, double dc, int r, int sy,
+                                              int sz, int has_z) {
+  double acc = __ldg(a.P + r) * dc;
+  acc = fma(__ldg(a.W + r), to_f64(f.at(r - 1)), acc);
+  acc = fma(__ldg(a.E + r), to_f64(f.at(r + 1)), acc);
+  acc = fma(__ldg(a.S + r), to_f64(f.at(r - sy)), acc);
+  acc = fma(__ldg(a.N + r), to_f64(f.at(r + sy)), acc);
+  if (has_z) {
+    acc = fma(__ldg(a.B + r), to_f64(f.at(r - sz)), acc);
+    acc = fma(__ldg(a.T_ + r), to_f64(f.at(r + sz)), acc);
+  }
+  return acc;
+}
 
 __device__ __forceinline__ void ir_solve(const BcgArgs& A, const Team& tm, unsigned int& epoch) {
   const int n = (int)A.sys.d.n;
@@ -506,19 +600,30 @@ __device__ __forceinline__ void ir_solve(const BcgArgs& A, const Team& tm, unsig
   double* x = A.sys.x;
   const double* b = A.sys.b;
   double* r64 = A.v64.r;
+  float* r32 = A.f32.t;                           // the residual's FP32 copy, read by the inner solve
+  if (A.after_presolve && A.st->presolve_done) {  // the pre-solve met tol on the true FP64 residual
+    record(A.st, tm.rank == 0, A.stat_index, 0, 0, true, A.st->presolve_rel);
+    return;
+  }
   Vec<2> acc = {{0.0, 0.0}};
   for (int i = t0; i < n; i += gs) {
     const double ri = b[i] - spmv_row(A.sys.a, x, i, sy, sz, A.has_z);
     r64[i] = ri;
+    r32[i] = to_f32(ri);
     acc.v[0] += ri * ri;
     acc.v[1] += b[i] * b[i];
   }
   // scalars formed by thread 0 of each block after each reduction
   __shared__ struct {
     double bnorm, rn, inv, rel, itol;
-    int conv, go;
+    float sc;
+    int conv, go, restage;
   } is;
   double thr = 0.0;                               // read by thread 0 only
+  auto stage_scale = [&]() {
+    is.restage = !(is.rn >= kStageLo && is.rn <= kStageHi);
+    is.sc = is.restage ? 1.f : (float)is.inv;
+  };
   if (!team_sum_post<2>(acc, tm, A.max_blocks, 13, A.st, epoch, [&](const double* tot) {
         is.bnorm = sqrt(tot[1]);
         is.rn = sqrt(tot[0]);
@@ -528,27 +633,34 @@ __device__ __forceinline__ void ir_solve(const BcgArgs& A, const Team& tm, unsig
         is.go = is.bnorm > 0.0 && is.rn > thr && isfinite(is.rn);
         is.rel = is.bnorm > 0.0 ? is.rn / is.bnorm : 0.0;
         is.itol = fmax(A.inner_tol, kSweepMargin * thr / is.rn);
+        stage_scale();
       }))
     return;
   int total = 0, ref = 0;
   while (is.go && ref < kMaxRefine && total < A.max_it) {
     ++ref;
-    // the inner solve sees the residual scaled to unit norm (no FP32 under- or overflow)
-    const double rn = is.rn, inv = is.inv;
-    // (bcg_fused first reads r0 on the rows this thread wrote; the reduction
-    // that follows orders it before any neighbour read)
-    for (int i = t0; i < n; i += gs) A.f32.r0[i] = (float)(r64[i] * inv);
+    const double rn = is.rn;
+    if (is.restage) {                             // |r| outside [2^-60, 2^60]: scale in FP64
+      const double inv = is.inv;
+      for (int i = t0; i < n; i += gs) r32[i] = to_f32(r64[i] * inv);
+      if (!team_barrier(A.st, tm, epoch)) return;
+    }
     CoreOut o;
     const int cap = (A.max_it - total < kMaxInner) ? A.max_it - total : kMaxInner;
-    if (!bcg_fused(A.sys.af, n, sy, sz, A.has_z, A.d32, A.f32, is.itol, cap, tm, A.max_blocks, A.st, epoch, o))
+    if (!bcg_fused(A.sys.af, n, sy, sz, A.has_z, A.d32, A.f32, is.sc, is.itol, cap, tm, A.max_blocks, A.st, epoch,
+                   o))
       return;
+    if (o.it == 0) break;                         // the inner solve made no progress
     total += o.it;
-    for (int i = t0; i < n; i += gs) x[i] += rn * (double)A.d32[i];
-    if (!team_barrier(A.st, tm, epoch)) return;
+    // x += rn d, r -= rn A d, and the FP32 copy of the new r
+    const DCorr dc{A.d32, A.sys.af.idiag, o.p, o.al, !o.half ? 0 : (o.it == 1 ? 1 : 2)};
     Vec<1> s1 = {{0.0}};
     for (int i = t0; i < n; i += gs) {
-      const double ri = b[i] - spmv_row(A.sys.a, x, i, sy, sz, A.has_z);
+      const double di = to_f64(dc.at(i));
+      const double ri = fma(-rn, spmv64_corr(A.sys.a, dc, di, i, sy, sz, A.has_z), r64[i]);
+      x[i] = fma(rn, di, x[i]);
       r64[i] = ri;
+      r32[i] = to_f32(ri);
       s1.v[0] += ri * ri;
     }
     if (!team_sum_post<1>(s1, tm, A.max_blocks, 15, A.st, epoch, [&](const double* tot) {
@@ -558,9 +670,9 @@ __device__ __forceinline__ void ir_solve(const BcgArgs& A, const Team& tm, unsig
           is.go = is.rn > thr && isfinite(is.rn);
           is.rel = is.rn / is.bnorm;
           is.itol = fmax(A.inner_tol, kSweepMargin * thr / is.rn);
+          stage_scale();
         }))
       return;
-    if (o.it == 0 && !is.conv) break;          // the inner solve made no progress
   }
   record(A.st, tm.rank == 0, A.stat_index, total, ref, is.conv != 0, is.rel);
 }
@@ -786,6 +898,7 @@ void fill_bcg_args(BcgArgs& A, const Sys& sys, int has_z, const SolverCtl& ctl, 
   A.partial = c.partial;
   A.max_blocks = c.max_blocks;
   A.st = st;
+  A.after_presolve = ctl.after_presolve;
 }
 
 int g_num_sms = 0;

@@ -72,6 +72,8 @@ struct DevStatus {
   unsigned int selftest_counter; // counter of the wait self-test (ss_wait_selftest)
   long long presolve_sweeps;     // T* transform pre-solve sweeps since the host last read them
   long long spin_limit;          // polls a barrier waits before giving up (0: kSpinLimit)
+  double presolve_rel;           // relative FP64 residual the last T* pre-solve reached
+  int presolve_done;             // 1: the last T* pre-solve met the tolerance (its BiCGSTAB has nothing to do)
 };
 
 template <typename T>
@@ -526,6 +528,7 @@ struct SolverCtl {
   double inner_tol;      // relative tolerance of each FP32 inner solve (mixed path)
   int block_cap;         // > 0: at most this many blocks in the cooperative launch
   int warm_start = 0;    // 1: the solution buffer holds the initial guess (multigrid pressure, mixed path)
+  int after_presolve = 0;  // 1: the T* pre-solve ran just before on this stream (mixed path)
 };
 cudaError_t launch_bicgstab(const Sys& sys, int has_z, const SolverCtl& ctl, Scratch& sc, DevStatus* st,
                             cudaStream_t s);
