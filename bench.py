@@ -79,6 +79,11 @@ HELM_BYTES_PER_CELL = 76.0
 HELM_BYTES_PER_CELL_SWEEP = 112.0
 # k_bicgstab (FP64 transport), per row and iteration: two SpMVs over 7 FP64 planes (2 x 72)
 # and the vector updates (~156 B): 300 B; 2 x 13 + 20 = 46 FP64 flops.
+# FP64 Jacobi sweep of a transport solve (both paths), per row: 7 FP64 planes, x and b read,
+#   x written, the inverse diagonal (FP32 on the mixed path, FP64 otherwise): 84 / 88 B;
+#   2 x 7 + 1 + 2 + 2 FP64 flop (the residual row, the update, its square).
+JAC_BYTES_ROW = {"mixed": 84.0, "fp64": 88.0}
+JAC_FLOPS_ROW = 19.0
 BCG_BYTES_ROW_IT = 300.0
 BCG_FLOPS_ROW_IT = 46.0
 FP64_FLOP_PER_CLK_PER_SM = 4.0    # 2 DFMA per clock per SM (1.26 TFLOP/s at 2070 MHz, 152 SMs)
@@ -521,14 +526,18 @@ def kernel_work(stage, precision_name, case, prof, stats):
     for q in systems:
         rows = _rows(case, q)
         its = prof["iters"][q]
+        jac = prof.get("jacobi", {}).get(q, 0)
+        nbytes += rows * JAC_BYTES_ROW[precision_name] * jac
+        flops += rows * JAC_FLOPS_ROW * jac
         if mixed:
             sweeps = stats["refinements"][q] * launches    # sweeps of the last step, for each launch
-            nbytes += rows * (BCG_IR_BYTES_ROW * launches + BCG_IR_BYTES_ROW_SWEEP * sweeps + BCG_IR_BYTES_ROW_IT * its)
-            counts[q] = {"rows": rows, "inner_iterations": its, "sweeps": sweeps}
+            krylov = launches if sweeps > 0 else 0         # launches whose Jacobi sweeps did not converge
+            nbytes += rows * (BCG_IR_BYTES_ROW * krylov + BCG_IR_BYTES_ROW_SWEEP * sweeps + BCG_IR_BYTES_ROW_IT * its)
+            counts[q] = {"rows": rows, "jacobi_sweeps": jac, "inner_iterations": its, "sweeps": sweeps}
         else:
             nbytes += rows * BCG_BYTES_ROW_IT * its
             flops += rows * BCG_FLOPS_ROW_IT * its
-            counts[q] = {"rows": rows, "iterations": its}
+            counts[q] = {"rows": rows, "jacobi_sweeps": jac, "iterations": its}
     return ("k_bicgstab_ir" if mixed else "k_bicgstab"), launches, nbytes, flops, "fp64", counts
 
 
@@ -632,6 +641,7 @@ def run_ours(args):
         "roofline": roofline(head, h, case, args.steps, workload_name(args)),
         "stage_ms_per_step": {k: v / args.steps for k, v in h["prof"]["ms"].items() if v > 0},
         "iters_per_step": {k: v / args.steps for k, v in h["prof"]["iters"].items()},
+        "jacobi_sweeps_per_step": {k: v / args.steps for k, v in h["prof"]["jacobi"].items()},
         "refinements_last_step": dict(h["stats"]["refinements"]),
     }
     for name in names[1:]:

@@ -497,7 +497,6 @@ __device__ __forceinline__ void poisson_rhs_rows(const Params& pr, const double*
                                                  const double* __restrict__ vs, const double* __restrict__ ws,
                                                  double* b, int first, int stride, int end) {
   const Axes ax = axes_of(pr);
-  const int nx = pr.nx, ny = pr.ny;
   const double scale = pr.rhs_scale;
   for (int r = first; r < end; r += stride) {
     int i, j, k;

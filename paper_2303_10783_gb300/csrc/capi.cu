@@ -487,6 +487,7 @@ ss_status stage_solve(ss_case* c, int sys, bool fuse_project = false) {
     if (sys == SS_SYS_W && c->pr.dim != 3) return SS_OK;
     ctl.tol = c->g.tol_t;
     ctl.max_it = c->g.max_it_t;
+    ctl.jacobi = sys != SS_SYS_T;   // T* is diffusion-dominated: a Jacobi sweep gains little
     e = cudaSuccess;
     if (sys == SS_SYS_T && transform_energy_solve(c)) {
       ctl.after_presolve = 1;
@@ -546,6 +547,7 @@ ss_status stage_solve_momentum(ss_case* c) {
     ctl[q].inner_tol = kInnerTolTransport;
     ctl[q].tol = c->g.tol_t;
     ctl[q].max_it = c->g.max_it_t;
+    ctl[q].jacobi = 1;
     sys[q] = &c->sys[q];
     sc[q] = &c->sc[q];
   }
@@ -1052,6 +1054,7 @@ ss_status ss_get_stats(ss_case* c, ss_stats* out) {
     out->iters[q] = h.stat[q].iters;
     out->refinements[q] = h.stat[q].refinements;
     out->relres[q] = h.stat[q].relres;
+    out->jacobi[q] = h.stat[q].jacobi;
   }
   out->status = (s == SS_OK) ? SS_OK : (int)s;
   return s;
@@ -1085,7 +1088,8 @@ ss_status ss_get_profile(ss_case* c, ss_profile* out) {
   CUDA_TRY(cudaMemcpy(&h, c->st, sizeof(DevStatus), cudaMemcpyDeviceToHost));
   for (int s = 0; s < SS_NSYS; ++s) {
     out->iters[s] = h.stat[s].iters_total;
-    CUDA_TRY(cudaMemsetAsync(&c->st->stat[s].iters_total, 0, sizeof(long long), c->stream));
+    out->jacobi[s] = h.stat[s].jacobi_total;
+    CUDA_TRY(cudaMemsetAsync(&c->st->stat[s].iters_total, 0, 2 * sizeof(long long), c->stream));
   }
   out->presolve_sweeps = h.presolve_sweeps;
   CUDA_TRY(cudaMemsetAsync(&c->st->presolve_sweeps, 0, sizeof(long long), c->stream));
@@ -1275,7 +1279,7 @@ ss_status ss_batch_create(ss_case* const* cases, int n, void* workspace, size_t 
     const Sys* sys[3];
     for (int a = 0; a < c->pr.dim; ++a) {
       ctl[a].mixed = 1; ctl[a].block_cap = 0; ctl[a].stat_index = a; ctl[a].inner_tol = kInnerTolTransport;
-      ctl[a].tol = c->g.tol_t; ctl[a].max_it = c->g.max_it_t;
+      ctl[a].tol = c->g.tol_t; ctl[a].max_it = c->g.max_it_t; ctl[a].jacobi = 1;
       sys[a] = &c->sys[a];
     }
     fill_packed_bcg_team(&bcg[(0 * (size_t)n + q) * bt], sys, c->pr.dim, c->pr.dim == 3, ctl, c->sc[0], c->st);
@@ -1287,6 +1291,7 @@ ss_status ss_batch_create(ss_case* const* cases, int n, void* workspace, size_t 
     ct.stat_index = SS_SYS_T;
     ct.inner_tol = kInnerTolEnergy;
     ct.after_presolve = transform_energy_solve(c) ? 1 : 0;
+    ct.jacobi = 0;
     sys[0] = &c->sys[SS_SYS_T];
     fill_packed_bcg_team(&bcg[(2 * (size_t)n + q) * bt], sys, 1, c->pr.dim == 3, &ct, c->sc[0], c->st);
     SolverCtl cp;

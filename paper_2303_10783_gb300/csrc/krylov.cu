@@ -52,6 +52,7 @@ struct BcgArgs {
   int max_blocks;
   DevStatus* st;
   int after_presolve;      // 1: the T* pre-solve ran before this launch and may have met tol
+  int jacobi;              // 1: FP64 Jacobi sweeps first (jacobi64)
 };
 
 template <typename T>
@@ -70,11 +71,13 @@ __device__ __forceinline__ T spmv_row(const Planes<T>& a, const T* x, int r, int
 
 // Solve statistics, written by thread 0 of the leading block of the solving team.
 __device__ void record(DevStatus* st, bool leader, int idx, int iters, int refinements, bool converged,
-                       double relres) {
+                       double relres, int jacobi = 0) {
   if (leader && threadIdx.x == 0) {
     SolveStat& s = st->stat[idx];
     s.iters = iters;
     s.iters_total += iters;
+    s.jacobi = jacobi;
+    s.jacobi_total += jacobi;
     s.refinements = refinements;
     s.converged = converged ? 1 : 0;
     s.nonfinite = isfinite(relres) ? 0 : 1;
@@ -531,14 +534,97 @@ __device__ bool bcg_fused(const Planes<float>& a, int n, int sy, int sz, int has
   return true;
 }
 
+// FP64 Jacobi sweeps x <- x + D^-1 (b - A x) ahead of the Krylov solve of a
+// transport system. Where 1/dt outweighs convection and diffusion the rows
+// are strongly diagonally dominant (Eq. 3.3 and 3.10: on the 128x96x96 box
+// a sweep reduces the residual ~50-fold for the momentum components and
+// ~3000-fold for the solute), and a sweep reads each row's FP64 planes once,
+// where a refinement sweep of the mixed solve needs its FP32 iterations and
+// an FP64 update pass. Sweep k forms r_k = b - A x_k and x_{k+1} in one pass,
+// ping-ponging between x and a scratch vector, and reduces |r_k|:
+//   |r_k| <= tol |b|: x_k is the solution (copied into x if it sits in the
+//     scratch vector); returns 1;
+//   |r_k| > kJacobiRate |r_{k-1}|, or kJacobiMax sweeps: the sweeps stop and
+//     x_{k+1} (in x) is the Krylov solve's initial guess; returns 0;
+//   a barrier gave up: returns -1.
+// The diagonal's inverse is the FP32 plane on the mixed path (a Jacobi
+// preconditioner need not be exact) and the FP64 one otherwise.
+constexpr double kJacobiRate = 0.05;   // per-sweep reduction below which BiCGSTAB is faster
+constexpr int kJacobiMax = 40;
+
+template <bool MIXED>
+__device__ int jacobi64(const BcgArgs& A, const Team& tm, unsigned int& epoch, int& sweeps, double& rel) {
+  const int n = (int)A.sys.d.n;
+  const int sy = A.sys.d.mx, sz = A.sys.d.mx * A.sys.d.my;
+  const int t0 = tm.rank * blockDim.x + threadIdx.x, gs = tm.size * blockDim.x;
+  const Planes<double>& a = A.sys.a;
+  const double* b = A.sys.b;
+  double* const x0 = A.sys.x;
+  double* const x1 = A.v64.p;
+  __shared__ struct {
+    double bn, rn, rel;
+    int state;   // 0 sweep on, 1 converged on x_k, 2 hand x_{k+1} to the Krylov solve
+  } js;
+  double thr = 0.0, prev = 0.0;   // read by thread 0 only
+  int k = 0;
+  while (true) {
+    const double* xk = (k & 1) ? x1 : x0;
+    double* xn = (k & 1) ? x0 : x1;
+    Vec<2> acc = {{0.0, 0.0}};
+    for (int r = t0; r < n; r += gs) {
+      const double rr = b[r] - spmv_row(a, xk, r, sy, sz, A.has_z);
+      const double dinv = MIXED ? (double)__ldg(A.sys.af.idiag + r) : __ldg(a.idiag + r);
+      xn[r] = fma(dinv, rr, xk[r]);
+      acc.v[0] += rr * rr;
+      if (k == 0) acc.v[1] += b[r] * b[r];
+    }
+    if (!team_sum_post<2>(acc, tm, A.max_blocks, (k & 1) ? 10 : 8, A.st, epoch, [&](const double* tot) {
+          const double rn = sqrt(tot[0]);
+          if (k == 0) {
+            js.bn = sqrt(tot[1]);
+            thr = A.tol * js.bn;
+          }
+          js.rn = rn;
+          js.rel = js.bn > 0.0 ? rn / js.bn : 0.0;
+          if (js.bn == 0.0 || rn <= thr) js.state = 1;
+          else if (!isfinite(rn) || (k > 0 && rn > kJacobiRate * prev) || k + 1 >= kJacobiMax) js.state = 2;
+          else js.state = 0;
+          prev = rn;
+        }))
+      return -1;
+    ++k;
+    if (js.state == 0) continue;
+    // the result (x_{k-1} when converged, else x_k) into x; the Krylov solve
+    // reads x at neighbouring rows, hence the barrier after a copy
+    const int src = (js.state == 1) ? ((k - 1) & 1) : (k & 1);
+    if (src == 1) {
+      for (int r = t0; r < n; r += gs) x0[r] = x1[r];
+      if (js.state == 2 && !team_barrier(A.st, tm, epoch)) return -1;
+    }
+    sweeps = k;
+    rel = js.rel;
+    return js.state == 1 ? 1 : 0;
+  }
+}
+
 __device__ __forceinline__ void fp64_solve(const BcgArgs& A, const Team& tm, unsigned int& epoch) {
   const int n = (int)A.sys.d.n;
   const int sy = A.sys.d.mx, sz = A.sys.d.mx * A.sys.d.my;
+  int jac = 0;
+  if (A.jacobi) {
+    double rel = 0.0;
+    const int j = jacobi64<false>(A, tm, epoch, jac, rel);
+    if (j < 0) return;
+    if (j == 1) {
+      record(A.st, tm.rank == 0, A.stat_index, 0, 0, true, rel, jac);
+      return;
+    }
+  }
   CoreOut o;
   if (!bcg_core<double>(A.sys.a, n, sy, sz, A.has_z, A.sys.b, A.sys.x, false, A.v64, A.tol, A.max_it, tm,
                         A.max_blocks, A.st, epoch, o))
     return;
-  record(A.st, tm.rank == 0, A.stat_index, o.it, 0, o.conv, o.bnorm > 0.0 ? o.res / o.bnorm : 0.0);
+  record(A.st, tm.rank == 0, A.stat_index, o.it, 0, o.conv, o.bnorm > 0.0 ? o.res / o.bnorm : 0.0, jac);
 }
 
 // Mixed precision: FP64 iterative refinement around an FP32 BiCGSTAB on the
@@ -565,32 +651,50 @@ constexpr double kSweepMargin = 0.1;
 // copy from the FP64 residual, scaled in FP64.
 constexpr double kStageLo = 0x1p-60, kStageHi = 0x1p60;
 
-// The inner correction d at row q as the update pass reads it (see CoreOut).
+// The inner correction d at row q as the update pass reads it (see CoreOut):
+// MODE 0: x; 1: al D^-1 p; 2: x + al D^-1 p. A template parameter, so that
+// the loads of all seven stencil points issue together.
+template <int MODE>
 struct DCorr {
   const float *x, *d, *p;
   float al;
-  int mode;   // 0: x; 1: al D^-1 p; 2: x + al D^-1 p
   __device__ __forceinline__ float at(int q) const {
-    if (mode == 0) return x[q];
+    if (MODE == 0) return x[q];
     const float y = d[q] * p[q];
-    return mode == 1 ? al * y : fmaf(al, y, x[q]);
+    return MODE == 1 ? al * y : fmaf(al, y, x[q]);
   }
 };
 
-// (A d)_r in FP64 with the FP64 planes, d widened exactly (same order of
-// operations as spmv_row)
-__device__ __forceinline__ double spmv64_corr(const Planes<double>& a, const DCorr& f, double dc, int r, int sy,
-                                              int sz, int has_z) {
-  double acc = __ldg(a.P + r) * dc;
-  acc = fma(__ldg(a.W + r), to_f64(f.at(r - 1)), acc);
-  acc = fma(__ldg(a.E + r), to_f64(f.at(r + 1)), acc);
-  acc = fma(__ldg(a.S + r), to_f64(f.at(r - sy)), acc);
-  acc = fma(__ldg(a.N + r), to_f64(f.at(r + sy)), acc);
-  if (has_z) {
-    acc = fma(__ldg(a.B + r), to_f64(f.at(r - sz)), acc);
-    acc = fma(__ldg(a.T_ + r), to_f64(f.at(r + sz)), acc);
+// x += rn d, r -= rn A d with the FP64 planes (d widened exactly; the same
+// order of operations as spmv_row), and the FP32 copy of the new r; returns
+// this thread's part of |r|^2.
+template <int MODE>
+__device__ __forceinline__ double ir_update(const BcgArgs& A, const DCorr<MODE>& f, double rn, int t0, int gs,
+                                            float* r32) {
+  const int n = (int)A.sys.d.n;
+  const int sy = A.sys.d.mx, sz = A.sys.d.mx * A.sys.d.my;
+  const Planes<double>& a = A.sys.a;
+  double* x = A.sys.x;
+  double* r64 = A.v64.r;
+  double s = 0.0;
+  for (int r = t0; r < n; r += gs) {
+    const double dc = (double)(f.at(r));
+    double acc = __ldg(a.P + r) * dc;
+    acc = fma(__ldg(a.W + r), (double)(f.at(r - 1)), acc);
+    acc = fma(__ldg(a.E + r), (double)(f.at(r + 1)), acc);
+    acc = fma(__ldg(a.S + r), (double)(f.at(r - sy)), acc);
+    acc = fma(__ldg(a.N + r), (double)(f.at(r + sy)), acc);
+    if (A.has_z) {
+      acc = fma(__ldg(a.B + r), (double)(f.at(r - sz)), acc);
+      acc = fma(__ldg(a.T_ + r), (double)(f.at(r + sz)), acc);
+    }
+    const double ri = fma(-rn, acc, r64[r]);
+    x[r] = fma(rn, dc, x[r]);
+    r64[r] = ri;
+    r32[r] = to_f32(ri);
+    s += ri * ri;
   }
-  return acc;
+  return s;
 }
 
 __device__ __forceinline__ void ir_solve(const BcgArgs& A, const Team& tm, unsigned int& epoch) {
@@ -604,6 +708,16 @@ __device__ __forceinline__ void ir_solve(const BcgArgs& A, const Team& tm, unsig
   if (A.after_presolve && A.st->presolve_done) {  // the pre-solve met tol on the true FP64 residual
     record(A.st, tm.rank == 0, A.stat_index, 0, 0, true, A.st->presolve_rel);
     return;
+  }
+  int jac = 0;
+  if (A.jacobi) {
+    double rel = 0.0;
+    const int j = jacobi64<true>(A, tm, epoch, jac, rel);
+    if (j < 0) return;
+    if (j == 1) {
+      record(A.st, tm.rank == 0, A.stat_index, 0, 0, true, rel, jac);
+      return;
+    }
   }
   Vec<2> acc = {{0.0, 0.0}};
   for (int i = t0; i < n; i += gs) {
@@ -653,16 +767,11 @@ __device__ __forceinline__ void ir_solve(const BcgArgs& A, const Team& tm, unsig
     if (o.it == 0) break;                         // the inner solve made no progress
     total += o.it;
     // x += rn d, r -= rn A d, and the FP32 copy of the new r
-    const DCorr dc{A.d32, A.sys.af.idiag, o.p, o.al, !o.half ? 0 : (o.it == 1 ? 1 : 2)};
-    Vec<1> s1 = {{0.0}};
-    for (int i = t0; i < n; i += gs) {
-      const double di = to_f64(dc.at(i));
-      const double ri = fma(-rn, spmv64_corr(A.sys.a, dc, di, i, sy, sz, A.has_z), r64[i]);
-      x[i] = fma(rn, di, x[i]);
-      r64[i] = ri;
-      r32[i] = to_f32(ri);
-      s1.v[0] += ri * ri;
-    }
+    const float* dg = A.sys.af.idiag;
+    Vec<1> s1;
+    if (!o.half) s1.v[0] = ir_update(A, DCorr<0>{A.d32, dg, o.p, o.al}, rn, t0, gs, r32);
+    else if (o.it == 1) s1.v[0] = ir_update(A, DCorr<1>{A.d32, dg, o.p, o.al}, rn, t0, gs, r32);
+    else s1.v[0] = ir_update(A, DCorr<2>{A.d32, dg, o.p, o.al}, rn, t0, gs, r32);
     if (!team_sum_post<1>(s1, tm, A.max_blocks, 15, A.st, epoch, [&](const double* tot) {
           is.rn = sqrt(tot[0]);
           is.inv = 1.0 / is.rn;
@@ -674,7 +783,7 @@ __device__ __forceinline__ void ir_solve(const BcgArgs& A, const Team& tm, unsig
         }))
       return;
   }
-  record(A.st, tm.rank == 0, A.stat_index, total, ref, is.conv != 0, is.rel);
+  record(A.st, tm.rank == 0, A.stat_index, total, ref, is.conv != 0, is.rel, jac);
 }
 
 // Up to kMaxTeams independent systems in one cooperative launch: team s is
@@ -899,6 +1008,7 @@ void fill_bcg_args(BcgArgs& A, const Sys& sys, int has_z, const SolverCtl& ctl, 
   A.max_blocks = c.max_blocks;
   A.st = st;
   A.after_presolve = ctl.after_presolve;
+  A.jacobi = ctl.jacobi;
 }
 
 int g_num_sms = 0;

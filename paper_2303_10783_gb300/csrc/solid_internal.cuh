@@ -48,7 +48,9 @@ struct Dims {
 // Per-solve outcome written by the solver kernels.
 struct SolveStat {
   long long iters_total;   // summed over solves since the host last read it
+  long long jacobi_total;  // FP64 Jacobi sweeps, summed likewise
   int iters;
+  int jacobi;              // FP64 Jacobi sweeps before the Krylov iterations (transport systems)
   int refinements;
   int converged;       // 1 converged, 0 hit the cap
   int nonfinite;       // 1 if a non-finite residual appeared
@@ -529,6 +531,7 @@ struct SolverCtl {
   int block_cap;         // > 0: at most this many blocks in the cooperative launch
   int warm_start = 0;    // 1: the solution buffer holds the initial guess (multigrid pressure, mixed path)
   int after_presolve = 0;  // 1: the T* pre-solve ran just before on this stream (mixed path)
+  int jacobi = 0;          // 1: FP64 Jacobi sweeps first, while they contract fast (transport systems)
 };
 cudaError_t launch_bicgstab(const Sys& sys, int has_z, const SolverCtl& ctl, Scratch& sc, DevStatus* st,
                             cudaStream_t s);

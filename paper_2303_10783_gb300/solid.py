@@ -48,7 +48,7 @@ class BC(ctypes.Structure):
 
 class Stats(ctypes.Structure):
     _fields_ = [("steps", ctypes.c_longlong), ("iters", ctypes.c_int * 6), ("refinements", ctypes.c_int * 6),
-                ("relres", ctypes.c_double * 6), ("status", ctypes.c_int)]
+                ("relres", ctypes.c_double * 6), ("status", ctypes.c_int), ("jacobi", ctypes.c_int * 6)]
 
 
 PROF_NAMES = (tuple("assemble_" + s for s in SYSTEMS) + tuple("solve_" + s for s in SYSTEMS) +
@@ -57,7 +57,8 @@ PROF_NAMES = (tuple("assemble_" + s for s in SYSTEMS) + tuple("solve_" + s for s
 
 class Profile(ctypes.Structure):
     _fields_ = [("ms", ctypes.c_double * 15), ("launches", ctypes.c_longlong * 15), ("kernels", ctypes.c_longlong),
-                ("iters", ctypes.c_longlong * 6), ("presolve_sweeps", ctypes.c_longlong)]
+                ("iters", ctypes.c_longlong * 6), ("presolve_sweeps", ctypes.c_longlong),
+                ("jacobi", ctypes.c_longlong * 6)]
 
 
 class SolidError(RuntimeError):
@@ -345,7 +346,8 @@ class Case:
         return dict(steps=s.steps, status=st,
                     iters={k: s.iters[i] for i, k in enumerate(SYSTEMS)},
                     refinements={k: s.refinements[i] for i, k in enumerate(SYSTEMS)},
-                    relres={k: s.relres[i] for i, k in enumerate(SYSTEMS)})
+                    relres={k: s.relres[i] for i, k in enumerate(SYSTEMS)},
+                    jacobi={k: s.jacobi[i] for i, k in enumerate(SYSTEMS)})
 
     def set_profiling(self, on=True):
         check(self.lib.ss_set_profiling(self.h, int(bool(on))))
@@ -356,7 +358,8 @@ class Case:
         check(self.lib.ss_get_profile(self.h, ctypes.byref(p)))
         return dict(ms={k: p.ms[i] for i, k in enumerate(PROF_NAMES)},
                     launches={k: p.launches[i] for i, k in enumerate(PROF_NAMES)}, kernels=p.kernels,
-                    iters={k: p.iters[i] for i, k in enumerate(SYSTEMS)}, presolve_sweeps=p.presolve_sweeps)
+                    iters={k: p.iters[i] for i, k in enumerate(SYSTEMS)}, presolve_sweeps=p.presolve_sweeps,
+                    jacobi={k: p.jacobi[i] for i, k in enumerate(SYSTEMS)})
 
     def close(self):
         if getattr(self, "h", None):
