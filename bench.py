@@ -62,14 +62,13 @@ MG_FLOPS_PER_CELL_IT = 125.0
 DCT_BYTES_PER_CELL_SWEEP_BASE = 48.0
 DCT_BYTES_PER_CELL_LAUNCH = 56.0
 DCT_THOMAS_FLOPS = 8.0
-# k_bicgstab_ir (mixed transport: FP32 BiCGSTAB in FP64 refinement), per row:
+# k_bicgstab_ir (mixed transport: FP32 inner solve in FP64 refinement), per row:
 #   the first FP64 residual reads 7 FP64 planes, x and b and writes r and its FP32 copy (84);
-#   each sweep's update pass reads the 7 FP64 planes, the correction, r and x and writes r, x
-#   and the FP32 copy (96), and its first inner pass stages r, rhat and p from the copy
-#   (4 B fewer than a later pass 1) and its first pass 3 does not read x (4): 88; each inner
+#   each sweep adds the correction (x read and written, d read: 20) and forms the next
+#   residual (7 planes, x, b read, r and its copy written: 84): 104; a BiCGSTAB inner
 #   iteration moves 7 FP32 planes twice (56) and ~80 B of FP32 vectors: 136.
 BCG_IR_BYTES_ROW = 84.0
-BCG_IR_BYTES_ROW_SWEEP = 88.0
+BCG_IR_BYTES_ROW_SWEEP = 104.0
 BCG_IR_BYTES_ROW_IT = 136.0
 # k_helmholtz_dct (the T* pre-solve of the mixed path), per cell: the first FP64 residual with
 #   the system's 7 FP64 planes, x and b, staged in FP32 (76 B); per sweep the transforms move
@@ -79,11 +78,11 @@ HELM_BYTES_PER_CELL = 76.0
 HELM_BYTES_PER_CELL_SWEEP = 112.0
 # k_bicgstab (FP64 transport), per row and iteration: two SpMVs over 7 FP64 planes (2 x 72)
 # and the vector updates (~156 B): 300 B; 2 x 13 + 20 = 46 FP64 flops.
-# FP64 Jacobi sweep of a transport solve (both paths), per row: 7 FP64 planes, x and b read,
-#   x written, the inverse diagonal (FP32 on the mixed path, FP64 otherwise): 84 / 88 B;
-#   2 x 7 + 1 + 2 + 2 FP64 flop (the residual row, the update, its square).
-JAC_BYTES_ROW = {"mixed": 84.0, "fp64": 88.0}
-JAC_FLOPS_ROW = 19.0
+# Jacobi sweep of a transport solve, per row: mixed (FP32, inside the refinement) 7 FP32
+#   planes, the inverse diagonal, the staged residual and d read, d written: 44 B, ~16 FP32
+#   flop; FP64: 7 FP64 planes, x, b and the inverse diagonal read, x written: 88 B, 19 FP64 flop.
+JAC_BYTES_ROW = {"mixed": 44.0, "fp64": 88.0}
+JAC_FLOPS_ROW = {"mixed": 16.0, "fp64": 19.0}
 BCG_BYTES_ROW_IT = 300.0
 BCG_FLOPS_ROW_IT = 46.0
 FP64_FLOP_PER_CLK_PER_SM = 4.0    # 2 DFMA per clock per SM (1.26 TFLOP/s at 2070 MHz, 152 SMs)
@@ -528,11 +527,11 @@ def kernel_work(stage, precision_name, case, prof, stats):
         its = prof["iters"][q]
         jac = prof.get("jacobi", {}).get(q, 0)
         nbytes += rows * JAC_BYTES_ROW[precision_name] * jac
-        flops += rows * JAC_FLOPS_ROW * jac
+        if not mixed:
+            flops += rows * JAC_FLOPS_ROW["fp64"] * jac
         if mixed:
             sweeps = stats["refinements"][q] * launches    # sweeps of the last step, for each launch
-            krylov = launches if sweeps > 0 else 0         # launches whose Jacobi sweeps did not converge
-            nbytes += rows * (BCG_IR_BYTES_ROW * krylov + BCG_IR_BYTES_ROW_SWEEP * sweeps + BCG_IR_BYTES_ROW_IT * its)
+            nbytes += rows * (BCG_IR_BYTES_ROW * launches + BCG_IR_BYTES_ROW_SWEEP * sweeps + BCG_IR_BYTES_ROW_IT * its)
             counts[q] = {"rows": rows, "jacobi_sweeps": jac, "inner_iterations": its, "sweeps": sweeps}
         else:
             nbytes += rows * BCG_BYTES_ROW_IT * its

@@ -140,8 +140,8 @@ typedef struct {
   int refinements[SS_NSYS]; /* FP64 refinement sweeps (SS_MIXED), else 0 */
   double relres[SS_NSYS];   /* final relative residual of each solve (FP64 residual) */
   int status;               /* sticky ss_status of the solves since the last read */
-  int jacobi[SS_NSYS];      /* FP64 Jacobi sweeps of each transport solve before its
-                               Krylov iterations (see ss_solve) */
+  int jacobi[SS_NSYS];      /* Jacobi sweeps of each transport solve (see ss_solve);
+                               `iters` then counts the BiCGSTAB iterations only */
 } ss_stats;
 
 /* Stage timing: when profiling is on, the step driver records a CUDA event
@@ -163,7 +163,7 @@ typedef struct {
   long long iters[SS_NSYS]; /* Krylov iterations summed over the solves of each system
                                (refinement sweeps for the transform pressure solver) */
   long long presolve_sweeps;/* sweeps of the T* transform pre-solve */
-  long long jacobi[SS_NSYS];/* FP64 Jacobi sweeps summed over the solves of each system */
+  long long jacobi[SS_NSYS];/* Jacobi sweeps summed over the solves of each system */
 } ss_profile;
 
 /* Bytes of device workspace a case of this grid needs (256-byte aligned
@@ -281,9 +281,10 @@ const char* ss_last_error(void);
  *   mixed-precision case with the multigrid or cosine-transform solver, 0 in
  *   a new case, after ss_set_fields and on the other paths) into the system's
  *   solution vector;
- *   U/V/W/C start with FP64 Jacobi sweeps x += D^-1 (b - A x) while each
- *   reduces the residual at least 20-fold, then continue with BiCGSTAB (FP64,
- *   or FP32 inside FP64 refinement in SS_MIXED) from the last sweep;
+ *   U/V/W/C use Jacobi sweeps x += D^-1 (b - A x) while each reduces the
+ *   residual at least 20-fold, and BiCGSTAB after a sweep that does not:
+ *   SS_FP64 sweeps in FP64 before its BiCGSTAB; SS_MIXED sweeps in FP32 as
+ *   the inner solve of each FP64 refinement sweep;
  *   returns the solve's outcome.
  * ss_get_system(c, sys, dst, dst_is_device): copy planes and vectors of the
  *   system into dst[0..8] = P, W, E, S, N, B, T (DIA planes, Eq. 4.1), b

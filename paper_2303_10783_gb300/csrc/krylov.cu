@@ -97,8 +97,9 @@ struct CoreOut {
   int it;
   bool conv;
   double res, bnorm;
-  // bcg_fused only: the solve stopped on the half step, and its correction is
-  // x + al D^-1 p (x read as 0 when it == 1), formed where the caller reads it
+  // bcg_fused: the solve stopped on the half step, and its correction is
+  // x + al D^-1 p (x read as 0 when it == 1), formed where the caller reads it;
+  // jac_fused: the sweeps stalled, and p is the buffer holding the correction
   bool half = false;
   float al = 0.f;
   const float* p = nullptr;
@@ -541,18 +542,17 @@ __device__ bool bcg_fused(const Planes<float>& a, int n, int sy, int sz, int has
 // ~3000-fold for the solute), and a sweep reads each row's FP64 planes once,
 // where a refinement sweep of the mixed solve needs its FP32 iterations and
 // an FP64 update pass. Sweep k forms r_k = b - A x_k and x_{k+1} in one pass,
-// ping-ponging between x and a scratch vector, and reduces |r_k|:
+// ping-ponging between x and the residual vector, and reduces |r_k|:
 //   |r_k| <= tol |b|: x_k is the solution (copied into x if it sits in the
 //     scratch vector); returns 1;
 //   |r_k| > kJacobiRate |r_{k-1}|, or kJacobiMax sweeps: the sweeps stop and
 //     x_{k+1} (in x) is the Krylov solve's initial guess; returns 0;
 //   a barrier gave up: returns -1.
-// The diagonal's inverse is the FP32 plane on the mixed path (a Jacobi
-// preconditioner need not be exact) and the FP64 one otherwise.
+// This is the FP64 path's form; the mixed path runs the same sweeps in FP32
+// inside its FP64 refinement (jac_fused).
 constexpr double kJacobiRate = 0.05;   // per-sweep reduction below which BiCGSTAB is faster
 constexpr int kJacobiMax = 40;
 
-template <bool MIXED>
 __device__ int jacobi64(const BcgArgs& A, const Team& tm, unsigned int& epoch, int& sweeps, double& rel) {
   const int n = (int)A.sys.d.n;
   const int sy = A.sys.d.mx, sz = A.sys.d.mx * A.sys.d.my;
@@ -560,7 +560,7 @@ __device__ int jacobi64(const BcgArgs& A, const Team& tm, unsigned int& epoch, i
   const Planes<double>& a = A.sys.a;
   const double* b = A.sys.b;
   double* const x0 = A.sys.x;
-  double* const x1 = A.v64.p;
+  double* const x1 = A.v64.r;   // every scratch set has it; the Krylov solve writes it only after the sweeps
   __shared__ struct {
     double bn, rn, rel;
     int state;   // 0 sweep on, 1 converged on x_k, 2 hand x_{k+1} to the Krylov solve
@@ -573,7 +573,7 @@ __device__ int jacobi64(const BcgArgs& A, const Team& tm, unsigned int& epoch, i
     Vec<2> acc = {{0.0, 0.0}};
     for (int r = t0; r < n; r += gs) {
       const double rr = b[r] - spmv_row(a, xk, r, sy, sz, A.has_z);
-      const double dinv = MIXED ? (double)__ldg(A.sys.af.idiag + r) : __ldg(a.idiag + r);
+      const double dinv = __ldg(a.idiag + r);
       xn[r] = fma(dinv, rr, xk[r]);
       acc.v[0] += rr * rr;
       if (k == 0) acc.v[1] += b[r] * b[r];
@@ -613,7 +613,7 @@ __device__ __forceinline__ void fp64_solve(const BcgArgs& A, const Team& tm, uns
   int jac = 0;
   if (A.jacobi) {
     double rel = 0.0;
-    const int j = jacobi64<false>(A, tm, epoch, jac, rel);
+    const int j = jacobi64(A, tm, epoch, jac, rel);
     if (j < 0) return;
     if (j == 1) {
       record(A.st, tm.rank == 0, A.stat_index, 0, 0, true, rel, jac);
@@ -627,14 +627,15 @@ __device__ __forceinline__ void fp64_solve(const BcgArgs& A, const Team& tm, uns
   record(A.st, tm.rank == 0, A.stat_index, o.it, 0, o.conv, o.bnorm > 0.0 ? o.res / o.bnorm : 0.0, jac);
 }
 
-// Mixed precision: FP64 iterative refinement around an FP32 BiCGSTAB on the
-// FP32 copies of the planes. Each sweep solves A d = r / |r| in FP32 to the
+// Mixed precision: FP64 iterative refinement around an FP32 inner solve on
+// the FP32 copies of the planes: Jacobi sweeps (jac_fused) for the strongly
+// diagonally dominant systems the caller marks, until they stall, else
+// BiCGSTAB (bcg_fused). Each sweep solves A d = r / |r| in FP32 to the
 // relative inner tolerance chosen per system by the caller, adds |r| d to the
-// FP64 iterate, and updates the FP64 residual r -= |r| A d with the FP64
-// planes (b - A x in exact arithmetic; the launch starts from the true
-// residual of its initial guess). It stops when the FP64 residual meets tol
-// (the same test as the FP64 path). The pass that forms the residual also
-// stores its FP32 copy, which the inner solve scales by 1/|r| as it reads it.
+// FP64 iterate and forms the true FP64 residual b - A x with the FP64 planes.
+// It stops when that residual meets tol (the same test as the FP64 path). The
+// pass that forms the residual also stores its FP32 copy, which the inner
+// solve scales by 1/|r| as it reads it.
 constexpr int kMaxRefine = 12;
 // Inner iterations per refinement sweep: bounds a sweep whose FP32 iteration
 // stalls (the outer FP64 loop then continues from the best iterate).
@@ -651,49 +652,126 @@ constexpr double kSweepMargin = 0.1;
 // copy from the FP64 residual, scaled in FP64.
 constexpr double kStageLo = 0x1p-60, kStageHi = 0x1p60;
 
-// The inner correction d at row q as the update pass reads it (see CoreOut):
-// MODE 0: x; 1: al D^-1 p; 2: x + al D^-1 p. A template parameter, so that
-// the loads of all seven stencil points issue together.
-template <int MODE>
-struct DCorr {
-  const float *x, *d, *p;
-  float al;
-  __device__ __forceinline__ float at(int q) const {
-    if (MODE == 0) return x[q];
-    const float y = d[q] * p[q];
-    return MODE == 1 ? al * y : fmaf(al, y, x[q]);
+// FP32 Jacobi sweeps for the inner solve A d = r0, r0 = sc r32 (unit norm;
+// r32 is the caller's FP32 copy of its residual in V.t), for the strongly
+// diagonally dominant transport systems (see jacobi64): d_1 = D^-1 r0 (no
+// operator application), then d_{k+1} = d_k + D^-1 (r0 - A d_k) with
+// s_k = |r0 - A d_k| reduced in the same pass. It stops when s_k <= tol
+// (out.conv; the result is d_{k+1}), when a sweep reduced s less than
+// 1/kJacobiRate-fold (out.half is set as the stall flag: the caller's
+// later sweeps use BiCGSTAB), or after max_it sweeps. d ping-pongs between x
+// and V.p0; out.p is the result, out.it the sweeps. Reduction slots 0..3.
+__device__ bool jac_fused(const Planes<float>& a, int n, int sy, int sz, int has_z, float* x, FusedVec V, float sc,
+                          double tol, int max_it, const Team& tm, int max_blocks, DevStatus* st,
+                          unsigned int& epoch, CoreOut& out) {
+  const int t0 = tm.rank * blockDim.x + threadIdx.x, gs = tm.size * blockDim.x;
+  const int n4 = n >> 2, tail = n4 << 2;
+  const bool ay = (sy & 3) == 0, az = (sz & 3) == 0;
+  const float* r32 = V.t;
+  const float* dg = a.idiag;
+  float* const b0 = x;
+  float* const b1 = V.p0;
+  __shared__ struct {
+    double res, prev;
+    int state;   // 0 sweep on, 1 converged, 2 stalled, 3 sweep cap
+  } js;
+  for (int m = t0; m < n4; m += gs) {             // d_1 = D^-1 r0
+    const float4 q = ld4(r32, m), dv = ldg4(dg, m);
+    st4(b0, m, make_float4(dv.x * (q.x * sc), dv.y * (q.y * sc), dv.z * (q.z * sc), dv.w * (q.w * sc)));
   }
-};
+  for (int i = tail + t0; i < n; i += gs) b0[i] = __ldg(dg + i) * (r32[i] * sc);
+  out.half = false;
+  out.bnorm = 1.0;
+  if (max_it <= 1) {
+    out.it = 1;
+    out.p = b0;
+    out.conv = false;
+    out.res = 1.0;
+    return true;
+  }
+  if (threadIdx.x == 0) js.prev = 1.0;
+  if (!team_barrier(st, tm, epoch)) return false;
+  int k = 1;
+  while (true) {
+    const float* dk = (k & 1) ? b0 : b1;
+    float* dn = (k & 1) ? b1 : b0;
+    float s2 = 0.f;
+    for (int m = t0; m < n4; m += gs) {
+      const int r = 4 * m;
+      const float4 P = ldg4(a.P, m), W = ldg4(a.W, m), E = ldg4(a.E, m), S = ldg4(a.S, m), N = ldg4(a.N, m);
+      const float4 xc = ld4(dk, m);
+      const float xw = dk[r - 1], xe = dk[r + 4];
+      const float4 xs = ay ? ld4(dk, (r - sy) >> 2) : make_float4(dk[r - sy], dk[r - sy + 1], dk[r - sy + 2], dk[r - sy + 3]);
+      const float4 xn = ay ? ld4(dk, (r + sy) >> 2) : make_float4(dk[r + sy], dk[r + sy + 1], dk[r + sy + 2], dk[r + sy + 3]);
+      float4 o;
+      o.x = P.x * xc.x; o.y = P.y * xc.y; o.z = P.z * xc.z; o.w = P.w * xc.w;
+      o.x = fmaf(W.x, xw, o.x); o.y = fmaf(W.y, xc.x, o.y); o.z = fmaf(W.z, xc.y, o.z); o.w = fmaf(W.w, xc.z, o.w);
+      o.x = fmaf(E.x, xc.y, o.x); o.y = fmaf(E.y, xc.z, o.y); o.z = fmaf(E.z, xc.w, o.z); o.w = fmaf(E.w, xe, o.w);
+      o.x = fmaf(S.x, xs.x, o.x); o.y = fmaf(S.y, xs.y, o.y); o.z = fmaf(S.z, xs.z, o.z); o.w = fmaf(S.w, xs.w, o.w);
+      o.x = fmaf(N.x, xn.x, o.x); o.y = fmaf(N.y, xn.y, o.y); o.z = fmaf(N.z, xn.z, o.z); o.w = fmaf(N.w, xn.w, o.w);
+      if (has_z) {
+        const float4 B = ldg4(a.B, m), T = ldg4(a.T_, m);
+        const float4 xb = az ? ld4(dk, (r - sz) >> 2)
+                             : make_float4(dk[r - sz], dk[r - sz + 1], dk[r - sz + 2], dk[r - sz + 3]);
+        const float4 xt = az ? ld4(dk, (r + sz) >> 2)
+                             : make_float4(dk[r + sz], dk[r + sz + 1], dk[r + sz + 2], dk[r + sz + 3]);
+        o.x = fmaf(B.x, xb.x, o.x); o.y = fmaf(B.y, xb.y, o.y); o.z = fmaf(B.z, xb.z, o.z); o.w = fmaf(B.w, xb.w, o.w);
+        o.x = fmaf(T.x, xt.x, o.x); o.y = fmaf(T.y, xt.y, o.y); o.z = fmaf(T.z, xt.z, o.z); o.w = fmaf(T.w, xt.w, o.w);
+      }
+      const float4 q = ld4(r32, m), dv = ldg4(dg, m);
+      float4 sv;
+      sv.x = fmaf(q.x, sc, -o.x); sv.y = fmaf(q.y, sc, -o.y); sv.z = fmaf(q.z, sc, -o.z); sv.w = fmaf(q.w, sc, -o.w);
+      st4(dn, m, make_float4(fmaf(dv.x, sv.x, xc.x), fmaf(dv.y, sv.y, xc.y), fmaf(dv.z, sv.z, xc.z),
+                             fmaf(dv.w, sv.w, xc.w)));
+      s2 += dot4(sv, sv);
+    }
+    for (int i = tail + t0; i < n; i += gs) {
+      float acc = __ldg(a.P + i) * dk[i];
+      acc = fmaf(__ldg(a.W + i), dk[i - 1], acc);
+      acc = fmaf(__ldg(a.E + i), dk[i + 1], acc);
+      acc = fmaf(__ldg(a.S + i), dk[i - sy], acc);
+      acc = fmaf(__ldg(a.N + i), dk[i + sy], acc);
+      if (has_z) {
+        acc = fmaf(__ldg(a.B + i), dk[i - sz], acc);
+        acc = fmaf(__ldg(a.T_ + i), dk[i + sz], acc);
+      }
+      const float si = fmaf(r32[i], sc, -acc);
+      dn[i] = fmaf(__ldg(dg + i), si, dk[i]);
+      s2 += si * si;
+    }
+    if (!team_sum_post<1>(VecF<1>{{s2}}, tm, max_blocks, (k & 1) ? 0 : 2, st, epoch, [&](const double* tot) {
+          const double res = sqrt(tot[0]);
+          js.state = (res <= tol) ? 1 : (!isfinite(res) || res > kJacobiRate * js.prev) ? 2 : (k + 1 >= max_it) ? 3 : 0;
+          js.res = res;
+          js.prev = res;
+        }))
+      return false;
+    ++k;
+    if (js.state != 0) break;
+  }
+  out.it = k;                  // d_1 .. d_k: k sweeps, the last result in dn
+  out.p = ((k - 1) & 1) ? b1 : b0;
+  out.conv = js.state == 1;
+  out.half = js.state == 2;
+  out.res = js.res;
+  return true;
+}
 
-// x += rn d, r -= rn A d with the FP64 planes (d widened exactly; the same
-// order of operations as spmv_row), and the FP32 copy of the new r; returns
-// this thread's part of |r|^2.
-template <int MODE>
-__device__ __forceinline__ double ir_update(const BcgArgs& A, const DCorr<MODE>& f, double rn, int t0, int gs,
-                                            float* r32) {
+// FP64 residual r = b - A x and its FP32 copy; returns this thread's |r|^2
+// (and |b|^2 in bb when asked).
+__device__ __forceinline__ double ir_residual(const BcgArgs& A, int t0, int gs, float* r32, double* bb) {
   const int n = (int)A.sys.d.n;
   const int sy = A.sys.d.mx, sz = A.sys.d.mx * A.sys.d.my;
-  const Planes<double>& a = A.sys.a;
-  double* x = A.sys.x;
-  double* r64 = A.v64.r;
-  double s = 0.0;
-  for (int r = t0; r < n; r += gs) {
-    const double dc = (double)(f.at(r));
-    double acc = __ldg(a.P + r) * dc;
-    acc = fma(__ldg(a.W + r), (double)(f.at(r - 1)), acc);
-    acc = fma(__ldg(a.E + r), (double)(f.at(r + 1)), acc);
-    acc = fma(__ldg(a.S + r), (double)(f.at(r - sy)), acc);
-    acc = fma(__ldg(a.N + r), (double)(f.at(r + sy)), acc);
-    if (A.has_z) {
-      acc = fma(__ldg(a.B + r), (double)(f.at(r - sz)), acc);
-      acc = fma(__ldg(a.T_ + r), (double)(f.at(r + sz)), acc);
-    }
-    const double ri = fma(-rn, acc, r64[r]);
-    x[r] = fma(rn, dc, x[r]);
-    r64[r] = ri;
-    r32[r] = to_f32(ri);
+  const double* b = A.sys.b;
+  double s = 0.0, sb = 0.0;
+  for (int i = t0; i < n; i += gs) {
+    const double ri = b[i] - spmv_row(A.sys.a, A.sys.x, i, sy, sz, A.has_z);
+    A.v64.r[i] = ri;
+    r32[i] = to_f32(ri);
     s += ri * ri;
+    if (bb) sb += b[i] * b[i];
   }
+  if (bb) *bb = sb;
   return s;
 }
 
@@ -702,31 +780,14 @@ __device__ __forceinline__ void ir_solve(const BcgArgs& A, const Team& tm, unsig
   const int sy = A.sys.d.mx, sz = A.sys.d.mx * A.sys.d.my;
   const int t0 = tm.rank * blockDim.x + threadIdx.x, gs = tm.size * blockDim.x;
   double* x = A.sys.x;
-  const double* b = A.sys.b;
   double* r64 = A.v64.r;
   float* r32 = A.f32.t;                           // the residual's FP32 copy, read by the inner solve
   if (A.after_presolve && A.st->presolve_done) {  // the pre-solve met tol on the true FP64 residual
     record(A.st, tm.rank == 0, A.stat_index, 0, 0, true, A.st->presolve_rel);
     return;
   }
-  int jac = 0;
-  if (A.jacobi) {
-    double rel = 0.0;
-    const int j = jacobi64<true>(A, tm, epoch, jac, rel);
-    if (j < 0) return;
-    if (j == 1) {
-      record(A.st, tm.rank == 0, A.stat_index, 0, 0, true, rel, jac);
-      return;
-    }
-  }
-  Vec<2> acc = {{0.0, 0.0}};
-  for (int i = t0; i < n; i += gs) {
-    const double ri = b[i] - spmv_row(A.sys.a, x, i, sy, sz, A.has_z);
-    r64[i] = ri;
-    r32[i] = to_f32(ri);
-    acc.v[0] += ri * ri;
-    acc.v[1] += b[i] * b[i];
-  }
+  Vec<2> acc;
+  acc.v[0] = ir_residual(A, t0, gs, r32, &acc.v[1]);
   // scalars formed by thread 0 of each block after each reduction
   __shared__ struct {
     double bnorm, rn, inv, rel, itol;
@@ -750,8 +811,10 @@ __device__ __forceinline__ void ir_solve(const BcgArgs& A, const Team& tm, unsig
         stage_scale();
       }))
     return;
-  int total = 0, ref = 0;
-  while (is.go && ref < kMaxRefine && total < A.max_it) {
+  int total = 0, jac = 0, ref = 0;
+  bool jacobi = A.jacobi != 0;
+  const float* dg = A.sys.af.idiag;
+  while (is.go && ref < kMaxRefine && total + jac < A.max_it) {
     ++ref;
     const double rn = is.rn;
     if (is.restage) {                             // |r| outside [2^-60, 2^60]: scale in FP64
@@ -760,18 +823,40 @@ __device__ __forceinline__ void ir_solve(const BcgArgs& A, const Team& tm, unsig
       if (!team_barrier(A.st, tm, epoch)) return;
     }
     CoreOut o;
-    const int cap = (A.max_it - total < kMaxInner) ? A.max_it - total : kMaxInner;
-    if (!bcg_fused(A.sys.af, n, sy, sz, A.has_z, A.d32, A.f32, is.sc, is.itol, cap, tm, A.max_blocks, A.st, epoch,
-                   o))
-      return;
-    if (o.it == 0) break;                         // the inner solve made no progress
-    total += o.it;
-    // x += rn d, r -= rn A d, and the FP32 copy of the new r
-    const float* dg = A.sys.af.idiag;
+    const int left = A.max_it - total - jac;
+    const int cap = left < kMaxInner ? left : kMaxInner;
+    const float* d = A.d32;
+    if (jacobi) {
+      if (!jac_fused(A.sys.af, n, sy, sz, A.has_z, A.d32, A.f32, is.sc, is.itol, cap, tm, A.max_blocks, A.st,
+                     epoch, o))
+        return;
+      jac += o.it;
+      d = o.p;
+      if (o.half) jacobi = false;                 // the sweeps stalled: BiCGSTAB from the next sweep on
+      // x += rn d
+      for (int i = t0; i < n; i += gs) x[i] = fma(rn, (double)d[i], x[i]);
+    } else {
+      if (!bcg_fused(A.sys.af, n, sy, sz, A.has_z, A.d32, A.f32, is.sc, is.itol, cap, tm, A.max_blocks, A.st,
+                     epoch, o))
+        return;
+      if (o.it == 0) break;                       // the inner solve made no progress
+      total += o.it;
+      // x += rn d, d completed by the half step's update where it stopped there
+      if (!o.half) {
+        for (int i = t0; i < n; i += gs) x[i] = fma(rn, (double)d[i], x[i]);
+      } else {
+        const float al = o.al;
+        const float* pp = o.p;
+        const bool first = o.it == 1;             // d was not written on the first iteration
+        for (int i = t0; i < n; i += gs) {
+          const float y = __ldg(dg + i) * pp[i];
+          x[i] = fma(rn, (double)(first ? al * y : fmaf(al, y, d[i])), x[i]);
+        }
+      }
+    }
+    if (!team_barrier(A.st, tm, epoch)) return;
     Vec<1> s1;
-    if (!o.half) s1.v[0] = ir_update(A, DCorr<0>{A.d32, dg, o.p, o.al}, rn, t0, gs, r32);
-    else if (o.it == 1) s1.v[0] = ir_update(A, DCorr<1>{A.d32, dg, o.p, o.al}, rn, t0, gs, r32);
-    else s1.v[0] = ir_update(A, DCorr<2>{A.d32, dg, o.p, o.al}, rn, t0, gs, r32);
+    s1.v[0] = ir_residual(A, t0, gs, r32, nullptr);
     if (!team_sum_post<1>(s1, tm, A.max_blocks, 15, A.st, epoch, [&](const double* tot) {
           is.rn = sqrt(tot[0]);
           is.inv = 1.0 / is.rn;
