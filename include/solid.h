@@ -388,6 +388,19 @@ ss_status ss_batch_destroy(ss_batch* b);
 ss_status ss_set_wait_limit(ss_case* c, long long polls);
 ss_status ss_wait_selftest(ss_case* c);
 
+/* ---- Tensor-core GEMM self-test.
+ *
+ * The cosine transforms of the FP32 transform solvers (SS_PRECOND_DCT in
+ * SS_MIXED, and the T* pre-solve) are dense products; their tiles run on the
+ * tcgen05 tensor cores as three TF32 products per K step (hi*hi + hi*lo +
+ * lo*hi of a TF32 split of each FP32 operand), accumulated in FP32.
+ * ss_tc_selftest(c, a, b, d, n, k) enqueues one block that forms
+ * d = a b^T by that path on the case's stream: a is 128 x k, b is n x k and
+ * d is 128 x n, FP32, row-major, device pointers (n a multiple of 16 in
+ * [16, 256]; 1 <= k <= 4096; SS_EINVAL otherwise). A wait that runs out
+ * sets the case's sticky timeout (reported by the next ss_sync). */
+ss_status ss_tc_selftest(ss_case* c, const float* a, const float* b, float* d, int n, int k);
+
 /* ---- Pressure-correction solve that allocates nothing.
  *
  * The paper has no counterpart to this call; it exists for callers that

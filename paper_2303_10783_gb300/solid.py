@@ -107,6 +107,7 @@ def _declare(lib):
         "ss_batch_destroy": [P],
         "ss_set_wait_limit": [P, ctypes.c_longlong],
         "ss_wait_selftest": [P],
+        "ss_tc_selftest": [P, P, P, P, ctypes.c_int, ctypes.c_int],
         "ss_poisson_solve_noalloc": [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                      ctypes.c_double, ctypes.c_double, P, P, ctypes.c_double, ctypes.c_int,
                                      ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double), P],
@@ -215,6 +216,11 @@ class Case:
     def wait_selftest(self):
         """Enqueue a wait that nothing completes; the next sync reports SS_ETIMEOUT."""
         check(self.lib.ss_wait_selftest(self.h))
+
+    def tc_selftest(self, a_ptr, b_ptr, d_ptr, n, k):
+        """Enqueue d = a b^T (a: 128 x k, b: n x k, d: 128 x n; FP32 row-major
+        device pointers) on the tensor-core path of the transform solvers."""
+        check(self.lib.ss_tc_selftest(self.h, a_ptr, b_ptr, d_ptr, int(n), int(k)))
 
     def set_time(self, t):
         check(self.lib.ss_set_time(self.h, float(t)))
