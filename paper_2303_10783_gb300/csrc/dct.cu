@@ -40,6 +40,7 @@
 #include <vector>
 
 #include "solid_internal.cuh"
+#include "umma.cuh"
 
 namespace solid {
 namespace {
@@ -77,6 +78,8 @@ struct DctArgs {
   int warm;                 // start from the x in place (else from 0)
   int thomas_cols;          // columns per shared-memory chunk of the tridiagonal solves
   int slab_smem;            // 1: pass B keeps each slab in shared memory (FP32 slabs that fit)
+  int tc;                   // 1: the FP32 transforms of passes A and C run on the tensor cores
+  int tc_slab;              // 1: so do pass B's, with the slab's tridiagonal solves in shared memory
   // Helmholtz mode (the T* pre-solve): the transforms invert s0 I - L instead
   // of -L (no null space), s0 = shift, for the operator I/dt - alpha L
   double shift;
@@ -352,6 +355,46 @@ __host__ __device__ __forceinline__ size_t slab_smem_floats(int My, int Mt) {
   return (size_t)My * (Mt + 4) + (size_t)My * (My + 4) + 2 * (size_t)Mt * P;
 }
 
+// The tridiagonal solves along t of slab kx, one column ky per thread: Ts
+// holds the transformed slab [t][ky] (rows of P floats) and receives the
+// solution; Ps takes the eliminated super-diagonal.
+__device__ __forceinline__ void slab_thomas(const DctArgs<float>& A, int kx, float* Ts, float* Ps, int P) {
+  const int My = A.My, Mt = A.Mt;
+  const float at = A.at;
+  const float sx = A.lx[kx];
+  for (int c = threadIdx.x; c < My; c += blockDim.x) {
+    const float s = sx + A.ly[c] + (float)A.shift;
+    const bool singular = !A.helm && kx == 0 && c == 0;
+    const int m = singular ? Mt - 1 : Mt;
+    if (m <= 0) {
+      Ts[c] = 0.f;
+    } else {
+      float prev_c = 0.f, prev_y = 0.f;
+      for (int t = 0; t < m; ++t) {
+        const float nb = (float)((t > 0) + (t < Mt - 1));
+        const float d = fmaf(at, prev_c, fmaf(at, nb, s));
+        const float inv = 1.f / d;
+        prev_y = fmaf(at, prev_y, Ts[(size_t)t * P + c]) * inv;
+        prev_c = -at * inv;
+        Ts[(size_t)t * P + c] = prev_y;
+        Ps[(size_t)t * P + c] = prev_c;
+      }
+      float next = 0.f;
+      if (singular) Ts[(size_t)(Mt - 1) * P + c] = 0.f;
+      for (int t = m - 1; t >= 0; --t) {
+        next = Ts[(size_t)t * P + c] - Ps[(size_t)t * P + c] * next;
+        Ts[(size_t)t * P + c] = next;
+      }
+      if (singular) {
+        float sum = 0.f;
+        for (int t = 0; t < Mt; ++t) sum += Ts[(size_t)t * P + c];
+        const float mean = sum / (float)Mt;
+        for (int t = 0; t < Mt; ++t) Ts[(size_t)t * P + c] -= mean;
+      }
+    }
+  }
+}
+
 // Pass B with the whole slab in shared memory (FP32, 3D): the transform along
 // y, the tridiagonal solves along t and the inverse transform never wait on
 // global memory between their steps.
@@ -363,7 +406,6 @@ __device__ void pass_b_slab(const DctArgs<float>& A, const Team& tm, float* sm) 
   float* Cs = Xs + (size_t)My * LX;               // [My][LC]: Cy transposed (GEMM 1), then Cy (GEMM 2)
   float* Ts = Cs + (size_t)My * LC;               // [Mt][P]: transformed slab, ky fastest
   float* Ps = Ts + (size_t)Mt * P;                // [Mt][P]: c' of the tridiagonal solves
-  const float at = A.at;
   for (int kx = tm.rank; kx < Mx; kx += tm.size) {
     float* S1 = A.T1 + (size_t)kx * R;            // [t][j] in global memory
     for (int e = threadIdx.x; e < My * Mt; e += blockDim.x) {
@@ -382,39 +424,7 @@ __device__ void pass_b_slab(const DctArgs<float>& A, const Team& tm, float* sm) 
       const int ky = e / My, j = e - ky * My;
       Cs[(size_t)ky * LC + j] = A.Cy[e];          // Cy: k-major for GEMM 2
     }
-    // tridiagonal solves along t, one column ky per thread
-    const float sx = A.lx[kx];
-    for (int c = threadIdx.x; c < My; c += blockDim.x) {
-      const float s = sx + A.ly[c] + (float)A.shift;
-      const bool singular = !A.helm && kx == 0 && c == 0;
-      const int m = singular ? Mt - 1 : Mt;
-      if (m <= 0) {
-        Ts[c] = 0.f;
-      } else {
-        float prev_c = 0.f, prev_y = 0.f;
-        for (int t = 0; t < m; ++t) {
-          const float nb = (float)((t > 0) + (t < Mt - 1));
-          const float d = fmaf(at, prev_c, fmaf(at, nb, s));
-          const float inv = 1.f / d;
-          prev_y = fmaf(at, prev_y, Ts[(size_t)t * P + c]) * inv;
-          prev_c = -at * inv;
-          Ts[(size_t)t * P + c] = prev_y;
-          Ps[(size_t)t * P + c] = prev_c;
-        }
-        float next = 0.f;
-        if (singular) Ts[(size_t)(Mt - 1) * P + c] = 0.f;
-        for (int t = m - 1; t >= 0; --t) {
-          next = Ts[(size_t)t * P + c] - Ps[(size_t)t * P + c] * next;
-          Ts[(size_t)t * P + c] = next;
-        }
-        if (singular) {
-          float sum = 0.f;
-          for (int t = 0; t < Mt; ++t) sum += Ts[(size_t)t * P + c];
-          const float mean = sum / (float)Mt;
-          for (int t = 0; t < Mt; ++t) Ts[(size_t)t * P + c] -= mean;
-        }
-      }
-    }
+    slab_thomas(A, kx, Ts, Ps, P);
     __syncthreads();
     for (int e = threadIdx.x; e < My * Mt; e += blockDim.x) {
       const int ky = e / Mt, t = e - ky * Mt;
@@ -425,6 +435,137 @@ __device__ void pass_b_slab(const DctArgs<float>& A, const Team& tm, float* sm) 
     smem_gemm(My, Mt, My, Cs, LC, Xs, LX, [&](int j, int t, float v) { S1[(size_t)t * My + j] = v; });
     __syncthreads();
   }
+}
+
+// ---- The FP32 transforms on the tensor cores (umma.cuh): the same products
+// as gemm_tile and smem_gemm, as 128-row accumulator tiles in TMEM.
+constexpr int kTcKc = 32;   // K chunk staged per round of MMAs
+
+// Floats of shared memory one tensor-core tile of width w stages.
+__host__ __device__ constexpr size_t tc_stage_floats(int w) { return 2 * (size_t)(kTcM + w) * kTcKc; }
+
+// Accumulator width (a multiple of 16, at most kTcCols) for an output of
+// `extent` columns by `row_tiles` tiles of 128 rows on a team of `blocks`:
+// the fewest rounds of tiles per block, then the least staging per round
+// (each tile stages its 128 x K operand and its w x K one).
+__device__ __forceinline__ int tc_width(int extent, int row_tiles, int blocks) {
+  int best = 16;
+  long long best_cost = -1;
+  const int top = ((extent + 15) & ~15) < kTcCols ? ((extent + 15) & ~15) : kTcCols;
+  for (int w = top; w >= 16; w -= 16) {
+    const long long tiles = (long long)row_tiles * ((extent + w - 1) / w);
+    const long long rounds = (tiles + blocks - 1) / blocks;
+    const long long cost = rounds * (kTcM + w);
+    if (best_cost < 0 || cost < best_cost) {
+      best_cost = cost;
+      best = w;
+    }
+  }
+  return best;
+}
+
+// Pass A: T1[m][n] = sum_k Cx[m][k] (rs[n][k] sc + off), as D[n][m]: rows
+// are 128 lines n, columns the modes m of the tile.
+__device__ bool pass_a_tc(const DctArgs<float>& A, const Team& tm, float sc, float off, float* sm, TcState& tc) {
+  const int Mx = A.Mx, R = A.R;
+  const int lt = (R + kTcM - 1) / kTcM;
+  const int w = tc_width(Mx, lt, tm.size);
+  const int mt = (Mx + w - 1) / w;
+  const float* Cx = A.Cx;
+  const float* rs = A.T2;
+  float* T1 = A.T1;
+  for (int tile = tm.rank; tile < lt * mt; tile += tm.size) {
+    const int n0 = (tile % lt) * kTcM, m0 = (tile / lt) * w;
+    if (!tc_gemm(
+            tc, w, Mx, kTcKc,
+            [&](int r, int k) {
+              const int n = n0 + r;
+              return (n < R && k < Mx) ? fmaf(rs[(size_t)n * Mx + k], sc, off) : 0.f;
+            },
+            false,
+            [&](int m, int k) {
+              const int mm = m0 + m;
+              return (mm < Mx && k < Mx) ? Cx[(size_t)mm * Mx + k] : 0.f;
+            },
+            false, sm, A.st))
+      return false;
+    tc_store(tc, w, [&](int r, int c, float v) {
+      const int n = n0 + r, m = m0 + c;
+      if (n < R && m < Mx) T1[(size_t)m * R + n] = v;
+    });
+  }
+  return true;
+}
+
+// Pass C: x[n][i] += rn sum_m Cx[m][i] T1[m][n], as D[i][n]: rows are 128
+// points i along x, columns the lines n of the tile.
+__device__ bool pass_c_tc(const DctArgs<float>& A, const Team& tm, double rn, float* sm, TcState& tc) {
+  const int Mx = A.Mx, R = A.R;
+  const int xt = (Mx + kTcM - 1) / kTcM;
+  const int w = tc_width(R, xt, tm.size);
+  const int nt = (R + w - 1) / w;
+  const float* Cx = A.Cx;
+  const float* T1 = A.T1;
+  double* x = A.x;
+  for (int tile = tm.rank; tile < xt * nt; tile += tm.size) {
+    const int i0 = (tile % xt) * kTcM, n0 = (tile / xt) * w;
+    if (!tc_gemm(
+            tc, w, Mx, kTcKc,
+            [&](int r, int m) {
+              const int i = i0 + r;
+              return (i < Mx && m < Mx) ? Cx[(size_t)m * Mx + i] : 0.f;
+            },
+            true,
+            [&](int c, int m) {
+              const int n = n0 + c;
+              return (n < R && m < Mx) ? T1[(size_t)m * R + n] : 0.f;
+            },
+            true, sm, A.st))
+      return false;
+    tc_store(tc, w, [&](int r, int c, float v) {
+      const int i = i0 + r, n = n0 + c;
+      if (i < Mx && n < R) {
+        const size_t q = (size_t)n * Mx + i;
+        x[q] = fma(rn, widen(v), x[q]);
+      }
+    });
+  }
+  return true;
+}
+
+// Pass B (3D, My <= 128, Mt <= 256) with the transforms along y on the
+// tensor cores: per mode kx, Ts[t][ky] = sum_j Cy[ky][j] S[t][j] (rows ky),
+// the tridiagonal solves along t in shared memory, then
+// S[t][j] = sum_ky Cy[ky][j] Ts[t][ky] (rows j) back into T1.
+__device__ bool pass_b_tc(const DctArgs<float>& A, const Team& tm, float* sm, TcState& tc) {
+  const int Mx = A.Mx, My = A.My, Mt = A.Mt, R = A.R;
+  const int P = My | 1;
+  const int w = (Mt + 15) & ~15;
+  float* Ts = sm + tc_stage_floats(w);   // [Mt][P]
+  float* Ps = Ts + (size_t)Mt * P;       // [Mt][P]
+  const float* Cy = A.Cy;
+  for (int kx = tm.rank; kx < Mx; kx += tm.size) {
+    float* S1 = A.T1 + (size_t)kx * R;   // [t][j]
+    if (!tc_gemm(
+            tc, w, My, kTcKc, [&](int ky, int j) { return (ky < My && j < My) ? Cy[(size_t)ky * My + j] : 0.f; },
+            false, [&](int t, int j) { return (t < Mt && j < My) ? S1[(size_t)t * My + j] : 0.f; }, false, sm,
+            A.st))
+      return false;
+    tc_store(tc, w, [&](int ky, int t, float v) {
+      if (ky < My && t < Mt) Ts[(size_t)t * P + ky] = v;
+    });
+    slab_thomas(A, kx, Ts, Ps, P);
+    __syncthreads();
+    if (!tc_gemm(
+            tc, w, My, kTcKc, [&](int j, int ky) { return (j < My && ky < My) ? Cy[(size_t)ky * My + j] : 0.f; },
+            true, [&](int t, int ky) { return (t < Mt && ky < My) ? Ts[(size_t)t * P + ky] : 0.f; }, false, sm,
+            A.st))
+      return false;
+    tc_store(tc, w, [&](int j, int t, float v) {
+      if (j < My && t < Mt) S1[(size_t)t * My + j] = v;
+    });
+  }
+  return true;
 }
 
 template <typename TP>
@@ -503,10 +644,40 @@ __device__ void pass_c(const DctArgs<TP>& A, const Team& tm, double rn, TP* sm) 
   }
 }
 
+// The passes on the tensor cores where the kernel opened them (tc not null;
+// FP32 only), else on the FP32 / FP64 pipes. False if a wait ran out.
+template <typename TP>
+__device__ __forceinline__ bool run_pass_a(const DctArgs<TP>& A, const Team& tm, TP sc, TP off, TP* sm,
+                                           TcState* tc) {
+  if constexpr (sizeof(TP) == 4) {
+    if (tc) return pass_a_tc(A, tm, sc, off, sm, *tc);
+  }
+  pass_a<TP>(A, tm, sc, off, sm);
+  return true;
+}
+
+template <typename TP>
+__device__ __forceinline__ bool run_pass_b(const DctArgs<TP>& A, const Team& tm, TP* sm, TcState* tc) {
+  if constexpr (sizeof(TP) == 4) {
+    if (tc && A.tc_slab) return pass_b_tc(A, tm, sm, *tc);
+  }
+  pass_b<TP>(A, tm, sm);
+  return true;
+}
+
+template <typename TP>
+__device__ __forceinline__ bool run_pass_c(const DctArgs<TP>& A, const Team& tm, double rn, TP* sm, TcState* tc) {
+  if constexpr (sizeof(TP) == 4) {
+    if (tc) return pass_c_tc(A, tm, rn, sm, *tc);
+  }
+  pass_c<TP>(A, tm, rn, sm);
+  return true;
+}
+
 // The whole solve by one team of blocks (a whole grid is one team); sm is the
 // block's dynamic shared memory. Returns false if a barrier gave up.
 template <typename TP>
-__device__ bool poisson_dct_team(const DctArgs<TP>& A, const Team& tm, TP* sm) {
+__device__ bool poisson_dct_team(const DctArgs<TP>& A, const Team& tm, TP* sm, TcState* tc) {
   __shared__ double s_diag[27];
   if (threadIdx.x < 27) {
     const int c = threadIdx.x;
@@ -590,11 +761,11 @@ __device__ bool poisson_dct_team(const DctArgs<TP>& A, const Team& tm, TP* sm) {
     ++sweeps;
     const double rn = ds.rn;
     ps = ds.pscale;
-    pass_a<TP>(A, tm, (TP)ds.sc, (TP)ds.off, sm);
+    if (!run_pass_a<TP>(A, tm, (TP)ds.sc, (TP)ds.off, sm, tc)) return false;
     if (!team_barrier(A.st, tm, epoch)) return false;
-    pass_b<TP>(A, tm, sm);
+    if (!run_pass_b<TP>(A, tm, sm, tc)) return false;
     if (!team_barrier(A.st, tm, epoch)) return false;
-    pass_c<TP>(A, tm, rn, sm);
+    if (!run_pass_c<TP>(A, tm, rn, sm, tc)) return false;
     if (!team_barrier(A.st, tm, epoch)) return false;
     Vec<2> s = {{0.0, 0.0}};
     for (int c = t0; c < n; c += gsz) {
@@ -706,7 +877,7 @@ __device__ __forceinline__ double spmv64(const Planes<double>& a, const double* 
 // continues from x. The sweeps are counted in the status block's pre-solve
 // counter. x holds the initial guess.
 __device__ bool helmholtz_team(const DctArgs<float>& A, const Sys& S, int has_z, double inv_alpha, int max_sweeps,
-                               const Team& tm, float* sm) {
+                               const Team& tm, float* sm, TcState* tc) {
   unsigned int epoch = 0;
   const int n = (int)S.d.n;
   const int sy = S.d.mx, sz = S.d.mx * S.d.my;
@@ -745,11 +916,11 @@ __device__ bool helmholtz_team(const DctArgs<float>& A, const Sys& S, int has_z,
   while (hs.go && sweeps < max_sweeps) {
     ++sweeps;
     const double rn = hs.rn;
-    pass_a<float>(A, tm, (float)hs.sc, 0.f, sm);
+    if (!run_pass_a<float>(A, tm, (float)hs.sc, 0.f, sm, tc)) return false;
     if (!team_barrier(A.st, tm, epoch)) return false;
-    pass_b<float>(A, tm, sm);
+    if (!run_pass_b<float>(A, tm, sm, tc)) return false;
     if (!team_barrier(A.st, tm, epoch)) return false;
-    pass_c<float>(A, tm, rn * inv_alpha, sm);
+    if (!run_pass_c<float>(A, tm, rn * inv_alpha, sm, tc)) return false;
     if (!team_barrier(A.st, tm, epoch)) return false;
     ps = hs.pscale;
     Vec<1> s1 = {{0.0}};
@@ -786,10 +957,28 @@ struct HelmArgs {
   int max_sweeps;
 };
 
+// Runs f(tc) with the block's tensor cores opened (TMEM allocated, closed
+// again on every way out) when on, else f(nullptr).
+template <class F>
+__device__ __forceinline__ void with_tc(bool on, F f) {
+  __shared__ uint32_t s_tmem;
+  __shared__ __align__(8) unsigned long long s_mbar;
+  if (on) {
+    TcState tc;
+    tc_open(tc, &s_tmem, &s_mbar);
+    f(&tc);
+    tc_close(tc);
+  } else {
+    f(nullptr);
+  }
+}
+
 __global__ void __launch_bounds__(kBlock, 1) k_helmholtz_dct(HelmArgs H) {
   extern __shared__ __align__(16) unsigned char dsm[];
   const Team tm{(int)blockIdx.x, (int)gridDim.x, &H.dct.st->barrier, H.dct.partial};
-  helmholtz_team(H.dct, H.sys, H.has_z, H.inv_alpha, H.max_sweeps, tm, reinterpret_cast<float*>(dsm));
+  with_tc(H.dct.tc != 0, [&](TcState* tc) {
+    helmholtz_team(H.dct, H.sys, H.has_z, H.inv_alpha, H.max_sweeps, tm, reinterpret_cast<float*>(dsm), tc);
+  });
 }
 
 // The T* pre-solve of a packed batch: team q runs case q's sweeps (none
@@ -815,21 +1004,27 @@ __global__ void __launch_bounds__(kBlock, 1) k_helmholtz_dct_packed(const HelmAr
   const HelmArgs& H = *reinterpret_cast<const HelmArgs*>(buf);
   if (H.max_sweeps <= 0) return;
   const Team tm{(int)blockIdx.x - first[q], first[q + 1] - first[q], &H.dct.st->barrier, H.dct.partial};
-  helmholtz_team(H.dct, H.sys, H.has_z, H.inv_alpha, H.max_sweeps, tm, reinterpret_cast<float*>(dsm));
+  with_tc(H.dct.tc != 0, [&](TcState* tc) {
+    helmholtz_team(H.dct, H.sys, H.has_z, H.inv_alpha, H.max_sweeps, tm, reinterpret_cast<float*>(dsm), tc);
+  });
 }
 
 template <typename TP>
 __global__ void __launch_bounds__(kBlock, 1) k_poisson_dct(DctArgs<TP> A) {
   extern __shared__ __align__(16) unsigned char dsm[];
   const Team tm{(int)blockIdx.x, (int)gridDim.x, &A.st->barrier, A.partial};
-  poisson_dct_team<TP>(A, tm, reinterpret_cast<TP*>(dsm));
+  if constexpr (sizeof(TP) == 4) {
+    with_tc(A.tc != 0, [&](TcState* tc) { poisson_dct_team<TP>(A, tm, reinterpret_cast<TP*>(dsm), tc); });
+  } else {
+    poisson_dct_team<TP>(A, tm, reinterpret_cast<TP*>(dsm), nullptr);
+  }
 }
 
 // Shared memory a block may give the slab-resident pass B.
 constexpr size_t kSlabSmemBytes = 200 * 1024;
 
 template <typename TP>
-size_t smem_bytes(const DctPlan& pl, int* cols, int* slab) {
+size_t smem_bytes(const DctPlan& pl, int* cols, int* slab, int* tc, int* tc_slab) {
   const int P = (pl.Mt & 1) ? pl.Mt : pl.Mt + 1;
   const int ncols = pl.dim == 3 ? pl.My : pl.Mx;
   long long w = (long long)(kThomasSmemBytes / (2 * (size_t)P * sizeof(TP)));
@@ -843,6 +1038,22 @@ size_t smem_bytes(const DctPlan& pl, int* cols, int* slab) {
   const size_t slab_bytes = slab_smem_floats(pl.My, pl.Mt) * sizeof(float);
   *slab = sizeof(TP) == 4 && pl.dim == 3 && slab_bytes <= kSlabSmemBytes;
   if (*slab && slab_bytes > need) need = slab_bytes;
+  // the tensor-core passes (FP32): tiles of width up to kTcCols in A and C;
+  // in B the slab's accumulator width, its transformed slab and the
+  // eliminated super-diagonal
+  *tc = sizeof(TP) == 4;
+  *tc_slab = 0;
+  if (*tc) {
+    const size_t ac = tc_stage_floats(kTcCols) * sizeof(float);
+    if (ac > need) need = ac;
+    const int wt = (pl.Mt + 15) & ~15;
+    const size_t b = (tc_stage_floats(wt) + 2 * (size_t)pl.Mt * (pl.My | 1)) * sizeof(float);
+    if (pl.dim == 3 && pl.My <= kTcM && wt <= kTcCols && b <= kSlabSmemBytes) {
+      *tc_slab = 1;
+      *slab = 0;
+      if (b > need) need = b;
+    }
+  }
   return need;
 }
 
@@ -869,7 +1080,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_poisson_dct_packed(const DctArgs<
   __syncthreads();
   const DctArgs<float>& A = *reinterpret_cast<const DctArgs<float>*>(buf);
   const Team tm{(int)blockIdx.x - first[q], first[q + 1] - first[q], &A.st->barrier, A.partial};
-  poisson_dct_team<float>(A, tm, reinterpret_cast<float*>(dsm));
+  with_tc(A.tc != 0, [&](TcState* tc) { poisson_dct_team<float>(A, tm, reinterpret_cast<float*>(dsm), tc); });
 }
 
 // The arguments of one solve; returns the dynamic shared memory it needs.
@@ -912,7 +1123,7 @@ size_t make_args(DctArgs<TP>& A, const DctPlan& pl, const Params& pr, double* b,
   A.partial = sc.partial;
   A.max_blocks = sc.max_blocks;
   A.st = st;
-  return smem_bytes<TP>(pl, &A.thomas_cols, &A.slab_smem);
+  return smem_bytes<TP>(pl, &A.thomas_cols, &A.slab_smem, &A.tc, &A.tc_slab);
 }
 
 template <typename TP>
