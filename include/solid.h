@@ -394,12 +394,14 @@ ss_status ss_wait_selftest(ss_case* c);
  * SS_MIXED, and the T* pre-solve) are dense products; their tiles run on the
  * tcgen05 tensor cores as three TF32 products per K step (hi*hi + hi*lo +
  * lo*hi of a TF32 split of each FP32 operand), accumulated in FP32.
- * ss_tc_selftest(c, a, b, d, n, k) enqueues one block that forms
+ * ss_tc_selftest(c, a, b, d, n, k, transposed) enqueues one block that forms
  * d = a b^T by that path on the case's stream: a is 128 x k, b is n x k and
- * d is 128 x n, FP32, row-major, device pointers (n a multiple of 16 in
- * [16, 256]; 1 <= k <= 4096; SS_EINVAL otherwise). A wait that runs out
- * sets the case's sticky timeout (reported by the next ss_sync). */
-ss_status ss_tc_selftest(ss_case* c, const float* a, const float* b, float* d, int n, int k);
+ * d is 128 x n, FP32 device pointers, row-major; with transposed != 0, a and
+ * b are stored transposed (k x 128 and k x n, row-major), the layout of the
+ * inverse transform's operands. n a multiple of 16 in [16, 256] and
+ * 1 <= k <= 4096, else SS_EINVAL. A wait that runs out sets the case's
+ * sticky timeout (reported by the next ss_sync). */
+ss_status ss_tc_selftest(ss_case* c, const float* a, const float* b, float* d, int n, int k, int transposed);
 
 /* ---- Pressure-correction solve that allocates nothing.
  *

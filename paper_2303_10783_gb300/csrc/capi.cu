@@ -1214,12 +1214,12 @@ ss_status ss_wait_selftest(ss_case* c) {
   return SS_OK;
 }
 
-ss_status ss_tc_selftest(ss_case* c, const float* a, const float* b, float* d, int n, int k) {
+ss_status ss_tc_selftest(ss_case* c, const float* a, const float* b, float* d, int n, int k, int transposed) {
   STAGE_TRY(check_case(c));
   if (!a || !b || !d) return fail(SS_EINVAL, "a, b and d must be device pointers");
   if (n < 16 || n > 256 || n % 16 != 0) return fail(SS_EINVAL, "n = %d: need a multiple of 16 in [16, 256]", n);
   if (k < 1 || k > 4096) return fail(SS_EINVAL, "k = %d: need 1 <= k <= 4096", k);
-  CUDA_TRY(launch_tc_selftest(a, b, d, n, k, c->st, c->stream));
+  CUDA_TRY(launch_tc_selftest(a, b, d, n, k, transposed ? 1 : 0, c->st, c->stream));
   return SS_OK;
 }
 

@@ -439,19 +439,16 @@ __device__ void pass_b_slab(const DctArgs<float>& A, const Team& tm, float* sm) 
 
 // ---- The FP32 transforms on the tensor cores (umma.cuh): the same products
 // as gemm_tile and smem_gemm, as 128-row accumulator tiles in TMEM.
-constexpr int kTcKc = 32;   // K chunk staged per round of MMAs
+constexpr int kTcMaxWidth = 128;   // accumulator width of passes A and C (two staging buffers: 133 KB)
 
-// Floats of shared memory one tensor-core tile of width w stages.
-__host__ __device__ constexpr size_t tc_stage_floats(int w) { return 2 * (size_t)(kTcM + w) * kTcKc; }
-
-// Accumulator width (a multiple of 16, at most kTcCols) for an output of
+// Accumulator width (a multiple of 16, at most kTcMaxWidth) for an output of
 // `extent` columns by `row_tiles` tiles of 128 rows on a team of `blocks`:
 // the fewest rounds of tiles per block, then the least staging per round
 // (each tile stages its 128 x K operand and its w x K one).
 __device__ __forceinline__ int tc_width(int extent, int row_tiles, int blocks) {
   int best = 16;
   long long best_cost = -1;
-  const int top = ((extent + 15) & ~15) < kTcCols ? ((extent + 15) & ~15) : kTcCols;
+  const int top = ((extent + 15) & ~15) < kTcMaxWidth ? ((extent + 15) & ~15) : kTcMaxWidth;
   for (int w = top; w >= 16; w -= 16) {
     const long long tiles = (long long)row_tiles * ((extent + w - 1) / w);
     const long long rounds = (tiles + blocks - 1) / blocks;
@@ -471,24 +468,12 @@ __device__ bool pass_a_tc(const DctArgs<float>& A, const Team& tm, float sc, flo
   const int lt = (R + kTcM - 1) / kTcM;
   const int w = tc_width(Mx, lt, tm.size);
   const int mt = (Mx + w - 1) / w;
-  const float* Cx = A.Cx;
-  const float* rs = A.T2;
   float* T1 = A.T1;
+  const TcOperand data{A.T2, Mx, 1, R, Mx, sc, off, 0};     // (line n, k) = rs[n Mx + k] sc + off
+  const TcOperand cx{A.Cx, Mx, 1, Mx, Mx, 1.f, 0.f, 0};     // (mode m, k) = Cx[m Mx + k]
   for (int tile = tm.rank; tile < lt * mt; tile += tm.size) {
     const int n0 = (tile % lt) * kTcM, m0 = (tile / lt) * w;
-    if (!tc_gemm(
-            tc, w, Mx, kTcKc,
-            [&](int r, int k) {
-              const int n = n0 + r;
-              return (n < R && k < Mx) ? fmaf(rs[(size_t)n * Mx + k], sc, off) : 0.f;
-            },
-            false,
-            [&](int m, int k) {
-              const int mm = m0 + m;
-              return (mm < Mx && k < Mx) ? Cx[(size_t)mm * Mx + k] : 0.f;
-            },
-            false, sm, A.st))
-      return false;
+    if (!tc_gemm(tc, w, Mx, data, n0, cx, m0, sm, A.st)) return false;
     tc_store(tc, w, [&](int r, int c, float v) {
       const int n = n0 + r, m = m0 + c;
       if (n < R && m < Mx) T1[(size_t)m * R + n] = v;
@@ -504,24 +489,12 @@ __device__ bool pass_c_tc(const DctArgs<float>& A, const Team& tm, double rn, fl
   const int xt = (Mx + kTcM - 1) / kTcM;
   const int w = tc_width(R, xt, tm.size);
   const int nt = (R + w - 1) / w;
-  const float* Cx = A.Cx;
-  const float* T1 = A.T1;
   double* x = A.x;
+  const TcOperand cxt{A.Cx, 1, Mx, Mx, Mx, 1.f, 0.f, 1};    // (point i, mode m) = Cx[m Mx + i]
+  const TcOperand t1{A.T1, 1, R, R, Mx, 1.f, 0.f, 1};       // (line n, mode m) = T1[m R + n]
   for (int tile = tm.rank; tile < xt * nt; tile += tm.size) {
     const int i0 = (tile % xt) * kTcM, n0 = (tile / xt) * w;
-    if (!tc_gemm(
-            tc, w, Mx, kTcKc,
-            [&](int r, int m) {
-              const int i = i0 + r;
-              return (i < Mx && m < Mx) ? Cx[(size_t)m * Mx + i] : 0.f;
-            },
-            true,
-            [&](int c, int m) {
-              const int n = n0 + c;
-              return (n < R && m < Mx) ? T1[(size_t)m * R + n] : 0.f;
-            },
-            true, sm, A.st))
-      return false;
+    if (!tc_gemm(tc, w, Mx, cxt, i0, t1, n0, sm, A.st)) return false;
     tc_store(tc, w, [&](int r, int c, float v) {
       const int i = i0 + r, n = n0 + c;
       if (i < Mx && n < R) {
@@ -533,34 +506,33 @@ __device__ bool pass_c_tc(const DctArgs<float>& A, const Team& tm, double rn, fl
   return true;
 }
 
+// Rows of the transformed slab of the tensor-core pass B: 16-byte aligned
+// (the staging loads read them four at a time).
+__host__ __device__ constexpr int tc_slab_row(int My) { return (My + 3) & ~3; }
+
 // Pass B (3D, My <= 128, Mt <= 256) with the transforms along y on the
 // tensor cores: per mode kx, Ts[t][ky] = sum_j Cy[ky][j] S[t][j] (rows ky),
 // the tridiagonal solves along t in shared memory, then
 // S[t][j] = sum_ky Cy[ky][j] Ts[t][ky] (rows j) back into T1.
 __device__ bool pass_b_tc(const DctArgs<float>& A, const Team& tm, float* sm, TcState& tc) {
   const int Mx = A.Mx, My = A.My, Mt = A.Mt, R = A.R;
-  const int P = My | 1;
+  const int P = tc_slab_row(My);
   const int w = (Mt + 15) & ~15;
-  float* Ts = sm + tc_stage_floats(w);   // [Mt][P]
-  float* Ps = Ts + (size_t)Mt * P;       // [Mt][P]
-  const float* Cy = A.Cy;
+  float* Ts = sm + tc_smem_bytes(w) / sizeof(float);   // [Mt][P]
+  float* Ps = Ts + (size_t)Mt * P;                       // [Mt][P]
+  const TcOperand cy{A.Cy, My, 1, My, My, 1.f, 0.f, 0};    // (ky, j) = Cy[ky My + j]
+  const TcOperand cyt{A.Cy, 1, My, My, My, 1.f, 0.f, 1};   // (j, ky) = Cy[ky My + j]
+  const TcOperand ts{Ts, P, 1, Mt, My, 1.f, 0.f, 0};       // (t, ky) = Ts[t P + ky]
   for (int kx = tm.rank; kx < Mx; kx += tm.size) {
     float* S1 = A.T1 + (size_t)kx * R;   // [t][j]
-    if (!tc_gemm(
-            tc, w, My, kTcKc, [&](int ky, int j) { return (ky < My && j < My) ? Cy[(size_t)ky * My + j] : 0.f; },
-            false, [&](int t, int j) { return (t < Mt && j < My) ? S1[(size_t)t * My + j] : 0.f; }, false, sm,
-            A.st))
-      return false;
+    const TcOperand slab{S1, My, 1, Mt, My, 1.f, 0.f, 0};  // (t, j) = S1[t My + j]
+    if (!tc_gemm(tc, w, My, cy, 0, slab, 0, sm, A.st)) return false;
     tc_store(tc, w, [&](int ky, int t, float v) {
       if (ky < My && t < Mt) Ts[(size_t)t * P + ky] = v;
     });
     slab_thomas(A, kx, Ts, Ps, P);
     __syncthreads();
-    if (!tc_gemm(
-            tc, w, My, kTcKc, [&](int j, int ky) { return (j < My && ky < My) ? Cy[(size_t)ky * My + j] : 0.f; },
-            true, [&](int t, int ky) { return (t < Mt && ky < My) ? Ts[(size_t)t * P + ky] : 0.f; }, false, sm,
-            A.st))
-      return false;
+    if (!tc_gemm(tc, w, My, cyt, 0, ts, 0, sm, A.st)) return false;
     tc_store(tc, w, [&](int j, int t, float v) {
       if (j < My && t < Mt) S1[(size_t)t * My + j] = v;
     });
@@ -962,10 +934,10 @@ struct HelmArgs {
 template <class F>
 __device__ __forceinline__ void with_tc(bool on, F f) {
   __shared__ uint32_t s_tmem;
-  __shared__ __align__(8) unsigned long long s_mbar;
+  __shared__ __align__(8) unsigned long long s_mbar[2];
   if (on) {
     TcState tc;
-    tc_open(tc, &s_tmem, &s_mbar);
+    tc_open(tc, &s_tmem, s_mbar);
     f(&tc);
     tc_close(tc);
   } else {
@@ -1044,10 +1016,10 @@ size_t smem_bytes(const DctPlan& pl, int* cols, int* slab, int* tc, int* tc_slab
   *tc = sizeof(TP) == 4;
   *tc_slab = 0;
   if (*tc) {
-    const size_t ac = tc_stage_floats(kTcCols) * sizeof(float);
+    const size_t ac = tc_smem_bytes(kTcMaxWidth);
     if (ac > need) need = ac;
     const int wt = (pl.Mt + 15) & ~15;
-    const size_t b = (tc_stage_floats(wt) + 2 * (size_t)pl.Mt * (pl.My | 1)) * sizeof(float);
+    const size_t b = tc_smem_bytes(wt) + 2 * (size_t)pl.Mt * tc_slab_row(pl.My) * sizeof(float);
     if (pl.dim == 3 && pl.My <= kTcM && wt <= kTcCols && b <= kSlabSmemBytes) {
       *tc_slab = 1;
       *slab = 0;

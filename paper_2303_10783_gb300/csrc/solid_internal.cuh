@@ -628,8 +628,9 @@ cudaError_t launch_poisson_dct(const DctPlan& pl, const Params& pr, double* b, d
 // transform inverse of I/dt - alpha L, at most max_sweeps sweeps, starting
 // from the x in place; the BiCGSTAB refinement follows it.
 // tcgemm.cu: one block forms D (128 x n) = A (128 x k) B (n x k)^T on the tensor cores
-cudaError_t launch_tc_selftest(const float* a, const float* b, float* d, int n, int k, DevStatus* st,
-                               cudaStream_t s);
+// (transposed: A and B stored k x 128 and k x n)
+cudaError_t launch_tc_selftest(const float* a, const float* b, float* d, int n, int k, int transposed,
+                               DevStatus* st, cudaStream_t s);
 cudaError_t launch_helmholtz_dct(const DctPlan& pl, const Params& pr, const Sys& sys, int has_z, int max_sweeps,
                                  const SolverCtl& ctl, Scratch& sc, DevStatus* st, cudaStream_t s);
 // the same for a packed batch, one team per case (max_sweeps = 0: none)

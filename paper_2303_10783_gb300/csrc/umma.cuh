@@ -8,9 +8,12 @@
 //
 // Layout: both operands K-major in the canonical no-swizzle form of the
 // shared-memory matrix descriptor: core matrices of 8 rows x 16 bytes
-// (4 FP32), the two core matrices of one K step of 8 next to each other
-// (leading byte offset 128), 8-row groups Kc/4 * 128 bytes apart (stride
-// byte offset) for a chunk of Kc values of K.
+// (4 FP32), the core matrices along K 128 bytes apart (leading byte offset),
+// so one K step of 8 is two adjacent core matrices, and 8-row groups
+// kTcSbo = 32 kTcKc + 16 bytes apart (stride byte offset) for a chunk of
+// kTcKc values of K. The extra 16 bytes put the rows of a group and the
+// groups on different shared-memory banks, so the 16-byte stores of the
+// staging threads are conflict-free.
 //
 // Accumulator: M = 128 rows, row i in TMEM lane i, column j in TMEM column
 // j (32-bit). Warp w reads lanes 32 (w % 4) .. 32 (w % 4) + 31.
@@ -28,6 +31,8 @@ namespace solid {
 
 constexpr int kTcM = 128;            // accumulator rows (one TMEM lane each)
 constexpr int kTcCols = 256;         // TMEM columns a block allocates (the widest accumulator)
+constexpr int kTcKc = 32;            // K values per staged chunk
+constexpr int kTcSbo = 32 * kTcKc + 16;   // bytes between 8-row groups of a chunk
 constexpr long long kTcWaitPolls = 1ll << 22;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -42,17 +47,17 @@ __device__ __forceinline__ float tf32_rn(float x) {
   return __uint_as_float(u & 0xFFFFE000u);
 }
 
-// byte offset of element (r, k) of a K-major operand chunk of Kc columns
-// (Kc a multiple of 8) in the canonical no-swizzle layout
-__device__ __forceinline__ uint32_t kmaj_off(int r, int k, int Kc) {
-  return (uint32_t)((r >> 3) * (Kc * 32) + (k >> 2) * 128 + (r & 7) * 16 + (k & 3) * 4);
+// byte offset of the 16-byte group k4 (values 4 k4 .. 4 k4 + 3) of row r of
+// a staged K-major chunk
+__device__ __forceinline__ uint32_t kmaj_off4(int r, int k4) {
+  return (uint32_t)((r >> 3) * kTcSbo + k4 * 128 + (r & 7) * 16);
 }
 
 // shared-memory matrix descriptor of a K-major chunk starting at saddr
 // (16-byte aligned): no swizzle, leading byte offset 128, stride byte
-// offset 32 Kc, descriptor version 1
-__device__ __forceinline__ uint64_t kmaj_desc(uint32_t saddr, int Kc) {
-  const uint64_t lbo = 128, sbo = 32ull * (uint64_t)Kc;
+// offset kTcSbo, descriptor version 1
+__device__ __forceinline__ uint64_t kmaj_desc(uint32_t saddr) {
+  const uint64_t lbo = 128, sbo = kTcSbo;
   return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((lbo >> 4) << 16) | ((sbo >> 4) << 32) | (1ull << 46);
 }
 
@@ -115,13 +120,15 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16]) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// The block's tensor-core state: its TMEM columns and the mbarrier the MMAs
-// complete on. Set up by tc_open (all threads) at the start of a kernel and
-// released by tc_close (all threads) at its end.
+
+// The block's tensor-core state: its TMEM columns and one mbarrier per
+// staging buffer (the MMAs of a chunk complete on its buffer's barrier).
+// Set up by tc_open (all threads) at the start of a kernel and released by
+// tc_close (all threads) at its end.
 struct TcState {
-  uint32_t tmem;      // TMEM address of column 0, lane 0
-  uint32_t mbar;      // shared address of the mbarrier
-  uint32_t phase;     // parity of the next phase to wait for
+  uint32_t tmem;       // TMEM address of column 0, lane 0
+  uint32_t mbar[2];    // shared addresses of the two mbarriers
+  uint32_t phase[2];   // parity of the next phase to wait for on each
 };
 
 __device__ __forceinline__ void tc_open(TcState& tc, uint32_t* s_tmem, unsigned long long* s_mbar) {
@@ -131,13 +138,17 @@ __device__ __forceinline__ void tc_open(TcState& tc, uint32_t* s_tmem, unsigned 
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
-  if (threadIdx.x == 32) mbar_init(smem_u32(s_mbar), 1);
+  if (threadIdx.x == 32) {
+    mbar_init(smem_u32(s_mbar), 1);
+    mbar_init(smem_u32(s_mbar + 1), 1);
+  }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   tc.tmem = *s_tmem;
-  tc.mbar = smem_u32(s_mbar);
-  tc.phase = 0;
+  tc.mbar[0] = smem_u32(s_mbar);
+  tc.mbar[1] = smem_u32(s_mbar + 1);
+  tc.phase[0] = tc.phase[1] = 0;
 }
 
 __device__ __forceinline__ void tc_close(const TcState& tc) {
@@ -150,45 +161,130 @@ __device__ __forceinline__ void tc_close(const TcState& tc) {
   }
 }
 
-// One accumulator tile: D[r][n] = sum_k A(r, k) B(n, k), r < 128, n < N
-// (N a multiple of 16, at most kTcCols), k < K. la(r, k) and lb(n, k) load
-// one FP32 operand value (0 outside the operand); a_rfast / b_rfast say
-// whether consecutive rows (else consecutive k) are adjacent in memory, and
-// the staging threads walk that index fastest. K is taken in chunks of Kc
-// (a multiple of 8); sm holds 2 (128 + N) Kc floats. The result stays in
-// TMEM columns [0, N). Returns false if a wait ran out (error flag set).
-template <class LA, class LB>
-__device__ bool tc_gemm(TcState& tc, int N, int K, int Kc, LA la, bool a_rfast, LB lb, bool b_rfast, float* sm,
-                        DevStatus* st) {
+// A GEMM operand in global or shared memory: element (r, k) at
+// p[r * rs + k * ks], the value p[..] * sc + off for r < rows and k < cols
+// and 0 elsewhere. rfast: consecutive rows are adjacent (rs = 1), else
+// consecutive k (ks = 1).
+struct TcOperand {
+  const float* p;
+  long long rs, ks;
+  int rows, cols;
+  float sc, off;
+  int rfast;
+};
+
+__device__ __forceinline__ float tc_elem(const TcOperand& o, int r, int k) {
+  return (r < o.rows && k < o.cols) ? fmaf(o.p[(long long)r * o.rs + (long long)k * o.ks], o.sc, o.off) : 0.f;
+}
+
+// 16-byte loads are possible when the pointer and the strided dimension
+// keep every group of four on a 16-byte boundary
+__device__ __forceinline__ bool tc_vec(const TcOperand& o) {
+  return ((reinterpret_cast<uintptr_t>(o.p) & 15) == 0) && (((o.rfast ? o.ks : o.rs) & 3) == 0);
+}
+
+// Splits four values into TF32 hi and lo and stores them as one 16-byte
+// group of the hi and lo chunks.
+__device__ __forceinline__ void tc_put4(unsigned char* hi, unsigned char* lo, uint32_t off, float4 v) {
+  float4 h, l;
+  h.x = tf32_rn(v.x); l.x = tf32_rn(v.x - h.x);
+  h.y = tf32_rn(v.y); l.y = tf32_rn(v.y - h.y);
+  h.z = tf32_rn(v.z); l.z = tf32_rn(v.z - h.z);
+  h.w = tf32_rn(v.w); l.w = tf32_rn(v.w - h.w);
+  *reinterpret_cast<float4*>(hi + off) = h;
+  *reinterpret_cast<float4*>(lo + off) = l;
+}
+
+// Stages rows [r0, r0 + nrows) (nrows a multiple of 16) and K values
+// [k0, k0 + kc) (kc a multiple of 8) of operand o as TF32 pairs. Each warp
+// takes blocks of 8 rows x 4 groups of four k (k-adjacent operands: a lane
+// loads one row's four k) or 32 rows x 4 groups (row-adjacent operands: a
+// lane loads four rows at each of four k and transposes them in registers).
+__device__ __forceinline__ void tc_stage(const TcOperand& o, int r0, int nrows, int k0, int kc, unsigned char* hi,
+                                         unsigned char* lo) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int nk4 = kc >> 2, kg = (nk4 + 3) >> 2;
+  const bool vec = tc_vec(o);
+  if (!o.rfast) {
+    const int nblk = (nrows >> 3) * kg;
+    for (int b = warp; b < nblk; b += nw) {
+      const int r = (b / kg) * 8 + (lane & 7);
+      const int k4 = (b % kg) * 4 + (lane >> 3);
+      if (k4 >= nk4) continue;
+      const int gr = r0 + r, gk = k0 + 4 * k4;
+      float4 v;
+      if (vec && gr < o.rows && gk + 3 < o.cols) {
+        v = *reinterpret_cast<const float4*>(o.p + (long long)gr * o.rs + gk);
+        v.x = fmaf(v.x, o.sc, o.off); v.y = fmaf(v.y, o.sc, o.off);
+        v.z = fmaf(v.z, o.sc, o.off); v.w = fmaf(v.w, o.sc, o.off);
+      } else {
+        v = make_float4(tc_elem(o, gr, gk), tc_elem(o, gr, gk + 1), tc_elem(o, gr, gk + 2), tc_elem(o, gr, gk + 3));
+      }
+      tc_put4(hi, lo, kmaj_off4(r, k4), v);
+    }
+  } else {
+    const int nblk = ((nrows + 31) >> 5) * kg;
+    for (int b = warp; b < nblk; b += nw) {
+      const int r = (b / kg) * 32 + (lane & 7) * 4;
+      const int k4 = (b % kg) * 4 + (lane >> 3);
+      if (k4 >= nk4 || r >= nrows) continue;
+      const int gr = r0 + r, gk = k0 + 4 * k4;
+      float4 c[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        if (vec && gr + 3 < o.rows && gk + q < o.cols) {
+          c[q] = *reinterpret_cast<const float4*>(o.p + gr + (long long)(gk + q) * o.ks);
+          c[q].x = fmaf(c[q].x, o.sc, o.off); c[q].y = fmaf(c[q].y, o.sc, o.off);
+          c[q].z = fmaf(c[q].z, o.sc, o.off); c[q].w = fmaf(c[q].w, o.sc, o.off);
+        } else {
+          c[q] = make_float4(tc_elem(o, gr, gk + q), tc_elem(o, gr + 1, gk + q), tc_elem(o, gr + 2, gk + q),
+                             tc_elem(o, gr + 3, gk + q));
+        }
+      }
+      tc_put4(hi, lo, kmaj_off4(r, k4), make_float4(c[0].x, c[1].x, c[2].x, c[3].x));
+      tc_put4(hi, lo, kmaj_off4(r + 1, k4), make_float4(c[0].y, c[1].y, c[2].y, c[3].y));
+      tc_put4(hi, lo, kmaj_off4(r + 2, k4), make_float4(c[0].z, c[1].z, c[2].z, c[3].z));
+      tc_put4(hi, lo, kmaj_off4(r + 3, k4), make_float4(c[0].w, c[1].w, c[2].w, c[3].w));
+    }
+  }
+}
+
+// Bytes of one staging buffer for an accumulator of width N: the hi and lo
+// chunks of A (128 rows) and of B (N rows).
+__host__ __device__ constexpr size_t tc_buffer_bytes(int N) { return 2 * (size_t)((kTcM + N) / 8) * kTcSbo; }
+// Bytes of shared memory tc_gemm uses: two buffers.
+__host__ __device__ constexpr size_t tc_smem_bytes(int N) { return 2 * tc_buffer_bytes(N); }
+
+// One accumulator tile: D[r][n] = sum_k A(a_r0 + r, k) B(b_r0 + n, k) for
+// r < 128, n < N (N a multiple of 16, at most kTcCols) and k < K. K goes in
+// chunks of kTcKc through two staging buffers, so that chunk c + 1 is staged
+// while the tensor cores multiply chunk c; sm holds tc_smem_bytes(N) bytes.
+// The result stays in TMEM columns [0, N). Returns false (error flag set)
+// if a wait ran out; the block then leaves together.
+__device__ inline bool tc_gemm(TcState& tc, int N, int K, const TcOperand& a, int a_r0, const TcOperand& b, int b_r0,
+                               float* sm, DevStatus* st) {
   unsigned char* base = reinterpret_cast<unsigned char*>(sm);
-  const uint32_t a_bytes = (uint32_t)kTcM * Kc * 4, b_bytes = (uint32_t)N * Kc * 4;
-  unsigned char* Ahi = base;
-  unsigned char* Alo = Ahi + a_bytes;
-  unsigned char* Bhi = Alo + a_bytes;
-  unsigned char* Blo = Bhi + b_bytes;
+  const uint32_t a_bytes = (uint32_t)(kTcM / 8) * kTcSbo, b_bytes = (uint32_t)(N / 8) * kTcSbo;
+  const uint32_t buf_bytes = 2 * (a_bytes + b_bytes);
   const uint32_t idesc = idesc_tf32(kTcM, N);
-  bool ok = true;
-  for (int k0 = 0; k0 < K; k0 += Kc) {
-    const int kc = (K - k0 < Kc) ? ((K - k0 + 7) & ~7) : Kc;   // the last chunk, padded to a K step
-    const int na = kTcM * kc, nb = N * kc;
-    for (int e = threadIdx.x; e < na; e += blockDim.x) {
-      const int r = a_rfast ? e % kTcM : e / kc;
-      const int k = a_rfast ? e / kTcM : e % kc;
-      const float v = la(r, k0 + k);
-      const float hi = tf32_rn(v);
-      const uint32_t o = kmaj_off(r, k, Kc);
-      *reinterpret_cast<float*>(Ahi + o) = hi;
-      *reinterpret_cast<float*>(Alo + o) = tf32_rn(v - hi);
-    }
-    for (int e = threadIdx.x; e < nb; e += blockDim.x) {
-      const int n = b_rfast ? e % N : e / kc;
-      const int k = b_rfast ? e / N : e % kc;
-      const float v = lb(n, k0 + k);
-      const float hi = tf32_rn(v);
-      const uint32_t o = kmaj_off(n, k, Kc);
-      *reinterpret_cast<float*>(Bhi + o) = hi;
-      *reinterpret_cast<float*>(Blo + o) = tf32_rn(v - hi);
-    }
+  const int nchunks = (K + kTcKc - 1) / kTcKc;
+  auto wait_buffer = [&](int q) {   // (selects, not indexing: TcState stays in registers)
+    const bool done = mbar_wait(q ? tc.mbar[1] : tc.mbar[0], q ? tc.phase[1] : tc.phase[0]);
+    if (q) tc.phase[1] ^= 1u; else tc.phase[0] ^= 1u;
+    if (!done) atomicExch(&st->err, kErrBarrier);
+    return !__syncthreads_or(!done);
+  };
+  for (int c = 0; c < nchunks; ++c) {
+    const int q = c & 1;
+    if (c >= 2 && !wait_buffer(q)) return false;   // buffer q was last read by chunk c - 2
+    unsigned char* Ahi = base + q * buf_bytes;
+    unsigned char* Alo = Ahi + a_bytes;
+    unsigned char* Bhi = Alo + a_bytes;
+    unsigned char* Blo = Bhi + b_bytes;
+    const int k0 = c * kTcKc;
+    const int kc = (K - k0 < kTcKc) ? ((K - k0 + 7) & ~7) : kTcKc;   // the last chunk, padded to a K step
+    tc_stage(a, a_r0, kTcM, k0, kc, Ahi, Alo);
+    tc_stage(b, b_r0, N, k0, kc, Bhi, Blo);
     fence_async_smem();
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -196,26 +292,21 @@ __device__ bool tc_gemm(TcState& tc, int N, int K, int Kc, LA la, bool a_rfast, 
       const uint32_t ah = smem_u32(Ahi), al = smem_u32(Alo), bh = smem_u32(Bhi), bl = smem_u32(Blo);
       for (int s = 0; s < kc / 8; ++s) {
         const uint32_t off = (uint32_t)s * 256;   // two core matrices of 128 bytes per K step
-        const uint64_t dah = kmaj_desc(ah + off, Kc), dal = kmaj_desc(al + off, Kc);
-        const uint64_t dbh = kmaj_desc(bh + off, Kc), dbl = kmaj_desc(bl + off, Kc);
-        umma_tf32(tc.tmem, dah, dbh, idesc, (k0 > 0 || s > 0) ? 1u : 0u);
+        const uint64_t dah = kmaj_desc(ah + off), dal = kmaj_desc(al + off);
+        const uint64_t dbh = kmaj_desc(bh + off), dbl = kmaj_desc(bl + off);
+        umma_tf32(tc.tmem, dah, dbh, idesc, (c > 0 || s > 0) ? 1u : 0u);
         umma_tf32(tc.tmem, dah, dbl, idesc, 1u);
         umma_tf32(tc.tmem, dal, dbh, idesc, 1u);
       }
-      umma_commit(tc.mbar);
-    }
-    // every thread waits: the chunk's shared memory is reused by the next
-    // chunk, and the accumulator is read after the last one
-    const bool done = mbar_wait(tc.mbar, tc.phase);
-    if (!done) atomicExch(&st->err, kErrBarrier);
-    tc.phase ^= 1u;
-    tc_fence_after();
-    if (__syncthreads_or(!done)) {   // the block leaves together
-      ok = false;
-      break;
+      umma_commit(q ? tc.mbar[1] : tc.mbar[0]);
     }
   }
-  return ok;
+  // the chunks not waited for yet: the accumulator is read next, and the
+  // next tile restages both buffers
+  for (int c = nchunks >= 2 ? nchunks - 2 : 0; c < nchunks; ++c)
+    if (!wait_buffer(c & 1)) return false;
+  tc_fence_after();
+  return true;
 }
 
 // Hands the accumulator's columns [0, N) to st(r, n, v), 16 columns per

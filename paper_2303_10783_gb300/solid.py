@@ -107,7 +107,7 @@ def _declare(lib):
         "ss_batch_destroy": [P],
         "ss_set_wait_limit": [P, ctypes.c_longlong],
         "ss_wait_selftest": [P],
-        "ss_tc_selftest": [P, P, P, P, ctypes.c_int, ctypes.c_int],
+        "ss_tc_selftest": [P, P, P, P, ctypes.c_int, ctypes.c_int, ctypes.c_int],
         "ss_poisson_solve_noalloc": [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                      ctypes.c_double, ctypes.c_double, P, P, ctypes.c_double, ctypes.c_int,
                                      ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double), P],
@@ -217,10 +217,11 @@ class Case:
         """Enqueue a wait that nothing completes; the next sync reports SS_ETIMEOUT."""
         check(self.lib.ss_wait_selftest(self.h))
 
-    def tc_selftest(self, a_ptr, b_ptr, d_ptr, n, k):
+    def tc_selftest(self, a_ptr, b_ptr, d_ptr, n, k, transposed=False):
         """Enqueue d = a b^T (a: 128 x k, b: n x k, d: 128 x n; FP32 row-major
-        device pointers) on the tensor-core path of the transform solvers."""
-        check(self.lib.ss_tc_selftest(self.h, a_ptr, b_ptr, d_ptr, int(n), int(k)))
+        device pointers, a and b stored transposed when asked) on the
+        tensor-core path of the transform solvers."""
+        check(self.lib.ss_tc_selftest(self.h, a_ptr, b_ptr, d_ptr, int(n), int(k), 1 if transposed else 0))
 
     def set_time(self, t):
         check(self.lib.ss_set_time(self.h, float(t)))
