@@ -222,6 +222,7 @@ void plan(ss_case* c, Planner& pl) {
     c->dct.T1 = mixed ? (void*)pl.vec<float>(c->n_cell) : (void*)pl.vec<double>(c->n_cell);
     c->dct.T2 = mixed ? (void*)pl.vec<float>(c->n_cell) : (void*)pl.vec<double>(c->n_cell);
     c->dct.tables = pl.raw<char>(dct_table_elems(c->dct) * esz);
+    c->dct.img = mixed ? pl.raw<char>(dct_image_bytes(c->dct)) : nullptr;
   }
   // Krylov scratch: set 0 serves every solve (multigrid included); sets 1, 2
   // serve the v* and w* teams of the joint momentum solve, with only the
@@ -865,6 +866,13 @@ ss_status ss_create_case(const ss_grid* grid, void* workspace, size_t workspace_
       bytes = tab32.size() * sizeof(float);
     }
     e = cudaMemcpyAsync(c->dct.tables, src, bytes, cudaMemcpyHostToDevice, c->stream);
+    std::vector<unsigned char> img;
+    if (e == cudaSuccess && c->dct.img) {
+      // the constant operands of the tensor-core transforms, staged once
+      img.resize(dct_image_bytes(c->dct));
+      dct_images(c->dct, tab32.data(), tab32.data() + (size_t)c->dct.Mx * c->dct.Mx, img.data());
+      e = cudaMemcpyAsync(c->dct.img, img.data(), img.size(), cudaMemcpyHostToDevice, c->stream);
+    }
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   }
   if (e != cudaSuccess) {

@@ -80,6 +80,9 @@ struct DctArgs {
   int slab_smem;            // 1: pass B keeps each slab in shared memory (FP32 slabs that fit)
   int tc;                   // 1: the FP32 transforms of passes A and C run on the tensor cores
   int tc_slab;              // 1: so do pass B's, with the slab's tridiagonal solves in shared memory
+  // the constant operands of the tensor-core passes in their staged layout
+  const unsigned char *img_cx, *img_cxt, *img_cy, *img_cyt;
+  int img_gx, img_gy;       // 8-row groups per half of a chunk of the x and y images
   // Helmholtz mode (the T* pre-solve): the transforms invert s0 I - L instead
   // of -L (no null space), s0 = shift, for the operator I/dt - alpha L
   double shift;
@@ -470,7 +473,7 @@ __device__ bool pass_a_tc(const DctArgs<float>& A, const Team& tm, float sc, flo
   const int mt = (Mx + w - 1) / w;
   float* T1 = A.T1;
   const TcOperand data{A.T2, Mx, 1, R, Mx, sc, off, 0};     // (line n, k) = rs[n Mx + k] sc + off
-  const TcOperand cx{A.Cx, Mx, 1, Mx, Mx, 1.f, 0.f, 0};     // (mode m, k) = Cx[m Mx + k]
+  const TcOperand cx{A.Cx, Mx, 1, Mx, Mx, 1.f, 0.f, 0, A.img_cx, A.img_gx};     // (mode m, k) = Cx[m Mx + k]
   for (int tile = tm.rank; tile < lt * mt; tile += tm.size) {
     const int n0 = (tile % lt) * kTcM, m0 = (tile / lt) * w;
     if (!tc_gemm(tc, w, Mx, data, n0, cx, m0, sm, A.st)) return false;
@@ -490,7 +493,7 @@ __device__ bool pass_c_tc(const DctArgs<float>& A, const Team& tm, double rn, fl
   const int w = tc_width(R, xt, tm.size);
   const int nt = (R + w - 1) / w;
   double* x = A.x;
-  const TcOperand cxt{A.Cx, 1, Mx, Mx, Mx, 1.f, 0.f, 1};    // (point i, mode m) = Cx[m Mx + i]
+  const TcOperand cxt{A.Cx, 1, Mx, Mx, Mx, 1.f, 0.f, 1, A.img_cxt, A.img_gx};   // (point i, mode m) = Cx[m Mx + i]
   const TcOperand t1{A.T1, 1, R, R, Mx, 1.f, 0.f, 1};       // (line n, mode m) = T1[m R + n]
   for (int tile = tm.rank; tile < xt * nt; tile += tm.size) {
     const int i0 = (tile % xt) * kTcM, n0 = (tile / xt) * w;
@@ -520,8 +523,8 @@ __device__ bool pass_b_tc(const DctArgs<float>& A, const Team& tm, float* sm, Tc
   const int w = (Mt + 15) & ~15;
   float* Ts = sm + tc_smem_bytes(w) / sizeof(float);   // [Mt][P]
   float* Ps = Ts + (size_t)Mt * P;                       // [Mt][P]
-  const TcOperand cy{A.Cy, My, 1, My, My, 1.f, 0.f, 0};    // (ky, j) = Cy[ky My + j]
-  const TcOperand cyt{A.Cy, 1, My, My, My, 1.f, 0.f, 1};   // (j, ky) = Cy[ky My + j]
+  const TcOperand cy{A.Cy, My, 1, My, My, 1.f, 0.f, 0, A.img_cy, A.img_gy};    // (ky, j) = Cy[ky My + j]
+  const TcOperand cyt{A.Cy, 1, My, My, My, 1.f, 0.f, 1, A.img_cyt, A.img_gy};  // (j, ky) = Cy[ky My + j]
   const TcOperand ts{Ts, P, 1, Mt, My, 1.f, 0.f, 0};       // (t, ky) = Ts[t P + ky]
   for (int kx = tm.rank; kx < Mx; kx += tm.size) {
     float* S1 = A.T1 + (size_t)kx * R;   // [t][j]
@@ -992,6 +995,48 @@ __global__ void __launch_bounds__(kBlock, 1) k_poisson_dct(DctArgs<TP> A) {
   }
 }
 
+// Rows of a staged image of an n x n matrix: whole tiles of 128 rows plus
+// one more, so that any tile of rows the passes stage lies inside it (the
+// rows beyond n are zero).
+size_t tc_image_rows(int n) { return (size_t)((n + kTcM - 1) / kTcM) * kTcM + kTcM; }
+
+// Bytes of that image: per chunk of kTcKc values of K, the hi and the lo half.
+size_t tc_image_bytes(int n) {
+  const size_t chunks = (size_t)(n + kTcKc - 1) / kTcKc;
+  return chunks * 2 * (tc_image_rows(n) / 8) * kTcSbo;
+}
+
+// FP32 -> TF32, round to nearest, ties to even (the device's tf32_rn, on the host)
+float tf32_rn_host(float x) {
+  uint32_t u;
+  std::memcpy(&u, &x, 4);
+  u += 0xFFFu + ((u >> 13) & 1u);
+  u &= 0xFFFFE000u;
+  float r;
+  std::memcpy(&r, &u, 4);
+  return r;
+}
+
+// The image of the n x n operand f(r, k) in the staged layout of tc_stage.
+template <class F>
+void tc_image(int n, F f, unsigned char* out) {
+  const size_t rows = tc_image_rows(n), half = rows / 8 * kTcSbo;
+  const int chunks = (n + kTcKc - 1) / kTcKc;
+  std::memset(out, 0, tc_image_bytes(n));
+  for (int c = 0; c < chunks; ++c) {
+    unsigned char* hi = out + (size_t)c * 2 * half;
+    unsigned char* lo = hi + half;
+    for (int r = 0; r < n; ++r)
+      for (int kk = 0; kk < kTcKc && c * kTcKc + kk < n; ++kk) {
+        const float v = f(r, c * kTcKc + kk);
+        const float h = tf32_rn_host(v), l = tf32_rn_host(v - h);
+        const size_t off = (size_t)(r >> 3) * kTcSbo + (size_t)(kk >> 2) * 128 + (size_t)(r & 7) * 16 + (kk & 3) * 4;
+        std::memcpy(hi + off, &h, 4);
+        std::memcpy(lo + off, &l, 4);
+      }
+  }
+}
+
 // Shared memory a block may give the slab-resident pass B.
 constexpr size_t kSlabSmemBytes = 200 * 1024;
 
@@ -1095,7 +1140,17 @@ size_t make_args(DctArgs<TP>& A, const DctPlan& pl, const Params& pr, double* b,
   A.partial = sc.partial;
   A.max_blocks = sc.max_blocks;
   A.st = st;
-  return smem_bytes<TP>(pl, &A.thomas_cols, &A.slab_smem, &A.tc, &A.tc_slab);
+  const size_t need = smem_bytes<TP>(pl, &A.thomas_cols, &A.slab_smem, &A.tc, &A.tc_slab);
+  if (A.tc && pl.img) {
+    const unsigned char* img = (const unsigned char*)pl.img;
+    A.img_gx = (int)(tc_image_rows(pl.Mx) / 8);
+    A.img_gy = (int)(tc_image_rows(pl.My) / 8);
+    A.img_cx = img;
+    A.img_cxt = A.img_cx + tc_image_bytes(pl.Mx);
+    A.img_cy = pl.dim == 3 ? A.img_cxt + tc_image_bytes(pl.Mx) : nullptr;
+    A.img_cyt = pl.dim == 3 ? A.img_cy + tc_image_bytes(pl.My) : nullptr;
+  }
+  return need;
 }
 
 template <typename TP>
@@ -1151,6 +1206,29 @@ void dct_tables(const DctPlan& pl, const Params& pr, double* out) {
   } else {
     Cy[0] = 1.0;
     ly[0] = 0.0;
+  }
+}
+
+size_t dct_image_bytes(const DctPlan& pl) {
+  if (!pl.fp32) return 0;
+  return 2 * tc_image_bytes(pl.Mx) + (pl.dim == 3 ? 2 * tc_image_bytes(pl.My) : 0);
+}
+
+// Cx as rows m (K along i), Cx^T as rows i (K along m), and in 3D Cy as rows
+// ky (K along j), Cy^T as rows j (K along ky): the constant operands of
+// passes A, C and B.
+void dct_images(const DctPlan& pl, const float* Cx, const float* Cy, unsigned char* out) {
+  if (!pl.fp32) return;
+  const int Mx = pl.Mx, My = pl.My;
+  unsigned char* p = out;
+  tc_image(Mx, [&](int r, int k) { return Cx[(size_t)r * Mx + k]; }, p);
+  p += tc_image_bytes(Mx);
+  tc_image(Mx, [&](int r, int k) { return Cx[(size_t)k * Mx + r]; }, p);
+  p += tc_image_bytes(Mx);
+  if (pl.dim == 3) {
+    tc_image(My, [&](int r, int k) { return Cy[(size_t)r * My + k]; }, p);
+    p += tc_image_bytes(My);
+    tc_image(My, [&](int r, int k) { return Cy[(size_t)k * My + r]; }, p);
   }
 }
 

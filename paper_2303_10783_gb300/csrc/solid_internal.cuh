@@ -609,11 +609,16 @@ struct DctPlan {
   void* T1;              // work arrays of Mx*My*Mt elements (float or double)
   void* T2;
   void* tables;          // cosine matrices Cx [Mx][Mx], Cy [My][My], eigenvalues lx [Mx], ly [My]
+  void* img;             // FP32 plans: Cx, Cx^T, Cy, Cy^T in the tensor cores' staged layout
 };
 void plan_dct(const Params& pr, DctPlan& pl, int fp32);
 size_t dct_table_elems(const DctPlan& pl);
 // the tables in FP64, packed as above, into out[dct_table_elems]
 void dct_tables(const DctPlan& pl, const Params& pr, double* out);
+// bytes of the staged images of an FP32 plan (0 otherwise), and the images
+// built from the FP32 tables (Cx [Mx][Mx] and Cy [My][My] as packed above)
+size_t dct_image_bytes(const DctPlan& pl);
+void dct_images(const DctPlan& pl, const float* Cx, const float* Cy, unsigned char* out);
 // The fields of the projection (Eq. 3.5) that the transform solve can end with.
 struct ProjectPtrs {
   double* vel[3];          // u^{n+1} (written)

@@ -171,6 +171,11 @@ struct TcOperand {
   int rows, cols;
   float sc, off;
   int rfast;
+  // or, for a constant operand, its image in the staged layout (per chunk of
+  // kTcKc values of K: the hi then the lo half, each img_groups 8-row groups
+  // of kTcSbo bytes), copied 16 bytes at a time
+  const unsigned char* img = nullptr;
+  int img_groups = 0;
 };
 
 __device__ __forceinline__ float tc_elem(const TcOperand& o, int r, int k) {
@@ -202,6 +207,17 @@ __device__ __forceinline__ void tc_put4(unsigned char* hi, unsigned char* lo, ui
 // lane loads four rows at each of four k and transposes them in registers).
 __device__ __forceinline__ void tc_stage(const TcOperand& o, int r0, int nrows, int k0, int kc, unsigned char* hi,
                                          unsigned char* lo) {
+  if (o.img) {   // rows r0 .. r0 + nrows of the chunk's image (r0 a multiple of 8)
+    const size_t half = (size_t)o.img_groups * kTcSbo;
+    const unsigned char* src = o.img + (size_t)(k0 / kTcKc) * 2 * half + (size_t)(r0 >> 3) * kTcSbo;
+    const int n16 = (nrows >> 3) * (kTcSbo / 16);
+    for (int e = threadIdx.x; e < 2 * n16; e += blockDim.x) {
+      const int h = e >= n16 ? 1 : 0, u = e - h * n16;
+      const uint4 v = reinterpret_cast<const uint4*>(src + h * half)[u];
+      reinterpret_cast<uint4*>(h ? lo : hi)[u] = v;
+    }
+    return;
+  }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int nk4 = kc >> 2, kg = (nk4 + 3) >> 2;
   const bool vec = tc_vec(o);
