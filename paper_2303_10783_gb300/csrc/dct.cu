@@ -78,7 +78,8 @@ struct DctArgs {
   int warm;                 // start from the x in place (else from 0)
   int thomas_cols;          // columns per shared-memory chunk of the tridiagonal solves
   int slab_smem;            // 1: pass B keeps each slab in shared memory (FP32 slabs that fit)
-  int tc;                   // 1: the FP32 transforms of passes A and C run on the tensor cores
+  int tc;                   // 1: the kernel opens the tensor cores (some pass below uses them)
+  int tc_ac;                // 1: the FP32 transforms of passes A and C run on the tensor cores
   int tc_slab;              // 1: so do pass B's, with the slab's tridiagonal solves in shared memory
   // the constant operands of the tensor-core passes in their staged layout
   const unsigned char *img_cx, *img_cxt, *img_cy, *img_cyt;
@@ -443,6 +444,13 @@ __device__ void pass_b_slab(const DctArgs<float>& A, const Team& tm, float* sm) 
 // ---- The FP32 transforms on the tensor cores (umma.cuh): the same products
 // as gemm_tile and smem_gemm, as 128-row accumulator tiles in TMEM.
 constexpr int kTcMaxWidth = 128;   // accumulator width of passes A and C (two staging buffers: 133 KB)
+// Passes A and C take the tensor cores from this many multiply-adds per
+// transform (Mx * Mx * My * Mt) on: a tile's K chunks are latency-bound
+// (~2 us of staging and ~1 us of MMA issue each, measured on GB300), which
+// only pays where each block has several tiles. Measured per sweep: 128 x 96
+// x 96, pass A 12.3 us (FP32 pipes 12.9), pass C 23.7 (17.3); 384 x 256 x
+// 256, pass A 0.51 ms (0.68), pass C 0.83 ms (0.94).
+constexpr long long kTcAcMinWork = 1ll << 30;
 
 // Accumulator width (a multiple of 16, at most kTcMaxWidth) for an output of
 // `extent` columns by `row_tiles` tiles of 128 rows on a team of `blocks`:
@@ -625,7 +633,7 @@ template <typename TP>
 __device__ __forceinline__ bool run_pass_a(const DctArgs<TP>& A, const Team& tm, TP sc, TP off, TP* sm,
                                            TcState* tc) {
   if constexpr (sizeof(TP) == 4) {
-    if (tc) return pass_a_tc(A, tm, sc, off, sm, *tc);
+    if (tc && A.tc_ac) return pass_a_tc(A, tm, sc, off, sm, *tc);
   }
   pass_a<TP>(A, tm, sc, off, sm);
   return true;
@@ -643,7 +651,7 @@ __device__ __forceinline__ bool run_pass_b(const DctArgs<TP>& A, const Team& tm,
 template <typename TP>
 __device__ __forceinline__ bool run_pass_c(const DctArgs<TP>& A, const Team& tm, double rn, TP* sm, TcState* tc) {
   if constexpr (sizeof(TP) == 4) {
-    if (tc) return pass_c_tc(A, tm, rn, sm, *tc);
+    if (tc && A.tc_ac) return pass_c_tc(A, tm, rn, sm, *tc);
   }
   pass_c<TP>(A, tm, rn, sm);
   return true;
@@ -1041,7 +1049,7 @@ void tc_image(int n, F f, unsigned char* out) {
 constexpr size_t kSlabSmemBytes = 200 * 1024;
 
 template <typename TP>
-size_t smem_bytes(const DctPlan& pl, int* cols, int* slab, int* tc, int* tc_slab) {
+size_t smem_bytes(const DctPlan& pl, int* cols, int* slab, int* tc, int* tc_ac, int* tc_slab) {
   const int P = (pl.Mt & 1) ? pl.Mt : pl.Mt + 1;
   const int ncols = pl.dim == 3 ? pl.My : pl.Mx;
   long long w = (long long)(kThomasSmemBytes / (2 * (size_t)P * sizeof(TP)));
@@ -1055,14 +1063,16 @@ size_t smem_bytes(const DctPlan& pl, int* cols, int* slab, int* tc, int* tc_slab
   const size_t slab_bytes = slab_smem_floats(pl.My, pl.Mt) * sizeof(float);
   *slab = sizeof(TP) == 4 && pl.dim == 3 && slab_bytes <= kSlabSmemBytes;
   if (*slab && slab_bytes > need) need = slab_bytes;
-  // the tensor-core passes (FP32): tiles of width up to kTcCols in A and C;
-  // in B the slab's accumulator width, its transformed slab and the
-  // eliminated super-diagonal
-  *tc = sizeof(TP) == 4;
+  // the tensor-core passes (FP32): tiles of width up to kTcMaxWidth in A and
+  // C, where the grid is large enough; in B the slab's accumulator width,
+  // its transformed slab and the eliminated super-diagonal
+  *tc_ac = sizeof(TP) == 4 && (long long)pl.Mx * pl.Mx * pl.My * pl.Mt >= kTcAcMinWork;
   *tc_slab = 0;
-  if (*tc) {
+  if (*tc_ac) {
     const size_t ac = tc_smem_bytes(kTcMaxWidth);
     if (ac > need) need = ac;
+  }
+  if (sizeof(TP) == 4) {
     const int wt = (pl.Mt + 15) & ~15;
     const size_t b = tc_smem_bytes(wt) + 2 * (size_t)pl.Mt * tc_slab_row(pl.My) * sizeof(float);
     if (pl.dim == 3 && pl.My <= kTcM && wt <= kTcCols && b <= kSlabSmemBytes) {
@@ -1071,6 +1081,7 @@ size_t smem_bytes(const DctPlan& pl, int* cols, int* slab, int* tc, int* tc_slab
       if (b > need) need = b;
     }
   }
+  *tc = *tc_ac || *tc_slab;
   return need;
 }
 
@@ -1140,7 +1151,7 @@ size_t make_args(DctArgs<TP>& A, const DctPlan& pl, const Params& pr, double* b,
   A.partial = sc.partial;
   A.max_blocks = sc.max_blocks;
   A.st = st;
-  const size_t need = smem_bytes<TP>(pl, &A.thomas_cols, &A.slab_smem, &A.tc, &A.tc_slab);
+  const size_t need = smem_bytes<TP>(pl, &A.thomas_cols, &A.slab_smem, &A.tc, &A.tc_ac, &A.tc_slab);
   if (A.tc && pl.img) {
     const unsigned char* img = (const unsigned char*)pl.img;
     A.img_gx = (int)(tc_image_rows(pl.Mx) / 8);
