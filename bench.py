@@ -251,15 +251,16 @@ def measured_peaks():
         return {}
 
 
-KERNEL_SOURCES = {"k_pcg_mg": "mg.cu", "k_poisson_dct": "dct.cu", "k_bicgstab_ir": "krylov.cu",
-                  "k_bicgstab": "krylov.cu", "k_pcg_poisson": "krylov.cu", "k_helmholtz_dct": "dct.cu"}
+KERNEL_SOURCES = {"k_pcg_mg": ("mg.cu",), "k_poisson_dct": ("dct.cu", "umma.cuh"),
+                  "k_helmholtz_dct": ("dct.cu", "umma.cuh"), "k_bicgstab_ir": ("krylov.cu",),
+                  "k_bicgstab": ("krylov.cu",), "k_pcg_poisson": ("krylov.cu",)}
 
 
-def kernel_source_sha(kernel="k_pcg_mg"):
-    """sha256 over the source file of `kernel` and the shared header."""
+def kernel_source_sha(kernel="k_bicgstab_ir"):
+    """sha256 over the source files of `kernel` and the shared header."""
     h = hashlib.sha256()
     base = kernel.split("<")[0]
-    for f in (KERNEL_SOURCES.get(base, "mg.cu"), "solid_internal.cuh"):
+    for f in KERNEL_SOURCES.get(base, ("krylov.cu",)) + ("solid_internal.cuh",):
         h.update(open(os.path.join(ROOT, "paper_2303_10783_gb300", "csrc", f), "rb").read())
     return h.hexdigest()
 
@@ -531,7 +532,10 @@ def kernel_work(stage, precision_name, case, prof, stats):
             flops += rows * JAC_FLOPS_ROW["fp64"] * jac
         if mixed:
             sweeps = stats["refinements"][q] * launches    # sweeps of the last step, for each launch
-            nbytes += rows * (BCG_IR_BYTES_ROW * launches + BCG_IR_BYTES_ROW_SWEEP * sweeps + BCG_IR_BYTES_ROW_IT * its)
+            # a launch with no sweeps, iterations or Jacobi sweeps found its system solved
+            # (the T* pre-solve met the tolerance) and read nothing per row
+            active = launches if (sweeps or its or jac) else 0
+            nbytes += rows * (BCG_IR_BYTES_ROW * active + BCG_IR_BYTES_ROW_SWEEP * sweeps + BCG_IR_BYTES_ROW_IT * its)
             counts[q] = {"rows": rows, "jacobi_sweeps": jac, "inner_iterations": its, "sweeps": sweeps}
         else:
             nbytes += rows * BCG_BYTES_ROW_IT * its

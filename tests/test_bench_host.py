@@ -41,17 +41,22 @@ def test_oracle_samples_are_bounded_and_keep_the_case():
 
 
 def test_traffic_record_is_keyed_by_workload():
-    rec = None
+    """Every record of the committed DRAM traffic is looked up by its kernel,
+    source hash and workload; a record taken on other sources or another
+    workload is not reported."""
+    recs = []
     for line in open(os.path.join(ROOT, "profiles", "traffic.txt")):
-        if line.startswith("k_pcg_mg<float>"):
-            rec = dict(f.split("=", 1) for f in line.split()[1:])
-    assert rec is not None
-    got = bench.kernel_traffic("k_pcg_mg<float>", rec["workload"])
-    if rec["sha256"] == bench.kernel_source_sha():
-        assert got is not None and got[0] == float(rec["bytes_per_launch"])
-    else:
-        assert got is None
-    assert bench.kernel_traffic("k_pcg_mg<float>", "some_other_workload") is None
+        if line.strip() and not line.startswith("#"):
+            kern = line.split()[0]
+            recs.append((kern, dict(f.split("=", 1) for f in line.split()[1:])))
+    assert recs
+    for kern, rec in recs:
+        got = bench.kernel_traffic(kern, rec["workload"])
+        if rec["sha256"] == bench.kernel_source_sha(kern):
+            assert got is not None and got[0] == float(rec["bytes_per_launch"])
+        else:
+            assert got is None
+        assert bench.kernel_traffic(kern, "some_other_workload") is None
 
 
 def test_reference_arm_prints_the_contract_line():
