@@ -235,6 +235,20 @@ ss_status ss_equilibrate(ss_case* c);
  * Drops a captured step graph. SS_EINVAL for max_blocks < 0. */
 ss_status ss_set_block_cap(ss_case* c, int max_blocks);
 
+/* Where the FP32 cosine transforms of the mixed path's pressure solve and
+ * T* pre-solve form their products (SS_PRECOND_DCT; no effect otherwise):
+ * SS_TC_AUTO (default): the tcgen05 tensor cores (three TF32 products per
+ * step, see ss_tc_selftest) for the transforms along y of 3D slabs that fit
+ * (n_y <= 128, n_z <= 256) and, on grids of at least 2^30 multiply-adds per
+ * transform along x (n_x^2 n_y n_z), for those along x too, else the FP32
+ * pipes; SS_TC_ON: the tensor cores for every transform they can take;
+ * SS_TC_OFF: the FP32 pipes only. Results agree at rounding level. Takes
+ * effect for the case's later launches (a packed batch keeps what its cases
+ * had when it was created); drops a captured step graph. SS_EINVAL for
+ * another mode. */
+enum { SS_TC_AUTO = 0, SS_TC_ON = 1, SS_TC_OFF = 2 };
+ss_status ss_set_tensor_cores(ss_case* c, int mode);
+
 /* The FP64 -> FP32 rounding (to nearest, ties to even) that forms the FP32
  * plane copies, applied to n device values src -> dst in order on `stream`
  * (a cudaStream_t; NULL: the legacy default stream). For checking that

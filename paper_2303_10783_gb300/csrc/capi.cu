@@ -1036,6 +1036,14 @@ ss_status ss_set_block_cap(ss_case* c, int max_blocks) {
   return SS_OK;
 }
 
+ss_status ss_set_tensor_cores(ss_case* c, int mode) {
+  STAGE_TRY(check_case(c));
+  if (mode != SS_TC_AUTO && mode != SS_TC_ON && mode != SS_TC_OFF) return fail(SS_EINVAL, "unknown mode %d", mode);
+  drop_graph(c);   // launch configurations are part of a captured step
+  c->dct.tc_mode = mode;
+  return SS_OK;
+}
+
 ss_status ss_set_time(ss_case* c, double t) {
   STAGE_TRY(check_case(c));
   if (!std::isfinite(t)) return fail(SS_EINVAL, "time must be finite");

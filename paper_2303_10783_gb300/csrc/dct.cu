@@ -1066,13 +1066,14 @@ size_t smem_bytes(const DctPlan& pl, int* cols, int* slab, int* tc, int* tc_ac, 
   // the tensor-core passes (FP32): tiles of width up to kTcMaxWidth in A and
   // C, where the grid is large enough; in B the slab's accumulator width,
   // its transformed slab and the eliminated super-diagonal
-  *tc_ac = sizeof(TP) == 4 && (long long)pl.Mx * pl.Mx * pl.My * pl.Mt >= kTcAcMinWork;
+  *tc_ac = sizeof(TP) == 4 && pl.tc_mode != SS_TC_OFF &&
+           (pl.tc_mode == SS_TC_ON || (long long)pl.Mx * pl.Mx * pl.My * pl.Mt >= kTcAcMinWork);
   *tc_slab = 0;
   if (*tc_ac) {
     const size_t ac = tc_smem_bytes(kTcMaxWidth);
     if (ac > need) need = ac;
   }
-  if (sizeof(TP) == 4) {
+  if (sizeof(TP) == 4 && pl.tc_mode != SS_TC_OFF) {
     const int wt = (pl.Mt + 15) & ~15;
     const size_t b = tc_smem_bytes(wt) + 2 * (size_t)pl.Mt * tc_slab_row(pl.My) * sizeof(float);
     if (pl.dim == 3 && pl.My <= kTcM && wt <= kTcCols && b <= kSlabSmemBytes) {

@@ -610,6 +610,7 @@ struct DctPlan {
   void* T2;
   void* tables;          // cosine matrices Cx [Mx][Mx], Cy [My][My], eigenvalues lx [Mx], ly [My]
   void* img;             // FP32 plans: Cx, Cx^T, Cy, Cy^T in the tensor cores' staged layout
+  int tc_mode;           // SS_TC_AUTO, SS_TC_ON or SS_TC_OFF
 };
 void plan_dct(const Params& pr, DctPlan& pl, int fp32);
 size_t dct_table_elems(const DctPlan& pl);

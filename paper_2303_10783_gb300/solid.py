@@ -18,6 +18,7 @@ STATUS_NAMES = {0: "SS_OK", 1: "SS_EINVAL", 2: "SS_ENOMEM", 3: "SS_ENOTCONV", 4:
                 6: "SS_ESTATE", 7: "SS_ETIMEOUT"}
 SS_FP64, SS_MIXED = 0, 1
 SS_PRECOND_MG, SS_PRECOND_JACOBI, SS_PRECOND_DCT = 0, 1, 2
+SS_TC_AUTO, SS_TC_ON, SS_TC_OFF = 0, 1, 2
 SS_ADIABATIC, SS_ROBIN, SS_DIRICHLET = 0, 1, 2
 SS_NOSLIP, SS_FREESLIP = 0, 1
 FIELDS = ("u", "v", "w", "p", "T", "C", "gl", "Cl", "Cs")
@@ -86,6 +87,7 @@ def _declare(lib):
         "ss_get_stats": [P, ctypes.POINTER(Stats)],
         "ss_set_time": [P, ctypes.c_double],
         "ss_set_block_cap": [P, ctypes.c_int],
+        "ss_set_tensor_cores": [P, ctypes.c_int],
         "ss_get_time": [P, ctypes.POINTER(ctypes.c_double)],
         "ss_destroy": [P],
         "ss_assemble": [P, ctypes.c_int],
@@ -208,6 +210,12 @@ class Case:
     def set_block_cap(self, max_blocks):
         """At most ``max_blocks`` blocks per cooperative solver launch (0: no cap)."""
         check(self.lib.ss_set_block_cap(self.h, int(max_blocks)))
+
+    def set_tensor_cores(self, mode):
+        """Where the FP32 transforms form their products: "auto", "on" or "off"
+        (or SS_TC_AUTO / SS_TC_ON / SS_TC_OFF)."""
+        mode = {"auto": SS_TC_AUTO, "on": SS_TC_ON, "off": SS_TC_OFF}.get(mode, mode)
+        check(self.lib.ss_set_tensor_cores(self.h, int(mode)))
 
     def set_wait_limit(self, polls):
         """Polls per device-side wait before it gives up (0: the default, about a second)."""

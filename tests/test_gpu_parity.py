@@ -216,6 +216,44 @@ def test_step_parity_100_steps(lib, case, prec, precond):
     assert st.gl.min() < 1.0   # the mush formed: the lever rule and Darcy terms were exercised
 
 
+TC_CASES = [cases.cavity_2d(40, 24), cases.box_3d(19, 13, 11), cases.box_3d(32, 24, 16, seed=3)]
+
+
+@pytest.mark.parametrize("mode", ["on", "off"])
+@pytest.mark.parametrize("case", TC_CASES, ids=["%s-%dx%dx%d" % ("2d" if c["dim"] == 2 else "3d", c["nx"], c["ny"],
+                                                                   c["nz"]) for c in TC_CASES])
+def test_transform_products_on_and_off_the_tensor_cores_match_oracle(lib, case, mode):
+    """Mixed steps with the cosine transforms' products on the tensor cores
+    wherever they can run (passes A, C and, in 3D, B: "on") or on the FP32
+    pipes ("off") match the oracle after 20 steps at the step-parity bound,
+    the pressure solve and the T* pre-solve included."""
+    case = _tight(dict(case, precond_p="dct"))
+    case.update(tol_p=1e-13, tol_t=1e-13)
+    f = cases.initial_fields(case)
+    T0 = f["T"] - 0.8
+    c = solid.Case(case, precision=solid.SS_MIXED)
+    c.set_tensor_cores(mode)
+    c.initialize(T0, f["C"])
+    c.get_profile()
+    c.step(20)
+    assert c.sync() == solid.SS_OK
+    prof = c.get_profile()
+    gpu = c.get_fields()
+    assert lib.ss_set_tensor_cores(c.h, 3) == solid.SS_EINVAL
+    c.close()
+    g = oracle.Grid(case)
+    st = oracle.initial_state(case, T0, f["C"])
+    for _ in range(20):
+        st = oracle.step(g, st, case)
+    for k in ("p", "T", "C", "gl", "Cl", "Cs"):
+        assert _rel(gpu[k], getattr(st, k)) < STEP_TOL, (k, _rel(gpu[k], getattr(st, k)))
+    vmax = max(np.abs(x).max() for x in st.vel)
+    for a, k in enumerate("uvw"[: case["dim"]]):
+        assert np.abs(gpu[k] - st.vel[a]).max() / vmax < STEP_TOL, k
+    assert prof["iters"]["p"] > 0          # transform sweeps of the pressure solve
+    print("tensor cores %s, %s: T* pre-solve sweeps %d" % (mode, case["dim"], prof["presolve_sweeps"]))
+
+
 def _example2(dim, slip):
     """Example 2's walls (Sec. 5): bottom wall temperature falling linearly in
     time, free-slip or no-slip sides, perturbed centre line; the rate is raised
