@@ -228,7 +228,10 @@ def test_transform_products_on_and_off_the_tensor_cores_match_oracle(lib, case, 
     pipes ("off") match the oracle after 20 steps at the step-parity bound,
     the pressure solve and the T* pre-solve included."""
     case = _tight(dict(case, precond_p="dct"))
-    case.update(tol_p=1e-13, tol_t=1e-13)
+    # T* to 1e-14: the transform pre-solve stops just below its tolerance (a
+    # sweep gains ~3 digits), and the 2D cavity's buoyancy-driven velocity
+    # reflects a 1e-13 T* residual at ~1e-9 of its size
+    case.update(tol_p=1e-13, tol_t=1e-14)
     f = cases.initial_fields(case)
     T0 = f["T"] - 0.8
     c = solid.Case(case, precision=solid.SS_MIXED)
