@@ -33,7 +33,8 @@
  *     case bookkeeping is malloc'd by the library.
  *   - Streams: every device operation of a case is enqueued on the stream
  *     given to ss_create_case (a cudaStream_t passed as void*; NULL = legacy
- *     default stream). Calls that return data synchronise that stream.
+ *     default stream). Calls that return data to the host synchronise that
+ *     stream; copies into device buffers stay stream-ordered.
  *   - Errors: every call returns an ss_status and never exits or traps.
  *     ss_last_error() gives a message for the calling thread. Solver
  *     outcomes are sticky on the device: a solve that reaches its iteration
@@ -205,7 +206,10 @@ ss_status ss_step_graph(ss_case* c, int n);
 ss_status ss_sync(ss_case* c);
 
 /* Copy the fields selected by `mask` into caller-owned buffers dst[id]
- * (device pointers if dst_is_device, else host). Synchronises the stream. */
+ * (device pointers if dst_is_device, else host). Host copies synchronise the
+ * case's stream before returning; device copies are only enqueued on it
+ * (stream-ordered, like ss_step), so work on another stream that reads dst
+ * must first wait for the case's stream. */
 ss_status ss_get_fields(ss_case* c, unsigned mask, void* const* dst, int dst_is_device);
 
 /* Overwrite the fields selected by `mask` from src[id] (restart, or seeded

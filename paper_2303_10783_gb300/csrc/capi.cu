@@ -991,7 +991,7 @@ ss_status ss_get_fields(ss_case* c, unsigned mask, void* const* dst, int dst_is_
     CUDA_TRY(cudaMemcpyAsync(dst[id], field_ptr(c, id), field_len(c, id) * sizeof(double),
                              dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
   }
-  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  if (!dst_is_device) CUDA_TRY(cudaStreamSynchronize(c->stream));   // device copies stay stream-ordered
   return SS_OK;
 }
 

@@ -289,7 +289,9 @@ class Case:
 
     def get_fields(self, names=FIELDS, device=False, out=None):
         """Dict name -> numpy array (or CUDA tensor when ``device``) of the
-        current fields; ``out`` may supply the destination arrays (e.g. pinned)."""
+        current fields; ``out`` may supply the destination arrays (e.g. pinned).
+        Host copies wait for the case's stream; device copies are ordered
+        before the caller's current stream's later work."""
         import torch
         names = [n for n in names if not (n == "w" and self.dim != 3)]
         ptrs = (ctypes.c_void_p * 9)()
@@ -309,6 +311,10 @@ class Case:
             res[name] = t
             mask |= 1 << i
         check(self.lib.ss_get_fields(self.h, mask, ptrs, int(device)))
+        if device:
+            # device copies are stream-ordered on the case's stream: order the
+            # caller's current stream after them (no host wait)
+            torch.cuda.current_stream().wait_stream(self.stream)
         if self.dim != 3 and not device and out is None:
             res.setdefault("w", np.zeros(self.shapes["w"]))
         return res
