@@ -252,7 +252,10 @@ class Case:
         check(self.lib.ss_equilibrate(self.h))
 
     def set_fields(self, fields):
-        """``fields``: dict name -> numpy array (host) or CUDA tensor (device), float64, C-contiguous."""
+        """``fields``: dict name -> numpy array (host) or CUDA tensor (device), float64, C-contiguous.
+        Host sources are copied before the call returns; device sources are
+        copied in stream order (after the caller's current stream's earlier
+        work, before its later work)."""
         import torch
         mask = 0
         ptrs = (ctypes.c_void_p * 9)()
@@ -278,9 +281,19 @@ class Case:
                 raise ValueError("mix of host and device sources")
             on_dev = dev
             mask |= 1 << i
-        check(self.lib.ss_set_fields(self.h, mask, ptrs, int(bool(on_dev))))
         if on_dev:
-            self.stream.synchronize()
+            # device sources: stream-ordered both ways, no host wait. The case's
+            # stream waits for the caller's current stream (which produced the
+            # sources), the caller's later work waits for the copies, and the
+            # allocator keeps converted temporaries until the case's stream is done
+            cur = torch.cuda.current_stream()
+            self.stream.wait_stream(cur)
+            check(self.lib.ss_set_fields(self.h, mask, ptrs, 1))
+            for t in keep:
+                t.record_stream(self.stream)
+            cur.wait_stream(self.stream)
+        else:
+            check(self.lib.ss_set_fields(self.h, mask, ptrs, 0))
 
     def initialize(self, T, C):
         """Seeded initial fields: set T and C, then the equilibrium g_l, C_l, C_s."""
