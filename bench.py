@@ -418,8 +418,7 @@ def measure(args, precision_name, case, dist, local):
         if not args.no_e2e:
             # end to end through the public API with host buffers: every step uploads its full
             # input state from pinned host memory, steps, and reads every field back to pinned
-            # host memory. The copies run on two side streams (uploads and read-backs, so the
-            # two directions of the host link run at once), double-buffered through device
+            # host memory. The copies run on a side stream, double-buffered through device
             # buffers: step k+1's upload and step k's read-back overlap the compute of the
             # neighbouring step; every byte still crosses inside the timed region.
             state = c.get_fields()
@@ -431,8 +430,7 @@ def measure(args, precision_name, case, dist, local):
                       for _ in range(2)]
             dev_out = [{k: torch.empty(v.shape, dtype=torch.float64, device="cuda") for k, v in host.items()}
                        for _ in range(2)]
-            side = torch.cuda.Stream()                       # uploads
-            back = torch.cuda.Stream()                       # read-backs
+            side = torch.cuda.Stream()
             up = [torch.cuda.Event() for _ in range(2)]     # input buffer q holds its step's upload
             used = [torch.cuda.Event() for _ in range(2)]   # input buffer q has been consumed
             down = [torch.cuda.Event() for _ in range(2)]   # output buffer q has been read back
@@ -459,13 +457,12 @@ def measure(args, precision_name, case, dist, local):
                 c.step(1)
                 stream.wait_event(down[q])
                 c.get_fields(names, device=True, out=dev_out[q])
-                with torch.cuda.stream(back):
-                    back.wait_stream(stream)
+                with torch.cuda.stream(side):
+                    side.wait_stream(stream)
                     for k in names:
                         out[k].copy_(dev_out[q][k], non_blocking=True)
-                    down[q].record(back)
+                    down[q].record(side)
             side.synchronize()
-            back.synchronize()
             stream.synchronize()
             e2e_s = time.perf_counter() - t0
             barrier(dist)
@@ -640,9 +637,9 @@ def run_ours(args):
         "clocks": h["clocks"],
         "e2e": ({"value": h["e2e_value"], "unit": "cell-steps/s", "h2d_bytes_per_step": h["e2e"]["h2d"],
                  "d2h_bytes_per_step": h["e2e"]["d2h"], "steps": h["e2e"]["steps"],
-                 "path": "per step: pinned host -> device buffer (upload stream, during the previous step), "
+                 "path": "per step: pinned host -> device buffer (side stream, during the previous step), "
                          "ss_set_fields(device) + ss_step(1) + ss_get_fields(device), device buffer -> pinned "
-                         "host (read-back stream, during the next step)"} if h["e2e"] else None),
+                         "host (side stream, during the next step)"} if h["e2e"] else None),
         "gpu_launches": h["prof"]["kernels"],
         "roofline": roofline(head, h, case, args.steps, workload_name(args)),
         "stage_ms_per_step": {k: v / args.steps for k, v in h["prof"]["ms"].items() if v > 0},
