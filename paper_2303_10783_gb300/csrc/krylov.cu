@@ -103,6 +103,7 @@ struct CoreOut {
   bool half = false;
   float al = 0.f;
   const float* p = nullptr;
+  bool x_done = false;   // jac_fused: the correction was already added to the FP64 iterate
 };
 
 // The BiCGSTAB scalars, formed by thread 0 of each block after each
@@ -652,28 +653,101 @@ constexpr double kSweepMargin = 0.1;
 // copy from the FP64 residual, scaled in FP64.
 constexpr double kStageLo = 0x1p-60, kStageHi = 0x1p60;
 
+// One FP32 Jacobi sweep d_{k+1} = d_k + D^-1 (r0 - A d_k), r0 = sc r32, on
+// the rows of this thread; returns its part of |r0 - A d_k|^2 when REDUCE.
+// XUPD: also x += rn d_{k+1} in FP64 for the same rows (the sweep that ends
+// the inner solve adds the correction to the FP64 iterate).
+template <bool REDUCE, bool XUPD>
+__device__ __forceinline__ float jac_pass(const Planes<float>& a, int n, int sy, int sz, int has_z, const float* dk,
+                                          float* dn, const float* r32, float sc, int t0, int gs, double* x64,
+                                          double rn) {
+  const int n4 = n >> 2, tail = n4 << 2;
+  const bool ay = (sy & 3) == 0, az = (sz & 3) == 0;
+  const float* dg = a.idiag;
+  float s2 = 0.f;
+  for (int m = t0; m < n4; m += gs) {
+    const int r = 4 * m;
+    const float4 P = ldg4(a.P, m), W = ldg4(a.W, m), E = ldg4(a.E, m), S = ldg4(a.S, m), N = ldg4(a.N, m);
+    const float4 xc = ld4(dk, m);
+    const float xw = dk[r - 1], xe = dk[r + 4];
+    const float4 xs = ay ? ld4(dk, (r - sy) >> 2) : make_float4(dk[r - sy], dk[r - sy + 1], dk[r - sy + 2], dk[r - sy + 3]);
+    const float4 xn = ay ? ld4(dk, (r + sy) >> 2) : make_float4(dk[r + sy], dk[r + sy + 1], dk[r + sy + 2], dk[r + sy + 3]);
+    float4 o;
+    o.x = P.x * xc.x; o.y = P.y * xc.y; o.z = P.z * xc.z; o.w = P.w * xc.w;
+    o.x = fmaf(W.x, xw, o.x); o.y = fmaf(W.y, xc.x, o.y); o.z = fmaf(W.z, xc.y, o.z); o.w = fmaf(W.w, xc.z, o.w);
+    o.x = fmaf(E.x, xc.y, o.x); o.y = fmaf(E.y, xc.z, o.y); o.z = fmaf(E.z, xc.w, o.z); o.w = fmaf(E.w, xe, o.w);
+    o.x = fmaf(S.x, xs.x, o.x); o.y = fmaf(S.y, xs.y, o.y); o.z = fmaf(S.z, xs.z, o.z); o.w = fmaf(S.w, xs.w, o.w);
+    o.x = fmaf(N.x, xn.x, o.x); o.y = fmaf(N.y, xn.y, o.y); o.z = fmaf(N.z, xn.z, o.z); o.w = fmaf(N.w, xn.w, o.w);
+    if (has_z) {
+      const float4 B = ldg4(a.B, m), T = ldg4(a.T_, m);
+      const float4 xb = az ? ld4(dk, (r - sz) >> 2)
+                           : make_float4(dk[r - sz], dk[r - sz + 1], dk[r - sz + 2], dk[r - sz + 3]);
+      const float4 xt = az ? ld4(dk, (r + sz) >> 2)
+                           : make_float4(dk[r + sz], dk[r + sz + 1], dk[r + sz + 2], dk[r + sz + 3]);
+      o.x = fmaf(B.x, xb.x, o.x); o.y = fmaf(B.y, xb.y, o.y); o.z = fmaf(B.z, xb.z, o.z); o.w = fmaf(B.w, xb.w, o.w);
+      o.x = fmaf(T.x, xt.x, o.x); o.y = fmaf(T.y, xt.y, o.y); o.z = fmaf(T.z, xt.z, o.z); o.w = fmaf(T.w, xt.w, o.w);
+    }
+    const float4 q = ld4(r32, m), dv = ldg4(dg, m);
+    float4 sv;
+    sv.x = fmaf(q.x, sc, -o.x); sv.y = fmaf(q.y, sc, -o.y); sv.z = fmaf(q.z, sc, -o.z); sv.w = fmaf(q.w, sc, -o.w);
+    const float4 dnv = make_float4(fmaf(dv.x, sv.x, xc.x), fmaf(dv.y, sv.y, xc.y), fmaf(dv.z, sv.z, xc.z),
+                                   fmaf(dv.w, sv.w, xc.w));
+    st4(dn, m, dnv);
+    if (REDUCE) s2 += dot4(sv, sv);
+    if (XUPD) {
+      x64[r] = fma(rn, (double)dnv.x, x64[r]);
+      x64[r + 1] = fma(rn, (double)dnv.y, x64[r + 1]);
+      x64[r + 2] = fma(rn, (double)dnv.z, x64[r + 2]);
+      x64[r + 3] = fma(rn, (double)dnv.w, x64[r + 3]);
+    }
+  }
+  for (int i = tail + t0; i < n; i += gs) {
+    float acc = __ldg(a.P + i) * dk[i];
+    acc = fmaf(__ldg(a.W + i), dk[i - 1], acc);
+    acc = fmaf(__ldg(a.E + i), dk[i + 1], acc);
+    acc = fmaf(__ldg(a.S + i), dk[i - sy], acc);
+    acc = fmaf(__ldg(a.N + i), dk[i + sy], acc);
+    if (has_z) {
+      acc = fmaf(__ldg(a.B + i), dk[i - sz], acc);
+      acc = fmaf(__ldg(a.T_ + i), dk[i + sz], acc);
+    }
+    const float si = fmaf(r32[i], sc, -acc);
+    const float di = fmaf(__ldg(dg + i), si, dk[i]);
+    dn[i] = di;
+    if (REDUCE) s2 += si * si;
+    if (XUPD) x64[i] = fma(rn, (double)di, x64[i]);
+  }
+  return s2;
+}
+
 // FP32 Jacobi sweeps for the inner solve A d = r0, r0 = sc r32 (unit norm;
 // r32 is the caller's FP32 copy of its residual in V.t), for the strongly
 // diagonally dominant transport systems (see jacobi64): d_1 = D^-1 r0 (no
-// operator application), then d_{k+1} = d_k + D^-1 (r0 - A d_k) with
-// s_k = |r0 - A d_k| reduced in the same pass. It stops when s_k <= tol
-// (out.conv; the result is d_{k+1}), when a sweep reduced s less than
-// 1/kJacobiRate-fold (out.half is set as the stall flag: the caller's
-// later sweeps use BiCGSTAB), or after max_it sweeps. d ping-pongs between x
-// and V.p0; out.p is the result, out.it the sweeps. Reduction slots 0..3.
+// operator application), then d_{k+1} = d_k + D^-1 (r0 - A d_k). The first
+// sweep reduces s_1 = |r0 - A d_1|, which is the sweeps' contraction rate
+// rho: if s_1 <= tol the solve stops with d_2 (out.conv); if rho exceeds
+// kJacobiRate it stops with d_2 and sets out.half as the stall flag (the
+// caller's later sweeps use BiCGSTAB). Otherwise it runs the k sweeps for
+// which (kJacobiMargin rho)^k <= tol with barriers only (no reductions), and
+// the last of them adds rn d_{k+1} to the FP64 iterate x64 (out.x_done); the
+// caller's FP64 residual then tells how far the correction went. d
+// ping-pongs between x and V.p0; out.p is the result, out.it the iterates.
+// Reduction slots 0..1.
+constexpr double kJacobiMargin = 1.2;   // later sweeps contract a little less than the first
+constexpr int kJacobiMaxPredicted = 16;
 __device__ bool jac_fused(const Planes<float>& a, int n, int sy, int sz, int has_z, float* x, FusedVec V, float sc,
                           double tol, int max_it, const Team& tm, int max_blocks, DevStatus* st,
-                          unsigned int& epoch, CoreOut& out) {
+                          unsigned int& epoch, double* x64, double rn, CoreOut& out) {
   const int t0 = tm.rank * blockDim.x + threadIdx.x, gs = tm.size * blockDim.x;
   const int n4 = n >> 2, tail = n4 << 2;
-  const bool ay = (sy & 3) == 0, az = (sz & 3) == 0;
   const float* r32 = V.t;
   const float* dg = a.idiag;
   float* const b0 = x;
   float* const b1 = V.p0;
   __shared__ struct {
-    double res, prev;
-    int state;   // 0 sweep on, 1 converged, 2 stalled, 3 sweep cap
+    double res;
+    int state;   // 0 predicted sweeps follow, 1 converged, 2 stalled
+    int kpred;   // sweeps in all (the first included)
   } js;
   for (int m = t0; m < n4; m += gs) {             // d_1 = D^-1 r0
     const float4 q = ld4(r32, m), dv = ldg4(dg, m);
@@ -681,79 +755,59 @@ __device__ bool jac_fused(const Planes<float>& a, int n, int sy, int sz, int has
   }
   for (int i = tail + t0; i < n; i += gs) b0[i] = __ldg(dg + i) * (r32[i] * sc);
   out.half = false;
+  out.x_done = false;
   out.bnorm = 1.0;
-  if (max_it <= 1) {
-    out.it = 1;
-    out.p = b0;
-    out.conv = false;
-    out.res = 1.0;
+  out.p = b0;
+  out.it = 1;
+  out.conv = false;
+  out.res = 1.0;
+  if (max_it <= 1) return true;
+  if (!team_barrier(st, tm, epoch)) return false;
+  // sweep 1, reduced
+  const float s2 = jac_pass<true, false>(a, n, sy, sz, has_z, b0, b1, r32, sc, t0, gs, nullptr, 0.0);
+  if (!team_sum_post<1>(VecF<1>{{s2}}, tm, max_blocks, 0, st, epoch, [&](const double* tot) {
+        const double rho = sqrt(tot[0]);
+        js.res = rho;
+        js.kpred = 1;
+        if (rho <= tol) {
+          js.state = 1;
+        } else if (!isfinite(rho) || rho > kJacobiRate) {
+          js.state = 2;
+        } else {
+          int k = 2;
+          const double q = fmin(kJacobiMargin * rho, 0.5);
+          double pk = q * q;
+          while (pk > tol && k < kJacobiMaxPredicted) {
+            pk *= q;
+            ++k;
+          }
+          js.kpred = k < max_it - 1 ? k : max_it - 1;
+          js.state = js.kpred >= 2 ? 0 : 1;
+        }
+      }))
+    return false;
+  out.res = js.res;
+  out.p = b1;
+  out.it = 2;
+  if (js.state != 0) {
+    out.conv = js.state == 1;
+    out.half = js.state == 2;
     return true;
   }
-  if (threadIdx.x == 0) js.prev = 1.0;
-  if (!team_barrier(st, tm, epoch)) return false;
-  int k = 1;
-  while (true) {
+  // sweeps 2 .. kpred, separated by barriers; the last one updates x64
+  const int kpred = js.kpred;
+  for (int k = 2; k <= kpred; ++k) {
+    if (k > 2 && !team_barrier(st, tm, epoch)) return false;
     const float* dk = (k & 1) ? b0 : b1;
     float* dn = (k & 1) ? b1 : b0;
-    float s2 = 0.f;
-    for (int m = t0; m < n4; m += gs) {
-      const int r = 4 * m;
-      const float4 P = ldg4(a.P, m), W = ldg4(a.W, m), E = ldg4(a.E, m), S = ldg4(a.S, m), N = ldg4(a.N, m);
-      const float4 xc = ld4(dk, m);
-      const float xw = dk[r - 1], xe = dk[r + 4];
-      const float4 xs = ay ? ld4(dk, (r - sy) >> 2) : make_float4(dk[r - sy], dk[r - sy + 1], dk[r - sy + 2], dk[r - sy + 3]);
-      const float4 xn = ay ? ld4(dk, (r + sy) >> 2) : make_float4(dk[r + sy], dk[r + sy + 1], dk[r + sy + 2], dk[r + sy + 3]);
-      float4 o;
-      o.x = P.x * xc.x; o.y = P.y * xc.y; o.z = P.z * xc.z; o.w = P.w * xc.w;
-      o.x = fmaf(W.x, xw, o.x); o.y = fmaf(W.y, xc.x, o.y); o.z = fmaf(W.z, xc.y, o.z); o.w = fmaf(W.w, xc.z, o.w);
-      o.x = fmaf(E.x, xc.y, o.x); o.y = fmaf(E.y, xc.z, o.y); o.z = fmaf(E.z, xc.w, o.z); o.w = fmaf(E.w, xe, o.w);
-      o.x = fmaf(S.x, xs.x, o.x); o.y = fmaf(S.y, xs.y, o.y); o.z = fmaf(S.z, xs.z, o.z); o.w = fmaf(S.w, xs.w, o.w);
-      o.x = fmaf(N.x, xn.x, o.x); o.y = fmaf(N.y, xn.y, o.y); o.z = fmaf(N.z, xn.z, o.z); o.w = fmaf(N.w, xn.w, o.w);
-      if (has_z) {
-        const float4 B = ldg4(a.B, m), T = ldg4(a.T_, m);
-        const float4 xb = az ? ld4(dk, (r - sz) >> 2)
-                             : make_float4(dk[r - sz], dk[r - sz + 1], dk[r - sz + 2], dk[r - sz + 3]);
-        const float4 xt = az ? ld4(dk, (r + sz) >> 2)
-                             : make_float4(dk[r + sz], dk[r + sz + 1], dk[r + sz + 2], dk[r + sz + 3]);
-        o.x = fmaf(B.x, xb.x, o.x); o.y = fmaf(B.y, xb.y, o.y); o.z = fmaf(B.z, xb.z, o.z); o.w = fmaf(B.w, xb.w, o.w);
-        o.x = fmaf(T.x, xt.x, o.x); o.y = fmaf(T.y, xt.y, o.y); o.z = fmaf(T.z, xt.z, o.z); o.w = fmaf(T.w, xt.w, o.w);
-      }
-      const float4 q = ld4(r32, m), dv = ldg4(dg, m);
-      float4 sv;
-      sv.x = fmaf(q.x, sc, -o.x); sv.y = fmaf(q.y, sc, -o.y); sv.z = fmaf(q.z, sc, -o.z); sv.w = fmaf(q.w, sc, -o.w);
-      st4(dn, m, make_float4(fmaf(dv.x, sv.x, xc.x), fmaf(dv.y, sv.y, xc.y), fmaf(dv.z, sv.z, xc.z),
-                             fmaf(dv.w, sv.w, xc.w)));
-      s2 += dot4(sv, sv);
-    }
-    for (int i = tail + t0; i < n; i += gs) {
-      float acc = __ldg(a.P + i) * dk[i];
-      acc = fmaf(__ldg(a.W + i), dk[i - 1], acc);
-      acc = fmaf(__ldg(a.E + i), dk[i + 1], acc);
-      acc = fmaf(__ldg(a.S + i), dk[i - sy], acc);
-      acc = fmaf(__ldg(a.N + i), dk[i + sy], acc);
-      if (has_z) {
-        acc = fmaf(__ldg(a.B + i), dk[i - sz], acc);
-        acc = fmaf(__ldg(a.T_ + i), dk[i + sz], acc);
-      }
-      const float si = fmaf(r32[i], sc, -acc);
-      dn[i] = fmaf(__ldg(dg + i), si, dk[i]);
-      s2 += si * si;
-    }
-    if (!team_sum_post<1>(VecF<1>{{s2}}, tm, max_blocks, (k & 1) ? 0 : 2, st, epoch, [&](const double* tot) {
-          const double res = sqrt(tot[0]);
-          js.state = (res <= tol) ? 1 : (!isfinite(res) || res > kJacobiRate * js.prev) ? 2 : (k + 1 >= max_it) ? 3 : 0;
-          js.res = res;
-          js.prev = res;
-        }))
-      return false;
-    ++k;
-    if (js.state != 0) break;
+    if (k == kpred)
+      jac_pass<false, true>(a, n, sy, sz, has_z, dk, dn, r32, sc, t0, gs, x64, rn);
+    else
+      jac_pass<false, false>(a, n, sy, sz, has_z, dk, dn, r32, sc, t0, gs, nullptr, 0.0);
+    out.p = dn;
   }
-  out.it = k;                  // d_1 .. d_k: k sweeps, the last result in dn
-  out.p = ((k - 1) & 1) ? b1 : b0;
-  out.conv = js.state == 1;
-  out.half = js.state == 2;
-  out.res = js.res;
+  out.it = kpred + 1;
+  out.x_done = true;
   return true;
 }
 
@@ -828,13 +882,14 @@ __device__ __forceinline__ void ir_solve(const BcgArgs& A, const Team& tm, unsig
     const float* d = A.d32;
     if (jacobi) {
       if (!jac_fused(A.sys.af, n, sy, sz, A.has_z, A.d32, A.f32, is.sc, is.itol, cap, tm, A.max_blocks, A.st,
-                     epoch, o))
+                     epoch, x, rn, o))
         return;
       jac += o.it;
       d = o.p;
       if (o.half) jacobi = false;                 // the sweeps stalled: BiCGSTAB from the next sweep on
-      // x += rn d
-      for (int i = t0; i < n; i += gs) x[i] = fma(rn, (double)d[i], x[i]);
+      // x += rn d (unless the last sweep did)
+      if (!o.x_done)
+        for (int i = t0; i < n; i += gs) x[i] = fma(rn, (double)d[i], x[i]);
     } else {
       if (!bcg_fused(A.sys.af, n, sy, sz, A.has_z, A.d32, A.f32, is.sc, is.itol, cap, tm, A.max_blocks, A.st,
                      epoch, o))
