@@ -576,10 +576,15 @@ __device__ __forceinline__ Phase phase_of(const Params& pr, double C, double g) 
     o.Cl = C;
     o.Kinv = 0.0;
   } else {
-    // g + kp (1 - g) = 1 - (1 - kp)(1 - g): the denominator of Eq. 3.18 is 1/A_g (Eq. 3.8)
-    o.Ag = 1.0 / (1.0 - pr.lev_a * s);               // Eq. 3.8, for the next solute step
+    // g + kp (1 - g) = 1 - (1 - kp)(1 - g): the denominator of Eq. 3.18 is 1/A_g (Eq. 3.8);
+    // both quotients from one reciprocal (a few ulps, where two divisions
+    // would cost the FP64 pipe twice)
+    const double d1 = 1.0 - pr.lev_a * s;            // 1 / A_g
+    const double d2 = pr.K0 * (g * g * g + pr.eps);  // Carman-Kozeny denominator, regularised
+    const double inv = 1.0 / (d1 * d2);
+    o.Ag = d2 * inv;                                 // Eq. 3.8, for the next solute step
     o.Cl = C * o.Ag;                                 // Eq. 3.18
-    o.Kinv = s * s / (pr.K0 * (g * g * g + pr.eps));  // Eq. 2.8, regularised
+    o.Kinv = s * s * (d1 * inv);                     // Eq. 2.8
   }
   if (pr.has_eutectic) o.Cl = fmin(o.Cl, pr.Ce);
   return o;
@@ -612,7 +617,7 @@ __device__ __forceinline__ void lever_rows(const Params& pr, double* time, doubl
       const double c = -(gn + cpL * Ts) * kp + cpL * (Tl - pr.lev_aTm);
       const double sq = sqrt(fmax(b * b - pr.lev_4a * c, 0.0));
       // larger root of Eq. 3.16 (a > 0), in the form free of cancellation
-      g = (b > 0.0) ? (2.0 * c) / (-b - sq) : (-b + sq) / pr.lev_2a;
+      g = (b > 0.0) ? (2.0 * c) / (-b - sq) : (-b + sq) * pr.lev_inv2a;
       g = fmin(fmax(g, 0.0), 1.0);
       Tn = Ts - Lcp * (g - gn);                                              // Eq. 3.13
     }

@@ -287,6 +287,7 @@ void fill_params(ss_case* c, const ss_alloy* al) {
     pr.lev_aTm = pr.lev_a * pr.Tm;
     pr.lev_4a = 4.0 * pr.lev_a;
     pr.lev_2a = 2.0 * pr.lev_a;
+    pr.lev_inv2a = 1.0 / pr.lev_2a;
     pr.Te = pr.Tm + pr.m * pr.Ce;
     for (int a = 0; a < 3; ++a) {
       pr.hh[a] = 0.5 * pr.ih[a];

@@ -128,7 +128,7 @@ struct Params {
   double alpha_ih2[3];       // k/(rho cp h^2) (energy diffusion across one face)
   double half_Dl_ih2[3];     // D_l/(2 h^2) (solute diffusion: face mean of g_l D_l)
   // lever rule (Eq. 3.16-3.17): a = 1 - kp and products of constants with it
-  double lev_a, lev_cpLa, lev_aTm, lev_4a, lev_2a;
+  double lev_a, lev_cpLa, lev_aTm, lev_4a, lev_2a, lev_inv2a;
   double Te;                 // eutectic temperature Tm + m Ce
   // the assembly constants as double-floats (mixed-path assembly)
   dfl df_hh[3], df_ih[3], df_nu_ih2[3], df_two_nu_ih2[3], df_alpha_ih2[3], df_half_Dl_ih2[3];
