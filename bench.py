@@ -84,6 +84,14 @@ HELM_BYTES_PER_CELL_SWEEP = 112.0
 JAC_BYTES_ROW = {"mixed": 44.0, "fp64": 88.0}
 JAC_FLOPS_ROW = {"mixed": 16.0, "fp64": 19.0}
 BCG_BYTES_ROW_IT = 300.0
+# assembly of one transport row (a1, a6, a8): ~6 inputs read (48 B) and 7 FP64 planes, the
+#   right-hand side and 8 FP32 planes written (96 B) on the mixed path; the FP64 path writes
+#   7 FP64 planes, b and the FP64 inverse diagonal (72 B)
+ASM_BYTES_ROW = {"mixed": 144.0, "fp64": 120.0}
+# pressure right-hand side: u*, v*, w* read at each cell's faces (24 B), b written (8 B)
+RHS_BYTES_CELL = 32.0
+# lever rule: T*, g_l, C and the T* increment read, T, g_l, C_l, C_s, K^-1, A_g, increment written
+LEVER_BYTES_CELL = 88.0
 BCG_FLOPS_ROW_IT = 46.0
 FP64_FLOP_PER_CLK_PER_SM = 4.0    # 2 DFMA per clock per SM (1.26 TFLOP/s at 2070 MHz, 152 SMs)
 FP32_FLOP_PER_CLK_PER_SM = 256.0  # 128 FP32 FMA per clock per SM (80.6 TFLOP/s at 2070 MHz)
@@ -593,6 +601,25 @@ def roofline(precision_name, m, case, steps, wname):
     out = dict(detail[top])
     out["kernel"] = top
     out["all_kernels"] = {k: {q: v for q, v in d.items() if q != "stages"} for k, d in detail.items() if k != top}
+    # the assembly and pointwise kernels against the HBM roof by their algorithmic bytes
+    point = {}
+    for st, ms in stage_ms.items():
+        if ms <= 0 or not (st.startswith("assemble_") or st == "lever"):
+            continue
+        if st == "lever":
+            kern, per, rows = "k_lever", LEVER_BYTES_CELL, _rows(case, "p")
+        elif st == "assemble_p":
+            kern, per, rows = "k_poisson_rhs", RHS_BYTES_CELL, _rows(case, "p")
+        else:
+            q = st.split("_", 1)[1]
+            mom = q in ("u", "v", "w")
+            kern = ("k_assemble_momentum" if mom else "k_assemble_cells") + ("_df" if precision_name == "mixed" else "")
+            per, rows = ASM_BYTES_ROW[precision_name], _rows(case, q)
+        launches = max(prof["launches"].get(st, 1), 1)
+        ach = rows * per * launches / (ms * 1e-3) / 1e9
+        point[st] = {"kernel": kern, "bytes_per_launch": rows * per, "launch_ms": ms / launches, "achieved": ach,
+                     "unit": "GB/s", "hbm_frac": ach / hbm}
+    out["pointwise_kernels"] = point
     return out
 
 
