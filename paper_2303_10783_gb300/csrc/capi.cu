@@ -559,22 +559,17 @@ ss_status stage_solve_momentum(ss_case* c) {
 }
 
 // When the momentum systems are solved in one joint launch. Measured on the
-// 1.2 M-cell box, mixed precision: three sequential solves take 0.76 ms
-// against 0.79 ms for the joint launch (the three FP32 working sets exceed L2
-// together, one at a time they do not); in FP64 the joint launch wins (0.79
-// against 0.97 ms: those solves are bound by the FP64 pipe, not by L2). A
+// 1.2 M-cell box: mixed, 0.44 ms joint against 0.49 ms for three sequential
+// solves (each solve is bound by its FP64 residual passes and its barriers;
+// three teams overlap their barrier waits); FP64, 0.64 against ~0.9 ms. A
 // case under a solver block cap (a batch or a server running cases side by
 // side) gains ~10% from the joint launch, and so does a small case, whose
-// solves are latency-bound. At 25 M cells the joint launch is 15% slower
+// solves are latency-bound. At 25 M cells the joint launch was 15% slower
 // (each team streams its own vectors from HBM on a third of the SMs, and the
 // team with the most iterations sets the time).
-constexpr long long kJointMomentumMaxCells = 1LL << 22;        // capped or FP64 cases
-constexpr long long kJointMomentumMaxCellsUncapped = 1LL << 20;
+constexpr long long kJointMomentumMaxCells = 1LL << 22;
 
-bool joint_momentum(const ss_case* c) {
-  const bool wide = c->block_cap > 0 || c->g.precision == SS_FP64;
-  return c->n_cell <= (wide ? kJointMomentumMaxCells : kJointMomentumMaxCellsUncapped);
-}
+bool joint_momentum(const ss_case* c) { return c->n_cell <= kJointMomentumMaxCells; }
 
 ss_status one_step(ss_case* c) {
   const int ncomp = c->pr.dim;
