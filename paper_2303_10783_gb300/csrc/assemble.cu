@@ -193,7 +193,8 @@ __device__ __forceinline__ void assemble_momentum_rows(const Params& pr, const S
 // bounds the FP64 kernels at ~30 FP64 operations per row. The right-hand side
 // stays FP64 (its pressure difference and Boussinesq deviations cancel). The
 // planes agree with the FP64 ones to ~1e-14 relative to the row's scale, and
-// the FP32 copies are their IEEE rounding as before.
+// the FP32 copies are their IEEE rounding as before (formed from the pairs,
+// see df_round).
 
 // max(F, 0) and min(F, 0) of a double-float by the sign of its leading part
 struct SplitDf {
@@ -205,15 +206,41 @@ __device__ __forceinline__ SplitDf split_df(dfl F) {
   return {negative ? z : F, negative ? F : z};
 }
 
+// The FP64 planes are the pairs' sums (exact widening, one FP64 add). The
+// FP32 copies are the same sums rounded once in FP32: rounding hi + lo to
+// binary64 and then to binary32 gives the binary32 rounding of hi + lo itself
+// (double rounding through 53 bits is innocuous for a sum of two 24-bit
+// numbers, as 53 >= 2 * 24 + 1), so they equal the FP64 planes' IEEE
+// rounding bit for bit, without the integer-pipe conversion.
+__device__ __forceinline__ float df_round(dfl a) { return __fadd_rn(a.hi, a.lo); }
+
 __device__ __forceinline__ void write_row_df(const Sys& s, int r, int dim, dfl P, const dfl nbB[3], const dfl nbF[3],
                                              double b) {
-  double nb[3], nf[3];
-#pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    nb[d] = d < dim ? df_to_f64(nbB[d]) : 0.0;
-    nf[d] = d < dim ? df_to_f64(nbF[d]) : 0.0;
+  s.a.P[r] = df_to_f64(P);
+  s.a.W[r] = df_to_f64(nbB[0]);
+  s.a.E[r] = df_to_f64(nbF[0]);
+  s.a.S[r] = df_to_f64(nbB[1]);
+  s.a.N[r] = df_to_f64(nbF[1]);
+  if (dim == 3) {
+    s.a.B[r] = df_to_f64(nbB[2]);
+    s.a.T_[r] = df_to_f64(nbF[2]);
   }
-  write_row(s, r, dim, df_to_f64(P), nb, nf, b);
+  s.b[r] = b;
+  if (s.af.P) {
+    const float Pf = df_round(P);
+    s.af.P[r] = Pf;
+    s.af.W[r] = df_round(nbB[0]);
+    s.af.E[r] = df_round(nbF[0]);
+    s.af.S[r] = df_round(nbB[1]);
+    s.af.N[r] = df_round(nbF[1]);
+    if (dim == 3) {
+      s.af.B[r] = df_round(nbB[2]);
+      s.af.T_[r] = df_round(nbF[2]);
+    }
+    s.af.idiag[r] = 1.0f / Pf;
+  } else {
+    s.a.idiag[r] = 1.0 / df_to_f64(P);
+  }
 }
 
 template <int A>

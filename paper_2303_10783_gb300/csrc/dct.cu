@@ -115,12 +115,13 @@ __device__ __forceinline__ void lds4<double>(const double* p, double v[4]) {
 }
 
 // FP64 <-> transform type, the FP32 conversions on the integer pipes
+// (v * p for p = 2^e, narrowed)
 template <typename TP>
-__device__ __forceinline__ TP narrow(double v);
+__device__ __forceinline__ TP narrow_scaled(double v, int e, double p);
 template <>
-__device__ __forceinline__ float narrow<float>(double v) { return to_f32(v); }
+__device__ __forceinline__ float narrow_scaled<float>(double v, int e, double p) { return to_f32_scaled(v, e, p); }
 template <>
-__device__ __forceinline__ double narrow<double>(double v) { return v; }
+__device__ __forceinline__ double narrow_scaled<double>(double v, int, double p) { return v * p; }
 __device__ __forceinline__ double widen(float v) { return to_f64(v); }
 __device__ __forceinline__ double widen(double v) { return v; }
 
@@ -278,16 +279,26 @@ __device__ void thomas_chunk(TP* buf, long long st, long long sc, int Mt, int c0
   __syncthreads();
 }
 
-// (A v)_c, A = -L with zero-flux walls (FP64, the refinement residual)
-__device__ __forceinline__ double lap64(const double* v, int c, int i, int j, int k, int nx, int ny, int nz,
-                                        double ax, double ay, double az, double diag) {
+// b_c - (A v)_c, A = -L with zero-flux walls (FP64, the refinement residual):
+// each product is fused into the running difference (one FP64 operation per
+// neighbour pair and one for the centre; GB300's FP64 pipe bounds this loop)
+__device__ __forceinline__ double res_lap64(double bc, const double* v, int c, int i, int j, int k, int nx, int ny,
+                                            int nz, double ax, double ay, double az, double diag) {
   const int sy = nx, sz = nx * ny;
-  double acc = diag * v[c];
-  acc = fma(-ax, (i > 0 ? v[c - 1] : 0.0) + (i < nx - 1 ? v[c + 1] : 0.0), acc);
-  acc = fma(-ay, (j > 0 ? v[c - sy] : 0.0) + (j < ny - 1 ? v[c + sy] : 0.0), acc);
-  if (nz > 1) acc = fma(-az, (k > 0 ? v[c - sz] : 0.0) + (k < nz - 1 ? v[c + sz] : 0.0), acc);
+  double acc = fma(-diag, v[c], bc);
+  acc = fma(ax, (i > 0 ? v[c - 1] : 0.0) + (i < nx - 1 ? v[c + 1] : 0.0), acc);
+  acc = fma(ay, (j > 0 ? v[c - sy] : 0.0) + (j < ny - 1 ? v[c + sy] : 0.0), acc);
+  if (nz > 1) acc = fma(az, (k > 0 ? v[c - sz] : 0.0) + (k < nz - 1 ? v[c + sz] : 0.0), acc);
   return acc;
 }
+
+// The FP32 transform path sums the staged residual r * 2^e (a few units at
+// most) in FP32 partial sums of at most kNormChunk terms, each added to an
+// FP64 total: a partial is within kNormChunk * 2^-24 of its exact value, so a
+// norm is within ~1e-6 of the FP64 one, and convergence is declared only when
+// the norm times kNormMargin meets the tolerance. The FP64 path sums in FP64.
+constexpr int kNormChunk = 16;
+constexpr double kNormMargin = 1.0 + 1.0 / 65536.0;
 
 // Pass A: T1 = (Cx ⊗ I) (rs * sc + off): rs is the residual staged in T2 in
 // the transform type, scaled by a power of two (exactly) when it was formed;
@@ -675,7 +686,7 @@ __device__ bool poisson_dct_team(const DctArgs<TP>& A, const Team& tm, TP* sm, T
   double* r = A.r;
   __shared__ struct {
     double mean, bn, rn, rmean, sc, off, pscale;
-    int go, conv;
+    int pexp, go, conv;   // pscale = 2^pexp
   } ds;
   double thr = 0.0;   // read by thread 0 only
   TP* rs = A.T2;       // the residual of the next sweep, staged in the transform type (T2 is free outside pass B)
@@ -693,6 +704,7 @@ __device__ bool poisson_dct_team(const DctArgs<TP>& A, const Team& tm, TP* sm, T
         int e = 0;
         frexp(sqrt(fmax(tot[1] - (double)n * ds.mean * ds.mean, 0.0)), &e);
         ds.pscale = ldexp(1.0, -e);
+        ds.pexp = -e;
       }))
     return false;
   const double mean_b = ds.mean;
@@ -701,6 +713,7 @@ __device__ bool poisson_dct_team(const DctArgs<TP>& A, const Team& tm, TP* sm, T
   // first residual is b itself.
   const bool warm = A.warm != 0;
   double ps = ds.pscale;   // the staged residual is r * ps (ps a power of two: exact)
+  int pe = ds.pexp;
   Vec<3> s2 = {{0.0, 0.0, 0.0}};
   for (int c = t0; c < n; c += gsz) {
     const double bc = b[c] - mean_b;
@@ -711,14 +724,14 @@ __device__ bool poisson_dct_team(const DctArgs<TP>& A, const Team& tm, TP* sm, T
       int i, j, k;
       decompose3(c, A.fx, A.fy, i, j, k);
       const int code = ((i > 0) + (i < A.nx - 1)) + 3 * ((j > 0) + (j < A.ny - 1)) + 9 * ((k > 0) + (k < A.nz - 1));
-      rc = bc - lap64(x, c, i, j, k, A.nx, A.ny, A.nz, A.cx, A.cy, A.cz, s_diag[code]);
+      rc = res_lap64(bc, x, c, i, j, k, A.nx, A.ny, A.nz, A.cx, A.cy, A.cz, s_diag[code]);
       r[c] = rc;
       s2.v[1] += rc;
       s2.v[2] += rc * rc;
     } else {
       x[c] = 0.0;
     }
-    rs[c] = narrow<TP>(rc * ps);
+    rs[c] = narrow_scaled<TP>(rc, pe, ps);
   }
   if (!team_sum_post<3>(s2, tm, A.max_blocks, 1, A.st, epoch, [&](const double* tot) {
         ds.bn = sqrt(tot[0]);
@@ -737,6 +750,7 @@ __device__ bool poisson_dct_team(const DctArgs<TP>& A, const Team& tm, TP* sm, T
         int e = 0;
         frexp(ds.rn, &e);
         ds.pscale = ldexp(1.0, -e);   // for the residual of the next sweep
+        ds.pexp = -e;
       }))
     return false;
   int sweeps = 0;
@@ -744,27 +758,50 @@ __device__ bool poisson_dct_team(const DctArgs<TP>& A, const Team& tm, TP* sm, T
     ++sweeps;
     const double rn = ds.rn;
     ps = ds.pscale;
+    pe = ds.pexp;
     if (!run_pass_a<TP>(A, tm, (TP)ds.sc, (TP)ds.off, sm, tc)) return false;
     if (!team_barrier(A.st, tm, epoch)) return false;
     if (!run_pass_b<TP>(A, tm, sm, tc)) return false;
     if (!team_barrier(A.st, tm, epoch)) return false;
     if (!run_pass_c<TP>(A, tm, rn, sm, tc)) return false;
     if (!team_barrier(A.st, tm, epoch)) return false;
+    constexpr bool f32 = sizeof(TP) == 4;
     Vec<2> s = {{0.0, 0.0}};
+    float f0 = 0.f, f1 = 0.f;   // FP32 partial sums of r * ps (FP32 path)
+    int nf = 0;
     for (int c = t0; c < n; c += gsz) {
       int i, j, k;
       decompose3(c, A.fx, A.fy, i, j, k);
       const int code = ((i > 0) + (i < A.nx - 1)) + 3 * ((j > 0) + (j < A.ny - 1)) + 9 * ((k > 0) + (k < A.nz - 1));
-      const double rc = b[c] - lap64(x, c, i, j, k, A.nx, A.ny, A.nz, A.cx, A.cy, A.cz, s_diag[code]);
-      rs[c] = narrow<TP>(rc * ps);
-      s.v[0] += rc;
-      s.v[1] += rc * rc;
+      const double rc = res_lap64(b[c], x, c, i, j, k, A.nx, A.ny, A.nz, A.cx, A.cy, A.cz, s_diag[code]);
+      const TP rv = narrow_scaled<TP>(rc, pe, ps);
+      rs[c] = rv;
+      if constexpr (f32) {
+        f0 += rv;
+        f1 = fmaf(rv, rv, f1);
+        if (++nf == kNormChunk) {
+          s.v[0] += f0;
+          s.v[1] += f1;
+          f0 = f1 = 0.f;
+          nf = 0;
+        }
+      } else {
+        s.v[0] += rc;
+        s.v[1] += rc * rc;
+      }
+    }
+    if constexpr (f32) {
+      s.v[0] += f0;
+      s.v[1] += f1;
     }
     if (!team_sum_post<2>(s, tm, A.max_blocks, 2, A.st, epoch, [&](const double* tot) {
-          // norm of the part of r outside the constants: sum (r - mean)^2
-          const double rmean = tot[0] / (double)n;
-          const double rn_new = sqrt(fmax(tot[1] - (double)n * rmean * rmean, 0.0));
-          ds.conv = rn_new <= thr;
+          // norm of the part of r outside the constants: sum (r - mean)^2 (the
+          // FP32 path's sums are of r * ps: 1 / ps is exact)
+          const double us = f32 ? 1.0 / ps : 1.0;
+          const double m = tot[0] / (double)n;
+          const double rmean = m * us;
+          const double rn_new = us * sqrt(fmax(tot[1] - (double)n * m * m, 0.0));
+          ds.conv = rn_new * (f32 ? kNormMargin : 1.0) <= thr;
           // stop when a sweep no longer halves the residual (rounding floor)
           ds.go = !ds.conv && isfinite(rn_new) && rn_new < 0.5 * ds.rn;
           ds.rn = rn_new;
@@ -774,6 +811,7 @@ __device__ bool poisson_dct_team(const DctArgs<TP>& A, const Team& tm, TP* sm, T
           int e = 0;
           frexp(rn_new, &e);
           ds.pscale = ldexp(1.0, -e);
+          ds.pexp = -e;
         }))
       return false;
   }
@@ -833,17 +871,19 @@ __device__ bool poisson_dct_team(const DctArgs<TP>& A, const Team& tm, TP* sm, T
   return true;
 }
 
-// One row of a DIA system in FP64 (the guard bands make every neighbour
-// read valid; an absent neighbour's coefficient is 0).
-__device__ __forceinline__ double spmv64(const Planes<double>& a, const double* x, int r, int sy, int sz, int has_z) {
-  double acc = a.P[r] * x[r];
-  acc = fma(a.W[r], x[r - 1], acc);
-  acc = fma(a.E[r], x[r + 1], acc);
-  acc = fma(a.S[r], x[r - sy], acc);
-  acc = fma(a.N[r], x[r + sy], acc);
+// b_r - (A x)_r for one row of a DIA system in FP64, each product fused into
+// the running difference (the guard bands make every neighbour read valid; an
+// absent neighbour's coefficient is 0).
+__device__ __forceinline__ double res64(double br, const Planes<double>& a, const double* x, int r, int sy, int sz,
+                                        int has_z) {
+  double acc = fma(-a.P[r], x[r], br);
+  acc = fma(-a.W[r], x[r - 1], acc);
+  acc = fma(-a.E[r], x[r + 1], acc);
+  acc = fma(-a.S[r], x[r - sy], acc);
+  acc = fma(-a.N[r], x[r + sy], acc);
   if (has_z) {
-    acc = fma(a.B[r], x[r - sz], acc);
-    acc = fma(a.T_[r], x[r + sz], acc);
+    acc = fma(-a.B[r], x[r - sz], acc);
+    acc = fma(-a.T_[r], x[r + sz], acc);
   }
   return acc;
 }
@@ -870,14 +910,14 @@ __device__ bool helmholtz_team(const DctArgs<float>& A, const Sys& S, int has_z,
   float* rs = A.T2;
   __shared__ struct {
     double rn, bn, sc, pscale;
-    int go, conv;
+    int pexp, go, conv;   // pscale = 2^pexp
   } hs;
   double thr = 0.0;   // read by thread 0 only
   double ps = 1.0;    // the first staged residual is not scaled (T* residuals are O(1) in K/s)
   if (tm.rank == 0 && threadIdx.x == 0) A.st->presolve_done = 0;
   Vec<2> s0 = {{0.0, 0.0}};
   for (int c = t0; c < n; c += gsz) {
-    const double rc = b[c] - spmv64(S.a, x, c, sy, sz, has_z);
+    const double rc = res64(b[c], S.a, x, c, sy, sz, has_z);
     rs[c] = to_f32(rc);
     s0.v[0] += b[c] * b[c];
     s0.v[1] += rc * rc;
@@ -893,6 +933,7 @@ __device__ bool helmholtz_team(const DctArgs<float>& A, const Sys& S, int has_z,
         int e = 0;
         frexp(hs.rn, &e);
         hs.pscale = ldexp(1.0, -e);
+        hs.pexp = -e;
       }))
     return false;
   int sweeps = 0;
@@ -906,21 +947,32 @@ __device__ bool helmholtz_team(const DctArgs<float>& A, const Sys& S, int has_z,
     if (!run_pass_c<float>(A, tm, rn * inv_alpha, sm, tc)) return false;
     if (!team_barrier(A.st, tm, epoch)) return false;
     ps = hs.pscale;
+    const int pe = hs.pexp;
+    // the norm from FP32 partial sums of the staged r * ps (see kNormChunk)
     Vec<1> s1 = {{0.0}};
+    float f1 = 0.f;
+    int nf = 0;
     for (int c = t0; c < n; c += gsz) {
-      const double rc = b[c] - spmv64(S.a, x, c, sy, sz, has_z);
-      rs[c] = to_f32(rc * ps);
-      s1.v[0] += rc * rc;
+      const float rv = to_f32_scaled(res64(b[c], S.a, x, c, sy, sz, has_z), pe, ps);
+      rs[c] = rv;
+      f1 = fmaf(rv, rv, f1);
+      if (++nf == kNormChunk) {
+        s1.v[0] += f1;
+        f1 = 0.f;
+        nf = 0;
+      }
     }
+    s1.v[0] += f1;
     if (!team_sum_post<1>(s1, tm, A.max_blocks, 1, A.st, epoch, [&](const double* tot) {
-          const double rn_new = sqrt(tot[0]);
-          hs.conv = rn_new <= thr;
-          hs.go = rn_new > thr && isfinite(rn_new) && rn_new < 0.5 * hs.rn;
+          const double rn_new = sqrt(tot[0]) / ps;
+          hs.conv = rn_new * kNormMargin <= thr;
+          hs.go = !hs.conv && isfinite(rn_new) && rn_new < 0.5 * hs.rn;
           hs.sc = 1.0 / (hs.pscale * rn_new);
           hs.rn = rn_new;
           int e = 0;
           frexp(rn_new, &e);
           hs.pscale = ldexp(1.0, -e);
+          hs.pexp = -e;
         }))
       return false;
   }

@@ -69,6 +69,22 @@ __device__ __forceinline__ T spmv_row(const Planes<T>& a, const T* x, int r, int
   return acc;
 }
 
+// b_r - (A x)_r in FP64 with each product fused into the running difference
+// (one FP64 operation per coefficient: the refinement residuals' FP64 work)
+__device__ __forceinline__ double res_row64(double br, const Planes<double>& a, const double* x, int r, int sy,
+                                            int sz, int has_z) {
+  double acc = fma(-__ldg(a.P + r), x[r], br);
+  acc = fma(-__ldg(a.W + r), x[r - 1], acc);
+  acc = fma(-__ldg(a.E + r), x[r + 1], acc);
+  acc = fma(-__ldg(a.S + r), x[r - sy], acc);
+  acc = fma(-__ldg(a.N + r), x[r + sy], acc);
+  if (has_z) {
+    acc = fma(-__ldg(a.B + r), x[r - sz], acc);
+    acc = fma(-__ldg(a.T_ + r), x[r + sz], acc);
+  }
+  return acc;
+}
+
 // Solve statistics, written by thread 0 of the leading block of the solving team.
 __device__ void record(DevStatus* st, bool leader, int idx, int iters, int refinements, bool converged,
                        double relres, int jacobi = 0) {
@@ -573,7 +589,7 @@ __device__ int jacobi64(const BcgArgs& A, const Team& tm, unsigned int& epoch, i
     double* xn = (k & 1) ? x0 : x1;
     Vec<2> acc = {{0.0, 0.0}};
     for (int r = t0; r < n; r += gs) {
-      const double rr = b[r] - spmv_row(a, xk, r, sy, sz, A.has_z);
+      const double rr = res_row64(b[r], a, xk, r, sy, sz, A.has_z);
       const double dinv = __ldg(a.idiag + r);
       xn[r] = fma(dinv, rr, xk[r]);
       acc.v[0] += rr * rr;
@@ -819,7 +835,7 @@ __device__ __forceinline__ double ir_residual(const BcgArgs& A, int t0, int gs, 
   const double* b = A.sys.b;
   double s = 0.0, sb = 0.0;
   for (int i = t0; i < n; i += gs) {
-    const double ri = b[i] - spmv_row(A.sys.a, A.sys.x, i, sy, sz, A.has_z);
+    const double ri = res_row64(b[i], A.sys.a, A.sys.x, i, sy, sz, A.has_z);
     A.v64.r[i] = ri;
     r32[i] = to_f32(ri);
     s += ri * ri;

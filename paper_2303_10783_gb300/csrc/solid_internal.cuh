@@ -386,6 +386,25 @@ __device__ __forceinline__ float to_f32(double d) {
   return __double2float_rn(d);
 }
 
+// to_f32(d * p) for p = 2^e: where d is a normal FP64 value and d * 2^e has
+// an exponent that FP32 holds as a normal number, the power of two goes into
+// the exponent field on the integer pipes (d * 2^e is exact in FP64 there, so
+// the result is bit-identical); other values take the FP64 product.
+__device__ __forceinline__ float to_f32_scaled(double d, int e, double p) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(d);
+  const unsigned hi = (unsigned)(u >> 32), lo = (unsigned)u;
+  const unsigned ed = (hi >> 20) & 0x7FFu;
+  const unsigned es = ed + (unsigned)e;   // biased exponent of d * 2^e (wraps when negative)
+  if (ed - 1u < 2046u && es - 897u <= 253u) {
+    const unsigned m = ((hi & 0xFFFFFu) << 3) | (lo >> 29);
+    const unsigned rest = lo & 0x1FFFFFFFu;
+    unsigned bits = (hi & 0x80000000u) | ((es - 896u) << 23) | m;
+    bits += (rest > 0x10000000u || (rest == 0x10000000u && (m & 1u))) ? 1u : 0u;
+    return __uint_as_float(bits);
+  }
+  return to_f32(d * p);
+}
+
 // binary32 -> binary64 (exact) on the integer pipes for normal floats and
 // zeros: the exponent is rebiased (127 -> 1023) and the fraction shifted into
 // place; subnormal and non-finite values take the hardware conversion.
