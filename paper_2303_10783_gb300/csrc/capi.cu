@@ -223,6 +223,8 @@ void plan(ss_case* c, Planner& pl) {
     c->dct.T2 = mixed ? (void*)pl.vec<float>(c->n_cell) : (void*)pl.vec<double>(c->n_cell);
     c->dct.tables = pl.raw<char>(dct_table_elems(c->dct) * esz);
     c->dct.img = mixed ? pl.raw<char>(dct_image_bytes(c->dct)) : nullptr;
+    const size_t tb = dct_thomas_bytes(c->dct);
+    c->dct.thomas = tb ? pl.raw<char>(tb) : nullptr;
   }
   // Krylov scratch: set 0 serves every solve (multigrid included); sets 1, 2
   // serve the v* and w* teams of the joint momentum solve, with only the
@@ -869,6 +871,8 @@ ss_status ss_create_case(const ss_grid* grid, void* workspace, size_t workspace_
       dct_images(c->dct, tab32.data(), tab32.data() + (size_t)c->dct.Mx * c->dct.Mx, img.data());
       e = cudaMemcpyAsync(c->dct.img, img.data(), img.size(), cudaMemcpyHostToDevice, c->stream);
     }
+    // the slab solves' factorisations, formed from the tables just copied
+    if (e == cudaSuccess) e = dct_thomas_ensure(c->dct, c->pr, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   }
   if (e != cudaSuccess) {
@@ -892,6 +896,7 @@ ss_status ss_set_alloy(ss_case* c, const ss_alloy* al) {
   if (al->Dl < 0) return fail(SS_EINVAL, "Dl must be >= 0");
   c->alloy_set = 1;
   fill_params(c, al);
+  CUDA_TRY(dct_thomas_ensure(c->dct, c->pr, c->stream));   // the T* operator's shift depends on the alloy
   const long long nf[3] = {c->n_face[0], c->n_face[1], c->n_face[2]};
   CUDA_TRY(cudaMemsetAsync(c->u, 0, nf[0] * sizeof(double), c->stream));
   CUDA_TRY(cudaMemsetAsync(c->v, 0, nf[1] * sizeof(double), c->stream));

@@ -88,6 +88,10 @@ struct DctArgs {
   // of -L (no null space), s0 = shift, for the operator I/dt - alpha L
   double shift;
   int helm;
+  // 3D FP32 slab solves: 1/d_t of the tridiagonal factorisation of every
+  // (kx, ky) column, [Mx][Mt][My], formed once for this operator (or null:
+  // formed on the fly)
+  const float* tinv;
   double* partial;
   int max_blocks;
   DevStatus* st;
@@ -373,10 +377,41 @@ __host__ __device__ __forceinline__ size_t slab_smem_floats(int My, int Mt) {
 // The tridiagonal solves along t of slab kx, one column ky per thread: Ts
 // holds the transformed slab [t][ky] (rows of P floats) and receives the
 // solution; Ps takes the eliminated super-diagonal.
-__device__ __forceinline__ void slab_thomas(const DctArgs<float>& A, int kx, float* Ts, float* Ps, int P) {
+// inv: where the factorisation is a constant of the operator (A.tinv), the
+// slab's 1/d_t, [Mt][My], in shared memory or straight from A.tinv; only the
+// substitutions remain then.
+__device__ __forceinline__ void slab_thomas(const DctArgs<float>& A, int kx, float* Ts, float* Ps, int P,
+                                            const float* inv = nullptr) {
   const int My = A.My, Mt = A.Mt;
   const float at = A.at;
   const float sx = A.lx[kx];
+  if (A.tinv) {
+    if (!inv) inv = A.tinv + (size_t)kx * Mt * My;
+    for (int c = threadIdx.x; c < My; c += blockDim.x) {
+      const bool singular = !A.helm && kx == 0 && c == 0;
+      const int m = singular ? Mt - 1 : Mt;
+      float y = 0.f;
+#pragma unroll 8
+      for (int t = 0; t < m; ++t) {
+        y = fmaf(at, y, Ts[(size_t)t * P + c]) * inv[(size_t)t * My + c];
+        Ts[(size_t)t * P + c] = y;
+      }
+      float next = 0.f;
+      if (singular) Ts[(size_t)(Mt - 1) * P + c] = 0.f;
+#pragma unroll 8
+      for (int t = m - 1; t >= 0; --t) {
+        next = fmaf(at * inv[(size_t)t * My + c], next, Ts[(size_t)t * P + c]);
+        Ts[(size_t)t * P + c] = next;
+      }
+      if (singular) {
+        float sum = 0.f;
+        for (int t = 0; t < Mt; ++t) sum += Ts[(size_t)t * P + c];
+        const float mean = sum / (float)Mt;
+        for (int t = 0; t < Mt; ++t) Ts[(size_t)t * P + c] -= mean;
+      }
+    }
+    return;
+  }
   for (int c = threadIdx.x; c < My; c += blockDim.x) {
     const float s = sx + A.ly[c] + (float)A.shift;
     const bool singular = !A.helm && kx == 0 && c == 0;
@@ -545,14 +580,33 @@ __device__ bool pass_b_tc(const DctArgs<float>& A, const Team& tm, float* sm, Tc
   const TcOperand cy{A.Cy, My, 1, My, My, 1.f, 0.f, 0, A.img_cy, A.img_gy};    // (ky, j) = Cy[ky My + j]
   const TcOperand cyt{A.Cy, 1, My, My, My, 1.f, 0.f, 1, A.img_cyt, A.img_gy};  // (j, ky) = Cy[ky My + j]
   const TcOperand ts{Ts, P, 1, Mt, My, 1.f, 0.f, 0};       // (t, ky) = Ts[t P + ky]
+  // the slab's factorisation (when formed) comes into Ps by the copy engine
+  // during the first product, where its offsets keep 16-byte alignment
+  const uint32_t inv_bytes = (uint32_t)Mt * My * sizeof(float);
+  const bool inv_async = A.tinv && (inv_bytes & 15u) == 0 && (reinterpret_cast<uintptr_t>(A.tinv) & 15u) == 0;
   for (int kx = tm.rank; kx < Mx; kx += tm.size) {
     float* S1 = A.T1 + (size_t)kx * R;   // [t][j]
     const TcOperand slab{S1, My, 1, Mt, My, 1.f, 0.f, 0};  // (t, j) = S1[t My + j]
-    if (!tc_gemm(tc, w, My, cy, 0, slab, 0, sm, A.st)) return false;
+    if (inv_async && threadIdx.x == 0) {
+      fence_async_smem();   // Ps was last written by the threads
+      mbar_expect_tx(tc.xbar, inv_bytes);
+      bulk_g2s(smem_u32(Ps), A.tinv + (size_t)kx * Mt * My, inv_bytes, tc.xbar);
+    }
+    const bool ok = tc_gemm(tc, w, My, cy, 0, slab, 0, sm, A.st);
+    if (inv_async) {   // the copy has been issued: wait for it (bounded) on every way on
+      const bool got = mbar_wait(tc.xbar, tc.xphase);
+      if (!got) mbar_wait(tc.xbar, tc.xphase);
+      tc.xphase ^= 1u;
+      if (__syncthreads_or(!got)) {
+        if (threadIdx.x == 0) atomicExch(&A.st->err, kErrBarrier);
+        return false;
+      }
+    }
+    if (!ok) return false;
     tc_store(tc, w, [&](int ky, int t, float v) {
       if (ky < My && t < Mt) Ts[(size_t)t * P + ky] = v;
     });
-    slab_thomas(A, kx, Ts, Ps, P);
+    slab_thomas(A, kx, Ts, Ps, P, inv_async ? Ps : nullptr);
     __syncthreads();
     if (!tc_gemm(tc, w, My, cyt, 0, ts, 0, sm, A.st)) return false;
     tc_store(tc, w, [&](int j, int t, float v) {
@@ -997,7 +1051,7 @@ struct HelmArgs {
 template <class F>
 __device__ __forceinline__ void with_tc(bool on, F f) {
   __shared__ uint32_t s_tmem;
-  __shared__ __align__(8) unsigned long long s_mbar[2];
+  __shared__ __align__(8) unsigned long long s_mbar[kTcBarriers];
   if (on) {
     TcState tc;
     tc_open(tc, &s_tmem, s_mbar);
@@ -1196,6 +1250,7 @@ size_t make_args(DctArgs<TP>& A, const DctPlan& pl, const Params& pr, double* b,
   A.ly = A.lx + pl.Mx;
   A.T1 = (TP*)pl.T1;
   A.T2 = (TP*)pl.T2;
+  A.tinv = (sizeof(TP) == 4 && pl.thomas && pl.thomas_p) ? (const float*)pl.thomas : nullptr;
   A.b = b; A.x = x; A.r = sc.v[0];
   A.tol = ctl.tol;
   A.warm = ctl.warm_start;
@@ -1297,12 +1352,67 @@ void dct_images(const DctPlan& pl, const float* Cx, const float* Cy, unsigned ch
 }
 
 namespace {
+// 1/d_t of the factorisation of T_t + (lx[kx] + ly[c] + shift) I for every
+// column (kx, c): the recurrence of slab_thomas, once per operator
+__global__ void k_thomas_table(float* inv, const float* lx, const float* ly, float at, float shift, int helm, int Mx,
+                               int My, int Mt) {
+  const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= (long long)Mx * My) return;
+  const int kx = (int)(id / My), c = (int)(id - (long long)kx * My);
+  const float s = lx[kx] + ly[c] + shift;
+  const bool singular = !helm && kx == 0 && c == 0;
+  const int m = singular ? Mt - 1 : Mt;
+  float* o = inv + (size_t)kx * Mt * My + c;
+  float prev_c = 0.f;
+  for (int t = 0; t < Mt; ++t) {
+    float v = 0.f;
+    if (t < m) {
+      const float nb = (float)((t > 0) + (t < Mt - 1));
+      const float d = fmaf(at, prev_c, fmaf(at, nb, s));
+      v = 1.f / d;
+      prev_c = -at * v;
+    }
+    o[(size_t)t * My] = v;
+  }
+}
+}  // namespace
+
+size_t dct_thomas_bytes(const DctPlan& pl) {
+  return (pl.fp32 && pl.dim == 3) ? 2 * (size_t)pl.Mx * pl.My * pl.Mt * sizeof(float) : 0;
+}
+
+cudaError_t dct_thomas_ensure(DctPlan& pl, const Params& pr, cudaStream_t s) {
+  if (!pl.thomas || !pl.tables || !pl.fp32 || pl.dim != 3) return cudaSuccess;
+  const size_t n = (size_t)pl.Mx * pl.My * pl.Mt;
+  const float* lx = (const float*)pl.tables + (size_t)pl.Mx * pl.Mx + (size_t)pl.My * pl.My;
+  const float* ly = lx + pl.Mx;
+  const float at = (float)(1.0 / (pr.hz * pr.hz));   // the transforms' 1/h^2 along the tridiagonal axis
+  const int threads = 256;
+  const int blocks = (int)(((long long)pl.Mx * pl.My + threads - 1) / threads);
+  float* tab = (float*)pl.thomas;
+  if (!pl.thomas_p) {
+    k_thomas_table<<<blocks, threads, 0, s>>>(tab, lx, ly, at, 0.f, 0, pl.Mx, pl.My, pl.Mt);
+    pl.thomas_p = 1;
+  }
+  const double sh = 1.0 / (pr.alphaT * pr.dt);   // the T* pre-solve's shift (as in its arguments)
+  if (std::isfinite(sh) && (!pl.thomas_h || sh != pl.thomas_shift)) {
+    k_thomas_table<<<blocks, threads, 0, s>>>(tab + n, lx, ly, at, (float)sh, 1, pl.Mx, pl.My, pl.Mt);
+    pl.thomas_h = 1;
+    pl.thomas_shift = sh;
+  }
+  return cudaGetLastError();
+}
+
+namespace {
 size_t make_helm_args(HelmArgs& H, const DctPlan& pl, const Params& pr, const Sys& sys, int has_z, int max_sweeps,
                       const SolverCtl& ctl, Scratch& sc, DevStatus* st) {
   memset(&H, 0, sizeof H);
   const size_t smem = make_args<float>(H.dct, pl, pr, sys.b, sys.x, ctl, sc, st, nullptr);
   H.dct.helm = 1;
   H.dct.shift = 1.0 / (pr.alphaT * pr.dt);   // 1/(alpha dt), in the 1/h^2 units of the transforms
+  H.dct.tinv = (pl.thomas && pl.thomas_h && pl.thomas_shift == H.dct.shift)
+                   ? (const float*)pl.thomas + (size_t)pl.Mx * pl.My * pl.Mt
+                   : nullptr;
   H.sys = sys;
   H.has_z = has_z;
   H.inv_alpha = 1.0 / pr.alphaT;

@@ -630,6 +630,12 @@ struct DctPlan {
   void* tables;          // cosine matrices Cx [Mx][Mx], Cy [My][My], eigenvalues lx [Mx], ly [My]
   void* img;             // FP32 plans: Cx, Cx^T, Cy, Cy^T in the tensor cores' staged layout
   int tc_mode;           // SS_TC_AUTO, SS_TC_ON or SS_TC_OFF
+  // 3D FP32 plans: the tridiagonal factorisations of the slab solves (1/d_t
+  // per column), [Mx][Mt][My] for the pressure operator, then the same for
+  // the T* operator with the shift thomas_shift
+  void* thomas;
+  int thomas_p, thomas_h;   // which half is formed
+  double thomas_shift;
 };
 void plan_dct(const Params& pr, DctPlan& pl, int fp32);
 size_t dct_table_elems(const DctPlan& pl);
@@ -638,6 +644,11 @@ void dct_tables(const DctPlan& pl, const Params& pr, double* out);
 // bytes of the staged images of an FP32 plan (0 otherwise), and the images
 // built from the FP32 tables (Cx [Mx][Mx] and Cy [My][My] as packed above)
 size_t dct_image_bytes(const DctPlan& pl);
+// bytes of the slab solves' factorisations (0 for 2D and FP64 plans), and
+// forming them on stream s for the current parameters where not yet formed
+// (after the tables are on the device; stream-ordered)
+size_t dct_thomas_bytes(const DctPlan& pl);
+cudaError_t dct_thomas_ensure(DctPlan& pl, const Params& pr, cudaStream_t s);
 void dct_images(const DctPlan& pl, const float* Cx, const float* Cy, unsigned char* out);
 // The fields of the projection (Eq. 3.5) that the transform solve can end with.
 struct ProjectPtrs {

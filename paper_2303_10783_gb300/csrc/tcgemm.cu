@@ -12,7 +12,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_tc_selftest(const float* __restri
                                                            DevStatus* st) {
   extern __shared__ __align__(16) unsigned char dsm[];
   __shared__ uint32_t s_tmem;
-  __shared__ __align__(8) unsigned long long s_mbar[2];
+  __shared__ __align__(8) unsigned long long s_mbar[kTcBarriers];
   TcState tc;
   tc_open(tc, &s_tmem, s_mbar);
   const TcOperand oa = transposed ? TcOperand{a, 1, kTcM, kTcM, k, 1.f, 0.f, 1} : TcOperand{a, k, 1, kTcM, k, 1.f, 0.f, 0};

@@ -91,6 +91,21 @@ __device__ __forceinline__ void mbar_init(uint32_t mbar, uint32_t count) {
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 
+// one arrival on the mbarrier that also expects `bytes` of asynchronous copies
+// to complete on it (the phase ends when both have happened)
+__device__ __forceinline__ void mbar_expect_tx(uint32_t mbar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
+}
+
+// bulk copy (the copy engine, no threads) of `bytes` from global memory to
+// this block's shared memory, completing on mbar; both addresses 16-byte
+// aligned and bytes a multiple of 16
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t mbar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(mbar)
+               : "memory");
+}
+
 // bounded wait for the phase with the given parity to complete
 __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
   for (long long i = 0; i < kTcWaitPolls; ++i) {
@@ -127,9 +142,16 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16]) {
 // tc_close (all threads) at its end.
 struct TcState {
   uint32_t tmem;       // TMEM address of column 0, lane 0
-  uint32_t mbar[2];    // shared addresses of the two mbarriers
+  uint32_t mbar[2];    // shared addresses of the two mbarriers the MMAs complete on
   uint32_t phase[2];   // parity of the next phase to wait for on each
+  uint32_t cbar[2];    // and of the two the bulk copies of constant operands complete on
+  uint32_t cphase[2];
+  uint32_t xbar;       // one more for a caller's own bulk copies
+  uint32_t xphase;
 };
+
+// mbarriers tc_open sets up (s_mbar of tc_open holds this many)
+constexpr int kTcBarriers = 5;
 
 __device__ __forceinline__ void tc_open(TcState& tc, uint32_t* s_tmem, unsigned long long* s_mbar) {
   if (threadIdx.x < 32) {
@@ -138,10 +160,8 @@ __device__ __forceinline__ void tc_open(TcState& tc, uint32_t* s_tmem, unsigned 
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
-  if (threadIdx.x == 32) {
-    mbar_init(smem_u32(s_mbar), 1);
-    mbar_init(smem_u32(s_mbar + 1), 1);
-  }
+  if (threadIdx.x == 32)
+    for (int q = 0; q < kTcBarriers; ++q) mbar_init(smem_u32(s_mbar + q), 1);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -149,6 +169,11 @@ __device__ __forceinline__ void tc_open(TcState& tc, uint32_t* s_tmem, unsigned 
   tc.mbar[0] = smem_u32(s_mbar);
   tc.mbar[1] = smem_u32(s_mbar + 1);
   tc.phase[0] = tc.phase[1] = 0;
+  tc.cbar[0] = smem_u32(s_mbar + 2);
+  tc.cbar[1] = smem_u32(s_mbar + 3);
+  tc.cphase[0] = tc.cphase[1] = 0;
+  tc.xbar = smem_u32(s_mbar + 4);
+  tc.xphase = 0;
 }
 
 __device__ __forceinline__ void tc_close(const TcState& tc) {
@@ -207,17 +232,6 @@ __device__ __forceinline__ void tc_put4(unsigned char* hi, unsigned char* lo, ui
 // lane loads four rows at each of four k and transposes them in registers).
 __device__ __forceinline__ void tc_stage(const TcOperand& o, int r0, int nrows, int k0, int kc, unsigned char* hi,
                                          unsigned char* lo) {
-  if (o.img) {   // rows r0 .. r0 + nrows of the chunk's image (r0 a multiple of 8)
-    const size_t half = (size_t)o.img_groups * kTcSbo;
-    const unsigned char* src = o.img + (size_t)(k0 / kTcKc) * 2 * half + (size_t)(r0 >> 3) * kTcSbo;
-    const int n16 = (nrows >> 3) * (kTcSbo / 16);
-    for (int e = threadIdx.x; e < 2 * n16; e += blockDim.x) {
-      const int h = e >= n16 ? 1 : 0, u = e - h * n16;
-      const uint4 v = reinterpret_cast<const uint4*>(src + h * half)[u];
-      reinterpret_cast<uint4*>(h ? lo : hi)[u] = v;
-    }
-    return;
-  }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int nk4 = kc >> 2, kg = (nk4 + 3) >> 2;
   const bool vec = tc_vec(o);
@@ -265,6 +279,20 @@ __device__ __forceinline__ void tc_stage(const TcOperand& o, int r0, int nrows, 
   }
 }
 
+// A constant operand's rows [r0, r0 + nrows) (r0 a multiple of 8, nrows of
+// 16) of the chunk at k0, copied from its image by the copy engine: two
+// contiguous runs of (nrows / 8) groups, the hi and the lo half, completing
+// on mbar. Issued by one thread; the image holds a whole 128-row tile past
+// any r0 and its offsets are multiples of 16 bytes.
+__device__ __forceinline__ void tc_image_async(const TcOperand& o, int r0, int nrows, int k0, unsigned char* hi,
+                                               unsigned char* lo, uint32_t mbar) {
+  const size_t half = (size_t)o.img_groups * kTcSbo;
+  const unsigned char* src = o.img + (size_t)(k0 / kTcKc) * 2 * half + (size_t)(r0 >> 3) * kTcSbo;
+  const uint32_t bytes = (uint32_t)(nrows >> 3) * kTcSbo;
+  bulk_g2s(smem_u32(hi), src, bytes, mbar);
+  bulk_g2s(smem_u32(lo), src + half, bytes, mbar);
+}
+
 // Bytes of one staging buffer for an accumulator of width N: the hi and lo
 // chunks of A (128 rows) and of B (N rows).
 __host__ __device__ constexpr size_t tc_buffer_bytes(int N) { return 2 * (size_t)((kTcM + N) / 8) * kTcSbo; }
@@ -299,10 +327,32 @@ __device__ inline bool tc_gemm(TcState& tc, int N, int K, const TcOperand& a, in
     unsigned char* Blo = Bhi + b_bytes;
     const int k0 = c * kTcKc;
     const int kc = (K - k0 < kTcKc) ? ((K - k0 + 7) & ~7) : kTcKc;   // the last chunk, padded to a K step
-    tc_stage(a, a_r0, kTcM, k0, kc, Ahi, Alo);
-    tc_stage(b, b_r0, N, k0, kc, Bhi, Blo);
+    // constant operands by the copy engine (in flight while the threads stage
+    // the data operand), data operands by the threads
+    const uint32_t tx = (a.img ? 2 * a_bytes : 0u) + (b.img ? 2 * b_bytes : 0u);
+    const uint32_t cb = q ? tc.cbar[1] : tc.cbar[0];
+    if (tx && threadIdx.x == 0) {
+      fence_async_smem();   // this buffer's earlier generic-proxy writes before the copy's
+      mbar_expect_tx(cb, tx);
+      if (a.img) tc_image_async(a, a_r0, kTcM, k0, Ahi, Alo, cb);
+      if (b.img) tc_image_async(b, b_r0, N, k0, Bhi, Blo, cb);
+    }
+    if (!a.img) tc_stage(a, a_r0, kTcM, k0, kc, Ahi, Alo);
+    if (!b.img) tc_stage(b, b_r0, N, k0, kc, Bhi, Blo);
+    bool copied = true;
+    if (tx) {
+      const uint32_t par = q ? tc.cphase[1] : tc.cphase[0];
+      copied = mbar_wait(cb, par);
+      if (!copied) mbar_wait(cb, par);   // gave up: a second bounded wait for the copies in flight
+      if (q) tc.cphase[1] ^= 1u; else tc.cphase[0] ^= 1u;
+    }
     fence_async_smem();
-    __syncthreads();
+    if (__syncthreads_or(!copied)) {
+      if (threadIdx.x == 0) atomicExch(&st->err, kErrBarrier);
+      // the MMAs already issued complete on their barriers: bounded waits before leaving
+      for (int p = c >= 1 ? c - 1 : 0; p < c; ++p) wait_buffer(p & 1);
+      return false;
+    }
     if (threadIdx.x == 0) {
       tc_fence_after();
       const uint32_t ah = smem_u32(Ahi), al = smem_u32(Alo), bh = smem_u32(Bhi), bl = smem_u32(Blo);
