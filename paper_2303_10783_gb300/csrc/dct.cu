@@ -1006,11 +1006,19 @@ __device__ bool helmholtz_team(const DctArgs<float>& A, const Sys& S, int has_z,
     Vec<1> s1 = {{0.0}};
     float f1 = 0.f;
     int nf = 0;
-    for (int c = t0; c < n; c += gsz) {
-      const float rv = to_f32_scaled(res64(b[c], S.a, x, c, sy, sz, has_z), pe, ps);
-      rs[c] = rv;
-      f1 = fmaf(rv, rv, f1);
-      if (++nf == kNormChunk) {
+    // two rows per pass (the second a repeat of the first past the end, then
+    // dropped): two independent FP64 chains, whose loads overlap
+    for (int c = t0; c < n; c += 2 * gsz) {
+      const bool two = c + gsz < n;
+      const int c2 = two ? c + gsz : c;
+      const double r1 = res64(b[c], S.a, x, c, sy, sz, has_z);
+      const double r2 = res64(b[c2], S.a, x, c2, sy, sz, has_z);
+      const float v1 = to_f32_scaled(r1, pe, ps), v2 = two ? to_f32_scaled(r2, pe, ps) : 0.f;
+      rs[c] = v1;
+      if (two) rs[c2] = v2;
+      f1 = fmaf(v2, v2, fmaf(v1, v1, f1));
+      nf += 2;
+      if (nf >= kNormChunk) {
         s1.v[0] += f1;
         f1 = 0.f;
         nf = 0;

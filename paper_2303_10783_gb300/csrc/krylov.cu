@@ -834,12 +834,24 @@ __device__ __forceinline__ double ir_residual(const BcgArgs& A, int t0, int gs, 
   const int sy = A.sys.d.mx, sz = A.sys.d.mx * A.sys.d.my;
   const double* b = A.sys.b;
   double s = 0.0, sb = 0.0;
-  for (int i = t0; i < n; i += gs) {
-    const double ri = res_row64(b[i], A.sys.a, A.sys.x, i, sy, sz, A.has_z);
-    A.v64.r[i] = ri;
-    r32[i] = to_f32(ri);
-    s += ri * ri;
-    if (bb) sb += b[i] * b[i];
+  // two rows per pass (the second a repeat of the first past the end, then
+  // dropped): two independent FP64 chains, whose loads overlap
+  for (int i = t0; i < n; i += 2 * gs) {
+    const bool two = i + gs < n;
+    const int i2 = two ? i + gs : i;
+    const double b1 = b[i], b2 = b[i2];
+    const double r1 = res_row64(b1, A.sys.a, A.sys.x, i, sy, sz, A.has_z);
+    const double r2 = res_row64(b2, A.sys.a, A.sys.x, i2, sy, sz, A.has_z);
+    A.v64.r[i] = r1;
+    r32[i] = to_f32(r1);
+    s += r1 * r1;
+    if (bb) sb += b1 * b1;
+    if (two) {
+      A.v64.r[i2] = r2;
+      r32[i2] = to_f32(r2);
+      s += r2 * r2;
+      if (bb) sb += b2 * b2;
+    }
   }
   if (bb) *bb = sb;
   return s;
