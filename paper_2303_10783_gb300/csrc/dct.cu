@@ -823,25 +823,42 @@ __device__ bool poisson_dct_team(const DctArgs<TP>& A, const Team& tm, TP* sm, T
     Vec<2> s = {{0.0, 0.0}};
     float f0 = 0.f, f1 = 0.f;   // FP32 partial sums of r * ps (FP32 path)
     int nf = 0;
-    for (int c = t0; c < n; c += gsz) {
-      int i, j, k;
+    // two rows per pass (the second a repeat of the first past the end, then
+    // dropped): two independent FP64 chains, whose loads overlap
+    auto code_of = [&](int i, int j, int k) {
+      return ((i > 0) + (i < A.nx - 1)) + 3 * ((j > 0) + (j < A.ny - 1)) + 9 * ((k > 0) + (k < A.nz - 1));
+    };
+    for (int c = t0; c < n; c += 2 * gsz) {
+      const bool two = c + gsz < n;
+      const int c2 = two ? c + gsz : c;
+      int i, j, k, i2, j2, k2;
       decompose3(c, A.fx, A.fy, i, j, k);
-      const int code = ((i > 0) + (i < A.nx - 1)) + 3 * ((j > 0) + (j < A.ny - 1)) + 9 * ((k > 0) + (k < A.nz - 1));
-      const double rc = res_lap64(b[c], x, c, i, j, k, A.nx, A.ny, A.nz, A.cx, A.cy, A.cz, s_diag[code]);
-      const TP rv = narrow_scaled<TP>(rc, pe, ps);
-      rs[c] = rv;
+      decompose3(c2, A.fx, A.fy, i2, j2, k2);
+      const double r1 = res_lap64(b[c], x, c, i, j, k, A.nx, A.ny, A.nz, A.cx, A.cy, A.cz, s_diag[code_of(i, j, k)]);
+      const double r2 =
+          res_lap64(b[c2], x, c2, i2, j2, k2, A.nx, A.ny, A.nz, A.cx, A.cy, A.cz, s_diag[code_of(i2, j2, k2)]);
+      const TP v1 = narrow_scaled<TP>(r1, pe, ps), v2 = narrow_scaled<TP>(r2, pe, ps);
+      rs[c] = v1;
+      if (two) rs[c2] = v2;
       if constexpr (f32) {
-        f0 += rv;
-        f1 = fmaf(rv, rv, f1);
-        if (++nf == kNormChunk) {
+        const float w2 = two ? v2 : 0.f;
+        f0 += v1;
+        f0 += w2;
+        f1 = fmaf(w2, w2, fmaf(v1, v1, f1));
+        nf += 2;
+        if (nf >= kNormChunk) {
           s.v[0] += f0;
           s.v[1] += f1;
           f0 = f1 = 0.f;
           nf = 0;
         }
       } else {
-        s.v[0] += rc;
-        s.v[1] += rc * rc;
+        s.v[0] += r1;
+        s.v[1] += r1 * r1;
+        if (two) {
+          s.v[0] += r2;
+          s.v[1] += r2 * r2;
+        }
       }
     }
     if constexpr (f32) {
