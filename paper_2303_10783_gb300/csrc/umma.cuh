@@ -13,7 +13,10 @@
 // kTcSbo = 32 kTcKc + 16 bytes apart (stride byte offset) for a chunk of
 // kTcKc values of K. The extra 16 bytes put the rows of a group and the
 // groups on different shared-memory banks, so the 16-byte stores of the
-// staging threads are conflict-free.
+// staging threads are conflict-free. Constant operands (cosine matrices)
+// are stored once in exactly this layout and come into the staging buffers
+// by bulk copies (cp.async.bulk) that complete on an mbarrier per buffer,
+// while the threads stage the data operand.
 //
 // Accumulator: M = 128 rows, row i in TMEM lane i, column j in TMEM column
 // j (32-bit). Warp w reads lanes 32 (w % 4) .. 32 (w % 4) + 31.
@@ -198,7 +201,7 @@ struct TcOperand {
   int rfast;
   // or, for a constant operand, its image in the staged layout (per chunk of
   // kTcKc values of K: the hi then the lo half, each img_groups 8-row groups
-  // of kTcSbo bytes), copied 16 bytes at a time
+  // of kTcSbo bytes), which the copy engine brings in (tc_image_async)
   const unsigned char* img = nullptr;
   int img_groups = 0;
 };
