@@ -1403,7 +1403,18 @@ __global__ void k_thomas_table(float* inv, const float* lx, const float* ly, flo
 }  // namespace
 
 size_t dct_thomas_bytes(const DctPlan& pl) {
-  return (pl.fp32 && pl.dim == 3) ? 2 * (size_t)pl.Mx * pl.My * pl.Mt * sizeof(float) : 0;
+  if (!pl.fp32 || pl.dim != 3) return 0;
+  // only the slab solves read the tables: the tensor-core slab (any mode but
+  // off) or the shared-memory slab (tensor cores off)
+  DctPlan q = pl;
+  int cols, slab, tc, tc_ac, tc_slab;
+  q.tc_mode = SS_TC_AUTO;
+  smem_bytes<float>(q, &cols, &slab, &tc, &tc_ac, &tc_slab);
+  const bool slab_tc = tc_slab != 0;
+  q.tc_mode = SS_TC_OFF;
+  smem_bytes<float>(q, &cols, &slab, &tc, &tc_ac, &tc_slab);
+  if (!slab_tc && !slab) return 0;
+  return 2 * (size_t)pl.Mx * pl.My * pl.Mt * sizeof(float);
 }
 
 cudaError_t dct_thomas_ensure(DctPlan& pl, const Params& pr, cudaStream_t s) {
